@@ -1,0 +1,181 @@
+/*
+ * hmc.h -- C ABI of the GB300 subset-HMC library (libhmc.so).
+ *
+ * The library runs the hot path of the hybrid VI-HMC method of arXiv
+ * 2507.14652: full-batch Hamiltonian Monte Carlo over a selected subset
+ * Theta_s of a network's parameters, the rest Theta_~s held at caller-supplied
+ * values (Sec. 3.2 and Algorithm 2).  Every step runs in CUDA kernels on one GPU.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * Parameter order: for each Linear layer in order, W[out][in] row-major, then
+ *   b[out] if the layer has a bias.  A DeepONet lists all branch layers, then
+ *   all trunk layers, then its scalar output bias b0.  P = total count.
+ * Subset: subset_mask[P] (1 = sampled).  The sampled entries, in ascending
+ *   parameter index, form the position vector q of length k.
+ * Energy (Sec. 2.2, constants Z and normalisers dropped):
+ *   U(q) = sum over data terms (F(x) - y)^2 / (2 sigma^2) + sum_j q_j^2 / (2 alpha^2)
+ *   with sigma = noise_sigma (Gaussian likelihood over the full batch) and
+ *   alpha = prior_sigma (N(0, alpha^2) prior on the sampled parameters only).
+ * Kinetic energy K(p) = p.p / 2 (mass matrix M = I); H = U + K.
+ * Precision of q, p, grad and samples: double for HMC_PREC_FP64, float for
+ *   every other precision.  U and dH are always double.
+ * Pointers: every array argument may be host or device memory (detected with
+ *   cudaPointerGetAttributes).  Device arrays must be contiguous, row-major
+ *   and stay owned by the caller.  Work is queued on the handle's stream;
+ *   when an output is host memory the call copies it back and synchronises
+ *   before returning, otherwise it returns without waiting.
+ * Errors: every call returns an hmc_status; hmc_last_error() gives the
+ *   message of the last failure on the calling thread.  No call aborts, throws
+ *   across the ABI or traps on the device.
+ */
+#ifndef HMC_H
+#define HMC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HMC_MAX_LAYERS 16
+
+/* Symbols of the C ABI are exported even when the library hides everything else. */
+#if defined(__GNUC__)
+#define HMC_API __attribute__((visibility("default")))
+#else
+#define HMC_API
+#endif
+
+typedef struct hmc_handle_s *hmc_handle;
+
+typedef enum {
+    HMC_OK = 0,
+    HMC_ERR_ARG = 1,          /* invalid argument (sizes, spec, pointers) */
+    HMC_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    HMC_ERR_OOM = 3,          /* device allocation failed */
+    HMC_ERR_NONFINITE = 4,    /* U was NaN or +-Inf (outputs are still written) */
+    HMC_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out */
+    HMC_ERR_UNSUPPORTED = 6   /* valid request this build does not implement */
+} hmc_status;
+
+typedef enum { HMC_ACT_IDENTITY = 0, HMC_ACT_TANH = 1, HMC_ACT_SIN = 2 } hmc_act;
+
+/* Arithmetic of the network evaluation.  FP64 and FP32 run plain CUDA-core
+ * kernels.  BF16 runs the wide layers on tcgen05 tensor cores (bf16 operands,
+ * fp32 accumulation) with fp32 positions/momenta and fp64 energy sums. */
+typedef enum { HMC_PREC_FP64 = 0, HMC_PREC_FP32 = 1, HMC_PREC_TF32 = 2, HMC_PREC_BF16 = 3 } hmc_prec;
+
+typedef enum { HMC_NET_MLP = 0, HMC_NET_DEEPONET = 1 } hmc_net_kind;
+
+/* One feed-forward stack: widths[0] inputs, widths[n_layers] outputs;
+ * act[l] and has_bias[l] for Linear layer l. */
+typedef struct {
+    int n_layers;
+    int widths[HMC_MAX_LAYERS + 1];
+    int act[HMC_MAX_LAYERS];
+    int has_bias[HMC_MAX_LAYERS];
+} hmc_mlp_spec;
+
+/* An MLP (kind = HMC_NET_MLP, uses `net`) or a DeepONet (uses `branch` and
+ * `trunk`, whose output widths must match; output = <branch(u), trunk(y)> + b0,
+ * Sec. 4.2 and App. A). */
+typedef struct {
+    int kind;
+    hmc_mlp_spec net;
+    hmc_mlp_spec branch;
+    hmc_mlp_spec trunk;
+    int deeponet_out_bias;   /* 1 = scalar b0 present */
+    int prec;                /* hmc_prec */
+} hmc_net_spec;
+
+/* Training set, FP64, host or device.  MLP: x[n][dx], y[n][dout].
+ * DeepONet (aligned): u[n_u][du] input functions, yq[n_y][dy] query points
+ * shared by all functions, t[n_u][n_y] targets.  Unused fields are ignored. */
+typedef struct {
+    const double *x; long n; int dx;
+    const double *y;
+    const double *u; long n_u; int du;
+    const double *yq; long n_y; int dy;
+    const double *t;
+} hmc_data;
+
+/*
+ * Create a sampler for one problem (Algorithm 2 after its subset is fixed).
+ *   spec          network and precision
+ *   data          training set (copied to the device and converted)
+ *   prior_sigma   alpha > 0, noise_sigma = sigma > 0
+ *   subset_mask   [P] bytes, 1 = sampled (the set Theta_s); k = its popcount, k >= 1
+ *   frozen_params [P] doubles; entries off the subset are held fixed (Theta_~s = mu_~s)
+ *   n_chains      C >= 1 independent chains, batched inside every launch
+ *   cuda_stream   cudaStream_t to queue all work on (NULL = legacy default stream)
+ * The handle copies everything it needs; the caller may free its arrays on return.
+ */
+HMC_API hmc_status hmc_create(hmc_handle *out, const hmc_net_spec *spec, const hmc_data *data,
+                      double prior_sigma, double noise_sigma,
+                      const unsigned char *subset_mask, const double *frozen_params,
+                      int n_chains, void *cuda_stream);
+
+/*
+ * Create one handle over n_problems independent problems (each with its own
+ * spec, data, sigmas, mask and frozen vector, all with n_chains chains), whose
+ * launches cover every problem at once.  State vectors of a batch handle are
+ * packed per problem: q = [problem][chain][k_problem]; U, accepted and dH are
+ * [problem][chain] per trajectory.  Momenta of problem p use Philox stream p.
+ */
+HMC_API hmc_status hmc_create_batch(hmc_handle *out, int n_problems, const hmc_net_spec *specs,
+                            const hmc_data *data, const double *prior_sigma,
+                            const double *noise_sigma, const unsigned char *const *subset_masks,
+                            const double *const *frozen_params, int n_chains, void *cuda_stream);
+
+/* k (for a batch: the sum of k over problems), or -1 for a bad handle. */
+HMC_API long hmc_subset_size(hmc_handle h);
+
+/* P (for a batch: the sum over problems), or -1 for a bad handle. */
+HMC_API long hmc_param_count(hmc_handle h);
+
+/* Number of chains C, or -1. */
+HMC_API int hmc_num_chains(hmc_handle h);
+
+/*
+ * U and grad U for every chain (Sec. 2.2 potential; its gradient is the force of
+ * Hamilton's equations).  q [C][k] (batch: packed per problem) in the handle's
+ * position precision; U [C] doubles; grad [C][k] or NULL.  Returns
+ * HMC_ERR_NONFINITE (after writing the outputs) when U is a host array and some
+ * U is not finite.
+ */
+HMC_API hmc_status hmc_energy_grad(hmc_handle h, const void *q, double *U, void *grad);
+
+/*
+ * L leapfrog steps of size eps in place on (q, p) [C][k] (Sec. 2.2):
+ *   p -= eps/2 grad U(q); repeat L times { q += eps p; p -= eps grad U(q) }, the
+ *   last kick being eps/2.  L >= 0.
+ */
+HMC_API hmc_status hmc_leapfrog(hmc_handle h, void *q, void *p, double eps, int L);
+
+/*
+ * n_samples HMC trajectories per chain starting from q0 [C][k] (Algorithm 1 on
+ * the subset, as in Algorithm 2).  Trajectory t = first_traj + i draws
+ * p ~ N(0, I) from Philox4x64-10 keyed by seed (bit-identical to the reference
+ * generator), integrates L leapfrog steps of size eps, and accepts iff
+ * log u < H(q, p) - H(q*, p*) with u ~ U(0, 1] from the same generator (a
+ * non-finite difference rejects).  Outputs (any may be NULL):
+ *   samples  [n][C][k]  the chain state after each trajectory (repeats on rejection)
+ *   accepted [n][C]     1 = accepted
+ *   dH       [n][C]     H(q*, p*) - H(q, p)
+ *   q_last   [C][k]     final state
+ * Restarting from q_last with first_traj advanced by n continues the same chains.
+ */
+HMC_API hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_samples,
+                      unsigned long long seed, long first_traj,
+                      void *samples, unsigned char *accepted, double *dH, void *q_last);
+
+/* Free the handle and all its device memory. NULL is accepted. */
+HMC_API hmc_status hmc_destroy(hmc_handle h);
+
+/* Message of the last failed call on this thread ("" if none).  Owned by the library. */
+HMC_API const char *hmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMC_H */

@@ -1,0 +1,45 @@
+/*
+ * hmc_diag.h -- diagnostic entry points of libhmc.so, used by the tests to
+ * check the device random-number stream bit by bit against an independent
+ * implementation.  They allocate, compute on the legacy default stream and
+ * copy the result into the host array before returning.
+ */
+#ifndef HMC_DIAG_H
+#define HMC_DIAG_H
+
+#include "hmc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox4x64-10 (Salmon et al., SC'11) of n counters ctr[n][4] under keys
+ * key[n][2]; out_host[n][4] receives the output words. */
+HMC_API hmc_status hmc_diag_philox(const unsigned long long *ctr, const unsigned long long *key, long n,
+                           unsigned long long *out_host);
+
+/* Momentum components 0..k-1 of (problem, chain, traj) exactly as hmc_sample
+ * draws them (p ~ N(0, I), Algorithm 1), as doubles in out_host[k]. */
+HMC_API hmc_status hmc_diag_momenta(unsigned long long seed, unsigned long long problem, unsigned long long chain,
+                            unsigned long long traj, long k, double *out_host);
+
+/* log u of the Metropolis uniform (Algorithm 1) for chains 0..n_chain-1 and
+ * trajectories 0..n_traj-1: out_host[chain][traj]. */
+HMC_API hmc_status hmc_diag_log_uniform(unsigned long long seed, unsigned long long problem, long n_chain, long n_traj,
+                                double *out_host);
+
+/* One batched BF16 tensor-core GEMM on the library's tcgen05 pipeline (TMA ->
+ * shared memory -> tcgen05.mma -> TMEM -> registers), FP32 result:
+ *   C[b][m][n] = sum_k A(m, k) B(n, k),  b < batch.
+ * A is [batch][M][K] (a_mn = 0, K-major) or [batch][K][M] (a_mn = 1);
+ * B is [batch][N][K] (b_mn = 0) or [batch][K][N] (b_mn = 1); all device pointers,
+ * bf16, row-major.  N must be 64, 128, 192 or 256; M and K multiples of 8.
+ * Synchronises the device before returning. */
+HMC_API hmc_status hmc_diag_umma_gemm(int M, int N, int K, int batch, int a_mn, int b_mn, const void *A,
+                                      const void *B, float *C);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMC_DIAG_H */

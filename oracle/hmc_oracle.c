@@ -461,6 +461,7 @@ void or_leapfrog(const or_problem *pr, double *q, double *p, double eps, int L, 
 {
     long k = pr->k;
     double half = 0.5 * eps;
+    if (L <= 0) return;   /* zero steps: the identity map */
     for (long j = 0; j < k; ++j) p[j] = p[j] - half * g[j];
     for (int s = 1; s <= L; ++s) {
         for (long j = 0; j < k; ++j) q[j] = q[j] + eps * p[j];

@@ -1,0 +1,347 @@
+"""Python binding of libhmc.so -- the GB300 subset-HMC library.
+
+Argument marshalling only: every step of U, grad U, the leapfrog integrator and
+the Metropolis step runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: if the compiled library is missing
+the import of :func:`lib` raises.
+
+Typical use::
+
+    import paper_2507_14652_gb300 as hmc
+    s = hmc.Sampler.mlp([2, 256, 256, 1], x, y, mask, frozen, chains=16,
+                        prior_sigma=1.0, noise_sigma=0.05, prec=hmc.PREC_BF16)
+    U, g = s.energy_grad(q)                      # torch CUDA tensors
+    S, acc, dH, q_last = s.sample(q0, eps=5e-4, L=50, n=100, seed=0)
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhmc.so")
+MAXL = 16
+
+ACT_IDENTITY, ACT_TANH, ACT_SIN = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2, 3
+NET_MLP, NET_DEEPONET = 0, 1
+STATUS = {0: "HMC_OK", 1: "HMC_ERR_ARG", 2: "HMC_ERR_CUDA", 3: "HMC_ERR_OOM", 4: "HMC_ERR_NONFINITE",
+          5: "HMC_ERR_TIMEOUT", 6: "HMC_ERR_UNSUPPORTED"}
+
+# every symbol the C ABI (include/hmc.h, include/hmc_diag.h) declares
+EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_subset_size", "hmc_param_count", "hmc_num_chains",
+           "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_destroy", "hmc_last_error",
+           "hmc_diag_philox", "hmc_diag_momenta", "hmc_diag_log_uniform"]
+
+
+class HmcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MlpSpec(ct.Structure):
+    _fields_ = [("n_layers", ct.c_int), ("widths", ct.c_int * (MAXL + 1)),
+                ("act", ct.c_int * MAXL), ("has_bias", ct.c_int * MAXL)]
+
+
+class NetSpec(ct.Structure):
+    _fields_ = [("kind", ct.c_int), ("net", MlpSpec), ("branch", MlpSpec), ("trunk", MlpSpec),
+                ("deeponet_out_bias", ct.c_int), ("prec", ct.c_int)]
+
+
+class Data(ct.Structure):
+    _fields_ = [("x", ct.c_void_p), ("n", ct.c_long), ("dx", ct.c_int), ("y", ct.c_void_p),
+                ("u", ct.c_void_p), ("n_u", ct.c_long), ("du", ct.c_int),
+                ("yq", ct.c_void_p), ("n_y", ct.c_long), ("dy", ct.c_int), ("t", ct.c_void_p)]
+
+
+_lib = None
+
+
+def build(force=False, verbose=False):
+    from . import _build
+    return _build.build(force=force, verbose=verbose)
+
+
+def lib():
+    """Load libhmc.so.  Raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2507_14652_gb300.build() first")
+        L = ct.CDLL(LIB_PATH)
+        vp, d, i, lg, u64 = ct.c_void_p, ct.c_double, ct.c_int, ct.c_long, ct.c_ulonglong
+        L.hmc_create.argtypes = [ct.POINTER(vp), ct.POINTER(NetSpec), ct.POINTER(Data), d, d, vp, vp, i, vp]
+        L.hmc_create_batch.argtypes = [ct.POINTER(vp), i, ct.POINTER(NetSpec), ct.POINTER(Data),
+                                       ct.POINTER(d), ct.POINTER(d), ct.POINTER(vp), ct.POINTER(vp), i, vp]
+        L.hmc_subset_size.argtypes = [vp]
+        L.hmc_subset_size.restype = lg
+        L.hmc_param_count.argtypes = [vp]
+        L.hmc_param_count.restype = lg
+        L.hmc_num_chains.argtypes = [vp]
+        L.hmc_num_chains.restype = i
+        L.hmc_energy_grad.argtypes = [vp, vp, vp, vp]
+        L.hmc_leapfrog.argtypes = [vp, vp, vp, d, i]
+        L.hmc_sample.argtypes = [vp, vp, d, i, lg, u64, lg, vp, vp, vp, vp]
+        L.hmc_destroy.argtypes = [vp]
+        L.hmc_last_error.restype = ct.c_char_p
+        L.hmc_diag_philox.argtypes = [vp, vp, lg, vp]
+        L.hmc_diag_momenta.argtypes = [u64, u64, u64, u64, lg, vp]
+        L.hmc_diag_log_uniform.argtypes = [u64, u64, lg, lg, vp]
+        for f in EXPORTS:
+            if f not in ("hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_last_error"):
+                getattr(L, f).restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != 0:
+        raise HmcError(st, lib().hmc_last_error().decode())
+
+
+def mlp_spec(widths, act=None, bias=True):
+    """MlpSpec from widths; default act: tanh hidden layers, identity output."""
+    s = MlpSpec()
+    n = len(widths) - 1
+    assert 1 <= n <= MAXL
+    if act is None:
+        act = [ACT_TANH] * (n - 1) + [ACT_IDENTITY]
+    if isinstance(bias, bool):
+        bias = [bias] * n
+    s.n_layers = n
+    for l, w in enumerate(widths):
+        s.widths[l] = int(w)
+    for l in range(n):
+        s.act[l] = int(act[l])
+        s.has_bias[l] = 1 if bias[l] else 0
+    return s
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array (host) or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _f64(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float64)
+    import torch
+    return a.detach().to(torch.float64).contiguous()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Sampler:
+    """One libhmc handle: a problem (or a batch of problems) with C chains."""
+
+    def __init__(self, spec, data, arrays, prior_sigma, noise_sigma, mask, frozen, chains, stream=None):
+        import torch
+        self.prec = spec.prec
+        self.dtype = torch.float64 if spec.prec == PREC_FP64 else torch.float32
+        self._keep = list(arrays)
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+        f = _f64(np.asarray(frozen)) if not hasattr(frozen, "data_ptr") else _f64(frozen)
+        self._keep += [m, f]
+        h = ct.c_void_p()
+        _check(lib().hmc_create(ct.byref(h), ct.byref(spec), ct.byref(data), float(prior_sigma),
+                                float(noise_sigma), _ptr(m), _ptr(f), int(chains), _stream_ptr(stream)))
+        self._h = h
+        self.chains = int(chains)
+        self.k = int(lib().hmc_subset_size(h))
+        self.P = int(lib().hmc_param_count(h))
+        self.n_problems = 1
+
+    @classmethod
+    def mlp(cls, widths, x, y, mask, frozen, chains, prior_sigma=1.0, noise_sigma=1.0, prec=PREC_FP32,
+            act=None, bias=True, stream=None):
+        spec = NetSpec()
+        spec.kind = NET_MLP
+        spec.net = mlp_spec(widths, act, bias)
+        spec.prec = prec
+        x, y = _f64(x), _f64(y)
+        d = Data()
+        d.x, d.n, d.dx, d.y = _ptr(x), x.shape[0], x.shape[1], _ptr(y)
+        return cls(spec, d, [x, y], prior_sigma, noise_sigma, mask, frozen, chains, stream)
+
+    @classmethod
+    def deeponet(cls, branch, trunk, u, yq, t, mask, frozen, chains, prior_sigma=1.0, noise_sigma=1.0,
+                 prec=PREC_FP32, out_bias=True, branch_act=None, trunk_act=None, branch_bias=True,
+                 trunk_bias=True, stream=None):
+        spec = NetSpec()
+        spec.kind = NET_DEEPONET
+        spec.branch = mlp_spec(branch, branch_act, branch_bias)
+        spec.trunk = mlp_spec(trunk, trunk_act, trunk_bias)
+        spec.deeponet_out_bias = 1 if out_bias else 0
+        spec.prec = prec
+        u, yq, t = _f64(u), _f64(yq), _f64(t)
+        d = Data()
+        d.u, d.n_u, d.du = _ptr(u), u.shape[0], u.shape[1]
+        d.yq, d.n_y, d.dy = _ptr(yq), yq.shape[0], yq.shape[1]
+        d.t = _ptr(t)
+        return cls(spec, d, [u, yq, t], prior_sigma, noise_sigma, mask, frozen, chains, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().hmc_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _state(self, q):
+        import torch
+        if isinstance(q, np.ndarray):
+            q = torch.from_numpy(q)
+        return q.to(device="cuda", dtype=self.dtype).contiguous()
+
+    def energy_grad(self, q, want_grad=True):
+        """U [C] (float64) and grad U [C][k] for states q [C][k] (CUDA tensors)."""
+        import torch
+        q = self._state(q)
+        U = torch.empty(self.n_problems * self.chains, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(q) if want_grad else None
+        _check(lib().hmc_energy_grad(self._h, _ptr(q), _ptr(U), _ptr(g)))
+        return U, g
+
+    def leapfrog(self, q, p, eps, L):
+        q = self._state(q).clone()
+        p = self._state(p).clone()
+        _check(lib().hmc_leapfrog(self._h, _ptr(q), _ptr(p), float(eps), int(L)))
+        return q, p
+
+    def sample(self, q0, eps, L, n, seed=0, first_traj=0, keep_samples=True):
+        """n trajectories per chain; returns (samples [n][C][k], accepted [n][C], dH [n][C], q_last [C][k])."""
+        import torch
+        q0 = self._state(q0)
+        nseg = self.n_problems * self.chains
+        S = torch.empty((n,) + tuple(q0.shape), dtype=self.dtype, device="cuda") if keep_samples else None
+        acc = torch.empty((n, nseg), dtype=torch.uint8, device="cuda")
+        dH = torch.empty((n, nseg), dtype=torch.float64, device="cuda")
+        ql = torch.empty_like(q0)
+        _check(lib().hmc_sample(self._h, _ptr(q0), float(eps), int(L), int(n), int(seed), int(first_traj),
+                                _ptr(S), _ptr(acc), _ptr(dH), _ptr(ql)))
+        return S, acc, dH, ql
+
+    def sample_host(self, q0, eps, L, n, seed=0, first_traj=0):
+        """Same as sample() with numpy (host) buffers: the library stages the copies."""
+        dt = np.float64 if self.prec == PREC_FP64 else np.float32
+        q0 = np.ascontiguousarray(q0, dtype=dt)
+        nseg = self.n_problems * self.chains
+        S = np.empty((n,) + q0.shape, dtype=dt)
+        acc = np.empty((n, nseg), dtype=np.uint8)
+        dH = np.empty((n, nseg), dtype=np.float64)
+        ql = np.empty_like(q0)
+        _check(lib().hmc_sample(self._h, _ptr(q0), float(eps), int(L), int(n), int(seed), int(first_traj),
+                                _ptr(S), _ptr(acc), _ptr(dH), _ptr(ql)))
+        return S, acc, dH, ql
+
+
+class BatchSampler(Sampler):
+    """Several independent problems behind one handle (hmc_create_batch)."""
+
+    def __init__(self, problems, chains, prec, stream=None):
+        n = len(problems)
+        specs = (NetSpec * n)()
+        datas = (Data * n)()
+        alphas = (ct.c_double * n)()
+        sigmas = (ct.c_double * n)()
+        masks = (ct.c_void_p * n)()
+        frozens = (ct.c_void_p * n)()
+        keep = []
+        for i, pr in enumerate(problems):
+            widths, x, y, mask, frozen, alpha, sigma = pr
+            specs[i].kind = NET_MLP
+            specs[i].net = mlp_spec(widths)
+            specs[i].prec = prec
+            x, y = _f64(x), _f64(y)
+            m = np.ascontiguousarray(mask, dtype=np.uint8)
+            f = _f64(np.asarray(frozen))
+            keep += [x, y, m, f]
+            datas[i].x, datas[i].n, datas[i].dx, datas[i].y = _ptr(x), x.shape[0], x.shape[1], _ptr(y)
+            alphas[i], sigmas[i] = alpha, sigma
+            masks[i], frozens[i] = _ptr(m), _ptr(f)
+        import torch
+        self.prec = prec
+        self.dtype = torch.float64 if prec == PREC_FP64 else torch.float32
+        self._keep = keep
+        h = ct.c_void_p()
+        _check(lib().hmc_create_batch(ct.byref(h), n, specs, datas, alphas, sigmas, masks, frozens, int(chains),
+                                      _stream_ptr(stream)))
+        self._h = h
+        self.chains = int(chains)
+        self.n_problems = n
+        self.k = int(lib().hmc_subset_size(h))
+        self.P = int(lib().hmc_param_count(h))
+
+
+def _energy_grad_fn():
+    import torch
+
+    class EnergyGrad(torch.autograd.Function):
+        """U(q) per chain with the library's hand-written adjoint as its backward.
+
+        forward(q [C][k], sampler) -> U [C] (float64); backward multiplies the stored
+        grad U by the upstream gradient of each chain's U.
+        """
+
+        @staticmethod
+        def forward(ctx, q, sampler):
+            U, g = sampler.energy_grad(q.detach())
+            ctx.save_for_backward(g)
+            return U
+
+        @staticmethod
+        def backward(ctx, gU):
+            (g,) = ctx.saved_tensors
+            return (gU.to(g.dtype)[:, None] * g), None
+
+    return EnergyGrad
+
+
+_EG = None
+
+
+def energy(q, sampler):
+    """Differentiable U(q): torch.autograd sees the library's adjoint kernel as the gradient."""
+    global _EG
+    if _EG is None:
+        _EG = _energy_grad_fn()
+    return _EG.apply(q, sampler)
+
+
+def diag_philox(ctr, key):
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint64).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint64).reshape(-1, 2)
+    out = np.zeros_like(ctr)
+    _check(lib().hmc_diag_philox(_ptr(ctr), _ptr(key), ctr.shape[0], _ptr(out)))
+    return out
+
+
+def diag_momenta(seed, chain, traj, k, problem=0):
+    out = np.zeros(k)
+    _check(lib().hmc_diag_momenta(int(seed), int(problem), int(chain), int(traj), int(k), _ptr(out)))
+    return out
+
+
+def diag_log_uniform(seed, n_chain, n_traj, problem=0):
+    out = np.zeros((n_chain, n_traj))
+    _check(lib().hmc_diag_log_uniform(int(seed), int(problem), int(n_chain), int(n_traj), _ptr(out)))
+    return out

@@ -1,0 +1,744 @@
+// hmc_capi.cu -- the C ABI (include/hmc.h): handles, argument checks, and the
+// trajectory kernels that implement Algorithm 1 on the sampled subset
+// (Algorithm 2): momentum draw, leapfrog kicks/drifts with the scatter of q into
+// the network, kinetic energy and the Metropolis step.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "hmc_internal.cuh"
+#include "k_rng.cuh"
+#include "hmc_diag.h"
+
+namespace hmc {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+void DevBuf::alloc(size_t bytes)
+{
+    if (ptr) {
+        cudaFree(ptr);
+        ptr = nullptr;
+    }
+    n = bytes;
+    if (bytes == 0) return;
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+        throw Fail{e == cudaErrorMemoryAllocation ? HMC_ERR_OOM : HMC_ERR_CUDA};
+    }
+}
+
+DevBuf::~DevBuf()
+{
+    if (ptr) cudaFree(ptr);
+}
+
+void build_net_desc(NetDesc &nd, const hmc_mlp_spec &s, long base, const std::vector<long> &idx)
+{
+    nd.L = s.n_layers;
+    long off = base;
+    for (int l = 0; l <= nd.L; ++l) nd.w[l] = s.widths[l];
+    for (int l = 0; l < nd.L; ++l) {
+        nd.act[l] = s.act[l];
+        nd.bias[l] = s.has_bias[l] ? 1 : 0;
+        nd.woff[l] = off;
+        off += (long)nd.w[l + 1] * nd.w[l];
+        nd.boff[l] = -1;
+        if (nd.bias[l]) {
+            nd.boff[l] = off;
+            off += nd.w[l + 1];
+        }
+    }
+    nd.base = base;
+    nd.P = off - base;
+    nd.any_sampled = false;
+    nd.lmin = nd.L;
+    for (int l = 0; l < nd.L; ++l) {
+        long lo = nd.woff[l];
+        long hi = nd.woff[l] + (long)nd.w[l + 1] * nd.w[l] + (nd.bias[l] ? nd.w[l + 1] : 0);
+        auto it = std::lower_bound(idx.begin(), idx.end(), lo);
+        if (it != idx.end() && *it < hi) {
+            if (!nd.any_sampled) nd.lmin = l;
+            nd.any_sampled = true;
+        }
+    }
+    if (!nd.any_sampled) nd.lmin = nd.L;
+}
+
+// ---------------------------------------------------------------------------
+// Trajectory kernels.  One block per (problem, chain) segment.
+// ---------------------------------------------------------------------------
+
+struct TrajState {
+    long long traj;
+    long long slot;
+};
+
+template <typename T>
+__device__ __forceinline__ void scatter_one(const ScatterPlan &sc, long c, long j, T q)
+{
+    const int b = sc.buf_id ? (int)sc.buf_id[j] : 0;
+    const long o = c * sc.cstride[b] + (long)sc.off[j];
+    if (sc.is_bf16[b]) reinterpret_cast<__nv_bfloat16 *>(sc.base[b])[o] = __float2bfloat16_rn((float)q);
+    else reinterpret_cast<T *>(sc.base[b])[o] = q;
+}
+
+__device__ __forceinline__ double seg_sum(double v, double *sm)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sm[i];
+    __syncthreads();
+    return r;
+}
+
+// p ~ N(0, I); K0 = p.p/2; first half kick p -= eps/2 g; first drift q* = q + eps p; scatter q*.
+template <typename T>
+__global__ void __launch_bounds__(256) k_traj_begin(const SegDesc *segs, int C, const T *q_cur, const T *g_cur,
+                                                    T *q_prop, T *p, double *K0, double eps, uint64_t seed,
+                                                    const TrajState *st)
+{
+    __shared__ double sm[8];
+    const int s = blockIdx.x, pi = s / C, c = s % C;
+    const SegDesc &sd = segs[pi];
+    const long base = sd.qoff + (long)c * sd.k;
+    const uint64_t traj = (uint64_t)st->traj;
+    const T h = (T)(0.5 * eps), e = (T)eps;
+    double kin = 0.0;
+    for (long blk = threadIdx.x; blk * 4 < sd.k; blk += blockDim.x) {
+        double z[4];
+        momenta4(seed, (uint64_t)sd.problem, (uint64_t)c, traj, (uint64_t)blk, z);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const long j = blk * 4 + t;
+            if (j >= sd.k) break;
+            T pj = (T)z[t];
+            kin += (double)pj * (double)pj;
+            pj = pj - h * g_cur[base + j];
+            const T qj = q_cur[base + j] + e * pj;
+            p[base + j] = pj;
+            q_prop[base + j] = qj;
+            scatter_one<T>(sd.sc, c, j, qj);
+        }
+    }
+    const double tot = seg_sum(kin, sm);
+    if (threadIdx.x == 0) K0[s] = 0.5 * tot;
+}
+
+// p -= eps g; q += eps p; scatter q.
+template <typename T>
+__global__ void __launch_bounds__(256) k_kick_drift(const SegDesc *segs, int C, const T *g, T *p, T *q, double kick,
+                                                    double drift)
+{
+    const int s = blockIdx.x, pi = s / C, c = s % C;
+    const SegDesc &sd = segs[pi];
+    const long base = sd.qoff + (long)c * sd.k;
+    const T kk = (T)kick, dd = (T)drift;
+    for (long j = threadIdx.x; j < sd.k; j += blockDim.x) {
+        T pj = p[base + j];
+        if (kick != 0.0) pj = pj - kk * g[base + j];
+        p[base + j] = pj;
+        if (drift != 0.0) {
+            const T qj = q[base + j] + dd * pj;
+            q[base + j] = qj;
+            scatter_one<T>(sd.sc, c, j, qj);
+        }
+    }
+}
+
+// Last half kick, K1, dH = H1 - H0, accept iff log u < H0 - H1, record outputs.
+template <typename T>
+__global__ void __launch_bounds__(256) k_traj_end(const SegDesc *segs, int C, int nseg, long S_total, T *q_cur,
+                                                  T *g_cur, double *U_cur, const T *q_prop, const T *p,
+                                                  const T *g_prop, const double *U_prop, const double *K0,
+                                                  double eps, uint64_t seed, const TrajState *st, T *samples,
+                                                  unsigned char *acc_out, double *dH_out)
+{
+    __shared__ double sm[8];
+    __shared__ int s_acc;
+    const int s = blockIdx.x, pi = s / C, c = s % C;
+    const SegDesc &sd = segs[pi];
+    const long base = sd.qoff + (long)c * sd.k;
+    const T h = (T)(0.5 * eps);
+    double kin = 0.0;
+    for (long j = threadIdx.x; j < sd.k; j += blockDim.x) {
+        const T pj = p[base + j] - h * g_prop[base + j];
+        kin += (double)pj * (double)pj;
+    }
+    const double K1 = 0.5 * seg_sum(kin, sm);
+    const long long slot = st->slot;
+    if (threadIdx.x == 0) {
+        const double H0 = U_cur[s] + K0[s];
+        const double H1 = U_prop[s] + K1;
+        const double lu = mh_log_uniform(seed, (uint64_t)sd.problem, (uint64_t)c, (uint64_t)st->traj);
+        const int a = lu < H0 - H1;
+        s_acc = a;
+        if (a) U_cur[s] = U_prop[s];
+        if (acc_out) acc_out[slot * nseg + s] = (unsigned char)a;
+        if (dH_out) dH_out[slot * nseg + s] = H1 - H0;
+    }
+    __syncthreads();
+    const int a = s_acc;
+    for (long j = threadIdx.x; j < sd.k; j += blockDim.x) {
+        T qj = q_cur[base + j];
+        if (a) {
+            qj = q_prop[base + j];
+            q_cur[base + j] = qj;
+            g_cur[base + j] = g_prop[base + j];
+        }
+        if (samples) samples[slot * S_total + base + j] = qj;
+    }
+}
+
+__global__ void k_traj_advance(TrajState *st)
+{
+    st->traj += 1;
+    st->slot += 1;
+}
+
+__global__ void k_set_state(TrajState *st, long long traj, long long slot)
+{
+    st->traj = traj;
+    st->slot = slot;
+}
+
+__global__ void k_debug_momenta(uint64_t seed, uint64_t problem, uint64_t chain, uint64_t traj, long k, double *out)
+{
+    for (long blk = (long)blockIdx.x * blockDim.x + threadIdx.x; blk * 4 < k; blk += (long)gridDim.x * blockDim.x) {
+        double z[4];
+        momenta4(seed, problem, chain, traj, (uint64_t)blk, z);
+        for (int t = 0; t < 4; ++t)
+            if (blk * 4 + t < k) out[blk * 4 + t] = z[t];
+    }
+}
+
+__global__ void k_debug_logu(uint64_t seed, uint64_t problem, long n_chain, long n_traj, double *out)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n_chain * n_traj; i += (long)gridDim.x * blockDim.x)
+        out[i] = mh_log_uniform(seed, problem, (uint64_t)(i / n_traj), (uint64_t)(i % n_traj));
+}
+
+__global__ void k_debug_philox(const uint64_t *ctr, const uint64_t *key, long n, uint64_t *out)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        uint64_t c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+        philox4x64_10(c, key[2 * i], key[2 * i + 1]);
+        for (int t = 0; t < 4; ++t) out[4 * i + t] = c[t];
+    }
+}
+
+__global__ void k_nonfinite_count(const double *U, int n, int *out)
+{
+    int bad = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) bad += isfinite(U[i]) ? 0 : 1;
+    atomicAdd(out, bad);
+}
+
+}  // namespace hmc
+
+using namespace hmc;
+
+struct hmc_handle_s {
+    int prec = 0;
+    int C = 0;
+    int nprob = 0;
+    size_t elem = 4;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<std::unique_ptr<Problem>> probs;
+    std::vector<std::unique_ptr<Engine>> engines;
+    std::vector<long> qoff;
+    long k_total = 0, P_total = 0, S_total = 0;
+    DevBuf q_cur, g_cur, q_prop, p, g_prop, U_cur, U_prop, K0, segs, state, scratch;
+    std::vector<std::unique_ptr<DevBuf>> stage;
+};
+
+namespace {
+
+bool is_device_ptr(const void *ptr)
+{
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void check_mlp_spec(const hmc_mlp_spec &s, const char *what)
+{
+    HMC_REQUIRE(s.n_layers >= 1 && s.n_layers <= HMC_MAX_LAYERS, "%s: n_layers must be in [1, %d]", what,
+                HMC_MAX_LAYERS);
+    for (int l = 0; l <= s.n_layers; ++l)
+        HMC_REQUIRE(s.widths[l] >= 1 && s.widths[l] <= (1 << 20), "%s: widths[%d] = %d is out of range", what, l,
+                    s.widths[l]);
+    for (int l = 0; l < s.n_layers; ++l)
+        HMC_REQUIRE(s.act[l] >= HMC_ACT_IDENTITY && s.act[l] <= HMC_ACT_SIN, "%s: act[%d] = %d is invalid", what, l,
+                    s.act[l]);
+}
+
+template <typename V> std::vector<V> fetch(const V *src, long n, const char *what)
+{
+    HMC_REQUIRE(n == 0 || src != nullptr, "%s is NULL", what);
+    std::vector<V> v((size_t)n);
+    if (n > 0) HMC_CK(cudaMemcpy(v.data(), src, sizeof(V) * (size_t)n, cudaMemcpyDefault));
+    return v;
+}
+
+std::unique_ptr<Problem> build_problem(const hmc_net_spec &spec, const hmc_data &d, double alpha, double sigma,
+                                       const unsigned char *mask, const double *frozen, int C)
+{
+    HMC_REQUIRE(spec.kind == HMC_NET_MLP || spec.kind == HMC_NET_DEEPONET, "unknown net kind %d", spec.kind);
+    HMC_REQUIRE(alpha > 0 && sigma > 0 && std::isfinite(alpha) && std::isfinite(sigma),
+                "prior_sigma and noise_sigma must be positive and finite");
+    auto p = std::make_unique<Problem>();
+    p->kind = spec.kind;
+    p->C = C;
+    p->alpha = alpha;
+    p->sigma = sigma;
+    long P = 0;
+    if (spec.kind == HMC_NET_MLP) {
+        check_mlp_spec(spec.net, "net");
+        HMC_REQUIRE(d.n >= 0 && d.dx == spec.net.widths[0], "data.dx (%d) must equal widths[0] (%d)", d.dx,
+                    spec.net.widths[0]);
+        for (int l = 0; l < spec.net.n_layers; ++l)
+            P += (long)spec.net.widths[l + 1] * spec.net.widths[l] + (spec.net.has_bias[l] ? spec.net.widths[l + 1] : 0);
+    } else {
+        check_mlp_spec(spec.branch, "branch");
+        check_mlp_spec(spec.trunk, "trunk");
+        HMC_REQUIRE(spec.branch.widths[spec.branch.n_layers] == spec.trunk.widths[spec.trunk.n_layers],
+                    "branch and trunk output widths differ");
+        HMC_REQUIRE(d.n_u >= 0 && d.n_y >= 0 && d.du == spec.branch.widths[0] && d.dy == spec.trunk.widths[0],
+                    "DeepONet data dimensions do not match the spec");
+        for (const hmc_mlp_spec *s : {&spec.branch, &spec.trunk})
+            for (int l = 0; l < s->n_layers; ++l)
+                P += (long)s->widths[l + 1] * s->widths[l] + (s->has_bias[l] ? s->widths[l + 1] : 0);
+        P += spec.deeponet_out_bias ? 1 : 0;
+    }
+    HMC_REQUIRE(P < (1L << 31), "too many parameters (%ld)", P);
+    p->P = P;
+    auto m = fetch(mask, P, "subset_mask");
+    p->frozen = fetch(frozen, P, "frozen_params");
+    for (long i = 0; i < P; ++i)
+        if (m[i]) p->idx.push_back(i);
+    p->k = (long)p->idx.size();
+    HMC_REQUIRE(p->k >= 1, "subset_mask selects no parameter");
+    if (spec.kind == HMC_NET_MLP) {
+        build_net_desc(p->net, spec.net, 0, p->idx);
+        p->n = d.n;
+        p->dx = d.dx;
+        p->dout = spec.net.widths[spec.net.n_layers];
+        p->x = fetch(d.x, d.n * d.dx, "data.x");
+        p->y = fetch(d.y, d.n * p->dout, "data.y");
+    } else {
+        build_net_desc(p->branch, spec.branch, 0, p->idx);
+        build_net_desc(p->trunk, spec.trunk, p->branch.P, p->idx);
+        p->out_bias = spec.deeponet_out_bias ? 1 : 0;
+        p->b0_off = p->out_bias ? p->branch.P + p->trunk.P : -1;
+        p->n_u = d.n_u;
+        p->n_y = d.n_y;
+        p->du = d.du;
+        p->dy = d.dy;
+        p->u = fetch(d.u, d.n_u * d.du, "data.u");
+        p->yq = fetch(d.yq, d.n_y * d.dy, "data.yq");
+        p->t = fetch(d.t, d.n_u * d.n_y, "data.t");
+    }
+    return p;
+}
+
+void join_in(hmc_handle h)
+{
+    HMC_CK(cudaEventRecord(h->ev_in, h->user_stream));
+    HMC_CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+}
+
+void join_out(hmc_handle h)
+{
+    HMC_CK(cudaEventRecord(h->ev_out, h->stream));
+    HMC_CK(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0));
+}
+
+void energy_grad_all(hmc_handle h, void *q, double *U, void *g, bool scattered)
+{
+    for (int i = 0; i < h->nprob; ++i) {
+        char *qb = static_cast<char *>(q) + h->qoff[i] * h->elem;
+        char *gb = g ? static_cast<char *>(g) + h->qoff[i] * h->elem : nullptr;
+        h->engines[i]->energy_grad(qb, U + (long)i * h->C, gb, scattered, h->stream);
+    }
+}
+
+// A device view of a user array: the pointer itself when it is device memory,
+// otherwise a staging buffer (copied in when `in`).
+void *dev_view(hmc_handle h, const void *user, size_t bytes, bool in, bool *staged)
+{
+    *staged = false;
+    if (!user) return nullptr;
+    if (is_device_ptr(user)) return const_cast<void *>(user);
+    h->stage.emplace_back(new DevBuf(bytes));
+    void *d = h->stage.back()->ptr;
+    if (in) HMC_CK(cudaMemcpyAsync(d, user, bytes, cudaMemcpyHostToDevice, h->stream));
+    *staged = true;
+    return d;
+}
+
+void kick_drift(hmc_handle h, void *q, void *p, const void *g, double kick, double drift)
+{
+    const int nseg = h->nprob * h->C;
+    const SegDesc *sd = h->segs.as<SegDesc>();
+    if (h->prec == HMC_PREC_FP64)
+        k_kick_drift<double><<<nseg, 256, 0, h->stream>>>(sd, h->C, (const double *)g, (double *)p, (double *)q, kick,
+                                                          drift);
+    else
+        k_kick_drift<float><<<nseg, 256, 0, h->stream>>>(sd, h->C, (const float *)g, (float *)p, (float *)q, kick,
+                                                         drift);
+    HMC_LAUNCH_CK();
+}
+
+template <typename T>
+void enqueue_trajectory(hmc_handle h, double eps, int L, uint64_t seed, void *samples, unsigned char *acc, double *dH)
+{
+    const int nseg = h->nprob * h->C;
+    const SegDesc *sd = h->segs.as<SegDesc>();
+    TrajState *st = h->state.as<TrajState>();
+    k_traj_begin<T><<<nseg, 256, 0, h->stream>>>(sd, h->C, h->q_cur.as<T>(), h->g_cur.as<T>(), h->q_prop.as<T>(),
+                                                 h->p.as<T>(), h->K0.as<double>(), eps, seed, st);
+    HMC_LAUNCH_CK();
+    for (int s = 1; s <= L; ++s) {
+        energy_grad_all(h, h->q_prop.ptr, h->U_prop.as<double>(), h->g_prop.ptr, true);
+        if (s < L) {
+            k_kick_drift<T><<<nseg, 256, 0, h->stream>>>(sd, h->C, h->g_prop.as<T>(), h->p.as<T>(), h->q_prop.as<T>(),
+                                                         eps, eps);
+            HMC_LAUNCH_CK();
+        }
+    }
+    k_traj_end<T><<<nseg, 256, 0, h->stream>>>(sd, h->C, nseg, h->S_total, h->q_cur.as<T>(), h->g_cur.as<T>(),
+                                               h->U_cur.as<double>(), h->q_prop.as<T>(), h->p.as<T>(),
+                                               h->g_prop.as<T>(), h->U_prop.as<double>(), h->K0.as<double>(), eps,
+                                               seed, st, static_cast<T *>(samples), acc, dH);
+    HMC_LAUNCH_CK();
+    k_traj_advance<<<1, 1, 0, h->stream>>>(st);
+    HMC_LAUNCH_CK();
+}
+
+hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, const hmc_data *data,
+                       const double *alpha, const double *sigma, const unsigned char *const *masks,
+                       const double *const *frozen, int C, void *stream)
+{
+    HMC_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    HMC_REQUIRE(nprob >= 1, "n_problems must be >= 1");
+    HMC_REQUIRE(specs && data && alpha && sigma && masks && frozen, "NULL argument");
+    HMC_REQUIRE(C >= 1 && C <= 65535, "n_chains must be in [1, 65535]");
+    const int prec = specs[0].prec;
+    HMC_REQUIRE(prec >= HMC_PREC_FP64 && prec <= HMC_PREC_BF16, "unknown precision %d", prec);
+    for (int i = 0; i < nprob; ++i) HMC_REQUIRE(specs[i].prec == prec, "all problems of a batch share one precision");
+    std::unique_ptr<hmc_handle_s> h(new hmc_handle_s);
+    h->prec = prec;
+    h->C = C;
+    h->nprob = nprob;
+    h->elem = prec == HMC_PREC_FP64 ? 8 : 4;
+    h->user_stream = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    HMC_CK(cudaGetDevice(&dev));
+    HMC_CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    HMC_CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    HMC_CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    for (int i = 0; i < nprob; ++i) {
+        h->probs.push_back(build_problem(specs[i], data[i], alpha[i], sigma[i], masks[i], frozen[i], C));
+        Problem &p = *h->probs.back();
+        Engine *e = nullptr;
+        if (prec == HMC_PREC_FP64) e = make_simt_engine_f64(p, C);
+        else if (prec == HMC_PREC_FP32) e = make_simt_engine_f32(p, C);
+        else if (prec == HMC_PREC_BF16) {
+            std::string why;
+            if (!umma_engine_supports(p, &why)) {
+                set_error("BF16 tensor-core path does not support this network: %s", why.c_str());
+                throw Fail{HMC_ERR_UNSUPPORTED};
+            }
+            e = make_umma_engine_bf16(p, C);
+        } else {
+            set_error("HMC_PREC_TF32 is not implemented");
+            throw Fail{HMC_ERR_UNSUPPORTED};
+        }
+        h->engines.emplace_back(e);
+        p.engine = e;
+        h->qoff.push_back(h->k_total * C);
+        h->k_total += p.k;
+        h->P_total += p.P;
+    }
+    h->S_total = h->k_total * C;
+    const size_t sb = h->elem * (size_t)h->S_total;
+    h->q_cur.alloc(sb);
+    h->g_cur.alloc(sb);
+    h->q_prop.alloc(sb);
+    h->p.alloc(sb);
+    h->g_prop.alloc(sb);
+    const size_t nseg = (size_t)nprob * C;
+    h->U_cur.alloc(sizeof(double) * nseg);
+    h->U_prop.alloc(sizeof(double) * nseg);
+    h->K0.alloc(sizeof(double) * nseg);
+    h->scratch.alloc(sizeof(int) * 4);
+    h->state.alloc(sizeof(TrajState));
+    std::vector<SegDesc> sd(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        sd[i].qoff = h->qoff[i];
+        sd[i].k = (int)h->probs[i]->k;
+        sd[i].problem = i;
+        sd[i].sc = h->engines[i]->scatter_plan();
+    }
+    h->segs.alloc(sizeof(SegDesc) * nprob);
+    HMC_CK(cudaMemcpy(h->segs.ptr, sd.data(), sizeof(SegDesc) * nprob, cudaMemcpyHostToDevice));
+    HMC_CK(cudaDeviceSynchronize());
+    *out = h.release();
+    return HMC_OK;
+}
+
+template <typename F> hmc_status guarded(F &&f)
+{
+    try {
+        return f();
+    } catch (const Fail &e) {
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return HMC_ERR_OOM;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return HMC_ERR_CUDA;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+hmc_status hmc_create(hmc_handle *out, const hmc_net_spec *spec, const hmc_data *data, double prior_sigma,
+                      double noise_sigma, const unsigned char *subset_mask, const double *frozen_params,
+                      int n_chains, void *cuda_stream)
+{
+    g_err.clear();
+    return guarded([&] {
+        return create_impl(out, 1, spec, data, &prior_sigma, &noise_sigma, &subset_mask, &frozen_params, n_chains,
+                           cuda_stream);
+    });
+}
+
+hmc_status hmc_create_batch(hmc_handle *out, int n_problems, const hmc_net_spec *specs, const hmc_data *data,
+                            const double *prior_sigma, const double *noise_sigma,
+                            const unsigned char *const *subset_masks, const double *const *frozen_params,
+                            int n_chains, void *cuda_stream)
+{
+    g_err.clear();
+    return guarded([&] {
+        return create_impl(out, n_problems, specs, data, prior_sigma, noise_sigma, subset_masks, frozen_params,
+                           n_chains, cuda_stream);
+    });
+}
+
+long hmc_subset_size(hmc_handle h) { return h ? h->k_total : -1; }
+long hmc_param_count(hmc_handle h) { return h ? h->P_total : -1; }
+int hmc_num_chains(hmc_handle h) { return h ? h->C : -1; }
+
+hmc_status hmc_energy_grad(hmc_handle h, const void *q, double *U, void *grad)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(h && q && U, "NULL argument");
+        h->stage.clear();
+        join_in(h);
+        bool sq, su, sg;
+        const size_t sb = h->elem * (size_t)h->S_total;
+        void *dq = dev_view(h, q, sb, true, &sq);
+        double *dU = static_cast<double *>(dev_view(h, U, sizeof(double) * h->nprob * h->C, false, &su));
+        void *dg = dev_view(h, grad, sb, false, &sg);
+        energy_grad_all(h, dq, dU, dg, false);
+        if (sg) HMC_CK(cudaMemcpyAsync(grad, dg, sb, cudaMemcpyDeviceToHost, h->stream));
+        if (su) HMC_CK(cudaMemcpyAsync(U, dU, sizeof(double) * h->nprob * h->C, cudaMemcpyDeviceToHost, h->stream));
+        join_out(h);
+        if (su || sg || sq) HMC_CK(cudaStreamSynchronize(h->stream));
+        if (su) {
+            for (int i = 0; i < h->nprob * h->C; ++i)
+                if (!std::isfinite(U[i])) {
+                    set_error("U is not finite for (problem, chain) %d", i);
+                    return HMC_ERR_NONFINITE;
+                }
+        }
+        return HMC_OK;
+    });
+}
+
+hmc_status hmc_leapfrog(hmc_handle h, void *q, void *p, double eps, int L)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(h && q && p, "NULL argument");
+        HMC_REQUIRE(L >= 0 && std::isfinite(eps), "L must be >= 0 and eps finite");
+        h->stage.clear();
+        join_in(h);
+        const size_t sb = h->elem * (size_t)h->S_total;
+        bool sq, sp;
+        void *dq = dev_view(h, q, sb, true, &sq);
+        void *dp = dev_view(h, p, sb, true, &sp);
+        if (L > 0) {
+            energy_grad_all(h, dq, h->U_prop.as<double>(), h->g_prop.ptr, false);
+            kick_drift(h, dq, dp, h->g_prop.ptr, 0.5 * eps, eps);
+            for (int s = 1; s <= L; ++s) {
+                energy_grad_all(h, dq, h->U_prop.as<double>(), h->g_prop.ptr, true);
+                if (s < L) kick_drift(h, dq, dp, h->g_prop.ptr, eps, eps);
+                else kick_drift(h, dq, dp, h->g_prop.ptr, 0.5 * eps, 0.0);
+            }
+        }
+        if (sq) HMC_CK(cudaMemcpyAsync(q, dq, sb, cudaMemcpyDeviceToHost, h->stream));
+        if (sp) HMC_CK(cudaMemcpyAsync(p, dp, sb, cudaMemcpyDeviceToHost, h->stream));
+        join_out(h);
+        if (sq || sp) HMC_CK(cudaStreamSynchronize(h->stream));
+        return HMC_OK;
+    });
+}
+
+hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_samples, unsigned long long seed,
+                      long first_traj, void *samples, unsigned char *accepted, double *dH, void *q_last)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(h && q0, "NULL argument");
+        HMC_REQUIRE(L >= 1 && n_samples >= 0 && first_traj >= 0 && std::isfinite(eps) && eps > 0,
+                    "need L >= 1, eps > 0, n_samples >= 0, first_traj >= 0");
+        h->stage.clear();
+        join_in(h);
+        const size_t sb = h->elem * (size_t)h->S_total;
+        const long nseg = (long)h->nprob * h->C;
+        bool s0, ss, sa, sd, sl;
+        void *dq0 = dev_view(h, q0, sb, true, &s0);
+        HMC_CK(cudaMemcpyAsync(h->q_cur.ptr, dq0, sb, cudaMemcpyDeviceToDevice, h->stream));
+        void *ds = dev_view(h, samples, sb * (size_t)n_samples, false, &ss);
+        unsigned char *da = static_cast<unsigned char *>(dev_view(h, accepted, (size_t)nseg * n_samples, false, &sa));
+        double *ddh = static_cast<double *>(dev_view(h, dH, sizeof(double) * nseg * n_samples, false, &sd));
+        void *dl = dev_view(h, q_last, sb, false, &sl);
+        energy_grad_all(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr, false);
+        k_set_state<<<1, 1, 0, h->stream>>>(h->state.as<TrajState>(), first_traj, 0);
+        HMC_LAUNCH_CK();
+        if (n_samples > 0) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            HMC_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+            try {
+                if (h->prec == HMC_PREC_FP64) enqueue_trajectory<double>(h, eps, L, seed, ds, da, ddh);
+                else enqueue_trajectory<float>(h, eps, L, seed, ds, da, ddh);
+            } catch (...) {
+                cudaStreamEndCapture(h->stream, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                throw;
+            }
+            HMC_CK(cudaStreamEndCapture(h->stream, &graph));
+            cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            HMC_CK(e);
+            for (long i = 0; i < n_samples; ++i) {
+                e = cudaGraphLaunch(exec, h->stream);
+                if (e != cudaSuccess) break;
+            }
+            cudaGraphExecDestroy(exec);
+            HMC_CK(e);
+        }
+        if (dl) HMC_CK(cudaMemcpyAsync(dl, h->q_cur.ptr, sb, cudaMemcpyDeviceToDevice, h->stream));
+        if (ss) HMC_CK(cudaMemcpyAsync(samples, ds, sb * (size_t)n_samples, cudaMemcpyDeviceToHost, h->stream));
+        if (sa) HMC_CK(cudaMemcpyAsync(accepted, da, (size_t)nseg * n_samples, cudaMemcpyDeviceToHost, h->stream));
+        if (sd) HMC_CK(cudaMemcpyAsync(dH, ddh, sizeof(double) * nseg * n_samples, cudaMemcpyDeviceToHost, h->stream));
+        if (sl) HMC_CK(cudaMemcpyAsync(q_last, dl, sb, cudaMemcpyDeviceToHost, h->stream));
+        join_out(h);
+        if (s0 || ss || sa || sd || sl) HMC_CK(cudaStreamSynchronize(h->stream));
+        return HMC_OK;
+    });
+}
+
+hmc_status hmc_destroy(hmc_handle h)
+{
+    g_err.clear();
+    if (!h) return HMC_OK;
+    return guarded([&]() -> hmc_status {
+        cudaStreamSynchronize(h->stream);
+        h->engines.clear();
+        h->probs.clear();
+        h->stage.clear();
+        cudaStream_t s = h->stream;
+        cudaEvent_t a = h->ev_in, b = h->ev_out;
+        delete h;
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        cudaStreamDestroy(s);
+        return HMC_OK;
+    });
+}
+
+const char *hmc_last_error(void) { return g_err.c_str(); }
+
+// --- diagnostics (include/hmc_diag.h) ---------------------------------------
+
+hmc_status hmc_diag_momenta(unsigned long long seed, unsigned long long problem, unsigned long long chain,
+                            unsigned long long traj, long k, double *out_host)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(out_host && k >= 0, "bad argument");
+        DevBuf d(sizeof(double) * std::max<long>(k, 1));
+        k_debug_momenta<<<64, 256>>>(seed, problem, chain, traj, k, d.as<double>());
+        HMC_LAUNCH_CK();
+        HMC_CK(cudaMemcpy(out_host, d.ptr, sizeof(double) * k, cudaMemcpyDeviceToHost));
+        return HMC_OK;
+    });
+}
+
+hmc_status hmc_diag_log_uniform(unsigned long long seed, unsigned long long problem, long n_chain, long n_traj,
+                                double *out_host)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(out_host && n_chain >= 0 && n_traj >= 0, "bad argument");
+        DevBuf d(sizeof(double) * std::max<long>(n_chain * n_traj, 1));
+        k_debug_logu<<<64, 256>>>(seed, problem, n_chain, n_traj, d.as<double>());
+        HMC_LAUNCH_CK();
+        HMC_CK(cudaMemcpy(out_host, d.ptr, sizeof(double) * n_chain * n_traj, cudaMemcpyDeviceToHost));
+        return HMC_OK;
+    });
+}
+
+hmc_status hmc_diag_philox(const unsigned long long *ctr, const unsigned long long *key, long n,
+                           unsigned long long *out_host)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(ctr && key && out_host && n >= 0, "bad argument");
+        DevBuf dc(32 * std::max<long>(n, 1)), dk(16 * std::max<long>(n, 1)), dout(32 * std::max<long>(n, 1));
+        HMC_CK(cudaMemcpy(dc.ptr, ctr, 32 * n, cudaMemcpyHostToDevice));
+        HMC_CK(cudaMemcpy(dk.ptr, key, 16 * n, cudaMemcpyHostToDevice));
+        k_debug_philox<<<64, 256>>>(dc.as<uint64_t>(), dk.as<uint64_t>(), n, dout.as<uint64_t>());
+        HMC_LAUNCH_CK();
+        HMC_CK(cudaMemcpy(out_host, dout.ptr, 32 * n, cudaMemcpyDeviceToHost));
+        return HMC_OK;
+    });
+}
+
+}  // extern "C"

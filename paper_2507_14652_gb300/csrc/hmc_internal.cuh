@@ -1,0 +1,127 @@
+// hmc_internal.cuh -- structures shared by the translation units of libhmc.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hmc.h"
+
+namespace hmc {
+
+constexpr int MAXL = HMC_MAX_LAYERS;
+constexpr int MAX_SCATTER_BUFS = 40;
+
+// Thread-local error message behind hmc_last_error().
+void set_error(const char *fmt, ...);
+
+// Status helpers: every CUDA call on the host goes through CK().
+struct Fail {
+    hmc_status st;
+};
+#define HMC_CK(call)                                                                   \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            ::hmc::set_error("%s failed at %s:%d: %s", #call, __FILE__, __LINE__,       \
+                             cudaGetErrorString(e_));                                  \
+            throw ::hmc::Fail{e_ == cudaErrorMemoryAllocation ? HMC_ERR_OOM : HMC_ERR_CUDA}; \
+        }                                                                              \
+    } while (0)
+#define HMC_LAUNCH_CK() HMC_CK(cudaGetLastError())
+#define HMC_REQUIRE(cond, ...)                                                         \
+    do {                                                                               \
+        if (!(cond)) {                                                                 \
+            ::hmc::set_error(__VA_ARGS__);                                             \
+            throw ::hmc::Fail{HMC_ERR_ARG};                                            \
+        }                                                                              \
+    } while (0)
+
+// One feed-forward stack with its parameter offsets inside the problem's theta.
+struct NetDesc {
+    int L = 0;
+    int w[MAXL + 1] = {};
+    int act[MAXL] = {};
+    int bias[MAXL] = {};
+    long woff[MAXL] = {};
+    long boff[MAXL] = {};   // -1 when the layer has no bias
+    long base = 0;          // offset of the first parameter of this net
+    long P = 0;             // parameters of this net
+    int lmin = 0;           // lowest layer that holds a sampled parameter
+    bool any_sampled = false;
+};
+
+// Where the drift kernel writes each sampled coordinate (one plan per problem).
+struct ScatterPlan {
+    int nbuf = 0;
+    void *base[MAX_SCATTER_BUFS] = {};
+    long cstride[MAX_SCATTER_BUFS] = {};   // elements between chains
+    int is_bf16[MAX_SCATTER_BUFS] = {};
+    const uint8_t *buf_id = nullptr;       // [k] (nullptr: all in buffer 0)
+    const int *off = nullptr;              // [k] element offset inside one chain's slice
+};
+
+// Per-(problem) view used by the trajectory kernels; lives in device memory.
+struct SegDesc {
+    long qoff;     // offset of this problem's [C][k] block in the packed state
+    int k;
+    int problem;   // Philox stream of this problem
+    ScatterPlan sc;
+};
+
+struct Problem;
+
+// Engine interface: U and grad U of one problem for all its chains.
+struct Engine {
+    virtual ~Engine() {}
+    // q, g: [C][k] device, handle precision. U: [C] device doubles.
+    // The sampled coordinates are assumed already scattered into the network
+    // when `scattered` is true (the trajectory kernels do it in the drift).
+    virtual void energy_grad(const void *q, double *U, void *g, bool scattered, cudaStream_t s) = 0;
+    virtual ScatterPlan scatter_plan() = 0;
+    virtual size_t bytes() const = 0;
+};
+
+struct Problem {
+    int kind = 0;
+    NetDesc net, branch, trunk;
+    int out_bias = 0;
+    long b0_off = -1;
+    long P = 0, k = 0;
+    int C = 0;
+    long n = 0;
+    int dx = 0, dout = 0;
+    long n_u = 0, n_y = 0;
+    int du = 0, dy = 0;
+    double sigma = 1.0, alpha = 1.0;
+    std::vector<long> idx;          // host copy, ascending
+    std::vector<double> frozen;     // host copy
+    std::vector<double> x, y, u, yq, t;   // host copies of the data (FP64)
+    Engine *engine = nullptr;
+};
+
+void build_net_desc(NetDesc &nd, const hmc_mlp_spec &s, long base, const std::vector<long> &idx);
+
+// Engines (one per precision family).
+Engine *make_simt_engine_f64(Problem &p, int C);
+Engine *make_simt_engine_f32(Problem &p, int C);
+Engine *make_umma_engine_bf16(Problem &p, int C);
+bool umma_engine_supports(const Problem &p, std::string *why);
+
+// Device allocation helper that tracks bytes and frees on destruction.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t n = 0;
+    DevBuf() {}
+    explicit DevBuf(size_t bytes) { alloc(bytes); }
+    void alloc(size_t bytes);
+    ~DevBuf();
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    template <typename T> T *as() const { return reinterpret_cast<T *>(ptr); }
+};
+
+}  // namespace hmc

@@ -1,0 +1,463 @@
+// k_simt.cu -- CUDA-core engine for U and grad U in FP64 or FP32.
+//
+// Any MLP or DeepONet shape.  Per gradient evaluation (all chains batched in
+// the grid's z dimension):
+//   forward   A_l = act(A_{l-1} W_l^T + b_l), keeping A_l and act'(Z_l)
+//   residual  r = F - y, U_lik partials sum r^2 in FP64, delta_L = r/sigma^2 * act'
+//   reverse   dW_l = delta_l^T A_{l-1}, db_l = column sums of delta_l,
+//             delta_{l-1} = (delta_l W_l) * act'(Z_{l-1}); it stops at the lowest
+//             layer that holds a sampled parameter
+//   DeepONet  S = B T^T + b0, dB = dS T, dT = dS^T B (Sec. 4.2 operator output)
+//   finalize  U = sum partials / (2 sigma^2) + |q|^2/(2 alpha^2) (FP64, fixed order),
+//             g_j = dU/dtheta_{idx_j} + q_j / alpha^2
+// Every reduction has a fixed order, so results are bit-reproducible.
+#include <cstdio>
+#include <memory>
+
+#include "hmc_internal.cuh"
+
+namespace hmc {
+namespace {
+
+constexpr int TILE = 64;
+constexpr int TK = 16;
+
+template <typename T> struct GemmArgs {
+    int M, N, K;
+    const T *A; long a_m, a_k, a_b;
+    const T *B; long b_k, b_n, b_b;
+};
+
+enum { EPI_ACT = 0, EPI_SCALE = 1, EPI_STORE = 2 };
+
+template <typename T> struct EpiArgs {
+    int mode;
+    T *out; long o_m, o_n, o_b;
+    const T *bias; long bias_n, bias_b;
+    int act;
+    T *slope;   // EPI_ACT: receives act'(z); EPI_SCALE: multiplies the result (same layout as out)
+};
+
+__device__ __forceinline__ void act_eval(int act, double z, double &a, double &s)
+{
+    if (act == HMC_ACT_TANH) { a = tanh(z); s = 1.0 - a * a; }
+    else if (act == HMC_ACT_SIN) { a = sin(z); s = cos(z); }
+    else { a = z; s = 1.0; }
+}
+__device__ __forceinline__ void act_eval(int act, float z, float &a, float &s)
+{
+    if (act == HMC_ACT_TANH) { a = tanhf(z); s = 1.0f - a * a; }
+    else if (act == HMC_ACT_SIN) { a = sinf(z); s = cosf(z); }
+    else { a = z; s = 1.0f; }
+}
+
+// C[b](m, n) = sum_k A[b](m, k) B[b](k, n), 64x64 tile, 16-deep K steps, 4x4 per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g, EpiArgs<T> e)
+{
+    __shared__ T As[TK][TILE + 1];
+    __shared__ T Bs[TK][TILE + 1];
+    const int b = blockIdx.z;
+    const long m0 = (long)blockIdx.y * TILE, n0 = (long)blockIdx.x * TILE;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const T *A = g.A + (long)b * g.a_b;
+    const T *B = g.B + (long)b * g.b_b;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+
+    for (int k0 = 0; k0 < g.K; k0 += TK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int el = tid + 256 * r;
+            int mm, kk;
+            if (g.a_k == 1) { kk = el % TK; mm = el / TK; } else { mm = el % TILE; kk = el / TILE; }
+            long gm = m0 + mm; int gk = k0 + kk;
+            As[kk][mm] = (gm < g.M && gk < g.K) ? A[gm * g.a_m + (long)gk * g.a_k] : T(0);
+            int nn;
+            if (g.b_n == 1) { nn = el % TILE; kk = el / TILE; } else { kk = el % TK; nn = el / TK; }
+            long gn = n0 + nn; gk = k0 + kk;
+            Bs[kk][nn] = (gn < g.N && gk < g.K) ? B[(long)gk * g.b_k + gn * g.b_n] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            T a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        long m = m0 + ty + 16 * i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            long n = n0 + tx + 16 * j;
+            if (n >= g.N) continue;
+            long o = (long)b * e.o_b + m * e.o_m + n * e.o_n;
+            if (e.mode == EPI_ACT) {
+                T z = acc[i][j] + (e.bias ? e.bias[(long)b * e.bias_b + n * e.bias_n] : T(0));
+                T a, s;
+                act_eval(e.act, z, a, s);
+                e.out[o] = a;
+                if (e.slope) e.slope[o] = s;
+            } else if (e.mode == EPI_SCALE) {
+                e.out[o] = acc[i][j] * e.slope[o];
+            } else {
+                e.out[o] = acc[i][j];
+            }
+        }
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *sm)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < NT / 32; ++i) r += sm[i];
+    __syncthreads();
+    return r;   // valid in thread 0
+}
+
+// r = F - y; U partials (sum r^2, FP64); delta = r/sigma^2 * slope; sum of delta.
+template <typename T>
+__global__ void __launch_bounds__(256) k_residual(const T *f, long f_b, const T *y, long n_el,
+                                                  const T *slope, double inv_s2, T *delta,
+                                                  double *part_r2, double *part_d, int nparts)
+{
+    __shared__ double sm[8];
+    const int b = blockIdx.y;
+    double r2 = 0.0, ds = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n_el; i += (long)gridDim.x * blockDim.x) {
+        T r = f[(long)b * f_b + i] - y[i];
+        double rd = (double)r;
+        r2 += rd * rd;
+        T d = (T)(rd * inv_s2);
+        if (slope) d = d * slope[(long)b * f_b + i];
+        delta[(long)b * f_b + i] = d;
+        ds += (double)d;
+    }
+    double a = block_sum<256>(r2, sm);
+    double c = block_sum<256>(ds, sm);
+    if (threadIdx.x == 0) {
+        part_r2[(long)b * nparts + blockIdx.x] = a;
+        if (part_d) part_d[(long)b * nparts + blockIdx.x] = c;
+    }
+}
+
+// out[b][col] = sum over rows of d[b][row][col] (FP64 accumulation, fixed order).
+template <typename T>
+__global__ void k_colsum(const T *d, long rows, int cols, long d_b, T *out, long out_b)
+{
+    __shared__ double sm[8][33];
+    const int b = blockIdx.y;
+    const int col = blockIdx.x * 32 + threadIdx.x;
+    double s = 0.0;
+    if (col < cols)
+        for (long r = threadIdx.y; r < rows; r += 8) s += (double)d[(long)b * d_b + r * cols + col];
+    sm[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && col < cols) {
+        double t = 0.0;
+        for (int i = 0; i < 8; ++i) t += sm[i][threadIdx.x];
+        out[(long)b * out_b + col] = (T)t;
+    }
+}
+
+template <typename T>
+__global__ void k_scatter(const T *q, const int *idx, long k, T *theta, long P)
+{
+    const int b = blockIdx.y;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (long)gridDim.x * blockDim.x)
+        theta[(long)b * P + idx[j]] = q[(long)b * k + j];
+}
+
+// U[b] and g[b][:] from the partials and the dense gradient G[b][P].
+template <typename T>
+__global__ void __launch_bounds__(256) k_finalize(const double *part_r2, const double *part_d, int nparts,
+                                                  double half_inv_s2, const T *q, long k, const int *idx,
+                                                  const T *G, long P, long b0_off, double inv_a2,
+                                                  double *U, T *g)
+{
+    __shared__ double sm[8];
+    __shared__ double s_db0;
+    const int b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        if (part_d)
+            for (int i = 0; i < nparts; ++i) t += part_d[(long)b * nparts + i];
+        s_db0 = t;
+    }
+    __syncthreads();
+    const double db0 = s_db0;
+    double pr = 0.0;
+    for (long j = threadIdx.x; j < k; j += blockDim.x) {
+        T qj = q[(long)b * k + j];
+        pr += (double)qj * (double)qj;
+        long id = idx[j];
+        T gj = (id == b0_off) ? (T)db0 : G[(long)b * P + id];
+        if (g) g[(long)b * k + j] = gj + qj * (T)inv_a2;
+    }
+    double prs = block_sum<256>(pr, sm);
+    if (threadIdx.x == 0) {
+        double lik = 0.0;
+        for (int i = 0; i < nparts; ++i) lik += part_r2[(long)b * nparts + i];
+        U[b] = lik * half_inv_s2 + 0.5 * prs * inv_a2;
+    }
+}
+
+template <typename T>
+void launch_gemm(const GemmArgs<T> &g, const EpiArgs<T> &e, int batch, cudaStream_t s)
+{
+    if (g.M <= 0 || g.N <= 0) return;
+    dim3 grid((g.N + TILE - 1) / TILE, (g.M + TILE - 1) / TILE, batch);
+    k_gemm<T><<<grid, 256, 0, s>>>(g, e);
+    HMC_LAUNCH_CK();
+}
+
+template <typename T> struct NetBufs {
+    std::vector<std::unique_ptr<DevBuf>> act, slope;   // index l = 1..L (output of layer l-1)
+};
+
+template <typename T> class SimtEngine final : public Engine {
+  public:
+    SimtEngine(Problem &p, int C) : p_(p), C_(C)
+    {
+        const long P = p.P;
+        theta_.alloc(sizeof(T) * C * P);
+        G_.alloc(sizeof(T) * C * P);
+        idx_.alloc(sizeof(int) * std::max<long>(p.k, 1));
+        std::vector<int> idx32(p.idx.begin(), p.idx.end());
+        HMC_CK(cudaMemcpy(idx_.ptr, idx32.data(), sizeof(int) * p.k, cudaMemcpyHostToDevice));
+        std::vector<T> th(C * P);
+        for (int c = 0; c < C; ++c)
+            for (long i = 0; i < P; ++i) th[c * P + i] = (T)p.frozen[i];
+        HMC_CK(cudaMemcpy(theta_.ptr, th.data(), sizeof(T) * C * P, cudaMemcpyHostToDevice));
+        HMC_CK(cudaMemset(G_.ptr, 0, sizeof(T) * C * P));
+        if (p.kind == HMC_NET_MLP) {
+            upload(x_, p.x);
+            upload(y_, p.y);
+            alloc_net(p.net, p.n, netb_);
+            long wmax = max_width(p.net);
+            delta_[0].alloc(sizeof(T) * C * p.n * wmax);
+            delta_[1].alloc(sizeof(T) * C * p.n * wmax);
+            n_el_ = p.n * p.dout;
+        } else {
+            upload(u_, p.u);
+            upload(yq_, p.yq);
+            upload(t_, p.t);
+            alloc_net(p.branch, p.n_u, brb_);
+            alloc_net(p.trunk, p.n_y, trb_);
+            const int lat = p.branch.w[p.branch.L];
+            S_.alloc(sizeof(T) * C * std::max<long>(p.n_u * p.n_y, 1));
+            dB_.alloc(sizeof(T) * C * p.n_u * lat);
+            dT_.alloc(sizeof(T) * C * p.n_y * lat);
+            long wmax = std::max(max_width(p.branch), max_width(p.trunk));
+            long rows = std::max(p.n_u, p.n_y);
+            delta_[0].alloc(sizeof(T) * C * rows * wmax);
+            delta_[1].alloc(sizeof(T) * C * rows * wmax);
+            n_el_ = p.n_u * p.n_y;
+        }
+        nparts_ = (int)std::min<long>(64, std::max<long>(1, (n_el_ + 255) / 256));
+        part_r2_.alloc(sizeof(double) * C * nparts_);
+        part_d_.alloc(sizeof(double) * C * nparts_);
+    }
+
+    ScatterPlan scatter_plan() override
+    {
+        ScatterPlan sp;
+        sp.nbuf = 1;
+        sp.base[0] = theta_.ptr;
+        sp.cstride[0] = p_.P;
+        sp.is_bf16[0] = 0;
+        sp.buf_id = nullptr;
+        sp.off = idx_.as<int>();
+        return sp;
+    }
+
+    size_t bytes() const override { return bytes_; }
+
+    void energy_grad(const void *qv, double *U, void *gv, bool scattered, cudaStream_t s) override
+    {
+        const T *q = static_cast<const T *>(qv);
+        T *g = static_cast<T *>(gv);
+        const long P = p_.P, k = p_.k;
+        T *theta = theta_.as<T>();
+        if (!scattered && k > 0) {
+            dim3 grid((unsigned)std::min<long>((k + 255) / 256, 1024), C_);
+            k_scatter<T><<<grid, 256, 0, s>>>(q, idx_.as<int>(), k, theta, P);
+            HMC_LAUNCH_CK();
+        }
+        const double inv_s2 = 1.0 / (p_.sigma * p_.sigma);
+        if (p_.kind == HMC_NET_MLP) {
+            const NetDesc &nd = p_.net;
+            forward(nd, x_.as<T>(), 0, p_.n, netb_, s);
+            T *f = netb_.act[nd.L]->template as<T>();
+            const T *sl = nd.act[nd.L - 1] == HMC_ACT_IDENTITY ? nullptr : netb_.slope[nd.L]->template as<T>();
+            residual(f, p_.n * p_.dout, y_.as<T>(), sl, inv_s2, delta_[0].as<T>(), false, s);
+            if (nd.any_sampled) backward(nd, x_.as<T>(), 0, p_.n, netb_, delta_[0].as<T>(), s);
+        } else {
+            const NetDesc &bn = p_.branch, &tn = p_.trunk;
+            const int lat = bn.w[bn.L];
+            forward(bn, u_.as<T>(), 0, p_.n_u, brb_, s);
+            forward(tn, yq_.as<T>(), 0, p_.n_y, trb_, s);
+            T *Bm = brb_.act[bn.L]->template as<T>();
+            T *Tm = trb_.act[tn.L]->template as<T>();
+            T *S = S_.as<T>();
+            {   // S = B T^T + b0
+                GemmArgs<T> ga{(int)p_.n_u, (int)p_.n_y, lat, Bm, lat, 1, p_.n_u * lat,
+                               Tm, 1, lat, p_.n_y * lat};
+                EpiArgs<T> ea{EPI_ACT, S, p_.n_y, 1, p_.n_u * p_.n_y,
+                              p_.out_bias ? theta + p_.b0_off : nullptr, 0, P, HMC_ACT_IDENTITY, nullptr};
+                launch_gemm(ga, ea, C_, s);
+            }
+            residual(S, p_.n_u * p_.n_y, t_.as<T>(), nullptr, inv_s2, S, true, s);
+            if (bn.any_sampled) {   // dB = dS T (times the branch output slope)
+                const bool id = bn.act[bn.L - 1] == HMC_ACT_IDENTITY;
+                GemmArgs<T> ga{(int)p_.n_u, lat, (int)p_.n_y, S, p_.n_y, 1, p_.n_u * p_.n_y,
+                               Tm, lat, 1, p_.n_y * lat};
+                EpiArgs<T> ea{id ? EPI_STORE : EPI_SCALE, dB_.as<T>(), lat, 1, p_.n_u * lat, nullptr, 0, 0, 0,
+                              id ? nullptr : brb_.slope[bn.L]->template as<T>()};
+                launch_gemm(ga, ea, C_, s);
+                backward(bn, u_.as<T>(), 0, p_.n_u, brb_, dB_.as<T>(), s);
+            }
+            if (tn.any_sampled) {   // dT = dS^T B
+                const bool id = tn.act[tn.L - 1] == HMC_ACT_IDENTITY;
+                GemmArgs<T> ga{(int)p_.n_y, lat, (int)p_.n_u, S, 1, p_.n_y, p_.n_u * p_.n_y,
+                               Bm, lat, 1, p_.n_u * lat};
+                EpiArgs<T> ea{id ? EPI_STORE : EPI_SCALE, dT_.as<T>(), lat, 1, p_.n_y * lat, nullptr, 0, 0, 0,
+                              id ? nullptr : trb_.slope[tn.L]->template as<T>()};
+                launch_gemm(ga, ea, C_, s);
+                backward(tn, yq_.as<T>(), 0, p_.n_y, trb_, dT_.as<T>(), s);
+            }
+        }
+        k_finalize<T><<<C_, 256, 0, s>>>(part_r2_.as<double>(), p_.kind == HMC_NET_DEEPONET ? part_d_.as<double>() : nullptr,
+                                         nparts_, 0.5 * inv_s2, q, k, idx_.as<int>(), G_.as<T>(), P,
+                                         p_.kind == HMC_NET_DEEPONET && p_.out_bias ? p_.b0_off : -1,
+                                         1.0 / (p_.alpha * p_.alpha), U, g);
+        HMC_LAUNCH_CK();
+    }
+
+  private:
+    static long max_width(const NetDesc &nd)
+    {
+        long w = 1;
+        for (int l = 0; l <= nd.L; ++l) w = std::max<long>(w, nd.w[l]);
+        return w;
+    }
+
+    void upload(DevBuf &dst, const std::vector<double> &src)
+    {
+        std::vector<T> v(src.begin(), src.end());
+        dst.alloc(sizeof(T) * std::max<size_t>(v.size(), 1));
+        if (!v.empty()) HMC_CK(cudaMemcpy(dst.ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+        bytes_ += dst.n;
+    }
+
+    void alloc_net(const NetDesc &nd, long rows, NetBufs<T> &nb)
+    {
+        nb.act.resize(nd.L + 1);
+        nb.slope.resize(nd.L + 1);
+        for (int l = 1; l <= nd.L; ++l) {
+            size_t n = sizeof(T) * C_ * std::max<long>(rows * nd.w[l], 1);
+            nb.act[l].reset(new DevBuf(n));
+            nb.slope[l].reset(new DevBuf(n));
+            bytes_ += 2 * n;
+        }
+    }
+
+    void forward(const NetDesc &nd, const T *in, long in_b, long rows, NetBufs<T> &nb, cudaStream_t s)
+    {
+        const long P = p_.P;
+        T *theta = theta_.as<T>();
+        const T *a = in;
+        long a_b = in_b;
+        for (int l = 0; l < nd.L; ++l) {
+            const int wi = nd.w[l], wo = nd.w[l + 1];
+            GemmArgs<T> ga{(int)rows, wo, wi, a, wi, 1, a_b, theta + nd.woff[l], 1, wi, P};
+            EpiArgs<T> ea{EPI_ACT, nb.act[l + 1]->template as<T>(), wo, 1, rows * wo,
+                          nd.boff[l] >= 0 ? theta + nd.boff[l] : nullptr, 1, P, nd.act[l],
+                          nd.act[l] == HMC_ACT_IDENTITY ? nullptr : nb.slope[l + 1]->template as<T>()};
+            launch_gemm(ga, ea, C_, s);
+            a = nb.act[l + 1]->template as<T>();
+            a_b = rows * wo;
+        }
+    }
+
+    // delta_L (already multiplied by the output slope) in dL [C][rows][w_L].
+    void backward(const NetDesc &nd, const T *in, long in_b, long rows, NetBufs<T> &nb, T *dL, cudaStream_t s)
+    {
+        const long P = p_.P;
+        T *theta = theta_.as<T>();
+        T *G = G_.as<T>();
+        T *d = dL;
+        int pp = 0;
+        for (int l = nd.L - 1; l >= nd.lmin; --l) {
+            const int wi = nd.w[l], wo = nd.w[l + 1];
+            const T *ap = l == 0 ? in : nb.act[l]->template as<T>();
+            const long ap_b = l == 0 ? in_b : rows * wi;
+            {   // dW_l = delta_l^T A_{l-1}
+                GemmArgs<T> ga{wo, wi, (int)rows, d, 1, wo, rows * wo, ap, wi, 1, ap_b};
+                EpiArgs<T> ea{EPI_STORE, G + nd.woff[l], wi, 1, P, nullptr, 0, 0, 0, nullptr};
+                launch_gemm(ga, ea, C_, s);
+            }
+            if (nd.boff[l] >= 0) {
+                dim3 grid((wo + 31) / 32, C_);
+                k_colsum<T><<<grid, dim3(32, 8), 0, s>>>(d, rows, wo, rows * wo, G + nd.boff[l], P);
+                HMC_LAUNCH_CK();
+            }
+            if (l > nd.lmin) {   // delta_{l-1} = (delta_l W_l) * act'(Z_{l-1})
+                T *nx = delta_[pp].as<T>();
+                if (nx == d) nx = delta_[pp ^ 1].as<T>();
+                GemmArgs<T> ga{(int)rows, wi, wo, d, wo, 1, rows * wo, theta + nd.woff[l], wi, 1, P};
+                const bool id = nd.act[l - 1] == HMC_ACT_IDENTITY;
+                EpiArgs<T> ea{id ? EPI_STORE : EPI_SCALE, nx, wi, 1, rows * wi, nullptr, 0, 0, 0,
+                              id ? nullptr : nb.slope[l]->template as<T>()};
+                launch_gemm(ga, ea, C_, s);
+                d = nx;
+                pp ^= 1;
+            }
+        }
+    }
+
+    void residual(const T *f, long n_el, const T *y, const T *slope, double inv_s2, T *delta, bool want_d,
+                  cudaStream_t s)
+    {
+        dim3 grid(nparts_, C_);
+        k_residual<T><<<grid, 256, 0, s>>>(f, n_el, y, n_el, slope, inv_s2, delta, part_r2_.as<double>(),
+                                           want_d ? part_d_.as<double>() : nullptr, nparts_);
+        HMC_LAUNCH_CK();
+    }
+
+    Problem &p_;
+    int C_;
+    size_t bytes_ = 0;
+    DevBuf theta_, G_, idx_, x_, y_, u_, yq_, t_, S_, dB_, dT_, part_r2_, part_d_;
+    DevBuf delta_[2];
+    NetBufs<T> netb_, brb_, trb_;
+    long n_el_ = 0;
+    int nparts_ = 1;
+};
+
+}  // namespace
+
+Engine *make_simt_engine_f64(Problem &p, int C) { return new SimtEngine<double>(p, C); }
+Engine *make_simt_engine_f32(Problem &p, int C) { return new SimtEngine<float>(p, C); }
+
+}  // namespace hmc

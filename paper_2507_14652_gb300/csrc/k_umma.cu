@@ -1,0 +1,904 @@
+// k_umma.cu -- tcgen05 tensor-core engine for U and grad U (BF16 operands,
+// FP32 accumulation in TMEM, FP64 energy sums).
+//
+// Network pattern: MLP  dx -> w -> ... -> w -> 1, tanh hidden layers, identity
+// output, biases everywhere, hidden width w in {64, 128, 192, 256}.
+//
+// One gradient evaluation for all C chains (rows n = data points, tiles of 128):
+//   first layer   A_1 = tanh(X W_0^T + b_0)                        CUDA cores
+//   hidden fwd    A_{i+1} = tanh(A_i W_i^T + b_i)                  UMMA, epilogue tanh
+//   last hidden   A_{L-1} = tanh(A_{L-2} W^T + b) fused with the output layer:
+//                 f = A_{L-1} w_out + b_out, r = f - y, U partial (FP64),
+//                 delta_L = r / sigma^2, dW_out/db_out partials,
+//                 delta_{L-1} = delta_L w_out (1 - A_{L-1}^2)   (A_{L-1} never stored)
+//   hidden bwd    delta_i = (delta_{i+1} W_i) (1 - A_i^2)          UMMA, W_i read MN-major
+//   first bwd     delta_1 as above, fused with dW_0 = delta_1^T X and db_0 (never stored)
+//   weight grads  dW_i = delta_{i+1}^T A_i                          UMMA, both operands MN-major,
+//                 split over rows, only the sampled entries leave the chip
+//   finalize      U, g = sum of partials in fixed order + q / alpha^2
+// Every partial sum is written to its own slot (no atomics), so the result is
+// bit-reproducible.
+#include <cstdio>
+#include <cstring>
+#include <memory>
+
+#include "hmc_diag.h"
+#include "hmc_internal.cuh"
+#include "umma.cuh"
+
+namespace hmc {
+namespace {
+
+using namespace umma;
+
+constexpr int BM = 128;                         // rows per tile (UMMA M)
+constexpr int BK = 64;                          // K per stage (one 128-byte swizzle atom of bf16)
+constexpr int STAGES = 2;
+constexpr int A_STAGE_BYTES = BM * BK * 2;      // 16 KB
+constexpr int B_STAGE_BYTES = 256 * BK * 2;     // 32 KB (room for N up to 256)
+constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
+constexpr int TMEM_COLS = 256;
+constexpr int NTHREADS = 192;                   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int RED_BYTES = 3 * 4 * 256 * 4 + 4 * 8 + 4 * 4 + 64;   // [3][4][256] floats, 4 doubles, 4 floats
+constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256 + RED_BYTES;
+
+enum Mode { M_STORE_F32 = 0, M_FWD_TANH = 1, M_FWD_OUT = 2, M_BWD_TANH = 3, M_BWD_FIRST = 4, M_DW = 5 };
+
+struct Params {
+    int M, N, K;           // per-batch GEMM: out[M][N] = sum_k A(m,k) B(n,k)
+    int kb_per_split;      // k-blocks handled by one CTA (grid.y splits the K range)
+    int ntiles;            // ceil(rows / 128) for the per-tile partial arrays
+    int *err;
+    // outputs / epilogue operands
+    float *out_f32;                       // M_STORE_F32: [b][M][N]
+    __nv_bfloat16 *out; long out_b;       // bf16 [b][M][N]
+    const float *bias; long bias_b;       // [b][N]
+    const __nv_bfloat16 *aux; long aux_b; // A_i for the tanh slope [b][M][N]
+    const float *wout; long wout_b;       // output weights [b][N]
+    const float *bout;                    // [b]
+    const float *y;                       // targets [M]
+    float inv_s2;
+    double *u_part;                       // [b][ntiles]
+    float *dbout_part;                    // [b][ntiles]
+    float *dwout_part;                    // [b][ntiles][N]
+    float *db_part;                       // [b][ntiles][N] column sums of the produced delta
+    const float *x; int dx;               // M_BWD_FIRST: inputs [M][dx]
+    float *dw0_part;                      // [b][ntiles][N][dx]
+    const int *rowptr;                    // M_DW: entries of output row o are [rowptr[o], rowptr[o+1])
+    const int *ecol;                      // M_DW: column of entry j inside the layer
+    const int *erow;                      // M_DW: row of entry j
+    float *gw_part; long gw_split; long gw_b;   // M_DW: [split][b][k]
+};
+
+template <int MODE, bool A_MN, bool B_MN>
+__global__ void __launch_bounds__(NTHREADS, 2) k_umma(const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB, const Params p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 1);
+    float *red = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 256);   // [3][4][256]
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m_tile = blockIdx.x, split = blockIdx.y, b = blockIdx.z;
+    const int m0 = m_tile * BM;
+    const int BN = p.N;
+    const int total_kb = (p.K + BK - 1) / BK;
+    const int kb0 = split * p.kb_per_split;
+    const int nkb = min(p.kb_per_split, total_kb - kb0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        fence_mbar_init();
+        prefetch_map(&tmA);
+        prefetch_map(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer
+            const uint32_t bbytes = (uint32_t)BN * BK * 2;
+            int issued = 0;
+            for (int i = 0; i < nkb; ++i) {
+                const int s = i % STAGES;
+                const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.err)) { ok = false; break; }
+                const uint32_t fb = full0 + 8 * s;
+                mbar_expect_tx(fb, A_STAGE_BYTES + bbytes);
+                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_STAGE_BYTES;
+                const int kc = (kb0 + i) * BK;
+                if (!A_MN) {
+                    tma_load_3d(sa, &tmA, kc, m0, b, fb);
+                } else {
+                    tma_load_3d(sa, &tmA, m0, kc, b, fb);
+                    tma_load_3d(sa + 8192, &tmA, m0 + 64, kc, b, fb);
+                }
+                if (!B_MN) {
+                    tma_load_3d(sb, &tmB, kc, 0, b, fb);
+                } else {
+                    for (int a = 0; a < BN / 64; ++a) tma_load_3d(sb + 8192 * a, &tmB, 64 * a, kc, b, fb);
+                }
+                ++issued;
+            }
+            if (!ok) {   // let the copies already in flight land before the CTA exits
+                for (int i = max(0, issued - STAGES); i < issued; ++i)
+                    mbar_wait(full0 + 8 * (i % STAGES), (uint32_t)(i / STAGES) & 1u, p.err, 100000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            const uint32_t idesc = idesc_bf16(BM, BN, A_MN, B_MN);
+            for (int i = 0; i < nkb; ++i) {
+                const int s = i % STAGES;
+                const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+                if (!mbar_wait(full0 + 8 * s, ph, p.err)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_STAGE_BYTES;
+#pragma unroll
+                for (int ks = 0; ks < BK / 16; ++ks) {
+                    const uint64_t ad = A_MN ? sdesc(sa + 2048 * ks, 8192, 1024) : sdesc(sa + 32 * ks, 0, 1024);
+                    const uint64_t bd = B_MN ? sdesc(sb + 2048 * ks, 8192, 1024) : sdesc(sb + 32 * ks, 0, 1024);
+                    mma_bf16(tmem, ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
+                }
+                mma_commit(empty0 + 8 * s);
+            }
+            mma_commit(accb);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, one accumulator row per thread ----------------
+        const int q = warp & 3;               // TMEM lane quadrant this warp may access
+        const int row = 32 * q + lane;
+        const int m = m0 + row;
+        const bool valid = m < p.M;
+        const int et = threadIdx.x - 64;      // 0..127
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16);
+        ok = mbar_wait(accb, 0, p.err);
+        tc_fence_after();
+        if (ok) {
+            if (MODE == M_STORE_F32) {
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
+                    if (valid) {
+                        float4 *o = reinterpret_cast<float4 *>(p.out_f32 + ((long)b * p.M + m) * p.N + c0);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    }
+                }
+            } else if (MODE == M_FWD_TANH) {
+                const float *bias = p.bias + (long)b * p.bias_b;
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
+                    if (valid) {
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            pk[j] = pack_bf16(tanh_fast(v[2 * j] + bias[c0 + 2 * j]),
+                                              tanh_fast(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
+                        uint4 *o = reinterpret_cast<uint4 *>(p.out + (long)b * p.out_b + (long)m * p.N + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    }
+                }
+            } else if (MODE == M_FWD_OUT) {
+                const float *bias = p.bias + (long)b * p.bias_b;
+                const float *wo = p.wout + (long)b * p.wout_b;
+                float f = p.bout[b];
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) f += tanh_fast(v[j] + bias[c0 + j]) * wo[c0 + j];
+                }
+                const float r = valid ? f - p.y[m] : 0.0f;
+                const float d = r * p.inv_s2;   // delta of the output
+                double r2 = (double)r * (double)r;
+                float dsum = d;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+                    dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+                }
+                double *rd = reinterpret_cast<double *>(red + 3 * 4 * 256);   // 4 doubles after the float arrays
+                float *dsm = red + 3 * 4 * 256 + 8;                           // 4 floats after the doubles
+                if (lane == 0) {
+                    rd[q] = r2;
+                    dsm[q] = dsum;
+                }
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    float v[32], dw[32], dd[32];
+                    tmem_ld32(taddr + c0, v);
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float a = tanh_fast(v[j] + bias[c0 + j]);
+                        dw[j] = d * a;
+                        dd[j] = d * wo[c0 + j] * (1.0f - a * a);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
+                    if (valid) {
+                        uint4 *o = reinterpret_cast<uint4 *>(p.out + (long)b * p.out_b + (long)m * p.N + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    }
+                    red[(0 * 4 + q) * 256 + c0 + lane] = reduce_scatter32(dw);
+                    red[(1 * 4 + q) * 256 + c0 + lane] = reduce_scatter32(dd);
+                }
+                named_bar_sync(1, 128);
+                for (int c = et; c < BN; c += 128) {
+                    const long o = ((long)b * p.ntiles + m_tile) * p.N + c;
+                    p.dwout_part[o] = red[(0 * 4 + 0) * 256 + c] + red[(0 * 4 + 1) * 256 + c] +
+                                      red[(0 * 4 + 2) * 256 + c] + red[(0 * 4 + 3) * 256 + c];
+                    p.db_part[o] = red[(1 * 4 + 0) * 256 + c] + red[(1 * 4 + 1) * 256 + c] +
+                                   red[(1 * 4 + 2) * 256 + c] + red[(1 * 4 + 3) * 256 + c];
+                }
+                if (et == 0) {
+                    p.u_part[(long)b * p.ntiles + m_tile] = rd[0] + rd[1] + rd[2] + rd[3];
+                    p.dbout_part[(long)b * p.ntiles + m_tile] = dsm[0] + dsm[1] + dsm[2] + dsm[3];
+                }
+            } else if (MODE == M_BWD_TANH || MODE == M_BWD_FIRST) {
+                const __nv_bfloat16 *aux = p.aux + (long)b * p.aux_b + (long)(valid ? m : 0) * p.N;
+                float xv[8];
+#pragma unroll
+                for (int d = 0; d < 8; ++d) xv[d] = (MODE == M_BWD_FIRST && valid && d < p.dx) ? p.x[(long)m * p.dx + d] : 0.0f;
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    float v[32], dd[32];
+                    tmem_ld32(taddr + c0, v);
+                    if (valid) {
+                        const uint4 *ap = reinterpret_cast<const uint4 *>(aux + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const uint4 u = ap[j];
+                            const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                const float2 a = unpack_bf16(w4[t]);
+                                dd[8 * j + 2 * t] = v[8 * j + 2 * t] * (1.0f - a.x * a.x);
+                                dd[8 * j + 2 * t + 1] = v[8 * j + 2 * t + 1] * (1.0f - a.y * a.y);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) dd[j] = 0.0f;
+                    }
+                    if (MODE == M_BWD_TANH && valid) {
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
+                        uint4 *o = reinterpret_cast<uint4 *>(p.out + (long)b * p.out_b + (long)m * p.N + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    }
+                    if (MODE == M_BWD_FIRST) {
+                        for (int d = 0; d < p.dx; ++d) {
+                            float t[32];
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) t[j] = dd[j] * xv[d];
+                            const float cs = reduce_scatter32(t);
+                            // per-warp column sums of delta_1 * x_d go to dw0_part via the reduction buffer below
+                            red[(2 * 4 + q) * 256 + c0 + lane] = cs;
+                            named_bar_sync(1, 128);
+                            if (et < 32) {
+                                const int c = c0 + et;
+                                const float s = red[(2 * 4 + 0) * 256 + c] + red[(2 * 4 + 1) * 256 + c] +
+                                                red[(2 * 4 + 2) * 256 + c] + red[(2 * 4 + 3) * 256 + c];
+                                p.dw0_part[(((long)b * p.ntiles + m_tile) * p.N + c) * p.dx + d] = s;
+                            }
+                            named_bar_sync(1, 128);
+                        }
+                    }
+                    red[(1 * 4 + q) * 256 + c0 + lane] = reduce_scatter32(dd);
+                }
+                named_bar_sync(1, 128);
+                for (int c = et; c < BN; c += 128) {
+                    const long o = ((long)b * p.ntiles + m_tile) * p.N + c;
+                    p.db_part[o] = red[(1 * 4 + 0) * 256 + c] + red[(1 * 4 + 1) * 256 + c] +
+                                   red[(1 * 4 + 2) * 256 + c] + red[(1 * 4 + 3) * 256 + c];
+                }
+            } else if (MODE == M_DW) {
+                // stage the fp32 tile in the (now idle) operand buffers, half of the columns at a time
+                float *stg = reinterpret_cast<float *>(smem);
+                const int r_end = min(m0 + BM, p.M);
+                const int j0 = p.rowptr[m0], j1 = p.rowptr[r_end];
+                for (int h0 = 0; h0 < BN; h0 += 128) {
+                    const int hc = min(128, BN - h0);
+                    for (int c0 = 0; c0 < hc; c0 += 32) {
+                        float v[32];
+                        tmem_ld32(taddr + h0 + c0, v);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) stg[row * 129 + c0 + j] = v[j];
+                    }
+                    named_bar_sync(1, 128);
+                    for (int j = j0 + et; j < j1; j += 128) {
+                        const int c = p.ecol[j] - h0;
+                        if (c >= 0 && c < hc)
+                            p.gw_part[(long)split * p.gw_split + (long)b * p.gw_b + j] = stg[(p.erow[j] - m0) * 129 + c];
+                    }
+                    named_bar_sync(1, 128);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core kernels around the tensor-core GEMMs
+// ---------------------------------------------------------------------------
+
+// A_1[b][n][o] = tanh(sum_d X[n][d] W0[b][o][d] + b0[b][o]) in bf16.
+__global__ void __launch_bounds__(256) k_first_fwd(const float *x, int dx, long N, int w, const float *W0,
+                                                   const float *b0, __nv_bfloat16 *A1)
+{
+    const int b = blockIdx.y;
+    const long total = N * (long)(w / 2);
+    const float *Wb = W0 + (long)b * w * dx;
+    const float *bb = b0 + (long)b * w;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const long n = i / (w / 2);
+        const int o = (int)(i % (w / 2)) * 2;
+        float z0 = bb[o], z1 = bb[o + 1];
+        for (int d = 0; d < dx; ++d) {
+            const float xv = x[n * dx + d];
+            z0 += xv * Wb[(long)o * dx + d];
+            z1 += xv * Wb[(long)(o + 1) * dx + d];
+        }
+        reinterpret_cast<uint32_t *>(A1 + (long)b * N * w)[(n * w + o) / 2] = pack_bf16(tanh_fast(z0), tanh_fast(z1));
+    }
+}
+
+// Per-entry source of the gradient, decoded by k_finalize_bf16.
+enum EntryKind { E_HIDDEN_W = 0, E_BIAS = 1, E_W0 = 2, E_WOUT = 3, E_BOUT = 4 };
+
+struct FinalArgs {
+    int k, ntiles, nsplit, w, dx;
+    const int *kind, *layer, *off;   // per entry
+    const double *u_part;            // [b][ntiles]
+    const float *gw_part;            // [split][b][k]
+    long gw_split;
+    const float *const *db_part;     // per bias layer: [b][ntiles][w]
+    const float *dw0_part;           // [b][ntiles][w][dx]
+    const float *dwout_part;         // [b][ntiles][w]
+    const float *dbout_part;         // [b][ntiles]
+    double half_inv_s2, inv_a2;
+};
+
+__global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float *q, double *U, float *g)
+{
+    __shared__ double sm[8];
+    const int b = blockIdx.x;
+    double pr = 0.0;
+    for (int j = threadIdx.x; j < a.k; j += blockDim.x) {
+        const float qj = q[(long)b * a.k + j];
+        pr += (double)qj * (double)qj;
+        const int kd = a.kind[j], off = a.off[j];
+        float s = 0.0f;
+        if (kd == E_HIDDEN_W) {
+            for (int t = 0; t < a.nsplit; ++t) s += a.gw_part[t * a.gw_split + (long)b * a.k + j];
+        } else if (kd == E_BIAS) {
+            const float *dp = a.db_part[a.layer[j]] + (long)b * a.ntiles * a.w + off;
+            for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w];
+        } else if (kd == E_W0) {
+            const float *dp = a.dw0_part + (long)b * a.ntiles * a.w * a.dx + off;
+            for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w * a.dx];
+        } else if (kd == E_WOUT) {
+            const float *dp = a.dwout_part + (long)b * a.ntiles * a.w + off;
+            for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w];
+        } else {
+            const float *dp = a.dbout_part + (long)b * a.ntiles;
+            for (int t = 0; t < a.ntiles; ++t) s += dp[t];
+        }
+        if (g) g[(long)b * a.k + j] = s + qj * (float)a.inv_a2;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, o);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = pr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < 8; ++i) t += sm[i];
+        double lik = 0.0;
+        for (int i = 0; i < a.ntiles; ++i) lik += a.u_part[(long)b * a.ntiles + i];
+        U[b] = lik * a.half_inv_s2 + 0.5 * t * a.inv_a2;
+    }
+}
+
+template <typename V>
+__global__ void k_scatter_plan(const float *q, long k, ScatterPlan sc)
+{
+    const int b = blockIdx.y;
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (long)gridDim.x * blockDim.x) {
+        const int bi = sc.buf_id[j];
+        const long o = (long)b * sc.cstride[bi] + sc.off[j];
+        const float v = q[(long)b * k + j];
+        if (sc.is_bf16[bi]) reinterpret_cast<__nv_bfloat16 *>(sc.base[bi])[o] = __float2bfloat16_rn(v);
+        else reinterpret_cast<float *>(sc.base[bi])[o] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        HMC_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &qr));
+        if (qr != cudaDriverEntryPointSuccess || !ptr) {
+            set_error("cuTensorMapEncodeTiled is not available from the driver");
+            throw Fail{HMC_ERR_CUDA};
+        }
+        fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    return fn;
+}
+
+// bf16 tensor [outer][mid][inner] with a (box_inner x box_mid x 1) box, 128-byte swizzle.
+CUtensorMap make_map(const void *base, uint64_t inner, uint64_t mid, uint64_t outer, uint32_t box_inner,
+                     uint32_t box_mid)
+{
+    CUtensorMap m;
+    memset(&m, 0, sizeof m);
+    cuuint64_t dims[3] = {inner, mid, outer};
+    cuuint64_t strides[2] = {inner * 2, inner * mid * 2};
+    cuuint32_t box[3] = {box_inner, box_mid, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for dims %llu x %llu x %llu box %u x %u", (int)r,
+                  (unsigned long long)inner, (unsigned long long)mid, (unsigned long long)outer, box_inner, box_mid);
+        throw Fail{HMC_ERR_CUDA};
+    }
+    return m;
+}
+
+template <int MODE, bool A_MN, bool B_MN>
+void launch_umma(const CUtensorMap &a, const CUtensorMap &b, const Params &p, dim3 grid, cudaStream_t s)
+{
+    static bool configured = false;
+    if (!configured) {
+        HMC_CK(cudaFuncSetAttribute(k_umma<MODE, A_MN, B_MN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        configured = true;
+    }
+    k_umma<MODE, A_MN, B_MN><<<grid, NTHREADS, SMEM_BYTES, s>>>(a, b, p);
+    HMC_LAUNCH_CK();
+}
+
+int pick_splits(int total_kb, int ctas_without_split, int target)
+{
+    int s = std::max(1, target / std::max(1, ctas_without_split));
+    return std::min(s, total_kb);
+}
+
+class UmmaEngine final : public Engine {
+  public:
+    UmmaEngine(Problem &p, int C) : p_(p), C_(C)
+    {
+        const NetDesc &nd = p.net;
+        L_ = nd.L;
+        w_ = nd.w[1];
+        dx_ = nd.w[0];
+        N_ = p.n;
+        k_ = p.k;
+        ntiles_ = (int)std::max<long>(1, (N_ + BM - 1) / BM);
+        int dev = 0;
+        HMC_CK(cudaGetDevice(&dev));
+        HMC_CK(cudaDeviceGetAttribute(&num_sms_, cudaDevAttrMultiProcessorCount, dev));
+        HMC_CK(cudaMalloc(&err_, sizeof(int)));
+        HMC_CK(cudaMemset(err_, 0, sizeof(int)));
+
+        // data
+        std::vector<float> xf(p.x.begin(), p.x.end()), yf(p.y.begin(), p.y.end());
+        x_.alloc(sizeof(float) * std::max<size_t>(xf.size(), 1));
+        y_.alloc(sizeof(float) * std::max<size_t>(yf.size(), 1));
+        if (!xf.empty()) HMC_CK(cudaMemcpy(x_.ptr, xf.data(), sizeof(float) * xf.size(), cudaMemcpyHostToDevice));
+        if (!yf.empty()) HMC_CK(cudaMemcpy(y_.ptr, yf.data(), sizeof(float) * yf.size(), cudaMemcpyHostToDevice));
+
+        // parameters per chain, initialised from the frozen vector
+        const int nh = L_ - 2;   // hidden w->w layers 1..L-2
+        W0_.alloc(sizeof(float) * C * w_ * dx_);
+        b0_.alloc(sizeof(float) * C * w_);
+        Wh_.resize(nh);
+        bh_.resize(nh);
+        for (int i = 0; i < nh; ++i) {
+            Wh_[i].reset(new DevBuf(sizeof(__nv_bfloat16) * C * w_ * w_));
+            bh_[i].reset(new DevBuf(sizeof(float) * C * w_));
+        }
+        wout_.alloc(sizeof(float) * C * w_);
+        bout_.alloc(sizeof(float) * C);
+        upload_rep(W0_, nd.woff[0], (long)w_ * dx_);
+        upload_rep(b0_, nd.boff[0], w_);
+        for (int i = 0; i < nh; ++i) {
+            upload_rep_bf16(*Wh_[i], nd.woff[i + 1], (long)w_ * w_);
+            upload_rep(*bh_[i], nd.boff[i + 1], w_);
+        }
+        upload_rep(wout_, nd.woff[L_ - 1], w_);
+        upload_rep(bout_, nd.boff[L_ - 1], 1);
+
+        // activations A_1..A_{L-2} and deltas delta_2..delta_{L-1}
+        const size_t act_bytes = sizeof(__nv_bfloat16) * C * std::max<long>(N_, 1) * w_;
+        A_.resize(L_);   // index i = 1..L-2
+        D_.resize(L_);   // index i = 2..L-1
+        for (int i = 1; i <= L_ - 2; ++i) A_[i].reset(new DevBuf(act_bytes));
+        for (int i = 2; i <= L_ - 1; ++i) D_[i].reset(new DevBuf(act_bytes));
+
+        // partials
+        u_part_.alloc(sizeof(double) * C * ntiles_);
+        dbout_part_.alloc(sizeof(float) * C * ntiles_);
+        dwout_part_.alloc(sizeof(float) * C * ntiles_ * w_);
+        dw0_part_.alloc(sizeof(float) * C * ntiles_ * w_ * dx_);
+        db_part_.resize(L_ - 1);   // biases of layers 0..L-2
+        for (int l = 0; l <= L_ - 2; ++l) db_part_[l].reset(new DevBuf(sizeof(float) * C * ntiles_ * w_));
+        std::vector<const float *> dbp(L_ - 1);
+        for (int l = 0; l <= L_ - 2; ++l) dbp[l] = db_part_[l]->as<float>();
+        db_ptrs_.alloc(sizeof(float *) * dbp.size());
+        HMC_CK(cudaMemcpy(db_ptrs_.ptr, dbp.data(), sizeof(float *) * dbp.size(), cudaMemcpyHostToDevice));
+
+        // per-entry metadata, scatter plan, per-layer CSR of the sampled hidden weights
+        build_entries();
+
+        // split of the weight-gradient GEMMs over rows: about two CTAs per SM
+        const int total_kb = (int)((N_ + BK - 1) / BK);
+        nsplit_ = pick_splits(total_kb, ((w_ + BM - 1) / BM) * C, 2 * num_sms_);
+        gw_part_.alloc(sizeof(float) * nsplit_ * C * std::max<long>(k_, 1));
+        HMC_CK(cudaMemset(gw_part_.ptr, 0, gw_part_.n));
+
+        // tensor maps
+        for (int i = 1; i <= L_ - 2; ++i) {
+            A_row_[i] = make_map(A_[i]->ptr, w_, N_, C, 64, 128);
+            A_atom_[i] = make_map(A_[i]->ptr, w_, N_, C, 64, 64);
+            W_fwd_[i] = make_map(Wh_[i - 1]->ptr, w_, w_, C, 64, w_);
+            W_atom_[i] = make_map(Wh_[i - 1]->ptr, w_, w_, C, 64, 64);
+        }
+        for (int i = 2; i <= L_ - 1; ++i) {
+            D_row_[i] = make_map(D_[i]->ptr, w_, N_, C, 64, 128);
+            D_atom_[i] = make_map(D_[i]->ptr, w_, N_, C, 64, 64);
+        }
+    }
+
+    ~UmmaEngine() override
+    {
+        if (err_) cudaFree(err_);
+    }
+
+    size_t bytes() const override { return 0; }
+
+    ScatterPlan scatter_plan() override { return plan_; }
+
+    void energy_grad(const void *qv, double *U, void *gv, bool scattered, cudaStream_t s) override
+    {
+        const float *q = static_cast<const float *>(qv);
+        float *g = static_cast<float *>(gv);
+        if (!scattered) {
+            dim3 grid((unsigned)std::min<long>((k_ + 255) / 256, 1024), C_);
+            k_scatter_plan<float><<<grid, 256, 0, s>>>(q, k_, plan_);
+            HMC_LAUNCH_CK();
+        }
+        const NetDesc &nd = p_.net;
+        Params base{};
+        base.err = err_;
+        base.ntiles = ntiles_;
+        const long act_b = N_ * (long)w_;
+        const dim3 row_grid(ntiles_, 1, C_);
+        // first layer
+        {
+            const long total = N_ * (long)(w_ / 2);
+            dim3 grid((unsigned)std::min<long>((total + 255) / 256, 4 * num_sms_), C_);
+            k_first_fwd<<<grid, 256, 0, s>>>(x_.as<float>(), dx_, N_, w_, W0_.as<float>(), b0_.as<float>(),
+                                             A_[1]->as<__nv_bfloat16>());
+            HMC_LAUNCH_CK();
+        }
+        // hidden layers i = 1..L-3 (tanh), then layer L-2 fused with the output layer
+        for (int i = 1; i <= L_ - 2; ++i) {
+            Params pp = base;
+            pp.M = (int)N_;
+            pp.N = w_;
+            pp.K = w_;
+            pp.kb_per_split = (w_ + BK - 1) / BK;
+            pp.bias = bh_[i - 1]->as<float>();
+            pp.bias_b = w_;
+            if (i < L_ - 2) {
+                pp.out = A_[i + 1]->as<__nv_bfloat16>();
+                pp.out_b = act_b;
+                launch_umma<M_FWD_TANH, false, false>(A_row_[i], W_fwd_[i], pp, row_grid, s);
+            } else {
+                pp.out = D_[L_ - 1]->as<__nv_bfloat16>();
+                pp.out_b = act_b;
+                pp.wout = wout_.as<float>();
+                pp.wout_b = w_;
+                pp.bout = bout_.as<float>();
+                pp.y = y_.as<float>();
+                pp.inv_s2 = (float)(1.0 / (p_.sigma * p_.sigma));
+                pp.u_part = u_part_.as<double>();
+                pp.dbout_part = dbout_part_.as<float>();
+                pp.dwout_part = dwout_part_.as<float>();
+                pp.db_part = db_part_[L_ - 2]->as<float>();
+                launch_umma<M_FWD_OUT, false, false>(A_row_[i], W_fwd_[i], pp, row_grid, s);
+            }
+        }
+        // reverse: delta_i = (delta_{i+1} W_i) (1 - A_i^2) for i = L-2 .. 1 (down to the lowest sampled layer)
+        for (int i = L_ - 2; i >= 1; --i) {
+            if (i <= nd.lmin) break;   // no layer below i holds a sampled parameter
+            Params pp = base;
+            pp.M = (int)N_;
+            pp.N = w_;
+            pp.K = w_;
+            pp.kb_per_split = (w_ + BK - 1) / BK;
+            pp.aux = A_[i]->as<__nv_bfloat16>();
+            pp.aux_b = act_b;
+            pp.db_part = db_part_[i - 1]->as<float>();
+            if (i > 1) {
+                pp.out = D_[i]->as<__nv_bfloat16>();
+                pp.out_b = act_b;
+                launch_umma<M_BWD_TANH, false, true>(D_row_[i + 1], W_atom_[i], pp, row_grid, s);
+            } else {
+                pp.x = x_.as<float>();
+                pp.dx = dx_;
+                pp.dw0_part = dw0_part_.as<float>();
+                launch_umma<M_BWD_FIRST, false, true>(D_row_[i + 1], W_atom_[i], pp, row_grid, s);
+            }
+        }
+        // weight gradients of the hidden layers at the sampled entries
+        for (int i = 1; i <= L_ - 2; ++i) {
+            if (layer_entries_[i] == 0) continue;
+            Params pp = base;
+            pp.M = w_;
+            pp.N = w_;
+            pp.K = (int)N_;
+            const int total_kb = (int)((N_ + BK - 1) / BK);
+            pp.kb_per_split = (total_kb + nsplit_ - 1) / nsplit_;
+            pp.rowptr = rowptr_[i]->as<int>();
+            pp.ecol = ecol_.as<int>();
+            pp.erow = erow_.as<int>();
+            pp.gw_part = gw_part_.as<float>();
+            pp.gw_split = (long)C_ * k_;
+            pp.gw_b = k_;
+            const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
+            dim3 grid((w_ + BM - 1) / BM, splits, C_);
+            launch_umma<M_DW, true, true>(D_atom_[i + 1], A_atom_[i], pp, grid, s);
+        }
+        FinalArgs fa{};
+        fa.k = (int)k_;
+        fa.ntiles = ntiles_;
+        fa.nsplit = nsplit_eff();
+        fa.w = w_;
+        fa.dx = dx_;
+        fa.kind = kind_.as<int>();
+        fa.layer = layer_.as<int>();
+        fa.off = off_.as<int>();
+        fa.u_part = u_part_.as<double>();
+        fa.gw_part = gw_part_.as<float>();
+        fa.gw_split = (long)C_ * k_;
+        fa.db_part = db_ptrs_.as<const float *>();
+        fa.dw0_part = dw0_part_.as<float>();
+        fa.dwout_part = dwout_part_.as<float>();
+        fa.dbout_part = dbout_part_.as<float>();
+        fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
+        fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
+        k_finalize_bf16<<<C_, 256, 0, s>>>(fa, q, U, g);
+        HMC_LAUNCH_CK();
+    }
+
+  private:
+    int nsplit_eff() const
+    {
+        const int total_kb = (int)((N_ + BK - 1) / BK);
+        const int per = (total_kb + nsplit_ - 1) / nsplit_;
+        return (total_kb + per - 1) / per;
+    }
+
+    void upload_rep(DevBuf &dst, long off, long count)
+    {
+        std::vector<float> v(C_ * count);
+        for (int c = 0; c < C_; ++c)
+            for (long i = 0; i < count; ++i) v[c * count + i] = (float)p_.frozen[off + i];
+        HMC_CK(cudaMemcpy(dst.ptr, v.data(), sizeof(float) * v.size(), cudaMemcpyHostToDevice));
+    }
+
+    void upload_rep_bf16(DevBuf &dst, long off, long count)
+    {
+        std::vector<__nv_bfloat16> v(C_ * count);
+        for (int c = 0; c < C_; ++c)
+            for (long i = 0; i < count; ++i) v[c * count + i] = __float2bfloat16_rn((float)p_.frozen[off + i]);
+        HMC_CK(cudaMemcpy(dst.ptr, v.data(), sizeof(__nv_bfloat16) * v.size(), cudaMemcpyHostToDevice));
+    }
+
+    void build_entries()
+    {
+        const NetDesc &nd = p_.net;
+        std::vector<int> kind(k_), layer(k_), off(k_), erow(k_, 0), ecol(k_, 0), bid(k_), boff(k_);
+        std::vector<std::vector<int>> rp(L_, std::vector<int>(w_ + 1, 0));
+        layer_entries_.assign(L_, 0);
+        // scatter buffers: 0 W0, 1 b0, 2+2(i-1) W_i (bf16), 3+2(i-1) b_i, then wout, bout
+        const int nh = L_ - 2;
+        plan_.nbuf = 2 + 2 * nh + 2;
+        HMC_REQUIRE(plan_.nbuf <= MAX_SCATTER_BUFS, "too many layers for the scatter plan");
+        plan_.base[0] = W0_.ptr; plan_.cstride[0] = (long)w_ * dx_; plan_.is_bf16[0] = 0;
+        plan_.base[1] = b0_.ptr; plan_.cstride[1] = w_; plan_.is_bf16[1] = 0;
+        for (int i = 1; i <= nh; ++i) {
+            plan_.base[2 + 2 * (i - 1)] = Wh_[i - 1]->ptr;
+            plan_.cstride[2 + 2 * (i - 1)] = (long)w_ * w_;
+            plan_.is_bf16[2 + 2 * (i - 1)] = 1;
+            plan_.base[3 + 2 * (i - 1)] = bh_[i - 1]->ptr;
+            plan_.cstride[3 + 2 * (i - 1)] = w_;
+            plan_.is_bf16[3 + 2 * (i - 1)] = 0;
+        }
+        plan_.base[2 + 2 * nh] = wout_.ptr; plan_.cstride[2 + 2 * nh] = w_; plan_.is_bf16[2 + 2 * nh] = 0;
+        plan_.base[3 + 2 * nh] = bout_.ptr; plan_.cstride[3 + 2 * nh] = 1; plan_.is_bf16[3 + 2 * nh] = 0;
+        for (long j = 0; j < k_; ++j) {
+            const long id = p_.idx[j];
+            int l = 0;
+            while (l + 1 < L_ && id >= nd.woff[l + 1]) ++l;
+            const long wend = nd.woff[l] + (long)nd.w[l + 1] * nd.w[l];
+            const bool is_w = id < wend;
+            const long rel = is_w ? id - nd.woff[l] : id - nd.boff[l];
+            const int in = nd.w[l];
+            if (l == 0) {
+                kind[j] = is_w ? E_W0 : E_BIAS;
+                layer[j] = 0;
+                off[j] = (int)rel;   // o*dx + d, or o
+                bid[j] = is_w ? 0 : 1;
+                boff[j] = (int)rel;
+            } else if (l == L_ - 1) {
+                kind[j] = is_w ? E_WOUT : E_BOUT;
+                off[j] = is_w ? (int)rel : 0;
+                bid[j] = is_w ? 2 + 2 * nh : 3 + 2 * nh;
+                boff[j] = is_w ? (int)rel : 0;
+            } else {
+                if (is_w) {
+                    kind[j] = E_HIDDEN_W;
+                    erow[j] = (int)(rel / in);
+                    ecol[j] = (int)(rel % in);
+                    rp[l][erow[j] + 1]++;
+                    layer_entries_[l]++;
+                    bid[j] = 2 + 2 * (l - 1);
+                } else {
+                    kind[j] = E_BIAS;
+                    layer[j] = l;
+                    off[j] = (int)rel;
+                    bid[j] = 3 + 2 * (l - 1);
+                }
+                boff[j] = (int)rel;
+            }
+        }
+        // row pointers: entries are ascending in parameter index, so a layer's weight entries
+        // are contiguous and sorted by (row, column); rowptr holds absolute entry indices
+        rowptr_.resize(L_);
+        for (int l = 1; l <= L_ - 2; ++l) {
+            long first = std::lower_bound(p_.idx.begin(), p_.idx.end(), nd.woff[l]) - p_.idx.begin();
+            std::vector<int> r(w_ + 1);
+            r[0] = (int)first;
+            for (int o = 0; o < w_; ++o) r[o + 1] = r[o] + rp[l][o + 1];
+            rowptr_[l].reset(new DevBuf(sizeof(int) * (w_ + 1)));
+            HMC_CK(cudaMemcpy(rowptr_[l]->ptr, r.data(), sizeof(int) * (w_ + 1), cudaMemcpyHostToDevice));
+        }
+        auto up = [&](DevBuf &d, const std::vector<int> &v) {
+            d.alloc(sizeof(int) * std::max<size_t>(v.size(), 1));
+            if (!v.empty()) HMC_CK(cudaMemcpy(d.ptr, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
+        };
+        up(kind_, kind);
+        up(layer_, layer);
+        up(off_, off);
+        up(erow_, erow);
+        up(ecol_, ecol);
+        up(sc_off_, boff);
+        std::vector<uint8_t> b8(bid.begin(), bid.end());
+        sc_bid_.alloc(std::max<size_t>(b8.size(), 1));
+        HMC_CK(cudaMemcpy(sc_bid_.ptr, b8.data(), b8.size(), cudaMemcpyHostToDevice));
+        plan_.buf_id = sc_bid_.as<uint8_t>();
+        plan_.off = sc_off_.as<int>();
+    }
+
+    Problem &p_;
+    int C_, L_ = 0, w_ = 0, dx_ = 0, ntiles_ = 1, nsplit_ = 1, num_sms_ = 148;
+    long N_ = 0, k_ = 0;
+    int *err_ = nullptr;
+    DevBuf x_, y_, W0_, b0_, wout_, bout_, u_part_, dbout_part_, dwout_part_, dw0_part_, db_ptrs_, gw_part_;
+    DevBuf kind_, layer_, off_, erow_, ecol_, sc_off_, sc_bid_;
+    std::vector<std::unique_ptr<DevBuf>> Wh_, bh_, A_, D_, db_part_, rowptr_;
+    std::vector<int> layer_entries_;
+    CUtensorMap A_row_[MAXL], A_atom_[MAXL], W_fwd_[MAXL], W_atom_[MAXL], D_row_[MAXL], D_atom_[MAXL];
+    ScatterPlan plan_;
+};
+
+}  // namespace
+
+bool umma_engine_supports(const Problem &p, std::string *why)
+{
+    auto no = [&](const char *m) {
+        if (why) *why = m;
+        return false;
+    };
+    if (p.kind != HMC_NET_MLP) return no("only MLPs run on the tensor-core path (DeepONet: use FP32/FP64)");
+    const NetDesc &nd = p.net;
+    if (nd.L < 3) return no("need at least one hidden-to-hidden layer");
+    const int w = nd.w[1];
+    if (w % 64 != 0 || w > 256) return no("hidden width must be 64, 128, 192 or 256");
+    for (int l = 1; l < nd.L; ++l)
+        if (nd.w[l] != w) return no("all hidden layers must have the same width");
+    if (nd.w[nd.L] != 1) return no("the output width must be 1");
+    if (nd.w[0] < 1 || nd.w[0] > 8) return no("input width must be 1..8");
+    for (int l = 0; l < nd.L - 1; ++l)
+        if (nd.act[l] != HMC_ACT_TANH) return no("hidden activations must be tanh");
+    if (nd.act[nd.L - 1] != HMC_ACT_IDENTITY) return no("the output activation must be the identity");
+    for (int l = 0; l < nd.L; ++l)
+        if (!nd.bias[l]) return no("every layer must have a bias");
+    if (p.n < 1) return no("need at least one data point");
+    return true;
+}
+
+Engine *make_umma_engine_bf16(Problem &p, int C) { return new UmmaEngine(p, C); }
+
+}  // namespace hmc
+
+// ---------------------------------------------------------------------------
+// Diagnostic: one batched tensor-core GEMM, C[b][m][n] = sum_k A(m,k) B(n,k)
+// ---------------------------------------------------------------------------
+extern "C" hmc_status hmc_diag_umma_gemm(int M, int N, int K, int batch, int a_mn, int b_mn, const void *A,
+                                         const void *B, float *Cout)
+{
+    using namespace hmc;
+    try {
+        HMC_REQUIRE(M >= 1 && K >= 1 && batch >= 1 && N >= 64 && N <= 256 && N % 64 == 0, "bad GEMM shape");
+        HMC_REQUIRE(A && B && Cout, "NULL pointer");
+        HMC_REQUIRE(K % 8 == 0 && M % 8 == 0, "row strides must be 16-byte multiples");
+        CUtensorMap ma = a_mn ? make_map(A, M, K, batch, 64, 64) : make_map(A, K, M, batch, 64, 128);
+        CUtensorMap mb = b_mn ? make_map(B, N, K, batch, 64, 64) : make_map(B, K, N, batch, 64, N);
+        Params p{};
+        p.M = M;
+        p.N = N;
+        p.K = K;
+        p.kb_per_split = (K + BK - 1) / BK;
+        p.out_f32 = Cout;
+        int *err = nullptr;
+        HMC_CK(cudaMalloc(&err, sizeof(int)));
+        HMC_CK(cudaMemset(err, 0, sizeof(int)));
+        p.err = err;
+        dim3 grid((M + BM - 1) / BM, 1, batch);
+        if (!a_mn && !b_mn) launch_umma<M_STORE_F32, false, false>(ma, mb, p, grid, 0);
+        else if (!a_mn && b_mn) launch_umma<M_STORE_F32, false, true>(ma, mb, p, grid, 0);
+        else if (a_mn && !b_mn) launch_umma<M_STORE_F32, true, false>(ma, mb, p, grid, 0);
+        else launch_umma<M_STORE_F32, true, true>(ma, mb, p, grid, 0);
+        HMC_CK(cudaDeviceSynchronize());
+        int herr = 0;
+        HMC_CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
+        cudaFree(err);
+        if (herr) {
+            set_error("a tensor-core pipeline wait timed out");
+            return HMC_ERR_TIMEOUT;
+        }
+        return HMC_OK;
+    } catch (const Fail &f) {
+        return f.st;
+    }
+}

@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Throughput of full-batch subset HMC on one GB300 (or N replicas on N GPUs).
+
+Workload: the wide-MLP subset-HMC configuration -- MLP 2-256-256-256-256-1 with
+tanh, 198,401 parameters, 8192 synthetic points (x ~ U[-1,1]^2,
+y = sin(pi x1) cos(pi x2) + N(0, 0.05^2)), a 5% subset (9,920 parameters) chosen
+by a seeded |N(0,1)| score, the rest frozen at seeded N(0, 0.05^2) values, prior
+N(0, 1), noise sigma 0.05, 16 chains, L = 50 leapfrog steps of eps = 5e-4.
+
+One step = one HMC trajectory for all chains: momentum draw, L x (drift with
+the subset scatter, forward pass, energy, adjoint, gather, kick), kinetic
+energy and the Metropolis step -- every row of the hot path.  The metric is
+gradient evaluations per second (one grad-eval = U and grad U for one chain), so
+value = chains * L * steps / time, summed over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (a
+bounded sample of the same workload: one gradient evaluation per chain per step).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "grad-evals/s"
+WORKLOAD = "wide_mlp: MLP 2-256-256-256-256-1 tanh, N=8192, 5% subset (k=9920), 16 chains, L=50, eps=5e-4"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _clock_sampler(stop, out):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return
+    dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+
+    def reader():
+        for line in p.stdout:
+            out.append(line.strip())
+
+    t = threading.Thread(target=reader, daemon=True)
+    t.start()
+    stop.wait()
+    p.terminate()
+    try:
+        p.wait(timeout=2)
+    except subprocess.TimeoutExpired:
+        p.kill()
+    t.join(timeout=1)
+
+
+def _summarise_clocks(lines, gpu_index):
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx = float(f[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() in ("active", "1", "yes"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def cpu_baseline(prob, threads=None, chains=None):
+    """The FP64 oracle as it stands: one gradient evaluation per chain, chains in parallel."""
+    import oracle
+    cores = threads or os.cpu_count() or 1
+    C = chains or min(cores, prob.chains)
+    o = oracle.Oracle(prob)
+    Q = np.repeat(prob.q0[:1], C, axis=0) if C > prob.chains else prob.q0[:C]
+    t0 = time.perf_counter()
+    o.energy_grad_batch(Q, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": C / dt, "unit": METRIC, "cores": min(cores, C), "kind": "oracle",
+            "sample": f"{C} gradient evaluations (one per chain) of the full workload, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    prob = W.wide_mlp()
+    secs, evals, cb = [], 0, None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(prob)
+        if i >= args.warmup:
+            secs.append(time.perf_counter() - t0)
+            evals += int(cb["sample"].split()[0])
+    value = evals / float(np.sum(secs))
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle: one gradient evaluation per chain per step)"},
+            "cpu_baseline": {**cb, "value": value},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def algorithmic(prob, C):
+    """Per-launch algorithmic FLOPs and DRAM bytes of each tensor-core kernel kind."""
+    N, w = prob.x.shape[0], prob.net.widths[1]
+    gemm = 2.0 * N * w * w * C
+    act = 2.0 * N * w * C                     # one bf16 activation array, all chains
+    wts = 2.0 * 2.0 * w * w * C               # bf16 hi + lo weights
+    k_layer = prob.k / max(1, prob.net.n_layers)
+    return {
+        "umma_fwd_tanh": (gemm, act + act + wts),
+        "umma_fwd_out": (gemm, act + act + wts + 4.0 * N),
+        "umma_bwd_tanh": (gemm, 3 * act + wts),
+        "umma_bwd_first": (gemm, 2 * act + wts),
+        "umma_dw": (gemm, 2 * act + 4.0 * k_layer * C),
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ess-traj", type=int, default=200, help="trajectories for the ESS/s comparison (0 = skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3, "timing rules need at least 3 warm-up steps"
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2507_14652_gb300 as hmc
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    hmc.lib()
+
+    prob = W.wide_mlp()
+    C, L, eps = prob.chains, prob.L, prob.eps
+    seed = 1000 + rank                      # replicas: independent chains per rank
+    s = hmc.Sampler.mlp(prob.net.widths, prob.x, prob.y, prob.mask, prob.frozen, C, prior_sigma=prob.prior_sigma,
+                        noise_sigma=prob.noise_sigma, prec=hmc.PREC_BF16)
+    q0 = torch.from_numpy(prob.q0).float().cuda()
+
+    # warm-up (captures the trajectory graph)
+    _, acc_w, dH_w, q = s.sample(q0, eps, L, args.warmup, seed=seed, keep_samples=False)
+    torch.cuda.synchronize()
+
+    # timed region: exactly `steps` trajectories
+    clock_lines, stop = [], threading.Event()
+    th = threading.Thread(target=_clock_sampler, args=(stop, clock_lines), daemon=True)
+    th.start()
+    time.sleep(0.5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    S, acc, dH, q_last = s.sample(q, eps, L, args.steps, seed=seed, first_traj=args.warmup, keep_samples=False)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stop.set()
+    th.join(timeout=5)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * C * L * args.steps / (ms / 1000.0)
+    graph_k = hmc.graph_kernels(s)
+    acc_np, dH_np = acc.cpu().numpy(), dH.cpu().numpy()
+
+    # live per-kernel times on the library's stream (roofline of the dominant kernel)
+    prof = hmc.profile_energy_grad(s, q_last, reps=5)
+    per_eval_launches = int(round(sum(v[1] for v in prof.values())))
+    gpu_launches = args.steps * graph_k + per_eval_launches + 1
+    peaks, peak_src = _peaks()
+    alg = algorithmic(prob, C)
+    dom = max(prof, key=lambda k: prof[k][0] * prof[k][1])
+    roof = None
+    if dom in alg:
+        fl, by = alg[dom]
+        t_ms = prof[dom][0]
+        t_hbm = by / (peaks["hbm_gbs"] * 1e9)
+        t_tc = fl / (peaks["bf16_tflops_sustained"] * 1e12)
+        if t_hbm >= t_tc:
+            ach = by / (t_ms / 1e3) / 1e9
+            roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                    "peak_source": peak_src + " (hbm_gbs)"}
+        else:
+            ach = fl / (t_ms / 1e3) / 1e12
+            roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops_sustained"],
+                    "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops_sustained"], "traffic": None,
+                    "peak_source": peak_src + " (bf16_tflops_sustained)"}
+        roof["kernel_ms"] = t_ms
+
+    # end to end through the public C ABI with pinned host buffers: every step copies
+    # the chain state in and the step's sample, accept flags and dH out
+    qh = torch.empty((C, prob.k), dtype=torch.float32, pin_memory=True)
+    qh.copy_(q_last.cpu())
+    Sh = torch.empty((1, C, prob.k), dtype=torch.float32, pin_memory=True)
+    ah = torch.empty((1, C), dtype=torch.uint8, pin_memory=True)
+    dh = torch.empty((1, C), dtype=torch.float64, pin_memory=True)
+    L_ = hmc.lib()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        st = L_.hmc_sample(s._h, qh.data_ptr(), float(eps), int(L), 1, int(seed), int(args.warmup + args.steps + i),
+                           Sh.data_ptr(), ah.data_ptr(), dh.data_ptr(), qh.data_ptr())
+        if st != 0:
+            raise hmc.HmcError(st, L_.hmc_last_error().decode())
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": ws * C * L * args.steps / t_e2e, "unit": METRIC, "h2d_bytes_per_step": 4 * C * prob.k,
+           "d2h_bytes_per_step": 4 * C * prob.k + C + 8 * C + 4 * C * prob.k}
+
+    # ESS/s: batched BF16 sampler vs the plain one-chain FP32 CUDA-core sampler
+    ess = None
+    if args.ess_traj > 0 and rank == 0:
+        from oracle.ess import ess_chains
+        ess = {}
+        for name, prec, chains in (("bf16_batched", hmc.PREC_BF16, C), ("fp32_plain_1chain", hmc.PREC_FP32, 1)):
+            sp = s if prec == hmc.PREC_BF16 else hmc.Sampler.mlp(
+                prob.net.widths, prob.x, prob.y, prob.mask, prob.frozen, 1, prior_sigma=prob.prior_sigma,
+                noise_sigma=prob.noise_sigma, prec=prec)
+            qs = q_last[:chains].contiguous()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            Se, ae, de, _ = sp.sample(qs, eps, L, args.ess_traj, seed=seed + 77)
+            b.record()
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) / 1000.0
+            e = ess_chains(Se.cpu().double().numpy()[args.ess_traj // 5:])
+            ess[name] = {"chains": chains, "trajectories": args.ess_traj, "seconds": sec,
+                         "ess_min": float(e.min()), "ess_median": float(np.median(e)),
+                         "ess_min_per_s": float(e.min()) / sec, "ess_median_per_s": float(np.median(e)) / sec,
+                         "accept_rate": float(ae.float().mean().item()),
+                         "grad_evals_per_s": chains * L * args.ess_traj / sec}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob)
+
+    clocks = _summarise_clocks(clock_lines, local)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "chains": C, "leapfrog_steps": L, "eps": eps,
+                           "subset_k": prob.k, "params": prob.P, "points": int(prob.x.shape[0]),
+                           "step": "one HMC trajectory for all chains (L gradient evaluations each)",
+                           "l2": "inputs larger than L2: 0.4 GB of bf16 activations and deltas per gradient evaluation",
+                           "parallelism": f"replicas x{ws}"},
+                "accept_rate": float(acc_np.mean()), "abs_dH_mean": float(np.nanmean(np.abs(dH_np))),
+                "abs_dH_median": float(np.nanmedian(np.abs(dH_np))),
+                "gpu_launches": gpu_launches, "kernels_per_trajectory": graph_k,
+                "roofline": roof, "kernel_ms": {k: v[0] for k, v in prof.items()},
+                "kernel_launches_per_eval": {k: v[1] for k, v in prof.items()},
+                "e2e": e2e, "cpu_baseline": cpu, "ess": ess, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -28,6 +28,23 @@ HMC_API hmc_status hmc_diag_momenta(unsigned long long seed, unsigned long long 
 HMC_API hmc_status hmc_diag_log_uniform(unsigned long long seed, unsigned long long problem, long n_chain, long n_traj,
                                 double *out_host);
 
+/* Kernel nodes in the captured graph of one trajectory of the last hmc_sample
+ * call (the launches one trajectory costs), or -1 for a bad handle. */
+HMC_API long hmc_diag_graph_kernels(hmc_handle h);
+
+typedef struct {
+    char name[48];      /* kernel kind */
+    double ms_total;    /* summed CUDA-event time over all its launches */
+    long launches;
+} hmc_kernel_time;
+
+/* Run hmc_energy_grad on device states q (reps times, synchronously) with a
+ * CUDA event pair around every kernel launch on the stream it is launched on,
+ * and return per-kind totals in out[0..n-1]; the return value is n, or minus an
+ * hmc_status on failure. */
+HMC_API int hmc_diag_profile_energy_grad(hmc_handle h, const void *q, int reps, hmc_kernel_time *out,
+                                         int max_out);
+
 /* One batched BF16 tensor-core GEMM on the library's tcgen05 pipeline (TMA ->
  * shared memory -> tcgen05.mma -> TMEM -> registers), FP32 result:
  *   C[b][m][n] = sum_k A(m, k) B(n, k),  b < batch.

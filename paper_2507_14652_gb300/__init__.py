@@ -31,9 +31,10 @@ STATUS = {0: "HMC_OK", 1: "HMC_ERR_ARG", 2: "HMC_ERR_CUDA", 3: "HMC_ERR_OOM", 4:
           5: "HMC_ERR_TIMEOUT", 6: "HMC_ERR_UNSUPPORTED"}
 
 # every symbol the C ABI (include/hmc.h, include/hmc_diag.h) declares
-EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_subset_size", "hmc_param_count", "hmc_num_chains",
+EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_diag_umma_gemm",
            "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_destroy", "hmc_last_error",
-           "hmc_diag_philox", "hmc_diag_momenta", "hmc_diag_log_uniform"]
+           "hmc_diag_philox", "hmc_diag_momenta", "hmc_diag_log_uniform", "hmc_diag_graph_kernels",
+           "hmc_diag_profile_energy_grad"]
 
 
 class HmcError(RuntimeError):
@@ -91,8 +92,13 @@ def lib():
         L.hmc_diag_philox.argtypes = [vp, vp, lg, vp]
         L.hmc_diag_momenta.argtypes = [u64, u64, u64, u64, lg, vp]
         L.hmc_diag_log_uniform.argtypes = [u64, u64, lg, lg, vp]
+        L.hmc_diag_graph_kernels.argtypes = [vp]
+        L.hmc_diag_graph_kernels.restype = lg
+        L.hmc_diag_profile_energy_grad.argtypes = [vp, vp, i, vp, i]
+        L.hmc_diag_umma_gemm.argtypes = [i] * 6 + [vp] * 3
         for f in EXPORTS:
-            if f not in ("hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_last_error"):
+            if f not in ("hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_last_error",
+                         "hmc_diag_graph_kernels"):
                 getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -252,6 +258,27 @@ class Sampler:
         _check(lib().hmc_sample(self._h, _ptr(q0), float(eps), int(L), int(n), int(seed), int(first_traj),
                                 _ptr(S), _ptr(acc), _ptr(dH), _ptr(ql)))
         return S, acc, dH, ql
+
+
+class KernelTime(ct.Structure):
+    _fields_ = [("name", ct.c_char * 48), ("ms_total", ct.c_double), ("launches", ct.c_long)]
+
+
+def profile_energy_grad(sampler, q, reps=5):
+    """{kernel kind: (mean ms per launch, launches per evaluation)} from CUDA events
+    recorded around every launch on the library's stream."""
+    import torch
+    q = sampler._state(q)
+    buf = (KernelTime * 64)()
+    n = lib().hmc_diag_profile_energy_grad(sampler._h, _ptr(q), int(reps), buf, 64)
+    if n < 0:
+        _check(-n)
+    return {buf[i].name.decode(): (buf[i].ms_total / buf[i].launches, buf[i].launches / reps) for i in range(n)}
+
+
+def graph_kernels(sampler):
+    """Kernel launches in one captured trajectory of the last sample() call."""
+    return int(lib().hmc_diag_graph_kernels(sampler._h))
 
 
 class BatchSampler(Sampler):

@@ -48,6 +48,28 @@ DevBuf::~DevBuf()
     if (ptr) cudaFree(ptr);
 }
 
+Profiler *&active_profiler()
+{
+    static thread_local Profiler *p = nullptr;
+    return p;
+}
+
+ProfScope::ProfScope(const char *name, cudaStream_t st) : p(active_profiler()), s(st)
+{
+    if (!p) return;
+    Profiler::Rec r{name, nullptr, nullptr};
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    cudaEventRecord(r.a, s);
+    p->recs.push_back(r);
+    i = p->recs.size() - 1;
+}
+
+ProfScope::~ProfScope()
+{
+    if (p) cudaEventRecord(p->recs[i].b, s);
+}
+
 void build_net_desc(NetDesc &nd, const hmc_mlp_spec &s, long base, const std::vector<long> &idx)
 {
     nd.L = s.n_layers;
@@ -87,6 +109,9 @@ void build_net_desc(NetDesc &nd, const hmc_mlp_spec &s, long base, const std::ve
 struct TrajState {
     long long traj;
     long long slot;
+    void *samples;            // outputs of the current hmc_sample call (device; may be null)
+    unsigned char *accepted;
+    double *dH;
 };
 
 template <typename T>
@@ -94,8 +119,14 @@ __device__ __forceinline__ void scatter_one(const ScatterPlan &sc, long c, long 
 {
     const int b = sc.buf_id ? (int)sc.buf_id[j] : 0;
     const long o = c * sc.cstride[b] + (long)sc.off[j];
-    if (sc.is_bf16[b]) reinterpret_cast<__nv_bfloat16 *>(sc.base[b])[o] = __float2bfloat16_rn((float)q);
-    else reinterpret_cast<T *>(sc.base[b])[o] = q;
+    if (sc.is_bf16[b]) {
+        const __nv_bfloat16 hi = __float2bfloat16_rn((float)q);
+        reinterpret_cast<__nv_bfloat16 *>(sc.base[b])[o] = hi;
+        if (sc.base_lo[b])
+            reinterpret_cast<__nv_bfloat16 *>(sc.base_lo[b])[o] = __float2bfloat16_rn((float)q - __bfloat162float(hi));
+    } else {
+        reinterpret_cast<T *>(sc.base[b])[o] = q;
+    }
 }
 
 __device__ __forceinline__ double seg_sum(double v, double *sm)
@@ -170,9 +201,11 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_traj_end(const SegDesc *segs, int C, int nseg, long S_total, T *q_cur,
                                                   T *g_cur, double *U_cur, const T *q_prop, const T *p,
                                                   const T *g_prop, const double *U_prop, const double *K0,
-                                                  double eps, uint64_t seed, const TrajState *st, T *samples,
-                                                  unsigned char *acc_out, double *dH_out)
+                                                  double eps, uint64_t seed, const TrajState *st)
 {
+    T *samples = static_cast<T *>(st->samples);
+    unsigned char *acc_out = st->accepted;
+    double *dH_out = st->dH;
     __shared__ double sm[8];
     __shared__ int s_acc;
     const int s = blockIdx.x, pi = s / C, c = s % C;
@@ -215,10 +248,14 @@ __global__ void k_traj_advance(TrajState *st)
     st->slot += 1;
 }
 
-__global__ void k_set_state(TrajState *st, long long traj, long long slot)
+__global__ void k_set_state(TrajState *st, long long traj, long long slot, void *samples, unsigned char *acc,
+                            double *dH)
 {
     st->traj = traj;
     st->slot = slot;
+    st->samples = samples;
+    st->accepted = acc;
+    st->dH = dH;
 }
 
 __global__ void k_debug_momenta(uint64_t seed, uint64_t problem, uint64_t chain, uint64_t traj, long k, double *out)
@@ -271,6 +308,16 @@ struct hmc_handle_s {
     long k_total = 0, P_total = 0, S_total = 0;
     DevBuf q_cur, g_cur, q_prop, p, g_prop, U_cur, U_prop, K0, segs, state, scratch;
     std::vector<std::unique_ptr<DevBuf>> stage;
+    // one trajectory as an executable graph, reused while (eps, L, seed) stay the same
+    cudaGraphExec_t traj_exec = nullptr;
+    double traj_eps = 0.0;
+    int traj_L = -1;
+    unsigned long long traj_seed = 0;
+    long traj_kernels = 0;     // kernel nodes in that graph
+    ~hmc_handle_s()
+    {
+        if (traj_exec) cudaGraphExecDestroy(traj_exec);
+    }
 };
 
 namespace {
@@ -416,8 +463,7 @@ void kick_drift(hmc_handle h, void *q, void *p, const void *g, double kick, doub
     HMC_LAUNCH_CK();
 }
 
-template <typename T>
-void enqueue_trajectory(hmc_handle h, double eps, int L, uint64_t seed, void *samples, unsigned char *acc, double *dH)
+template <typename T> void enqueue_trajectory(hmc_handle h, double eps, int L, uint64_t seed)
 {
     const int nseg = h->nprob * h->C;
     const SegDesc *sd = h->segs.as<SegDesc>();
@@ -436,7 +482,7 @@ void enqueue_trajectory(hmc_handle h, double eps, int L, uint64_t seed, void *sa
     k_traj_end<T><<<nseg, 256, 0, h->stream>>>(sd, h->C, nseg, h->S_total, h->q_cur.as<T>(), h->g_cur.as<T>(),
                                                h->U_cur.as<double>(), h->q_prop.as<T>(), h->p.as<T>(),
                                                h->g_prop.as<T>(), h->U_prop.as<double>(), h->K0.as<double>(), eps,
-                                               seed, st, static_cast<T *>(samples), acc, dH);
+                                               seed, st);
     HMC_LAUNCH_CK();
     k_traj_advance<<<1, 1, 0, h->stream>>>(st);
     HMC_LAUNCH_CK();
@@ -638,30 +684,45 @@ hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_sa
         double *ddh = static_cast<double *>(dev_view(h, dH, sizeof(double) * nseg * n_samples, false, &sd));
         void *dl = dev_view(h, q_last, sb, false, &sl);
         energy_grad_all(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr, false);
-        k_set_state<<<1, 1, 0, h->stream>>>(h->state.as<TrajState>(), first_traj, 0);
+        k_set_state<<<1, 1, 0, h->stream>>>(h->state.as<TrajState>(), first_traj, 0, ds, da, ddh);
         HMC_LAUNCH_CK();
         if (n_samples > 0) {
-            cudaGraph_t graph = nullptr;
-            cudaGraphExec_t exec = nullptr;
-            HMC_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-            try {
-                if (h->prec == HMC_PREC_FP64) enqueue_trajectory<double>(h, eps, L, seed, ds, da, ddh);
-                else enqueue_trajectory<float>(h, eps, L, seed, ds, da, ddh);
-            } catch (...) {
-                cudaStreamEndCapture(h->stream, &graph);
-                if (graph) cudaGraphDestroy(graph);
-                throw;
+            if (!h->traj_exec || h->traj_eps != eps || h->traj_L != L || h->traj_seed != seed) {
+                if (h->traj_exec) {
+                    cudaGraphExecDestroy(h->traj_exec);
+                    h->traj_exec = nullptr;
+                }
+                cudaGraph_t graph = nullptr;
+                HMC_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+                try {
+                    if (h->prec == HMC_PREC_FP64) enqueue_trajectory<double>(h, eps, L, seed);
+                    else enqueue_trajectory<float>(h, eps, L, seed);
+                } catch (...) {
+                    cudaStreamEndCapture(h->stream, &graph);
+                    if (graph) cudaGraphDestroy(graph);
+                    throw;
+                }
+                HMC_CK(cudaStreamEndCapture(h->stream, &graph));
+                size_t nn = 0;
+                cudaGraphGetNodes(graph, nullptr, &nn);
+                std::vector<cudaGraphNode_t> nodes(nn);
+                long nk = 0;
+                if (nn) {
+                    cudaGraphGetNodes(graph, nodes.data(), &nn);
+                    for (auto nd : nodes) {
+                        cudaGraphNodeType t;
+                        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+                    }
+                }
+                cudaError_t e = cudaGraphInstantiate(&h->traj_exec, graph, 0);
+                cudaGraphDestroy(graph);
+                HMC_CK(e);
+                h->traj_eps = eps;
+                h->traj_L = L;
+                h->traj_seed = seed;
+                h->traj_kernels = nk;
             }
-            HMC_CK(cudaStreamEndCapture(h->stream, &graph));
-            cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            HMC_CK(e);
-            for (long i = 0; i < n_samples; ++i) {
-                e = cudaGraphLaunch(exec, h->stream);
-                if (e != cudaSuccess) break;
-            }
-            cudaGraphExecDestroy(exec);
-            HMC_CK(e);
+            for (long i = 0; i < n_samples; ++i) HMC_CK(cudaGraphLaunch(h->traj_exec, h->stream));
         }
         if (dl) HMC_CK(cudaMemcpyAsync(dl, h->q_cur.ptr, sb, cudaMemcpyDeviceToDevice, h->stream));
         if (ss) HMC_CK(cudaMemcpyAsync(samples, ds, sb * (size_t)n_samples, cudaMemcpyDeviceToHost, h->stream));
@@ -694,6 +755,51 @@ hmc_status hmc_destroy(hmc_handle h)
 }
 
 const char *hmc_last_error(void) { return g_err.c_str(); }
+
+long hmc_diag_graph_kernels(hmc_handle h) { return h ? h->traj_kernels : -1; }
+
+int hmc_diag_profile_energy_grad(hmc_handle h, const void *q, int reps, hmc_kernel_time *out, int max_out)
+{
+    g_err.clear();
+    Profiler prof;
+    int n = 0;
+    hmc_status st = guarded([&]() -> hmc_status {
+        HMC_REQUIRE(h && q && out && reps >= 1 && max_out >= 1, "bad argument");
+        HMC_REQUIRE(is_device_ptr(q), "q must be device memory");
+        join_in(h);
+        HMC_CK(cudaStreamSynchronize(h->stream));
+        active_profiler() = &prof;
+        try {
+            for (int r = 0; r < reps; ++r) energy_grad_all(h, const_cast<void *>(q), h->U_prop.as<double>(), h->g_prop.ptr, false);
+        } catch (...) {
+            active_profiler() = nullptr;
+            throw;
+        }
+        active_profiler() = nullptr;
+        HMC_CK(cudaStreamSynchronize(h->stream));
+        for (auto &r : prof.recs) {
+            float ms = 0.0f;
+            HMC_CK(cudaEventElapsedTime(&ms, r.a, r.b));
+            int k = 0;
+            while (k < n && strncmp(out[k].name, r.name, sizeof(out[k].name) - 1) != 0) ++k;
+            if (k == n) {
+                if (n == max_out) continue;
+                memset(&out[n], 0, sizeof(out[n]));
+                strncpy(out[n].name, r.name, sizeof(out[n].name) - 1);
+                ++n;
+            }
+            out[k].ms_total += ms;
+            out[k].launches += 1;
+        }
+        join_out(h);
+        return HMC_OK;
+    });
+    for (auto &r : prof.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    return st == HMC_OK ? n : -(int)st;
+}
 
 // --- diagnostics (include/hmc_diag.h) ---------------------------------------
 

@@ -60,6 +60,7 @@ struct ScatterPlan {
     void *base[MAX_SCATTER_BUFS] = {};
     long cstride[MAX_SCATTER_BUFS] = {};   // elements between chains
     int is_bf16[MAX_SCATTER_BUFS] = {};
+    void *base_lo[MAX_SCATTER_BUFS] = {};  // bf16 buffers only: receives bf16(q - hi) when set
     const uint8_t *buf_id = nullptr;       // [k] (nullptr: all in buffer 0)
     const int *off = nullptr;              // [k] element offset inside one chain's slice
 };
@@ -110,6 +111,24 @@ Engine *make_simt_engine_f64(Problem &p, int C);
 Engine *make_simt_engine_f32(Problem &p, int C);
 Engine *make_umma_engine_bf16(Problem &p, int C);
 bool umma_engine_supports(const Problem &p, std::string *why);
+
+// Per-kernel timing for hmc_diag_profile_energy_grad: while a profiler is active on
+// this thread, every launch site records a CUDA event pair on its launching stream.
+struct Profiler {
+    struct Rec {
+        const char *name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+};
+Profiler *&active_profiler();
+struct ProfScope {
+    Profiler *p;
+    cudaStream_t s;
+    size_t i = 0;
+    ProfScope(const char *name, cudaStream_t st);
+    ~ProfScope();
+};
 
 // Device allocation helper that tracks bytes and frees on destruction.
 struct DevBuf {

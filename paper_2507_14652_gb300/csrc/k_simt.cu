@@ -227,6 +227,7 @@ void launch_gemm(const GemmArgs<T> &g, const EpiArgs<T> &e, int batch, cudaStrea
 {
     if (g.M <= 0 || g.N <= 0) return;
     dim3 grid((g.N + TILE - 1) / TILE, (g.M + TILE - 1) / TILE, batch);
+    ProfScope ps(sizeof(T) == 8 ? "simt_gemm_f64" : "simt_gemm_f32", s);
     k_gemm<T><<<grid, 256, 0, s>>>(g, e);
     HMC_LAUNCH_CK();
 }
@@ -347,6 +348,7 @@ template <typename T> class SimtEngine final : public Engine {
                 backward(tn, yq_.as<T>(), 0, p_.n_y, trb_, dT_.as<T>(), s);
             }
         }
+        ProfScope ps("simt_finalize", s);
         k_finalize<T><<<C_, 256, 0, s>>>(part_r2_.as<double>(), p_.kind == HMC_NET_DEEPONET ? part_d_.as<double>() : nullptr,
                                          nparts_, 0.5 * inv_s2, q, k, idx_.as<int>(), G_.as<T>(), P,
                                          p_.kind == HMC_NET_DEEPONET && p_.out_bias ? p_.b0_off : -1,
@@ -419,6 +421,7 @@ template <typename T> class SimtEngine final : public Engine {
             }
             if (nd.boff[l] >= 0) {
                 dim3 grid((wo + 31) / 32, C_);
+                ProfScope ps("simt_colsum", s);
                 k_colsum<T><<<grid, dim3(32, 8), 0, s>>>(d, rows, wo, rows * wo, G + nd.boff[l], P);
                 HMC_LAUNCH_CK();
             }
@@ -440,6 +443,7 @@ template <typename T> class SimtEngine final : public Engine {
                   cudaStream_t s)
     {
         dim3 grid(nparts_, C_);
+        ProfScope ps("simt_residual", s);
         k_residual<T><<<grid, 256, 0, s>>>(f, n_el, y, n_el, slope, inv_s2, delta, part_r2_.as<double>(),
                                            want_d ? part_d_.as<double>() : nullptr, nparts_);
         HMC_LAUNCH_CK();

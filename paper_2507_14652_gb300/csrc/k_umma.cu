@@ -7,6 +7,9 @@
 // One gradient evaluation for all C chains (rows n = data points, tiles of 128):
 //   first layer   A_1 = tanh(X W_0^T + b_0)                        CUDA cores
 //   hidden fwd    A_{i+1} = tanh(A_i W_i^T + b_i)                  UMMA, epilogue tanh
+//                 Hidden weights are held as a bf16 pair W = W_hi + W_lo (about 16
+//                 mantissa bits) and every K-slice issues two MMAs into the same
+//                 accumulator, so only activations and deltas are rounded to bf16.
 //   last hidden   A_{L-1} = tanh(A_{L-2} W^T + b) fused with the output layer:
 //                 f = A_{L-1} w_out + b_out, r = f - y, U partial (FP64),
 //                 delta_L = r / sigma^2, dW_out/db_out partials,
@@ -35,12 +38,12 @@ constexpr int BM = 128;                         // rows per tile (UMMA M)
 constexpr int BK = 64;                          // K per stage (one 128-byte swizzle atom of bf16)
 constexpr int STAGES = 2;
 constexpr int A_STAGE_BYTES = BM * BK * 2;      // 16 KB
-constexpr int B_STAGE_BYTES = 256 * BK * 2;     // 32 KB (room for N up to 256)
-constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
+constexpr int B_STAGE_BYTES = 256 * BK * 2;     // 32 KB (room for N up to 256); doubled for W_hi + W_lo
 constexpr int TMEM_COLS = 256;
 constexpr int NTHREADS = 192;                   // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int RED_BYTES = 3 * 4 * 256 * 4 + 4 * 8 + 4 * 4 + 64;   // [3][4][256] floats, 4 doubles, 4 floats
-constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 256 + RED_BYTES;
+__host__ __device__ constexpr int stage_bytes(bool wsplit) { return A_STAGE_BYTES + B_STAGE_BYTES * (wsplit ? 2 : 1); }
+__host__ __device__ constexpr int smem_bytes(bool wsplit) { return 1024 + STAGES * stage_bytes(wsplit) + 256 + RED_BYTES; }
 
 enum Mode { M_STORE_F32 = 0, M_FWD_TANH = 1, M_FWD_OUT = 2, M_BWD_TANH = 3, M_BWD_FIRST = 4, M_DW = 5 };
 
@@ -70,10 +73,12 @@ struct Params {
     float *gw_part; long gw_split; long gw_b;   // M_DW: [split][b][k]
 };
 
-template <int MODE, bool A_MN, bool B_MN>
-__global__ void __launch_bounds__(NTHREADS, 2) k_umma(const __grid_constant__ CUtensorMap tmA,
-                                                      const __grid_constant__ CUtensorMap tmB, const Params p)
+template <int MODE, bool A_MN, bool B_MN, bool WSPLIT>
+__global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
+    k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+           const __grid_constant__ CUtensorMap tmB2, const Params p)
 {
+    constexpr int STAGE_BYTES = stage_bytes(WSPLIT);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
@@ -98,6 +103,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_umma(const __grid_constant__ CU
         fence_mbar_init();
         prefetch_map(&tmA);
         prefetch_map(&tmB);
+        if (WSPLIT) prefetch_map(&tmB2);
     }
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
@@ -118,7 +124,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_umma(const __grid_constant__ CU
                 const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
                 if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.err)) { ok = false; break; }
                 const uint32_t fb = full0 + 8 * s;
-                mbar_expect_tx(fb, A_STAGE_BYTES + bbytes);
+                mbar_expect_tx(fb, A_STAGE_BYTES + bbytes * (WSPLIT ? 2u : 1u));
                 const uint32_t sa = smem_u32(smem + s * STAGE_BYTES), sb = sa + A_STAGE_BYTES;
                 const int kc = (kb0 + i) * BK;
                 if (!A_MN) {
@@ -129,8 +135,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_umma(const __grid_constant__ CU
                 }
                 if (!B_MN) {
                     tma_load_3d(sb, &tmB, kc, 0, b, fb);
+                    if (WSPLIT) tma_load_3d(sb + B_STAGE_BYTES, &tmB2, kc, 0, b, fb);
                 } else {
-                    for (int a = 0; a < BN / 64; ++a) tma_load_3d(sb + 8192 * a, &tmB, 64 * a, kc, b, fb);
+                    for (int a = 0; a < BN / 64; ++a) {
+                        tma_load_3d(sb + 8192 * a, &tmB, 64 * a, kc, b, fb);
+                        if (WSPLIT) tma_load_3d(sb + B_STAGE_BYTES + 8192 * a, &tmB2, 64 * a, kc, b, fb);
+                    }
                 }
                 ++issued;
             }
@@ -153,6 +163,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_umma(const __grid_constant__ CU
                     const uint64_t ad = A_MN ? sdesc(sa + 2048 * ks, 8192, 1024) : sdesc(sa + 32 * ks, 0, 1024);
                     const uint64_t bd = B_MN ? sdesc(sb + 2048 * ks, 8192, 1024) : sdesc(sb + 32 * ks, 0, 1024);
                     mma_bf16(tmem, ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
+                    if (WSPLIT) {
+                        const uint32_t sl = sb + B_STAGE_BYTES;
+                        const uint64_t bl = B_MN ? sdesc(sl + 2048 * ks, 8192, 1024) : sdesc(sl + 32 * ks, 0, 1024);
+                        mma_bf16(tmem, ad, bl, idesc, 1u);
+                    }
                 }
                 mma_commit(empty0 + 8 * s);
             }
@@ -432,8 +447,14 @@ __global__ void k_scatter_plan(const float *q, long k, ScatterPlan sc)
         const int bi = sc.buf_id[j];
         const long o = (long)b * sc.cstride[bi] + sc.off[j];
         const float v = q[(long)b * k + j];
-        if (sc.is_bf16[bi]) reinterpret_cast<__nv_bfloat16 *>(sc.base[bi])[o] = __float2bfloat16_rn(v);
-        else reinterpret_cast<float *>(sc.base[bi])[o] = v;
+        if (sc.is_bf16[bi]) {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            reinterpret_cast<__nv_bfloat16 *>(sc.base[bi])[o] = hi;
+            if (sc.base_lo[bi])
+                reinterpret_cast<__nv_bfloat16 *>(sc.base_lo[bi])[o] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        } else {
+            reinterpret_cast<float *>(sc.base[bi])[o] = v;
+        }
     }
 }
 
@@ -482,15 +503,20 @@ CUtensorMap make_map(const void *base, uint64_t inner, uint64_t mid, uint64_t ou
     return m;
 }
 
-template <int MODE, bool A_MN, bool B_MN>
-void launch_umma(const CUtensorMap &a, const CUtensorMap &b, const Params &p, dim3 grid, cudaStream_t s)
+template <int MODE, bool A_MN, bool B_MN, bool WSPLIT>
+void launch_umma(const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &b2, const Params &p, dim3 grid,
+                 cudaStream_t s)
 {
     static bool configured = false;
+    constexpr int sm = smem_bytes(WSPLIT);
     if (!configured) {
-        HMC_CK(cudaFuncSetAttribute(k_umma<MODE, A_MN, B_MN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+        HMC_CK(cudaFuncSetAttribute(k_umma<MODE, A_MN, B_MN, WSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
         configured = true;
     }
-    k_umma<MODE, A_MN, B_MN><<<grid, NTHREADS, SMEM_BYTES, s>>>(a, b, p);
+    static const char *names[] = {"umma_store_f32", "umma_fwd_tanh", "umma_fwd_out", "umma_bwd_tanh",
+                                  "umma_bwd_first", "umma_dw"};
+    ProfScope ps(names[MODE], s);
+    k_umma<MODE, A_MN, B_MN, WSPLIT><<<grid, NTHREADS, sm, s>>>(a, b, b2, p);
     HMC_LAUNCH_CK();
 }
 
@@ -529,9 +555,11 @@ class UmmaEngine final : public Engine {
         W0_.alloc(sizeof(float) * C * w_ * dx_);
         b0_.alloc(sizeof(float) * C * w_);
         Wh_.resize(nh);
+        Wl_.resize(nh);
         bh_.resize(nh);
         for (int i = 0; i < nh; ++i) {
             Wh_[i].reset(new DevBuf(sizeof(__nv_bfloat16) * C * w_ * w_));
+            Wl_[i].reset(new DevBuf(sizeof(__nv_bfloat16) * C * w_ * w_));
             bh_[i].reset(new DevBuf(sizeof(float) * C * w_));
         }
         wout_.alloc(sizeof(float) * C * w_);
@@ -539,7 +567,7 @@ class UmmaEngine final : public Engine {
         upload_rep(W0_, nd.woff[0], (long)w_ * dx_);
         upload_rep(b0_, nd.boff[0], w_);
         for (int i = 0; i < nh; ++i) {
-            upload_rep_bf16(*Wh_[i], nd.woff[i + 1], (long)w_ * w_);
+            upload_rep_bf16(*Wh_[i], *Wl_[i], nd.woff[i + 1], (long)w_ * w_);
             upload_rep(*bh_[i], nd.boff[i + 1], w_);
         }
         upload_rep(wout_, nd.woff[L_ - 1], w_);
@@ -579,6 +607,8 @@ class UmmaEngine final : public Engine {
             A_atom_[i] = make_map(A_[i]->ptr, w_, N_, C, 64, 64);
             W_fwd_[i] = make_map(Wh_[i - 1]->ptr, w_, w_, C, 64, w_);
             W_atom_[i] = make_map(Wh_[i - 1]->ptr, w_, w_, C, 64, 64);
+            W_fwd_lo_[i] = make_map(Wl_[i - 1]->ptr, w_, w_, C, 64, w_);
+            W_atom_lo_[i] = make_map(Wl_[i - 1]->ptr, w_, w_, C, 64, 64);
         }
         for (int i = 2; i <= L_ - 1; ++i) {
             D_row_[i] = make_map(D_[i]->ptr, w_, N_, C, 64, 128);
@@ -601,6 +631,7 @@ class UmmaEngine final : public Engine {
         float *g = static_cast<float *>(gv);
         if (!scattered) {
             dim3 grid((unsigned)std::min<long>((k_ + 255) / 256, 1024), C_);
+            ProfScope ps("scatter", s);
             k_scatter_plan<float><<<grid, 256, 0, s>>>(q, k_, plan_);
             HMC_LAUNCH_CK();
         }
@@ -614,6 +645,7 @@ class UmmaEngine final : public Engine {
         {
             const long total = N_ * (long)(w_ / 2);
             dim3 grid((unsigned)std::min<long>((total + 255) / 256, 4 * num_sms_), C_);
+            ProfScope ps("first_fwd", s);
             k_first_fwd<<<grid, 256, 0, s>>>(x_.as<float>(), dx_, N_, w_, W0_.as<float>(), b0_.as<float>(),
                                              A_[1]->as<__nv_bfloat16>());
             HMC_LAUNCH_CK();
@@ -630,7 +662,7 @@ class UmmaEngine final : public Engine {
             if (i < L_ - 2) {
                 pp.out = A_[i + 1]->as<__nv_bfloat16>();
                 pp.out_b = act_b;
-                launch_umma<M_FWD_TANH, false, false>(A_row_[i], W_fwd_[i], pp, row_grid, s);
+                launch_umma<M_FWD_TANH, false, false, true>(A_row_[i], W_fwd_[i], W_fwd_lo_[i], pp, row_grid, s);
             } else {
                 pp.out = D_[L_ - 1]->as<__nv_bfloat16>();
                 pp.out_b = act_b;
@@ -643,7 +675,7 @@ class UmmaEngine final : public Engine {
                 pp.dbout_part = dbout_part_.as<float>();
                 pp.dwout_part = dwout_part_.as<float>();
                 pp.db_part = db_part_[L_ - 2]->as<float>();
-                launch_umma<M_FWD_OUT, false, false>(A_row_[i], W_fwd_[i], pp, row_grid, s);
+                launch_umma<M_FWD_OUT, false, false, true>(A_row_[i], W_fwd_[i], W_fwd_lo_[i], pp, row_grid, s);
             }
         }
         // reverse: delta_i = (delta_{i+1} W_i) (1 - A_i^2) for i = L-2 .. 1 (down to the lowest sampled layer)
@@ -660,12 +692,12 @@ class UmmaEngine final : public Engine {
             if (i > 1) {
                 pp.out = D_[i]->as<__nv_bfloat16>();
                 pp.out_b = act_b;
-                launch_umma<M_BWD_TANH, false, true>(D_row_[i + 1], W_atom_[i], pp, row_grid, s);
+                launch_umma<M_BWD_TANH, false, true, true>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], pp, row_grid, s);
             } else {
                 pp.x = x_.as<float>();
                 pp.dx = dx_;
                 pp.dw0_part = dw0_part_.as<float>();
-                launch_umma<M_BWD_FIRST, false, true>(D_row_[i + 1], W_atom_[i], pp, row_grid, s);
+                launch_umma<M_BWD_FIRST, false, true, true>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], pp, row_grid, s);
             }
         }
         // weight gradients of the hidden layers at the sampled entries
@@ -685,7 +717,7 @@ class UmmaEngine final : public Engine {
             pp.gw_b = k_;
             const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
             dim3 grid((w_ + BM - 1) / BM, splits, C_);
-            launch_umma<M_DW, true, true>(D_atom_[i + 1], A_atom_[i], pp, grid, s);
+            launch_umma<M_DW, true, true, false>(D_atom_[i + 1], A_atom_[i], A_atom_[i], pp, grid, s);
         }
         FinalArgs fa{};
         fa.k = (int)k_;
@@ -705,8 +737,11 @@ class UmmaEngine final : public Engine {
         fa.dbout_part = dbout_part_.as<float>();
         fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
         fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
-        k_finalize_bf16<<<C_, 256, 0, s>>>(fa, q, U, g);
-        HMC_LAUNCH_CK();
+        {
+            ProfScope ps("finalize", s);
+            k_finalize_bf16<<<C_, 256, 0, s>>>(fa, q, U, g);
+            HMC_LAUNCH_CK();
+        }
     }
 
   private:
@@ -725,12 +760,19 @@ class UmmaEngine final : public Engine {
         HMC_CK(cudaMemcpy(dst.ptr, v.data(), sizeof(float) * v.size(), cudaMemcpyHostToDevice));
     }
 
-    void upload_rep_bf16(DevBuf &dst, long off, long count)
+    // W = hi + lo with hi = bf16(W) and lo = bf16(W - hi), W taken in float32
+    void upload_rep_bf16(DevBuf &hi, DevBuf &lo, long off, long count)
     {
-        std::vector<__nv_bfloat16> v(C_ * count);
+        std::vector<__nv_bfloat16> vh(C_ * count), vl(C_ * count);
         for (int c = 0; c < C_; ++c)
-            for (long i = 0; i < count; ++i) v[c * count + i] = __float2bfloat16_rn((float)p_.frozen[off + i]);
-        HMC_CK(cudaMemcpy(dst.ptr, v.data(), sizeof(__nv_bfloat16) * v.size(), cudaMemcpyHostToDevice));
+            for (long i = 0; i < count; ++i) {
+                const float w = (float)p_.frozen[off + i];
+                const __nv_bfloat16 h = __float2bfloat16_rn(w);
+                vh[c * count + i] = h;
+                vl[c * count + i] = __float2bfloat16_rn(w - __bfloat162float(h));
+            }
+        HMC_CK(cudaMemcpy(hi.ptr, vh.data(), sizeof(__nv_bfloat16) * vh.size(), cudaMemcpyHostToDevice));
+        HMC_CK(cudaMemcpy(lo.ptr, vl.data(), sizeof(__nv_bfloat16) * vl.size(), cudaMemcpyHostToDevice));
     }
 
     void build_entries()
@@ -749,6 +791,7 @@ class UmmaEngine final : public Engine {
             plan_.base[2 + 2 * (i - 1)] = Wh_[i - 1]->ptr;
             plan_.cstride[2 + 2 * (i - 1)] = (long)w_ * w_;
             plan_.is_bf16[2 + 2 * (i - 1)] = 1;
+            plan_.base_lo[2 + 2 * (i - 1)] = Wl_[i - 1]->ptr;
             plan_.base[3 + 2 * (i - 1)] = bh_[i - 1]->ptr;
             plan_.cstride[3 + 2 * (i - 1)] = w_;
             plan_.is_bf16[3 + 2 * (i - 1)] = 0;
@@ -825,9 +868,10 @@ class UmmaEngine final : public Engine {
     int *err_ = nullptr;
     DevBuf x_, y_, W0_, b0_, wout_, bout_, u_part_, dbout_part_, dwout_part_, dw0_part_, db_ptrs_, gw_part_;
     DevBuf kind_, layer_, off_, erow_, ecol_, sc_off_, sc_bid_;
-    std::vector<std::unique_ptr<DevBuf>> Wh_, bh_, A_, D_, db_part_, rowptr_;
+    std::vector<std::unique_ptr<DevBuf>> Wh_, Wl_, bh_, A_, D_, db_part_, rowptr_;
     std::vector<int> layer_entries_;
-    CUtensorMap A_row_[MAXL], A_atom_[MAXL], W_fwd_[MAXL], W_atom_[MAXL], D_row_[MAXL], D_atom_[MAXL];
+    CUtensorMap A_row_[MAXL], A_atom_[MAXL], W_fwd_[MAXL], W_atom_[MAXL], W_fwd_lo_[MAXL], W_atom_lo_[MAXL];
+    CUtensorMap D_row_[MAXL], D_atom_[MAXL];
     ScatterPlan plan_;
 };
 
@@ -885,10 +929,10 @@ extern "C" hmc_status hmc_diag_umma_gemm(int M, int N, int K, int batch, int a_m
         HMC_CK(cudaMemset(err, 0, sizeof(int)));
         p.err = err;
         dim3 grid((M + BM - 1) / BM, 1, batch);
-        if (!a_mn && !b_mn) launch_umma<M_STORE_F32, false, false>(ma, mb, p, grid, 0);
-        else if (!a_mn && b_mn) launch_umma<M_STORE_F32, false, true>(ma, mb, p, grid, 0);
-        else if (a_mn && !b_mn) launch_umma<M_STORE_F32, true, false>(ma, mb, p, grid, 0);
-        else launch_umma<M_STORE_F32, true, true>(ma, mb, p, grid, 0);
+        if (!a_mn && !b_mn) launch_umma<M_STORE_F32, false, false, false>(ma, mb, mb, p, grid, 0);
+        else if (!a_mn && b_mn) launch_umma<M_STORE_F32, false, true, false>(ma, mb, mb, p, grid, 0);
+        else if (a_mn && !b_mn) launch_umma<M_STORE_F32, true, false, false>(ma, mb, mb, p, grid, 0);
+        else launch_umma<M_STORE_F32, true, true, false>(ma, mb, mb, p, grid, 0);
         HMC_CK(cudaDeviceSynchronize());
         int herr = 0;
         HMC_CK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -30,3 +30,12 @@ def grad_ok(g, gref, tol):
     comp = np.abs(g - gref) <= tol * (np.abs(gref) + rms)
     return rel_err(g, gref) <= tol and bool(comp.all()), rel_err(g, gref), float(
         np.max(np.abs(g - gref) / (np.abs(gref) + rms)))
+
+
+def grad_ok_bf16(g, gref, tol=2e-2):
+    """BF16 gradient tolerance, per gradient evaluation: relative 2-norm error and
+    relative infinity-norm error both within tol."""
+    g, gref = np.asarray(g, dtype=np.float64), np.asarray(gref, dtype=np.float64)
+    r2 = rel_err(g, gref)
+    rinf = float(np.max(np.abs(g - gref)) / max(np.max(np.abs(gref)), 1e-300))
+    return r2 <= tol and rinf <= tol, r2, rinf

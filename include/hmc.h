@@ -171,6 +171,32 @@ HMC_API hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, l
 /* Free the handle and all its device memory. NULL is accepted. */
 HMC_API hmc_status hmc_destroy(hmc_handle h);
 
+/*
+ * U and grad U of an FP32 MLP for C chains without any device allocation.
+ * The paper has no counterpart: this exists for callers that must not allocate
+ * device memory -- code running while a stream is being captured into a CUDA
+ * graph (cudaMalloc is not allowed there), code embedded in a framework whose
+ * own memory pool owns the device, or a real-time loop that may not block in the
+ * allocator.  It runs the same CUDA-core kernels as hmc_energy_grad with
+ * HMC_PREC_FP32, without a handle.
+ *   net          the MLP (widths, activations, biases); parameter order as above
+ *   x [n][dx], y [n][dout], frozen [P], subset_idx [k] (ascending int32 parameter
+ *   indices of the sampled entries), q [C][k]: device arrays owned by the caller
+ *   U [C] (double) and grad [C][k] (float, may be NULL): device outputs
+ *   cuda_stream  where the work is queued; the call returns without waiting
+ * Every intermediate lives in one fixed 16 MiB array inside the library's device
+ * image, held by every GPU that loads the library until the process exits.
+ * Problems whose intermediates exceed it are rejected with HMC_ERR_ARG and a
+ * message giving the size needed.  All calls share that array and each call
+ * overwrites it, so calls that overlap on the GPU race; serialise them.  The
+ * first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.
+ */
+HMC_API hmc_status hmc_energy_grad_noalloc(const hmc_mlp_spec *net, const float *x, const float *y, long n,
+                                           const float *frozen, const int *subset_idx, long k,
+                                           double prior_sigma, double noise_sigma, int n_chains,
+                                           const float *q, double *U, float *grad, void *cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none).  Owned by the library. */
 HMC_API const char *hmc_last_error(void);
 

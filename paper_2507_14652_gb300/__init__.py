@@ -33,6 +33,7 @@ STATUS = {0: "HMC_OK", 1: "HMC_ERR_ARG", 2: "HMC_ERR_CUDA", 3: "HMC_ERR_OOM", 4:
 # every symbol the C ABI (include/hmc.h, include/hmc_diag.h) declares
 EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_diag_umma_gemm",
            "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_destroy", "hmc_last_error",
+           "hmc_energy_grad_noalloc",
            "hmc_diag_philox", "hmc_diag_momenta", "hmc_diag_log_uniform", "hmc_diag_graph_kernels",
            "hmc_diag_profile_energy_grad"]
 
@@ -92,6 +93,8 @@ def lib():
         L.hmc_diag_philox.argtypes = [vp, vp, lg, vp]
         L.hmc_diag_momenta.argtypes = [u64, u64, u64, u64, lg, vp]
         L.hmc_diag_log_uniform.argtypes = [u64, u64, lg, lg, vp]
+        L.hmc_energy_grad_noalloc.argtypes = [ct.POINTER(MlpSpec), vp, vp, lg, vp, vp, lg, d, d, i, vp, vp, vp,
+                                              vp]
         L.hmc_diag_graph_kernels.argtypes = [vp]
         L.hmc_diag_graph_kernels.restype = lg
         L.hmc_diag_profile_energy_grad.argtypes = [vp, vp, i, vp, i]

@@ -465,3 +465,176 @@ Engine *make_simt_engine_f64(Problem &p, int C) { return new SimtEngine<double>(
 Engine *make_simt_engine_f32(Problem &p, int C) { return new SimtEngine<float>(p, C); }
 
 }  // namespace hmc
+
+// ---------------------------------------------------------------------------
+// U and grad U without any device allocation (hmc_energy_grad_noalloc).
+//
+// Every intermediate of the CUDA-core FP32 evaluation (per-chain parameter
+// vectors, activations, slopes, deltas, the dense gradient and the energy
+// partials) is carved out of one fixed array that lives in the library's
+// device image.  Each GPU that loads the library holds this array until the
+// process exits.  All calls share it, so calls that overlap on the GPU (two
+// streams, two host threads) race and corrupt each other's results.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace hmc {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;   // 16 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array for the current device.  In host code the
+// array's name is only a host-side stand-in, so the address has to be asked
+// for once per device, with that device current.
+void *noalloc_scratch_address()
+{
+    int dev = 0;
+    HMC_CK(cudaGetDevice(&dev));
+    HMC_REQUIRE(dev >= 0 && dev < kMaxDevices, "device index %d is out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        HMC_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    return g_noalloc_ptr[dev];
+}
+
+__global__ void k_copy_rep(const float *src, long P, int C, float *dst)
+{
+    const long tot = P * (long)C;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long)gridDim.x * blockDim.x)
+        dst[i] = src[i % P];
+}
+
+}  // namespace
+}  // namespace hmc
+
+extern "C" hmc_status hmc_energy_grad_noalloc(const hmc_mlp_spec *net, const float *x, const float *y, long n,
+                                              const float *frozen, const int *subset_idx, long k,
+                                              double prior_sigma, double noise_sigma, int n_chains,
+                                              const float *q, double *U, float *grad, void *cuda_stream)
+{
+    using namespace hmc;
+    try {
+        HMC_REQUIRE(net && x && y && frozen && subset_idx && q && U, "NULL argument");
+        HMC_REQUIRE(net->n_layers >= 1 && net->n_layers <= HMC_MAX_LAYERS, "n_layers must be in [1, %d]",
+                    HMC_MAX_LAYERS);
+        HMC_REQUIRE(n >= 1 && k >= 1 && n_chains >= 1 && n_chains <= 65535, "need n >= 1, k >= 1, 1 <= C <= 65535");
+        HMC_REQUIRE(prior_sigma > 0 && noise_sigma > 0, "prior_sigma and noise_sigma must be positive");
+        cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+        const int C = n_chains, L = net->n_layers;
+        // layer offsets in the parameter vector (W[out][in] then b[out], layer by layer)
+        long woff[MAXL], boff[MAXL], P = 0;
+        long wmax = 1;
+        for (int l = 0; l < L; ++l) {
+            HMC_REQUIRE(net->widths[l] >= 1 && net->widths[l + 1] >= 1, "widths must be >= 1");
+            HMC_REQUIRE(net->act[l] >= HMC_ACT_IDENTITY && net->act[l] <= HMC_ACT_SIN, "bad activation");
+            woff[l] = P;
+            P += (long)net->widths[l + 1] * net->widths[l];
+            boff[l] = -1;
+            if (net->has_bias[l]) {
+                boff[l] = P;
+                P += net->widths[l + 1];
+            }
+        }
+        for (int l = 0; l <= L; ++l) wmax = std::max<long>(wmax, net->widths[l]);
+        HMC_REQUIRE(k <= P, "k (%ld) exceeds the parameter count (%ld)", k, P);
+        const int dout = net->widths[L];
+        const long n_el = n * dout;
+        const int nparts = (int)std::min<long>(64, std::max<long>(1, (n_el + 255) / 256));
+        // scratch layout, every block 256-byte aligned
+        auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+        size_t need = 0;
+        const size_t o_part = need; need += up(sizeof(double) * C * nparts);
+        const size_t o_theta = need; need += up(sizeof(float) * C * P);
+        const size_t o_G = need; need += up(sizeof(float) * C * P);
+        size_t o_act[MAXL + 1] = {}, o_slope[MAXL + 1] = {};
+        for (int l = 1; l <= L; ++l) {
+            o_act[l] = need; need += up(sizeof(float) * C * n * net->widths[l]);
+            o_slope[l] = need; need += up(sizeof(float) * C * n * net->widths[l]);
+        }
+        const size_t o_d0 = need; need += up(sizeof(float) * C * n * wmax);
+        const size_t o_d1 = need; need += up(sizeof(float) * C * n * wmax);
+        if (need > kNoAllocScratchBytes) {
+            set_error("hmc_energy_grad_noalloc needs %zu bytes of scratch for this problem; the fixed maximum is "
+                      "%zu bytes (16 MiB): use hmc_create/hmc_energy_grad instead", need, kNoAllocScratchBytes);
+            return HMC_ERR_ARG;
+        }
+        unsigned char *base = static_cast<unsigned char *>(noalloc_scratch_address());
+        double *part = reinterpret_cast<double *>(base + o_part);
+        float *theta = reinterpret_cast<float *>(base + o_theta);
+        float *G = reinterpret_cast<float *>(base + o_G);
+        float *d[2] = {reinterpret_cast<float *>(base + o_d0), reinterpret_cast<float *>(base + o_d1)};
+        auto act = [&](int l) { return reinterpret_cast<float *>(base + o_act[l]); };
+        auto slope = [&](int l) { return reinterpret_cast<float *>(base + o_slope[l]); };
+        // the gradient buffer is read only at the sampled entries, all of which the
+        // reverse pass rewrites; it is still cleared so no stale value can leak out
+        HMC_CK(cudaMemsetAsync(G, 0, sizeof(float) * C * P, s));
+        // theta[c] = frozen, then theta[c][idx[j]] = q[c][j]
+        k_copy_rep<<<(unsigned)std::min<long>((C * P + 255) / 256, 4096), 256, 0, s>>>(frozen, P, C, theta);
+        HMC_LAUNCH_CK();
+        {
+            dim3 grid((unsigned)std::min<long>((k + 255) / 256, 1024), C);
+            k_scatter<float><<<grid, 256, 0, s>>>(q, subset_idx, k, theta, P);
+            HMC_LAUNCH_CK();
+        }
+        // forward
+        const float *a = x;
+        long a_b = 0;
+        for (int l = 0; l < L; ++l) {
+            const int wi = net->widths[l], wo = net->widths[l + 1];
+            GemmArgs<float> ga{(int)n, wo, wi, a, wi, 1, a_b, theta + woff[l], 1, wi, P};
+            EpiArgs<float> ea{EPI_ACT, act(l + 1), wo, 1, n * wo, boff[l] >= 0 ? theta + boff[l] : nullptr, 1, P,
+                              net->act[l], net->act[l] == HMC_ACT_IDENTITY ? nullptr : slope(l + 1)};
+            launch_gemm(ga, ea, C, s);
+            a = act(l + 1);
+            a_b = n * wo;
+        }
+        // residual and energy partials
+        const double inv_s2 = 1.0 / (noise_sigma * noise_sigma);
+        {
+            dim3 grid(nparts, C);
+            const float *sl = net->act[L - 1] == HMC_ACT_IDENTITY ? nullptr : slope(L);
+            k_residual<float><<<grid, 256, 0, s>>>(act(L), n_el, y, n_el, sl, inv_s2, d[0], part, nullptr, nparts);
+            HMC_LAUNCH_CK();
+        }
+        // reverse pass over every layer
+        float *dd = d[0];
+        int pp = 1;
+        for (int l = L - 1; l >= 0; --l) {
+            const int wi = net->widths[l], wo = net->widths[l + 1];
+            const float *ap = l == 0 ? x : act(l);
+            const long ap_b = l == 0 ? 0 : n * wi;
+            GemmArgs<float> gw{wo, wi, (int)n, dd, 1, wo, n * wo, ap, wi, 1, ap_b};
+            EpiArgs<float> ew{EPI_STORE, G + woff[l], wi, 1, P, nullptr, 0, 0, 0, nullptr};
+            launch_gemm(gw, ew, C, s);
+            if (boff[l] >= 0) {
+                dim3 grid((wo + 31) / 32, C);
+                k_colsum<float><<<grid, dim3(32, 8), 0, s>>>(dd, n, wo, n * wo, G + boff[l], P);
+                HMC_LAUNCH_CK();
+            }
+            if (l > 0) {
+                const bool id = net->act[l - 1] == HMC_ACT_IDENTITY;
+                GemmArgs<float> gi{(int)n, wi, wo, dd, wo, 1, n * wo, theta + woff[l], wi, 1, P};
+                EpiArgs<float> ei{id ? EPI_STORE : EPI_SCALE, d[pp], wi, 1, n * wi, nullptr, 0, 0, 0,
+                                  id ? nullptr : slope(l)};
+                launch_gemm(gi, ei, C, s);
+                dd = d[pp];
+                pp ^= 1;
+            }
+        }
+        k_finalize<float><<<C, 256, 0, s>>>(part, nullptr, nparts, 0.5 * inv_s2, q, k, subset_idx, G, P, -1,
+                                            1.0 / (prior_sigma * prior_sigma), U, grad);
+        HMC_LAUNCH_CK();
+        return HMC_OK;
+    } catch (const Fail &f) {
+        return f.st;
+    }
+}

@@ -139,12 +139,17 @@ def algorithmic(prob, C):
     act = 2.0 * N * w * C                     # one bf16 activation array, all chains
     wts = 2.0 * 2.0 * w * w * C               # bf16 hi + lo weights
     k_layer = prob.k / max(1, prob.net.n_layers)
+    fwd = (gemm, act + act + wts)                              # read A_i, write A_{i+1}
+    out = (gemm, act + act + wts + 4.0 * N)                    # read A_i, write delta, read y
+    bwd = (gemm, 3 * act + wts / 2)                            # read delta, A_i; write delta_i (bf16 W)
+    first = (gemm, 2 * act + wts / 2)                          # read delta, A_1
+    dw = (gemm, 2 * act + 4.0 * k_layer * C)                   # read delta, A_i; sampled entries out
     return {
-        "umma_fwd_tanh": (gemm, act + act + wts),
-        "umma_fwd_out": (gemm, act + act + wts + 4.0 * N),
-        "umma_bwd_tanh": (gemm, 3 * act + wts),
-        "umma_bwd_first": (gemm, 2 * act + wts),
-        "umma_dw": (gemm, 2 * act + 4.0 * k_layer * C),
+        "umma_fwd_tanh": fwd, "layer_fwd_tanh": fwd, "umma_fwd_out": out, "layer_fwd_out": out,
+        "umma_bwd_tanh": bwd, "solo_bwd_tanh": bwd, "layer_bwd_tanh": bwd,
+        "umma_bwd_first": first, "solo_bwd_first": first, "layer_bwd_first": first,
+        "umma_dw": dw, "dw2": dw,
+        "first_fwd": (2.0 * N * w * prob.x.shape[1] * C, act),
     }
 
 

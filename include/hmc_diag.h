@@ -38,10 +38,11 @@ typedef struct {
     long launches;
 } hmc_kernel_time;
 
-/* Run hmc_energy_grad on device states q (reps times, synchronously) with a
- * CUDA event pair around every kernel launch on the stream it is launched on,
- * and return per-kind totals in out[0..n-1]; the return value is n, or minus an
- * hmc_status on failure. */
+/* Run hmc_energy_grad on device states q reps times, synchronously, with a CUDA
+ * event pair around every kernel launch on the stream it is launched on; the
+ * timed evaluations are replayed from a CUDA graph so that the kernels run back
+ * to back as in a trajectory.  Per-kind totals go to out[0..n-1]; the return
+ * value is n, or minus an hmc_status on failure. */
 HMC_API int hmc_diag_profile_energy_grad(hmc_handle h, const void *q, int reps, hmc_kernel_time *out,
                                          int max_out);
 

@@ -60,14 +60,14 @@ ProfScope::ProfScope(const char *name, cudaStream_t st) : p(active_profiler()), 
     Profiler::Rec r{name, nullptr, nullptr};
     cudaEventCreate(&r.a);
     cudaEventCreate(&r.b);
-    cudaEventRecord(r.a, s);
+    cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal);   // a real record node when captured
     p->recs.push_back(r);
     i = p->recs.size() - 1;
 }
 
 ProfScope::~ProfScope()
 {
-    if (p) cudaEventRecord(p->recs[i].b, s);
+    if (p) cudaEventRecordWithFlags(p->recs[i].b, s, cudaEventRecordExternal);
 }
 
 void build_net_desc(NetDesc &nd, const hmc_mlp_spec &s, long base, const std::vector<long> &idx)
@@ -142,49 +142,75 @@ __device__ __forceinline__ double seg_sum(double v, double *sm)
     return r;
 }
 
-// p ~ N(0, I); K0 = p.p/2; first half kick p -= eps/2 g; first drift q* = q + eps p; scatter q*.
-template <typename T>
-__global__ void __launch_bounds__(256) k_traj_begin(const SegDesc *segs, int C, const T *q_cur, const T *g_cur,
-                                                    T *q_prop, T *p, double *K0, double eps, uint64_t seed,
-                                                    const TrajState *st)
+// The trajectory kernels run on a (blocks per chain) x (problem, chain) grid; each
+// block owns TRAJ_ELEMS consecutive coordinates of one chain.  Sums over a chain are
+// per-block partials added in a fixed order, so results do not depend on scheduling.
+constexpr int TRAJ_THREADS = 256;
+constexpr int TRAJ_ELEMS = 4 * TRAJ_THREADS;
+
+__device__ __forceinline__ void load_seg(SegDesc &dst, const SegDesc *src)
 {
+    const int *a = reinterpret_cast<const int *>(src);
+    int *d = reinterpret_cast<int *>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(SegDesc) / 4); i += blockDim.x) d[i] = a[i];
+    __syncthreads();
+}
+
+// p ~ N(0, I); partial sums of p.p; first half kick p -= eps/2 g; first drift q* = q + eps p; scatter q*.
+template <typename T>
+__global__ void __launch_bounds__(TRAJ_THREADS) k_traj_begin(const SegDesc *segs, int C, int nblk, const T *q_cur,
+                                                             const T *g_cur, T *q_prop, T *p, double *K0p,
+                                                             double eps, uint64_t seed, const TrajState *st)
+{
+    __shared__ __align__(16) unsigned char sd_raw[sizeof(SegDesc)];
+    SegDesc &sd = *reinterpret_cast<SegDesc *>(sd_raw);
     __shared__ double sm[8];
-    const int s = blockIdx.x, pi = s / C, c = s % C;
-    const SegDesc &sd = segs[pi];
-    const long base = sd.qoff + (long)c * sd.k;
-    const uint64_t traj = (uint64_t)st->traj;
-    const T h = (T)(0.5 * eps), e = (T)eps;
+    const int s = blockIdx.y, pi = s / C, c = s % C;
+    load_seg(sd, &segs[pi]);
+    const long j0 = (long)blockIdx.x * TRAJ_ELEMS;
     double kin = 0.0;
-    for (long blk = threadIdx.x; blk * 4 < sd.k; blk += blockDim.x) {
-        double z[4];
-        momenta4(seed, (uint64_t)sd.problem, (uint64_t)c, traj, (uint64_t)blk, z);
+    if (j0 < sd.k) {
+        const long base = sd.qoff + (long)c * sd.k;
+        const uint64_t traj = (uint64_t)st->traj;
+        const T h = (T)(0.5 * eps), e = (T)eps;
+        const long blk = j0 / 4 + threadIdx.x;
+        if (blk * 4 < sd.k) {
+            double z[4];
+            momenta4(seed, (uint64_t)sd.problem, (uint64_t)c, traj, (uint64_t)blk, z);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const long j = blk * 4 + t;
-            if (j >= sd.k) break;
-            T pj = (T)z[t];
-            kin += (double)pj * (double)pj;
-            pj = pj - h * g_cur[base + j];
-            const T qj = q_cur[base + j] + e * pj;
-            p[base + j] = pj;
-            q_prop[base + j] = qj;
-            scatter_one<T>(sd.sc, c, j, qj);
+            for (int t = 0; t < 4; ++t) {
+                const long j = blk * 4 + t;
+                if (j >= sd.k) break;
+                T pj = (T)z[t];
+                kin += (double)pj * (double)pj;
+                pj = pj - h * g_cur[base + j];
+                const T qj = q_cur[base + j] + e * pj;
+                p[base + j] = pj;
+                q_prop[base + j] = qj;
+                scatter_one<T>(sd.sc, c, j, qj);
+            }
         }
     }
     const double tot = seg_sum(kin, sm);
-    if (threadIdx.x == 0) K0[s] = 0.5 * tot;
+    if (threadIdx.x == 0) K0p[(long)s * nblk + blockIdx.x] = tot;
 }
 
-// p -= eps g; q += eps p; scatter q.
+// p -= kick g; q += drift p; scatter q.
 template <typename T>
-__global__ void __launch_bounds__(256) k_kick_drift(const SegDesc *segs, int C, const T *g, T *p, T *q, double kick,
-                                                    double drift)
+__global__ void __launch_bounds__(TRAJ_THREADS) k_kick_drift(const SegDesc *segs, int C, const T *g, T *p, T *q,
+                                                             double kick, double drift)
 {
-    const int s = blockIdx.x, pi = s / C, c = s % C;
-    const SegDesc &sd = segs[pi];
+    __shared__ __align__(16) unsigned char sd_raw[sizeof(SegDesc)];
+    SegDesc &sd = *reinterpret_cast<SegDesc *>(sd_raw);
+    const int s = blockIdx.y, pi = s / C, c = s % C;
+    load_seg(sd, &segs[pi]);
     const long base = sd.qoff + (long)c * sd.k;
     const T kk = (T)kick, dd = (T)drift;
-    for (long j = threadIdx.x; j < sd.k; j += blockDim.x) {
+    const long j0 = (long)blockIdx.x * TRAJ_ELEMS;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const long j = j0 + threadIdx.x + (long)t * TRAJ_THREADS;
+        if (j >= sd.k) break;
         T pj = p[base + j];
         if (kick != 0.0) pj = pj - kk * g[base + j];
         p[base + j] = pj;
@@ -196,42 +222,69 @@ __global__ void __launch_bounds__(256) k_kick_drift(const SegDesc *segs, int C, 
     }
 }
 
-// Last half kick, K1, dH = H1 - H0, accept iff log u < H0 - H1, record outputs.
+// Last half kick (p itself is not needed afterwards) and partial sums of p.p.
 template <typename T>
-__global__ void __launch_bounds__(256) k_traj_end(const SegDesc *segs, int C, int nseg, long S_total, T *q_cur,
-                                                  T *g_cur, double *U_cur, const T *q_prop, const T *p,
-                                                  const T *g_prop, const double *U_prop, const double *K0,
-                                                  double eps, uint64_t seed, const TrajState *st)
+__global__ void __launch_bounds__(TRAJ_THREADS) k_traj_kinetic(const SegDesc *segs, int C, int nblk, const T *p,
+                                                               const T *g_prop, double *K1p, double eps)
 {
-    T *samples = static_cast<T *>(st->samples);
-    unsigned char *acc_out = st->accepted;
-    double *dH_out = st->dH;
     __shared__ double sm[8];
-    __shared__ int s_acc;
-    const int s = blockIdx.x, pi = s / C, c = s % C;
-    const SegDesc &sd = segs[pi];
-    const long base = sd.qoff + (long)c * sd.k;
+    const int s = blockIdx.y, pi = s / C, c = s % C;
+    const long k = segs[pi].k;
+    const long base = segs[pi].qoff + (long)c * k;
     const T h = (T)(0.5 * eps);
+    const long j0 = (long)blockIdx.x * TRAJ_ELEMS;
     double kin = 0.0;
-    for (long j = threadIdx.x; j < sd.k; j += blockDim.x) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const long j = j0 + threadIdx.x + (long)t * TRAJ_THREADS;
+        if (j >= k) break;
         const T pj = p[base + j] - h * g_prop[base + j];
         kin += (double)pj * (double)pj;
     }
-    const double K1 = 0.5 * seg_sum(kin, sm);
+    const double tot = seg_sum(kin, sm);
+    if (threadIdx.x == 0) K1p[(long)s * nblk + blockIdx.x] = tot;
+}
+
+// Metropolis step.  Every block of a chain recomputes the same decision from the same
+// fixed-order sums (H0 = U + K0, H1 = U* + K1, accept iff log u < H0 - H1), then
+// copies its slice of the state; block 0 records the outputs.
+template <typename T>
+__global__ void __launch_bounds__(TRAJ_THREADS) k_traj_accept(const SegDesc *segs, int C, int nblk, int nseg,
+                                                              long S_total, T *q_cur, T *g_cur, const double *U_cur,
+                                                              const T *q_prop, const T *g_prop, const double *U_prop,
+                                                              const double *K0p, const double *K1p, uint64_t seed,
+                                                              const TrajState *st, int *acc_int)
+{
+    __shared__ int s_acc;
+    const int s = blockIdx.y, pi = s / C, c = s % C;
+    const long k = segs[pi].k;
+    const long base = segs[pi].qoff + (long)c * k;
     const long long slot = st->slot;
     if (threadIdx.x == 0) {
-        const double H0 = U_cur[s] + K0[s];
-        const double H1 = U_prop[s] + K1;
-        const double lu = mh_log_uniform(seed, (uint64_t)sd.problem, (uint64_t)c, (uint64_t)st->traj);
+        double K0 = 0.0, K1 = 0.0;
+        for (int i = 0; i < nblk; ++i) {
+            K0 += K0p[(long)s * nblk + i];
+            K1 += K1p[(long)s * nblk + i];
+        }
+        const double H0 = U_cur[s] + 0.5 * K0;
+        const double H1 = U_prop[s] + 0.5 * K1;
+        const double lu = mh_log_uniform(seed, (uint64_t)segs[pi].problem, (uint64_t)c, (uint64_t)st->traj);
         const int a = lu < H0 - H1;
         s_acc = a;
-        if (a) U_cur[s] = U_prop[s];
-        if (acc_out) acc_out[slot * nseg + s] = (unsigned char)a;
-        if (dH_out) dH_out[slot * nseg + s] = H1 - H0;
+        if (blockIdx.x == 0) {
+            acc_int[s] = a;
+            if (st->accepted) st->accepted[slot * nseg + s] = (unsigned char)a;
+            if (st->dH) st->dH[slot * nseg + s] = H1 - H0;
+        }
     }
     __syncthreads();
     const int a = s_acc;
-    for (long j = threadIdx.x; j < sd.k; j += blockDim.x) {
+    T *samples = static_cast<T *>(st->samples);
+    const long j0 = (long)blockIdx.x * TRAJ_ELEMS;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const long j = j0 + threadIdx.x + (long)t * TRAJ_THREADS;
+        if (j >= k) break;
         T qj = q_cur[base + j];
         if (a) {
             qj = q_prop[base + j];
@@ -242,10 +295,15 @@ __global__ void __launch_bounds__(256) k_traj_end(const SegDesc *segs, int C, in
     }
 }
 
-__global__ void k_traj_advance(TrajState *st)
+// After every block has decided: commit U of accepted chains, advance the counters.
+__global__ void k_traj_advance(TrajState *st, int nseg, const int *acc_int, double *U_cur, const double *U_prop)
 {
-    st->traj += 1;
-    st->slot += 1;
+    for (int s = threadIdx.x; s < nseg; s += blockDim.x)
+        if (acc_int[s]) U_cur[s] = U_prop[s];
+    if (threadIdx.x == 0) {
+        st->traj += 1;
+        st->slot += 1;
+    }
 }
 
 __global__ void k_set_state(TrajState *st, long long traj, long long slot, void *samples, unsigned char *acc,
@@ -306,7 +364,8 @@ struct hmc_handle_s {
     std::vector<std::unique_ptr<Engine>> engines;
     std::vector<long> qoff;
     long k_total = 0, P_total = 0, S_total = 0;
-    DevBuf q_cur, g_cur, q_prop, p, g_prop, U_cur, U_prop, K0, segs, state, scratch;
+    DevBuf q_cur, g_cur, q_prop, p, g_prop, U_cur, U_prop, K0p, K1p, acc_int, segs, state, scratch;
+    int traj_nblk = 1;   // blocks per chain in the trajectory kernels
     std::vector<std::unique_ptr<DevBuf>> stage;
     // one trajectory as an executable graph, reused while (eps, L, seed) stay the same
     cudaGraphExec_t traj_exec = nullptr;
@@ -454,37 +513,45 @@ void kick_drift(hmc_handle h, void *q, void *p, const void *g, double kick, doub
 {
     const int nseg = h->nprob * h->C;
     const SegDesc *sd = h->segs.as<SegDesc>();
+    const dim3 grid(h->traj_nblk, nseg);
     if (h->prec == HMC_PREC_FP64)
-        k_kick_drift<double><<<nseg, 256, 0, h->stream>>>(sd, h->C, (const double *)g, (double *)p, (double *)q, kick,
-                                                          drift);
+        k_kick_drift<double><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, (const double *)g, (double *)p,
+                                                                   (double *)q, kick, drift);
     else
-        k_kick_drift<float><<<nseg, 256, 0, h->stream>>>(sd, h->C, (const float *)g, (float *)p, (float *)q, kick,
-                                                         drift);
+        k_kick_drift<float><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, (const float *)g, (float *)p, (float *)q,
+                                                                  kick, drift);
     HMC_LAUNCH_CK();
 }
 
 template <typename T> void enqueue_trajectory(hmc_handle h, double eps, int L, uint64_t seed)
 {
-    const int nseg = h->nprob * h->C;
+    const int nseg = h->nprob * h->C, nblk = h->traj_nblk;
     const SegDesc *sd = h->segs.as<SegDesc>();
     TrajState *st = h->state.as<TrajState>();
-    k_traj_begin<T><<<nseg, 256, 0, h->stream>>>(sd, h->C, h->q_cur.as<T>(), h->g_cur.as<T>(), h->q_prop.as<T>(),
-                                                 h->p.as<T>(), h->K0.as<double>(), eps, seed, st);
+    const dim3 grid(nblk, nseg);
+    k_traj_begin<T><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, nblk, h->q_cur.as<T>(), h->g_cur.as<T>(),
+                                                          h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(), eps,
+                                                          seed, st);
     HMC_LAUNCH_CK();
     for (int s = 1; s <= L; ++s) {
         energy_grad_all(h, h->q_prop.ptr, h->U_prop.as<double>(), h->g_prop.ptr, true);
         if (s < L) {
-            k_kick_drift<T><<<nseg, 256, 0, h->stream>>>(sd, h->C, h->g_prop.as<T>(), h->p.as<T>(), h->q_prop.as<T>(),
-                                                         eps, eps);
+            k_kick_drift<T><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, h->g_prop.as<T>(), h->p.as<T>(),
+                                                                  h->q_prop.as<T>(), eps, eps);
             HMC_LAUNCH_CK();
         }
     }
-    k_traj_end<T><<<nseg, 256, 0, h->stream>>>(sd, h->C, nseg, h->S_total, h->q_cur.as<T>(), h->g_cur.as<T>(),
-                                               h->U_cur.as<double>(), h->q_prop.as<T>(), h->p.as<T>(),
-                                               h->g_prop.as<T>(), h->U_prop.as<double>(), h->K0.as<double>(), eps,
-                                               seed, st);
+    k_traj_kinetic<T><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, nblk, h->p.as<T>(), h->g_prop.as<T>(),
+                                                            h->K1p.as<double>(), eps);
     HMC_LAUNCH_CK();
-    k_traj_advance<<<1, 1, 0, h->stream>>>(st);
+    k_traj_accept<T><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, nblk, nseg, h->S_total, h->q_cur.as<T>(),
+                                                           h->g_cur.as<T>(), h->U_cur.as<double>(), h->q_prop.as<T>(),
+                                                           h->g_prop.as<T>(), h->U_prop.as<double>(),
+                                                           h->K0p.as<double>(), h->K1p.as<double>(), seed, st,
+                                                           h->acc_int.as<int>());
+    HMC_LAUNCH_CK();
+    k_traj_advance<<<1, 256, 0, h->stream>>>(st, nseg, h->acc_int.as<int>(), h->U_cur.as<double>(),
+                                             h->U_prop.as<double>());
     HMC_LAUNCH_CK();
 }
 
@@ -544,7 +611,12 @@ hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, co
     const size_t nseg = (size_t)nprob * C;
     h->U_cur.alloc(sizeof(double) * nseg);
     h->U_prop.alloc(sizeof(double) * nseg);
-    h->K0.alloc(sizeof(double) * nseg);
+    long kmax = 1;
+    for (auto &pr : h->probs) kmax = std::max(kmax, pr->k);
+    h->traj_nblk = (int)((kmax + TRAJ_ELEMS - 1) / TRAJ_ELEMS);
+    h->K0p.alloc(sizeof(double) * nseg * h->traj_nblk);
+    h->K1p.alloc(sizeof(double) * nseg * h->traj_nblk);
+    h->acc_int.alloc(sizeof(int) * nseg);
     h->scratch.alloc(sizeof(int) * 4);
     h->state.alloc(sizeof(TrajState));
     std::vector<SegDesc> sd(nprob);
@@ -763,19 +835,33 @@ int hmc_diag_profile_energy_grad(hmc_handle h, const void *q, int reps, hmc_kern
     g_err.clear();
     Profiler prof;
     int n = 0;
+    cudaGraphExec_t exec = nullptr;
     hmc_status st = guarded([&]() -> hmc_status {
         HMC_REQUIRE(h && q && out && reps >= 1 && max_out >= 1, "bad argument");
         HMC_REQUIRE(is_device_ptr(q), "q must be device memory");
         join_in(h);
         HMC_CK(cudaStreamSynchronize(h->stream));
+        // one untimed evaluation, then `reps` timed ones replayed from a graph so that the
+        // GPU runs them back to back (the host never starves it between launches)
+        energy_grad_all(h, const_cast<void *>(q), h->U_prop.as<double>(), h->g_prop.ptr, false);
+        cudaGraph_t graph = nullptr;
+        HMC_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         active_profiler() = &prof;
         try {
-            for (int r = 0; r < reps; ++r) energy_grad_all(h, const_cast<void *>(q), h->U_prop.as<double>(), h->g_prop.ptr, false);
+            for (int r = 0; r < reps; ++r)
+                energy_grad_all(h, const_cast<void *>(q), h->U_prop.as<double>(), h->g_prop.ptr, false);
         } catch (...) {
             active_profiler() = nullptr;
+            cudaStreamEndCapture(h->stream, &graph);
+            if (graph) cudaGraphDestroy(graph);
             throw;
         }
         active_profiler() = nullptr;
+        HMC_CK(cudaStreamEndCapture(h->stream, &graph));
+        cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        HMC_CK(e);
+        HMC_CK(cudaGraphLaunch(exec, h->stream));
         HMC_CK(cudaStreamSynchronize(h->stream));
         for (auto &r : prof.recs) {
             float ms = 0.0f;
@@ -794,6 +880,7 @@ int hmc_diag_profile_energy_grad(hmc_handle h, const void *q, int reps, hmc_kern
         join_out(h);
         return HMC_OK;
     });
+    if (exec) cudaGraphExecDestroy(exec);
     for (auto &r : prof.recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);

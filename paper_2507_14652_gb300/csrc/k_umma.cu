@@ -70,6 +70,7 @@ struct Params {
     const int *rowptr;                    // M_DW: entries of output row o are [rowptr[o], rowptr[o+1])
     const int *ecol;                      // M_DW: column of entry j inside the layer
     const int *erow;                      // M_DW: row of entry j
+    const int *epack;                     // row << 16 | column of entry j (dW gather)
     float *gw_part; long gw_split; long gw_b;   // M_DW: [split][b][k]
 };
 
@@ -359,27 +360,574 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
 }
 
 // ---------------------------------------------------------------------------
+// Persistent layer kernel for the w x w hidden layers (w = 128 or 256).
+//
+// A cluster of two CTAs walks a contiguous range of (chain, 128-row tile) units;
+// CTA r owns output columns [r w/2, (r+1) w/2).  Its half of W (bf16 hi and lo,
+// all K) stays resident in shared memory while the chain does not change; the
+// A operand (activations or deltas) streams through a 4-stage ring of 16 KB
+// K-blocks.  Two TMEM accumulators alternate so the epilogue of one tile runs
+// while the MMAs of the next one are in flight.  The output-layer epilogue needs
+// whole rows: the two CTAs swap their partial dot products through distributed
+// shared memory, guarded by an mbarrier in each CTA.
+// ---------------------------------------------------------------------------
+enum LMode { L_FWD_TANH = 0, L_FWD_OUT = 1, L_BWD_TANH = 2, L_BWD_FIRST = 3 };
+constexpr int L_STAGES = 4;
+constexpr int L_A_BYTES = BM * BK * 2;                  // one 16 KB K-block of a 128-row tile
+constexpr int L_W_HALF = 64 * 1024;                     // resident half of W, hi or lo (4 K-blocks x 16 KB)
+constexpr int L_RED_FLOATS = 5 * 4 * 256;               // [1 + dx][4 warps][columns]: dx <= 8 at 128 columns, dx <= 4 at 256
+constexpr int L_SMEM = 1024 + 2 * L_W_HALF + L_STAGES * L_A_BYTES + 256 + L_RED_FLOATS * 4 + 2 * 128 * 4 + 64 + 64 +
+                       2 * 256 * 4;                      // + bias and output weights of the current chain
+
+struct LayerParams {
+    int N, W, C, ntiles, dx;
+    int *err;
+    __nv_bfloat16 *out;            // [c][N][W]
+    const float *bias;             // [c][W]
+    const __nv_bfloat16 *aux;      // [c][N][W]
+    const float *wout, *bout, *y;  // output layer and targets
+    float inv_s2;
+    double *u_part;                // [c][tiles]
+    float *dbout_part;             // [c][tiles]
+    float *dwout_part, *db_part;   // [c][tiles][W]
+    const float *x;                // [N][dx]
+    float *dw0_part;               // [c][tiles][W][dx]
+};
+
+// CLUSTER: two CTAs split the output columns (forward, with the hi/lo weights).
+// Otherwise one CTA computes all columns of its tiles with a single bf16 W resident
+// (the reverse pass, which does not need the lo part).  WIDTH = w (128 or 256).
+// The epilogue issues a tile's global loads (slopes, targets) before it waits for
+// the accumulator, so their latency overlaps the tile's MMAs.
+template <int MODE, bool CLUSTER, bool WSPLIT, int WIDTH>
+__device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtensorMap &tmWh, const CUtensorMap &tmWl,
+                                           const LayerParams &p)
+{
+    constexpr bool BWD = (MODE == L_BWD_TANH || MODE == L_BWD_FIRST);
+    constexpr int LN = CLUSTER ? WIDTH / 2 : WIDTH;    // output columns of this CTA
+    constexpr int NKB = WIDTH / 64;                    // K-blocks of the reduction
+    constexpr int NCH = LN / 32;                       // 32-column chunks of a row
+    constexpr int SLOT = CLUSTER ? 128 : 256;          // TMEM columns per accumulator
+    constexpr int TCOLS = 2 * SLOT;
+    constexpr int kblk = LN * 128;                     // bytes of one resident K-block
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sWh = smem;
+    uint8_t *sWl = smem + L_W_HALF;
+    uint8_t *sA = smem + 2 * L_W_HALF;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + L_STAGES * L_A_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * L_STAGES + 7);
+    float *red = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(bars) + 256);
+    float *xchg = red + L_RED_FLOATS;                          // [2][128] partial dot products from the peer
+    double *dred = reinterpret_cast<double *>(xchg + 256);     // [4]
+    float *fred = reinterpret_cast<float *>(dred + 4);         // [4]
+    float *sbias = fred + 16;                                  // [256] bias of the current chain
+    float *swo = sbias + 256;                                  // [256] output weights of the current chain
+    const uint32_t a_full0 = smem_u32(bars), a_empty0 = a_full0 + 8 * L_STAGES;
+    const uint32_t w_full = a_empty0 + 8 * L_STAGES, w_empty = w_full + 8;
+    const uint32_t acc_full0 = w_empty + 8, acc_empty0 = acc_full0 + 16, xbar = acc_empty0 + 16;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = CLUSTER ? cluster_ctarank() : 0u;
+    const long U = (long)p.C * p.ntiles;
+    const int ncl = CLUSTER ? gridDim.x / 2 : gridDim.x, ci = CLUSTER ? blockIdx.x / 2 : blockIdx.x;
+    const long u0 = U * ci / ncl, u1 = U * (ci + 1) / ncl;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < L_STAGES; ++s) {
+            mbar_init(a_full0 + 8 * s, 1);
+            mbar_init(a_empty0 + 8 * s, 1);
+        }
+        mbar_init(w_full, 1);
+        mbar_init(w_empty, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(acc_full0 + 8 * s, 1);
+            mbar_init(acc_empty0 + 8 * s, 128);
+        }
+        mbar_init(xbar, 128);
+        fence_mbar_init();
+        prefetch_map(&tmA);
+        prefetch_map(&tmWh);
+        if (WSPLIT) prefetch_map(&tmWl);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), TCOLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (CLUSTER) cluster_sync_all();   // the peer's barriers exist before anyone arrives on them
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {   // TMA producer
+            int cur_c = -1;
+            uint32_t wph = 0;
+            long kbi = 0;
+            bool ok = true, w_pending = false;
+            for (long u = u0; u < u1 && ok; ++u) {
+                const int c = (int)(u / p.ntiles), t = (int)(u % p.ntiles);
+                if (c != cur_c) {
+                    if (cur_c >= 0) {
+                        if (!mbar_wait(w_empty, wph, p.err)) { ok = false; break; }
+                        wph ^= 1u;
+                    }
+                    mbar_expect_tx(w_full, (WSPLIT ? 2u : 1u) * NKB * kblk);
+                    for (int kb = 0; kb < NKB; ++kb) {
+                        const uint32_t dh = smem_u32(sWh) + kb * kblk, dl = smem_u32(sWl) + kb * kblk;
+                        if (!BWD) {
+                            tma_load_3d(dh, &tmWh, kb * BK, (int)rank * LN, c, w_full);
+                            if (WSPLIT) tma_load_3d(dl, &tmWl, kb * BK, (int)rank * LN, c, w_full);
+                        } else {
+                            for (int a = 0; a < LN / 64; ++a) {
+                                tma_load_3d(dh + 8192 * a, &tmWh, (int)rank * LN + 64 * a, kb * BK, c, w_full);
+                                if (WSPLIT)
+                                    tma_load_3d(dl + 8192 * a, &tmWl, (int)rank * LN + 64 * a, kb * BK, c, w_full);
+                            }
+                        }
+                    }
+                    w_pending = true;
+                    cur_c = c;
+                }
+                for (int kb = 0; kb < NKB; ++kb) {
+                    const int s = (int)(kbi % L_STAGES);
+                    const uint32_t ph = (uint32_t)(kbi / L_STAGES) & 1u;
+                    if (!mbar_wait(a_empty0 + 8 * s, ph ^ 1u, p.err)) { ok = false; break; }
+                    mbar_expect_tx(a_full0 + 8 * s, L_A_BYTES);
+                    tma_load_3d(smem_u32(sA + s * L_A_BYTES), &tmA, kb * BK, t * BM, c, a_full0 + 8 * s);
+                    ++kbi;
+                }
+            }
+            if (!ok) {   // let copies already in flight land before the CTA exits
+                for (long i = std::max<long>(0, kbi - L_STAGES); i < kbi; ++i)
+                    mbar_wait(a_full0 + 8 * (int)(i % L_STAGES), (uint32_t)(i / L_STAGES) & 1u, p.err, 100000000ull);
+                if (w_pending) mbar_wait(w_full, wph, p.err, 100000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // MMA issuer
+            const uint32_t idesc = idesc_bf16(BM, LN, false, BWD);
+            int cur_c = -1;
+            uint32_t wph = 0;
+            long kbi = 0;
+            int it = 0;
+            bool ok = true;
+            for (long u = u0; u < u1 && ok; ++u, ++it) {
+                const int c = (int)(u / p.ntiles);
+                if (c != cur_c) {
+                    if (!mbar_wait(w_full, wph, p.err)) { ok = false; break; }
+                    wph ^= 1u;
+                    cur_c = c;
+                }
+                const int slot = it & 1;
+                if (!mbar_wait(acc_empty0 + 8 * slot, ((uint32_t)(it >> 1) & 1u) ^ 1u, p.err)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(slot * SLOT);
+                for (int kb = 0; kb < NKB; ++kb) {
+                    const int s = (int)(kbi % L_STAGES);
+                    const uint32_t ph = (uint32_t)(kbi / L_STAGES) & 1u;
+                    if (!mbar_wait(a_full0 + 8 * s, ph, p.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(sA + s * L_A_BYTES);
+                    const uint32_t wh = smem_u32(sWh) + kb * kblk, wl = smem_u32(sWl) + kb * kblk;
+#pragma unroll
+                    for (int ks = 0; ks < BK / 16; ++ks) {
+                        const uint64_t ad = sdesc(sa + 32 * ks, 0, 1024);
+                        const uint64_t bh = BWD ? sdesc(wh + 2048 * ks, 8192, 1024) : sdesc(wh + 32 * ks, 0, 1024);
+                        mma_bf16(d_tmem, ad, bh, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+                        if (WSPLIT) {
+                            const uint64_t bl = BWD ? sdesc(wl + 2048 * ks, 8192, 1024) : sdesc(wl + 32 * ks, 0, 1024);
+                            mma_bf16(d_tmem, ad, bl, idesc, 1u);
+                        }
+                    }
+                    mma_commit(a_empty0 + 8 * s);
+                    ++kbi;
+                }
+                if (!ok) break;
+                mma_commit(acc_full0 + 8 * slot);
+                const int next_c = (u + 1 < u1) ? (int)((u + 1) / p.ntiles) : -1;
+                if (next_c != c) mma_commit(w_empty);
+            }
+        }
+    } else {
+        // ---------------- epilogue warps 2..5, one tile row per thread ----------------
+        const int q = warp & 3, row = 32 * q + lane, et = threadIdx.x - 64;
+        const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+        const int col0 = (int)rank * LN;
+        int it = 0, chain_loaded = -1;
+        for (long u = u0; u < u1; ++u, ++it) {
+            const int c = (int)(u / p.ntiles), t = (int)(u % p.ntiles);
+            const int slot = it & 1;
+            const int m = t * BM + row;
+            const bool valid = m < p.N;
+            const long rowoff = ((long)c * p.N + (valid ? m : 0)) * p.W + col0;
+            const long part = ((long)c * p.ntiles + t) * p.W + col0;
+            // global loads of this tile, issued before the accumulator wait
+            uint4 ap[BWD ? NCH * 4 : 1];
+            if (BWD) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(p.aux + rowoff);
+#pragma unroll
+                for (int i = 0; i < NCH * 4; ++i) ap[i] = valid ? src[i] : make_uint4(0u, 0u, 0u, 0u);
+            }
+            const float yv = (MODE == L_FWD_OUT && valid) ? p.y[m] : 0.0f;
+            float xv[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d)
+                xv[d] = (MODE == L_BWD_FIRST && valid && d < p.dx) ? p.x[(long)m * p.dx + d] : 0.0f;
+            // per-chain constants into shared memory
+            if (!BWD && c != chain_loaded) {
+                named_bar_sync(1, 128);
+                for (int i = et; i < LN; i += 128) {
+                    sbias[i] = p.bias[(long)c * p.W + col0 + i];
+                    if (MODE == L_FWD_OUT) swo[i] = p.wout[(long)c * p.W + col0 + i];
+                }
+                named_bar_sync(1, 128);
+                chain_loaded = c;
+            }
+            if (!mbar_wait(acc_full0 + 8 * slot, (uint32_t)(it >> 1) & 1u, p.err)) break;
+            tc_fence_after();
+            const uint32_t taddr = tmem + lane_off + (uint32_t)(slot * SLOT);
+            bool ok = true;
+            if (MODE == L_FWD_TANH) {
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    const int c0 = 32 * ch;
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
+                    if (valid) {
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            pk[j] = pack_bf16(tanh_fast(v[2 * j] + sbias[c0 + 2 * j]),
+                                              tanh_fast(v[2 * j + 1] + sbias[c0 + 2 * j + 1]));
+                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    }
+                }
+            } else if (BWD) {
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    const int c0 = 32 * ch;
+                    float v[32], dd[32];
+                    tmem_ld32(taddr + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint4 uu = ap[4 * ch + j];
+                        const uint32_t w4[4] = {uu.x, uu.y, uu.z, uu.w};
+#pragma unroll
+                        for (int tt = 0; tt < 4; ++tt) {
+                            const float2 a = unpack_bf16(w4[tt]);
+                            dd[8 * j + 2 * tt] = valid ? v[8 * j + 2 * tt] * (1.0f - a.x * a.x) : 0.0f;
+                            dd[8 * j + 2 * tt + 1] = valid ? v[8 * j + 2 * tt + 1] * (1.0f - a.y * a.y) : 0.0f;
+                        }
+                    }
+                    if (MODE == L_BWD_TANH && valid) {
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
+                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    }
+                    if (MODE == L_BWD_FIRST) {
+                        for (int d = 0; d < p.dx; ++d) {
+                            float tv[32];
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) tv[j] = dd[j] * xv[d];
+                            red[((1 + d) * 4 + q) * LN + c0 + lane] = reduce_scatter32(tv);
+                        }
+                    }
+                    red[(0 * 4 + q) * LN + c0 + lane] = reduce_scatter32(dd);
+                }
+                named_bar_sync(1, 128);
+                for (int cc = et; cc < LN; cc += 128) {
+                    p.db_part[part + cc] = red[(0 * 4 + 0) * LN + cc] + red[(0 * 4 + 1) * LN + cc] +
+                                           red[(0 * 4 + 2) * LN + cc] + red[(0 * 4 + 3) * LN + cc];
+                    if (MODE == L_BWD_FIRST)
+                        for (int d = 0; d < p.dx; ++d)
+                            p.dw0_part[(part + cc) * p.dx + d] =
+                                red[((1 + d) * 4 + 0) * LN + cc] + red[((1 + d) * 4 + 1) * LN + cc] +
+                                red[((1 + d) * 4 + 2) * LN + cc] + red[((1 + d) * 4 + 3) * LN + cc];
+                }
+                named_bar_sync(1, 128);
+            } else if (MODE == L_FWD_OUT) {
+                float f = 0.0f;
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    const int c0 = 32 * ch;
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) f += tanh_fast(v[j] + sbias[c0 + j]) * swo[c0 + j];
+                }
+                float fp = 0.0f;
+                if (CLUSTER) {   // swap partial dot products with the peer CTA
+                    const int xb = it & 1;
+                    const uint32_t mine = smem_u32(xchg + xb * 128 + row);
+                    st_cluster_f32(mapa_shared(mine, rank ^ 1u), f);
+                    mbar_arrive_cluster(mapa_shared(xbar, rank ^ 1u));
+                    ok = mbar_wait_cluster(xbar, (uint32_t)it & 1u, p.err);
+                    fp = xchg[xb * 128 + row];
+                }
+                const float f0 = rank == 0 ? f : fp, f1 = rank == 0 ? fp : f;
+                const float fo = (p.bout[c] + f0) + f1;
+                const float r = valid ? fo - yv : 0.0f;
+                const float d = r * p.inv_s2;
+                if (rank == 0) {
+                    double r2 = (double)r * (double)r;
+                    float ds = d;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+                        ds += __shfl_xor_sync(0xffffffffu, ds, o);
+                    }
+                    if (lane == 0) {
+                        dred[q] = r2;
+                        fred[q] = ds;
+                    }
+                }
+#pragma unroll
+                for (int ch = 0; ch < NCH; ++ch) {
+                    const int c0 = 32 * ch;
+                    float v[32], dw[32], dd[32];
+                    tmem_ld32(taddr + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float a = tanh_fast(v[j] + sbias[c0 + j]);
+                        dw[j] = d * a;
+                        dd[j] = d * swo[c0 + j] * (1.0f - a * a);
+                    }
+                    if (valid) {
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
+                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    }
+                    red[(0 * 4 + q) * LN + c0 + lane] = reduce_scatter32(dw);
+                    red[(1 * 4 + q) * LN + c0 + lane] = reduce_scatter32(dd);
+                }
+                named_bar_sync(1, 128);
+                for (int cc = et; cc < LN; cc += 128) {
+                    p.dwout_part[part + cc] = red[(0 * 4 + 0) * LN + cc] + red[(0 * 4 + 1) * LN + cc] +
+                                              red[(0 * 4 + 2) * LN + cc] + red[(0 * 4 + 3) * LN + cc];
+                    p.db_part[part + cc] = red[(1 * 4 + 0) * LN + cc] + red[(1 * 4 + 1) * LN + cc] +
+                                           red[(1 * 4 + 2) * LN + cc] + red[(1 * 4 + 3) * LN + cc];
+                }
+                if (rank == 0 && et == 0) {
+                    p.u_part[(long)c * p.ntiles + t] = dred[0] + dred[1] + dred[2] + dred[3];
+                    p.dbout_part[(long)c * p.ntiles + t] = fred[0] + fred[1] + fred[2] + fred[3];
+                }
+                named_bar_sync(1, 128);
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty0 + 8 * slot);
+            if (!ok) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (CLUSTER) cluster_sync_all();   // no CTA leaves while its peer may still touch its shared memory
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, TCOLS);
+    }
+}
+
+template <int MODE, int WIDTH>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+    k_layer(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmWh,
+            const __grid_constant__ CUtensorMap tmWl, const LayerParams p)
+{
+    layer_body<MODE, true, true, WIDTH>(tmA, tmWh, tmWl, p);
+}
+
+template <int MODE, int WIDTH>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_layer_solo(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmWh,
+                 const __grid_constant__ CUtensorMap tmWl, const LayerParams p)
+{
+    layer_body<MODE, false, false, WIDTH>(tmA, tmWh, tmWl, p);
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient of a w x w hidden layer at the sampled entries, one CTA per
+// (row split, chain): dW = delta^T A over the CTA's rows, with both operands read
+// MN-major straight from their row-major [rows][w] arrays.  The CTA covers all w
+// output rows of dW as two M = 128 accumulators that share every B stage, so each
+// byte of delta and A is loaded once.  Only the sampled entries leave the chip.
+// ---------------------------------------------------------------------------
+constexpr int DW_STAGES = 3;
+constexpr int DW_A_BYTES = 2 * BM * BK * 2;    // 32 KB: delta, 256 output rows x 64 data rows
+constexpr int DW_B_BYTES = 256 * BK * 2;       // 32 KB: A_i, 256 columns x 64 data rows
+constexpr int DW_STAGE = DW_A_BYTES + DW_B_BYTES;
+constexpr int DW_SMEM = 1024 + DW_STAGES * DW_STAGE + 256;
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_dw2(const __grid_constant__ CUtensorMap tmD,
+                                                     const __grid_constant__ CUtensorMap tmA, const Params p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + DW_STAGES * DW_STAGE);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * DW_STAGES + 1);
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * DW_STAGES, accb = empty0 + 8 * DW_STAGES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int split = blockIdx.y, b = blockIdx.z;
+    const int BN = p.N;    // A_i columns (w)
+    const int MW = p.M;    // output rows of dW (w)
+    const int total_kb = (p.K + BK - 1) / BK;
+    const int kb0 = split * p.kb_per_split;
+    const int nkb = min(p.kb_per_split, total_kb - kb0);
+    const int nmh = (MW + BM - 1) / BM;     // 1 or 2 accumulators
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < DW_STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        fence_mbar_init();
+        prefetch_map(&tmD);
+        prefetch_map(&tmA);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            const uint32_t bytes = (uint32_t)(nmh * BM * BK * 2 + BN * BK * 2);
+            for (int i = 0; i < nkb; ++i) {
+                const int s = i % DW_STAGES;
+                const uint32_t ph = (uint32_t)(i / DW_STAGES) & 1u;
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.err)) { ok = false; break; }
+                const uint32_t fb = full0 + 8 * s;
+                mbar_expect_tx(fb, bytes);
+                const uint32_t sa = smem_u32(smem + s * DW_STAGE), sb = sa + DW_A_BYTES;
+                const int kc = (kb0 + i) * BK;
+                for (int mh = 0; mh < nmh; ++mh)
+                    for (int a = 0; a < 2; ++a)
+                        tma_load_3d(sa + (mh * 2 + a) * 8192, &tmD, mh * BM + 64 * a, kc, b, fb);
+                for (int a = 0; a < BN / 64; ++a) tma_load_3d(sb + 8192 * a, &tmA, 64 * a, kc, b, fb);
+                ++issued;
+            }
+            if (!ok)
+                for (int i = max(0, issued - DW_STAGES); i < issued; ++i)
+                    mbar_wait(full0 + 8 * (i % DW_STAGES), (uint32_t)(i / DW_STAGES) & 1u, p.err, 100000000ull);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(BM, BN, true, true);
+            for (int i = 0; i < nkb; ++i) {
+                const int s = i % DW_STAGES;
+                const uint32_t ph = (uint32_t)(i / DW_STAGES) & 1u;
+                if (!mbar_wait(full0 + 8 * s, ph, p.err)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * DW_STAGE), sb = sa + DW_A_BYTES;
+#pragma unroll
+                for (int ks = 0; ks < BK / 16; ++ks) {
+                    const uint64_t bd = sdesc(sb + 2048 * ks, 8192, 1024);
+                    for (int mh = 0; mh < nmh; ++mh) {
+                        const uint64_t ad = sdesc(sa + mh * 16384 + 2048 * ks, 8192, 1024);
+                        mma_bf16(tmem + (uint32_t)(mh * 256), ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
+                    }
+                }
+                mma_commit(empty0 + 8 * s);
+            }
+            mma_commit(accb);
+        }
+    } else {
+        const int q = warp & 3, row = 32 * q + lane, et = threadIdx.x - 64;
+        ok = mbar_wait(accb, 0, p.err);
+        tc_fence_after();
+        if (ok) {
+            float *stg = reinterpret_cast<float *>(smem);   // operand buffers are idle now
+            for (int mh = 0; mh < nmh; ++mh) {
+                const int m0 = mh * BM;
+                const int r_end = min(m0 + BM, MW);
+                const int j0 = p.rowptr[m0], j1 = p.rowptr[r_end];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(mh * 256);
+                for (int h0 = 0; h0 < BN; h0 += 128) {
+                    const int hc = min(128, BN - h0);
+                    for (int c0 = 0; c0 < hc; c0 += 32) {
+                        float v[32];
+                        tmem_ld32(taddr + h0 + c0, v);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) stg[row * 129 + c0 + j] = v[j];
+                    }
+                    named_bar_sync(1, 128);
+                    // eight index loads in flight per thread before any dependent access
+                    float *dst = p.gw_part + (long)split * p.gw_split + (long)b * p.gw_b;
+                    for (int base = j0; base < j1; base += 128 * 8) {
+                        int e[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int j = base + et + 128 * u;
+                            e[u] = j < j1 ? p.epack[j] : -1;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            if (e[u] < 0) continue;
+                            const int c = (e[u] & 0xFFFF) - h0;
+                            if (c >= 0 && c < hc) dst[base + et + 128 * u] = stg[((e[u] >> 16) - m0) * 129 + c];
+                        }
+                    }
+                    named_bar_sync(1, 128);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // CUDA-core kernels around the tensor-core GEMMs
 // ---------------------------------------------------------------------------
 
-// A_1[b][n][o] = tanh(sum_d X[n][d] W0[b][o][d] + b0[b][o]) in bf16.
-__global__ void __launch_bounds__(256) k_first_fwd(const float *x, int dx, long N, int w, const float *W0,
+// A_1[b][n][o] = tanh(sum_d X[n][d] W0[b][o][d] + b0[b][o]) in bf16.  One block per
+// (128-row tile, chain); thread o keeps row o of W0 and b0 in registers and walks the
+// tile's rows, whose inputs are staged in shared memory; a warp writes 64 contiguous bytes.
+__global__ void __launch_bounds__(256) k_first_fwd(const float *x, int dx, int N, int w, const float *W0,
                                                    const float *b0, __nv_bfloat16 *A1)
 {
-    const int b = blockIdx.y;
-    const long total = N * (long)(w / 2);
-    const float *Wb = W0 + (long)b * w * dx;
-    const float *bb = b0 + (long)b * w;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-        const long n = i / (w / 2);
-        const int o = (int)(i % (w / 2)) * 2;
-        float z0 = bb[o], z1 = bb[o + 1];
-        for (int d = 0; d < dx; ++d) {
-            const float xv = x[n * dx + d];
-            z0 += xv * Wb[(long)o * dx + d];
-            z1 += xv * Wb[(long)(o + 1) * dx + d];
+    __shared__ float xs[BM * 8];
+    const int b = blockIdx.y, n0 = blockIdx.x * BM;
+    const int nr = min(BM, N - n0);
+    for (int i = threadIdx.x; i < nr * dx; i += blockDim.x) xs[i] = x[(long)n0 * dx + i];
+    __syncthreads();
+    for (int o = threadIdx.x; o < w; o += blockDim.x) {
+        float wr[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) wr[d] = d < dx ? W0[((long)b * w + o) * dx + d] : 0.0f;
+        const float bo = b0[(long)b * w + o];
+        __nv_bfloat16 *out = A1 + ((long)b * N + n0) * w + o;
+        for (int r = 0; r < nr; r += 4) {   // four independent rows per step
+            float z[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                z[i] = bo;
+#pragma unroll
+                for (int d = 0; d < 8; ++d)
+                    if (d < dx) z[i] += xs[min(r + i, nr - 1) * dx + d] * wr[d];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (r + i < nr) out[(long)(r + i) * w] = __float2bfloat16_rn(tanh_fast(z[i]));
         }
-        reinterpret_cast<uint32_t *>(A1 + (long)b * N * w)[(n * w + o) / 2] = pack_bf16(tanh_fast(z0), tanh_fast(z1));
     }
 }
 
@@ -399,44 +947,52 @@ struct FinalArgs {
     double half_inv_s2, inv_a2;
 };
 
+// grid (gradient blocks + 1, C): blocks 0..nb-1 gather one entry per thread, the last
+// block of each chain computes U (fixed-order sums).
 __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float *q, double *U, float *g)
 {
     __shared__ double sm[8];
-    const int b = blockIdx.x;
-    double pr = 0.0;
-    for (int j = threadIdx.x; j < a.k; j += blockDim.x) {
-        const float qj = q[(long)b * a.k + j];
-        pr += (double)qj * (double)qj;
-        const int kd = a.kind[j], off = a.off[j];
-        float s = 0.0f;
-        if (kd == E_HIDDEN_W) {
-            for (int t = 0; t < a.nsplit; ++t) s += a.gw_part[t * a.gw_split + (long)b * a.k + j];
-        } else if (kd == E_BIAS) {
-            const float *dp = a.db_part[a.layer[j]] + (long)b * a.ntiles * a.w + off;
-            for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w];
-        } else if (kd == E_W0) {
-            const float *dp = a.dw0_part + (long)b * a.ntiles * a.w * a.dx + off;
-            for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w * a.dx];
-        } else if (kd == E_WOUT) {
-            const float *dp = a.dwout_part + (long)b * a.ntiles * a.w + off;
-            for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w];
-        } else {
-            const float *dp = a.dbout_part + (long)b * a.ntiles;
-            for (int t = 0; t < a.ntiles; ++t) s += dp[t];
+    const int b = blockIdx.y;
+    if (blockIdx.x == gridDim.x - 1) {
+        double pr = 0.0;
+        for (int j = threadIdx.x; j < a.k; j += blockDim.x) {
+            const double qj = q[(long)b * a.k + j];
+            pr += qj * qj;
         }
-        if (g) g[(long)b * a.k + j] = s + qj * (float)a.inv_a2;
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, o);
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = pr;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < 8; ++i) t += sm[i];
-        double lik = 0.0;
-        for (int i = 0; i < a.ntiles; ++i) lik += a.u_part[(long)b * a.ntiles + i];
-        U[b] = lik * a.half_inv_s2 + 0.5 * t * a.inv_a2;
+        for (int o = 16; o > 0; o >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, o);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = pr;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int i = 0; i < 8; ++i) t += sm[i];
+            double lik = 0.0;
+            for (int i = 0; i < a.ntiles; ++i) lik += a.u_part[(long)b * a.ntiles + i];
+            U[b] = lik * a.half_inv_s2 + 0.5 * t * a.inv_a2;
+        }
+        return;
     }
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.k || !g) return;
+    const float qj = q[(long)b * a.k + j];
+    const int kd = a.kind[j], off = a.off[j];
+    float s = 0.0f;
+    if (kd == E_HIDDEN_W) {
+        for (int t = 0; t < a.nsplit; ++t) s += a.gw_part[t * a.gw_split + (long)b * a.k + j];
+    } else if (kd == E_BIAS) {
+        const float *dp = a.db_part[a.layer[j]] + (long)b * a.ntiles * a.w + off;
+        for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w];
+    } else if (kd == E_W0) {
+        const float *dp = a.dw0_part + (long)b * a.ntiles * a.w * a.dx + off;
+        for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w * a.dx];
+    } else if (kd == E_WOUT) {
+        const float *dp = a.dwout_part + (long)b * a.ntiles * a.w + off;
+        for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w];
+    } else {
+        const float *dp = a.dbout_part + (long)b * a.ntiles;
+        for (int t = 0; t < a.ntiles; ++t) s += dp[t];
+    }
+    g[(long)b * a.k + j] = s + qj * (float)a.inv_a2;
 }
 
 template <typename V>
@@ -520,6 +1076,78 @@ void launch_umma(const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &
     HMC_LAUNCH_CK();
 }
 
+template <int MODE, int WIDTH>
+void launch_layer_w(const CUtensorMap &a, const CUtensorMap &wh, const CUtensorMap &wl, const LayerParams &p, int ncta,
+                    cudaStream_t s)
+{
+    static bool configured = false;
+    if (!configured) {
+        HMC_CK(cudaFuncSetAttribute(k_layer<MODE, WIDTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, L_SMEM));
+        configured = true;
+    }
+    static const char *names[] = {"layer_fwd_tanh", "layer_fwd_out", "layer_bwd_tanh", "layer_bwd_first"};
+    ProfScope ps(names[MODE], s);
+    k_layer<MODE, WIDTH><<<ncta, NTHREADS, L_SMEM, s>>>(a, wh, wl, p);
+    HMC_LAUNCH_CK();
+}
+
+template <int MODE>
+void launch_layer(const CUtensorMap &a, const CUtensorMap &wh, const CUtensorMap &wl, const LayerParams &p, int ncta,
+                  cudaStream_t s)
+{
+    if (p.W == 256) launch_layer_w<MODE, 256>(a, wh, wl, p, ncta, s);
+    else launch_layer_w<MODE, 128>(a, wh, wl, p, ncta, s);
+}
+
+template <int MODE, int WIDTH>
+void launch_layer_solo_w(const CUtensorMap &a, const CUtensorMap &wh, const LayerParams &p, int ncta, cudaStream_t s)
+{
+    static bool configured = false;
+    if (!configured) {
+        HMC_CK(cudaFuncSetAttribute(k_layer_solo<MODE, WIDTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, L_SMEM));
+        configured = true;
+    }
+    static const char *names[] = {"solo_fwd_tanh", "solo_fwd_out", "solo_bwd_tanh", "solo_bwd_first"};
+    ProfScope ps(names[MODE], s);
+    k_layer_solo<MODE, WIDTH><<<ncta, NTHREADS, L_SMEM, s>>>(a, wh, wh, p);
+    HMC_LAUNCH_CK();
+}
+
+template <int MODE>
+void launch_layer_solo(const CUtensorMap &a, const CUtensorMap &wh, const LayerParams &p, int ncta, cudaStream_t s)
+{
+    if (p.W == 256) launch_layer_solo_w<MODE, 256>(a, wh, p, ncta, s);
+    else launch_layer_solo_w<MODE, 128>(a, wh, p, ncta, s);
+}
+
+void launch_dw2(const CUtensorMap &d, const CUtensorMap &a, const Params &p, dim3 grid, cudaStream_t s)
+{
+    static bool configured = false;
+    if (!configured) {
+        HMC_CK(cudaFuncSetAttribute(k_dw2, cudaFuncAttributeMaxDynamicSharedMemorySize, DW_SMEM));
+        configured = true;
+    }
+    ProfScope ps("dw2", s);
+    k_dw2<<<grid, NTHREADS, DW_SMEM, s>>>(d, a, p);
+    HMC_LAUNCH_CK();
+}
+
+// How many two-CTA clusters of the layer kernel can be resident at once.
+int layer_max_clusters()
+{
+    HMC_CK(cudaFuncSetAttribute(k_layer<L_FWD_OUT, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, L_SMEM));
+    int dev = 0, sms = 0;
+    HMC_CK(cudaGetDevice(&dev));
+    HMC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (sms / 2), 1, 1);
+    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = L_SMEM;
+    int n = 0;
+    HMC_CK(cudaOccupancyMaxActiveClusters(&n, k_layer<L_FWD_OUT, 256>, &cfg));
+    return std::max(1, std::min(n, sms / 2));
+}
+
 int pick_splits(int total_kb, int ctas_without_split, int target)
 {
     int s = std::max(1, target / std::max(1, ctas_without_split));
@@ -598,10 +1226,14 @@ class UmmaEngine final : public Engine {
         // split of the weight-gradient GEMMs over rows: about two CTAs per SM
         const int total_kb = (int)((N_ + BK - 1) / BK);
         nsplit_ = pick_splits(total_kb, ((w_ + BM - 1) / BM) * C, 2 * num_sms_);
+        nsplit2_ = pick_splits(total_kb, C, num_sms_);
+        nsplit_ = std::max(nsplit_, nsplit2_);
         gw_part_.alloc(sizeof(float) * nsplit_ * C * std::max<long>(k_, 1));
         HMC_CK(cudaMemset(gw_part_.ptr, 0, gw_part_.n));
 
         // tensor maps
+        use_layer_ = (w_ == 128 || w_ == 256);
+        if (use_layer_) max_clusters_ = layer_max_clusters();
         for (int i = 1; i <= L_ - 2; ++i) {
             A_row_[i] = make_map(A_[i]->ptr, w_, N_, C, 64, 128);
             A_atom_[i] = make_map(A_[i]->ptr, w_, N_, C, 64, 64);
@@ -609,6 +1241,10 @@ class UmmaEngine final : public Engine {
             W_atom_[i] = make_map(Wh_[i - 1]->ptr, w_, w_, C, 64, 64);
             W_fwd_lo_[i] = make_map(Wl_[i - 1]->ptr, w_, w_, C, 64, w_);
             W_atom_lo_[i] = make_map(Wl_[i - 1]->ptr, w_, w_, C, 64, 64);
+            if (use_layer_) {
+                W_half_hi_[i] = make_map(Wh_[i - 1]->ptr, w_, w_, C, 64, w_ / 2);
+                W_half_lo_[i] = make_map(Wl_[i - 1]->ptr, w_, w_, C, 64, w_ / 2);
+            }
         }
         for (int i = 2; i <= L_ - 1; ++i) {
             D_row_[i] = make_map(D_[i]->ptr, w_, N_, C, 64, 128);
@@ -643,13 +1279,15 @@ class UmmaEngine final : public Engine {
         const dim3 row_grid(ntiles_, 1, C_);
         // first layer
         {
-            const long total = N_ * (long)(w_ / 2);
-            dim3 grid((unsigned)std::min<long>((total + 255) / 256, 4 * num_sms_), C_);
+            dim3 grid((unsigned)ntiles_, C_);
             ProfScope ps("first_fwd", s);
-            k_first_fwd<<<grid, 256, 0, s>>>(x_.as<float>(), dx_, N_, w_, W0_.as<float>(), b0_.as<float>(),
+            k_first_fwd<<<grid, 256, 0, s>>>(x_.as<float>(), dx_, (int)N_, w_, W0_.as<float>(), b0_.as<float>(),
                                              A_[1]->as<__nv_bfloat16>());
             HMC_LAUNCH_CK();
         }
+        if (use_layer_) {
+            layers_persistent(s);
+        } else {
         // hidden layers i = 1..L-3 (tanh), then layer L-2 fused with the output layer
         for (int i = 1; i <= L_ - 2; ++i) {
             Params pp = base;
@@ -700,6 +1338,7 @@ class UmmaEngine final : public Engine {
                 launch_umma<M_BWD_FIRST, false, true, true>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], pp, row_grid, s);
             }
         }
+        }
         // weight gradients of the hidden layers at the sampled entries
         for (int i = 1; i <= L_ - 2; ++i) {
             if (layer_entries_[i] == 0) continue;
@@ -712,12 +1351,19 @@ class UmmaEngine final : public Engine {
             pp.rowptr = rowptr_[i]->as<int>();
             pp.ecol = ecol_.as<int>();
             pp.erow = erow_.as<int>();
+            pp.epack = epack_.as<int>();
             pp.gw_part = gw_part_.as<float>();
             pp.gw_split = (long)C_ * k_;
             pp.gw_b = k_;
-            const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
-            dim3 grid((w_ + BM - 1) / BM, splits, C_);
-            launch_umma<M_DW, true, true, false>(D_atom_[i + 1], A_atom_[i], A_atom_[i], pp, grid, s);
+            if (use_layer_) {
+                pp.kb_per_split = (total_kb + nsplit2_ - 1) / nsplit2_;
+                const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
+                launch_dw2(D_atom_[i + 1], A_atom_[i], pp, dim3(1, splits, C_), s);
+            } else {
+                const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
+                dim3 grid((w_ + BM - 1) / BM, splits, C_);
+                launch_umma<M_DW, true, true, false>(D_atom_[i + 1], A_atom_[i], A_atom_[i], pp, grid, s);
+            }
         }
         FinalArgs fa{};
         fa.k = (int)k_;
@@ -739,16 +1385,72 @@ class UmmaEngine final : public Engine {
         fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
         {
             ProfScope ps("finalize", s);
-            k_finalize_bf16<<<C_, 256, 0, s>>>(fa, q, U, g);
+            dim3 grid((unsigned)((k_ + 255) / 256 + 1), C_);
+            k_finalize_bf16<<<grid, 256, 0, s>>>(fa, q, U, g);
             HMC_LAUNCH_CK();
         }
     }
 
   private:
+    // forward and reverse hidden layers on the persistent cluster kernel
+    void layers_persistent(cudaStream_t s)
+    {
+        const NetDesc &nd = p_.net;
+        LayerParams base{};
+        base.N = (int)N_;
+        base.W = w_;
+        base.C = C_;
+        base.ntiles = ntiles_;
+        base.dx = dx_;
+        base.err = err_;
+        const long U = (long)C_ * ntiles_;
+        const int ncta = 2 * (int)std::min<long>(max_clusters_, U);
+        for (int i = 1; i <= L_ - 2; ++i) {
+            LayerParams lp = base;
+            lp.bias = bh_[i - 1]->as<float>();
+            if (i < L_ - 2) {
+                lp.out = A_[i + 1]->as<__nv_bfloat16>();
+                launch_layer<L_FWD_TANH>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
+            } else {
+                lp.out = D_[L_ - 1]->as<__nv_bfloat16>();
+                lp.wout = wout_.as<float>();
+                lp.bout = bout_.as<float>();
+                lp.y = y_.as<float>();
+                lp.inv_s2 = (float)(1.0 / (p_.sigma * p_.sigma));
+                lp.u_part = u_part_.as<double>();
+                lp.dbout_part = dbout_part_.as<float>();
+                lp.dwout_part = dwout_part_.as<float>();
+                lp.db_part = db_part_[L_ - 2]->as<float>();
+                launch_layer<L_FWD_OUT>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
+            }
+        }
+        // reverse pass: one CTA per SM holds the whole bf16 W (the lo part is not needed there)
+        const int nsolo = (int)std::min<long>(num_sms_, U);
+        for (int i = L_ - 2; i >= 1; --i) {
+            if (i <= nd.lmin) break;
+            LayerParams lp = base;
+            lp.aux = A_[i]->as<__nv_bfloat16>();
+            lp.db_part = db_part_[i - 1]->as<float>();
+            if (i > 1) {
+                lp.out = D_[i]->as<__nv_bfloat16>();
+                launch_layer_solo<L_BWD_TANH>(D_row_[i + 1], W_atom_[i], lp, nsolo, s);
+            } else if (dx_ <= 4) {
+                lp.x = x_.as<float>();
+                lp.dw0_part = dw0_part_.as<float>();
+                launch_layer_solo<L_BWD_FIRST>(D_row_[i + 1], W_atom_[i], lp, nsolo, s);
+            } else {
+                lp.x = x_.as<float>();
+                lp.dw0_part = dw0_part_.as<float>();
+                launch_layer<L_BWD_FIRST>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], lp, ncta, s);
+            }
+        }
+    }
+
     int nsplit_eff() const
     {
         const int total_kb = (int)((N_ + BK - 1) / BK);
-        const int per = (total_kb + nsplit_ - 1) / nsplit_;
+        const int ns = use_layer_ ? nsplit2_ : nsplit_;
+        const int per = (total_kb + ns - 1) / ns;
         return (total_kb + per - 1) / per;
     }
 
@@ -854,6 +1556,9 @@ class UmmaEngine final : public Engine {
         up(off_, off);
         up(erow_, erow);
         up(ecol_, ecol);
+        std::vector<int> epack(k_);
+        for (long j = 0; j < k_; ++j) epack[j] = (erow[j] << 16) | ecol[j];
+        up(epack_, epack);
         up(sc_off_, boff);
         std::vector<uint8_t> b8(bid.begin(), bid.end());
         sc_bid_.alloc(std::max<size_t>(b8.size(), 1));
@@ -863,15 +1568,17 @@ class UmmaEngine final : public Engine {
     }
 
     Problem &p_;
-    int C_, L_ = 0, w_ = 0, dx_ = 0, ntiles_ = 1, nsplit_ = 1, num_sms_ = 148;
+    int C_, L_ = 0, w_ = 0, dx_ = 0, ntiles_ = 1, nsplit_ = 1, nsplit2_ = 1, num_sms_ = 148;
     long N_ = 0, k_ = 0;
     int *err_ = nullptr;
     DevBuf x_, y_, W0_, b0_, wout_, bout_, u_part_, dbout_part_, dwout_part_, dw0_part_, db_ptrs_, gw_part_;
-    DevBuf kind_, layer_, off_, erow_, ecol_, sc_off_, sc_bid_;
+    DevBuf kind_, layer_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_;
     std::vector<std::unique_ptr<DevBuf>> Wh_, Wl_, bh_, A_, D_, db_part_, rowptr_;
     std::vector<int> layer_entries_;
     CUtensorMap A_row_[MAXL], A_atom_[MAXL], W_fwd_[MAXL], W_atom_[MAXL], W_fwd_lo_[MAXL], W_atom_lo_[MAXL];
-    CUtensorMap D_row_[MAXL], D_atom_[MAXL];
+    CUtensorMap D_row_[MAXL], D_atom_[MAXL], W_half_hi_[MAXL], W_half_lo_[MAXL];
+    bool use_layer_ = false;
+    int max_clusters_ = 1;
     ScatterPlan plan_;
 };
 

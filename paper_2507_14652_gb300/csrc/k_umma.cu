@@ -377,7 +377,8 @@ constexpr int L_A_BYTES = BM * BK * 2;                  // one 16 KB K-block of 
 constexpr int L_W_HALF = 64 * 1024;                     // resident half of W, hi or lo (4 K-blocks x 16 KB)
 constexpr int L_RED_FLOATS = 5 * 4 * 256;               // [1 + dx][4 warps][columns]: dx <= 8 at 128 columns, dx <= 4 at 256
 constexpr int L_SMEM = 1024 + 2 * L_W_HALF + L_STAGES * L_A_BYTES + 256 + L_RED_FLOATS * 4 + 2 * 128 * 4 + 64 + 64 +
-                       2 * 256 * 4;                      // + bias and output weights of the current chain
+                       2 * 256 * 4 + 2 * 128 * 4;        // + bias and output weights of the chain, half-row sums
+constexpr int L_THREADS = 320;                          // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 
 struct LayerParams {
     int N, W, C, ntiles, dx;
@@ -406,7 +407,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
     constexpr bool BWD = (MODE == L_BWD_TANH || MODE == L_BWD_FIRST);
     constexpr int LN = CLUSTER ? WIDTH / 2 : WIDTH;    // output columns of this CTA
     constexpr int NKB = WIDTH / 64;                    // K-blocks of the reduction
-    constexpr int NCH = LN / 32;                       // 32-column chunks of a row
+    constexpr int NCH = LN / 64;                       // 32-column chunks of one epilogue warp's half row
     constexpr int SLOT = CLUSTER ? 128 : 256;          // TMEM columns per accumulator
     constexpr int TCOLS = 2 * SLOT;
     constexpr int kblk = LN * 128;                     // bytes of one resident K-block
@@ -442,7 +443,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
         mbar_init(w_empty, 1);
         for (int s = 0; s < 2; ++s) {
             mbar_init(acc_full0 + 8 * s, 1);
-            mbar_init(acc_empty0 + 8 * s, 128);
+            mbar_init(acc_empty0 + 8 * s, 256);
         }
         mbar_init(xbar, 128);
         fence_mbar_init();
@@ -551,10 +552,14 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
             }
         }
     } else {
-        // ---------------- epilogue warps 2..5, one tile row per thread ----------------
-        const int q = warp & 3, row = 32 * q + lane, et = threadIdx.x - 64;
+        // ---------------- epilogue warps 2..9: two per lane quadrant ----------------
+        // warp e = warp - 2 owns rows 32 q .. 32 q + 31 (q = warp mod 4, the TMEM lanes it
+        // may read) and the half row h = e / 4 of this CTA's columns.
+        const int q = warp & 3, row = 32 * q + lane, et = threadIdx.x - 64, h = (warp - 2) >> 2;
         const uint32_t lane_off = (uint32_t)(32 * q) << 16;
         const int col0 = (int)rank * LN;
+        const int hc0 = h * (LN / 2);          // first column (within this CTA) of this warp's half
+        float *fsum = sbias + 512;             // [2][128] half-row partial dot products
         int it = 0, chain_loaded = -1;
         for (long u = u0; u < u1; ++u, ++it) {
             const int c = (int)(u / p.ntiles), t = (int)(u % p.ntiles);
@@ -566,9 +571,13 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
             // global loads of this tile, issued before the accumulator wait
             uint4 ap[BWD ? NCH * 4 : 1];
             if (BWD) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(p.aux + rowoff);
+                const uint4 *src = reinterpret_cast<const uint4 *>(p.aux + rowoff + hc0);
 #pragma unroll
-                for (int i = 0; i < NCH * 4; ++i) ap[i] = valid ? src[i] : make_uint4(0u, 0u, 0u, 0u);
+                for (int i = 0; i < NCH * 4; ++i) ap[i] = make_uint4(0u, 0u, 0u, 0u);
+                if (valid) {
+#pragma unroll
+                    for (int i = 0; i < NCH * 4; ++i) ap[i] = src[i];
+                }
             }
             const float yv = (MODE == L_FWD_OUT && valid) ? p.y[m] : 0.0f;
             float xv[8];
@@ -577,41 +586,50 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                 xv[d] = (MODE == L_BWD_FIRST && valid && d < p.dx) ? p.x[(long)m * p.dx + d] : 0.0f;
             // per-chain constants into shared memory
             if (!BWD && c != chain_loaded) {
-                named_bar_sync(1, 128);
-                for (int i = et; i < LN; i += 128) {
+                named_bar_sync(1, 256);
+                for (int i = et; i < LN; i += 256) {
                     sbias[i] = p.bias[(long)c * p.W + col0 + i];
                     if (MODE == L_FWD_OUT) swo[i] = p.wout[(long)c * p.W + col0 + i];
                 }
-                named_bar_sync(1, 128);
+                named_bar_sync(1, 256);
                 chain_loaded = c;
             }
             if (!mbar_wait(acc_full0 + 8 * slot, (uint32_t)(it >> 1) & 1u, p.err)) break;
             tc_fence_after();
-            const uint32_t taddr = tmem + lane_off + (uint32_t)(slot * SLOT);
+            const uint32_t taddr = tmem + lane_off + (uint32_t)(slot * SLOT + hc0);
             bool ok = true;
+            uint32_t rb[2][32];
             if (MODE == L_FWD_TANH) {
+                tmem_ld32_issue(taddr, rb[0]);
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
                     const int c0 = 32 * ch;
+                    tmem_ld_wait(rb[ch & 1]);
+                    if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
                     float v[32];
-                    tmem_ld32(taddr + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rb[ch & 1][j]);
                     if (valid) {
                         uint32_t pk[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j)
-                            pk[j] = pack_bf16(tanh_fast(v[2 * j] + sbias[c0 + 2 * j]),
-                                              tanh_fast(v[2 * j + 1] + sbias[c0 + 2 * j + 1]));
-                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + c0);
+                            pk[j] = pack_bf16(tanh_fast(v[2 * j] + sbias[hc0 + c0 + 2 * j]),
+                                              tanh_fast(v[2 * j + 1] + sbias[hc0 + c0 + 2 * j + 1]));
+                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + hc0 + c0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
                     }
                 }
             } else if (BWD) {
+                tmem_ld32_issue(taddr, rb[0]);
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
                     const int c0 = 32 * ch;
                     float v[32], dd[32];
-                    tmem_ld32(taddr + c0, v);
+                    tmem_ld_wait(rb[ch & 1]);
+                    if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rb[ch & 1][j]);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const uint4 uu = ap[4 * ch + j];
@@ -627,7 +645,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                         uint32_t pk[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
-                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + c0);
+                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + hc0 + c0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
                     }
@@ -636,13 +654,13 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                             float tv[32];
 #pragma unroll
                             for (int j = 0; j < 32; ++j) tv[j] = dd[j] * xv[d];
-                            red[((1 + d) * 4 + q) * LN + c0 + lane] = reduce_scatter32(tv);
+                            red[((1 + d) * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(tv);
                         }
                     }
-                    red[(0 * 4 + q) * LN + c0 + lane] = reduce_scatter32(dd);
+                    red[(0 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dd);
                 }
-                named_bar_sync(1, 128);
-                for (int cc = et; cc < LN; cc += 128) {
+                named_bar_sync(1, 256);
+                for (int cc = et; cc < LN; cc += 256) {
                     p.db_part[part + cc] = red[(0 * 4 + 0) * LN + cc] + red[(0 * 4 + 1) * LN + cc] +
                                            red[(0 * 4 + 2) * LN + cc] + red[(0 * 4 + 3) * LN + cc];
                     if (MODE == L_BWD_FIRST)
@@ -651,23 +669,31 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                                 red[((1 + d) * 4 + 0) * LN + cc] + red[((1 + d) * 4 + 1) * LN + cc] +
                                 red[((1 + d) * 4 + 2) * LN + cc] + red[((1 + d) * 4 + 3) * LN + cc];
                 }
-                named_bar_sync(1, 128);
+                named_bar_sync(1, 256);
             } else if (MODE == L_FWD_OUT) {
-                float f = 0.0f;
+                float fh = 0.0f;
+                tmem_ld32_issue(taddr, rb[0]);
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
                     const int c0 = 32 * ch;
-                    float v[32];
-                    tmem_ld32(taddr + c0, v);
+                    tmem_ld_wait(rb[ch & 1]);
+                    if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) f += tanh_fast(v[j] + sbias[c0 + j]) * swo[c0 + j];
+                    for (int j = 0; j < 32; ++j)
+                        fh += tanh_fast(__uint_as_float(rb[ch & 1][j]) + sbias[hc0 + c0 + j]) * swo[hc0 + c0 + j];
                 }
+                // this CTA's partial dot product: both halves of the row, in a fixed order
+                fsum[h * 128 + row] = fh;
+                named_bar_sync(1, 256);
+                const float f = fsum[row] + fsum[128 + row];
                 float fp = 0.0f;
-                if (CLUSTER) {   // swap partial dot products with the peer CTA
+                if (CLUSTER) {   // swap partial dot products with the peer CTA (one arrival per row)
                     const int xb = it & 1;
-                    const uint32_t mine = smem_u32(xchg + xb * 128 + row);
-                    st_cluster_f32(mapa_shared(mine, rank ^ 1u), f);
-                    mbar_arrive_cluster(mapa_shared(xbar, rank ^ 1u));
+                    if (h == 0) {
+                        const uint32_t mine = smem_u32(xchg + xb * 128 + row);
+                        st_cluster_f32(mapa_shared(mine, rank ^ 1u), f);
+                        mbar_arrive_cluster(mapa_shared(xbar, rank ^ 1u));
+                    }
                     ok = mbar_wait_cluster(xbar, (uint32_t)it & 1u, p.err);
                     fp = xchg[xb * 128 + row];
                 }
@@ -675,7 +701,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                 const float fo = (p.bout[c] + f0) + f1;
                 const float r = valid ? fo - yv : 0.0f;
                 const float d = r * p.inv_s2;
-                if (rank == 0) {
+                if (rank == 0 && h == 0) {
                     double r2 = (double)r * (double)r;
                     float ds = d;
 #pragma unroll
@@ -688,30 +714,34 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                         fred[q] = ds;
                     }
                 }
+                tmem_ld32_issue(taddr, rb[0]);
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
                     const int c0 = 32 * ch;
                     float v[32], dw[32], dd[32];
-                    tmem_ld32(taddr + c0, v);
+                    tmem_ld_wait(rb[ch & 1]);
+                    if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rb[ch & 1][j]);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const float a = tanh_fast(v[j] + sbias[c0 + j]);
+                        const float a = tanh_fast(v[j] + sbias[hc0 + c0 + j]);
                         dw[j] = d * a;
-                        dd[j] = d * swo[c0 + j] * (1.0f - a * a);
+                        dd[j] = d * swo[hc0 + c0 + j] * (1.0f - a * a);
                     }
                     if (valid) {
                         uint32_t pk[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
-                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + c0);
+                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + hc0 + c0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
                     }
-                    red[(0 * 4 + q) * LN + c0 + lane] = reduce_scatter32(dw);
-                    red[(1 * 4 + q) * LN + c0 + lane] = reduce_scatter32(dd);
+                    red[(0 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dw);
+                    red[(1 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dd);
                 }
-                named_bar_sync(1, 128);
-                for (int cc = et; cc < LN; cc += 128) {
+                named_bar_sync(1, 256);
+                for (int cc = et; cc < LN; cc += 256) {
                     p.dwout_part[part + cc] = red[(0 * 4 + 0) * LN + cc] + red[(0 * 4 + 1) * LN + cc] +
                                               red[(0 * 4 + 2) * LN + cc] + red[(0 * 4 + 3) * LN + cc];
                     p.db_part[part + cc] = red[(1 * 4 + 0) * LN + cc] + red[(1 * 4 + 1) * LN + cc] +
@@ -721,7 +751,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     p.u_part[(long)c * p.ntiles + t] = dred[0] + dred[1] + dred[2] + dred[3];
                     p.dbout_part[(long)c * p.ntiles + t] = fred[0] + fred[1] + fred[2] + fred[3];
                 }
-                named_bar_sync(1, 128);
+                named_bar_sync(1, 256);
             }
             tc_fence_before();
             mbar_arrive(acc_empty0 + 8 * slot);
@@ -738,7 +768,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
 }
 
 template <int MODE, int WIDTH>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(L_THREADS, 1)
     k_layer(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmWh,
             const __grid_constant__ CUtensorMap tmWl, const LayerParams p)
 {
@@ -746,7 +776,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
 }
 
 template <int MODE, int WIDTH>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(L_THREADS, 1)
     k_layer_solo(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmWh,
                  const __grid_constant__ CUtensorMap tmWl, const LayerParams p)
 {
@@ -1087,7 +1117,7 @@ void launch_layer_w(const CUtensorMap &a, const CUtensorMap &wh, const CUtensorM
     }
     static const char *names[] = {"layer_fwd_tanh", "layer_fwd_out", "layer_bwd_tanh", "layer_bwd_first"};
     ProfScope ps(names[MODE], s);
-    k_layer<MODE, WIDTH><<<ncta, NTHREADS, L_SMEM, s>>>(a, wh, wl, p);
+    k_layer<MODE, WIDTH><<<ncta, L_THREADS, L_SMEM, s>>>(a, wh, wl, p);
     HMC_LAUNCH_CK();
 }
 
@@ -1109,7 +1139,7 @@ void launch_layer_solo_w(const CUtensorMap &a, const CUtensorMap &wh, const Laye
     }
     static const char *names[] = {"solo_fwd_tanh", "solo_fwd_out", "solo_bwd_tanh", "solo_bwd_first"};
     ProfScope ps(names[MODE], s);
-    k_layer_solo<MODE, WIDTH><<<ncta, NTHREADS, L_SMEM, s>>>(a, wh, wh, p);
+    k_layer_solo<MODE, WIDTH><<<ncta, L_THREADS, L_SMEM, s>>>(a, wh, wh, p);
     HMC_LAUNCH_CK();
 }
 
@@ -1141,7 +1171,7 @@ int layer_max_clusters()
     HMC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * (sms / 2), 1, 1);
-    cfg.blockDim = dim3(NTHREADS, 1, 1);
+    cfg.blockDim = dim3(L_THREADS, 1, 1);
     cfg.dynamicSmemBytes = L_SMEM;
     int n = 0;
     HMC_CK(cudaOccupancyMaxActiveClusters(&n, k_layer<L_FWD_OUT, 256>, &cfg));

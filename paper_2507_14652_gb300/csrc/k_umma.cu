@@ -362,23 +362,32 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
 // ---------------------------------------------------------------------------
 // Persistent layer kernel for the w x w hidden layers (w = 128 or 256).
 //
-// A cluster of two CTAs walks a contiguous range of (chain, 128-row tile) units;
-// CTA r owns output columns [r w/2, (r+1) w/2).  Its half of W (bf16 hi and lo,
-// all K) stays resident in shared memory while the chain does not change; the
-// A operand (activations or deltas) streams through a 4-stage ring of 16 KB
-// K-blocks.  Two TMEM accumulators alternate so the epilogue of one tile runs
-// while the MMAs of the next one are in flight.  The output-layer epilogue needs
-// whole rows: the two CTAs swap their partial dot products through distributed
-// shared memory, guarded by an mbarrier in each CTA.
+// A cluster of two CTAs acts as one M = 256 tensor-core unit (tcgen05
+// .cta_group::2).  Each CTA streams its own 128-row tile of the A operand
+// (activations or deltas) through a 4-stage ring of 16 KB K-blocks and keeps half
+// of W (its w/2 rows of the B operand, bf16 hi and lo, all K) resident while the
+// chain does not change; the even CTA issues every MMA and both receive whole
+// 128 x w rows of the product in their own tensor memory.  Loads of either CTA
+// complete on the even CTA's barriers; MMA completions are multicast to both.
+// Two TMEM accumulators alternate so the epilogue of one tile runs while the MMAs
+// of the next one are in flight.
+//
+// Epilogue: each warp owns 32 rows (its TMEM lane quadrant) and half of the
+// columns.  Row-per-thread values pass through a 2 KB swizzled staging buffer per
+// warp, so global loads and stores move 8 rows x 64 contiguous bytes per
+// instruction instead of 32 scattered 16-byte pieces.
 // ---------------------------------------------------------------------------
 enum LMode { L_FWD_TANH = 0, L_FWD_OUT = 1, L_BWD_TANH = 2, L_BWD_FIRST = 3 };
 constexpr int L_STAGES = 4;
 constexpr int L_A_BYTES = BM * BK * 2;                  // one 16 KB K-block of a 128-row tile
 constexpr int L_W_HALF = 64 * 1024;                     // resident half of W, hi or lo (4 K-blocks x 16 KB)
-constexpr int L_RED_FLOATS = 5 * 4 * 256;               // [1 + dx][4 warps][columns]: dx <= 8 at 128 columns, dx <= 4 at 256
-constexpr int L_SMEM = 1024 + 2 * L_W_HALF + L_STAGES * L_A_BYTES + 256 + L_RED_FLOATS * 4 + 2 * 128 * 4 + 64 + 64 +
+constexpr int L_STG = 2048;                             // staging bytes per epilogue warp (32 rows x 64 B)
+constexpr int L_SCR_FLOATS = 2 * 4 * 256 + 8 * L_STG / 4;   // forward: [2][4][w] column sums + staging
+constexpr int L_BWD_STG_OFF = 9 * 4 * 256 * 4;          // reverse: [1 + dx][4][w] sums (dx <= 8) in the free lo region, then staging
+constexpr int L_SMEM = 1024 + 2 * L_W_HALF + L_STAGES * L_A_BYTES + 256 + L_SCR_FLOATS * 4 + 64 + 64 +
                        2 * 256 * 4 + 2 * 128 * 4;        // + bias and output weights of the chain, half-row sums
 constexpr int L_THREADS = 320;                          // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+static_assert(L_BWD_STG_OFF + 8 * L_STG <= L_W_HALF, "reverse-pass scratch fits the lo region");
 
 struct LayerParams {
     int N, W, C, ntiles, dx;
@@ -395,22 +404,28 @@ struct LayerParams {
     float *dw0_part;               // [c][tiles][W][dx]
 };
 
-// CLUSTER: two CTAs split the output columns (forward, with the hi/lo weights).
-// Otherwise one CTA computes all columns of its tiles with a single bf16 W resident
-// (the reverse pass, which does not need the lo part).  WIDTH = w (128 or 256).
-// The epilogue issues a tile's global loads (slopes, targets) before it waits for
-// the accumulator, so their latency overlaps the tile's MMAs.
-template <int MODE, bool CLUSTER, bool WSPLIT, int WIDTH>
+// byte offset of 16-byte piece j (0..3) of row r (0..31) in a warp's staging buffer;
+// the XOR spreads both row-wise and 8-row-block accesses over all banks
+__device__ __forceinline__ uint32_t stg_off(int r, int j) { return (uint32_t)(r * 64 + ((j ^ ((r >> 1) & 3)) << 4)); }
+
+// Units: a unit is (chain, pair of consecutive tiles); CTA r takes tile 2 j + r.
+// WSPLIT adds the lo part of W (forward).  The epilogue issues a tile's global
+// loads (slopes, targets) before it waits for the accumulator, so their latency
+// overlaps the tile's MMAs.
+template <int MODE, bool WSPLIT, int WIDTH>
 __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtensorMap &tmWh, const CUtensorMap &tmWl,
                                            const LayerParams &p)
 {
     constexpr bool BWD = (MODE == L_BWD_TANH || MODE == L_BWD_FIRST);
-    constexpr int LN = CLUSTER ? WIDTH / 2 : WIDTH;    // output columns of this CTA
+    constexpr int LN = WIDTH;                          // accumulator columns: whole rows
+    constexpr int BN = WIDTH / 2;                      // rows of B (W) resident in this CTA
     constexpr int NKB = WIDTH / 64;                    // K-blocks of the reduction
     constexpr int NCH = LN / 64;                       // 32-column chunks of one epilogue warp's half row
-    constexpr int SLOT = CLUSTER ? 128 : 256;          // TMEM columns per accumulator
+    constexpr int SLOT = LN;                           // TMEM columns per accumulator
     constexpr int TCOLS = 2 * SLOT;
-    constexpr int kblk = LN * 128;                     // bytes of one resident K-block
+    constexpr int kblk = BN * 128;                     // bytes of one resident K-block of W
+    static_assert(NKB * kblk <= L_W_HALF, "resident half of W");
+    static_assert(!(BWD && WSPLIT), "the reverse pass keeps its scratch in the lo region");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sWh = smem;
@@ -418,21 +433,25 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
     uint8_t *sA = smem + 2 * L_W_HALF;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sA + L_STAGES * L_A_BYTES);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * L_STAGES + 7);
-    float *red = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(bars) + 256);
-    float *xchg = red + L_RED_FLOATS;                          // [2][128] partial dot products from the peer
-    double *dred = reinterpret_cast<double *>(xchg + 256);     // [4]
-    float *fred = reinterpret_cast<float *>(dred + 4);         // [4]
-    float *sbias = fred + 16;                                  // [256] bias of the current chain
-    float *swo = sbias + 256;                                  // [256] output weights of the current chain
+    float *scr = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(bars) + 256);
+    float *red = BWD ? reinterpret_cast<float *>(sWl) : scr;                          // column sums
+    uint8_t *stage0 = BWD ? sWl + L_BWD_STG_OFF : reinterpret_cast<uint8_t *>(scr + 2 * 4 * 256);
+    double *dred = reinterpret_cast<double *>(scr + L_SCR_FLOATS);   // [4]
+    float *fred = reinterpret_cast<float *>(dred + 4);               // [4]
+    float *sbias = fred + 16;                                        // [256] bias of the current chain
+    float *swo = sbias + 256;                                        // [256] output weights of the current chain
+    float *fsum = swo + 256;                                         // [2][128] half-row partial dot products
     const uint32_t a_full0 = smem_u32(bars), a_empty0 = a_full0 + 8 * L_STAGES;
     const uint32_t w_full = a_empty0 + 8 * L_STAGES, w_empty = w_full + 8;
-    const uint32_t acc_full0 = w_empty + 8, acc_empty0 = acc_full0 + 16, xbar = acc_empty0 + 16;
+    const uint32_t acc_full0 = w_empty + 8, acc_empty0 = acc_full0 + 16;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = CLUSTER ? cluster_ctarank() : 0u;
-    const long U = (long)p.C * p.ntiles;
-    const int ncl = CLUSTER ? gridDim.x / 2 : gridDim.x, ci = CLUSTER ? blockIdx.x / 2 : blockIdx.x;
-    const long u0 = U * ci / ncl, u1 = U * (ci + 1) / ncl;
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = rank == 0;
+    const int tpg = (p.ntiles + 1) / 2;                // tile pairs per chain
+    const long U = (long)p.C * tpg;
+    const int ngr = gridDim.x / 2, gi = blockIdx.x / 2;
+    const long u0 = U * gi / ngr, u1 = U * (gi + 1) / ngr;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < L_STAGES; ++s) {
@@ -443,49 +462,49 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
         mbar_init(w_empty, 1);
         for (int s = 0; s < 2; ++s) {
             mbar_init(acc_full0 + 8 * s, 1);
-            mbar_init(acc_empty0 + 8 * s, 256);
+            mbar_init(acc_empty0 + 8 * s, 16);   // one arrival per epilogue warp of the pair
         }
-        mbar_init(xbar, 128);
         fence_mbar_init();
         prefetch_map(&tmA);
         prefetch_map(&tmWh);
         if (WSPLIT) prefetch_map(&tmWl);
     }
     if (warp == 1) {
-        tmem_alloc(smem_u32(tmem_slot), TCOLS);
-        tmem_relinquish();
+        tmem_alloc2(smem_u32(tmem_slot), TCOLS);
+        tmem_relinquish2();
     }
     tc_fence_before();
     __syncthreads();
-    if (CLUSTER) cluster_sync_all();   // the peer's barriers exist before anyone arrives on them
+    cluster_sync_all();   // the leader's barriers exist before the peer signals them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // barriers that count loads and epilogue releases live in the leader CTA
+    const uint32_t lead_a_full0 = mapa_shared(a_full0, 0);
+    const uint32_t lead_w_full = mapa_shared(w_full, 0);
+    const uint32_t lead_acc_empty0 = mapa_shared(acc_empty0, 0);
 
     if (warp == 0) {
-        if (lane == 0) {   // TMA producer
+        if (lane == 0) {   // TMA producer (both CTAs)
             int cur_c = -1;
             uint32_t wph = 0;
             long kbi = 0;
             bool ok = true, w_pending = false;
             for (long u = u0; u < u1 && ok; ++u) {
-                const int c = (int)(u / p.ntiles), t = (int)(u % p.ntiles);
+                const int c = (int)(u / tpg), t = (int)(u % tpg) * 2 + (int)rank;
                 if (c != cur_c) {
                     if (cur_c >= 0) {
                         if (!mbar_wait(w_empty, wph, p.err)) { ok = false; break; }
                         wph ^= 1u;
                     }
-                    mbar_expect_tx(w_full, (WSPLIT ? 2u : 1u) * NKB * kblk);
+                    if (leader) mbar_expect_tx(w_full, 2u * (WSPLIT ? 2u : 1u) * NKB * kblk);
                     for (int kb = 0; kb < NKB; ++kb) {
                         const uint32_t dh = smem_u32(sWh) + kb * kblk, dl = smem_u32(sWl) + kb * kblk;
-                        if (!BWD) {
-                            tma_load_3d(dh, &tmWh, kb * BK, (int)rank * LN, c, w_full);
-                            if (WSPLIT) tma_load_3d(dl, &tmWl, kb * BK, (int)rank * LN, c, w_full);
-                        } else {
-                            for (int a = 0; a < LN / 64; ++a) {
-                                tma_load_3d(dh + 8192 * a, &tmWh, (int)rank * LN + 64 * a, kb * BK, c, w_full);
-                                if (WSPLIT)
-                                    tma_load_3d(dl + 8192 * a, &tmWl, (int)rank * LN + 64 * a, kb * BK, c, w_full);
-                            }
+                        if (!BWD) {   // B = W[f][k], K-major: this CTA's BN output features
+                            tma_load_3d_pair(dh, &tmWh, kb * BK, (int)rank * BN, c, lead_w_full);
+                            if (WSPLIT) tma_load_3d_pair(dl, &tmWl, kb * BK, (int)rank * BN, c, lead_w_full);
+                        } else {      // B = W^T read MN-major from W[o][i]: 64-feature atoms
+                            for (int a = 0; a < BN / 64; ++a)
+                                tma_load_3d_pair(dh + 8192 * a, &tmWh, (int)rank * BN + 64 * a, kb * BK, c, lead_w_full);
                         }
                     }
                     w_pending = true;
@@ -495,40 +514,43 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     const int s = (int)(kbi % L_STAGES);
                     const uint32_t ph = (uint32_t)(kbi / L_STAGES) & 1u;
                     if (!mbar_wait(a_empty0 + 8 * s, ph ^ 1u, p.err)) { ok = false; break; }
-                    mbar_expect_tx(a_full0 + 8 * s, L_A_BYTES);
-                    tma_load_3d(smem_u32(sA + s * L_A_BYTES), &tmA, kb * BK, t * BM, c, a_full0 + 8 * s);
+                    if (leader) mbar_expect_tx(a_full0 + 8 * s, 2u * L_A_BYTES);
+                    tma_load_3d_pair(smem_u32(sA + s * L_A_BYTES), &tmA, kb * BK, t * BM, c, lead_a_full0 + 8 * s);
                     ++kbi;
                 }
             }
-            if (!ok) {   // let copies already in flight land before the CTA exits
+            if (!ok && leader) {   // let copies already in flight land before the CTA exits
                 for (long i = std::max<long>(0, kbi - L_STAGES); i < kbi; ++i)
                     mbar_wait(a_full0 + 8 * (int)(i % L_STAGES), (uint32_t)(i / L_STAGES) & 1u, p.err, 100000000ull);
                 if (w_pending) mbar_wait(w_full, wph, p.err, 100000000ull);
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {   // MMA issuer
-            const uint32_t idesc = idesc_bf16(BM, LN, false, BWD);
+        if (lane == 0 && leader) {   // MMA issuer: the leader alone drives the pair
+            const uint32_t idesc = idesc_bf16(2 * BM, LN, false, BWD);
             int cur_c = -1;
             uint32_t wph = 0;
             long kbi = 0;
             int it = 0;
             bool ok = true;
             for (long u = u0; u < u1 && ok; ++u, ++it) {
-                const int c = (int)(u / p.ntiles);
+                const int c = (int)(u / tpg);
                 if (c != cur_c) {
-                    if (!mbar_wait(w_full, wph, p.err)) { ok = false; break; }
+                    if (!mbar_wait_cluster(w_full, wph, p.err)) { ok = false; break; }
                     wph ^= 1u;
                     cur_c = c;
                 }
                 const int slot = it & 1;
-                if (!mbar_wait(acc_empty0 + 8 * slot, ((uint32_t)(it >> 1) & 1u) ^ 1u, p.err)) { ok = false; break; }
+                if (!mbar_wait_cluster(acc_empty0 + 8 * slot, ((uint32_t)(it >> 1) & 1u) ^ 1u, p.err)) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(slot * SLOT);
                 for (int kb = 0; kb < NKB; ++kb) {
                     const int s = (int)(kbi % L_STAGES);
                     const uint32_t ph = (uint32_t)(kbi / L_STAGES) & 1u;
-                    if (!mbar_wait(a_full0 + 8 * s, ph, p.err)) { ok = false; break; }
+                    if (!mbar_wait_cluster(a_full0 + 8 * s, ph, p.err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(sA + s * L_A_BYTES);
                     const uint32_t wh = smem_u32(sWh) + kb * kblk, wl = smem_u32(sWl) + kb * kblk;
@@ -536,48 +558,49 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     for (int ks = 0; ks < BK / 16; ++ks) {
                         const uint64_t ad = sdesc(sa + 32 * ks, 0, 1024);
                         const uint64_t bh = BWD ? sdesc(wh + 2048 * ks, 8192, 1024) : sdesc(wh + 32 * ks, 0, 1024);
-                        mma_bf16(d_tmem, ad, bh, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
-                        if (WSPLIT) {
-                            const uint64_t bl = BWD ? sdesc(wl + 2048 * ks, 8192, 1024) : sdesc(wl + 32 * ks, 0, 1024);
-                            mma_bf16(d_tmem, ad, bl, idesc, 1u);
-                        }
+                        mma_bf16_pair(d_tmem, ad, bh, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+                        if (WSPLIT) mma_bf16_pair(d_tmem, ad, sdesc(wl + 32 * ks, 0, 1024), idesc, 1u);
                     }
-                    mma_commit(a_empty0 + 8 * s);
+                    mma_commit_pair(a_empty0 + 8 * s, (uint16_t)3);
                     ++kbi;
                 }
                 if (!ok) break;
-                mma_commit(acc_full0 + 8 * slot);
-                const int next_c = (u + 1 < u1) ? (int)((u + 1) / p.ntiles) : -1;
-                if (next_c != c) mma_commit(w_empty);
+                mma_commit_pair(acc_full0 + 8 * slot, (uint16_t)3);
+                const int next_c = (u + 1 < u1) ? (int)((u + 1) / tpg) : -1;
+                if (next_c != c) mma_commit_pair(w_empty, (uint16_t)3);
             }
         }
     } else {
         // ---------------- epilogue warps 2..9: two per lane quadrant ----------------
         // warp e = warp - 2 owns rows 32 q .. 32 q + 31 (q = warp mod 4, the TMEM lanes it
-        // may read) and the half row h = e / 4 of this CTA's columns.
+        // may read) and the half row h = e / 4 of the columns.
         const int q = warp & 3, row = 32 * q + lane, et = threadIdx.x - 64, h = (warp - 2) >> 2;
         const uint32_t lane_off = (uint32_t)(32 * q) << 16;
-        const int col0 = (int)rank * LN;
-        const int hc0 = h * (LN / 2);          // first column (within this CTA) of this warp's half
-        float *fsum = sbias + 512;             // [2][128] half-row partial dot products
+        const int hc0 = h * (LN / 2);          // first column of this warp's half
+        uint8_t *stg = stage0 + (warp - 2) * L_STG;
+        const int tr = lane >> 2, tj = lane & 3;   // transposed access: rows tr + 8 i, piece tj
         int it = 0, chain_loaded = -1;
         for (long u = u0; u < u1; ++u, ++it) {
-            const int c = (int)(u / p.ntiles), t = (int)(u % p.ntiles);
+            const int c = (int)(u / tpg), t = (int)(u % tpg) * 2 + (int)rank;
+            const bool tile_ok = t < p.ntiles;
             const int slot = it & 1;
-            const int m = t * BM + row;
+            const int r0 = t * BM + 32 * q;    // first data row of this warp
+            const int m = r0 + row - 32 * q;
             const bool valid = m < p.N;
-            const long rowoff = ((long)c * p.N + (valid ? m : 0)) * p.W + col0;
-            const long part = ((long)c * p.ntiles + t) * p.W + col0;
-            // global loads of this tile, issued before the accumulator wait
+            const long wbase = ((long)c * p.N + r0) * p.W + hc0;   // element (r0, hc0) of [c][N][W]
+            const long part = ((long)c * p.ntiles + t) * p.W;
+            // slopes of this tile, 8 rows x 64 B per load, issued before the accumulator wait
             uint4 ap[BWD ? NCH * 4 : 1];
             if (BWD) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(p.aux + rowoff + hc0);
 #pragma unroll
-                for (int i = 0; i < NCH * 4; ++i) ap[i] = make_uint4(0u, 0u, 0u, 0u);
-                if (valid) {
+                for (int ch = 0; ch < NCH; ++ch)
 #pragma unroll
-                    for (int i = 0; i < NCH * 4; ++i) ap[i] = src[i];
-                }
+                    for (int i = 0; i < 4; ++i) {
+                        const int rr = tr + 8 * i;
+                        ap[4 * ch + i] = make_uint4(0u, 0u, 0u, 0u);
+                        if (r0 + rr < p.N)
+                            ap[4 * ch + i] = __ldg(reinterpret_cast<const uint4 *>(p.aux + wbase + (long)rr * p.W + 32 * ch + 8 * tj));
+                    }
             }
             const float yv = (MODE == L_FWD_OUT && valid) ? p.y[m] : 0.0f;
             float xv[8];
@@ -588,16 +611,30 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
             if (!BWD && c != chain_loaded) {
                 named_bar_sync(1, 256);
                 for (int i = et; i < LN; i += 256) {
-                    sbias[i] = p.bias[(long)c * p.W + col0 + i];
-                    if (MODE == L_FWD_OUT) swo[i] = p.wout[(long)c * p.W + col0 + i];
+                    sbias[i] = p.bias[(long)c * p.W + i];
+                    if (MODE == L_FWD_OUT) swo[i] = p.wout[(long)c * p.W + i];
                 }
                 named_bar_sync(1, 256);
                 chain_loaded = c;
             }
+            // this thread's 32 packed bf16 of its row -> staging -> 8-row coalesced stores
+            auto store_chunk = [&](const uint32_t (&pk)[16], int col) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    *reinterpret_cast<uint4 *>(stg + stg_off(lane, j)) =
+                        make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int rr = tr + 8 * i;
+                    const uint4 v = *reinterpret_cast<const uint4 *>(stg + stg_off(rr, tj));
+                    if (r0 + rr < p.N) *reinterpret_cast<uint4 *>(p.out + wbase + (long)rr * p.W + col + 8 * tj) = v;
+                }
+                __syncwarp();
+            };
             if (!mbar_wait(acc_full0 + 8 * slot, (uint32_t)(it >> 1) & 1u, p.err)) break;
             tc_fence_after();
             const uint32_t taddr = tmem + lane_off + (uint32_t)(slot * SLOT + hc0);
-            bool ok = true;
             uint32_t rb[2][32];
             if (MODE == L_FWD_TANH) {
                 tmem_ld32_issue(taddr, rb[0]);
@@ -606,48 +643,44 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     const int c0 = 32 * ch;
                     tmem_ld_wait(rb[ch & 1]);
                     if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
-                    float v[32];
+                    uint32_t pk[16];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rb[ch & 1][j]);
-                    if (valid) {
-                        uint32_t pk[16];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            pk[j] = pack_bf16(tanh_fast(v[2 * j] + sbias[hc0 + c0 + 2 * j]),
-                                              tanh_fast(v[2 * j + 1] + sbias[hc0 + c0 + 2 * j + 1]));
-                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + hc0 + c0);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
-                    }
+                    for (int j = 0; j < 16; ++j)
+                        pk[j] = pack_bf16(tanh_fast(__uint_as_float(rb[ch & 1][2 * j]) + sbias[hc0 + c0 + 2 * j]),
+                                          tanh_fast(__uint_as_float(rb[ch & 1][2 * j + 1]) + sbias[hc0 + c0 + 2 * j + 1]));
+                    store_chunk(pk, c0);
                 }
             } else if (BWD) {
                 tmem_ld32_issue(taddr, rb[0]);
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
                     const int c0 = 32 * ch;
-                    float v[32], dd[32];
+                    float dd[32];
                     tmem_ld_wait(rb[ch & 1]);
                     if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
+                    // slopes of this chunk: 8-row pieces in, own row out
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rb[ch & 1][j]);
+                    for (int i = 0; i < 4; ++i) *reinterpret_cast<uint4 *>(stg + stg_off(tr + 8 * i, tj)) = ap[4 * ch + i];
+                    __syncwarp();
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const uint4 uu = ap[4 * ch + j];
+                        const uint4 uu = *reinterpret_cast<const uint4 *>(stg + stg_off(lane, j));
                         const uint32_t w4[4] = {uu.x, uu.y, uu.z, uu.w};
 #pragma unroll
                         for (int tt = 0; tt < 4; ++tt) {
                             const float2 a = unpack_bf16(w4[tt]);
-                            dd[8 * j + 2 * tt] = valid ? v[8 * j + 2 * tt] * (1.0f - a.x * a.x) : 0.0f;
-                            dd[8 * j + 2 * tt + 1] = valid ? v[8 * j + 2 * tt + 1] * (1.0f - a.y * a.y) : 0.0f;
+                            const int k = 8 * j + 2 * tt;
+                            dd[k] = valid ? __uint_as_float(rb[ch & 1][k]) * (1.0f - a.x * a.x) : 0.0f;
+                            dd[k + 1] = valid ? __uint_as_float(rb[ch & 1][k + 1]) * (1.0f - a.y * a.y) : 0.0f;
                         }
                     }
-                    if (MODE == L_BWD_TANH && valid) {
+                    if (MODE == L_BWD_TANH) {
                         uint32_t pk[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
-                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + hc0 + c0);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                        store_chunk(pk, c0);   // its first __syncwarp also orders the slope reads
+                    } else {
+                        __syncwarp();          // slope reads done before the next chunk's pieces land
                     }
                     if (MODE == L_BWD_FIRST) {
                         for (int d = 0; d < p.dx; ++d) {
@@ -660,14 +693,16 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     red[(0 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dd);
                 }
                 named_bar_sync(1, 256);
-                for (int cc = et; cc < LN; cc += 256) {
-                    p.db_part[part + cc] = red[(0 * 4 + 0) * LN + cc] + red[(0 * 4 + 1) * LN + cc] +
-                                           red[(0 * 4 + 2) * LN + cc] + red[(0 * 4 + 3) * LN + cc];
-                    if (MODE == L_BWD_FIRST)
-                        for (int d = 0; d < p.dx; ++d)
-                            p.dw0_part[(part + cc) * p.dx + d] =
-                                red[((1 + d) * 4 + 0) * LN + cc] + red[((1 + d) * 4 + 1) * LN + cc] +
-                                red[((1 + d) * 4 + 2) * LN + cc] + red[((1 + d) * 4 + 3) * LN + cc];
+                if (tile_ok) {
+                    for (int cc = et; cc < LN; cc += 256) {
+                        p.db_part[part + cc] = red[(0 * 4 + 0) * LN + cc] + red[(0 * 4 + 1) * LN + cc] +
+                                               red[(0 * 4 + 2) * LN + cc] + red[(0 * 4 + 3) * LN + cc];
+                        if (MODE == L_BWD_FIRST)
+                            for (int d = 0; d < p.dx; ++d)
+                                p.dw0_part[(part + cc) * p.dx + d] =
+                                    red[((1 + d) * 4 + 0) * LN + cc] + red[((1 + d) * 4 + 1) * LN + cc] +
+                                    red[((1 + d) * 4 + 2) * LN + cc] + red[((1 + d) * 4 + 3) * LN + cc];
+                    }
                 }
                 named_bar_sync(1, 256);
             } else if (MODE == L_FWD_OUT) {
@@ -682,26 +717,13 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     for (int j = 0; j < 32; ++j)
                         fh += tanh_fast(__uint_as_float(rb[ch & 1][j]) + sbias[hc0 + c0 + j]) * swo[hc0 + c0 + j];
                 }
-                // this CTA's partial dot product: both halves of the row, in a fixed order
+                // the row's dot product: both halves, in a fixed order
                 fsum[h * 128 + row] = fh;
                 named_bar_sync(1, 256);
-                const float f = fsum[row] + fsum[128 + row];
-                float fp = 0.0f;
-                if (CLUSTER) {   // swap partial dot products with the peer CTA (one arrival per row)
-                    const int xb = it & 1;
-                    if (h == 0) {
-                        const uint32_t mine = smem_u32(xchg + xb * 128 + row);
-                        st_cluster_f32(mapa_shared(mine, rank ^ 1u), f);
-                        mbar_arrive_cluster(mapa_shared(xbar, rank ^ 1u));
-                    }
-                    ok = mbar_wait_cluster(xbar, (uint32_t)it & 1u, p.err);
-                    fp = xchg[xb * 128 + row];
-                }
-                const float f0 = rank == 0 ? f : fp, f1 = rank == 0 ? fp : f;
-                const float fo = (p.bout[c] + f0) + f1;
+                const float fo = p.bout[c] + (fsum[row] + fsum[128 + row]);
                 const float r = valid ? fo - yv : 0.0f;
                 const float d = r * p.inv_s2;
-                if (rank == 0 && h == 0) {
+                if (h == 0) {
                     double r2 = (double)r * (double)r;
                     float ds = d;
 #pragma unroll
@@ -718,69 +740,58 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
                     const int c0 = 32 * ch;
-                    float v[32], dw[32], dd[32];
+                    float dw[32], dd[32];
                     tmem_ld_wait(rb[ch & 1]);
                     if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rb[ch & 1][j]);
-#pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const float a = tanh_fast(v[j] + sbias[hc0 + c0 + j]);
+                        const float a = tanh_fast(__uint_as_float(rb[ch & 1][j]) + sbias[hc0 + c0 + j]);
                         dw[j] = d * a;
                         dd[j] = d * swo[hc0 + c0 + j] * (1.0f - a * a);
                     }
-                    if (valid) {
-                        uint32_t pk[16];
+                    uint32_t pk[16];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
-                        uint4 *o = reinterpret_cast<uint4 *>(p.out + rowoff + hc0 + c0);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
-                    }
+                    for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
+                    store_chunk(pk, c0);
                     red[(0 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dw);
                     red[(1 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dd);
                 }
                 named_bar_sync(1, 256);
-                for (int cc = et; cc < LN; cc += 256) {
-                    p.dwout_part[part + cc] = red[(0 * 4 + 0) * LN + cc] + red[(0 * 4 + 1) * LN + cc] +
-                                              red[(0 * 4 + 2) * LN + cc] + red[(0 * 4 + 3) * LN + cc];
-                    p.db_part[part + cc] = red[(1 * 4 + 0) * LN + cc] + red[(1 * 4 + 1) * LN + cc] +
-                                           red[(1 * 4 + 2) * LN + cc] + red[(1 * 4 + 3) * LN + cc];
-                }
-                if (rank == 0 && et == 0) {
-                    p.u_part[(long)c * p.ntiles + t] = dred[0] + dred[1] + dred[2] + dred[3];
-                    p.dbout_part[(long)c * p.ntiles + t] = fred[0] + fred[1] + fred[2] + fred[3];
+                if (tile_ok) {
+                    for (int cc = et; cc < LN; cc += 256) {
+                        p.dwout_part[part + cc] = red[(0 * 4 + 0) * LN + cc] + red[(0 * 4 + 1) * LN + cc] +
+                                                  red[(0 * 4 + 2) * LN + cc] + red[(0 * 4 + 3) * LN + cc];
+                        p.db_part[part + cc] = red[(1 * 4 + 0) * LN + cc] + red[(1 * 4 + 1) * LN + cc] +
+                                               red[(1 * 4 + 2) * LN + cc] + red[(1 * 4 + 3) * LN + cc];
+                    }
+                    if (et == 0) {
+                        p.u_part[(long)c * p.ntiles + t] = dred[0] + dred[1] + dred[2] + dred[3];
+                        p.dbout_part[(long)c * p.ntiles + t] = fred[0] + fred[1] + fred[2] + fred[3];
+                    }
                 }
                 named_bar_sync(1, 256);
             }
+            // release the accumulator slot: one arrival per warp on the leader's barrier
             tc_fence_before();
-            mbar_arrive(acc_empty0 + 8 * slot);
-            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(lead_acc_empty0 + 8 * slot);
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (CLUSTER) cluster_sync_all();   // no CTA leaves while its peer may still touch its shared memory
+    cluster_sync_all();   // neither CTA leaves while the pair may still touch its memory
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, TCOLS);
+        tmem_dealloc2(tmem, TCOLS);
     }
 }
 
-template <int MODE, int WIDTH>
+template <int MODE, int WIDTH, bool SPLIT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(L_THREADS, 1)
-    k_layer(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmWh,
-            const __grid_constant__ CUtensorMap tmWl, const LayerParams p)
-{
-    layer_body<MODE, true, true, WIDTH>(tmA, tmWh, tmWl, p);
-}
-
-template <int MODE, int WIDTH>
-__global__ void __launch_bounds__(L_THREADS, 1)
-    k_layer_solo(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmWh,
+    k_layer_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmWh,
                  const __grid_constant__ CUtensorMap tmWl, const LayerParams p)
 {
-    layer_body<MODE, false, false, WIDTH>(tmA, tmWh, tmWl, p);
+    layer_body<MODE, SPLIT, WIDTH>(tmA, tmWh, tmWl, p);
 }
 
 // ---------------------------------------------------------------------------
@@ -1106,48 +1117,30 @@ void launch_umma(const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &
     HMC_LAUNCH_CK();
 }
 
-template <int MODE, int WIDTH>
+template <int MODE, int WIDTH, bool SPLIT>
 void launch_layer_w(const CUtensorMap &a, const CUtensorMap &wh, const CUtensorMap &wl, const LayerParams &p, int ncta,
                     cudaStream_t s)
 {
     static bool configured = false;
     if (!configured) {
-        HMC_CK(cudaFuncSetAttribute(k_layer<MODE, WIDTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, L_SMEM));
+        HMC_CK(cudaFuncSetAttribute(k_layer_pair<MODE, WIDTH, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    L_SMEM));
         configured = true;
     }
     static const char *names[] = {"layer_fwd_tanh", "layer_fwd_out", "layer_bwd_tanh", "layer_bwd_first"};
     ProfScope ps(names[MODE], s);
-    k_layer<MODE, WIDTH><<<ncta, L_THREADS, L_SMEM, s>>>(a, wh, wl, p);
+    k_layer_pair<MODE, WIDTH, SPLIT><<<ncta, L_THREADS, L_SMEM, s>>>(a, wh, wl, p);
     HMC_LAUNCH_CK();
 }
 
+// A hidden layer on CTA pairs: forward with the hi/lo weights, reverse with hi only.
 template <int MODE>
 void launch_layer(const CUtensorMap &a, const CUtensorMap &wh, const CUtensorMap &wl, const LayerParams &p, int ncta,
                   cudaStream_t s)
 {
-    if (p.W == 256) launch_layer_w<MODE, 256>(a, wh, wl, p, ncta, s);
-    else launch_layer_w<MODE, 128>(a, wh, wl, p, ncta, s);
-}
-
-template <int MODE, int WIDTH>
-void launch_layer_solo_w(const CUtensorMap &a, const CUtensorMap &wh, const LayerParams &p, int ncta, cudaStream_t s)
-{
-    static bool configured = false;
-    if (!configured) {
-        HMC_CK(cudaFuncSetAttribute(k_layer_solo<MODE, WIDTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, L_SMEM));
-        configured = true;
-    }
-    static const char *names[] = {"solo_fwd_tanh", "solo_fwd_out", "solo_bwd_tanh", "solo_bwd_first"};
-    ProfScope ps(names[MODE], s);
-    k_layer_solo<MODE, WIDTH><<<ncta, L_THREADS, L_SMEM, s>>>(a, wh, wh, p);
-    HMC_LAUNCH_CK();
-}
-
-template <int MODE>
-void launch_layer_solo(const CUtensorMap &a, const CUtensorMap &wh, const LayerParams &p, int ncta, cudaStream_t s)
-{
-    if (p.W == 256) launch_layer_solo_w<MODE, 256>(a, wh, p, ncta, s);
-    else launch_layer_solo_w<MODE, 128>(a, wh, p, ncta, s);
+    constexpr bool SPLIT = (MODE == L_FWD_TANH || MODE == L_FWD_OUT);
+    if (p.W == 256) launch_layer_w<MODE, 256, SPLIT>(a, wh, wl, p, ncta, s);
+    else launch_layer_w<MODE, 128, SPLIT>(a, wh, wl, p, ncta, s);
 }
 
 void launch_dw2(const CUtensorMap &d, const CUtensorMap &a, const Params &p, dim3 grid, cudaStream_t s)
@@ -1162,10 +1155,11 @@ void launch_dw2(const CUtensorMap &d, const CUtensorMap &a, const Params &p, dim
     HMC_LAUNCH_CK();
 }
 
-// How many two-CTA clusters of the layer kernel can be resident at once.
+// How many CTA pairs of the layer kernel can be resident at once.
 int layer_max_clusters()
 {
-    HMC_CK(cudaFuncSetAttribute(k_layer<L_FWD_OUT, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, L_SMEM));
+    auto kern = k_layer_pair<L_FWD_OUT, 256, true>;
+    HMC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L_SMEM));
     int dev = 0, sms = 0;
     HMC_CK(cudaGetDevice(&dev));
     HMC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1174,7 +1168,7 @@ int layer_max_clusters()
     cfg.blockDim = dim3(L_THREADS, 1, 1);
     cfg.dynamicSmemBytes = L_SMEM;
     int n = 0;
-    HMC_CK(cudaOccupancyMaxActiveClusters(&n, k_layer<L_FWD_OUT, 256>, &cfg));
+    HMC_CK(cudaOccupancyMaxActiveClusters(&n, kern, &cfg));
     return std::max(1, std::min(n, sms / 2));
 }
 
@@ -1433,8 +1427,8 @@ class UmmaEngine final : public Engine {
         base.ntiles = ntiles_;
         base.dx = dx_;
         base.err = err_;
-        const long U = (long)C_ * ntiles_;
-        const int ncta = 2 * (int)std::min<long>(max_clusters_, U);
+        const long U2 = (long)C_ * ((ntiles_ + 1) / 2);   // (chain, tile pair) units
+        const int ncta = 2 * (int)std::min<long>(max_clusters_, U2);
         for (int i = 1; i <= L_ - 2; ++i) {
             LayerParams lp = base;
             lp.bias = bh_[i - 1]->as<float>();
@@ -1454,8 +1448,7 @@ class UmmaEngine final : public Engine {
                 launch_layer<L_FWD_OUT>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
             }
         }
-        // reverse pass: one CTA per SM holds the whole bf16 W (the lo part is not needed there)
-        const int nsolo = (int)std::min<long>(num_sms_, U);
+        // reverse pass (bf16 W: the lo part is not needed there)
         for (int i = L_ - 2; i >= 1; --i) {
             if (i <= nd.lmin) break;
             LayerParams lp = base;
@@ -1463,15 +1456,11 @@ class UmmaEngine final : public Engine {
             lp.db_part = db_part_[i - 1]->as<float>();
             if (i > 1) {
                 lp.out = D_[i]->as<__nv_bfloat16>();
-                launch_layer_solo<L_BWD_TANH>(D_row_[i + 1], W_atom_[i], lp, nsolo, s);
-            } else if (dx_ <= 4) {
-                lp.x = x_.as<float>();
-                lp.dw0_part = dw0_part_.as<float>();
-                launch_layer_solo<L_BWD_FIRST>(D_row_[i + 1], W_atom_[i], lp, nsolo, s);
+                launch_layer<L_BWD_TANH>(D_row_[i + 1], W_atom_[i], W_atom_[i], lp, ncta, s);
             } else {
                 lp.x = x_.as<float>();
                 lp.dw0_part = dw0_part_.as<float>();
-                launch_layer<L_BWD_FIRST>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], lp, ncta, s);
+                launch_layer<L_BWD_FIRST>(D_row_[i + 1], W_atom_[i], W_atom_[i], lp, ncta, s);
             }
         }
     }

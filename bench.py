@@ -168,6 +168,7 @@ def main():
 
     import torch
     import paper_2507_14652_gb300 as hmc
+    from paper_2507_14652_gb300.replicas import job_rate, reduce_max, replica_seed
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -179,7 +180,7 @@ def main():
 
     prob = W.wide_mlp()
     C, L, eps = prob.chains, prob.L, prob.eps
-    seed = 1000 + rank                      # replicas: independent chains per rank
+    seed = replica_seed(rank)               # replicas: independent chains per rank
     s = hmc.Sampler.mlp(prob.net.widths, prob.x, prob.y, prob.mask, prob.frozen, C, prior_sigma=prob.prior_sigma,
                         noise_sigma=prob.noise_sigma, prec=hmc.PREC_BF16)
     q0 = torch.from_numpy(prob.q0).float().cuda()
@@ -205,12 +206,8 @@ def main():
         dist.barrier()
     stop.set()
     th.join(timeout=5)
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * C * L * args.steps / (ms / 1000.0)
+    ms = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+    value = job_rate(ws, C * L * args.steps, ms / 1000.0)
     graph_k = hmc.graph_kernels(s)
     acc_np, dH_np = acc.cpu().numpy(), dH.cpu().numpy()
 
@@ -256,12 +253,8 @@ def main():
                            Sh.data_ptr(), ah.data_ptr(), dh.data_ptr(), qh.data_ptr())
         if st != 0:
             raise hmc.HmcError(st, L_.hmc_last_error().decode())
-    t_e2e = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": ws * C * L * args.steps / t_e2e, "unit": METRIC, "h2d_bytes_per_step": 4 * C * prob.k,
+    t_e2e = reduce_max(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": job_rate(ws, C * L * args.steps, t_e2e), "unit": METRIC, "h2d_bytes_per_step": 4 * C * prob.k,
            "d2h_bytes_per_step": 4 * C * prob.k + C + 8 * C + 4 * C * prob.k}
 
     # ESS/s: batched BF16 sampler vs the plain one-chain FP32 CUDA-core sampler

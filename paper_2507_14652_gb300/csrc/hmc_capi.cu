@@ -165,6 +165,8 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_begin(const SegDesc *segs
     __shared__ __align__(16) unsigned char sd_raw[sizeof(SegDesc)];
     SegDesc &sd = *reinterpret_cast<SegDesc *>(sd_raw);
     __shared__ double sm[8];
+    pdl_wait();
+    pdl_trigger();
     const int s = blockIdx.y, pi = s / C, c = s % C;
     load_seg(sd, &segs[pi]);
     const long j0 = (long)blockIdx.x * TRAJ_ELEMS;
@@ -202,6 +204,8 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_kick_drift(const SegDesc *segs
 {
     __shared__ __align__(16) unsigned char sd_raw[sizeof(SegDesc)];
     SegDesc &sd = *reinterpret_cast<SegDesc *>(sd_raw);
+    pdl_wait();
+    pdl_trigger();
     const int s = blockIdx.y, pi = s / C, c = s % C;
     load_seg(sd, &segs[pi]);
     const long base = sd.qoff + (long)c * sd.k;
@@ -228,6 +232,8 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_kinetic(const SegDesc *se
                                                                const T *g_prop, double *K1p, double eps)
 {
     __shared__ double sm[8];
+    pdl_wait();
+    pdl_trigger();
     const int s = blockIdx.y, pi = s / C, c = s % C;
     const long k = segs[pi].k;
     const long base = segs[pi].qoff + (long)c * k;
@@ -256,6 +262,8 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_accept(const SegDesc *seg
                                                               const TrajState *st, int *acc_int)
 {
     __shared__ int s_acc;
+    pdl_wait();
+    pdl_trigger();
     const int s = blockIdx.y, pi = s / C, c = s % C;
     const long k = segs[pi].k;
     const long base = segs[pi].qoff + (long)c * k;
@@ -298,6 +306,8 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_accept(const SegDesc *seg
 // After every block has decided: commit U of accepted chains, advance the counters.
 __global__ void k_traj_advance(TrajState *st, int nseg, const int *acc_int, double *U_cur, const double *U_prop)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int s = threadIdx.x; s < nseg; s += blockDim.x)
         if (acc_int[s]) U_cur[s] = U_prop[s];
     if (threadIdx.x == 0) {
@@ -515,11 +525,11 @@ void kick_drift(hmc_handle h, void *q, void *p, const void *g, double kick, doub
     const SegDesc *sd = h->segs.as<SegDesc>();
     const dim3 grid(h->traj_nblk, nseg);
     if (h->prec == HMC_PREC_FP64)
-        k_kick_drift<double><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, (const double *)g, (double *)p,
-                                                                   (double *)q, kick, drift);
+        launch_pdl(k_kick_drift<double>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, (const double *)g,
+                   (double *)p, (double *)q, kick, drift);
     else
-        k_kick_drift<float><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, (const float *)g, (float *)p, (float *)q,
-                                                                  kick, drift);
+        launch_pdl(k_kick_drift<float>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, (const float *)g,
+                   (float *)p, (float *)q, kick, drift);
     HMC_LAUNCH_CK();
 }
 
@@ -529,29 +539,26 @@ template <typename T> void enqueue_trajectory(hmc_handle h, double eps, int L, u
     const SegDesc *sd = h->segs.as<SegDesc>();
     TrajState *st = h->state.as<TrajState>();
     const dim3 grid(nblk, nseg);
-    k_traj_begin<T><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, nblk, h->q_cur.as<T>(), h->g_cur.as<T>(),
-                                                          h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(), eps,
-                                                          seed, st);
+    launch_pdl(k_traj_begin<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, h->q_cur.as<T>(),
+               h->g_cur.as<T>(), h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(), eps, seed, st);
     HMC_LAUNCH_CK();
     for (int s = 1; s <= L; ++s) {
         energy_grad_all(h, h->q_prop.ptr, h->U_prop.as<double>(), h->g_prop.ptr, true);
         if (s < L) {
-            k_kick_drift<T><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, h->g_prop.as<T>(), h->p.as<T>(),
-                                                                  h->q_prop.as<T>(), eps, eps);
+            launch_pdl(k_kick_drift<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, h->g_prop.as<T>(),
+                       h->p.as<T>(), h->q_prop.as<T>(), eps, eps);
             HMC_LAUNCH_CK();
         }
     }
-    k_traj_kinetic<T><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, nblk, h->p.as<T>(), h->g_prop.as<T>(),
-                                                            h->K1p.as<double>(), eps);
+    launch_pdl(k_traj_kinetic<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, h->p.as<T>(),
+               h->g_prop.as<T>(), h->K1p.as<double>(), eps);
     HMC_LAUNCH_CK();
-    k_traj_accept<T><<<grid, TRAJ_THREADS, 0, h->stream>>>(sd, h->C, nblk, nseg, h->S_total, h->q_cur.as<T>(),
-                                                           h->g_cur.as<T>(), h->U_cur.as<double>(), h->q_prop.as<T>(),
-                                                           h->g_prop.as<T>(), h->U_prop.as<double>(),
-                                                           h->K0p.as<double>(), h->K1p.as<double>(), seed, st,
-                                                           h->acc_int.as<int>());
+    launch_pdl(k_traj_accept<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, nseg, h->S_total,
+               h->q_cur.as<T>(), h->g_cur.as<T>(), h->U_cur.as<double>(), h->q_prop.as<T>(), h->g_prop.as<T>(),
+               h->U_prop.as<double>(), h->K0p.as<double>(), h->K1p.as<double>(), seed, st, h->acc_int.as<int>());
     HMC_LAUNCH_CK();
-    k_traj_advance<<<1, 256, 0, h->stream>>>(st, nseg, h->acc_int.as<int>(), h->U_cur.as<double>(),
-                                             h->U_prop.as<double>());
+    launch_pdl(k_traj_advance, dim3(1), dim3(256), 0, h->stream, st, nseg, h->acc_int.as<int>(),
+               h->U_cur.as<double>(), h->U_prop.as<double>());
     HMC_LAUNCH_CK();
 }
 

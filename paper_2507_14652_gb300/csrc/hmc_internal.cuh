@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -111,6 +112,31 @@ Engine *make_simt_engine_f64(Problem &p, int C);
 Engine *make_simt_engine_f32(Problem &p, int C);
 Engine *make_umma_engine_bf16(Problem &p, int C);
 bool umma_engine_supports(const Problem &p, std::string *why);
+
+// Programmatic dependent launch.  A kernel started with launch_pdl may begin while
+// the previous kernel in its stream drains: it runs pdl_wait() before it touches any
+// global memory (that returns once the previous grid has finished and its writes are
+// visible), and pdl_trigger() lets the next kernel start its own prologue early.
+// Every kernel launched this way calls pdl_wait() in every block, so the completion
+// of any kernel implies the completion of all kernels before it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    HMC_CK(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}
 
 // Per-kernel timing for hmc_diag_profile_energy_grad: while a profiler is active on
 // this thread, every launch site records a CUDA event pair on its launching stream.

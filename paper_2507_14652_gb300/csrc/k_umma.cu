@@ -478,6 +478,8 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
     cluster_sync_all();   // the leader's barriers exist before the peer signals them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();      // the previous kernel's outputs are visible from here on
+    pdl_trigger();
     // barriers that count loads and epilogue releases live in the leader CTA
     const uint32_t lead_a_full0 = mapa_shared(a_full0, 0);
     const uint32_t lead_w_full = mapa_shared(w_full, 0);
@@ -842,6 +844,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dw2(const __grid_constant__ CUt
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();      // the reverse pass's deltas are visible from here on
+    pdl_trigger();
     bool ok = true;
     if (warp == 0) {
         if (lane == 0) {
@@ -940,34 +944,46 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dw2(const __grid_constant__ CUt
 // ---------------------------------------------------------------------------
 
 // A_1[b][n][o] = tanh(sum_d X[n][d] W0[b][o][d] + b0[b][o]) in bf16.  One block per
-// (128-row tile, chain); thread o keeps row o of W0 and b0 in registers and walks the
-// tile's rows, whose inputs are staged in shared memory; a warp writes 64 contiguous bytes.
+// (128-row tile, chain); a thread keeps four adjacent rows o of W0 and b0 in registers
+// and walks a slice of the tile's rows, whose inputs are staged in shared memory, so
+// a warp writes 256 contiguous bytes of a row per store.
 __global__ void __launch_bounds__(256) k_first_fwd(const float *x, int dx, int N, int w, const float *W0,
                                                    const float *b0, __nv_bfloat16 *A1)
 {
     __shared__ float xs[BM * 8];
+    pdl_wait();
+    pdl_trigger();
     const int b = blockIdx.y, n0 = blockIdx.x * BM;
     const int nr = min(BM, N - n0);
     for (int i = threadIdx.x; i < nr * dx; i += blockDim.x) xs[i] = x[(long)n0 * dx + i];
     __syncthreads();
-    for (int o = threadIdx.x; o < w; o += blockDim.x) {
-        float wr[8];
+    const int quads = w / 4;                                   // w is a multiple of 64 here
+    const int groups = max(1, (int)blockDim.x / quads);
+    const int per = (nr + groups - 1) / groups;
+    for (int item = threadIdx.x; item < quads * groups; item += blockDim.x) {
+        const int o0 = 4 * (item % quads), r0 = (item / quads) * per, r1 = min(nr, r0 + per);
+        float wr[4][8], bo[4];
 #pragma unroll
-        for (int d = 0; d < 8; ++d) wr[d] = d < dx ? W0[((long)b * w + o) * dx + d] : 0.0f;
-        const float bo = b0[(long)b * w + o];
-        __nv_bfloat16 *out = A1 + ((long)b * N + n0) * w + o;
-        for (int r = 0; r < nr; r += 4) {   // four independent rows per step
+        for (int c = 0; c < 4; ++c) {
+            bo[c] = b0[(long)b * w + o0 + c];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) wr[c][d] = d < dx ? W0[((long)b * w + o0 + c) * dx + d] : 0.0f;
+        }
+        __nv_bfloat16 *out = A1 + ((long)b * N + n0) * w + o0;
+        for (int r = r0; r < r1; ++r) {
+            float xv[8];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) xv[d] = d < dx ? xs[r * dx + d] : 0.0f;
             float z[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                z[i] = bo;
+            for (int c = 0; c < 4; ++c) {
+                z[c] = bo[c];
 #pragma unroll
                 for (int d = 0; d < 8; ++d)
-                    if (d < dx) z[i] += xs[min(r + i, nr - 1) * dx + d] * wr[d];
+                    if (d < dx) z[c] += xv[d] * wr[c][d];
             }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (r + i < nr) out[(long)(r + i) * w] = __float2bfloat16_rn(tanh_fast(z[i]));
+            *reinterpret_cast<uint2 *>(out + (long)r * w) =
+                make_uint2(pack_bf16(tanh_fast(z[0]), tanh_fast(z[1])), pack_bf16(tanh_fast(z[2]), tanh_fast(z[3])));
         }
     }
 }
@@ -992,24 +1008,34 @@ struct FinalArgs {
 // block of each chain computes U (fixed-order sums).
 __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float *q, double *U, float *g)
 {
-    __shared__ double sm[8];
+    __shared__ double sm[2][8];
+    pdl_wait();
+    pdl_trigger();
     const int b = blockIdx.y;
-    if (blockIdx.x == gridDim.x - 1) {
-        double pr = 0.0;
+    if (blockIdx.x == gridDim.x - 1) {   // U = likelihood + prior, block-parallel in a fixed order
+        double pr = 0.0, lik = 0.0;
         for (int j = threadIdx.x; j < a.k; j += blockDim.x) {
             const double qj = q[(long)b * a.k + j];
             pr += qj * qj;
         }
+        for (int i = threadIdx.x; i < a.ntiles; i += blockDim.x) lik += a.u_part[(long)b * a.ntiles + i];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) pr += __shfl_xor_sync(0xffffffffu, pr, o);
-        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = pr;
+        for (int o = 16; o > 0; o >>= 1) {
+            pr += __shfl_xor_sync(0xffffffffu, pr, o);
+            lik += __shfl_xor_sync(0xffffffffu, lik, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sm[0][threadIdx.x >> 5] = pr;
+            sm[1][threadIdx.x >> 5] = lik;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int i = 0; i < 8; ++i) t += sm[i];
-            double lik = 0.0;
-            for (int i = 0; i < a.ntiles; ++i) lik += a.u_part[(long)b * a.ntiles + i];
-            U[b] = lik * a.half_inv_s2 + 0.5 * t * a.inv_a2;
+            double t = 0.0, l = 0.0;
+            for (int i = 0; i < 8; ++i) {
+                t += sm[0][i];
+                l += sm[1][i];
+            }
+            U[b] = l * a.half_inv_s2 + 0.5 * t * a.inv_a2;
         }
         return;
     }
@@ -1017,28 +1043,40 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
     if (j >= a.k || !g) return;
     const float qj = q[(long)b * a.k + j];
     const int kd = a.kind[j], off = a.off[j];
-    float s = 0.0f;
+    const float *dp;
+    long stride;
+    int n;
     if (kd == E_HIDDEN_W) {
-        for (int t = 0; t < a.nsplit; ++t) s += a.gw_part[t * a.gw_split + (long)b * a.k + j];
+        dp = a.gw_part + (long)b * a.k + j, stride = a.gw_split, n = a.nsplit;
     } else if (kd == E_BIAS) {
-        const float *dp = a.db_part[a.layer[j]] + (long)b * a.ntiles * a.w + off;
-        for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w];
+        dp = a.db_part[a.layer[j]] + (long)b * a.ntiles * a.w + off, stride = a.w, n = a.ntiles;
     } else if (kd == E_W0) {
-        const float *dp = a.dw0_part + (long)b * a.ntiles * a.w * a.dx + off;
-        for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w * a.dx];
+        dp = a.dw0_part + (long)b * a.ntiles * a.w * a.dx + off, stride = (long)a.w * a.dx, n = a.ntiles;
     } else if (kd == E_WOUT) {
-        const float *dp = a.dwout_part + (long)b * a.ntiles * a.w + off;
-        for (int t = 0; t < a.ntiles; ++t) s += dp[(long)t * a.w];
+        dp = a.dwout_part + (long)b * a.ntiles * a.w + off, stride = a.w, n = a.ntiles;
     } else {
-        const float *dp = a.dbout_part + (long)b * a.ntiles;
-        for (int t = 0; t < a.ntiles; ++t) s += dp[t];
+        dp = a.dbout_part + (long)b * a.ntiles, stride = 1, n = a.ntiles;
     }
+    // partials in index order, four independent loads in flight per step
+    float s = 0.0f;
+    int t = 0;
+    for (; t + 4 <= n; t += 4) {
+        const float v0 = __ldg(dp + t * stride), v1 = __ldg(dp + (t + 1) * stride);
+        const float v2 = __ldg(dp + (t + 2) * stride), v3 = __ldg(dp + (t + 3) * stride);
+        s += v0;
+        s += v1;
+        s += v2;
+        s += v3;
+    }
+    for (; t < n; ++t) s += __ldg(dp + t * stride);
     g[(long)b * a.k + j] = s + qj * (float)a.inv_a2;
 }
 
 template <typename V>
 __global__ void k_scatter_plan(const float *q, long k, ScatterPlan sc)
 {
+    pdl_wait();
+    pdl_trigger();
     const int b = blockIdx.y;
     for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (long)gridDim.x * blockDim.x) {
         const int bi = sc.buf_id[j];
@@ -1129,7 +1167,7 @@ void launch_layer_w(const CUtensorMap &a, const CUtensorMap &wh, const CUtensorM
     }
     static const char *names[] = {"layer_fwd_tanh", "layer_fwd_out", "layer_bwd_tanh", "layer_bwd_first"};
     ProfScope ps(names[MODE], s);
-    k_layer_pair<MODE, WIDTH, SPLIT><<<ncta, L_THREADS, L_SMEM, s>>>(a, wh, wl, p);
+    launch_pdl(k_layer_pair<MODE, WIDTH, SPLIT>, dim3(ncta), dim3(L_THREADS), L_SMEM, s, a, wh, wl, p);
     HMC_LAUNCH_CK();
 }
 
@@ -1151,7 +1189,7 @@ void launch_dw2(const CUtensorMap &d, const CUtensorMap &a, const Params &p, dim
         configured = true;
     }
     ProfScope ps("dw2", s);
-    k_dw2<<<grid, NTHREADS, DW_SMEM, s>>>(d, a, p);
+    launch_pdl(k_dw2, grid, dim3(NTHREADS), DW_SMEM, s, d, a, p);
     HMC_LAUNCH_CK();
 }
 
@@ -1292,7 +1330,7 @@ class UmmaEngine final : public Engine {
         if (!scattered) {
             dim3 grid((unsigned)std::min<long>((k_ + 255) / 256, 1024), C_);
             ProfScope ps("scatter", s);
-            k_scatter_plan<float><<<grid, 256, 0, s>>>(q, k_, plan_);
+            launch_pdl(k_scatter_plan<float>, grid, dim3(256), 0, s, q, k_, plan_);
             HMC_LAUNCH_CK();
         }
         const NetDesc &nd = p_.net;
@@ -1305,9 +1343,8 @@ class UmmaEngine final : public Engine {
         {
             dim3 grid((unsigned)ntiles_, C_);
             ProfScope ps("first_fwd", s);
-            k_first_fwd<<<grid, 256, 0, s>>>(x_.as<float>(), dx_, (int)N_, w_, W0_.as<float>(), b0_.as<float>(),
-                                             A_[1]->as<__nv_bfloat16>());
-            HMC_LAUNCH_CK();
+            launch_pdl(k_first_fwd, grid, dim3(256), 0, s, x_.as<float>(), dx_, (int)N_, w_, W0_.as<float>(),
+                       b0_.as<float>(), A_[1]->as<__nv_bfloat16>());
         }
         if (use_layer_) {
             layers_persistent(s);
@@ -1363,32 +1400,10 @@ class UmmaEngine final : public Engine {
             }
         }
         }
-        // weight gradients of the hidden layers at the sampled entries
-        for (int i = 1; i <= L_ - 2; ++i) {
-            if (layer_entries_[i] == 0) continue;
-            Params pp = base;
-            pp.M = w_;
-            pp.N = w_;
-            pp.K = (int)N_;
-            const int total_kb = (int)((N_ + BK - 1) / BK);
-            pp.kb_per_split = (total_kb + nsplit_ - 1) / nsplit_;
-            pp.rowptr = rowptr_[i]->as<int>();
-            pp.ecol = ecol_.as<int>();
-            pp.erow = erow_.as<int>();
-            pp.epack = epack_.as<int>();
-            pp.gw_part = gw_part_.as<float>();
-            pp.gw_split = (long)C_ * k_;
-            pp.gw_b = k_;
-            if (use_layer_) {
-                pp.kb_per_split = (total_kb + nsplit2_ - 1) / nsplit2_;
-                const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
-                launch_dw2(D_atom_[i + 1], A_atom_[i], pp, dim3(1, splits, C_), s);
-            } else {
-                const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
-                dim3 grid((w_ + BM - 1) / BM, splits, C_);
-                launch_umma<M_DW, true, true, false>(D_atom_[i + 1], A_atom_[i], A_atom_[i], pp, grid, s);
-            }
-        }
+        // weight gradients of the hidden layers at the sampled entries (the persistent path
+        // launches each one next to the reverse kernel that reads the same delta)
+        if (!use_layer_)
+            for (int i = 1; i <= L_ - 2; ++i) dw_layer(i, s);
         FinalArgs fa{};
         fa.k = (int)k_;
         fa.ntiles = ntiles_;
@@ -1410,12 +1425,43 @@ class UmmaEngine final : public Engine {
         {
             ProfScope ps("finalize", s);
             dim3 grid((unsigned)((k_ + 255) / 256 + 1), C_);
-            k_finalize_bf16<<<grid, 256, 0, s>>>(fa, q, U, g);
+            launch_pdl(k_finalize_bf16, grid, dim3(256), 0, s, fa, q, U, g);
             HMC_LAUNCH_CK();
         }
     }
 
   private:
+    // weight gradient of hidden layer i (dW = delta_{i+1}^T A_i) at its sampled entries
+    void dw_layer(int i, cudaStream_t s)
+    {
+        if (layer_entries_[i] == 0) return;
+        Params base{};
+        base.err = err_;
+        base.ntiles = ntiles_;
+        Params pp = base;
+        pp.M = w_;
+        pp.N = w_;
+        pp.K = (int)N_;
+        const int total_kb = (int)((N_ + BK - 1) / BK);
+        pp.kb_per_split = (total_kb + nsplit_ - 1) / nsplit_;
+        pp.rowptr = rowptr_[i]->as<int>();
+        pp.ecol = ecol_.as<int>();
+        pp.erow = erow_.as<int>();
+        pp.epack = epack_.as<int>();
+        pp.gw_part = gw_part_.as<float>();
+        pp.gw_split = (long)C_ * k_;
+        pp.gw_b = k_;
+        if (use_layer_) {
+            pp.kb_per_split = (total_kb + nsplit2_ - 1) / nsplit2_;
+            const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
+            launch_dw2(D_atom_[i + 1], A_atom_[i], pp, dim3(1, splits, C_), s);
+        } else {
+            const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
+            dim3 grid((w_ + BM - 1) / BM, splits, C_);
+            launch_umma<M_DW, true, true, false>(D_atom_[i + 1], A_atom_[i], A_atom_[i], pp, grid, s);
+        }
+    }
+
     // forward and reverse hidden layers on the persistent cluster kernel
     void layers_persistent(cudaStream_t s)
     {
@@ -1448,8 +1494,10 @@ class UmmaEngine final : public Engine {
                 launch_layer<L_FWD_OUT>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
             }
         }
-        // reverse pass (bf16 W: the lo part is not needed there)
+        // reverse pass (bf16 W: the lo part is not needed there); the weight gradient of
+        // layer i runs first, while the delta written by the previous kernel is still in L2
         for (int i = L_ - 2; i >= 1; --i) {
+            dw_layer(i, s);
             if (i <= nd.lmin) break;
             LayerParams lp = base;
             lp.aux = A_[i]->as<__nv_bfloat16>();

@@ -114,11 +114,11 @@ struct TrajState {
     double *dH;
 };
 
+// Write q into the network buffer b at offset o of chain c (bf16 hi/lo pair or plain).
 template <typename T>
-__device__ __forceinline__ void scatter_one(const ScatterPlan &sc, long c, long j, T q)
+__device__ __forceinline__ void scatter_at(const ScatterPlan &sc, long c, int b, long off, T q)
 {
-    const int b = sc.buf_id ? (int)sc.buf_id[j] : 0;
-    const long o = c * sc.cstride[b] + (long)sc.off[j];
+    const long o = c * sc.cstride[b] + off;
     if (sc.is_bf16[b]) {
         const __nv_bfloat16 hi = __float2bfloat16_rn((float)q);
         reinterpret_cast<__nv_bfloat16 *>(sc.base[b])[o] = hi;
@@ -127,6 +127,12 @@ __device__ __forceinline__ void scatter_one(const ScatterPlan &sc, long c, long 
     } else {
         reinterpret_cast<T *>(sc.base[b])[o] = q;
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void scatter_one(const ScatterPlan &sc, long c, long j, T q)
+{
+    scatter_at<T>(sc, c, sc.buf_id ? (int)sc.buf_id[j] : 0, (long)sc.off[j], q);
 }
 
 __device__ __forceinline__ double seg_sum(double v, double *sm)
@@ -211,17 +217,37 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_kick_drift(const SegDesc *segs
     const long base = sd.qoff + (long)c * sd.k;
     const T kk = (T)kick, dd = (T)drift;
     const long j0 = (long)blockIdx.x * TRAJ_ELEMS;
+    // every load of the thread's four coordinates first, then the dependent updates
+    T pv[4], gv[4], qv[4];
+    int bv[4];
+    long ov[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const long j = j0 + threadIdx.x + (long)t * TRAJ_THREADS;
+        pv[t] = gv[t] = qv[t] = (T)0;
+        bv[t] = 0;
+        ov[t] = 0;
+        if (j < sd.k) {
+            pv[t] = p[base + j];
+            if (kick != 0.0) gv[t] = g[base + j];
+            if (drift != 0.0) {
+                qv[t] = q[base + j];
+                bv[t] = sd.sc.buf_id ? (int)sd.sc.buf_id[j] : 0;
+                ov[t] = (long)sd.sc.off[j];
+            }
+        }
+    }
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         const long j = j0 + threadIdx.x + (long)t * TRAJ_THREADS;
         if (j >= sd.k) break;
-        T pj = p[base + j];
-        if (kick != 0.0) pj = pj - kk * g[base + j];
+        T pj = pv[t];
+        if (kick != 0.0) pj = pj - kk * gv[t];
         p[base + j] = pj;
         if (drift != 0.0) {
-            const T qj = q[base + j] + dd * pj;
+            const T qj = qv[t] + dd * pj;
             q[base + j] = qj;
-            scatter_one<T>(sd.sc, c, j, qj);
+            scatter_at<T>(sd.sc, c, bv[t], ov[t], qj);
         }
     }
 }

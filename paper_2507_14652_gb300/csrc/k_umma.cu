@@ -64,7 +64,9 @@ struct Params {
     double *u_part;                       // [b][ntiles]
     float *dbout_part;                    // [b][ntiles]
     float *dwout_part;                    // [b][ntiles][N]
-    float *db_part;                       // [b][ntiles][N] column sums of the produced delta
+    float *db_part;                       // [b][ntiles][N] column sums of the produced delta;
+                                          // k_dw2: [split][b][M] row sums of delta, split stride db_split
+    long db_split;
     const float *x; int dx;               // M_BWD_FIRST: inputs [M][dx]
     float *dw0_part;                      // [b][ntiles][N][dx]
     const int *rowptr;                    // M_DW: entries of output row o are [rowptr[o], rowptr[o+1])
@@ -382,7 +384,7 @@ constexpr int L_STAGES = 4;
 constexpr int L_A_BYTES = BM * BK * 2;                  // one 16 KB K-block of a 128-row tile
 constexpr int L_W_HALF = 64 * 1024;                     // resident half of W, hi or lo (4 K-blocks x 16 KB)
 constexpr int L_STG = 2048;                             // staging bytes per epilogue warp (32 rows x 64 B)
-constexpr int L_SCR_FLOATS = 2 * 4 * 256 + 8 * L_STG / 4;   // forward: [2][4][w] column sums + staging
+constexpr int L_SCR_FLOATS = 4 * 256 + 8 * L_STG / 4;       // forward: [4][w] column sums + staging
 constexpr int L_BWD_STG_OFF = 9 * 4 * 256 * 4;          // reverse: [1 + dx][4][w] sums (dx <= 8) in the free lo region, then staging
 constexpr int L_SMEM = 1024 + 2 * L_W_HALF + L_STAGES * L_A_BYTES + 256 + L_SCR_FLOATS * 4 + 64 + 64 +
                        2 * 256 * 4 + 2 * 128 * 4;        // + bias and output weights of the chain, half-row sums
@@ -435,7 +437,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * L_STAGES + 7);
     float *scr = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(bars) + 256);
     float *red = BWD ? reinterpret_cast<float *>(sWl) : scr;                          // column sums
-    uint8_t *stage0 = BWD ? sWl + L_BWD_STG_OFF : reinterpret_cast<uint8_t *>(scr + 2 * 4 * 256);
+    uint8_t *stage0 = BWD ? sWl + L_BWD_STG_OFF : reinterpret_cast<uint8_t *>(scr + 4 * 256);
     double *dred = reinterpret_cast<double *>(scr + L_SCR_FLOATS);   // [4]
     float *fred = reinterpret_cast<float *>(dred + 4);               // [4]
     float *sbias = fred + 16;                                        // [256] bias of the current chain
@@ -684,29 +686,30 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     } else {
                         __syncwarp();          // slope reads done before the next chunk's pieces land
                     }
-                    if (MODE == L_BWD_FIRST) {
+                    if (MODE == L_BWD_FIRST) {   // first-layer weight and bias gradients: column sums
                         for (int d = 0; d < p.dx; ++d) {
                             float tv[32];
 #pragma unroll
                             for (int j = 0; j < 32; ++j) tv[j] = dd[j] * xv[d];
                             red[((1 + d) * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(tv);
                         }
+                        red[(0 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dd);
                     }
-                    red[(0 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dd);
                 }
-                named_bar_sync(1, 256);
-                if (tile_ok) {
-                    for (int cc = et; cc < LN; cc += 256) {
-                        p.db_part[part + cc] = red[(0 * 4 + 0) * LN + cc] + red[(0 * 4 + 1) * LN + cc] +
-                                               red[(0 * 4 + 2) * LN + cc] + red[(0 * 4 + 3) * LN + cc];
-                        if (MODE == L_BWD_FIRST)
+                if (MODE == L_BWD_FIRST) {
+                    named_bar_sync(1, 256);
+                    if (tile_ok) {
+                        for (int cc = et; cc < LN; cc += 256) {
+                            p.db_part[part + cc] = red[(0 * 4 + 0) * LN + cc] + red[(0 * 4 + 1) * LN + cc] +
+                                                   red[(0 * 4 + 2) * LN + cc] + red[(0 * 4 + 3) * LN + cc];
                             for (int d = 0; d < p.dx; ++d)
                                 p.dw0_part[(part + cc) * p.dx + d] =
                                     red[((1 + d) * 4 + 0) * LN + cc] + red[((1 + d) * 4 + 1) * LN + cc] +
                                     red[((1 + d) * 4 + 2) * LN + cc] + red[((1 + d) * 4 + 3) * LN + cc];
+                        }
                     }
+                    named_bar_sync(1, 256);
                 }
-                named_bar_sync(1, 256);
             } else if (MODE == L_FWD_OUT) {
                 float fh = 0.0f;
                 tmem_ld32_issue(taddr, rb[0]);
@@ -756,16 +759,12 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
                     store_chunk(pk, c0);
                     red[(0 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dw);
-                    red[(1 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dd);
                 }
                 named_bar_sync(1, 256);
                 if (tile_ok) {
-                    for (int cc = et; cc < LN; cc += 256) {
+                    for (int cc = et; cc < LN; cc += 256)
                         p.dwout_part[part + cc] = red[(0 * 4 + 0) * LN + cc] + red[(0 * 4 + 1) * LN + cc] +
                                                   red[(0 * 4 + 2) * LN + cc] + red[(0 * 4 + 3) * LN + cc];
-                        p.db_part[part + cc] = red[(1 * 4 + 0) * LN + cc] + red[(1 * 4 + 1) * LN + cc] +
-                                               red[(1 * 4 + 2) * LN + cc] + red[(1 * 4 + 3) * LN + cc];
-                    }
                     if (et == 0) {
                         p.u_part[(long)c * p.ntiles + t] = dred[0] + dred[1] + dred[2] + dred[3];
                         p.dbout_part[(long)c * p.ntiles + t] = fred[0] + fred[1] + fred[2] + fred[3];
@@ -797,34 +796,40 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(L_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradient of a w x w hidden layer at the sampled entries, one CTA per
-// (row split, chain): dW = delta^T A over the CTA's rows, with both operands read
-// MN-major straight from their row-major [rows][w] arrays.  The CTA covers all w
-// output rows of dW as two M = 128 accumulators that share every B stage, so each
-// byte of delta and A is loaded once.  Only the sampled entries leave the chip.
+// Weight and bias gradient of a w x w hidden layer at the sampled entries.
+// CTA (mh, nh) of a (row split, chain) computes the 128 x 128 block
+// dW[m0 : m0+128][n0 : n0+128] = delta^T A over its rows, both operands read
+// MN-major straight from their row-major [rows][w] arrays.  The CTAs with n0 = 0
+// also multiply delta^T by a 16-column block of ones, which sums delta over the rows:
+// the gradient of the layer's bias, from the same operand stages.  Only the sampled
+// entries leave the chip.  Two CTAs fit on an SM (shared and tensor memory).
 // ---------------------------------------------------------------------------
 constexpr int DW_STAGES = 3;
-constexpr int DW_A_BYTES = 2 * BM * BK * 2;    // 32 KB: delta, 256 output rows x 64 data rows
-constexpr int DW_B_BYTES = 256 * BK * 2;       // 32 KB: A_i, 256 columns x 64 data rows
+constexpr int DW_A_BYTES = BM * BK * 2;        // 16 KB: delta, 128 output features x 64 data rows
+constexpr int DW_B_BYTES = 128 * BK * 2;       // 16 KB: A_i, 128 input features x 64 data rows
 constexpr int DW_STAGE = DW_A_BYTES + DW_B_BYTES;
-constexpr int DW_SMEM = 1024 + DW_STAGES * DW_STAGE + 256;
+constexpr int DW_ONES = 16 * 128;              // 16 K-major rows of 64 bf16 ones
+constexpr int DW_SMEM = 1024 + DW_STAGES * DW_STAGE + DW_ONES + 256;
+constexpr int DW_TCOLS = 256;                  // 128 columns of dW + 16 of row sums
+static_assert(DW_STAGES * DW_STAGE >= 128 * 129 * 4, "the epilogue staging reuses the operand stages");
 
-__global__ void __launch_bounds__(NTHREADS, 1) k_dw2(const __grid_constant__ CUtensorMap tmD,
+__global__ void __launch_bounds__(NTHREADS, 2) k_dw2(const __grid_constant__ CUtensorMap tmD,
                                                      const __grid_constant__ CUtensorMap tmA, const Params p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + DW_STAGES * DW_STAGE);
+    uint8_t *ones = smem + DW_STAGES * DW_STAGE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ones + DW_ONES);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * DW_STAGES + 1);
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * DW_STAGES, accb = empty0 + 8 * DW_STAGES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int split = blockIdx.y, b = blockIdx.z;
-    const int BN = p.N;    // A_i columns (w)
-    const int MW = p.M;    // output rows of dW (w)
+    const int nnh = p.N / 128;                // column blocks of dW (w / 128)
+    const int m0 = (blockIdx.x / nnh) * BM, n0 = (blockIdx.x % nnh) * 128;
+    const bool with_db = n0 == 0 && p.db_part != nullptr;
     const int total_kb = (p.K + BK - 1) / BK;
     const int kb0 = split * p.kb_per_split;
     const int nkb = min(p.kb_per_split, total_kb - kb0);
-    const int nmh = (MW + BM - 1) / BM;     // 1 or 2 accumulators
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < DW_STAGES; ++s) {
@@ -836,8 +841,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dw2(const __grid_constant__ CUt
         prefetch_map(&tmD);
         prefetch_map(&tmA);
     }
+    for (int i = threadIdx.x; i < DW_ONES / 4; i += blockDim.x)   // bf16 1.0 pairs
+        reinterpret_cast<uint32_t *>(ones)[i] = 0x3F803F80u;
+    fence_proxy_async_smem();   // the tensor core reads what the threads wrote
     if (warp == 1) {
-        tmem_alloc(smem_u32(tmem_slot), 512);
+        tmem_alloc(smem_u32(tmem_slot), DW_TCOLS);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -850,19 +858,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dw2(const __grid_constant__ CUt
     if (warp == 0) {
         if (lane == 0) {
             int issued = 0;
-            const uint32_t bytes = (uint32_t)(nmh * BM * BK * 2 + BN * BK * 2);
             for (int i = 0; i < nkb; ++i) {
                 const int s = i % DW_STAGES;
                 const uint32_t ph = (uint32_t)(i / DW_STAGES) & 1u;
                 if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.err)) { ok = false; break; }
                 const uint32_t fb = full0 + 8 * s;
-                mbar_expect_tx(fb, bytes);
+                mbar_expect_tx(fb, DW_STAGE);
                 const uint32_t sa = smem_u32(smem + s * DW_STAGE), sb = sa + DW_A_BYTES;
                 const int kc = (kb0 + i) * BK;
-                for (int mh = 0; mh < nmh; ++mh)
-                    for (int a = 0; a < 2; ++a)
-                        tma_load_3d(sa + (mh * 2 + a) * 8192, &tmD, mh * BM + 64 * a, kc, b, fb);
-                for (int a = 0; a < BN / 64; ++a) tma_load_3d(sb + 8192 * a, &tmA, 64 * a, kc, b, fb);
+                for (int a = 0; a < 2; ++a) {
+                    tma_load_3d(sa + 8192 * a, &tmD, m0 + 64 * a, kc, b, fb);
+                    tma_load_3d(sb + 8192 * a, &tmA, n0 + 64 * a, kc, b, fb);
+                }
                 ++issued;
             }
             if (!ok)
@@ -871,7 +878,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dw2(const __grid_constant__ CUt
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(BM, BN, true, true);
+            const uint32_t idesc = idesc_bf16(BM, 128, true, true);
+            const uint32_t idesc1 = idesc_bf16(BM, 16, true, false);
+            const uint32_t so = smem_u32(ones);
             for (int i = 0; i < nkb; ++i) {
                 const int s = i % DW_STAGES;
                 const uint32_t ph = (uint32_t)(i / DW_STAGES) & 1u;
@@ -880,11 +889,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dw2(const __grid_constant__ CUt
                 const uint32_t sa = smem_u32(smem + s * DW_STAGE), sb = sa + DW_A_BYTES;
 #pragma unroll
                 for (int ks = 0; ks < BK / 16; ++ks) {
-                    const uint64_t bd = sdesc(sb + 2048 * ks, 8192, 1024);
-                    for (int mh = 0; mh < nmh; ++mh) {
-                        const uint64_t ad = sdesc(sa + mh * 16384 + 2048 * ks, 8192, 1024);
-                        mma_bf16(tmem + (uint32_t)(mh * 256), ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
-                    }
+                    const uint64_t ad = sdesc(sa + 2048 * ks, 8192, 1024);
+                    const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
+                    mma_bf16(tmem, ad, sdesc(sb + 2048 * ks, 8192, 1024), idesc, acc);
+                    if (with_db) mma_bf16(tmem + 128, ad, sdesc(so + 32 * ks, 0, 1024), idesc1, acc);
                 }
                 mma_commit(empty0 + 8 * s);
             }
@@ -892,41 +900,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dw2(const __grid_constant__ CUt
         }
     } else {
         const int q = warp & 3, row = 32 * q + lane, et = threadIdx.x - 64;
-        ok = mbar_wait(accb, 0, p.err);
+        ok = nkb > 0 && mbar_wait(accb, 0, p.err);
         tc_fence_after();
         if (ok) {
-            float *stg = reinterpret_cast<float *>(smem);   // operand buffers are idle now
-            for (int mh = 0; mh < nmh; ++mh) {
-                const int m0 = mh * BM;
-                const int r_end = min(m0 + BM, MW);
-                const int j0 = p.rowptr[m0], j1 = p.rowptr[r_end];
-                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(mh * 256);
-                for (int h0 = 0; h0 < BN; h0 += 128) {
-                    const int hc = min(128, BN - h0);
-                    for (int c0 = 0; c0 < hc; c0 += 32) {
-                        float v[32];
-                        tmem_ld32(taddr + h0 + c0, v);
+            float *stg = reinterpret_cast<float *>(smem);   // operand stages are idle now
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16);
+            if (with_db) {   // every column of the ones product holds the row sum
+                float v[32];
+                tmem_ld32(taddr + 128, v);
+                if (m0 + row < p.M) p.db_part[(long)split * p.db_split + (long)b * p.M + m0 + row] = v[0];
+            }
+            for (int c0 = 0; c0 < 128; c0 += 32) {
+                float v[32];
+                tmem_ld32(taddr + c0, v);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) stg[row * 129 + c0 + j] = v[j];
-                    }
-                    named_bar_sync(1, 128);
-                    // eight index loads in flight per thread before any dependent access
-                    float *dst = p.gw_part + (long)split * p.gw_split + (long)b * p.gw_b;
-                    for (int base = j0; base < j1; base += 128 * 8) {
-                        int e[8];
+                for (int j = 0; j < 32; ++j) stg[row * 129 + c0 + j] = v[j];
+            }
+            named_bar_sync(1, 128);
+            // eight index loads in flight per thread before any dependent access
+            const int j0 = p.rowptr[m0], j1 = p.rowptr[min(m0 + BM, p.M)];
+            float *dst = p.gw_part + (long)split * p.gw_split + (long)b * p.gw_b;
+            for (int base = j0; base < j1; base += 128 * 8) {
+                int e[8];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const int j = base + et + 128 * u;
-                            e[u] = j < j1 ? p.epack[j] : -1;
-                        }
+                for (int u = 0; u < 8; ++u) {
+                    const int j = base + et + 128 * u;
+                    e[u] = j < j1 ? p.epack[j] : -1;
+                }
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            if (e[u] < 0) continue;
-                            const int c = (e[u] & 0xFFFF) - h0;
-                            if (c >= 0 && c < hc) dst[base + et + 128 * u] = stg[((e[u] >> 16) - m0) * 129 + c];
-                        }
-                    }
-                    named_bar_sync(1, 128);
+                for (int u = 0; u < 8; ++u) {
+                    if (e[u] < 0) continue;
+                    const int c = (e[u] & 0xFFFF) - n0;
+                    if (c >= 0 && c < 128) dst[base + et + 128 * u] = stg[((e[u] >> 16) - m0) * 129 + c];
                 }
             }
         }
@@ -935,7 +940,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_dw2(const __grid_constant__ CUt
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 512);
+        tmem_dealloc(tmem, DW_TCOLS);
     }
 }
 
@@ -991,13 +996,21 @@ __global__ void __launch_bounds__(256) k_first_fwd(const float *x, int dx, int N
 // Per-entry source of the gradient, decoded by k_finalize_bf16.
 enum EntryKind { E_HIDDEN_W = 0, E_BIAS = 1, E_W0 = 2, E_WOUT = 3, E_BOUT = 4 };
 
+// Partial sums of one layer's bias gradient: entry (chain b, partial t, unit o) is at
+// p[b * bstride + t * tstride + o], t < n.
+struct DbDesc {
+    const float *p;
+    long bstride, tstride;
+    int n;
+};
+
 struct FinalArgs {
     int k, ntiles, nsplit, w, dx;
     const int *kind, *layer, *off;   // per entry
     const double *u_part;            // [b][ntiles]
     const float *gw_part;            // [split][b][k]
     long gw_split;
-    const float *const *db_part;     // per bias layer: [b][ntiles][w]
+    const DbDesc *db;                // per bias layer: where its partial sums live
     const float *dw0_part;           // [b][ntiles][w][dx]
     const float *dwout_part;         // [b][ntiles][w]
     const float *dbout_part;         // [b][ntiles]
@@ -1049,7 +1062,8 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
     if (kd == E_HIDDEN_W) {
         dp = a.gw_part + (long)b * a.k + j, stride = a.gw_split, n = a.nsplit;
     } else if (kd == E_BIAS) {
-        dp = a.db_part[a.layer[j]] + (long)b * a.ntiles * a.w + off, stride = a.w, n = a.ntiles;
+        const DbDesc d = a.db[a.layer[j]];
+        dp = d.p + (long)b * d.bstride + off, stride = d.tstride, n = d.n;
     } else if (kd == E_W0) {
         dp = a.dw0_part + (long)b * a.ntiles * a.w * a.dx + off, stride = (long)a.w * a.dx, n = a.ntiles;
     } else if (kd == E_WOUT) {
@@ -1275,12 +1289,9 @@ class UmmaEngine final : public Engine {
         dbout_part_.alloc(sizeof(float) * C * ntiles_);
         dwout_part_.alloc(sizeof(float) * C * ntiles_ * w_);
         dw0_part_.alloc(sizeof(float) * C * ntiles_ * w_ * dx_);
-        db_part_.resize(L_ - 1);   // biases of layers 0..L-2
+        db_part_.resize(L_ - 1);   // biases of layers 0..L-2, per-tile column sums
         for (int l = 0; l <= L_ - 2; ++l) db_part_[l].reset(new DevBuf(sizeof(float) * C * ntiles_ * w_));
-        std::vector<const float *> dbp(L_ - 1);
-        for (int l = 0; l <= L_ - 2; ++l) dbp[l] = db_part_[l]->as<float>();
-        db_ptrs_.alloc(sizeof(float *) * dbp.size());
-        HMC_CK(cudaMemcpy(db_ptrs_.ptr, dbp.data(), sizeof(float *) * dbp.size(), cudaMemcpyHostToDevice));
+        use_layer_ = (w_ == 128 || w_ == 256);
 
         // per-entry metadata, scatter plan, per-layer CSR of the sampled hidden weights
         build_entries();
@@ -1288,13 +1299,26 @@ class UmmaEngine final : public Engine {
         // split of the weight-gradient GEMMs over rows: about two CTAs per SM
         const int total_kb = (int)((N_ + BK - 1) / BK);
         nsplit_ = pick_splits(total_kb, ((w_ + BM - 1) / BM) * C, 2 * num_sms_);
-        nsplit2_ = pick_splits(total_kb, C, num_sms_);
+        nsplit2_ = pick_splits(total_kb, (w_ / 128) * (w_ / 128) * C, 2 * num_sms_);
         nsplit_ = std::max(nsplit_, nsplit2_);
         gw_part_.alloc(sizeof(float) * nsplit_ * C * std::max<long>(k_, 1));
         HMC_CK(cudaMemset(gw_part_.ptr, 0, gw_part_.n));
 
+        // bias gradients: the first layer's from its reverse kernel (per tile); the hidden
+        // layers' from the weight-gradient kernel (per row split) on the persistent path
+        std::vector<DbDesc> dbd(L_ - 1);
+        dbw_part_.resize(L_ - 1);
+        for (int l = 0; l <= L_ - 2; ++l) {
+            dbd[l] = DbDesc{db_part_[l]->as<float>(), (long)ntiles_ * w_, w_, ntiles_};
+            if (use_layer_ && l >= 1) {
+                dbw_part_[l].reset(new DevBuf(sizeof(float) * nsplit_eff() * C * w_));
+                dbd[l] = DbDesc{dbw_part_[l]->as<float>(), w_, (long)C * w_, nsplit_eff()};
+            }
+        }
+        db_desc_.alloc(sizeof(DbDesc) * dbd.size());
+        HMC_CK(cudaMemcpy(db_desc_.ptr, dbd.data(), sizeof(DbDesc) * dbd.size(), cudaMemcpyHostToDevice));
+
         // tensor maps
-        use_layer_ = (w_ == 128 || w_ == 256);
         if (use_layer_) max_clusters_ = layer_max_clusters();
         for (int i = 1; i <= L_ - 2; ++i) {
             A_row_[i] = make_map(A_[i]->ptr, w_, N_, C, 64, 128);
@@ -1416,7 +1440,7 @@ class UmmaEngine final : public Engine {
         fa.u_part = u_part_.as<double>();
         fa.gw_part = gw_part_.as<float>();
         fa.gw_split = (long)C_ * k_;
-        fa.db_part = db_ptrs_.as<const float *>();
+        fa.db = db_desc_.as<const DbDesc>();
         fa.dw0_part = dw0_part_.as<float>();
         fa.dwout_part = dwout_part_.as<float>();
         fa.dbout_part = dbout_part_.as<float>();
@@ -1434,7 +1458,7 @@ class UmmaEngine final : public Engine {
     // weight gradient of hidden layer i (dW = delta_{i+1}^T A_i) at its sampled entries
     void dw_layer(int i, cudaStream_t s)
     {
-        if (layer_entries_[i] == 0) return;
+        if (layer_entries_[i] == 0 && !(use_layer_ && bias_entries_[i] > 0)) return;
         Params base{};
         base.err = err_;
         base.ntiles = ntiles_;
@@ -1454,7 +1478,9 @@ class UmmaEngine final : public Engine {
         if (use_layer_) {
             pp.kb_per_split = (total_kb + nsplit2_ - 1) / nsplit2_;
             const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
-            launch_dw2(D_atom_[i + 1], A_atom_[i], pp, dim3(1, splits, C_), s);
+            pp.db_part = dbw_part_[i]->as<float>();
+            pp.db_split = (long)C_ * w_;
+            launch_dw2(D_atom_[i + 1], A_atom_[i], pp, dim3((w_ / 128) * (w_ / 128), splits, C_), s);
         } else {
             const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
             dim3 grid((w_ + BM - 1) / BM, splits, C_);
@@ -1490,7 +1516,6 @@ class UmmaEngine final : public Engine {
                 lp.u_part = u_part_.as<double>();
                 lp.dbout_part = dbout_part_.as<float>();
                 lp.dwout_part = dwout_part_.as<float>();
-                lp.db_part = db_part_[L_ - 2]->as<float>();
                 launch_layer<L_FWD_OUT>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
             }
         }
@@ -1501,11 +1526,11 @@ class UmmaEngine final : public Engine {
             if (i <= nd.lmin) break;
             LayerParams lp = base;
             lp.aux = A_[i]->as<__nv_bfloat16>();
-            lp.db_part = db_part_[i - 1]->as<float>();
             if (i > 1) {
                 lp.out = D_[i]->as<__nv_bfloat16>();
                 launch_layer<L_BWD_TANH>(D_row_[i + 1], W_atom_[i], W_atom_[i], lp, ncta, s);
             } else {
+                lp.db_part = db_part_[0]->as<float>();
                 lp.x = x_.as<float>();
                 lp.dw0_part = dw0_part_.as<float>();
                 launch_layer<L_BWD_FIRST>(D_row_[i + 1], W_atom_[i], W_atom_[i], lp, ncta, s);
@@ -1550,6 +1575,7 @@ class UmmaEngine final : public Engine {
         std::vector<int> kind(k_), layer(k_), off(k_), erow(k_, 0), ecol(k_, 0), bid(k_), boff(k_);
         std::vector<std::vector<int>> rp(L_, std::vector<int>(w_ + 1, 0));
         layer_entries_.assign(L_, 0);
+        bias_entries_.assign(L_, 0);
         // scatter buffers: 0 W0, 1 b0, 2+2(i-1) W_i (bf16), 3+2(i-1) b_i, then wout, bout
         const int nh = L_ - 2;
         plan_.nbuf = 2 + 2 * nh + 2;
@@ -1598,6 +1624,7 @@ class UmmaEngine final : public Engine {
                     kind[j] = E_BIAS;
                     layer[j] = l;
                     off[j] = (int)rel;
+                    bias_entries_[l]++;
                     bid[j] = 3 + 2 * (l - 1);
                 }
                 boff[j] = (int)rel;
@@ -1638,10 +1665,10 @@ class UmmaEngine final : public Engine {
     int C_, L_ = 0, w_ = 0, dx_ = 0, ntiles_ = 1, nsplit_ = 1, nsplit2_ = 1, num_sms_ = 148;
     long N_ = 0, k_ = 0;
     int *err_ = nullptr;
-    DevBuf x_, y_, W0_, b0_, wout_, bout_, u_part_, dbout_part_, dwout_part_, dw0_part_, db_ptrs_, gw_part_;
+    DevBuf x_, y_, W0_, b0_, wout_, bout_, u_part_, dbout_part_, dwout_part_, dw0_part_, db_desc_, gw_part_;
     DevBuf kind_, layer_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_;
-    std::vector<std::unique_ptr<DevBuf>> Wh_, Wl_, bh_, A_, D_, db_part_, rowptr_;
-    std::vector<int> layer_entries_;
+    std::vector<std::unique_ptr<DevBuf>> Wh_, Wl_, bh_, A_, D_, db_part_, dbw_part_, rowptr_;
+    std::vector<int> layer_entries_, bias_entries_;
     CUtensorMap A_row_[MAXL], A_atom_[MAXL], W_fwd_[MAXL], W_atom_[MAXL], W_fwd_lo_[MAXL], W_atom_lo_[MAXL];
     CUtensorMap D_row_[MAXL], D_atom_[MAXL], W_half_hi_[MAXL], W_half_lo_[MAXL];
     bool use_layer_ = false;

@@ -132,6 +132,23 @@ def run_reference(args):
     return 0
 
 
+def _traffic(kernel):
+    """DRAM bytes per launch of a bench kernel from the committed ncu capture, or None
+    when there is none or the kernel source changed since it was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+        if not rec:
+            return None
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
+                return None
+        return float(rec["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def algorithmic(prob, C):
     """Per-launch algorithmic FLOPs and DRAM bytes of each tensor-core kernel kind."""
     N, w = prob.x.shape[0], prob.net.widths[1]
@@ -227,7 +244,7 @@ def main():
         if t_hbm >= t_tc:
             ach = by / (t_ms / 1e3) / 1e9
             roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                    "frac": ach / peaks["hbm_gbs"], "traffic": _traffic(dom),
                     "peak_source": peak_src + " (hbm_gbs)"}
         else:
             ach = fl / (t_ms / 1e3) / 1e12

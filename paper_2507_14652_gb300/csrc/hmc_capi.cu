@@ -619,11 +619,12 @@ hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, co
         else if (prec == HMC_PREC_FP32) e = make_simt_engine_f32(p, C);
         else if (prec == HMC_PREC_BF16) {
             std::string why;
-            if (!umma_engine_supports(p, &why)) {
+            const bool don = p.kind == HMC_NET_DEEPONET;
+            if (!(don ? don_engine_supports(p, &why) : umma_engine_supports(p, &why))) {
                 set_error("BF16 tensor-core path does not support this network: %s", why.c_str());
                 throw Fail{HMC_ERR_UNSUPPORTED};
             }
-            e = make_umma_engine_bf16(p, C);
+            e = don ? make_don_engine_bf16(p, C) : make_umma_engine_bf16(p, C);
         } else {
             set_error("HMC_PREC_TF32 is not implemented");
             throw Fail{HMC_ERR_UNSUPPORTED};

@@ -112,6 +112,8 @@ Engine *make_simt_engine_f64(Problem &p, int C);
 Engine *make_simt_engine_f32(Problem &p, int C);
 Engine *make_umma_engine_bf16(Problem &p, int C);
 bool umma_engine_supports(const Problem &p, std::string *why);
+Engine *make_don_engine_bf16(Problem &p, int C);
+bool don_engine_supports(const Problem &p, std::string *why);
 
 // Programmatic dependent launch.  A kernel started with launch_pdl may begin while
 // the previous kernel in its stream drains: it runs pdl_wait() before it touches any

@@ -45,7 +45,17 @@ constexpr int RED_BYTES = 3 * 4 * 256 * 4 + 4 * 8 + 4 * 4 + 64;   // [3][4][256]
 __host__ __device__ constexpr int stage_bytes(bool wsplit) { return A_STAGE_BYTES + B_STAGE_BYTES * (wsplit ? 2 : 1); }
 __host__ __device__ constexpr int smem_bytes(bool wsplit) { return 1024 + STAGES * stage_bytes(wsplit) + 256 + RED_BYTES; }
 
-enum Mode { M_STORE_F32 = 0, M_FWD_TANH = 1, M_FWD_OUT = 2, M_BWD_TANH = 3, M_BWD_FIRST = 4, M_DW = 5 };
+enum Mode {
+    M_STORE_F32 = 0,   // out_f32 = A B^T
+    M_FWD_TANH = 1,    // out = bf16(tanh(A W^T + b))
+    M_FWD_OUT = 2,     // last hidden layer + scalar output layer + residual
+    M_BWD_TANH = 3,    // out = bf16((A B^T) (1 - aux^2)), column sums
+    M_BWD_FIRST = 4,   // as M_BWD_TANH, fused with the first layer's weight and bias sums
+    M_DW = 5,          // sampled entries of A^T B
+    M_FWD_LIN = 6,     // out = bf16(A W^T + b), no activation (a linear last layer)
+    M_S = 7,           // operator output S = B T^T on 128 x N tiles: residual, energy, dS
+    M_GEMM_BF16 = 8    // out = bf16(A B^T), column sums
+};
 
 struct Params {
     int M, N, K;           // per-batch GEMM: out[M][N] = sum_k A(m,k) B(n,k)
@@ -74,6 +84,11 @@ struct Params {
     const int *erow;                      // M_DW: row of entry j
     const int *epack;                     // row << 16 | column of entry j (dW gather)
     float *gw_part; long gw_split; long gw_b;   // M_DW: [split][b][k]
+    // M_S: targets Yt [M][ny] (shared by the chains), valid columns ny, output row
+    // stride ldo, per-chain scalar bias b0s [b]; partials per (row tile, column tile)
+    const float *Yt; int ny, ldo, ntn;
+    const float *b0s;
+    float *db0_part;                      // [b][ntiles][ntn]
 };
 
 template <int MODE, bool A_MN, bool B_MN, bool WSPLIT>
@@ -90,7 +105,9 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m_tile = blockIdx.x, split = blockIdx.y, b = blockIdx.z;
+    const int m_tile = blockIdx.x, b = blockIdx.z;
+    const int split = MODE == M_S ? 0 : blockIdx.y;          // M_S: grid.y walks column tiles
+    const int n0 = MODE == M_S ? blockIdx.y * p.N : 0;
     const int m0 = m_tile * BM;
     const int BN = p.N;
     const int total_kb = (p.K + BK - 1) / BK;
@@ -137,8 +154,8 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                     tma_load_3d(sa + 8192, &tmA, m0 + 64, kc, b, fb);
                 }
                 if (!B_MN) {
-                    tma_load_3d(sb, &tmB, kc, 0, b, fb);
-                    if (WSPLIT) tma_load_3d(sb + B_STAGE_BYTES, &tmB2, kc, 0, b, fb);
+                    tma_load_3d(sb, &tmB, kc, n0, b, fb);
+                    if (WSPLIT) tma_load_3d(sb + B_STAGE_BYTES, &tmB2, kc, n0, b, fb);
                 } else {
                     for (int a = 0; a < BN / 64; ++a) {
                         tma_load_3d(sb + 8192 * a, &tmB, 64 * a, kc, b, fb);
@@ -212,6 +229,96 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
                     }
+                }
+            } else if (MODE == M_FWD_LIN) {
+                const float *bias = p.bias + (long)b * p.bias_b;
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
+                    if (valid) {
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            pk[j] = pack_bf16(v[2 * j] + bias[c0 + 2 * j], v[2 * j + 1] + bias[c0 + 2 * j + 1]);
+                        uint4 *o = reinterpret_cast<uint4 *>(p.out + (long)b * p.out_b + (long)m * p.N + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    }
+                }
+            } else if (MODE == M_S) {
+                // r = S + b0 - Y; dS = r / sigma^2 in bf16; sum r^2 (FP64) and dS per tile
+                const float b0 = p.b0s[b];
+                const float *yrow = p.Yt + (long)(valid ? m : 0) * p.ny;
+                __nv_bfloat16 *orow = p.out + (long)b * p.out_b + (long)(valid ? m : 0) * p.ldo;
+                double r2 = 0.0;
+                float dsum = 0.0f;
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
+                    const int y0 = n0 + c0;
+                    if (valid && y0 < p.ny) {
+                        float ds[32], r2c = 0.0f;   // 32 squares in FP32, their sum carried in FP64
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const bool ok = y0 + j < p.ny;
+                            const float r = ok ? (v[j] + b0) - yrow[y0 + j] : 0.0f;
+                            r2c += r * r;
+                            ds[j] = r * p.inv_s2;
+                            dsum += ds[j];
+                        }
+                        r2 += (double)r2c;
+#pragma unroll
+                        for (int g8 = 0; g8 < 4; ++g8) {
+                            const int y = y0 + 8 * g8;
+                            if (y + 8 <= p.ny) {
+                                *reinterpret_cast<uint4 *>(orow + y) =
+                                    make_uint4(pack_bf16(ds[8 * g8], ds[8 * g8 + 1]), pack_bf16(ds[8 * g8 + 2], ds[8 * g8 + 3]),
+                                               pack_bf16(ds[8 * g8 + 4], ds[8 * g8 + 5]), pack_bf16(ds[8 * g8 + 6], ds[8 * g8 + 7]));
+                            } else {
+                                for (int e = 0; e < 8 && y + e < p.ny; ++e) orow[y + e] = __float2bfloat16_rn(ds[8 * g8 + e]);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+                    dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+                }
+                double *rd = reinterpret_cast<double *>(red + 3 * 4 * 256);
+                float *dsm = red + 3 * 4 * 256 + 8;
+                if (lane == 0) {
+                    rd[q] = r2;
+                    dsm[q] = dsum;
+                }
+                named_bar_sync(1, 128);
+                if (et == 0) {
+                    const long o = ((long)b * p.ntiles + m_tile) * p.ntn + blockIdx.y;
+                    p.u_part[o] = rd[0] + rd[1] + rd[2] + rd[3];
+                    p.db0_part[o] = dsm[0] + dsm[1] + dsm[2] + dsm[3];
+                }
+            } else if (MODE == M_GEMM_BF16) {
+                for (int c0 = 0; c0 < BN; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
+                    if (!valid) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = 0.0f;
+                    } else {
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
+                        uint4 *o = reinterpret_cast<uint4 *>(p.out + (long)b * p.out_b + (long)m * p.N + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+                    }
+                    red[(1 * 4 + q) * 256 + c0 + lane] = reduce_scatter32(v);
+                }
+                named_bar_sync(1, 128);
+                for (int c = et; c < BN; c += 128) {
+                    const long o = ((long)b * p.ntiles + m_tile) * p.N + c;
+                    p.db_part[o] = red[(1 * 4 + 0) * 256 + c] + red[(1 * 4 + 1) * 256 + c] +
+                                   red[(1 * 4 + 2) * 256 + c] + red[(1 * 4 + 3) * 256 + c];
                 }
             } else if (MODE == M_FWD_OUT) {
                 const float *bias = p.bias + (long)b * p.bias_b;
@@ -994,7 +1101,9 @@ __global__ void __launch_bounds__(256) k_first_fwd(const float *x, int dx, int N
 }
 
 // Per-entry source of the gradient, decoded by k_finalize_bf16.
-enum EntryKind { E_HIDDEN_W = 0, E_BIAS = 1, E_W0 = 2, E_WOUT = 3, E_BOUT = 4 };
+// E_GW: a weight entry gathered by a weight-gradient kernel ([split][b][k] partials);
+// E_PART: anything summed from per-tile column sums, found through a DbDesc.
+enum EntryKind { E_GW = 0, E_PART = 1 };
 
 // Partial sums of one layer's bias gradient: entry (chain b, partial t, unit o) is at
 // p[b * bstride + t * tstride + o], t < n.
@@ -1005,15 +1114,12 @@ struct DbDesc {
 };
 
 struct FinalArgs {
-    int k, ntiles, nsplit, w, dx;
-    const int *kind, *layer, *off;   // per entry
-    const double *u_part;            // [b][ntiles]
+    int k, nsplit, nu;               // entries, weight-gradient splits, energy partials per chain
+    const int *kind, *desc, *off;    // per entry
+    const double *u_part;            // [b][nu]
     const float *gw_part;            // [split][b][k]
     long gw_split;
-    const DbDesc *db;                // per bias layer: where its partial sums live
-    const float *dw0_part;           // [b][ntiles][w][dx]
-    const float *dwout_part;         // [b][ntiles][w]
-    const float *dbout_part;         // [b][ntiles]
+    const DbDesc *db;                // column-sum sources
     double half_inv_s2, inv_a2;
 };
 
@@ -1031,7 +1137,7 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
             const double qj = q[(long)b * a.k + j];
             pr += qj * qj;
         }
-        for (int i = threadIdx.x; i < a.ntiles; i += blockDim.x) lik += a.u_part[(long)b * a.ntiles + i];
+        for (int i = threadIdx.x; i < a.nu; i += blockDim.x) lik += a.u_part[(long)b * a.nu + i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             pr += __shfl_xor_sync(0xffffffffu, pr, o);
@@ -1055,21 +1161,14 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= a.k || !g) return;
     const float qj = q[(long)b * a.k + j];
-    const int kd = a.kind[j], off = a.off[j];
     const float *dp;
     long stride;
     int n;
-    if (kd == E_HIDDEN_W) {
+    if (a.kind[j] == E_GW) {
         dp = a.gw_part + (long)b * a.k + j, stride = a.gw_split, n = a.nsplit;
-    } else if (kd == E_BIAS) {
-        const DbDesc d = a.db[a.layer[j]];
-        dp = d.p + (long)b * d.bstride + off, stride = d.tstride, n = d.n;
-    } else if (kd == E_W0) {
-        dp = a.dw0_part + (long)b * a.ntiles * a.w * a.dx + off, stride = (long)a.w * a.dx, n = a.ntiles;
-    } else if (kd == E_WOUT) {
-        dp = a.dwout_part + (long)b * a.ntiles * a.w + off, stride = a.w, n = a.ntiles;
     } else {
-        dp = a.dbout_part + (long)b * a.ntiles, stride = 1, n = a.ntiles;
+        const DbDesc d = a.db[a.desc[j]];
+        dp = d.p + (long)b * d.bstride + a.off[j], stride = d.tstride, n = d.n;
     }
     // partials in index order, four independent loads in flight per step
     float s = 0.0f;
@@ -1162,8 +1261,9 @@ void launch_umma(const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &
         HMC_CK(cudaFuncSetAttribute(k_umma<MODE, A_MN, B_MN, WSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
         configured = true;
     }
-    static const char *names[] = {"umma_store_f32", "umma_fwd_tanh", "umma_fwd_out", "umma_bwd_tanh",
-                                  "umma_bwd_first", "umma_dw"};
+    static const char *names[] = {"umma_store_f32", "umma_fwd_tanh", "umma_fwd_out", "umma_bwd_tanh", "umma_bwd_first",
+                                  "umma_dw",        "umma_fwd_lin",  "umma_s",       "umma_gemm_bf16"};
+    static_assert(MODE >= 0 && MODE < (int)(sizeof(names) / sizeof(names[0])), "profile name");
     ProfScope ps(names[MODE], s);
     k_umma<MODE, A_MN, B_MN, WSPLIT><<<grid, NTHREADS, sm, s>>>(a, b, b2, p);
     HMC_LAUNCH_CK();
@@ -1306,7 +1406,8 @@ class UmmaEngine final : public Engine {
 
         // bias gradients: the first layer's from its reverse kernel (per tile); the hidden
         // layers' from the weight-gradient kernel (per row split) on the persistent path
-        std::vector<DbDesc> dbd(L_ - 1);
+        // descriptors 0..L-2: biases; L-1: first-layer weights; L: output weights; L+1: output bias
+        std::vector<DbDesc> dbd(L_ + 2);
         dbw_part_.resize(L_ - 1);
         for (int l = 0; l <= L_ - 2; ++l) {
             dbd[l] = DbDesc{db_part_[l]->as<float>(), (long)ntiles_ * w_, w_, ntiles_};
@@ -1315,6 +1416,9 @@ class UmmaEngine final : public Engine {
                 dbd[l] = DbDesc{dbw_part_[l]->as<float>(), w_, (long)C * w_, nsplit_eff()};
             }
         }
+        dbd[L_ - 1] = DbDesc{dw0_part_.as<float>(), (long)ntiles_ * w_ * dx_, (long)w_ * dx_, ntiles_};
+        dbd[L_] = DbDesc{dwout_part_.as<float>(), (long)ntiles_ * w_, w_, ntiles_};
+        dbd[L_ + 1] = DbDesc{dbout_part_.as<float>(), ntiles_, 1, ntiles_};
         db_desc_.alloc(sizeof(DbDesc) * dbd.size());
         HMC_CK(cudaMemcpy(db_desc_.ptr, dbd.data(), sizeof(DbDesc) * dbd.size(), cudaMemcpyHostToDevice));
 
@@ -1430,20 +1534,15 @@ class UmmaEngine final : public Engine {
             for (int i = 1; i <= L_ - 2; ++i) dw_layer(i, s);
         FinalArgs fa{};
         fa.k = (int)k_;
-        fa.ntiles = ntiles_;
         fa.nsplit = nsplit_eff();
-        fa.w = w_;
-        fa.dx = dx_;
+        fa.nu = ntiles_;
         fa.kind = kind_.as<int>();
-        fa.layer = layer_.as<int>();
+        fa.desc = layer_.as<int>();
         fa.off = off_.as<int>();
         fa.u_part = u_part_.as<double>();
         fa.gw_part = gw_part_.as<float>();
         fa.gw_split = (long)C_ * k_;
         fa.db = db_desc_.as<const DbDesc>();
-        fa.dw0_part = dw0_part_.as<float>();
-        fa.dwout_part = dwout_part_.as<float>();
-        fa.dbout_part = dbout_part_.as<float>();
         fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
         fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
         {
@@ -1602,26 +1701,27 @@ class UmmaEngine final : public Engine {
             const long rel = is_w ? id - nd.woff[l] : id - nd.boff[l];
             const int in = nd.w[l];
             if (l == 0) {
-                kind[j] = is_w ? E_W0 : E_BIAS;
-                layer[j] = 0;
+                kind[j] = E_PART;
+                layer[j] = is_w ? L_ - 1 : 0;
                 off[j] = (int)rel;   // o*dx + d, or o
                 bid[j] = is_w ? 0 : 1;
                 boff[j] = (int)rel;
             } else if (l == L_ - 1) {
-                kind[j] = is_w ? E_WOUT : E_BOUT;
+                kind[j] = E_PART;
+                layer[j] = is_w ? L_ : L_ + 1;
                 off[j] = is_w ? (int)rel : 0;
                 bid[j] = is_w ? 2 + 2 * nh : 3 + 2 * nh;
                 boff[j] = is_w ? (int)rel : 0;
             } else {
                 if (is_w) {
-                    kind[j] = E_HIDDEN_W;
+                    kind[j] = E_GW;
                     erow[j] = (int)(rel / in);
                     ecol[j] = (int)(rel % in);
                     rp[l][erow[j] + 1]++;
                     layer_entries_[l]++;
                     bid[j] = 2 + 2 * (l - 1);
                 } else {
-                    kind[j] = E_BIAS;
+                    kind[j] = E_PART;
                     layer[j] = l;
                     off[j] = (int)rel;
                     bias_entries_[l]++;
@@ -1676,6 +1776,524 @@ class UmmaEngine final : public Engine {
     ScatterPlan plan_;
 };
 
+// ---------------------------------------------------------------------------
+// DeepONet on the tensor cores (Sec. 4.2 operator output): branch and trunk MLPs
+// as bf16 GEMMs with the weights as a hi/lo pair, then S = B T^T + b0 on 128 x N
+// tiles whose epilogue forms the residual, the FP64 energy partials and
+// dS = (S - Y) / sigma^2 in bf16; dB = dS T and dT = dS^T B are bf16 GEMMs whose
+// column sums give the last layers' bias gradients; each net's reverse pass and
+// its sampled weight-gradient entries use the same kernels as the MLP path.
+// ---------------------------------------------------------------------------
+CUtensorMap make_map_ld(const void *base, uint64_t inner, uint64_t ld, uint64_t mid, uint64_t outer,
+                        uint32_t box_inner, uint32_t box_mid)
+{
+    CUtensorMap m;
+    memset(&m, 0, sizeof m);
+    cuuint64_t dims[3] = {inner, mid, outer};
+    cuuint64_t strides[2] = {ld * 2, ld * mid * 2};
+    cuuint32_t box[3] = {box_inner, box_mid, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d) for dims %llu (ld %llu) x %llu x %llu box %u x %u", (int)r,
+                  (unsigned long long)inner, (unsigned long long)ld, (unsigned long long)mid, (unsigned long long)outer,
+                  box_inner, box_mid);
+        throw Fail{HMC_ERR_CUDA};
+    }
+    return m;
+}
+
+long round_up(long v, long m) { return (v + m - 1) / m * m; }
+
+struct DonNet {
+    const NetDesc *nd = nullptr;
+    int L = 0, w = 0, p = 0, dx = 0, dxp = 0, ntiles = 1, nsplit = 1, kb_split = 1;
+    long R = 0;
+    bool gemm_first = false;              // first layer as a GEMM on bf16 inputs (dx > 8)
+    int width[MAXL + 1] = {};             // widths w_0 .. w_L
+    int inld[MAXL] = {};                  // row length of W_l in memory
+    int entries[MAXL] = {};               // sampled weight entries of layer l gathered by k_umma<M_DW>
+    int desc0 = 0;                        // first DbDesc of this net: biases 0..L-1, then dW_0 sums
+    DevBuf x32, xb, w0f, b0f, dw0;
+    std::unique_ptr<DevBuf> wh[MAXL], wl[MAXL], bias[MAXL], colsum[MAXL], rowptr[MAXL];
+    std::unique_ptr<DevBuf> act[MAXL + 1], del[MAXL + 1];   // A_l, D_l for l = 1..L ([C][R][w_l])
+    CUtensorMap act_row[MAXL + 1], act_atom[MAXL + 1], del_row[MAXL + 1], del_atom[MAXL + 1];
+    CUtensorMap w_row_h[MAXL], w_row_l[MAXL], w_atom_h[MAXL], w_atom_l[MAXL], x_row, x_atom;
+};
+
+class DonEngine final : public Engine {
+  public:
+    DonEngine(Problem &p, int C) : p_(p), C_(C)
+    {
+        k_ = p.k;
+        nu_ = p.n_u;
+        ny_ = p.n_y;
+        nyp_ = round_up(ny_, 8);
+        int dev = 0;
+        HMC_CK(cudaGetDevice(&dev));
+        HMC_CK(cudaDeviceGetAttribute(&num_sms_, cudaDevAttrMultiProcessorCount, dev));
+        HMC_CK(cudaMalloc(&err_, sizeof(int)));
+        HMC_CK(cudaMemset(err_, 0, sizeof(int)));
+        setup_net(br_, p.branch, p.u, nu_);
+        setup_net(tr_, p.trunk, p.yq, ny_);
+        pl_ = br_.p;
+
+        // operator output: targets, dS, partials
+        std::vector<float> tf(p.t.begin(), p.t.end());
+        yt_.alloc(sizeof(float) * std::max<size_t>(tf.size(), 1));
+        if (!tf.empty()) HMC_CK(cudaMemcpy(yt_.ptr, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice));
+        ds_.alloc(sizeof(__nv_bfloat16) * C * std::max<long>(nu_, 1) * nyp_);
+        HMC_CK(cudaMemset(ds_.ptr, 0, ds_.n));
+        bs_ = ny_ >= 256 ? 256 : (int)round_up(ny_, 32);
+        nut_ = (int)std::max<long>(1, (nu_ + BM - 1) / BM);
+        ntn_ = (int)std::max<long>(1, (ny_ + bs_ - 1) / bs_);
+        u_part_.alloc(sizeof(double) * C * nut_ * ntn_);
+        db0_part_.alloc(sizeof(float) * C * nut_ * ntn_);
+        b0v_.alloc(sizeof(float) * C);
+        {
+            std::vector<float> v(C, p.b0_off >= 0 ? (float)p.frozen[p.b0_off] : 0.0f);
+            HMC_CK(cudaMemcpy(b0v_.ptr, v.data(), sizeof(float) * C, cudaMemcpyHostToDevice));
+        }
+        ds_row_ = make_map_ld(ds_.ptr, ny_, nyp_, nu_, C, 64, 128);
+        ds_atom_ = make_map_ld(ds_.ptr, ny_, nyp_, nu_, C, 64, 64);
+        t_row_ = make_map(tr_.act[tr_.L]->ptr, pl_, ny_, C, 64, bs_);
+
+        build_entries();
+        nsplit_ = std::max(br_.nsplit, tr_.nsplit);
+        gw_part_.alloc(sizeof(float) * nsplit_ * C * std::max<long>(k_, 1));
+        HMC_CK(cudaMemset(gw_part_.ptr, 0, gw_part_.n));   // splits a net does not use stay zero
+    }
+
+    ~DonEngine() override
+    {
+        if (err_) cudaFree(err_);
+    }
+
+    ScatterPlan scatter_plan() override { return plan_; }
+    size_t bytes() const override { return bytes_; }
+
+    void energy_grad(const void *qv, double *U, void *gv, bool scattered, cudaStream_t s) override
+    {
+        const float *q = static_cast<const float *>(qv);
+        float *g = static_cast<float *>(gv);
+        if (!scattered) {
+            dim3 grid((unsigned)std::min<long>((k_ + 255) / 256, 1024), C_);
+            ProfScope ps("scatter", s);
+            launch_pdl(k_scatter_plan<float>, grid, dim3(256), 0, s, q, k_, plan_);
+        }
+        forward(br_, s);
+        forward(tr_, s);
+        // S = B T^T + b0, residual, energy partials and dS
+        {
+            Params pp = base();
+            pp.M = (int)nu_;
+            pp.N = bs_;
+            pp.K = pl_;
+            pp.kb_per_split = (pl_ + BK - 1) / BK;
+            pp.ntiles = nut_;
+            pp.Yt = yt_.as<float>();
+            pp.ny = (int)ny_;
+            pp.ldo = (int)nyp_;
+            pp.ntn = ntn_;
+            pp.b0s = b0v_.as<float>();
+            pp.out = ds_.as<__nv_bfloat16>();
+            pp.out_b = nu_ * nyp_;
+            pp.inv_s2 = (float)(1.0 / (p_.sigma * p_.sigma));
+            pp.u_part = u_part_.as<double>();
+            pp.db0_part = db0_part_.as<float>();
+            launch_umma<M_S, false, false, false>(br_.act_row[br_.L], t_row_, t_row_, pp, dim3(nut_, ntn_, C_), s);
+        }
+        // dB = dS T and dT = dS^T B: the deltas of the two nets' linear output layers
+        {
+            Params pp = base();
+            pp.M = (int)nu_;
+            pp.N = pl_;
+            pp.K = (int)ny_;
+            pp.kb_per_split = (int)((ny_ + BK - 1) / BK);
+            pp.ntiles = br_.ntiles;
+            pp.out = br_.del[br_.L]->as<__nv_bfloat16>();
+            pp.out_b = nu_ * pl_;
+            pp.db_part = br_.colsum[br_.L - 1]->as<float>();
+            launch_umma<M_GEMM_BF16, false, true, false>(ds_row_, tr_.act_atom[tr_.L], tr_.act_atom[tr_.L], pp,
+                                                          dim3(br_.ntiles, 1, C_), s);
+        }
+        {
+            Params pp = base();
+            pp.M = (int)ny_;
+            pp.N = pl_;
+            pp.K = (int)nu_;
+            pp.kb_per_split = (int)((nu_ + BK - 1) / BK);
+            pp.ntiles = tr_.ntiles;
+            pp.out = tr_.del[tr_.L]->as<__nv_bfloat16>();
+            pp.out_b = ny_ * pl_;
+            pp.db_part = tr_.colsum[tr_.L - 1]->as<float>();
+            launch_umma<M_GEMM_BF16, true, true, false>(ds_atom_, br_.act_atom[br_.L], br_.act_atom[br_.L], pp,
+                                                         dim3(tr_.ntiles, 1, C_), s);
+        }
+        backward(br_, s);
+        backward(tr_, s);
+        FinalArgs fa{};
+        fa.k = (int)k_;
+        fa.nsplit = nsplit_;
+        fa.nu = nut_ * ntn_;
+        fa.kind = kind_.as<int>();
+        fa.desc = desc_.as<int>();
+        fa.off = off_.as<int>();
+        fa.u_part = u_part_.as<double>();
+        fa.gw_part = gw_part_.as<float>();
+        fa.gw_split = (long)C_ * k_;
+        fa.db = db_desc_.as<const DbDesc>();
+        fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
+        fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
+        {
+            ProfScope ps("finalize", s);
+            dim3 grid((unsigned)((k_ + 255) / 256 + 1), C_);
+            launch_pdl(k_finalize_bf16, grid, dim3(256), 0, s, fa, q, U, g);
+        }
+    }
+
+  private:
+    Params base() const
+    {
+        Params pp{};
+        pp.err = err_;
+        return pp;
+    }
+
+    DevBuf *track(DevBuf *b)   // an allocated buffer
+    {
+        bytes_ += b->n;
+        return b;
+    }
+    void alloc_t(DevBuf &b, size_t n)
+    {
+        b.alloc(n);
+        bytes_ += n;
+    }
+
+    // value of parameter (layer l of net n, row o, column i) replicated over the chains
+    void upload_w(DonNet &n, int l, void *hi, void *lo, bool bf16)
+    {
+        const NetDesc &nd = *n.nd;
+        const int out = nd.w[l + 1], in = nd.w[l], ld = n.inld[l];
+        const size_t per = (size_t)out * ld;
+        if (bf16) {
+            std::vector<__nv_bfloat16> vh(C_ * per, __float2bfloat16_rn(0.0f)), vl(C_ * per, __float2bfloat16_rn(0.0f));
+            for (int c = 0; c < C_; ++c)
+                for (int o = 0; o < out; ++o)
+                    for (int i = 0; i < in; ++i) {
+                        const float w = (float)p_.frozen[nd.woff[l] + (long)o * in + i];
+                        const __nv_bfloat16 h = __float2bfloat16_rn(w);
+                        vh[c * per + (size_t)o * ld + i] = h;
+                        vl[c * per + (size_t)o * ld + i] = __float2bfloat16_rn(w - __bfloat162float(h));
+                    }
+            HMC_CK(cudaMemcpy(hi, vh.data(), sizeof(__nv_bfloat16) * vh.size(), cudaMemcpyHostToDevice));
+            HMC_CK(cudaMemcpy(lo, vl.data(), sizeof(__nv_bfloat16) * vl.size(), cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> v(C_ * per, 0.0f);
+            for (int c = 0; c < C_; ++c)
+                for (int o = 0; o < out; ++o)
+                    for (int i = 0; i < in; ++i) v[c * per + (size_t)o * ld + i] = (float)p_.frozen[nd.woff[l] + (long)o * in + i];
+            HMC_CK(cudaMemcpy(hi, v.data(), sizeof(float) * v.size(), cudaMemcpyHostToDevice));
+        }
+    }
+
+    void upload_b(const NetDesc &nd, int l, void *dst)
+    {
+        const int out = nd.w[l + 1];
+        std::vector<float> v((size_t)C_ * out);
+        for (int c = 0; c < C_; ++c)
+            for (int o = 0; o < out; ++o) v[(size_t)c * out + o] = (float)p_.frozen[nd.boff[l] + o];
+        HMC_CK(cudaMemcpy(dst, v.data(), sizeof(float) * v.size(), cudaMemcpyHostToDevice));
+    }
+
+    void setup_net(DonNet &n, const NetDesc &nd, const std::vector<double> &xin, long R)
+    {
+        n.nd = &nd;
+        n.L = nd.L;
+        n.R = R;
+        n.dx = nd.w[0];
+        n.w = nd.w[1];
+        n.p = nd.w[nd.L];
+        for (int l = 0; l <= nd.L; ++l) n.width[l] = nd.w[l];
+        n.gemm_first = n.dx > 8;
+        n.dxp = n.gemm_first ? (int)round_up(n.dx, 8) : n.dx;
+        n.ntiles = (int)std::max<long>(1, (R + BM - 1) / BM);
+        const int C = C_;
+        for (int l = 0; l < n.L; ++l) n.inld[l] = (l == 0) ? n.dxp : nd.w[l];
+        // inputs
+        std::vector<float> xf(xin.begin(), xin.end());
+        alloc_t(n.x32, sizeof(float) * std::max<size_t>(xf.size(), 1));
+        if (!xf.empty()) HMC_CK(cudaMemcpy(n.x32.ptr, xf.data(), sizeof(float) * xf.size(), cudaMemcpyHostToDevice));
+        if (n.gemm_first) {   // bf16 copy per chain, rows padded to dxp
+            std::vector<__nv_bfloat16> xb((size_t)C * std::max<long>(R, 1) * n.dxp, __float2bfloat16_rn(0.0f));
+            for (int c = 0; c < C; ++c)
+                for (long r = 0; r < R; ++r)
+                    for (int d = 0; d < n.dx; ++d)
+                        xb[((size_t)c * R + r) * n.dxp + d] = __float2bfloat16_rn(xf[(size_t)r * n.dx + d]);
+            alloc_t(n.xb, sizeof(__nv_bfloat16) * xb.size());
+            HMC_CK(cudaMemcpy(n.xb.ptr, xb.data(), sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyHostToDevice));
+            n.x_row = make_map_ld(n.xb.ptr, n.dx, n.dxp, R, C, 64, 128);
+            n.x_atom = make_map_ld(n.xb.ptr, n.dx, n.dxp, R, C, 64, 64);
+        }
+        // parameters
+        for (int l = 0; l < n.L; ++l) {
+            const int out = nd.w[l + 1];
+            n.bias[l].reset(track(new DevBuf(sizeof(float) * C * out)));
+            upload_b(nd, l, n.bias[l]->ptr);
+            if (l == 0 && !n.gemm_first) {
+                alloc_t(n.w0f, sizeof(float) * C * out * n.dx);
+                upload_w(n, 0, n.w0f.ptr, nullptr, false);
+                continue;
+            }
+            const size_t wb = sizeof(__nv_bfloat16) * C * out * n.inld[l];
+            n.wh[l].reset(track(new DevBuf(wb)));
+            n.wl[l].reset(track(new DevBuf(wb)));
+            upload_w(n, l, n.wh[l]->ptr, n.wl[l]->ptr, true);
+            const int in = nd.w[l];
+            n.w_row_h[l] = make_map_ld(n.wh[l]->ptr, in, n.inld[l], out, C, 64, out);
+            n.w_row_l[l] = make_map_ld(n.wl[l]->ptr, in, n.inld[l], out, C, 64, out);
+            if (l >= 1) {
+                n.w_atom_h[l] = make_map(n.wh[l]->ptr, in, out, C, 64, 64);
+                n.w_atom_l[l] = make_map(n.wl[l]->ptr, in, out, C, 64, 64);
+            }
+        }
+        // activations and deltas, per-tile column sums
+        for (int l = 1; l <= n.L; ++l) {
+            const size_t ab = sizeof(__nv_bfloat16) * C * std::max<long>(R, 1) * nd.w[l];
+            n.act[l].reset(track(new DevBuf(ab)));
+            n.del[l].reset(track(new DevBuf(ab)));
+            n.act_row[l] = make_map(n.act[l]->ptr, nd.w[l], R, C, 64, 128);
+            n.act_atom[l] = make_map(n.act[l]->ptr, nd.w[l], R, C, 64, 64);
+            n.del_row[l] = make_map(n.del[l]->ptr, nd.w[l], R, C, 64, 128);
+            n.del_atom[l] = make_map(n.del[l]->ptr, nd.w[l], R, C, 64, 64);
+        }
+        for (int l = 0; l < n.L; ++l)
+            n.colsum[l].reset(track(new DevBuf(sizeof(float) * C * n.ntiles * nd.w[l + 1])));
+        if (!n.gemm_first) alloc_t(n.dw0, sizeof(float) * C * n.ntiles * n.w * n.dx);
+        const int total_kb = (int)((R + BK - 1) / BK);
+        n.nsplit = pick_splits(total_kb, ((n.w + BM - 1) / BM) * C, 2 * num_sms_);
+        n.kb_split = (total_kb + n.nsplit - 1) / n.nsplit;
+        n.nsplit = (total_kb + n.kb_split - 1) / n.kb_split;
+    }
+
+    void forward(DonNet &n, cudaStream_t s)
+    {
+        const NetDesc &nd = *n.nd;
+        if (!n.gemm_first) {
+            dim3 grid((unsigned)n.ntiles, C_);
+            ProfScope ps("first_fwd", s);
+            launch_pdl(k_first_fwd, grid, dim3(256), 0, s, n.x32.as<float>(), n.dx, (int)n.R, n.w, n.w0f.as<float>(),
+                       n.bias[0]->as<float>(), n.act[1]->as<__nv_bfloat16>());
+        }
+        for (int l = n.gemm_first ? 0 : 1; l < n.L; ++l) {
+            Params pp = base();
+            pp.M = (int)n.R;
+            pp.N = nd.w[l + 1];
+            pp.K = nd.w[l];
+            pp.kb_per_split = (pp.K + BK - 1) / BK;
+            pp.bias = n.bias[l]->as<float>();
+            pp.bias_b = pp.N;
+            pp.out = n.act[l + 1]->as<__nv_bfloat16>();
+            pp.out_b = n.R * pp.N;
+            const CUtensorMap &a = (l == 0) ? n.x_row : n.act_row[l];
+            const dim3 grid(n.ntiles, 1, C_);
+            if (l < n.L - 1)
+                launch_umma<M_FWD_TANH, false, false, true>(a, n.w_row_h[l], n.w_row_l[l], pp, grid, s);
+            else
+                launch_umma<M_FWD_LIN, false, false, true>(a, n.w_row_h[l], n.w_row_l[l], pp, grid, s);
+        }
+    }
+
+    void backward(DonNet &n, cudaStream_t s)
+    {
+        const NetDesc &nd = *n.nd;
+        const int total_kb = (int)((n.R + BK - 1) / BK);
+        for (int l = n.L - 1; l >= 0; --l) {
+            // sampled entries of dW_l = D_{l+1}^T A_l
+            if (n.entries[l] > 0 && (l >= 1 || n.gemm_first)) {
+                Params pp = base();
+                pp.M = nd.w[l + 1];
+                pp.N = (l >= 1) ? nd.w[l] : (int)round_up(n.dx, 64);
+                pp.K = (int)n.R;
+                pp.kb_per_split = n.kb_split;
+                pp.rowptr = n.rowptr[l]->as<int>();
+                pp.ecol = ecol_.as<int>();
+                pp.erow = erow_.as<int>();
+                pp.epack = epack_.as<int>();
+                pp.gw_part = gw_part_.as<float>();
+                pp.gw_split = (long)C_ * k_;
+                pp.gw_b = k_;
+                const int splits = (total_kb + n.kb_split - 1) / n.kb_split;
+                const CUtensorMap &b = (l >= 1) ? n.act_atom[l] : n.x_atom;
+                launch_umma<M_DW, true, true, false>(n.del_atom[l + 1], b, b, pp,
+                                                     dim3((pp.M + BM - 1) / BM, splits, C_), s);
+            }
+            if (l == 0 || l <= nd.lmin) break;   // no delta is needed below layer l
+            // D_l = (D_{l+1} W_l) (1 - A_l^2); its column sums are the bias gradient of layer l-1
+            Params pp = base();
+            pp.M = (int)n.R;
+            pp.N = nd.w[l];
+            pp.K = nd.w[l + 1];
+            pp.kb_per_split = (pp.K + BK - 1) / BK;
+            pp.ntiles = n.ntiles;
+            pp.aux = n.act[l]->as<__nv_bfloat16>();
+            pp.aux_b = n.R * pp.N;
+            pp.db_part = n.colsum[l - 1]->as<float>();
+            const dim3 grid(n.ntiles, 1, C_);
+            if (l == 1 && !n.gemm_first) {
+                pp.x = n.x32.as<float>();
+                pp.dx = n.dx;
+                pp.dw0_part = n.dw0.as<float>();
+                launch_umma<M_BWD_FIRST, false, true, true>(n.del_row[l + 1], n.w_atom_h[l], n.w_atom_l[l], pp, grid, s);
+            } else {
+                pp.out = n.del[l]->as<__nv_bfloat16>();
+                pp.out_b = n.R * pp.N;
+                launch_umma<M_BWD_TANH, false, true, true>(n.del_row[l + 1], n.w_atom_h[l], n.w_atom_l[l], pp, grid, s);
+            }
+        }
+    }
+
+    // per-entry sources of the gradient, scatter plan, CSR rows of the gathered weights
+    void build_entries()
+    {
+        std::vector<int> kind(k_), desc(k_), off(k_), erow(k_, 0), ecol(k_, 0), bid(k_), boff(k_);
+        std::vector<DbDesc> dbd;
+        DonNet *nets[2] = {&br_, &tr_};
+        int nb = 0;
+        int wbuf[2][MAXL], bbuf[2][MAXL];
+        std::vector<std::vector<int>> rp[2];
+        for (int t = 0; t < 2; ++t) {
+            DonNet &n = *nets[t];
+            n.desc0 = (int)dbd.size();
+            for (int l = 0; l < n.L; ++l)
+                dbd.push_back(DbDesc{n.colsum[l]->as<float>(), (long)n.ntiles * n.width[l + 1], n.width[l + 1], n.ntiles});
+            dbd.push_back(DbDesc{n.gemm_first ? nullptr : n.dw0.as<float>(), (long)n.ntiles * n.w * n.dx,
+                                 (long)n.w * n.dx, n.ntiles});
+            rp[t].assign(n.L, std::vector<int>());
+            for (int l = 0; l < n.L; ++l) {
+                rp[t][l].assign(n.width[l + 1] + 1, 0);
+                const int out = n.width[l + 1];
+                wbuf[t][l] = nb;
+                if (l == 0 && !n.gemm_first) {
+                    plan_.base[nb] = n.w0f.ptr;
+                    plan_.cstride[nb] = (long)out * n.dx;
+                    plan_.is_bf16[nb] = 0;
+                } else {
+                    plan_.base[nb] = n.wh[l]->ptr;
+                    plan_.base_lo[nb] = n.wl[l]->ptr;
+                    plan_.cstride[nb] = (long)out * n.inld[l];
+                    plan_.is_bf16[nb] = 1;
+                }
+                ++nb;
+                bbuf[t][l] = nb;
+                plan_.base[nb] = n.bias[l]->ptr;
+                plan_.cstride[nb] = out;
+                plan_.is_bf16[nb] = 0;
+                ++nb;
+            }
+        }
+        const int b0buf = nb;
+        plan_.base[nb] = b0v_.ptr;
+        plan_.cstride[nb] = 1;
+        plan_.is_bf16[nb] = 0;
+        ++nb;
+        HMC_REQUIRE(nb <= MAX_SCATTER_BUFS, "too many layers for the scatter plan");
+        plan_.nbuf = nb;
+        const int b0desc = (int)dbd.size();
+        dbd.push_back(DbDesc{db0_part_.as<float>(), (long)nut_ * ntn_, 1, nut_ * ntn_});
+
+        for (long j = 0; j < k_; ++j) {
+            const long id = p_.idx[j];
+            if (p_.b0_off >= 0 && id == p_.b0_off) {
+                kind[j] = E_PART;
+                desc[j] = b0desc;
+                off[j] = 0;
+                bid[j] = b0buf;
+                boff[j] = 0;
+                continue;
+            }
+            const int t = id < p_.branch.base + p_.branch.P ? 0 : 1;
+            DonNet &n = *nets[t];
+            const NetDesc &nd = *n.nd;
+            int l = 0;
+            while (l + 1 < n.L && id >= nd.woff[l + 1]) ++l;
+            const int in = nd.w[l];
+            const bool is_w = id < nd.woff[l] + (long)nd.w[l + 1] * in;
+            if (is_w) {
+                const long rel = id - nd.woff[l];
+                const int o = (int)(rel / in), i = (int)(rel % in);
+                bid[j] = wbuf[t][l];
+                boff[j] = o * n.inld[l] + i;
+                if (l == 0 && !n.gemm_first) {
+                    kind[j] = E_PART;
+                    desc[j] = n.desc0 + n.L;
+                    off[j] = o * n.dx + i;
+                } else {
+                    kind[j] = E_GW;
+                    erow[j] = o;
+                    ecol[j] = i;
+                    rp[t][l][o + 1]++;
+                    n.entries[l]++;
+                }
+            } else {
+                const int rel = (int)(id - nd.boff[l]);
+                kind[j] = E_PART;
+                desc[j] = n.desc0 + l;
+                off[j] = rel;
+                bid[j] = bbuf[t][l];
+                boff[j] = rel;
+            }
+        }
+        // CSR rows: a layer's weight entries are contiguous and sorted by (row, column)
+        for (int t = 0; t < 2; ++t) {
+            DonNet &n = *nets[t];
+            for (int l = 0; l < n.L; ++l) {
+                const int out = n.width[l + 1];
+                const long first = std::lower_bound(p_.idx.begin(), p_.idx.end(), n.nd->woff[l]) - p_.idx.begin();
+                std::vector<int> r(out + 1);
+                r[0] = (int)first;
+                for (int o = 0; o < out; ++o) r[o + 1] = r[o] + rp[t][l][o + 1];
+                n.rowptr[l].reset(track(new DevBuf(sizeof(int) * (out + 1))));
+                HMC_CK(cudaMemcpy(n.rowptr[l]->ptr, r.data(), sizeof(int) * (out + 1), cudaMemcpyHostToDevice));
+            }
+        }
+        auto up = [&](DevBuf &d, const std::vector<int> &v) {
+            alloc_t(d, sizeof(int) * std::max<size_t>(v.size(), 1));
+            if (!v.empty()) HMC_CK(cudaMemcpy(d.ptr, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
+        };
+        up(kind_, kind);
+        up(desc_, desc);
+        up(off_, off);
+        up(erow_, erow);
+        up(ecol_, ecol);
+        std::vector<int> epack(k_);
+        for (long j = 0; j < k_; ++j) epack[j] = (erow[j] << 16) | ecol[j];
+        up(epack_, epack);
+        up(sc_off_, boff);
+        std::vector<uint8_t> b8(bid.begin(), bid.end());
+        alloc_t(sc_bid_, std::max<size_t>(b8.size(), 1));
+        HMC_CK(cudaMemcpy(sc_bid_.ptr, b8.data(), b8.size(), cudaMemcpyHostToDevice));
+        plan_.buf_id = sc_bid_.as<uint8_t>();
+        plan_.off = sc_off_.as<int>();
+        alloc_t(db_desc_, sizeof(DbDesc) * dbd.size());
+        HMC_CK(cudaMemcpy(db_desc_.ptr, dbd.data(), sizeof(DbDesc) * dbd.size(), cudaMemcpyHostToDevice));
+    }
+
+    Problem &p_;
+    int C_, nut_ = 1, ntn_ = 1, bs_ = 128, pl_ = 64, nsplit_ = 1, num_sms_ = 148;
+    long k_ = 0, nu_ = 0, ny_ = 0, nyp_ = 0;
+    size_t bytes_ = 0;
+    int *err_ = nullptr;
+    DonNet br_, tr_;
+    DevBuf yt_, ds_, u_part_, db0_part_, b0v_, gw_part_, db_desc_;
+    DevBuf kind_, desc_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_;
+    CUtensorMap ds_row_, ds_atom_, t_row_;
+    ScatterPlan plan_;
+};
+
 }  // namespace
 
 bool umma_engine_supports(const Problem &p, std::string *why)
@@ -1703,6 +2321,33 @@ bool umma_engine_supports(const Problem &p, std::string *why)
 }
 
 Engine *make_umma_engine_bf16(Problem &p, int C) { return new UmmaEngine(p, C); }
+
+bool don_engine_supports(const Problem &p, std::string *why)
+{
+    auto no = [&](const char *m) {
+        if (why) *why = m;
+        return false;
+    };
+    if (p.kind != HMC_NET_DEEPONET) return no("not a DeepONet");
+    for (const NetDesc *nd : {&p.branch, &p.trunk}) {
+        if (nd->L < 2) return no("branch and trunk need a hidden layer");
+        const int w = nd->w[1], pl = nd->w[nd->L];
+        if (w % 64 != 0 || w > 256) return no("hidden widths must be 64, 128, 192 or 256");
+        for (int l = 1; l < nd->L; ++l)
+            if (nd->w[l] != w) return no("all hidden layers of a net must have the same width");
+        if (pl % 64 != 0 || pl > 256) return no("the latent width must be 64, 128, 192 or 256");
+        if (nd->w[0] < 1 || nd->w[0] > 256) return no("input widths must be 1..256");
+        for (int l = 0; l + 1 < nd->L; ++l)
+            if (nd->act[l] != HMC_ACT_TANH) return no("hidden activations must be tanh");
+        if (nd->act[nd->L - 1] != HMC_ACT_IDENTITY) return no("the last layer of each net must be linear");
+        for (int l = 0; l < nd->L; ++l)
+            if (!nd->bias[l]) return no("every layer must have a bias");
+    }
+    if (p.n_u < 1 || p.n_y < 1) return no("empty data");
+    return true;
+}
+
+Engine *make_don_engine_bf16(Problem &p, int C) { return new DonEngine(p, C); }
 
 }  // namespace hmc
 

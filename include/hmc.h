@@ -168,6 +168,24 @@ HMC_API hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, l
                       unsigned long long seed, long first_traj,
                       void *samples, unsigned char *accepted, double *dH, void *q_last);
 
+/*
+ * Step-size adaptation for the warm-up (the paper tunes eps to about 80% acceptance;
+ * Sec. 4.3): runs n_warmup trajectories of L steps from q, one at a time, and adapts
+ * log eps by dual averaging (Hoffman and Gelman 2014, Sec. 3.2) so that the mean
+ * over all chains (and problems) of the Metropolis acceptance probability
+ * min(1, exp(-dH)) approaches target_accept; a non-finite dH counts as 0.
+ *   q [C][k]        in: start state; out: state after the warm-up (device or host)
+ *   eps0            initial step; the shrinkage point is log(10 eps0)
+ *   seed, first_traj  Philox stream and trajectory index of the first warm-up
+ *                   trajectory; continue sampling with first_traj + n_warmup
+ *   eps_out         the averaged step after the last update (host double)
+ * Each warm-up trajectory is one hmc_sample call, so the trajectory graph is
+ * recaptured for every new eps.  Errors as hmc_sample.
+ */
+HMC_API hmc_status hmc_adapt_step_size(hmc_handle h, void *q, int L, double eps0, long n_warmup,
+                               double target_accept, unsigned long long seed, long first_traj,
+                               double *eps_out);
+
 /* Free the handle and all its device memory. NULL is accepted. */
 HMC_API hmc_status hmc_destroy(hmc_handle h);
 

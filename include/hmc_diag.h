@@ -32,6 +32,11 @@ HMC_API hmc_status hmc_diag_log_uniform(unsigned long long seed, unsigned long l
  * call (the launches one trajectory costs), or -1 for a bad handle. */
 HMC_API long hmc_diag_graph_kernels(hmc_handle h);
 
+/* The energy the Metropolis test uses, for states q [C][k] (device or host; U [C] host
+ * or device doubles): on the bf16 tensor-core engines the accurate forward pass with
+ * hi/lo activations, elsewhere the energy of hmc_energy_grad. */
+HMC_API hmc_status hmc_diag_metropolis_energy(hmc_handle h, const void *q, double *U);
+
 typedef struct {
     char name[48];      /* kernel kind */
     double ms_total;    /* summed CUDA-event time over all its launches */

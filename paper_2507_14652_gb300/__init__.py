@@ -32,10 +32,10 @@ STATUS = {0: "HMC_OK", 1: "HMC_ERR_ARG", 2: "HMC_ERR_CUDA", 3: "HMC_ERR_OOM", 4:
 
 # every symbol the C ABI (include/hmc.h, include/hmc_diag.h) declares
 EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_diag_umma_gemm",
-           "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_destroy", "hmc_last_error",
+           "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_adapt_step_size", "hmc_destroy", "hmc_last_error",
            "hmc_energy_grad_noalloc",
            "hmc_diag_philox", "hmc_diag_momenta", "hmc_diag_log_uniform", "hmc_diag_graph_kernels",
-           "hmc_diag_profile_energy_grad"]
+           "hmc_diag_profile_energy_grad", "hmc_diag_metropolis_energy"]
 
 
 class HmcError(RuntimeError):
@@ -88,6 +88,7 @@ def lib():
         L.hmc_energy_grad.argtypes = [vp, vp, vp, vp]
         L.hmc_leapfrog.argtypes = [vp, vp, vp, d, i]
         L.hmc_sample.argtypes = [vp, vp, d, i, lg, u64, lg, vp, vp, vp, vp]
+        L.hmc_adapt_step_size.argtypes = [vp, vp, i, d, lg, d, u64, lg, ct.POINTER(d)]
         L.hmc_destroy.argtypes = [vp]
         L.hmc_last_error.restype = ct.c_char_p
         L.hmc_diag_philox.argtypes = [vp, vp, lg, vp]
@@ -99,6 +100,7 @@ def lib():
         L.hmc_diag_graph_kernels.restype = lg
         L.hmc_diag_profile_energy_grad.argtypes = [vp, vp, i, vp, i]
         L.hmc_diag_umma_gemm.argtypes = [i] * 6 + [vp] * 3
+        L.hmc_diag_metropolis_energy.argtypes = [vp, vp, vp]
         for f in EXPORTS:
             if f not in ("hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_last_error",
                          "hmc_diag_graph_kernels"):
@@ -248,6 +250,22 @@ class Sampler:
         _check(lib().hmc_sample(self._h, _ptr(q0), float(eps), int(L), int(n), int(seed), int(first_traj),
                                 _ptr(S), _ptr(acc), _ptr(dH), _ptr(ql)))
         return S, acc, dH, ql
+
+    def adapt_step_size(self, q0, L, eps0, n_warmup, target_accept=0.8, seed=0, first_traj=0):
+        """Dual-averaging warm-up (hmc_adapt_step_size): returns (eps, q after the warm-up)."""
+        q = self._state(q0).clone()
+        eps = ct.c_double(0.0)
+        _check(lib().hmc_adapt_step_size(self._h, _ptr(q), int(L), float(eps0), int(n_warmup), float(target_accept),
+                                         int(seed), int(first_traj), ct.byref(eps)))
+        return eps.value, q
+
+    def metropolis_energy(self, q):
+        """U [C] used by the Metropolis test (hmc_diag_metropolis_energy)."""
+        import torch
+        q = self._state(q)
+        U = torch.empty(self.n_problems * self.chains, dtype=torch.float64, device="cuda")
+        _check(lib().hmc_diag_metropolis_energy(self._h, _ptr(q), _ptr(U)))
+        return U
 
     def sample_host(self, q0, eps, L, n, seed=0, first_traj=0):
         """Same as sample() with numpy (host) buffers: the library stages the copies."""

@@ -531,6 +531,18 @@ void energy_grad_all(hmc_handle h, void *q, double *U, void *g, bool scattered)
     }
 }
 
+// Overwrite U with the accurate energy where an engine's energy_grad U is a
+// reduced-precision one (q already scattered by the preceding energy_grad_all).
+void accurate_energy_all(hmc_handle h, void *q, double *U)
+{
+    for (int i = 0; i < h->nprob; ++i) {
+        Engine *e = h->engines[i].get();
+        if (!e->has_accurate_energy()) continue;
+        char *qb = static_cast<char *>(q) + h->qoff[i] * h->elem;
+        e->accurate_energy(qb, U + (long)i * h->C, h->stream);
+    }
+}
+
 // A device view of a user array: the pointer itself when it is device memory,
 // otherwise a staging buffer (copied in when `in`).
 void *dev_view(hmc_handle h, const void *user, size_t bytes, bool in, bool *staged)
@@ -570,6 +582,7 @@ template <typename T> void enqueue_trajectory(hmc_handle h, double eps, int L, u
     HMC_LAUNCH_CK();
     for (int s = 1; s <= L; ++s) {
         energy_grad_all(h, h->q_prop.ptr, h->U_prop.as<double>(), h->g_prop.ptr, true);
+        if (s == L) accurate_energy_all(h, h->q_prop.ptr, h->U_prop.as<double>());   // H1 for the Metropolis test
         if (s < L) {
             launch_pdl(k_kick_drift<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, h->g_prop.as<T>(),
                        h->p.as<T>(), h->q_prop.as<T>(), eps, eps);
@@ -790,6 +803,7 @@ hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_sa
         double *ddh = static_cast<double *>(dev_view(h, dH, sizeof(double) * nseg * n_samples, false, &sd));
         void *dl = dev_view(h, q_last, sb, false, &sl);
         energy_grad_all(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr, false);
+        accurate_energy_all(h, h->q_cur.ptr, h->U_cur.as<double>());   // H0 of the first trajectory
         k_set_state<<<1, 1, 0, h->stream>>>(h->state.as<TrajState>(), first_traj, 0, ds, da, ddh);
         HMC_LAUNCH_CK();
         if (n_samples > 0) {
@@ -841,6 +855,49 @@ hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_sa
     });
 }
 
+hmc_status hmc_adapt_step_size(hmc_handle h, void *q, int L, double eps0, long n_warmup, double target_accept,
+                               unsigned long long seed, long first_traj, double *eps_out)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(h && q && eps_out, "NULL argument");
+        HMC_REQUIRE(L >= 1 && n_warmup >= 1 && first_traj >= 0 && std::isfinite(eps0) && eps0 > 0,
+                    "need L >= 1, n_warmup >= 1, eps0 > 0, first_traj >= 0");
+        HMC_REQUIRE(target_accept > 0.0 && target_accept < 1.0, "target_accept must lie in (0, 1)");
+        const long nseg = (long)h->nprob * h->C;
+        const size_t sb = h->elem * (size_t)h->S_total;
+        const bool on_host = !is_device_ptr(q);
+        DevBuf state(sb), dh_dev(sizeof(double) * nseg);
+        if (on_host) HMC_CK(cudaMemcpy(state.ptr, q, sb, cudaMemcpyHostToDevice));
+        void *dq = on_host ? state.ptr : q;
+        std::vector<double> dh(nseg);
+        // Dual averaging of log eps (Hoffman and Gelman 2014, Sec. 3.2) towards a mean
+        // Metropolis acceptance probability `target_accept` over all chains; shrinkage
+        // towards log(10 eps0), gamma = 0.05, t0 = 10, kappa = 0.75.  The returned step is
+        // the averaged iterate.
+        const double mu = std::log(10.0 * eps0), gamma = 0.05, t0 = 10.0, kappa = 0.75;
+        double hbar = 0.0, log_eps = std::log(eps0), log_eps_bar = 0.0;
+        for (long m = 1; m <= n_warmup; ++m) {
+            const hmc_status st = hmc_sample(h, dq, std::exp(log_eps), L, 1, seed, first_traj + m - 1, nullptr, nullptr,
+                                             dh_dev.as<double>(), dq);
+            if (st != HMC_OK) return st;
+            HMC_CK(cudaMemcpyAsync(dh.data(), dh_dev.ptr, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->stream));
+            HMC_CK(cudaStreamSynchronize(h->stream));
+            double a = 0.0;
+            for (long i = 0; i < nseg; ++i) a += std::isfinite(dh[i]) ? std::min(1.0, std::exp(-dh[i])) : 0.0;
+            a /= (double)nseg;
+            const double w = 1.0 / ((double)m + t0);
+            hbar = (1.0 - w) * hbar + w * (target_accept - a);
+            log_eps = mu - std::sqrt((double)m) / gamma * hbar;
+            const double eta = std::pow((double)m, -kappa);
+            log_eps_bar = eta * log_eps + (1.0 - eta) * log_eps_bar;
+        }
+        *eps_out = std::exp(log_eps_bar);
+        if (on_host) HMC_CK(cudaMemcpy(q, state.ptr, sb, cudaMemcpyDeviceToHost));
+        return HMC_OK;
+    });
+}
+
 hmc_status hmc_destroy(hmc_handle h)
 {
     g_err.clear();
@@ -863,6 +920,26 @@ hmc_status hmc_destroy(hmc_handle h)
 const char *hmc_last_error(void) { return g_err.c_str(); }
 
 long hmc_diag_graph_kernels(hmc_handle h) { return h ? h->traj_kernels : -1; }
+
+hmc_status hmc_diag_metropolis_energy(hmc_handle h, const void *q, double *U)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(h && q && U, "NULL argument");
+        h->stage.clear();
+        join_in(h);
+        bool sq, su;
+        const size_t sb = h->elem * (size_t)h->S_total;
+        void *dq = dev_view(h, q, sb, true, &sq);
+        double *dU = static_cast<double *>(dev_view(h, U, sizeof(double) * h->nprob * h->C, false, &su));
+        energy_grad_all(h, dq, dU, h->g_prop.ptr, false);
+        accurate_energy_all(h, dq, dU);
+        if (su) HMC_CK(cudaMemcpyAsync(U, dU, sizeof(double) * h->nprob * h->C, cudaMemcpyDeviceToHost, h->stream));
+        join_out(h);
+        if (sq || su) HMC_CK(cudaStreamSynchronize(h->stream));
+        return HMC_OK;
+    });
+}
 
 int hmc_diag_profile_energy_grad(hmc_handle h, const void *q, int reps, hmc_kernel_time *out, int max_out)
 {

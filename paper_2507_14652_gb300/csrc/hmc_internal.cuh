@@ -85,6 +85,11 @@ struct Engine {
     virtual void energy_grad(const void *q, double *U, void *g, bool scattered, cudaStream_t s) = 0;
     virtual ScatterPlan scatter_plan() = 0;
     virtual size_t bytes() const = 0;
+    // The energy for the Metropolis test.  Engines whose energy_grad U is only as
+    // accurate as their reduced-precision gradient (the bf16 tensor-core engines)
+    // provide a second, accurate U(q); q is already scattered into the network.
+    virtual bool has_accurate_energy() const { return false; }
+    virtual void accurate_energy(const void *q, double *U, cudaStream_t s) {}
 };
 
 struct Problem {

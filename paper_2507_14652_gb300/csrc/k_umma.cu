@@ -105,9 +105,13 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), accb = smem_u32(bars + 2 * STAGES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m_tile = blockIdx.x, b = blockIdx.z;
-    const int split = MODE == M_S ? 0 : blockIdx.y;          // M_S: grid.y walks column tiles
-    const int n0 = MODE == M_S ? blockIdx.y * p.N : 0;
+    // M_S runs on a (chain, row tile, column tile) grid with the chain fastest, so the
+    // chains' CTAs for one tile of the shared targets follow each other through L2
+    const int m_tile = MODE == M_S ? blockIdx.y : blockIdx.x;
+    const int b = MODE == M_S ? blockIdx.x : blockIdx.z;
+    const int n_tile = MODE == M_S ? blockIdx.z : 0;
+    const int split = MODE == M_S ? 0 : blockIdx.y;
+    const int n0 = n_tile * p.N;
     const int m0 = m_tile * BM;
     const int BN = p.N;
     const int total_kb = (p.K + BK - 1) / BK;
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                 }
                 named_bar_sync(1, 128);
                 if (et == 0) {
-                    const long o = ((long)b * p.ntiles + m_tile) * p.ntn + blockIdx.y;
+                    const long o = ((long)b * p.ntiles + m_tile) * p.ntn + n_tile;
                     p.u_part[o] = rd[0] + rd[1] + rd[2] + rd[3];
                     p.db0_part[o] = dsm[0] + dsm[1] + dsm[2] + dsm[3];
                 }
@@ -1052,6 +1056,206 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_dw2(const __grid_constant__ CUt
 }
 
 // ---------------------------------------------------------------------------
+// Energy for the Metropolis test.  The trajectory's forces come from the bf16
+// GEMMs; the accept/reject decision needs U(q) itself, and rounding every hidden
+// activation to bf16 makes U jump by order one between nearby states (dH would
+// carry that noise).  This forward pass carries the activations as bf16 hi/lo
+// pairs and accumulates A_hi W_hi + A_hi W_lo + A_lo W_hi (the A_lo W_lo term is
+// below 2^-16 of the product), with tanhf in the epilogue, so U follows an FP32
+// forward pass.  OUT fuses the last hidden layer with the output layer and the
+// residual and writes only the per-tile sums of squares (FP64).
+// ---------------------------------------------------------------------------
+constexpr int E3_STAGES = 2;
+constexpr int E3_A = BM * BK * 2;            // 16 KB: one half of an A K-block
+constexpr int E3_B = 256 * BK * 2;           // 32 KB: one half of a W K-block
+constexpr int E3_STAGE = 2 * E3_A + 2 * E3_B;
+constexpr int E3_SMEM = 1024 + E3_STAGES * E3_STAGE + 256 + 64;
+
+struct E3Params {
+    int M, N, K, ntiles;
+    int *err;
+    const float *bias;                   // [b][N]
+    __nv_bfloat16 *out_hi, *out_lo;      // [b][M][N]
+    const float *wout, *bout, *y;        // OUT: output layer [b][N], [b]; targets [M]
+    double *u_part;                      // OUT: [b][ntiles]
+};
+
+template <bool OUT>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_energy3(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+              const __grid_constant__ CUtensorMap tmWh, const __grid_constant__ CUtensorMap tmWl, const E3Params p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + E3_STAGES * E3_STAGE);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * E3_STAGES + 1);
+    double *rd = reinterpret_cast<double *>(bars + 2 * E3_STAGES + 2);   // [4]
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * E3_STAGES, accb = empty0 + 8 * E3_STAGES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m_tile = blockIdx.x, b = blockIdx.z, m0 = m_tile * BM;
+    const int nkb = (p.K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < E3_STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), 256);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    pdl_wait();
+    pdl_trigger();
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t bytes = 2u * E3_A + 2u * (uint32_t)p.N * BK * 2u;
+            int issued = 0;
+            bool ok = true;
+            for (int i = 0; i < nkb; ++i) {
+                const int s = i % E3_STAGES;
+                const uint32_t ph = (uint32_t)(i / E3_STAGES) & 1u;
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, p.err)) { ok = false; break; }
+                const uint32_t fb = full0 + 8 * s, sa = smem_u32(smem + s * E3_STAGE), sb = sa + 2 * E3_A;
+                mbar_expect_tx(fb, bytes);
+                tma_load_3d(sa, &tmAh, i * BK, m0, b, fb);
+                tma_load_3d(sa + E3_A, &tmAl, i * BK, m0, b, fb);
+                tma_load_3d(sb, &tmWh, i * BK, 0, b, fb);
+                tma_load_3d(sb + E3_B, &tmWl, i * BK, 0, b, fb);
+                ++issued;
+            }
+            if (!ok)
+                for (int i = max(0, issued - E3_STAGES); i < issued; ++i)
+                    mbar_wait(full0 + 8 * (i % E3_STAGES), (uint32_t)(i / E3_STAGES) & 1u, p.err, 100000000ull);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(BM, p.N, false, false);
+            for (int i = 0; i < nkb; ++i) {
+                const int s = i % E3_STAGES;
+                const uint32_t ph = (uint32_t)(i / E3_STAGES) & 1u;
+                if (!mbar_wait(full0 + 8 * s, ph, p.err)) break;
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * E3_STAGE), sb = sa + 2 * E3_A;
+#pragma unroll
+                for (int ks = 0; ks < BK / 16; ++ks) {
+                    const uint64_t ah = sdesc(sa + 32 * ks, 0, 1024), al = sdesc(sa + E3_A + 32 * ks, 0, 1024);
+                    const uint64_t wh = sdesc(sb + 32 * ks, 0, 1024), wl = sdesc(sb + E3_B + 32 * ks, 0, 1024);
+                    mma_bf16(tmem, ah, wh, idesc, (i > 0 || ks > 0) ? 1u : 0u);
+                    mma_bf16(tmem, ah, wl, idesc, 1u);
+                    mma_bf16(tmem, al, wh, idesc, 1u);
+                }
+                mma_commit(empty0 + 8 * s);
+            }
+            mma_commit(accb);
+        }
+    } else {
+        const int q = warp & 3, row = 32 * q + lane, m = m0 + row, et = threadIdx.x - 64;
+        const bool valid = m < p.M;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16);
+        const float *bias = p.bias + (long)b * p.N;
+        const bool ok = mbar_wait(accb, 0, p.err);
+        tc_fence_after();
+        if (!OUT) {
+            for (int c0 = 0; ok && c0 < p.N; c0 += 32) {
+                float v[32];
+                tmem_ld32(taddr + c0, v);
+                if (valid) {
+                    uint32_t ph[16], pl[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float a0 = tanhf(v[2 * j] + bias[c0 + 2 * j]);
+                        const float a1 = tanhf(v[2 * j + 1] + bias[c0 + 2 * j + 1]);
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(a0), h1 = __float2bfloat16_rn(a1);
+                        ph[j] = pack_bf16(__bfloat162float(h0), __bfloat162float(h1));
+                        pl[j] = pack_bf16(a0 - __bfloat162float(h0), a1 - __bfloat162float(h1));
+                    }
+                    uint4 *oh = reinterpret_cast<uint4 *>(p.out_hi + ((long)b * p.M + m) * p.N + c0);
+                    uint4 *ol = reinterpret_cast<uint4 *>(p.out_lo + ((long)b * p.M + m) * p.N + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        oh[j] = make_uint4(ph[4 * j], ph[4 * j + 1], ph[4 * j + 2], ph[4 * j + 3]);
+                        ol[j] = make_uint4(pl[4 * j], pl[4 * j + 1], pl[4 * j + 2], pl[4 * j + 3]);
+                    }
+                }
+            }
+        } else {
+            const float *wo = p.wout + (long)b * p.N;
+            float f = p.bout[b];
+            for (int c0 = 0; ok && c0 < p.N; c0 += 32) {
+                float v[32];
+                tmem_ld32(taddr + c0, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) f += tanhf(v[j] + bias[c0 + j]) * wo[c0 + j];
+            }
+            const double r = valid ? (double)f - (double)p.y[m] : 0.0;
+            double r2 = r * r;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+            if (lane == 0) rd[q] = r2;
+            named_bar_sync(1, 128);
+            if (et == 0) p.u_part[(long)b * p.ntiles + m_tile] = rd[0] + rd[1] + rd[2] + rd[3];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+template <bool OUT>
+void launch_energy3(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &wh, const CUtensorMap &wl,
+                    const E3Params &p, dim3 grid, cudaStream_t s)
+{
+    static bool configured = false;
+    if (!configured) {
+        HMC_CK(cudaFuncSetAttribute(k_energy3<OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, E3_SMEM));
+        configured = true;
+    }
+    ProfScope ps(OUT ? "energy3_out" : "energy3_hidden", s);
+    launch_pdl(k_energy3<OUT>, grid, dim3(NTHREADS), E3_SMEM, s, ah, al, wh, wl, p);
+}
+
+// First layer of the accurate forward pass: A_1 = tanh(X W_0^T + b_0) in FP32, stored
+// as a bf16 hi/lo pair.  Thread = (column o, slice of rows) of a (128-row tile, chain).
+__global__ void __launch_bounds__(256) k_first_fwd3(const float *x, int dx, int N, int w, const float *W0,
+                                                    const float *b0, __nv_bfloat16 *A1h, __nv_bfloat16 *A1l)
+{
+    __shared__ float xs[BM * 8];
+    pdl_wait();
+    pdl_trigger();
+    const int b = blockIdx.y, n0 = blockIdx.x * BM;
+    const int nr = min(BM, N - n0);
+    for (int i = threadIdx.x; i < nr * dx; i += blockDim.x) xs[i] = x[(long)n0 * dx + i];
+    __syncthreads();
+    for (int o = threadIdx.x; o < w; o += blockDim.x) {
+        float wr[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) wr[d] = d < dx ? W0[((long)b * w + o) * dx + d] : 0.0f;
+        const float bo = b0[(long)b * w + o];
+        const long base = ((long)b * N + n0) * w + o;
+        for (int r = 0; r < nr; ++r) {
+            float z = bo;
+#pragma unroll
+            for (int d = 0; d < 8; ++d)
+                if (d < dx) z += xs[r * dx + d] * wr[d];
+            const float a = tanhf(z);
+            const __nv_bfloat16 h = __float2bfloat16_rn(a);
+            A1h[base + (long)r * w] = h;
+            A1l[base + (long)r * w] = __float2bfloat16_rn(a - __bfloat162float(h));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // CUDA-core kernels around the tensor-core GEMMs
 // ---------------------------------------------------------------------------
 
@@ -1553,6 +1757,50 @@ class UmmaEngine final : public Engine {
         }
     }
 
+    bool has_accurate_energy() const override { return true; }
+
+    // U(q) from the hi/lo-activation forward pass; the activation and delta buffers are
+    // free after the gradient that preceded it: a_i's hi part goes to A_i, its lo part to D_{i+1}
+    void accurate_energy(const void *qv, double *U, cudaStream_t s) override
+    {
+        const float *q = static_cast<const float *>(qv);
+        {
+            dim3 grid((unsigned)ntiles_, C_);
+            ProfScope ps("first_fwd3", s);
+            launch_pdl(k_first_fwd3, grid, dim3(256), 0, s, x_.as<float>(), dx_, (int)N_, w_, W0_.as<float>(),
+                       b0_.as<float>(), A_[1]->as<__nv_bfloat16>(), D_[2]->as<__nv_bfloat16>());
+        }
+        for (int i = 1; i <= L_ - 2; ++i) {
+            E3Params e{};
+            e.M = (int)N_;
+            e.N = w_;
+            e.K = w_;
+            e.ntiles = ntiles_;
+            e.err = err_;
+            e.bias = bh_[i - 1]->as<float>();
+            const dim3 grid(ntiles_, 1, C_);
+            if (i < L_ - 2) {
+                e.out_hi = A_[i + 1]->as<__nv_bfloat16>();
+                e.out_lo = D_[i + 2]->as<__nv_bfloat16>();
+                launch_energy3<false>(A_row_[i], D_row_[i + 1], W_fwd_[i], W_fwd_lo_[i], e, grid, s);
+            } else {
+                e.wout = wout_.as<float>();
+                e.bout = bout_.as<float>();
+                e.y = y_.as<float>();
+                e.u_part = u_part_.as<double>();
+                launch_energy3<true>(A_row_[i], D_row_[i + 1], W_fwd_[i], W_fwd_lo_[i], e, grid, s);
+            }
+        }
+        FinalArgs fa{};
+        fa.k = (int)k_;
+        fa.nu = ntiles_;
+        fa.u_part = u_part_.as<double>();
+        fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
+        fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
+        ProfScope ps("energy3_final", s);
+        launch_pdl(k_finalize_bf16, dim3(1, C_), dim3(256), 0, s, fa, q, U, (float *)nullptr);
+    }
+
   private:
     // weight gradient of hidden layer i (dW = delta_{i+1}^T A_i) at its sampled entries
     void dw_layer(int i, cudaStream_t s)
@@ -1903,7 +2151,7 @@ class DonEngine final : public Engine {
             pp.inv_s2 = (float)(1.0 / (p_.sigma * p_.sigma));
             pp.u_part = u_part_.as<double>();
             pp.db0_part = db0_part_.as<float>();
-            launch_umma<M_S, false, false, false>(br_.act_row[br_.L], t_row_, t_row_, pp, dim3(nut_, ntn_, C_), s);
+            launch_umma<M_S, false, false, false>(br_.act_row[br_.L], t_row_, t_row_, pp, dim3(C_, nut_, ntn_), s);
         }
         // dB = dS T and dT = dS^T B: the deltas of the two nets' linear output layers
         {

@@ -203,3 +203,17 @@ def test_nonfinite_energy_is_flagged_and_rejected():
     S, acc, dH, ql = s.sample(torch.from_numpy(prob.q0), 50.0, 5, 3, seed=2)
     bad = ~np.isfinite(dH.cpu().numpy())
     assert not acc.cpu().numpy()[bad].any()
+
+
+@pytest.mark.parametrize("eps0", [2e-1, 1e-3])
+def test_step_size_adaptation_reaches_the_target_acceptance(eps0):
+    # dual averaging during warm-up (the paper tunes eps to ~80% acceptance): from a step
+    # far too large or far too small, the adapted step gives acceptance near the target
+    prob = W.bayes_linear(chains=4)
+    s = sampler_from(prob, hmc.PREC_FP64)
+    L = 10
+    eps, q = s.adapt_step_size(torch.from_numpy(prob.q0), L, eps0, 80, target_accept=0.8, seed=12)
+    assert np.isfinite(eps) and eps > 0
+    S, acc, dH, ql = s.sample(q, eps, L, 60, seed=12, first_traj=80)
+    a = float(np.minimum(1.0, np.exp(-dH.cpu().numpy())).mean())
+    assert 0.6 <= a <= 0.95, (eps0, eps, a)

@@ -132,3 +132,24 @@ def test_bf16_sampler_runs_and_resumes():
     S1, a1, d1, q1 = s.sample(q0, 2e-4, 8, 5, seed=4)
     S2, a2, d2, q2 = s.sample(q1, 2e-4, 8, 3, seed=4, first_traj=5)
     assert torch.equal(torch.cat([S1, S2]), S) and torch.equal(q2, ql)
+
+
+def test_bf16_metropolis_energy_is_accurate():
+    # bf16 activations make energy_grad's U jump by order one between nearby states; the
+    # Metropolis test uses the forward pass with hi/lo activations, which follows FP32
+    prob = W.small_mlp(n=2000, widths=(2, 256, 256, 256, 1), frac=0.05, chains=4, seed=51)
+    s = sampler_from(prob, hmc.PREC_BF16)
+    o = oracle.Oracle(prob)
+    q = prob.q0
+    Um = s.metropolis_energy(torch.from_numpy(q)).cpu().numpy()
+    Ub = s.energy_grad(torch.from_numpy(q))[0].cpu().numpy()
+    Ur, _ = o.energy_grad_batch(q)
+    err_m = np.abs(Um - Ur) / np.abs(Ur)
+    err_b = np.abs(Ub - Ur) / np.abs(Ur)
+    assert np.all(err_m <= 1e-4), (err_m, err_b)
+    # a trajectory's dH follows the FP64 oracle's from the same state and momenta
+    eps, L = 2e-4, 10
+    _, _, dH, _ = s.sample(torch.from_numpy(q), eps, L, 1, seed=6)
+    _, _, dHr, _ = o.sample(q, eps, L, 1, seed=6)
+    dH = dH.cpu().numpy()
+    assert np.all(np.abs(dH - dHr) <= 0.05 + 0.05 * np.abs(dHr)), (dH, dHr, err_m, err_b)

@@ -312,7 +312,7 @@ template <typename T> class SimtEngine final : public Engine {
             T *f = netb_.act[nd.L]->template as<T>();
             const T *sl = nd.act[nd.L - 1] == HMC_ACT_IDENTITY ? nullptr : netb_.slope[nd.L]->template as<T>();
             residual(f, p_.n * p_.dout, y_.as<T>(), sl, inv_s2, delta_[0].as<T>(), false, s);
-            if (nd.any_sampled) backward(nd, x_.as<T>(), 0, p_.n, netb_, delta_[0].as<T>(), s);
+            if (nd.any_sampled && g) backward(nd, x_.as<T>(), 0, p_.n, netb_, delta_[0].as<T>(), s);
         } else {
             const NetDesc &bn = p_.branch, &tn = p_.trunk;
             const int lat = bn.w[bn.L];
@@ -329,7 +329,7 @@ template <typename T> class SimtEngine final : public Engine {
                 launch_gemm(ga, ea, C_, s);
             }
             residual(S, p_.n_u * p_.n_y, t_.as<T>(), nullptr, inv_s2, S, true, s);
-            if (bn.any_sampled) {   // dB = dS T (times the branch output slope)
+            if (bn.any_sampled && g) {   // dB = dS T (times the branch output slope)
                 const bool id = bn.act[bn.L - 1] == HMC_ACT_IDENTITY;
                 GemmArgs<T> ga{(int)p_.n_u, lat, (int)p_.n_y, S, p_.n_y, 1, p_.n_u * p_.n_y,
                                Tm, lat, 1, p_.n_y * lat};
@@ -338,7 +338,7 @@ template <typename T> class SimtEngine final : public Engine {
                 launch_gemm(ga, ea, C_, s);
                 backward(bn, u_.as<T>(), 0, p_.n_u, brb_, dB_.as<T>(), s);
             }
-            if (tn.any_sampled) {   // dT = dS^T B
+            if (tn.any_sampled && g) {   // dT = dS^T B
                 const bool id = tn.act[tn.L - 1] == HMC_ACT_IDENTITY;
                 GemmArgs<T> ga{(int)p_.n_y, lat, (int)p_.n_u, S, 1, p_.n_y, p_.n_u * p_.n_y,
                                Bm, lat, 1, p_.n_u * lat};

@@ -2112,6 +2112,7 @@ class DonEngine final : public Engine {
         nsplit_ = std::max(br_.nsplit, tr_.nsplit);
         gw_part_.alloc(sizeof(float) * nsplit_ * C * std::max<long>(k_, 1));
         HMC_CK(cudaMemset(gw_part_.ptr, 0, gw_part_.n));   // splits a net does not use stay zero
+        exact_.reset(make_simt_engine_f32(p, C));           // before any stream capture
     }
 
     ~DonEngine() override
@@ -2120,7 +2121,15 @@ class DonEngine final : public Engine {
     }
 
     ScatterPlan scatter_plan() override { return plan_; }
-    size_t bytes() const override { return bytes_; }
+    size_t bytes() const override { return bytes_ + (exact_ ? exact_->bytes() : 0); }
+
+    // The Metropolis energy comes from the FP32 CUDA-core engine's forward pass (the
+    // bf16 operator output would carry order-one noise into dH); it scatters q itself.
+    bool has_accurate_energy() const override { return true; }
+    void accurate_energy(const void *q, double *U, cudaStream_t s) override
+    {
+        exact_->energy_grad(q, U, nullptr, false, s);
+    }
 
     void energy_grad(const void *qv, double *U, void *gv, bool scattered, cudaStream_t s) override
     {
@@ -2540,6 +2549,7 @@ class DonEngine final : public Engine {
     DevBuf kind_, desc_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_;
     CUtensorMap ds_row_, ds_atom_, t_row_;
     ScatterPlan plan_;
+    std::unique_ptr<Engine> exact_;
 };
 
 }  // namespace

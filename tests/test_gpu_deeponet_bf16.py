@@ -106,3 +106,11 @@ def test_deeponet_bf16_sampler_runs_and_resumes():
     S2, acc2, dH2, q2 = s.sample(q1, 2e-5, 5, 2, seed=3, first_traj=2)
     assert torch.equal(torch.cat([S1, S2]), S) and torch.equal(torch.cat([dH1, dH2]), dH)
     assert torch.equal(q2, ql)
+
+
+def test_deeponet_bf16_metropolis_energy_is_accurate():
+    prob = W.small_deeponet(n_u=150, n_y=90, du=12, width=64, latent=64, frac=0.3, chains=3, seed=41)
+    s = sampler_from(prob, hmc.PREC_BF16)
+    Um = s.metropolis_energy(torch.from_numpy(prob.q0)).cpu().numpy()
+    Ur, _ = oracle.Oracle(prob).energy_grad_batch(prob.q0)
+    assert np.all(np.abs(Um - Ur) <= 1e-5 * np.abs(Ur)), (Um, Ur)

@@ -656,7 +656,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     cur_c = c;
                 }
                 const int slot = it & 1;
-                if (!mbar_wait_cluster(acc_empty0 + 8 * slot, ((uint32_t)(it >> 1) & 1u) ^ 1u, p.err)) {
+                if (!mbar_wait(acc_empty0 + 8 * slot, ((uint32_t)(it >> 1) & 1u) ^ 1u, p.err)) {
                     ok = false;
                     break;
                 }
@@ -886,7 +886,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
             // release the accumulator slot: one arrival per warp on the leader's barrier
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(lead_acc_empty0 + 8 * slot);
+            if (lane == 0) mbar_arrive_remote(lead_acc_empty0 + 8 * slot);
         }
     }
     tc_fence_before();

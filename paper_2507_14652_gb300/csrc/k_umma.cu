@@ -495,12 +495,13 @@ constexpr int L_STAGES = 4;
 constexpr int L_A_BYTES = BM * BK * 2;                  // one 16 KB K-block of a 128-row tile
 constexpr int L_W_HALF = 64 * 1024;                     // resident half of W, hi or lo (4 K-blocks x 16 KB)
 constexpr int L_STG = 2048;                             // staging bytes per epilogue warp (32 rows x 64 B)
-constexpr int L_SCR_FLOATS = 4 * 256 + 8 * L_STG / 4;       // forward: [4][w] column sums + staging
-constexpr int L_BWD_STG_OFF = 9 * 4 * 256 * 4;          // reverse: [1 + dx][4][w] sums (dx <= 8) in the free lo region, then staging
+constexpr int L_SCR_FLOATS = 4 * 256 + 8 * L_STG / 4;       // forward: [4][w] column sums + staging;
+                                                             // reverse: staging, or [1 + dx][4][w] sums (dx <= 4 at w = 256)
+constexpr int L_AUX = 4 * L_STG;                        // reverse: a warp's 32 x 128 slopes of a tile, in the free lo region
 constexpr int L_SMEM = 1024 + 2 * L_W_HALF + L_STAGES * L_A_BYTES + 256 + L_SCR_FLOATS * 4 + 64 + 64 +
                        2 * 256 * 4 + 2 * 128 * 4;        // + bias and output weights of the chain, half-row sums
 constexpr int L_THREADS = 320;                          // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
-static_assert(L_BWD_STG_OFF + 8 * L_STG <= L_W_HALF, "reverse-pass scratch fits the lo region");
+static_assert(8 * L_AUX <= L_W_HALF, "reverse-pass slope buffers fit the lo region");
 
 struct LayerParams {
     int N, W, C, ntiles, dx;
@@ -538,7 +539,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
     constexpr int TCOLS = 2 * SLOT;
     constexpr int kblk = BN * 128;                     // bytes of one resident K-block of W
     static_assert(NKB * kblk <= L_W_HALF, "resident half of W");
-    static_assert(!(BWD && WSPLIT), "the reverse pass keeps its scratch in the lo region");
+    static_assert(!(BWD && WSPLIT), "the reverse pass keeps its slope buffers in the lo region");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sWh = smem;
@@ -547,8 +548,8 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
     uint64_t *bars = reinterpret_cast<uint64_t *>(sA + L_STAGES * L_A_BYTES);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * L_STAGES + 7);
     float *scr = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(bars) + 256);
-    float *red = BWD ? reinterpret_cast<float *>(sWl) : scr;                          // column sums
-    uint8_t *stage0 = BWD ? sWl + L_BWD_STG_OFF : reinterpret_cast<uint8_t *>(scr + 4 * 256);
+    float *red = scr;                                                                  // column sums
+    uint8_t *stage0 = BWD ? reinterpret_cast<uint8_t *>(scr) : reinterpret_cast<uint8_t *>(scr + 4 * 256);
     double *dred = reinterpret_cast<double *>(scr + L_SCR_FLOATS);   // [4]
     float *fred = reinterpret_cast<float *>(dred + 4);               // [4]
     float *sbias = fred + 16;                                        // [256] bias of the current chain
@@ -694,6 +695,25 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
         const int hc0 = h * (LN / 2);          // first column of this warp's half
         uint8_t *stg = stage0 + (warp - 2) * L_STG;
         const int tr = lane >> 2, tj = lane & 3;   // transposed access: rows tr + 8 i, piece tj
+        // reverse pass: the slopes of a unit's chunk ch land in abuf + ch * L_STG by cp.async,
+        // one commit group per chunk, issued a whole tile ahead of their use
+        const uint32_t abuf = smem_u32(sWl) + (uint32_t)(warp - 2) * L_AUX;
+        auto issue_aux = [&](long v, int ch) {
+            if (v < u1) {
+                const int cv = (int)(v / tpg), tv = (int)(v % tpg) * 2 + (int)rank;
+                const int rv0 = tv * BM + 32 * q;
+                const __nv_bfloat16 *src = p.aux + ((long)cv * p.N + rv0) * p.W + hc0 + 32 * ch + 8 * tj;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int rr = tr + 8 * i;
+                    const bool in = rv0 + rr < p.N;
+                    cp_async16(abuf + ch * L_STG + stg_off(rr, tj), in ? src + (long)rr * p.W : p.aux, in ? 16u : 0u);
+                }
+            }
+            cp_async_commit();
+        };
+        if (BWD)
+            for (int ch = 0; ch < NCH; ++ch) issue_aux(u0, ch);
         int it = 0, chain_loaded = -1;
         for (long u = u0; u < u1; ++u, ++it) {
             const int c = (int)(u / tpg), t = (int)(u % tpg) * 2 + (int)rank;
@@ -704,19 +724,6 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
             const bool valid = m < p.N;
             const long wbase = ((long)c * p.N + r0) * p.W + hc0;   // element (r0, hc0) of [c][N][W]
             const long part = ((long)c * p.ntiles + t) * p.W;
-            // slopes of this tile, 8 rows x 64 B per load, issued before the accumulator wait
-            uint4 ap[BWD ? NCH * 4 : 1];
-            if (BWD) {
-#pragma unroll
-                for (int ch = 0; ch < NCH; ++ch)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int rr = tr + 8 * i;
-                        ap[4 * ch + i] = make_uint4(0u, 0u, 0u, 0u);
-                        if (r0 + rr < p.N)
-                            ap[4 * ch + i] = __ldg(reinterpret_cast<const uint4 *>(p.aux + wbase + (long)rr * p.W + 32 * ch + 8 * tj));
-                    }
-            }
             const float yv = (MODE == L_FWD_OUT && valid) ? p.y[m] : 0.0f;
             float xv[8];
 #pragma unroll
@@ -773,13 +780,17 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     float dd[32];
                     tmem_ld_wait(rb[ch & 1]);
                     if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
-                    // slopes of this chunk: 8-row pieces in, own row out
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) *reinterpret_cast<uint4 *>(stg + stg_off(tr + 8 * i, tj)) = ap[4 * ch + i];
+                    // slopes of this chunk: exactly NCH - 1 groups were committed after this one
+                    cp_async_wait<NCH - 1>();
                     __syncwarp();
+                    uint4 av[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) av[j] = lds128(abuf + ch * L_STG + stg_off(lane, j));
+                    __syncwarp();   // every lane has its row: refill the chunk for the next unit
+                    issue_aux(u + 1, ch);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const uint4 uu = *reinterpret_cast<const uint4 *>(stg + stg_off(lane, j));
+                        const uint4 uu = av[j];
                         const uint32_t w4[4] = {uu.x, uu.y, uu.z, uu.w};
 #pragma unroll
                         for (int tt = 0; tt < 4; ++tt) {
@@ -793,9 +804,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                         uint32_t pk[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
-                        store_chunk(pk, c0);   // its first __syncwarp also orders the slope reads
-                    } else {
-                        __syncwarp();          // slope reads done before the next chunk's pieces land
+                        store_chunk(pk, c0);
                     }
                     if (MODE == L_BWD_FIRST) {   // first-layer weight and bias gradients: column sums
                         for (int d = 0; d < p.dx; ++d) {
@@ -888,6 +897,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
             __syncwarp();
             if (lane == 0) mbar_arrive_remote(lead_acc_empty0 + 8 * slot);
         }
+        if (BWD) cp_async_wait<0>();   // no copy into shared memory outlives the loop
     }
     tc_fence_before();
     __syncthreads();
@@ -1595,7 +1605,8 @@ class UmmaEngine final : public Engine {
         dw0_part_.alloc(sizeof(float) * C * ntiles_ * w_ * dx_);
         db_part_.resize(L_ - 1);   // biases of layers 0..L-2, per-tile column sums
         for (int l = 0; l <= L_ - 2; ++l) db_part_[l].reset(new DevBuf(sizeof(float) * C * ntiles_ * w_));
-        use_layer_ = (w_ == 128 || w_ == 256);
+        // the persistent pair kernels keep the first layer's column sums in 20 KB: dx <= 4 at w = 256
+        use_layer_ = (w_ == 128 || (w_ == 256 && dx_ <= 4));
 
         // per-entry metadata, scatter plan, per-layer CSR of the sampled hidden weights
         build_entries();

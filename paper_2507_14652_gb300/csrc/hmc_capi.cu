@@ -396,6 +396,11 @@ struct hmc_handle_s {
     cudaStream_t user_stream = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // batches: each problem's gradient runs on its own stream between a fork and a join
+    // event, so the problems overlap on the GPU (and become parallel graph branches)
+    std::vector<cudaStream_t> lanes;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
     std::vector<std::unique_ptr<Problem>> probs;
     std::vector<std::unique_ptr<Engine>> engines;
     std::vector<long> qoff;
@@ -412,6 +417,9 @@ struct hmc_handle_s {
     ~hmc_handle_s()
     {
         if (traj_exec) cudaGraphExecDestroy(traj_exec);
+        for (cudaStream_t l : lanes) cudaStreamDestroy(l);
+        for (cudaEvent_t e : ev_join) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
     }
 };
 
@@ -522,25 +530,46 @@ void join_out(hmc_handle h)
     HMC_CK(cudaStreamWaitEvent(h->user_stream, h->ev_out, 0));
 }
 
+// Run fn(problem, stream) for every problem.  Batches fork onto the handle's lanes
+// (problem i on lane i mod lanes) and join back on the handle's stream, so the
+// problems overlap on the GPU and a captured trajectory has one branch per lane.
+template <typename F> void for_each_problem(hmc_handle h, F &&fn)
+{
+    if (h->nprob == 1) {
+        fn(0, h->stream);
+        return;
+    }
+    HMC_CK(cudaEventRecord(h->ev_fork, h->stream));
+    for (cudaStream_t l : h->lanes) HMC_CK(cudaStreamWaitEvent(l, h->ev_fork, 0));
+    for (int i = 0; i < h->nprob; ++i) fn(i, h->lanes[i % h->lanes.size()]);
+    for (size_t j = 0; j < h->lanes.size(); ++j) {
+        HMC_CK(cudaEventRecord(h->ev_join[j], h->lanes[j]));
+        HMC_CK(cudaStreamWaitEvent(h->stream, h->ev_join[j], 0));
+    }
+}
+
 void energy_grad_all(hmc_handle h, void *q, double *U, void *g, bool scattered)
 {
-    for (int i = 0; i < h->nprob; ++i) {
+    for_each_problem(h, [&](int i, cudaStream_t s) {
         char *qb = static_cast<char *>(q) + h->qoff[i] * h->elem;
         char *gb = g ? static_cast<char *>(g) + h->qoff[i] * h->elem : nullptr;
-        h->engines[i]->energy_grad(qb, U + (long)i * h->C, gb, scattered, h->stream);
-    }
+        h->engines[i]->energy_grad(qb, U + (long)i * h->C, gb, scattered, s);
+    });
 }
 
 // Overwrite U with the accurate energy where an engine's energy_grad U is a
 // reduced-precision one (q already scattered by the preceding energy_grad_all).
 void accurate_energy_all(hmc_handle h, void *q, double *U)
 {
-    for (int i = 0; i < h->nprob; ++i) {
+    bool any = false;
+    for (auto &e : h->engines) any = any || e->has_accurate_energy();
+    if (!any) return;
+    for_each_problem(h, [&](int i, cudaStream_t s) {
         Engine *e = h->engines[i].get();
-        if (!e->has_accurate_energy()) continue;
+        if (!e->has_accurate_energy()) return;
         char *qb = static_cast<char *>(q) + h->qoff[i] * h->elem;
-        e->accurate_energy(qb, U + (long)i * h->C, h->stream);
-    }
+        e->accurate_energy(qb, U + (long)i * h->C, s);
+    });
 }
 
 // A device view of a user array: the pointer itself when it is device memory,
@@ -624,6 +653,16 @@ hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, co
     HMC_CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     HMC_CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
     HMC_CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    if (nprob > 1) {   // up to 16 concurrent problem lanes
+        HMC_CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        const int nl = std::min(nprob, 16);
+        h->lanes.resize(nl, nullptr);
+        h->ev_join.resize(nl, nullptr);
+        for (int j = 0; j < nl; ++j) {
+            HMC_CK(cudaStreamCreateWithFlags(&h->lanes[j], cudaStreamNonBlocking));
+            HMC_CK(cudaEventCreateWithFlags(&h->ev_join[j], cudaEventDisableTiming));
+        }
+    }
     for (int i = 0; i < nprob; ++i) {
         h->probs.push_back(build_problem(specs[i], data[i], alpha[i], sigma[i], masks[i], frozen[i], C));
         Problem &p = *h->probs.back();

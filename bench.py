@@ -322,6 +322,7 @@ def main():
                 "abs_dH_median": float(np.nanmedian(np.abs(dH_np))),
                 "gpu_launches": gpu_launches, "kernels_per_trajectory": graph_k,
                 "roofline": roof, "kernel_ms": {k: v[0] for k, v in prof.items()},
+                "tuning": s.tuning().strip(),
                 "kernel_launches_per_eval": {k: v[1] for k, v in prof.items()},
                 "e2e": e2e, "cpu_baseline": cpu, "ess": ess, "clocks": clocks}
         print(json.dumps(line), flush=True)

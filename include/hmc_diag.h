@@ -37,6 +37,11 @@ HMC_API long hmc_diag_graph_kernels(hmc_handle h);
  * hi/lo activations, elsewhere the energy of hmc_energy_grad. */
 HMC_API hmc_status hmc_diag_metropolis_energy(hmc_handle h, const void *q, double *U);
 
+/* What each problem's engine autotuned at creation (tile shapes and grids, with the
+ * measured candidates), one line per problem, NUL-terminated in buf (truncated to n
+ * bytes).  Returns the length of the full text. */
+HMC_API long hmc_diag_tuning(hmc_handle h, char *buf, long n);
+
 typedef struct {
     char name[48];      /* kernel kind */
     double ms_total;    /* summed CUDA-event time over all its launches */

@@ -35,7 +35,7 @@ EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_subset_size", "hmc_param_count
            "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_adapt_step_size", "hmc_destroy", "hmc_last_error",
            "hmc_energy_grad_noalloc",
            "hmc_diag_philox", "hmc_diag_momenta", "hmc_diag_log_uniform", "hmc_diag_graph_kernels",
-           "hmc_diag_profile_energy_grad", "hmc_diag_metropolis_energy"]
+           "hmc_diag_profile_energy_grad", "hmc_diag_metropolis_energy", "hmc_diag_tuning"]
 
 
 class HmcError(RuntimeError):
@@ -101,9 +101,11 @@ def lib():
         L.hmc_diag_profile_energy_grad.argtypes = [vp, vp, i, vp, i]
         L.hmc_diag_umma_gemm.argtypes = [i] * 6 + [vp] * 3
         L.hmc_diag_metropolis_energy.argtypes = [vp, vp, vp]
+        L.hmc_diag_tuning.argtypes = [vp, ct.c_char_p, lg]
+        L.hmc_diag_tuning.restype = lg
         for f in EXPORTS:
             if f not in ("hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_last_error",
-                         "hmc_diag_graph_kernels"):
+                         "hmc_diag_graph_kernels", "hmc_diag_tuning"):
                 getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -258,6 +260,13 @@ class Sampler:
         _check(lib().hmc_adapt_step_size(self._h, _ptr(q), int(L), float(eps0), int(n_warmup), float(target_accept),
                                          int(seed), int(first_traj), ct.byref(eps)))
         return eps.value, q
+
+    def tuning(self):
+        """What the engines autotuned at creation (hmc_diag_tuning)."""
+        n = lib().hmc_diag_tuning(self._h, None, 0)
+        buf = ct.create_string_buffer(int(n) + 1)
+        lib().hmc_diag_tuning(self._h, buf, int(n) + 1)
+        return buf.value.decode()
 
     def metropolis_energy(self, q):
         """U [C] used by the Metropolis test (hmc_diag_metropolis_energy)."""

@@ -960,6 +960,19 @@ const char *hmc_last_error(void) { return g_err.c_str(); }
 
 long hmc_diag_graph_kernels(hmc_handle h) { return h ? h->traj_kernels : -1; }
 
+long hmc_diag_tuning(hmc_handle h, char *buf, long n)
+{
+    if (!h) return -1;
+    std::string t;
+    for (int i = 0; i < h->nprob; ++i) t += "problem " + std::to_string(i) + ": " + h->engines[i]->tuning() + "\n";
+    if (buf && n > 0) {
+        const size_t m = std::min<size_t>((size_t)n - 1, t.size());
+        memcpy(buf, t.data(), m);
+        buf[m] = 0;
+    }
+    return (long)t.size();
+}
+
 hmc_status hmc_diag_metropolis_energy(hmc_handle h, const void *q, double *U)
 {
     g_err.clear();

@@ -90,6 +90,8 @@ struct Engine {
     // provide a second, accurate U(q); q is already scattered into the network.
     virtual bool has_accurate_energy() const { return false; }
     virtual void accurate_energy(const void *q, double *U, cudaStream_t s) {}
+    // what the engine's autotuner chose at creation ("" if it tunes nothing)
+    virtual std::string tuning() const { return std::string(); }
 };
 
 struct Problem {

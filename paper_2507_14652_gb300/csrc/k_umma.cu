@@ -23,7 +23,11 @@
 // bit-reproducible.
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
 
 #include "hmc_diag.h"
 #include "hmc_internal.cuh"
@@ -932,6 +936,7 @@ constexpr int DW_STAGE = DW_A_BYTES + DW_B_BYTES;
 constexpr int DW_ONES = 16 * 128;              // 16 K-major rows of 64 bf16 ones
 constexpr int DW_SMEM = 1024 + DW_STAGES * DW_STAGE + DW_ONES + 256;
 constexpr int DW_TCOLS = 256;                  // 128 columns of dW + 16 of row sums
+constexpr int kMaxSplits = 32;                 // largest row-split count the autotuner tries
 static_assert(DW_STAGES * DW_STAGE >= 128 * 129 * 4, "the epilogue staging reuses the operand stages");
 
 __global__ void __launch_bounds__(NTHREADS, 2) k_dw2(const __grid_constant__ CUtensorMap tmD,
@@ -1615,27 +1620,14 @@ class UmmaEngine final : public Engine {
         const int total_kb = (int)((N_ + BK - 1) / BK);
         nsplit_ = pick_splits(total_kb, ((w_ + BM - 1) / BM) * C, 2 * num_sms_);
         nsplit2_ = pick_splits(total_kb, (w_ / 128) * (w_ / 128) * C, 2 * num_sms_);
-        nsplit_ = std::max(nsplit_, nsplit2_);
+        // the autotuner may pick any row-split count up to kMaxSplits for the persistent path
+        const int max_splits = use_layer_ ? std::min(kMaxSplits, total_kb) : 1;
+        nsplit_ = std::max(std::max(nsplit_, nsplit2_), max_splits);
         gw_part_.alloc(sizeof(float) * nsplit_ * C * std::max<long>(k_, 1));
         HMC_CK(cudaMemset(gw_part_.ptr, 0, gw_part_.n));
-
-        // bias gradients: the first layer's from its reverse kernel (per tile); the hidden
-        // layers' from the weight-gradient kernel (per row split) on the persistent path
-        // descriptors 0..L-2: biases; L-1: first-layer weights; L: output weights; L+1: output bias
-        std::vector<DbDesc> dbd(L_ + 2);
         dbw_part_.resize(L_ - 1);
-        for (int l = 0; l <= L_ - 2; ++l) {
-            dbd[l] = DbDesc{db_part_[l]->as<float>(), (long)ntiles_ * w_, w_, ntiles_};
-            if (use_layer_ && l >= 1) {
-                dbw_part_[l].reset(new DevBuf(sizeof(float) * nsplit_eff() * C * w_));
-                dbd[l] = DbDesc{dbw_part_[l]->as<float>(), w_, (long)C * w_, nsplit_eff()};
-            }
-        }
-        dbd[L_ - 1] = DbDesc{dw0_part_.as<float>(), (long)ntiles_ * w_ * dx_, (long)w_ * dx_, ntiles_};
-        dbd[L_] = DbDesc{dwout_part_.as<float>(), (long)ntiles_ * w_, w_, ntiles_};
-        dbd[L_ + 1] = DbDesc{dbout_part_.as<float>(), ntiles_, 1, ntiles_};
-        db_desc_.alloc(sizeof(DbDesc) * dbd.size());
-        HMC_CK(cudaMemcpy(db_desc_.ptr, dbd.data(), sizeof(DbDesc) * dbd.size(), cudaMemcpyHostToDevice));
+        for (int l = 1; use_layer_ && l <= L_ - 2; ++l)
+            dbw_part_[l].reset(new DevBuf(sizeof(float) * nsplit_ * C * w_));
 
         // tensor maps
         if (use_layer_) max_clusters_ = layer_max_clusters();
@@ -1655,7 +1647,24 @@ class UmmaEngine final : public Engine {
             D_row_[i] = make_map(D_[i]->ptr, w_, N_, C, 64, 128);
             D_atom_[i] = make_map(D_[i]->ptr, w_, N_, C, 64, 64);
         }
+        if (use_layer_) tune_dw_splits(total_kb);
+
+        // bias gradients: the first layer's from its reverse kernel (per tile); the hidden
+        // layers' from the weight-gradient kernel (per row split) on the persistent path
+        // descriptors 0..L-2: biases; L-1: first-layer weights; L: output weights; L+1: output bias
+        std::vector<DbDesc> dbd(L_ + 2);
+        for (int l = 0; l <= L_ - 2; ++l) {
+            dbd[l] = DbDesc{db_part_[l]->as<float>(), (long)ntiles_ * w_, w_, ntiles_};
+            if (use_layer_ && l >= 1) dbd[l] = DbDesc{dbw_part_[l]->as<float>(), w_, (long)C * w_, nsplit_eff()};
+        }
+        dbd[L_ - 1] = DbDesc{dw0_part_.as<float>(), (long)ntiles_ * w_ * dx_, (long)w_ * dx_, ntiles_};
+        dbd[L_] = DbDesc{dwout_part_.as<float>(), (long)ntiles_ * w_, w_, ntiles_};
+        dbd[L_ + 1] = DbDesc{dbout_part_.as<float>(), ntiles_, 1, ntiles_};
+        db_desc_.alloc(sizeof(DbDesc) * dbd.size());
+        HMC_CK(cudaMemcpy(db_desc_.ptr, dbd.data(), sizeof(DbDesc) * dbd.size(), cudaMemcpyHostToDevice));
     }
+
+    std::string tuning() const override { return tuning_; }
 
     ~UmmaEngine() override
     {
@@ -1813,6 +1822,65 @@ class UmmaEngine final : public Engine {
     }
 
   private:
+    // Autotuner for the weight-gradient grid: time each row-split count on this engine's
+    // own buffers (one warm-up, three timed launches, CUDA events) and keep the fastest;
+    // the choice is cached per (rows, width, chains) for the process.
+    void tune_dw_splits(int total_kb)
+    {
+        int layer = -1;
+        for (int i = 1; i <= L_ - 2 && layer < 0; ++i)
+            if (layer_entries_[i] > 0 || bias_entries_[i] > 0) layer = i;
+        if (layer < 0) return;
+        static std::mutex mu;
+        static std::map<std::tuple<long, int, int>, int> cache;
+        const auto key = std::make_tuple(N_, w_, C_);
+        {
+            std::lock_guard<std::mutex> g(mu);
+            auto it = cache.find(key);
+            if (it != cache.end()) {
+                nsplit2_ = it->second;
+                tuning_ = "dw row splits " + std::to_string(nsplit2_) + " (cached)";
+                return;
+            }
+        }
+        cudaStream_t s;
+        cudaEvent_t a, b;
+        HMC_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        HMC_CK(cudaEventCreate(&a));
+        HMC_CK(cudaEventCreate(&b));
+        int best = nsplit2_;
+        float best_ms = 1e30f;
+        std::string log;
+        for (int cand : {1, 2, 4, 8, 16, 32}) {
+            if (cand > std::min(kMaxSplits, total_kb)) break;
+            nsplit2_ = cand;
+            dw_layer(layer, s);
+            HMC_CK(cudaEventRecord(a, s));
+            for (int r = 0; r < 3; ++r) dw_layer(layer, s);
+            HMC_CK(cudaEventRecord(b, s));
+            HMC_CK(cudaEventSynchronize(b));
+            float ms = 0.0f;
+            HMC_CK(cudaEventElapsedTime(&ms, a, b));
+            ms /= 3.0f;
+            char buf[48];
+            snprintf(buf, sizeof buf, "%s%d:%.1fus", log.empty() ? "" : " ", cand, 1000.0f * ms);
+            log += buf;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+            }
+        }
+        HMC_CK(cudaStreamSynchronize(s));
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        cudaStreamDestroy(s);
+        HMC_CK(cudaMemset(gw_part_.ptr, 0, gw_part_.n));
+        nsplit2_ = best;
+        tuning_ = "dw row splits " + std::to_string(best) + " of {" + log + "}";
+        std::lock_guard<std::mutex> g(mu);
+        cache[key] = best;
+    }
+
     // weight gradient of hidden layer i (dW = delta_{i+1}^T A_i) at its sampled entries
     void dw_layer(int i, cudaStream_t s)
     {
@@ -2033,6 +2101,7 @@ class UmmaEngine final : public Engine {
     bool use_layer_ = false;
     int max_clusters_ = 1;
     ScatterPlan plan_;
+    std::string tuning_;
 };
 
 // ---------------------------------------------------------------------------
@@ -2108,8 +2177,9 @@ class DonEngine final : public Engine {
         bs_ = ny_ >= 256 ? 256 : (int)round_up(ny_, 32);
         nut_ = (int)std::max<long>(1, (nu_ + BM - 1) / BM);
         ntn_ = (int)std::max<long>(1, (ny_ + bs_ - 1) / bs_);
-        u_part_.alloc(sizeof(double) * C * nut_ * ntn_);
-        db0_part_.alloc(sizeof(float) * C * nut_ * ntn_);
+        const long max_ntn = std::max<long>(1, (ny_ + 127) / 128);   // room for the narrowest tile
+        u_part_.alloc(sizeof(double) * C * nut_ * max_ntn);
+        db0_part_.alloc(sizeof(float) * C * nut_ * max_ntn);
         b0v_.alloc(sizeof(float) * C);
         {
             std::vector<float> v(C, p.b0_off >= 0 ? (float)p.frozen[p.b0_off] : 0.0f);
@@ -2117,6 +2187,7 @@ class DonEngine final : public Engine {
         }
         ds_row_ = make_map_ld(ds_.ptr, ny_, nyp_, nu_, C, 64, 128);
         ds_atom_ = make_map_ld(ds_.ptr, ny_, nyp_, nu_, C, 64, 64);
+        if (ny_ > 128) tune_s_tile();
         t_row_ = make_map(tr_.act[tr_.L]->ptr, pl_, ny_, C, 64, bs_);
 
         build_entries();
@@ -2153,26 +2224,7 @@ class DonEngine final : public Engine {
         }
         forward(br_, s);
         forward(tr_, s);
-        // S = B T^T + b0, residual, energy partials and dS
-        {
-            Params pp = base();
-            pp.M = (int)nu_;
-            pp.N = bs_;
-            pp.K = pl_;
-            pp.kb_per_split = (pl_ + BK - 1) / BK;
-            pp.ntiles = nut_;
-            pp.Yt = yt_.as<float>();
-            pp.ny = (int)ny_;
-            pp.ldo = (int)nyp_;
-            pp.ntn = ntn_;
-            pp.b0s = b0v_.as<float>();
-            pp.out = ds_.as<__nv_bfloat16>();
-            pp.out_b = nu_ * nyp_;
-            pp.inv_s2 = (float)(1.0 / (p_.sigma * p_.sigma));
-            pp.u_part = u_part_.as<double>();
-            pp.db0_part = db0_part_.as<float>();
-            launch_umma<M_S, false, false, false>(br_.act_row[br_.L], t_row_, t_row_, pp, dim3(C_, nut_, ntn_), s);
-        }
+        launch_s(t_row_, s);   // S = B T^T + b0, residual, energy partials and dS
         // dB = dS T and dT = dS^T B: the deltas of the two nets' linear output layers
         {
             Params pp = base();
@@ -2222,12 +2274,77 @@ class DonEngine final : public Engine {
         }
     }
 
+    std::string tuning() const override { return tuning_; }
+
   private:
     Params base() const
     {
         Params pp{};
         pp.err = err_;
         return pp;
+    }
+
+    void launch_s(const CUtensorMap &tmap, cudaStream_t s)
+    {
+        Params pp = base();
+        pp.M = (int)nu_;
+        pp.N = bs_;
+        pp.K = pl_;
+        pp.kb_per_split = (pl_ + BK - 1) / BK;
+        pp.ntiles = nut_;
+        pp.Yt = yt_.as<float>();
+        pp.ny = (int)ny_;
+        pp.ldo = (int)nyp_;
+        pp.ntn = ntn_;
+        pp.b0s = b0v_.as<float>();
+        pp.out = ds_.as<__nv_bfloat16>();
+        pp.out_b = nu_ * nyp_;
+        pp.inv_s2 = (float)(1.0 / (p_.sigma * p_.sigma));
+        pp.u_part = u_part_.as<double>();
+        pp.db0_part = db0_part_.as<float>();
+        launch_umma<M_S, false, false, false>(br_.act_row[br_.L], tmap, tmap, pp, dim3(C_, nut_, ntn_), s);
+    }
+
+    // Autotuner for the operator-output tile: time S on 128- and 256-column tiles on this
+    // engine's own buffers (one warm-up, three timed launches) and keep the faster one.
+    void tune_s_tile()
+    {
+        cudaStream_t s;
+        cudaEvent_t a, b;
+        HMC_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        HMC_CK(cudaEventCreate(&a));
+        HMC_CK(cudaEventCreate(&b));
+        int best = bs_;
+        float best_ms = 1e30f;
+        std::string log;
+        for (int cand : {128, 256}) {
+            if (cand > round_up(ny_, 32) && cand != 128) break;
+            bs_ = cand;
+            ntn_ = (int)((ny_ + bs_ - 1) / bs_);
+            const CUtensorMap tm = make_map(tr_.act[tr_.L]->ptr, pl_, ny_, C_, 64, bs_);
+            launch_s(tm, s);
+            HMC_CK(cudaEventRecord(a, s));
+            for (int r = 0; r < 3; ++r) launch_s(tm, s);
+            HMC_CK(cudaEventRecord(b, s));
+            HMC_CK(cudaEventSynchronize(b));
+            float ms = 0.0f;
+            HMC_CK(cudaEventElapsedTime(&ms, a, b));
+            ms /= 3.0f;
+            char buf[48];
+            snprintf(buf, sizeof buf, "%s%d:%.1fus", log.empty() ? "" : " ", cand, 1000.0f * ms);
+            log += buf;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+            }
+        }
+        HMC_CK(cudaStreamSynchronize(s));
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        cudaStreamDestroy(s);
+        bs_ = best;
+        ntn_ = (int)((ny_ + bs_ - 1) / bs_);
+        tuning_ = "S column tile " + std::to_string(best) + " of {" + log + "}";
     }
 
     DevBuf *track(DevBuf *b)   // an allocated buffer
@@ -2561,6 +2678,7 @@ class DonEngine final : public Engine {
     CUtensorMap ds_row_, ds_atom_, t_row_;
     ScatterPlan plan_;
     std::unique_ptr<Engine> exact_;
+    std::string tuning_;
 };
 
 }  // namespace

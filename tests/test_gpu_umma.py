@@ -153,3 +153,19 @@ def test_bf16_metropolis_energy_is_accurate():
     _, _, dHr, _ = o.sample(q, eps, L, 1, seed=6)
     dH = dH.cpu().numpy()
     assert np.all(np.abs(dH - dHr) <= 0.05 + 0.05 * np.abs(dHr)), (dH, dHr, err_m, err_b)
+
+
+def test_autotuner_reports_its_choices():
+    # the weight-gradient grid (row splits) is timed per shape at handle creation
+    prob = W.small_mlp(n=3000, widths=(2, 256, 256, 256, 1), frac=0.05, chains=4, seed=61)
+    s = sampler_from(prob, hmc.PREC_BF16)
+    t = s.tuning()
+    assert t.startswith("problem 0: dw row splits "), t
+    # a second handle of the same shape reuses the cached choice
+    s2 = sampler_from(prob, hmc.PREC_BF16)
+    assert "(cached)" in s2.tuning(), s2.tuning()
+    # results do not depend on which handle tuned
+    q = torch.from_numpy(prob.q0)
+    U1, g1 = s.energy_grad(q)
+    U2, g2 = s2.energy_grad(q)
+    assert torch.equal(U1, U2) and torch.equal(g1, g2)

@@ -88,9 +88,10 @@ struct Params {
     const int *erow;                      // M_DW: row of entry j
     const int *epack;                     // row << 16 | column of entry j (dW gather)
     float *gw_part; long gw_split; long gw_b;   // M_DW: [split][b][k]
-    // M_S: targets Yt [M][ny] (shared by the chains), valid columns ny, output row
-    // stride ldo, per-chain scalar bias b0s [b]; partials per (row tile, column tile)
-    const float *Yt; int ny, ldo, ntn;
+    // M_S computes S^T = T B^T: rows are the ny query points, columns the nu input
+    // functions; targets Yt [nu][ny] (shared by the chains), dS [b][nu][ldo], per-chain
+    // scalar bias b0s [b]; partials per (row tile, column tile)
+    const float *Yt; int ny, nu, ldo, ntn;
     const float *b0s;
     float *db0_part;                      // [b][ntiles][ntn]
 };
@@ -254,38 +255,34 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                     }
                 }
             } else if (MODE == M_S) {
-                // r = S + b0 - Y; dS = r / sigma^2 in bf16; sum r^2 (FP64) and dS per tile
+                // lane = query point y, columns = input functions u: r = S + b0 - Y[u][y] and
+                // dS[u][y] = r / sigma^2 in bf16; per load and store a warp covers 32
+                // consecutive y of one u.  Squares summed in FP32 per chunk, carried in FP64.
                 const float b0 = p.b0s[b];
-                const float *yrow = p.Yt + (long)(valid ? m : 0) * p.ny;
-                __nv_bfloat16 *orow = p.out + (long)b * p.out_b + (long)(valid ? m : 0) * p.ldo;
+                __nv_bfloat16 *ob = p.out + (long)b * p.out_b + m;
+                const float *yb = p.Yt + m;
                 double r2 = 0.0;
                 float dsum = 0.0f;
                 for (int c0 = 0; c0 < BN; c0 += 32) {
                     float v[32];
                     tmem_ld32(taddr + c0, v);
-                    const int y0 = n0 + c0;
-                    if (valid && y0 < p.ny) {
-                        float ds[32], r2c = 0.0f;   // 32 squares in FP32, their sum carried in FP64
+                    const int u0 = n0 + c0;
+                    if (valid && u0 < p.nu) {
+                        float yv[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) yv[j] = u0 + j < p.nu ? __ldg(yb + (long)(u0 + j) * p.ny) : 0.0f;
+                        float r2c = 0.0f;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
-                            const bool ok = y0 + j < p.ny;
-                            const float r = ok ? (v[j] + b0) - yrow[y0 + j] : 0.0f;
-                            r2c += r * r;
-                            ds[j] = r * p.inv_s2;
-                            dsum += ds[j];
-                        }
-                        r2 += (double)r2c;
-#pragma unroll
-                        for (int g8 = 0; g8 < 4; ++g8) {
-                            const int y = y0 + 8 * g8;
-                            if (y + 8 <= p.ny) {
-                                *reinterpret_cast<uint4 *>(orow + y) =
-                                    make_uint4(pack_bf16(ds[8 * g8], ds[8 * g8 + 1]), pack_bf16(ds[8 * g8 + 2], ds[8 * g8 + 3]),
-                                               pack_bf16(ds[8 * g8 + 4], ds[8 * g8 + 5]), pack_bf16(ds[8 * g8 + 6], ds[8 * g8 + 7]));
-                            } else {
-                                for (int e = 0; e < 8 && y + e < p.ny; ++e) orow[y + e] = __float2bfloat16_rn(ds[8 * g8 + e]);
+                            if (u0 + j < p.nu) {
+                                const float r = (v[j] + b0) - yv[j];
+                                r2c += r * r;
+                                const float ds = r * p.inv_s2;
+                                dsum += ds;
+                                ob[(long)(u0 + j) * p.ldo] = __float2bfloat16_rn(ds);
                             }
                         }
+                        r2 += (double)r2c;
                     }
                 }
 #pragma unroll
@@ -2174,10 +2171,11 @@ class DonEngine final : public Engine {
         if (!tf.empty()) HMC_CK(cudaMemcpy(yt_.ptr, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice));
         ds_.alloc(sizeof(__nv_bfloat16) * C * std::max<long>(nu_, 1) * nyp_);
         HMC_CK(cudaMemset(ds_.ptr, 0, ds_.n));
-        bs_ = ny_ >= 256 ? 256 : (int)round_up(ny_, 32);
-        nut_ = (int)std::max<long>(1, (nu_ + BM - 1) / BM);
-        ntn_ = (int)std::max<long>(1, (ny_ + bs_ - 1) / bs_);
-        const long max_ntn = std::max<long>(1, (ny_ + 127) / 128);   // room for the narrowest tile
+        // S^T tiles: 128 query points (rows) x bs_ input functions (columns)
+        bs_ = nu_ >= 256 ? 256 : (int)round_up(nu_, 32);
+        nut_ = (int)std::max<long>(1, (ny_ + BM - 1) / BM);
+        ntn_ = (int)std::max<long>(1, (nu_ + bs_ - 1) / bs_);
+        const long max_ntn = std::max<long>(1, (nu_ + 127) / 128);   // room for the narrowest tile
         u_part_.alloc(sizeof(double) * C * nut_ * max_ntn);
         db0_part_.alloc(sizeof(float) * C * nut_ * max_ntn);
         b0v_.alloc(sizeof(float) * C);
@@ -2187,8 +2185,8 @@ class DonEngine final : public Engine {
         }
         ds_row_ = make_map_ld(ds_.ptr, ny_, nyp_, nu_, C, 64, 128);
         ds_atom_ = make_map_ld(ds_.ptr, ny_, nyp_, nu_, C, 64, 64);
-        if (ny_ > 128) tune_s_tile();
-        t_row_ = make_map(tr_.act[tr_.L]->ptr, pl_, ny_, C, 64, bs_);
+        if (nu_ > 128) tune_s_tile();
+        b_col_ = make_map(br_.act[br_.L]->ptr, pl_, nu_, C, 64, bs_);
 
         build_entries();
         nsplit_ = std::max(br_.nsplit, tr_.nsplit);
@@ -2224,7 +2222,7 @@ class DonEngine final : public Engine {
         }
         forward(br_, s);
         forward(tr_, s);
-        launch_s(t_row_, s);   // S = B T^T + b0, residual, energy partials and dS
+        launch_s(b_col_, s);   // S = B T^T + b0, residual, energy partials and dS
         // dB = dS T and dT = dS^T B: the deltas of the two nets' linear output layers
         {
             Params pp = base();
@@ -2284,16 +2282,17 @@ class DonEngine final : public Engine {
         return pp;
     }
 
-    void launch_s(const CUtensorMap &tmap, cudaStream_t s)
+    void launch_s(const CUtensorMap &bmap, cudaStream_t s)
     {
         Params pp = base();
-        pp.M = (int)nu_;
+        pp.M = (int)ny_;
         pp.N = bs_;
         pp.K = pl_;
         pp.kb_per_split = (pl_ + BK - 1) / BK;
         pp.ntiles = nut_;
         pp.Yt = yt_.as<float>();
         pp.ny = (int)ny_;
+        pp.nu = (int)nu_;
         pp.ldo = (int)nyp_;
         pp.ntn = ntn_;
         pp.b0s = b0v_.as<float>();
@@ -2302,7 +2301,7 @@ class DonEngine final : public Engine {
         pp.inv_s2 = (float)(1.0 / (p_.sigma * p_.sigma));
         pp.u_part = u_part_.as<double>();
         pp.db0_part = db0_part_.as<float>();
-        launch_umma<M_S, false, false, false>(br_.act_row[br_.L], tmap, tmap, pp, dim3(C_, nut_, ntn_), s);
+        launch_umma<M_S, false, false, false>(tr_.act_row[tr_.L], bmap, bmap, pp, dim3(C_, nut_, ntn_), s);
     }
 
     // Autotuner for the operator-output tile: time S on 128- and 256-column tiles on this
@@ -2318,10 +2317,10 @@ class DonEngine final : public Engine {
         float best_ms = 1e30f;
         std::string log;
         for (int cand : {128, 256}) {
-            if (cand > round_up(ny_, 32) && cand != 128) break;
+            if (cand > round_up(nu_, 32) && cand != 128) break;
             bs_ = cand;
-            ntn_ = (int)((ny_ + bs_ - 1) / bs_);
-            const CUtensorMap tm = make_map(tr_.act[tr_.L]->ptr, pl_, ny_, C_, 64, bs_);
+            ntn_ = (int)((nu_ + bs_ - 1) / bs_);
+            const CUtensorMap tm = make_map(br_.act[br_.L]->ptr, pl_, nu_, C_, 64, bs_);
             launch_s(tm, s);
             HMC_CK(cudaEventRecord(a, s));
             for (int r = 0; r < 3; ++r) launch_s(tm, s);
@@ -2343,7 +2342,7 @@ class DonEngine final : public Engine {
         cudaEventDestroy(b);
         cudaStreamDestroy(s);
         bs_ = best;
-        ntn_ = (int)((ny_ + bs_ - 1) / bs_);
+        ntn_ = (int)((nu_ + bs_ - 1) / bs_);
         tuning_ = "S column tile " + std::to_string(best) + " of {" + log + "}";
     }
 
@@ -2675,7 +2674,7 @@ class DonEngine final : public Engine {
     DonNet br_, tr_;
     DevBuf yt_, ds_, u_part_, db0_part_, b0v_, gw_part_, db_desc_;
     DevBuf kind_, desc_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_;
-    CUtensorMap ds_row_, ds_atom_, t_row_;
+    CUtensorMap ds_row_, ds_atom_, b_col_;
     ScatterPlan plan_;
     std::unique_ptr<Engine> exact_;
     std::string tuning_;

@@ -1083,16 +1083,23 @@ constexpr int E3_B = 256 * BK * 2;           // 32 KB: one half of a W K-block
 constexpr int E3_STAGE = 2 * E3_A + 2 * E3_B;
 constexpr int E3_SMEM = 1024 + E3_STAGES * E3_STAGE + 256 + 64;
 
+// E3_TANH / E3_LIN: a layer whose output goes on as a hi/lo pair (tanh or linear);
+// E3_OUT: the MLP's last hidden layer + scalar output + residual; E3_S: the DeepONet's
+// S^T = T B^T on 128 x N tiles (N columns starting at blockIdx.y N) + residual.
+enum E3Mode { E3_TANH = 0, E3_LIN = 1, E3_OUT = 2, E3_S = 3 };
+
 struct E3Params {
     int M, N, K, ntiles;
     int *err;
     const float *bias;                   // [b][N]
     __nv_bfloat16 *out_hi, *out_lo;      // [b][M][N]
-    const float *wout, *bout, *y;        // OUT: output layer [b][N], [b]; targets [M]
-    double *u_part;                      // OUT: [b][ntiles]
+    const float *wout, *bout, *y;        // E3_OUT: output layer [b][N], [b]; targets [M]
+    double *u_part;                      // E3_OUT: [b][ntiles]; E3_S: [b][ntiles][ntn]
+    const float *Yt;                     // E3_S: targets [nu][ny] (rows of S^T are the ny points)
+    int nu, ntn;                         // E3_S: valid columns, column tiles
 };
 
-template <bool OUT>
+template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_energy3(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
               const __grid_constant__ CUtensorMap tmWh, const __grid_constant__ CUtensorMap tmWl, const E3Params p)
@@ -1105,6 +1112,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * E3_STAGES, accb = empty0 + 8 * E3_STAGES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m_tile = blockIdx.x, b = blockIdx.z, m0 = m_tile * BM;
+    const int n0 = MODE == E3_S ? blockIdx.y * p.N : 0;
     const int nkb = (p.K + BK - 1) / BK;
 
     if (threadIdx.x == 0) {
@@ -1138,8 +1146,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 mbar_expect_tx(fb, bytes);
                 tma_load_3d(sa, &tmAh, i * BK, m0, b, fb);
                 tma_load_3d(sa + E3_A, &tmAl, i * BK, m0, b, fb);
-                tma_load_3d(sb, &tmWh, i * BK, 0, b, fb);
-                tma_load_3d(sb + E3_B, &tmWl, i * BK, 0, b, fb);
+                tma_load_3d(sb, &tmWh, i * BK, n0, b, fb);
+                tma_load_3d(sb + E3_B, &tmWl, i * BK, n0, b, fb);
                 ++issued;
             }
             if (!ok)
@@ -1171,10 +1179,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int q = warp & 3, row = 32 * q + lane, m = m0 + row, et = threadIdx.x - 64;
         const bool valid = m < p.M;
         const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16);
-        const float *bias = p.bias + (long)b * p.N;
         const bool ok = mbar_wait(accb, 0, p.err);
         tc_fence_after();
-        if (!OUT) {
+        if (MODE == E3_TANH || MODE == E3_LIN) {
+            const float *bias = p.bias + (long)b * p.N;
             for (int c0 = 0; ok && c0 < p.N; c0 += 32) {
                 float v[32];
                 tmem_ld32(taddr + c0, v);
@@ -1182,8 +1190,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     uint32_t ph[16], pl[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const float a0 = tanhf(v[2 * j] + bias[c0 + 2 * j]);
-                        const float a1 = tanhf(v[2 * j + 1] + bias[c0 + 2 * j + 1]);
+                        float a0 = v[2 * j] + bias[c0 + 2 * j], a1 = v[2 * j + 1] + bias[c0 + 2 * j + 1];
+                        if (MODE == E3_TANH) {
+                            a0 = tanhf(a0);
+                            a1 = tanhf(a1);
+                        }
                         const __nv_bfloat16 h0 = __float2bfloat16_rn(a0), h1 = __float2bfloat16_rn(a1);
                         ph[j] = pack_bf16(__bfloat162float(h0), __bfloat162float(h1));
                         pl[j] = pack_bf16(a0 - __bfloat162float(h0), a1 - __bfloat162float(h1));
@@ -1198,21 +1209,48 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
         } else {
-            const float *wo = p.wout + (long)b * p.N;
-            float f = p.bout[b];
-            for (int c0 = 0; ok && c0 < p.N; c0 += 32) {
-                float v[32];
-                tmem_ld32(taddr + c0, v);
+            double r2 = 0.0;
+            if (MODE == E3_OUT) {
+                const float *bias = p.bias + (long)b * p.N;
+                const float *wo = p.wout + (long)b * p.N;
+                float f = p.bout[b];
+                for (int c0 = 0; ok && c0 < p.N; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) f += tanhf(v[j] + bias[c0 + j]) * wo[c0 + j];
+                    for (int j = 0; j < 32; ++j) f += tanhf(v[j] + bias[c0 + j]) * wo[c0 + j];
+                }
+                const double r = valid ? (double)f - (double)p.y[m] : 0.0;
+                r2 = r * r;
+            } else {   // E3_S: row m is a query point, columns are input functions
+                const float b0 = p.bout[b];
+                const float *yb = p.Yt + m;
+                for (int c0 = 0; ok && c0 < p.N; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + c0, v);
+                    const int u0 = n0 + c0;
+                    if (valid && u0 < p.nu) {
+                        float r2c = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (u0 + j < p.nu) {
+                                const float r = (v[j] + b0) - __ldg(yb + (long)(u0 + j) * p.M);
+                                r2c += r * r;
+                            }
+                        }
+                        r2 += (double)r2c;
+                    }
+                }
             }
-            const double r = valid ? (double)f - (double)p.y[m] : 0.0;
-            double r2 = r * r;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
             if (lane == 0) rd[q] = r2;
             named_bar_sync(1, 128);
-            if (et == 0) p.u_part[(long)b * p.ntiles + m_tile] = rd[0] + rd[1] + rd[2] + rd[3];
+            if (et == 0) {
+                const long o = MODE == E3_S ? ((long)b * p.ntiles + m_tile) * p.ntn + blockIdx.y
+                                            : (long)b * p.ntiles + m_tile;
+                p.u_part[o] = rd[0] + rd[1] + rd[2] + rd[3];
+            }
         }
     }
     tc_fence_before();
@@ -1223,17 +1261,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-template <bool OUT>
+template <int MODE>
 void launch_energy3(const CUtensorMap &ah, const CUtensorMap &al, const CUtensorMap &wh, const CUtensorMap &wl,
                     const E3Params &p, dim3 grid, cudaStream_t s)
 {
     static bool configured = false;
     if (!configured) {
-        HMC_CK(cudaFuncSetAttribute(k_energy3<OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, E3_SMEM));
+        HMC_CK(cudaFuncSetAttribute(k_energy3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, E3_SMEM));
         configured = true;
     }
-    ProfScope ps(OUT ? "energy3_out" : "energy3_hidden", s);
-    launch_pdl(k_energy3<OUT>, grid, dim3(NTHREADS), E3_SMEM, s, ah, al, wh, wl, p);
+    static const char *names[] = {"energy3_tanh", "energy3_lin", "energy3_out", "energy3_s"};
+    ProfScope ps(names[MODE], s);
+    launch_pdl(k_energy3<MODE>, grid, dim3(NTHREADS), E3_SMEM, s, ah, al, wh, wl, p);
 }
 
 // First layer of the accurate forward pass: A_1 = tanh(X W_0^T + b_0) in FP32, stored
@@ -1799,13 +1838,13 @@ class UmmaEngine final : public Engine {
             if (i < L_ - 2) {
                 e.out_hi = A_[i + 1]->as<__nv_bfloat16>();
                 e.out_lo = D_[i + 2]->as<__nv_bfloat16>();
-                launch_energy3<false>(A_row_[i], D_row_[i + 1], W_fwd_[i], W_fwd_lo_[i], e, grid, s);
+                launch_energy3<E3_TANH>(A_row_[i], D_row_[i + 1], W_fwd_[i], W_fwd_lo_[i], e, grid, s);
             } else {
                 e.wout = wout_.as<float>();
                 e.bout = bout_.as<float>();
                 e.y = y_.as<float>();
                 e.u_part = u_part_.as<double>();
-                launch_energy3<true>(A_row_[i], D_row_[i + 1], W_fwd_[i], W_fwd_lo_[i], e, grid, s);
+                launch_energy3<E3_OUT>(A_row_[i], D_row_[i + 1], W_fwd_[i], W_fwd_lo_[i], e, grid, s);
             }
         }
         FinalArgs fa{};
@@ -2141,11 +2180,11 @@ struct DonNet {
     int inld[MAXL] = {};                  // row length of W_l in memory
     int entries[MAXL] = {};               // sampled weight entries of layer l gathered by k_umma<M_DW>
     int desc0 = 0;                        // first DbDesc of this net: biases 0..L-1, then dW_0 sums
-    DevBuf x32, xb, w0f, b0f, dw0;
+    DevBuf x32, xb, xbl, w0f, b0f, dw0;   // xbl: bf16(x - xb), the lo half of the inputs
     std::unique_ptr<DevBuf> wh[MAXL], wl[MAXL], bias[MAXL], colsum[MAXL], rowptr[MAXL];
     std::unique_ptr<DevBuf> act[MAXL + 1], del[MAXL + 1];   // A_l, D_l for l = 1..L ([C][R][w_l])
     CUtensorMap act_row[MAXL + 1], act_atom[MAXL + 1], del_row[MAXL + 1], del_atom[MAXL + 1];
-    CUtensorMap w_row_h[MAXL], w_row_l[MAXL], w_atom_h[MAXL], w_atom_l[MAXL], x_row, x_atom;
+    CUtensorMap w_row_h[MAXL], w_row_l[MAXL], w_atom_h[MAXL], w_atom_l[MAXL], x_row, x_atom, x_row_lo;
 };
 
 class DonEngine final : public Engine {
@@ -2192,7 +2231,13 @@ class DonEngine final : public Engine {
         nsplit_ = std::max(br_.nsplit, tr_.nsplit);
         gw_part_.alloc(sizeof(float) * nsplit_ * C * std::max<long>(k_, 1));
         HMC_CK(cudaMemset(gw_part_.ptr, 0, gw_part_.n));   // splits a net does not use stay zero
-        exact_.reset(make_simt_engine_f32(p, C));           // before any stream capture
+        // accurate-energy S^T tiles: 128 query points x es_ input functions
+        es_ = nu_ >= 256 ? 256 : (int)round_up(nu_, 32);
+        nut_e_ = (int)std::max<long>(1, (ny_ + BM - 1) / BM);
+        ntn_e_ = (int)std::max<long>(1, (nu_ + es_ - 1) / es_);
+        alloc_t(u_acc_, sizeof(double) * C * nut_e_ * ntn_e_);
+        b_hi_e_ = make_map(br_.act[br_.L]->ptr, pl_, nu_, C, 64, es_);
+        b_lo_e_ = make_map(br_.del[br_.L]->ptr, pl_, nu_, C, 64, es_);
     }
 
     ~DonEngine() override
@@ -2201,14 +2246,62 @@ class DonEngine final : public Engine {
     }
 
     ScatterPlan scatter_plan() override { return plan_; }
-    size_t bytes() const override { return bytes_ + (exact_ ? exact_->bytes() : 0); }
+    size_t bytes() const override { return bytes_; }
 
-    // The Metropolis energy comes from the FP32 CUDA-core engine's forward pass (the
-    // bf16 operator output would carry order-one noise into dH); it scatters q itself.
+    // The Metropolis energy (the bf16 operator output would carry order-one noise into
+    // dH): branch and trunk again with hi/lo activations (their hi halves go to the
+    // activation buffers, the lo halves to the delta buffers, free after the gradient),
+    // then S^T = T B^T from the hi/lo outputs with only the residual's sums of squares.
     bool has_accurate_energy() const override { return true; }
-    void accurate_energy(const void *q, double *U, cudaStream_t s) override
+    void accurate_energy(const void *qv, double *U, cudaStream_t s) override
     {
-        exact_->energy_grad(q, U, nullptr, false, s);
+        const float *q = static_cast<const float *>(qv);
+        for (DonNet *np : {&br_, &tr_}) {
+            DonNet &n = *np;
+            const NetDesc &nd = *n.nd;
+            if (!n.gemm_first) {
+                ProfScope ps("first_fwd3", s);
+                launch_pdl(k_first_fwd3, dim3((unsigned)n.ntiles, C_), dim3(256), 0, s, n.x32.as<float>(), n.dx,
+                           (int)n.R, n.w, n.w0f.as<float>(), n.bias[0]->as<float>(), n.act[1]->as<__nv_bfloat16>(),
+                           n.del[1]->as<__nv_bfloat16>());
+            }
+            for (int l = n.gemm_first ? 0 : 1; l < n.L; ++l) {
+                E3Params e{};
+                e.M = (int)n.R;
+                e.N = nd.w[l + 1];
+                e.K = nd.w[l];
+                e.ntiles = n.ntiles;
+                e.err = err_;
+                e.bias = n.bias[l]->as<float>();
+                e.out_hi = n.act[l + 1]->as<__nv_bfloat16>();
+                e.out_lo = n.del[l + 1]->as<__nv_bfloat16>();
+                const CUtensorMap &ah = l == 0 ? n.x_row : n.act_row[l];
+                const CUtensorMap &al = l == 0 ? n.x_row_lo : n.del_row[l];
+                const dim3 grid(n.ntiles, 1, C_);
+                if (l < n.L - 1) launch_energy3<E3_TANH>(ah, al, n.w_row_h[l], n.w_row_l[l], e, grid, s);
+                else launch_energy3<E3_LIN>(ah, al, n.w_row_h[l], n.w_row_l[l], e, grid, s);
+            }
+        }
+        E3Params e{};
+        e.M = (int)ny_;
+        e.N = es_;
+        e.K = pl_;
+        e.ntiles = nut_e_;
+        e.err = err_;
+        e.bout = b0v_.as<float>();
+        e.Yt = yt_.as<float>();
+        e.nu = (int)nu_;
+        e.ntn = ntn_e_;
+        e.u_part = u_acc_.as<double>();
+        launch_energy3<E3_S>(tr_.act_row[tr_.L], tr_.del_row[tr_.L], b_hi_e_, b_lo_e_, e, dim3(nut_e_, ntn_e_, C_), s);
+        FinalArgs fa{};
+        fa.k = (int)k_;
+        fa.nu = nut_e_ * ntn_e_;
+        fa.u_part = u_acc_.as<double>();
+        fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
+        fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
+        ProfScope ps("energy3_final", s);
+        launch_pdl(k_finalize_bf16, dim3(1, C_), dim3(256), 0, s, fa, q, U, (float *)nullptr);
     }
 
     void energy_grad(const void *qv, double *U, void *gv, bool scattered, cudaStream_t s) override
@@ -2413,13 +2506,21 @@ class DonEngine final : public Engine {
         if (!xf.empty()) HMC_CK(cudaMemcpy(n.x32.ptr, xf.data(), sizeof(float) * xf.size(), cudaMemcpyHostToDevice));
         if (n.gemm_first) {   // bf16 copy per chain, rows padded to dxp
             std::vector<__nv_bfloat16> xb((size_t)C * std::max<long>(R, 1) * n.dxp, __float2bfloat16_rn(0.0f));
+            std::vector<__nv_bfloat16> xl(xb.size(), __float2bfloat16_rn(0.0f));
             for (int c = 0; c < C; ++c)
                 for (long r = 0; r < R; ++r)
-                    for (int d = 0; d < n.dx; ++d)
-                        xb[((size_t)c * R + r) * n.dxp + d] = __float2bfloat16_rn(xf[(size_t)r * n.dx + d]);
+                    for (int d = 0; d < n.dx; ++d) {
+                        const float v = xf[(size_t)r * n.dx + d];
+                        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                        xb[((size_t)c * R + r) * n.dxp + d] = h;
+                        xl[((size_t)c * R + r) * n.dxp + d] = __float2bfloat16_rn(v - __bfloat162float(h));
+                    }
             alloc_t(n.xb, sizeof(__nv_bfloat16) * xb.size());
+            alloc_t(n.xbl, sizeof(__nv_bfloat16) * xl.size());
             HMC_CK(cudaMemcpy(n.xb.ptr, xb.data(), sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyHostToDevice));
+            HMC_CK(cudaMemcpy(n.xbl.ptr, xl.data(), sizeof(__nv_bfloat16) * xl.size(), cudaMemcpyHostToDevice));
             n.x_row = make_map_ld(n.xb.ptr, n.dx, n.dxp, R, C, 64, 128);
+            n.x_row_lo = make_map_ld(n.xbl.ptr, n.dx, n.dxp, R, C, 64, 128);
             n.x_atom = make_map_ld(n.xb.ptr, n.dx, n.dxp, R, C, 64, 64);
         }
         // parameters
@@ -2674,9 +2775,10 @@ class DonEngine final : public Engine {
     DonNet br_, tr_;
     DevBuf yt_, ds_, u_part_, db0_part_, b0v_, gw_part_, db_desc_;
     DevBuf kind_, desc_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_;
-    CUtensorMap ds_row_, ds_atom_, b_col_;
+    CUtensorMap ds_row_, ds_atom_, b_col_, b_hi_e_, b_lo_e_;
+    int es_ = 256, nut_e_ = 1, ntn_e_ = 1;
+    DevBuf u_acc_;
     ScatterPlan plan_;
-    std::unique_ptr<Engine> exact_;
     std::string tuning_;
 };
 

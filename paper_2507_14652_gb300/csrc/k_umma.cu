@@ -1337,6 +1337,7 @@ __global__ void __launch_bounds__(256) k_first_fwd(const float *x, int dx, int N
             for (int d = 0; d < 8; ++d) wr[c][d] = d < dx ? W0[((long)b * w + o0 + c) * dx + d] : 0.0f;
         }
         __nv_bfloat16 *out = A1 + ((long)b * N + n0) * w + o0;
+#pragma unroll 4
         for (int r = r0; r < r1; ++r) {
             float xv[8];
 #pragma unroll
@@ -1387,11 +1388,18 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
     pdl_trigger();
     const int b = blockIdx.y;
     if (blockIdx.x == gridDim.x - 1) {   // U = likelihood + prior, block-parallel in a fixed order
-        double pr = 0.0, lik = 0.0;
-        for (int j = threadIdx.x; j < a.k; j += blockDim.x) {
-            const double qj = q[(long)b * a.k + j];
-            pr += qj * qj;
+        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, lik = 0.0;
+        for (int j0 = threadIdx.x; j0 < a.k; j0 += 8 * blockDim.x) {   // eight loads in flight
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u * blockDim.x;
+                v[u] = j < a.k ? __ldg(q + (long)b * a.k + j) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += (double)v[u] * (double)v[u];
         }
+        double pr = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
         for (int i = threadIdx.x; i < a.nu; i += blockDim.x) lik += a.u_part[(long)b * a.nu + i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -1425,18 +1433,17 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
         const DbDesc d = a.db[a.desc[j]];
         dp = d.p + (long)b * d.bstride + a.off[j], stride = d.tstride, n = d.n;
     }
-    // partials in index order, four independent loads in flight per step
+    // partials added in index order, sixteen independent loads in flight per step
     float s = 0.0f;
     int t = 0;
-    for (; t + 4 <= n; t += 4) {
-        const float v0 = __ldg(dp + t * stride), v1 = __ldg(dp + (t + 1) * stride);
-        const float v2 = __ldg(dp + (t + 2) * stride), v3 = __ldg(dp + (t + 3) * stride);
-        s += v0;
-        s += v1;
-        s += v2;
-        s += v3;
+    for (; t + 16 <= n; t += 16) {
+        float v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = __ldg(dp + (long)(t + u) * stride);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) s += v[u];
     }
-    for (; t < n; ++t) s += __ldg(dp + t * stride);
+    for (; t < n; ++t) s += __ldg(dp + (long)t * stride);
     g[(long)b * a.k + j] = s + qj * (float)a.inv_a2;
 }
 

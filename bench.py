@@ -134,16 +134,19 @@ def run_reference(args):
 
 def _traffic(kernel):
     """DRAM bytes per launch of a bench kernel from the committed ncu capture, or None
-    when there is none or the kernel source changed since it was taken."""
+    when there is none or the kernel's source text changed since it was taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel)
         if not rec:
             return None
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
-                return None
+        with open(os.path.join(ROOT, rec["source"]), encoding="utf-8") as f:
+            text = f.read()
+        i = text.index(rec["region_start"])           # the kernel's own source text
+        j = text.index(rec["region_end"], i + len(rec["region_start"]))
+        if hashlib.sha256(text[i:j].encode("utf-8")).hexdigest() != rec["region_sha256"]:
+            return None
         return float(rec["dram_bytes_per_launch"])
     except (OSError, ValueError, KeyError):
         return None

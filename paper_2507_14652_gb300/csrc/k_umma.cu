@@ -22,6 +22,7 @@
 // Every partial sum is written to its own slot (no atomics), so the result is
 // bit-reproducible.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -934,6 +935,14 @@ constexpr int DW_ONES = 16 * 128;              // 16 K-major rows of 64 bf16 one
 constexpr int DW_SMEM = 1024 + DW_STAGES * DW_STAGE + DW_ONES + 256;
 constexpr int DW_TCOLS = 256;                  // 128 columns of dW + 16 of row sums
 constexpr int kMaxSplits = 32;                 // largest row-split count the autotuner tries
+
+// HMC_AUTOTUNE=0 keeps the built-in heuristic choices instead of timing candidates at
+// handle creation (for runs under a profiler, whose overhead would skew the timings).
+bool autotune_enabled()
+{
+    const char *e = getenv("HMC_AUTOTUNE");
+    return !(e && e[0] == '0');
+}
 static_assert(DW_STAGES * DW_STAGE >= 128 * 129 * 4, "the epilogue staging reuses the operand stages");
 
 __global__ void __launch_bounds__(NTHREADS, 2) k_dw2(const __grid_constant__ CUtensorMap tmD,
@@ -1870,6 +1879,10 @@ class UmmaEngine final : public Engine {
     // the choice is cached per (rows, width, chains) for the process.
     void tune_dw_splits(int total_kb)
     {
+        if (!autotune_enabled()) {
+            tuning_ = "dw row splits " + std::to_string(nsplit2_) + " (heuristic; autotuner off)";
+            return;
+        }
         int layer = -1;
         for (int i = 1; i <= L_ - 2 && layer < 0; ++i)
             if (layer_entries_[i] > 0 || bias_entries_[i] > 0) layer = i;
@@ -2408,6 +2421,10 @@ class DonEngine final : public Engine {
     // engine's own buffers (one warm-up, three timed launches) and keep the faster one.
     void tune_s_tile()
     {
+        if (!autotune_enabled()) {
+            tuning_ = "S column tile " + std::to_string(bs_) + " (heuristic; autotuner off)";
+            return;
+        }
         cudaStream_t s;
         cudaEvent_t a, b;
         HMC_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));

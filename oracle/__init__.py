@@ -67,6 +67,20 @@ def lib():
         L.or_leapfrog.argtypes = [vp, vp, vp, d, i, vp, vp]
         L.or_sample.restype = None
         L.or_sample.argtypes = [vp, vp, i, d, i, lg, u64, u64, lg, vp, vp, vp, vp, i]
+        L.or_data_rows.restype = lg
+        L.or_data_rows.argtypes = [vp]
+        L.or_energy_grad_rows.restype = d
+        L.or_energy_grad_rows.argtypes = [vp, vp, vp, lg, lg, d]
+        L.or_batch_rows.restype = None
+        L.or_batch_rows.argtypes = [vp, i, i, vp, vp]
+        L.or_split_leapfrog.restype = None
+        L.or_split_leapfrog.argtypes = [vp, i, vp, vp, d, i]
+        L.or_split_sample.restype = None
+        L.or_split_sample.argtypes = [vp, i, vp, i, d, i, lg, u64, u64, lg, vp, vp, vp, vp, i]
+        L.or_sensitivity.restype = None
+        L.or_sensitivity.argtypes = [vp, vp, vp, vp]
+        L.or_truncate.restype = lg
+        L.or_truncate.argtypes = [vp, lg, d, vp, vp]
         _lib = L
     return _lib
 
@@ -156,6 +170,48 @@ class Oracle:
         lib().or_energy_grad_batch(self._sp, C, _ptr(Q), _ptr(U), _ptr(G), int(threads))
         return U, G
 
+    def data_rows(self):
+        return int(lib().or_data_rows(self._sp))
+
+    def batch_rows(self, M, m):
+        r0, r1 = ct.c_long(), ct.c_long()
+        lib().or_batch_rows(self._sp, int(M), int(m), ct.byref(r0), ct.byref(r1))
+        return r0.value, r1.value
+
+    def energy_grad_rows(self, q, r0, r1, w=1.0):
+        """Likelihood of data rows [r0, r1) plus the fraction w of the prior, and its gradient."""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        g = np.zeros(self.k)
+        U = lib().or_energy_grad_rows(self._sp, _ptr(q), _ptr(g), int(r0), int(r1), float(w))
+        return U, g
+
+    def split_leapfrog(self, q, p, eps, L, M):
+        """L steps of the symmetric split integrator over M data batches."""
+        q = np.array(q, dtype=np.float64)
+        p = np.array(p, dtype=np.float64)
+        lib().or_split_leapfrog(self._sp, int(M), _ptr(q), _ptr(p), float(eps), int(L))
+        return q, p
+
+    def split_sample(self, q0, eps, L, n, M, seed=0, first_traj=0, problem=0, threads=0):
+        q0 = np.ascontiguousarray(q0, dtype=np.float64)
+        C = q0.shape[0]
+        S = np.zeros((n, C, self.k))
+        acc = np.zeros((n, C), dtype=np.uint8)
+        dH = np.zeros((n, C))
+        ql = np.zeros((C, self.k))
+        lib().or_split_sample(self._sp, int(M), _ptr(q0), C, float(eps), int(L), int(n), int(seed), int(problem),
+                              int(first_traj), _ptr(S), _ptr(acc), _ptr(dH), _ptr(ql), int(threads))
+        return S, acc, dH, ql
+
+    def sensitivity(self, mu, sd):
+        """S_i^2 of Sec. 3.1 for every parameter: the network at the VI means mu [P]
+        with VI standard deviations sd [P]."""
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        sd = np.ascontiguousarray(sd, dtype=np.float64)
+        S2 = np.zeros(self.P)
+        lib().or_sensitivity(self._sp, _ptr(mu), _ptr(sd), _ptr(S2))
+        return S2
+
     def leapfrog(self, q, p, eps, L, U=None, g=None):
         q = np.array(q, dtype=np.float64)
         p = np.array(p, dtype=np.float64)
@@ -207,3 +263,13 @@ def momenta(seed, chain, traj, k, problem=0):
 
 def mh_uniform(seed, chain, traj, problem=0):
     return lib().or_mh_uniform(int(seed), int(problem), int(chain), int(traj))
+
+
+def truncate(S2, tau):
+    """N-hat of Sec. 3.1 and the subset mask [P] (uint8), plus the ranking [P]."""
+    S2 = np.ascontiguousarray(S2, dtype=np.float64)
+    P = S2.shape[0]
+    mask = np.zeros(P, dtype=np.uint8)
+    order = np.zeros(P, dtype=np.int64)
+    nhat = lib().or_truncate(_ptr(S2), P, float(tau), _ptr(mask), _ptr(order))
+    return int(nhat), mask, order

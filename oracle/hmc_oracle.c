@@ -223,13 +223,21 @@ void or_forward(const or_problem *pr, const double *theta, double *f)
     free(tb.buf); free(tt.buf); free(B); free(T);
 }
 
+/* Data rows: MLP data points, or DeepONet input functions (each with all its queries). */
+long or_data_rows(const or_problem *pr)
+{
+    return pr->kind == 0 ? pr->n : pr->n_u;
+}
+
 /*
- * U(q) and grad U(q) for one chain state q[k].
- *   U = sum over data terms of (F - y)^2 / (2 sigma^2) + sum_j q_j^2 / (2 alpha^2)
- *   g_j = dU/dtheta_{idx_j}
- * grad may be NULL (energy only).  Returns U.
+ * The part of U(q) and grad U(q) that comes from data rows [r0, r1), plus the
+ * fraction w of the prior term, for one chain state q[k]:
+ *   U_part = sum over the rows' data terms of (F - y)^2 / (2 sigma^2)
+ *            + w sum_j q_j^2 / (2 alpha^2)
+ * With r0 = 0, r1 = all rows and w = 1 this is U itself (or_energy_grad).
+ * grad may be NULL (energy only).  Returns U_part.
  */
-double or_energy_grad(const or_problem *pr, const double *q, double *g)
+double or_energy_grad_rows(const or_problem *pr, const double *q, double *g, long r0, long r1, double w)
 {
     double s2 = pr->noise_sigma * pr->noise_sigma;
     double a2 = pr->prior_sigma * pr->prior_sigma;
@@ -244,7 +252,7 @@ double or_energy_grad(const or_problem *pr, const double *q, double *g)
         int wmax = net_wmax(nt);
         double *work = (double *)malloc(sizeof(double) * (size_t)(2 * wmax));
         double *dout_v = (double *)malloc(sizeof(double) * (size_t)dout);
-        for (long n = 0; n < pr->n; ++n) {
+        for (long n = r0; n < r1; ++n) {
             net_forward(nt, theta, pr->x + n * pr->dx, &tp);
             for (int o = 0; o < dout; ++o) {
                 double r = tp.a[L][o] - pr->y[n * dout + o];
@@ -262,13 +270,13 @@ double or_energy_grad(const or_problem *pr, const double *q, double *g)
         /* forward both nets, keeping every sample's tape for the reverse pass */
         or_tape *tb = (or_tape *)malloc(sizeof(or_tape) * (size_t)(pr->n_u > 0 ? pr->n_u : 1));
         or_tape *tt = (or_tape *)malloc(sizeof(or_tape) * (size_t)(pr->n_y > 0 ? pr->n_y : 1));
-        for (long i = 0; i < pr->n_u; ++i) { tape_init(&tb[i], bn); net_forward(bn, theta, pr->u + i * pr->du, &tb[i]); }
+        for (long i = r0; i < r1; ++i) { tape_init(&tb[i], bn); net_forward(bn, theta, pr->u + i * pr->du, &tb[i]); }
         for (long j = 0; j < pr->n_y; ++j) { tape_init(&tt[j], tn); net_forward(tn, theta + pb, pr->yq + j * pr->dy, &tt[j]); }
         double *dB = (double *)calloc((size_t)(pr->n_u * p), sizeof(double));
         double *dT = (double *)calloc((size_t)(pr->n_y * p), sizeof(double));
         double db0 = 0.0;
         /* S_ij = <B_i, T_j> + b0;  dU/dS_ij = (S_ij - t_ij) / sigma^2 */
-        for (long i = 0; i < pr->n_u; ++i) {
+        for (long i = r0; i < r1; ++i) {
             const double *Bi = tb[i].a[bn->n_layers];
             for (long j = 0; j < pr->n_y; ++j) {
                 const double *Tj = tt[j].a[tn->n_layers];
@@ -286,21 +294,32 @@ double or_energy_grad(const or_problem *pr, const double *q, double *g)
         }
         int wmax = net_wmax(bn) > net_wmax(tn) ? net_wmax(bn) : net_wmax(tn);
         double *work = (double *)malloc(sizeof(double) * (size_t)(2 * wmax));
-        for (long i = 0; i < pr->n_u; ++i) net_backward(bn, theta, &tb[i], dB + i * p, grad, work);
+        for (long i = r0; i < r1; ++i) net_backward(bn, theta, &tb[i], dB + i * p, grad, work);
         for (long j = 0; j < pr->n_y; ++j) net_backward(tn, theta + pb, &tt[j], dT + j * p, grad + pb, work);
         if (pr->out_bias) grad[pb + pt] += db0;
-        for (long i = 0; i < pr->n_u; ++i) free(tb[i].buf);
+        for (long i = r0; i < r1; ++i) free(tb[i].buf);
         for (long j = 0; j < pr->n_y; ++j) free(tt[j].buf);
         free(tb); free(tt); free(dB); free(dT); free(work);
     }
 
     /* prior on the sampled subset only: alpha-Gaussian, constants dropped */
-    for (long j = 0; j < pr->k; ++j) U += q[j] * q[j] / (2.0 * a2);
+    for (long j = 0; j < pr->k; ++j) U += w * (q[j] * q[j] / (2.0 * a2));
     if (g)
-        for (long j = 0; j < pr->k; ++j) g[j] = grad[pr->idx[j]] + q[j] / a2;
+        for (long j = 0; j < pr->k; ++j) g[j] = grad[pr->idx[j]] + w * (q[j] / a2);
     free(grad);
     free(theta);
     return U;
+}
+
+/*
+ * U(q) and grad U(q) for one chain state q[k].
+ *   U = sum over data terms of (F - y)^2 / (2 sigma^2) + sum_j q_j^2 / (2 alpha^2)
+ *   g_j = dU/dtheta_{idx_j}
+ * grad may be NULL (energy only).  Returns U.
+ */
+double or_energy_grad(const or_problem *pr, const double *q, double *g)
+{
+    return or_energy_grad_rows(pr, q, g, 0, or_data_rows(pr), 1.0);
 }
 
 /* Several chain states at once (parallel over chains only; each sum keeps its order). */
@@ -526,4 +545,201 @@ void or_sample(const or_problem *pr, const double *q0, int C, double eps, int L,
         if (q_last) memcpy(q_last + (long)c * k, q, sizeof(double) * (size_t)k);
         free(q); free(qn); free(p); free(g); free(gn);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Symmetric split integrator over data batches                              */
+/* ------------------------------------------------------------------------ */
+
+/* Batch m of M: data rows [floor(m R / M), floor((m + 1) R / M)) of the R rows. */
+void or_batch_rows(const or_problem *pr, int M, int m, long *r0, long *r1)
+{
+    long R = or_data_rows(pr);
+    *r0 = (long)(((__int128)R * m) / M);
+    *r1 = (long)(((__int128)R * (m + 1)) / M);
+}
+
+/*
+ * The split Hamiltonian of symmetric split HMC (Sec. 4.2.3 uses it for the full-HMC
+ * runs): H = sum_m H_m with H_m = U_m(q) + K(p)/M, where U_m holds the likelihood of
+ * data batch m and 1/M of the prior.  One step of size eps is the forward sweep
+ * m = 1..M of  [p <- p - eps/2 grad U_m(q);  q <- q + eps/(2M) p]  followed by the
+ * backward sweep m = M..1 of  [q <- q + eps/(2M) p;  p <- p - eps/2 grad U_m(q)]:
+ * a palindromic composition of exact sub-flows, so the map is symplectic and
+ * reversible (the Metropolis test stays exact), of second order, and for M = 1 it is
+ * the leapfrog step.  L steps, in place on q and p.
+ */
+void or_split_leapfrog(const or_problem *pr, int M, double *q, double *p, double eps, int L)
+{
+    long k = pr->k;
+    double *g = (double *)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    double kick = 0.5 * eps, drift = eps / (2.0 * M), w = 1.0 / M;
+    for (int s = 0; s < L; ++s) {
+        for (int m = 0; m < M; ++m) {
+            long r0, r1;
+            or_batch_rows(pr, M, m, &r0, &r1);
+            or_energy_grad_rows(pr, q, g, r0, r1, w);
+            for (long j = 0; j < k; ++j) p[j] = p[j] - kick * g[j];
+            for (long j = 0; j < k; ++j) q[j] = q[j] + drift * p[j];
+        }
+        for (int m = M - 1; m >= 0; --m) {
+            long r0, r1;
+            or_batch_rows(pr, M, m, &r0, &r1);
+            for (long j = 0; j < k; ++j) q[j] = q[j] + drift * p[j];
+            or_energy_grad_rows(pr, q, g, r0, r1, w);
+            for (long j = 0; j < k; ++j) p[j] = p[j] - kick * g[j];
+        }
+    }
+    free(g);
+}
+
+/*
+ * HMC with the split integrator: as or_sample, with (q*, p*) from or_split_leapfrog
+ * and H = U + K evaluated on the whole data set at both ends.
+ */
+void or_split_sample(const or_problem *pr, int M, const double *q0, int C, double eps, int L, long n,
+                     uint64_t seed, uint64_t problem, long first_traj,
+                     double *samples, unsigned char *accepted, double *dH, double *q_last, int nthreads)
+{
+    long k = pr->k;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int c = 0; c < C; ++c) {
+        double *q = (double *)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+        double *qn = (double *)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+        double *p = (double *)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+        memcpy(q, q0 + (long)c * k, sizeof(double) * (size_t)k);
+        double U = or_energy_grad(pr, q, NULL);
+        for (long i = 0; i < n; ++i) {
+            uint64_t traj = (uint64_t)(first_traj + i);
+            for (long j = 0; j < k; ++j) p[j] = or_momentum(seed, problem, (uint64_t)c, traj, (uint64_t)j);
+            double H0 = U + kinetic(p, k);
+            memcpy(qn, q, sizeof(double) * (size_t)k);
+            or_split_leapfrog(pr, M, qn, p, eps, L);
+            double Un = or_energy_grad(pr, qn, NULL);
+            double H1 = Un + kinetic(p, k);
+            double lu = or_log(or_mh_uniform(seed, problem, (uint64_t)c, traj));
+            int acc = lu < H0 - H1;
+            if (acc) {
+                memcpy(q, qn, sizeof(double) * (size_t)k);
+                U = Un;
+            }
+            if (samples) memcpy(samples + (i * C + c) * k, q, sizeof(double) * (size_t)k);
+            if (accepted) accepted[i * C + c] = (unsigned char)acc;
+            if (dH) dH[i * C + c] = H1 - H0;
+        }
+        if (q_last) memcpy(q_last + (long)c * k, q, sizeof(double) * (size_t)k);
+        free(q); free(qn); free(p);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sensitivities and the truncation of the parameter set (Sec. 3.1)          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The sensitivity of the network output to each parameter around the VI mean
+ * (Sec. 3.1, the equation defining S_i^2): with F evaluated at theta = mu,
+ *   S2[i] = sd[i]^2 / N_d * sum over the data terms of (dF/dtheta_i)^2,
+ * the data terms being the outputs F_o(x_n) of an MLP (N_d = n * dout) or the
+ * DeepONet outputs S_jk = <B_j, T_k> + b0 (N_d = n_u * n_y).  The derivative of
+ * each data term is one reverse pass seeded with that term alone.
+ */
+void or_sensitivity(const or_problem *pr, const double *mu, const double *sd, double *S2)
+{
+    long P = or_param_count(pr);
+    double *acc = (double *)calloc((size_t)P, sizeof(double));
+    double *grad = (double *)malloc(sizeof(double) * (size_t)P);
+    double Nd;
+    if (pr->kind == 0) {
+        const or_net *nt = &pr->net;
+        int L = nt->n_layers, dout = nt->width[L];
+        Nd = (double)pr->n * dout;
+        or_tape tp; tape_init(&tp, nt);
+        double *work = (double *)malloc(sizeof(double) * (size_t)(2 * net_wmax(nt)));
+        double *seed = (double *)malloc(sizeof(double) * (size_t)dout);
+        for (long n = 0; n < pr->n; ++n) {
+            net_forward(nt, mu, pr->x + n * pr->dx, &tp);
+            for (int o = 0; o < dout; ++o) {
+                for (int c = 0; c < dout; ++c) seed[c] = c == o ? 1.0 : 0.0;
+                memset(grad, 0, sizeof(double) * (size_t)P);
+                net_backward(nt, mu, &tp, seed, grad, work);
+                for (long i = 0; i < P; ++i) acc[i] += grad[i] * grad[i];
+            }
+        }
+        free(tp.buf); free(work); free(seed);
+    } else {
+        const or_net *bn = &pr->branch, *tn = &pr->trunk;
+        int p = bn->width[bn->n_layers];
+        long pb = or_net_params(bn);
+        Nd = (double)pr->n_u * pr->n_y;
+        or_tape *tb = (or_tape *)malloc(sizeof(or_tape) * (size_t)(pr->n_u > 0 ? pr->n_u : 1));
+        or_tape *tt = (or_tape *)malloc(sizeof(or_tape) * (size_t)(pr->n_y > 0 ? pr->n_y : 1));
+        for (long j = 0; j < pr->n_u; ++j) { tape_init(&tb[j], bn); net_forward(bn, mu, pr->u + j * pr->du, &tb[j]); }
+        for (long k = 0; k < pr->n_y; ++k) { tape_init(&tt[k], tn); net_forward(tn, mu + pb, pr->yq + k * pr->dy, &tt[k]); }
+        int wmax = net_wmax(bn) > net_wmax(tn) ? net_wmax(bn) : net_wmax(tn);
+        double *work = (double *)malloc(sizeof(double) * (size_t)(2 * wmax));
+        for (long j = 0; j < pr->n_u; ++j)
+            for (long k = 0; k < pr->n_y; ++k) {
+                /* dS_jk/dB_j = T_k and dS_jk/dT_k = B_j; dS_jk/db0 = 1 */
+                memset(grad, 0, sizeof(double) * (size_t)P);
+                net_backward(bn, mu, &tb[j], tt[k].a[tn->n_layers], grad, work);
+                net_backward(tn, mu + pb, &tt[k], tb[j].a[bn->n_layers], grad + pb, work);
+                if (pr->out_bias) grad[P - 1] = 1.0;
+                for (long i = 0; i < P; ++i) acc[i] += grad[i] * grad[i];
+            }
+        (void)p;
+        for (long j = 0; j < pr->n_u; ++j) free(tb[j].buf);
+        for (long k = 0; k < pr->n_y; ++k) free(tt[k].buf);
+        free(tb); free(tt); free(work);
+    }
+    for (long i = 0; i < P; ++i) S2[i] = sd[i] * sd[i] / Nd * acc[i];
+    free(acc); free(grad);
+}
+
+static const double *g_rank_S2;   /* key of the ordering below (single-threaded use) */
+
+/* S2 descending; equal values by ascending parameter index. */
+static int rank_cmp(const void *a, const void *b)
+{
+    long i = *(const long *)a, j = *(const long *)b;
+    double si = g_rank_S2[i], sj = g_rank_S2[j];
+    if (si > sj) return -1;
+    if (si < sj) return 1;
+    return (i > j) - (i < j);
+}
+
+/*
+ * The truncation of Sec. 3.1 (the equation defining N-hat): with the parameters
+ * ordered from most to least sensitive (ties: lower index first),
+ *   N_hat = max{ N_T : sum_{r <= N_T} S2_(r) / sum_i S2_i <= tau },
+ * and the sampled subset Theta_s is the first N_hat of that order (Sec. 3.2).
+ * The total is summed in index order, the prefix in rank order, both in FP64.  An
+ * all-zero S2 gives N_hat = 0.  mask[P] receives 1 for Theta_s; order[P] (may be
+ * NULL) the ranking.  Returns N_hat.
+ */
+long or_truncate(const double *S2, long P, double tau, unsigned char *mask, long *order)
+{
+    long *ord = (long *)malloc(sizeof(long) * (size_t)(P > 0 ? P : 1));
+    for (long i = 0; i < P; ++i) ord[i] = i;
+    g_rank_S2 = S2;
+    qsort(ord, (size_t)P, sizeof(long), rank_cmp);
+    double total = 0.0;
+    for (long i = 0; i < P; ++i) total += S2[i];
+    long nhat = 0;
+    if (total > 0.0) {
+        double cum = 0.0;
+        for (long r = 0; r < P; ++r) {
+            cum += S2[ord[r]];
+            if (cum / total <= tau) nhat = r + 1;
+            else break;
+        }
+    }
+    for (long i = 0; i < P; ++i) mask[i] = 0;
+    for (long r = 0; r < nhat; ++r) mask[ord[r]] = 1;
+    if (order) memcpy(order, ord, sizeof(long) * (size_t)P);
+    free(ord);
+    return nhat;
 }

@@ -342,6 +342,26 @@ def small_deeponet(n_u=37, n_y=29, du=12, dy=2, width=24, latent=10, frac=0.3, c
                    u=u, yq=yq, t=t)
 
 
+def case1_sine(theta, mask=None, chains=1, eps=1e-5, L=724, noise=1e-3, prior=1.0,
+               true=(4.0, -3.0, 0.0, 1.57, 0.4, 0.5), seed=1111):
+    """Case I of the BNN example (Sec. 4.1.1): y = a sin(w1 x + p1) + b sin(w2 x + p2) + noise
+    on 20 points, ten equispaced on each of [-1, -0.2] and [0.2, 1].  The network is
+    1-2-1 with sine hidden units, a hidden bias and no output bias; its parameters
+    (W1 = (w1, w2), b1 = (p1, p2), W2 = (a, b)) are `theta`, which also gives the frozen
+    values.  `true` = (w1, w2, p1, p2, a, b) generates the data.  Default eps and L are
+    the paper's (App. D: step 1e-5, L = pi * 0.0679^2 / (2 * 1e-5))."""
+    rng = np.random.default_rng(seed)
+    net = Net([1, 2, 1], [ACT_SIN, ACT_IDENTITY], [True, False])
+    x = _f32(np.concatenate([np.linspace(-1.0, -0.2, 10), np.linspace(0.2, 1.0, 10)])[:, None])
+    w1, w2, p1, p2, a, b = true
+    y = _f32(a * np.sin(w1 * x + p1) + b * np.sin(w2 * x + p2) + noise * rng.standard_normal(x.shape))
+    frozen = _f32(theta)
+    mask = np.ones(6, dtype=np.uint8) if mask is None else np.asarray(mask, dtype=np.uint8)
+    q0 = np.repeat(frozen[mask.astype(bool)][None, :], chains, axis=0)
+    return Problem("case1_sine", KIND_MLP, noise, prior, frozen, mask, q0, eps=eps, L=L, n_samples=5000,
+                   seed=0, net=net, x=x, y=y)
+
+
 def harmonic(k=7, prior=0.7, chains=1, eps=0.1, L=13, seed=9009):
     """No data at all: U(q) = |q|^2 / (2 alpha^2), a harmonic oscillator."""
     rng = np.random.default_rng(seed)

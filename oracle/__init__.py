@@ -81,6 +81,10 @@ def lib():
         L.or_sensitivity.argtypes = [vp, vp, vp, vp]
         L.or_truncate.restype = lg
         L.or_truncate.argtypes = [vp, lg, d, vp, vp]
+        L.or_predict.restype = None
+        L.or_predict.argtypes = [vp, vp, lg, vp, vp]
+        L.or_rel_l2.restype = d
+        L.or_rel_l2.argtypes = [vp, vp, lg, lg]
         _lib = L
     return _lib
 
@@ -212,6 +216,16 @@ class Oracle:
         lib().or_sensitivity(self._sp, _ptr(mu), _ptr(sd), _ptr(S2))
         return S2
 
+    def predict(self, samples):
+        """Mean and standard deviation over posterior samples [S][k] of the network's
+        outputs on this problem's inputs (Sec. 4.2.1)."""
+        Q = np.ascontiguousarray(samples, dtype=np.float64).reshape(-1, self.k)
+        p = self.prob
+        shape = (p.x.shape[0], p.net.widths[-1]) if p.kind == 0 else (p.u.shape[0], p.yq.shape[0])
+        mean, sd = np.zeros(shape), np.zeros(shape)
+        lib().or_predict(self._sp, _ptr(Q), Q.shape[0], _ptr(mean), _ptr(sd))
+        return mean, sd
+
     def leapfrog(self, q, p, eps, L, U=None, g=None):
         q = np.array(q, dtype=np.float64)
         p = np.array(p, dtype=np.float64)
@@ -273,3 +287,11 @@ def truncate(S2, tau):
     order = np.zeros(P, dtype=np.int64)
     nhat = lib().or_truncate(_ptr(S2), P, float(tau), _ptr(mask), _ptr(order))
     return int(nhat), mask, order
+
+
+def rel_l2(Y, Yp):
+    """(1/N) sum_i ||Y_i - Yp_i|| / ||Y_i|| over the rows of Y [N][m] (Sec. 4.2.1)."""
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    Yp = np.ascontiguousarray(Yp, dtype=np.float64)
+    Y2, P2 = Y.reshape(Y.shape[0], -1), Yp.reshape(Y.shape[0], -1)
+    return float(lib().or_rel_l2(_ptr(Y2), _ptr(P2), Y2.shape[0], Y2.shape[1]))

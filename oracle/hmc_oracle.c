@@ -743,3 +743,55 @@ long or_truncate(const double *S2, long P, double tau, unsigned char *mask, long
     free(ord);
     return nhat;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Posterior predictive (Sec. 4.2.1)                                        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The network's outputs on the problem's inputs for every posterior sample
+ * q_s [S][k] (theta = frozen with the subset replaced by q_s), reduced over the
+ * samples to their mean and standard deviation per output,
+ *   mean = (1/S) sum_s F_s,   std = sqrt((1/S) sum_s (F_s - mean)^2),
+ * two passes over the samples.  Outputs are [n][dout] (MLP) or [n_u][n_y] (DeepONet).
+ */
+void or_predict(const or_problem *pr, const double *samples, long S, double *mean, double *sdev)
+{
+    long nout = pr->kind == 0 ? pr->n * pr->net.width[pr->net.n_layers] : pr->n_u * pr->n_y;
+    double *f = (double *)malloc(sizeof(double) * (size_t)(nout > 0 ? nout : 1));
+    for (long i = 0; i < nout; ++i) { mean[i] = 0.0; sdev[i] = 0.0; }
+    for (int pass = 0; pass < 2; ++pass)
+        for (long s = 0; s < S; ++s) {
+            double *theta = assemble_theta(pr, samples + s * pr->k);
+            or_forward(pr, theta, f);
+            for (long i = 0; i < nout; ++i) {
+                if (pass == 0) mean[i] += f[i];
+                else { double d = f[i] - mean[i]; sdev[i] += d * d; }
+            }
+            free(theta);
+            if (pass == 0 && s == S - 1)
+                for (long i = 0; i < nout; ++i) mean[i] /= (double)S;
+        }
+    for (long i = 0; i < nout; ++i) sdev[i] = sqrt(sdev[i] / (double)S);
+    free(f);
+}
+
+/*
+ * Mean relative L2 error of a prediction (Sec. 4.2.1): (1/N) sum_i ||Y_i - Yp_i||_2 / ||Y_i||_2
+ * over N rows of length m (a DeepONet: one row per input function over its queries;
+ * an MLP: the whole output as one row).
+ */
+double or_rel_l2(const double *Y, const double *Yp, long N, long m)
+{
+    double acc = 0.0;
+    for (long i = 0; i < N; ++i) {
+        double e = 0.0, y = 0.0;
+        for (long j = 0; j < m; ++j) {
+            double d = Y[i * m + j] - Yp[i * m + j];
+            e += d * d;
+            y += Y[i * m + j] * Y[i * m + j];
+        }
+        acc += sqrt(e) / sqrt(y);
+    }
+    return acc / (double)N;
+}

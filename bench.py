@@ -181,6 +181,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ess-traj", type=int, default=200, help="trajectories for the ESS/s comparison (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--split", type=int, default=4, help="data batches of the split-integrator run (0 = skip)")
     args = ap.parse_args()
     assert args.warmup >= 3, "timing rules need at least 3 warm-up steps"
     if args.impl == "reference":
@@ -307,6 +308,31 @@ def main():
                          "accept_rate": float(ae.float().mean().item()),
                          "grad_evals_per_s": chains * L * args.ess_traj / sec}
 
+    # the symmetric split integrator over data batches on the same workload and step:
+    # trajectories of the same L, each step 2M - 1 batch gradients of N/M points
+    split = None
+    if args.split > 1 and rank == 0:
+        M = args.split
+        ss = hmc.Sampler.mlp(prob.net.widths, prob.x, prob.y, prob.mask, prob.frozen, C,
+                             prior_sigma=prob.prior_sigma, noise_sigma=prob.noise_sigma, prec=hmc.PREC_BF16,
+                             n_splits=M)
+        # the same start state, momenta and uniforms as the timed leapfrog run, so the
+        # acceptance rates compare the two integrators on the same trajectories' starts
+        ss.sample(q, eps, L, 1, seed=seed, first_traj=10 ** 7, keep_samples=False)   # graph capture
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, acs, dhs, _ = ss.sample(q, eps, L, args.steps, seed=seed, first_traj=args.warmup, keep_samples=False)
+        b.record()
+        torch.cuda.synchronize()
+        sms = a.elapsed_time(b) / args.steps
+        split = {"n_splits": M, "ms_per_trajectory": sms, "leapfrog_ms_per_trajectory": ms / args.steps,
+                 "batch_gradients_per_step": 2 * M - 1, "points_per_batch": int(prob.x.shape[0]) // M,
+                 "accept_rate": float(acs.float().mean().item()), "leapfrog_accept_rate": float(acc_np.mean()),
+                 "abs_dH_median": float(np.nanmedian(np.abs(dhs.cpu().numpy()))),
+                 "full_gradient_equivalents_per_s": C * L * (2 * M - 1) / M / (sms / 1000.0)}
+        ss.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob)
@@ -327,7 +353,7 @@ def main():
                 "roofline": roof, "kernel_ms": {k: v[0] for k, v in prof.items()},
                 "tuning": s.tuning().strip(),
                 "kernel_launches_per_eval": {k: v[1] for k, v in prof.items()},
-                "e2e": e2e, "cpu_baseline": cpu, "ess": ess, "clocks": clocks}
+                "e2e": e2e, "cpu_baseline": cpu, "ess": ess, "split_hmc": split, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

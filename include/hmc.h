@@ -37,6 +37,7 @@ extern "C" {
 #endif
 
 #define HMC_MAX_LAYERS 16
+#define HMC_MAX_SPLITS 64
 
 /* Symbols of the C ABI are exported even when the library hides everything else. */
 #if defined(__GNUC__)
@@ -126,6 +127,30 @@ HMC_API hmc_status hmc_create_batch(hmc_handle *out, int n_problems, const hmc_n
                             const double *noise_sigma, const unsigned char *const *subset_masks,
                             const double *const *frozen_params, int n_chains, void *cuda_stream);
 
+/*
+ * Create a sampler for one problem whose trajectories use the symmetric split
+ * integrator over n_splits data batches (the split HMC Sec. 4.2.3 runs for its
+ * full-HMC comparisons) instead of the full-batch leapfrog.  Arguments as
+ * hmc_create, plus
+ *   n_splits   M in [1, HMC_MAX_SPLITS] and at most the number of data rows R
+ *              (MLP: data points; DeepONet: input functions, each with all its
+ *              queries).  Batch m holds rows [floor(m R / M), floor((m + 1) R / M)).
+ * The Hamiltonian is split as H = sum_m [U_m(q) + K(p)/M], U_m the likelihood of
+ * batch m plus 1/M of the prior.  One step of size eps is the forward sweep
+ * m = 1..M of {p -= eps/2 grad U_m(q); q += eps/(2M) p} followed by the backward
+ * sweep m = M..1 of {q += eps/(2M) p; p -= eps/2 grad U_m(q)}: symplectic and
+ * reversible, so the Metropolis test on H = U + K stays exact; M = 1 is the
+ * leapfrog.  A step costs 2M - 1 batch gradients (about two full ones); each
+ * batch's activations take 1/M of the full batch's device memory.
+ * On such a handle hmc_leapfrog, hmc_sample and hmc_adapt_step_size integrate
+ * with this scheme; hmc_energy_grad returns the full U and grad U (sums over the
+ * batches).  Everything else is as for hmc_create.
+ */
+HMC_API hmc_status hmc_create_split(hmc_handle *out, const hmc_net_spec *spec, const hmc_data *data,
+                                    double prior_sigma, double noise_sigma, const unsigned char *subset_mask,
+                                    const double *frozen_params, int n_chains, int n_splits,
+                                    void *cuda_stream);
+
 /* k (for a batch: the sum of k over problems), or -1 for a bad handle. */
 HMC_API long hmc_subset_size(hmc_handle h);
 
@@ -170,7 +195,7 @@ HMC_API hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, l
 
 /*
  * Step-size adaptation for the warm-up (the paper tunes eps to about 80% acceptance;
- * Sec. 4.3): runs n_warmup trajectories of L steps from q, one at a time, and adapts
+ * Sec. 4.2.3): runs n_warmup trajectories of L steps from q, one at a time, and adapts
  * log eps by dual averaging (Hoffman and Gelman 2014, Sec. 3.2) so that the mean
  * over all chains (and problems) of the Metropolis acceptance probability
  * min(1, exp(-dH)) approaches target_accept; a non-finite dH counts as 0.
@@ -185,6 +210,64 @@ HMC_API hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, l
 HMC_API hmc_status hmc_adapt_step_size(hmc_handle h, void *q, int L, double eps0, long n_warmup,
                                double target_accept, unsigned long long seed, long first_traj,
                                double *eps_out);
+
+/*
+ * Sensitivities of the network output to each parameter around the VI mean (Sec. 3.1,
+ * the equation defining S_i^2; the step before the sampler in Algorithm 2):
+ *   S2[i] = sd[i]^2 / N_d * sum over the data terms of (dF/dtheta_i)^2 at theta = mu,
+ * the data terms being the MLP outputs F_o(x_n) (N_d = n * d_out) or the DeepONet
+ * outputs S_jk = <B_j, T_k> + b0 over all (input function, query) pairs
+ * (N_d = n_u * n_y).
+ *   spec        network; spec->prec chooses the arithmetic: HMC_PREC_FP64 runs in
+ *               double, any other precision in float with double column sums
+ *   data        inputs x (MLP) or u and yq (DeepONet); targets are not read
+ *   mu, sd [P]  VI means and standard deviations (double), parameter order as above
+ *   S2 [P]      output (double)
+ *   cuda_stream where the work is queued; the call returns once S2 is written
+ * Cost: one forward pass, d_out (MLP) or p (DeepONet) reverse passes batched as GEMMs,
+ * and per layer one GEMM of the squared activations with the squared adjoints.
+ */
+HMC_API hmc_status hmc_sensitivity(const hmc_net_spec *spec, const hmc_data *data, const double *mu,
+                                   const double *sd, double *S2, void *cuda_stream);
+
+/*
+ * The truncation of the parameter set (Sec. 3.1, the equation defining N-hat, and the
+ * subsets of Sec. 3.2): with the parameters ranked by S2 from most to least sensitive
+ * (equal values: lower index first),
+ *   N_hat = max{ N_T : sum of the first N_T S2 / sum of all S2 <= tau },
+ * and the sampled subset Theta_s is the first N_hat of the ranking.  Sums are FP64,
+ * in rank order; an all-zero S2 gives N_hat = 0.
+ *   S2 [P]        sensitivities (double, non-negative and finite; else HMC_ERR_ARG)
+ *   tau           the variance share to keep
+ *   mask [P]      output: 1 for Theta_s (the subset_mask of hmc_create), else 0
+ *   n_hat         output (host): N_hat
+ *   order [P]     output, may be NULL: parameter indices in rank order (int64)
+ * The ranking is a stable radix sort, so it is exact and reproducible.
+ */
+HMC_API hmc_status hmc_select_subset(const double *S2, long P, double tau, unsigned char *mask, long *n_hat,
+                                     long long *order, void *cuda_stream);
+
+/*
+ * Posterior predictive (Sec. 4.2.1): the network's outputs on new inputs for every
+ * sample, reduced over the samples to
+ *   mean = (1/S) sum_s F_s   and   std = sqrt((1/S) sum_s (F_s - mean)^2)
+ * per output, and optionally the mean relative L2 error of the mean against targets,
+ *   rel_l2 = (1/N) sum_i ||Y_i - mean_i||_2 / ||Y_i||_2,
+ * over the N = n_u input functions of a DeepONet (each over its n_y queries), or with
+ * N = 1 over all outputs of an MLP.
+ *   h          a single-problem handle (hmc_create or hmc_create_split): its network,
+ *              frozen vector and subset
+ *   samples    [n_samples][k] positions in the handle's precision (e.g. the samples
+ *              array of hmc_sample, whose [n][C][k] is n*C samples)
+ *   inputs     new inputs: x, n, dx (MLP) or u, n_u, du, yq, n_y, dy (DeepONet); the
+ *              targets y or t are read only when rel_l2 is not NULL
+ *   mean, std  outputs [n][d_out] (MLP) or [n_u][n_y] (DeepONet), double
+ *   rel_l2     output (host double) or NULL
+ * Runs in the handle's arithmetic (double for HMC_PREC_FP64, float otherwise; the
+ * reduction over samples in double, samples in order) and returns when done.
+ */
+HMC_API hmc_status hmc_predict(hmc_handle h, const void *samples, long n_samples, const hmc_data *inputs,
+                               double *mean, double *std, double *rel_l2);
 
 /* Free the handle and all its device memory. NULL is accepted. */
 HMC_API hmc_status hmc_destroy(hmc_handle h);

@@ -31,7 +31,8 @@ STATUS = {0: "HMC_OK", 1: "HMC_ERR_ARG", 2: "HMC_ERR_CUDA", 3: "HMC_ERR_OOM", 4:
           5: "HMC_ERR_TIMEOUT", 6: "HMC_ERR_UNSUPPORTED"}
 
 # every symbol the C ABI (include/hmc.h, include/hmc_diag.h) declares
-EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_diag_umma_gemm",
+EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_create_split", "hmc_sensitivity", "hmc_select_subset",
+           "hmc_predict", "hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_diag_umma_gemm",
            "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_adapt_step_size", "hmc_destroy", "hmc_last_error",
            "hmc_energy_grad_noalloc",
            "hmc_diag_philox", "hmc_diag_momenta", "hmc_diag_log_uniform", "hmc_diag_graph_kernels",
@@ -79,6 +80,10 @@ def lib():
         L.hmc_create.argtypes = [ct.POINTER(vp), ct.POINTER(NetSpec), ct.POINTER(Data), d, d, vp, vp, i, vp]
         L.hmc_create_batch.argtypes = [ct.POINTER(vp), i, ct.POINTER(NetSpec), ct.POINTER(Data),
                                        ct.POINTER(d), ct.POINTER(d), ct.POINTER(vp), ct.POINTER(vp), i, vp]
+        L.hmc_predict.argtypes = [vp, vp, lg, ct.POINTER(Data), vp, vp, ct.POINTER(d)]
+        L.hmc_sensitivity.argtypes = [ct.POINTER(NetSpec), ct.POINTER(Data), vp, vp, vp, vp]
+        L.hmc_select_subset.argtypes = [vp, lg, d, vp, ct.POINTER(lg), vp, vp]
+        L.hmc_create_split.argtypes = [ct.POINTER(vp), ct.POINTER(NetSpec), ct.POINTER(Data), d, d, vp, vp, i, i, vp]
         L.hmc_subset_size.argtypes = [vp]
         L.hmc_subset_size.restype = lg
         L.hmc_param_count.argtypes = [vp]
@@ -162,7 +167,8 @@ def _stream_ptr(stream):
 class Sampler:
     """One libhmc handle: a problem (or a batch of problems) with C chains."""
 
-    def __init__(self, spec, data, arrays, prior_sigma, noise_sigma, mask, frozen, chains, stream=None):
+    def __init__(self, spec, data, arrays, prior_sigma, noise_sigma, mask, frozen, chains, stream=None,
+                 n_splits=1):
         import torch
         self.prec = spec.prec
         self.dtype = torch.float64 if spec.prec == PREC_FP64 else torch.float32
@@ -171,9 +177,16 @@ class Sampler:
         f = _f64(np.asarray(frozen)) if not hasattr(frozen, "data_ptr") else _f64(frozen)
         self._keep += [m, f]
         h = ct.c_void_p()
-        _check(lib().hmc_create(ct.byref(h), ct.byref(spec), ct.byref(data), float(prior_sigma),
-                                float(noise_sigma), _ptr(m), _ptr(f), int(chains), _stream_ptr(stream)))
+        if n_splits == 1:
+            _check(lib().hmc_create(ct.byref(h), ct.byref(spec), ct.byref(data), float(prior_sigma),
+                                    float(noise_sigma), _ptr(m), _ptr(f), int(chains), _stream_ptr(stream)))
+        else:   # symmetric split integrator over n_splits data batches
+            _check(lib().hmc_create_split(ct.byref(h), ct.byref(spec), ct.byref(data), float(prior_sigma),
+                                          float(noise_sigma), _ptr(m), _ptr(f), int(chains), int(n_splits),
+                                          _stream_ptr(stream)))
         self._h = h
+        self.n_splits = int(n_splits)
+        self.dout = spec.net.widths[spec.net.n_layers] if spec.kind == NET_MLP else 1
         self.chains = int(chains)
         self.k = int(lib().hmc_subset_size(h))
         self.P = int(lib().hmc_param_count(h))
@@ -181,7 +194,7 @@ class Sampler:
 
     @classmethod
     def mlp(cls, widths, x, y, mask, frozen, chains, prior_sigma=1.0, noise_sigma=1.0, prec=PREC_FP32,
-            act=None, bias=True, stream=None):
+            act=None, bias=True, stream=None, n_splits=1):
         spec = NetSpec()
         spec.kind = NET_MLP
         spec.net = mlp_spec(widths, act, bias)
@@ -189,12 +202,12 @@ class Sampler:
         x, y = _f64(x), _f64(y)
         d = Data()
         d.x, d.n, d.dx, d.y = _ptr(x), x.shape[0], x.shape[1], _ptr(y)
-        return cls(spec, d, [x, y], prior_sigma, noise_sigma, mask, frozen, chains, stream)
+        return cls(spec, d, [x, y], prior_sigma, noise_sigma, mask, frozen, chains, stream, n_splits)
 
     @classmethod
     def deeponet(cls, branch, trunk, u, yq, t, mask, frozen, chains, prior_sigma=1.0, noise_sigma=1.0,
                  prec=PREC_FP32, out_bias=True, branch_act=None, trunk_act=None, branch_bias=True,
-                 trunk_bias=True, stream=None):
+                 trunk_bias=True, stream=None, n_splits=1):
         spec = NetSpec()
         spec.kind = NET_DEEPONET
         spec.branch = mlp_spec(branch, branch_act, branch_bias)
@@ -206,7 +219,7 @@ class Sampler:
         d.u, d.n_u, d.du = _ptr(u), u.shape[0], u.shape[1]
         d.yq, d.n_y, d.dy = _ptr(yq), yq.shape[0], yq.shape[1]
         d.t = _ptr(t)
-        return cls(spec, d, [u, yq, t], prior_sigma, noise_sigma, mask, frozen, chains, stream)
+        return cls(spec, d, [u, yq, t], prior_sigma, noise_sigma, mask, frozen, chains, stream, n_splits)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -268,6 +281,42 @@ class Sampler:
         lib().hmc_diag_tuning(self._h, buf, int(n) + 1)
         return buf.value.decode()
 
+    def predict(self, samples, x=None, y=None, u=None, yq=None, t=None):
+        """Posterior predictive on new inputs (hmc_predict): mean and std ([n][d_out] for
+        an MLP, [n_u][n_y] for a DeepONet) as float64 CUDA tensors, and the mean relative
+        L2 error of the mean when targets (y or t) are given (else None)."""
+        import torch
+        S = samples.reshape(-1, self.k).to(device="cuda", dtype=self.dtype).contiguous()
+        d = Data()
+        keep = []
+        if x is not None:
+            x = _f64(x)
+            d.x, d.n, d.dx = _ptr(x), x.shape[0], x.shape[1]
+            keep.append(x)
+            shape = (x.shape[0], self.dout)
+            tg = y
+        else:
+            u, yq = _f64(u), _f64(yq)
+            d.u, d.n_u, d.du = _ptr(u), u.shape[0], u.shape[1]
+            d.yq, d.n_y, d.dy = _ptr(yq), yq.shape[0], yq.shape[1]
+            keep += [u, yq]
+            shape = (u.shape[0], yq.shape[0])
+            tg = t
+        rel = None
+        if tg is not None:
+            tg = _f64(tg)
+            keep.append(tg)
+            if x is not None:
+                d.y = _ptr(tg)
+            else:
+                d.t = _ptr(tg)
+            rel = ct.c_double()
+        mean = torch.empty(shape, dtype=torch.float64, device="cuda")
+        std = torch.empty_like(mean)
+        _check(lib().hmc_predict(self._h, _ptr(S), S.shape[0], ct.byref(d), _ptr(mean), _ptr(std),
+                                 ct.byref(rel) if rel is not None else None))
+        return mean, std, (rel.value if rel is not None else None)
+
     def metropolis_energy(self, q):
         """U [C] used by the Metropolis test (hmc_diag_metropolis_energy)."""
         import torch
@@ -288,6 +337,62 @@ class Sampler:
         _check(lib().hmc_sample(self._h, _ptr(q0), float(eps), int(L), int(n), int(seed), int(first_traj),
                                 _ptr(S), _ptr(acc), _ptr(dH), _ptr(ql)))
         return S, acc, dH, ql
+
+
+def _sens(spec, d, keep, mu, sd):
+    import torch
+    P = int(np.asarray(mu).shape[0]) if not hasattr(mu, "data_ptr") else int(mu.shape[0])
+    m = mu.to(device="cuda", dtype=torch.float64).contiguous() if hasattr(mu, "data_ptr") else \
+        torch.from_numpy(np.ascontiguousarray(mu, dtype=np.float64)).cuda()
+    v = sd.to(device="cuda", dtype=torch.float64).contiguous() if hasattr(sd, "data_ptr") else \
+        torch.from_numpy(np.ascontiguousarray(sd, dtype=np.float64)).cuda()
+    S2 = torch.empty(P, dtype=torch.float64, device="cuda")
+    _check(lib().hmc_sensitivity(ct.byref(spec), ct.byref(d), _ptr(m), _ptr(v), _ptr(S2), _stream_ptr(None)))
+    return S2
+
+
+def sensitivity_mlp(widths, x, mu, sd, prec=PREC_FP32, act=None, bias=True):
+    """S_i^2 (Sec. 3.1) of every parameter of an MLP at the VI means mu with VI standard
+    deviations sd (hmc_sensitivity); a float64 CUDA tensor [P]."""
+    spec = NetSpec()
+    spec.kind = NET_MLP
+    spec.net = mlp_spec(widths, act, bias)
+    spec.prec = prec
+    x = _f64(x)
+    d = Data()
+    d.x, d.n, d.dx = _ptr(x), x.shape[0], x.shape[1]
+    return _sens(spec, d, [x], mu, sd)
+
+
+def sensitivity_deeponet(branch, trunk, u, yq, mu, sd, prec=PREC_FP32, out_bias=True, branch_act=None,
+                         trunk_act=None, branch_bias=True, trunk_bias=True):
+    """S_i^2 (Sec. 3.1) of every DeepONet parameter over all (input function, query) pairs."""
+    spec = NetSpec()
+    spec.kind = NET_DEEPONET
+    spec.branch = mlp_spec(branch, branch_act, branch_bias)
+    spec.trunk = mlp_spec(trunk, trunk_act, trunk_bias)
+    spec.deeponet_out_bias = 1 if out_bias else 0
+    spec.prec = prec
+    u, yq = _f64(u), _f64(yq)
+    d = Data()
+    d.u, d.n_u, d.du = _ptr(u), u.shape[0], u.shape[1]
+    d.yq, d.n_y, d.dy = _ptr(yq), yq.shape[0], yq.shape[1]
+    return _sens(spec, d, [u, yq], mu, sd)
+
+
+def select_subset(S2, tau):
+    """N-hat of Sec. 3.1 and the subset (hmc_select_subset): (n_hat, mask [P] uint8,
+    ranking [P] int64), all from the GPU."""
+    import torch
+    S2 = S2.to(device="cuda", dtype=torch.float64).contiguous() if hasattr(S2, "data_ptr") else \
+        torch.from_numpy(np.ascontiguousarray(S2, dtype=np.float64)).cuda()
+    P = int(S2.shape[0])
+    mask = torch.empty(P, dtype=torch.uint8, device="cuda")
+    order = torch.empty(P, dtype=torch.int64, device="cuda")
+    n = ct.c_long()
+    _check(lib().hmc_select_subset(_ptr(S2), P, float(tau), _ptr(mask), ct.byref(n), _ptr(order),
+                                   _stream_ptr(None)))
+    return int(n.value), mask, order
 
 
 class KernelTime(ct.Structure):

@@ -162,11 +162,13 @@ __device__ __forceinline__ void load_seg(SegDesc &dst, const SegDesc *src)
     __syncthreads();
 }
 
-// p ~ N(0, I); partial sums of p.p; first half kick p -= eps/2 g; first drift q* = q + eps p; scatter q*.
+// p ~ N(0, I); partial sums of p.p; first half kick p -= eps/2 g; first drift q* = q + drift p
+// (drift = eps for the leapfrog); scatter q*.
 template <typename T>
 __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_begin(const SegDesc *segs, int C, int nblk, const T *q_cur,
                                                              const T *g_cur, T *q_prop, T *p, double *K0p,
-                                                             double eps, uint64_t seed, const TrajState *st)
+                                                             double eps, double drift, uint64_t seed,
+                                                             const TrajState *st)
 {
     __shared__ __align__(16) unsigned char sd_raw[sizeof(SegDesc)];
     SegDesc &sd = *reinterpret_cast<SegDesc *>(sd_raw);
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_begin(const SegDesc *segs
     if (j0 < sd.k) {
         const long base = sd.qoff + (long)c * sd.k;
         const uint64_t traj = (uint64_t)st->traj;
-        const T h = (T)(0.5 * eps), e = (T)eps;
+        const T h = (T)(0.5 * eps), e = (T)drift;
         const long blk = j0 / 4 + threadIdx.x;
         if (blk * 4 < sd.k) {
             double z[4];
@@ -384,6 +386,27 @@ __global__ void k_nonfinite_count(const double *U, int n, int *out)
     atomicAdd(out, bad);
 }
 
+// U[c] = sum over batches m (in order) of U_split[m][c].
+__global__ void k_split_energy_sum(const double *U_split, int M, int C, double *U)
+{
+    pdl_wait();
+    pdl_trigger();
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        double u = 0.0;
+        for (int m = 0; m < M; ++m) u += U_split[(long)m * C + c];
+        U[c] = u;
+    }
+}
+
+// g += d, elementwise over n entries.
+template <typename T> __global__ void k_accumulate(T *g, const T *d, long n)
+{
+    pdl_wait();
+    pdl_trigger();
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        g[i] = g[i] + d[i];
+}
+
 }  // namespace hmc
 
 using namespace hmc;
@@ -403,6 +426,10 @@ struct hmc_handle_s {
     std::vector<cudaEvent_t> ev_join;
     std::vector<std::unique_ptr<Problem>> probs;
     std::vector<std::unique_ptr<Engine>> engines;
+    // split handles (hmc_create_split): one problem whose data rows are cut into
+    // nsplit batches, engines[m] holding batch m with 1/nsplit of the prior
+    int nsplit = 1;
+    DevBuf U_split, g_tmp;
     std::vector<long> qoff;
     long k_total = 0, P_total = 0, S_total = 0;
     DevBuf q_cur, g_cur, q_prop, p, g_prop, U_cur, U_prop, K0p, K1p, acc_int, segs, state, scratch;
@@ -548,8 +575,14 @@ template <typename F> void for_each_problem(hmc_handle h, F &&fn)
     }
 }
 
+void split_energy_grad_full(hmc_handle h, const void *q, double *U, void *g);
+
 void energy_grad_all(hmc_handle h, void *q, double *U, void *g, bool scattered)
 {
+    if (h->nsplit > 1) {
+        split_energy_grad_full(h, q, U, g);
+        return;
+    }
     for_each_problem(h, [&](int i, cudaStream_t s) {
         char *qb = static_cast<char *>(q) + h->qoff[i] * h->elem;
         char *gb = g ? static_cast<char *>(g) + h->qoff[i] * h->elem : nullptr;
@@ -559,8 +592,19 @@ void energy_grad_all(hmc_handle h, void *q, double *U, void *g, bool scattered)
 
 // Overwrite U with the accurate energy where an engine's energy_grad U is a
 // reduced-precision one (q already scattered by the preceding energy_grad_all).
+void split_energy(hmc_handle h, int m, const void *q);
+void split_sum(hmc_handle h, double *U);
+
 void accurate_energy_all(hmc_handle h, void *q, double *U)
 {
+    if (h->nsplit > 1) {
+        bool any = false;
+        for (auto &e : h->engines) any = any || e->has_accurate_energy();
+        if (!any) return;
+        for (int m = 0; m < h->nsplit; ++m) split_energy(h, m, q);
+        split_sum(h, U);
+        return;
+    }
     bool any = false;
     for (auto &e : h->engines) any = any || e->has_accurate_energy();
     if (!any) return;
@@ -600,14 +644,131 @@ void kick_drift(hmc_handle h, void *q, void *p, const void *g, double kick, doub
     HMC_LAUNCH_CK();
 }
 
+// ---- symmetric split integrator (split handles) ----------------------------------
+// H = sum_m [U_m + K/M] with U_m the likelihood of data batch m plus 1/M of the prior
+// (engine m).  One step of size eps: for m = 1..M { p -= eps/2 grad U_m; q += eps/(2M) p }
+// then for m = M..1 { q += eps/(2M) p; p -= eps/2 grad U_m }.  The launches below fuse
+// each kick with the drift after it, and the last kick of a step (batch 1) with the
+// first kick of the next, so a step costs 2M - 1 batch gradients.
+
+// grad U_m(q) into g and U_m into U_split[m]; engine m scatters q itself.
+void split_grad(hmc_handle h, int m, const void *q, void *g)
+{
+    h->engines[m]->energy_grad(q, h->U_split.as<double>() + (long)m * h->C, g, false, h->stream);
+}
+
+// U_m(q) only, the accurate one where the engine has it.
+void split_energy(hmc_handle h, int m, const void *q)
+{
+    Engine *e = h->engines[m].get();
+    double *Um = h->U_split.as<double>() + (long)m * h->C;
+    if (e->has_accurate_energy()) {
+        e->scatter(q, h->stream);
+        e->accurate_energy(q, Um, h->stream);
+    } else {
+        e->energy_grad(q, Um, nullptr, false, h->stream);
+    }
+}
+
+void split_sum(hmc_handle h, double *U)
+{
+    launch_pdl(k_split_energy_sum, dim3((h->C + 255) / 256), dim3(256), 0, h->stream, h->U_split.as<double>(),
+               h->nsplit, h->C, U);
+    HMC_LAUNCH_CK();
+}
+
+// U and grad U of the whole data set: the sums over the batches.
+void split_energy_grad_full(hmc_handle h, const void *q, double *U, void *g)
+{
+    const long n = h->S_total;
+    for (int m = 0; m < h->nsplit; ++m) {
+        if (!g) {
+            h->engines[m]->energy_grad(q, h->U_split.as<double>() + (long)m * h->C, nullptr, false, h->stream);
+            continue;
+        }
+        split_grad(h, m, q, m == 0 ? g : h->g_tmp.ptr);
+        if (m == 0) continue;
+        const dim3 grid((unsigned)std::min<long>((n + 255) / 256, 4096));
+        if (h->prec == HMC_PREC_FP64)
+            launch_pdl(k_accumulate<double>, grid, dim3(256), 0, h->stream, (double *)g, h->g_tmp.as<double>(), n);
+        else
+            launch_pdl(k_accumulate<float>, grid, dim3(256), 0, h->stream, (float *)g, h->g_tmp.as<float>(), n);
+        HMC_LAUNCH_CK();
+    }
+    split_sum(h, U);
+}
+
+// The Metropolis energy sum_m U_m(q) into U, and grad U_1(q) (batch 1) into g1.
+void split_start(hmc_handle h, const void *q, double *U, void *g1)
+{
+    for (int m = h->nsplit - 1; m >= 1; --m) split_energy(h, m, q);
+    split_grad(h, 0, q, g1);
+    if (h->engines[0]->has_accurate_energy())
+        h->engines[0]->accurate_energy(q, h->U_split.as<double>(), h->stream);
+    split_sum(h, U);
+}
+
+// L split steps on (q, p).  On entry p has had the first half kick with grad U_1 and q
+// its first drift; on exit g1 = grad U_1(q_end) and U_split[0] = U_1(q_end), and the
+// final half kick is still to be applied.
+void split_steps(hmc_handle h, void *q, void *p, void *g1, double eps, int L)
+{
+    const int M = h->nsplit;
+    const double d = eps / (2.0 * M), d0 = M == 1 ? eps : d;
+    for (int s = 1; s <= L; ++s) {
+        for (int m = 1; m < M; ++m) {   // forward sweep, batches 2..M
+            split_grad(h, m, q, h->g_tmp.ptr);
+            kick_drift(h, q, p, h->g_tmp.ptr, 0.5 * eps, m < M - 1 ? d : 2.0 * d);
+        }
+        for (int m = M - 1; m >= 1; --m) {   // backward sweep, batches M..2
+            split_grad(h, m, q, h->g_tmp.ptr);
+            kick_drift(h, q, p, h->g_tmp.ptr, 0.5 * eps, d);
+        }
+        split_grad(h, 0, q, g1);
+        if (s < L) kick_drift(h, q, p, g1, eps, d0);
+    }
+}
+
+template <typename T> void enqueue_split_trajectory(hmc_handle h, double eps, int L, uint64_t seed)
+{
+    const int nseg = h->C, nblk = h->traj_nblk, M = h->nsplit;
+    const SegDesc *sd = h->segs.as<SegDesc>();
+    TrajState *st = h->state.as<TrajState>();
+    const dim3 grid(nblk, nseg);
+    const double d0 = M == 1 ? eps : eps / (2.0 * M);
+    launch_pdl(k_traj_begin<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, h->q_cur.as<T>(),
+               h->g_cur.as<T>(), h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(), eps, d0, seed, st);
+    HMC_LAUNCH_CK();
+    split_steps(h, h->q_prop.ptr, h->p.ptr, h->g_prop.ptr, eps, L);
+    // H1: the other batches' energies at the end point (batch 1's came with its gradient)
+    for (int m = M - 1; m >= 1; --m) split_energy(h, m, h->q_prop.ptr);
+    if (h->engines[0]->has_accurate_energy())
+        h->engines[0]->accurate_energy(h->q_prop.ptr, h->U_split.as<double>(), h->stream);
+    split_sum(h, h->U_prop.as<double>());
+    launch_pdl(k_traj_kinetic<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, h->p.as<T>(),
+               h->g_prop.as<T>(), h->K1p.as<double>(), eps);
+    HMC_LAUNCH_CK();
+    launch_pdl(k_traj_accept<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, nseg, h->S_total,
+               h->q_cur.as<T>(), h->g_cur.as<T>(), h->U_cur.as<double>(), h->q_prop.as<T>(), h->g_prop.as<T>(),
+               h->U_prop.as<double>(), h->K0p.as<double>(), h->K1p.as<double>(), seed, st, h->acc_int.as<int>());
+    HMC_LAUNCH_CK();
+    launch_pdl(k_traj_advance, dim3(1), dim3(256), 0, h->stream, st, nseg, h->acc_int.as<int>(),
+               h->U_cur.as<double>(), h->U_prop.as<double>());
+    HMC_LAUNCH_CK();
+}
+
 template <typename T> void enqueue_trajectory(hmc_handle h, double eps, int L, uint64_t seed)
 {
+    if (h->nsplit > 1) {
+        enqueue_split_trajectory<T>(h, eps, L, seed);
+        return;
+    }
     const int nseg = h->nprob * h->C, nblk = h->traj_nblk;
     const SegDesc *sd = h->segs.as<SegDesc>();
     TrajState *st = h->state.as<TrajState>();
     const dim3 grid(nblk, nseg);
     launch_pdl(k_traj_begin<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, h->q_cur.as<T>(),
-               h->g_cur.as<T>(), h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(), eps, seed, st);
+               h->g_cur.as<T>(), h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(), eps, eps, seed, st);
     HMC_LAUNCH_CK();
     for (int s = 1; s <= L; ++s) {
         energy_grad_all(h, h->q_prop.ptr, h->U_prop.as<double>(), h->g_prop.ptr, true);
@@ -630,9 +791,51 @@ template <typename T> void enqueue_trajectory(hmc_handle h, double eps, int L, u
     HMC_LAUNCH_CK();
 }
 
+Engine *make_engine(Problem &p, int prec, int C)
+{
+    if (prec == HMC_PREC_FP64) return make_simt_engine_f64(p, C);
+    if (prec == HMC_PREC_FP32) return make_simt_engine_f32(p, C);
+    if (prec == HMC_PREC_BF16) {
+        std::string why;
+        const bool don = p.kind == HMC_NET_DEEPONET;
+        if (!(don ? don_engine_supports(p, &why) : umma_engine_supports(p, &why))) {
+            set_error("BF16 tensor-core path does not support this network: %s", why.c_str());
+            throw Fail{HMC_ERR_UNSUPPORTED};
+        }
+        return don ? make_don_engine_bf16(p, C) : make_umma_engine_bf16(p, C);
+    }
+    set_error("HMC_PREC_TF32 is not implemented");
+    throw Fail{HMC_ERR_UNSUPPORTED};
+}
+
+// Data batch m of M (rows [floor(m R / M), floor((m + 1) R / M)) of the R data rows:
+// MLP points, or DeepONet input functions with all their queries), with 1/M of the
+// prior: alpha scaled by sqrt(M) makes its q^2 / (2 alpha^2) term 1/M of the whole.
+std::unique_ptr<Problem> batch_problem(const Problem &full, int M, int m)
+{
+    auto p = std::make_unique<Problem>(full);
+    p->engine = nullptr;
+    p->alpha = full.alpha * std::sqrt((double)M);
+    const long R = full.kind == HMC_NET_MLP ? full.n : full.n_u;
+    const long r0 = (long)((__int128)R * m / M), r1 = (long)((__int128)R * (m + 1) / M);
+    auto rows = [&](const std::vector<double> &v, long width) {
+        return std::vector<double>(v.begin() + r0 * width, v.begin() + r1 * width);
+    };
+    if (full.kind == HMC_NET_MLP) {
+        p->n = r1 - r0;
+        p->x = rows(full.x, full.dx);
+        p->y = rows(full.y, full.dout);
+    } else {
+        p->n_u = r1 - r0;
+        p->u = rows(full.u, full.du);
+        p->t = rows(full.t, full.n_y);
+    }
+    return p;
+}
+
 hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, const hmc_data *data,
                        const double *alpha, const double *sigma, const unsigned char *const *masks,
-                       const double *const *frozen, int C, void *stream)
+                       const double *const *frozen, int C, void *stream, int nsplit = 1)
 {
     HMC_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
@@ -663,29 +866,36 @@ hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, co
             HMC_CK(cudaEventCreateWithFlags(&h->ev_join[j], cudaEventDisableTiming));
         }
     }
-    for (int i = 0; i < nprob; ++i) {
-        h->probs.push_back(build_problem(specs[i], data[i], alpha[i], sigma[i], masks[i], frozen[i], C));
-        Problem &p = *h->probs.back();
-        Engine *e = nullptr;
-        if (prec == HMC_PREC_FP64) e = make_simt_engine_f64(p, C);
-        else if (prec == HMC_PREC_FP32) e = make_simt_engine_f32(p, C);
-        else if (prec == HMC_PREC_BF16) {
-            std::string why;
-            const bool don = p.kind == HMC_NET_DEEPONET;
-            if (!(don ? don_engine_supports(p, &why) : umma_engine_supports(p, &why))) {
-                set_error("BF16 tensor-core path does not support this network: %s", why.c_str());
-                throw Fail{HMC_ERR_UNSUPPORTED};
-            }
-            e = don ? make_don_engine_bf16(p, C) : make_umma_engine_bf16(p, C);
-        } else {
-            set_error("HMC_PREC_TF32 is not implemented");
-            throw Fail{HMC_ERR_UNSUPPORTED};
+    HMC_REQUIRE(nsplit >= 1 && nsplit <= HMC_MAX_SPLITS, "n_splits must be in [1, %d]", HMC_MAX_SPLITS);
+    HMC_REQUIRE(nsplit == 1 || nprob == 1, "a split handle holds one problem");
+    h->nsplit = nsplit;
+    if (nsplit > 1) {
+        auto full = build_problem(specs[0], data[0], alpha[0], sigma[0], masks[0], frozen[0], C);
+        const long R = full->kind == HMC_NET_MLP ? full->n : full->n_u;
+        HMC_REQUIRE(R >= nsplit, "n_splits (%d) exceeds the number of data rows (%ld)", nsplit, R);
+        for (int m = 0; m < nsplit; ++m) {
+            h->probs.push_back(batch_problem(*full, nsplit, m));
+            Problem &p = *h->probs.back();
+            Engine *e = make_engine(p, prec, C);
+            h->engines.emplace_back(e);
+            p.engine = e;
         }
-        h->engines.emplace_back(e);
-        p.engine = e;
-        h->qoff.push_back(h->k_total * C);
-        h->k_total += p.k;
-        h->P_total += p.P;
+        h->qoff.push_back(0);
+        h->k_total = full->k;
+        h->P_total = full->P;
+        h->U_split.alloc(sizeof(double) * nsplit * C);
+        h->g_tmp.alloc(h->elem * (size_t)full->k * C);
+    } else {
+        for (int i = 0; i < nprob; ++i) {
+            h->probs.push_back(build_problem(specs[i], data[i], alpha[i], sigma[i], masks[i], frozen[i], C));
+            Problem &p = *h->probs.back();
+            Engine *e = make_engine(p, prec, C);
+            h->engines.emplace_back(e);
+            p.engine = e;
+            h->qoff.push_back(h->k_total * C);
+            h->k_total += p.k;
+            h->P_total += p.P;
+        }
     }
     h->S_total = h->k_total * C;
     const size_t sb = h->elem * (size_t)h->S_total;
@@ -749,6 +959,17 @@ hmc_status hmc_create(hmc_handle *out, const hmc_net_spec *spec, const hmc_data 
     });
 }
 
+hmc_status hmc_create_split(hmc_handle *out, const hmc_net_spec *spec, const hmc_data *data, double prior_sigma,
+                            double noise_sigma, const unsigned char *subset_mask, const double *frozen_params,
+                            int n_chains, int n_splits, void *cuda_stream)
+{
+    g_err.clear();
+    return guarded([&] {
+        return create_impl(out, 1, spec, data, &prior_sigma, &noise_sigma, &subset_mask, &frozen_params, n_chains,
+                           cuda_stream, n_splits);
+    });
+}
+
 hmc_status hmc_create_batch(hmc_handle *out, int n_problems, const hmc_net_spec *specs, const hmc_data *data,
                             const double *prior_sigma, const double *noise_sigma,
                             const unsigned char *const *subset_masks, const double *const *frozen_params,
@@ -758,6 +979,150 @@ hmc_status hmc_create_batch(hmc_handle *out, int n_problems, const hmc_net_spec 
     return guarded([&] {
         return create_impl(out, n_problems, specs, data, prior_sigma, noise_sigma, subset_masks, frozen_params,
                            n_chains, cuda_stream);
+    });
+}
+
+hmc_status hmc_sensitivity(const hmc_net_spec *spec, const hmc_data *data, const double *mu, const double *sd,
+                           double *S2, void *cuda_stream)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(spec && data && mu && sd && S2, "NULL argument");
+        HMC_REQUIRE(spec->kind == HMC_NET_MLP || spec->kind == HMC_NET_DEEPONET, "unknown net kind %d", spec->kind);
+        SensProblem pr;
+        pr.kind = spec->kind;
+        const std::vector<long> none;
+        if (spec->kind == HMC_NET_MLP) {
+            check_mlp_spec(spec->net, "net");
+            HMC_REQUIRE(data->n >= 1 && data->dx == spec->net.widths[0], "data.n must be >= 1 and data.dx = widths[0]");
+            build_net_desc(pr.net, spec->net, 0, none);
+            pr.P = pr.net.P;
+            pr.n = data->n;
+            pr.x = fetch(data->x, data->n * data->dx, "data.x");
+        } else {
+            check_mlp_spec(spec->branch, "branch");
+            check_mlp_spec(spec->trunk, "trunk");
+            HMC_REQUIRE(spec->branch.widths[spec->branch.n_layers] == spec->trunk.widths[spec->trunk.n_layers],
+                        "branch and trunk output widths differ");
+            HMC_REQUIRE(data->n_u >= 1 && data->n_y >= 1 && data->du == spec->branch.widths[0] &&
+                            data->dy == spec->trunk.widths[0],
+                        "DeepONet data dimensions do not match the spec");
+            build_net_desc(pr.branch, spec->branch, 0, none);
+            build_net_desc(pr.trunk, spec->trunk, pr.branch.P, none);
+            pr.out_bias = spec->deeponet_out_bias ? 1 : 0;
+            pr.P = pr.branch.P + pr.trunk.P + pr.out_bias;
+            pr.n_u = data->n_u;
+            pr.n_y = data->n_y;
+            pr.u = fetch(data->u, data->n_u * data->du, "data.u");
+            pr.yq = fetch(data->yq, data->n_y * data->dy, "data.yq");
+        }
+        HMC_REQUIRE(pr.P < (1L << 31), "too many parameters (%ld)", pr.P);
+        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        const size_t pb = sizeof(double) * (size_t)pr.P;
+        DevBuf dmu, dsd, ds2;
+        const double *m = mu, *d = sd;
+        double *o = S2;
+        if (!is_device_ptr(mu)) {
+            dmu.alloc(pb);
+            HMC_CK(cudaMemcpy(dmu.ptr, mu, pb, cudaMemcpyHostToDevice));
+            m = dmu.as<double>();
+        }
+        if (!is_device_ptr(sd)) {
+            dsd.alloc(pb);
+            HMC_CK(cudaMemcpy(dsd.ptr, sd, pb, cudaMemcpyHostToDevice));
+            d = dsd.as<double>();
+        }
+        const bool host_out = !is_device_ptr(S2);
+        if (host_out) {
+            ds2.alloc(pb);
+            o = ds2.as<double>();
+        }
+        sensitivity_run(pr, spec->prec, m, d, o, st);
+        if (host_out) HMC_CK(cudaMemcpy(S2, o, pb, cudaMemcpyDeviceToHost));
+        return HMC_OK;
+    });
+}
+
+hmc_status hmc_select_subset(const double *S2, long P, double tau, unsigned char *mask, long *n_hat,
+                             long long *order, void *cuda_stream)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(S2 && mask && n_hat, "NULL argument");
+        HMC_REQUIRE(P >= 1 && P < (1L << 31), "P must be in [1, 2^31)");
+        HMC_REQUIRE(std::isfinite(tau), "tau must be finite");
+        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        DevBuf ds2, dm, dord;
+        const double *s2 = S2;
+        if (!is_device_ptr(S2)) {
+            ds2.alloc(sizeof(double) * P);
+            HMC_CK(cudaMemcpy(ds2.ptr, S2, sizeof(double) * P, cudaMemcpyHostToDevice));
+            s2 = ds2.as<double>();
+        }
+        const bool host_mask = !is_device_ptr(mask), host_ord = order && !is_device_ptr(order);
+        unsigned char *m = mask;
+        long long *od = order;
+        if (host_mask) {
+            dm.alloc(P);
+            m = dm.as<unsigned char>();
+        }
+        if (host_ord) {
+            dord.alloc(sizeof(long long) * P);
+            od = dord.as<long long>();
+        }
+        *n_hat = select_subset_run(s2, P, tau, m, od, st);
+        if (host_mask) HMC_CK(cudaMemcpy(mask, m, P, cudaMemcpyDeviceToHost));
+        if (host_ord) HMC_CK(cudaMemcpy(order, od, sizeof(long long) * P, cudaMemcpyDeviceToHost));
+        return HMC_OK;
+    });
+}
+
+hmc_status hmc_predict(hmc_handle h, const void *samples, long n_samples, const hmc_data *inputs, double *mean,
+                       double *std_out, double *rel_l2)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(h && samples && inputs && mean && std_out, "NULL argument");
+        HMC_REQUIRE(h->nprob == 1, "hmc_predict takes a single-problem handle");
+        HMC_REQUIRE(n_samples >= 1, "n_samples must be >= 1");
+        const Problem &p = *h->probs[0];
+        PredictInput in;
+        in.kind = p.kind;
+        in.net = p.net;
+        in.branch = p.branch;
+        in.trunk = p.trunk;
+        in.out_bias = p.out_bias;
+        in.P = p.P;
+        in.frozen = p.frozen;
+        in.idx = p.idx;
+        long nout;
+        if (p.kind == HMC_NET_MLP) {
+            HMC_REQUIRE(inputs->n >= 1 && inputs->dx == p.dx, "inputs: n must be >= 1 and dx = %d", p.dx);
+            in.n = inputs->n;
+            nout = in.n * p.dout;
+            in.x = fetch(inputs->x, in.n * p.dx, "inputs.x");
+            if (rel_l2) in.targets = fetch(inputs->y, nout, "inputs.y (targets for rel_l2)");
+        } else {
+            HMC_REQUIRE(inputs->n_u >= 1 && inputs->n_y >= 1 && inputs->du == p.du && inputs->dy == p.dy,
+                        "inputs: DeepONet dimensions do not match the handle's");
+            in.n_u = inputs->n_u;
+            in.n_y = inputs->n_y;
+            nout = in.n_u * in.n_y;
+            in.u = fetch(inputs->u, in.n_u * p.du, "inputs.u");
+            in.yq = fetch(inputs->yq, in.n_y * p.dy, "inputs.yq");
+            if (rel_l2) in.targets = fetch(inputs->t, nout, "inputs.t (targets for rel_l2)");
+        }
+        h->stage.clear();
+        join_in(h);
+        bool ss, sm, sv;
+        const void *ds = dev_view(h, samples, h->elem * (size_t)n_samples * p.k, true, &ss);
+        double *dm = static_cast<double *>(dev_view(h, mean, sizeof(double) * nout, false, &sm));
+        double *dv = static_cast<double *>(dev_view(h, std_out, sizeof(double) * nout, false, &sv));
+        predict_run(in, h->prec, ds, n_samples, dm, dv, rel_l2, h->stream);
+        if (sm) HMC_CK(cudaMemcpy(mean, dm, sizeof(double) * nout, cudaMemcpyDeviceToHost));
+        if (sv) HMC_CK(cudaMemcpy(std_out, dv, sizeof(double) * nout, cudaMemcpyDeviceToHost));
+        join_out(h);
+        return HMC_OK;
     });
 }
 
@@ -805,7 +1170,13 @@ hmc_status hmc_leapfrog(hmc_handle h, void *q, void *p, double eps, int L)
         bool sq, sp;
         void *dq = dev_view(h, q, sb, true, &sq);
         void *dp = dev_view(h, p, sb, true, &sp);
-        if (L > 0) {
+        if (L > 0 && h->nsplit > 1) {
+            const double d0 = eps / (2.0 * h->nsplit);
+            split_grad(h, 0, dq, h->g_prop.ptr);
+            kick_drift(h, dq, dp, h->g_prop.ptr, 0.5 * eps, d0);
+            split_steps(h, dq, dp, h->g_prop.ptr, eps, L);
+            kick_drift(h, dq, dp, h->g_prop.ptr, 0.5 * eps, 0.0);
+        } else if (L > 0) {
             energy_grad_all(h, dq, h->U_prop.as<double>(), h->g_prop.ptr, false);
             kick_drift(h, dq, dp, h->g_prop.ptr, 0.5 * eps, eps);
             for (int s = 1; s <= L; ++s) {
@@ -841,8 +1212,12 @@ hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_sa
         unsigned char *da = static_cast<unsigned char *>(dev_view(h, accepted, (size_t)nseg * n_samples, false, &sa));
         double *ddh = static_cast<double *>(dev_view(h, dH, sizeof(double) * nseg * n_samples, false, &sd));
         void *dl = dev_view(h, q_last, sb, false, &sl);
-        energy_grad_all(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr, false);
-        accurate_energy_all(h, h->q_cur.ptr, h->U_cur.as<double>());   // H0 of the first trajectory
+        if (h->nsplit > 1) {   // U for H0 and grad U of the first batch for the first kick
+            split_start(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr);
+        } else {
+            energy_grad_all(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr, false);
+            accurate_energy_all(h, h->q_cur.ptr, h->U_cur.as<double>());   // H0 of the first trajectory
+        }
         k_set_state<<<1, 1, 0, h->stream>>>(h->state.as<TrajState>(), first_traj, 0, ds, da, ddh);
         HMC_LAUNCH_CK();
         if (n_samples > 0) {
@@ -964,7 +1339,8 @@ long hmc_diag_tuning(hmc_handle h, char *buf, long n)
 {
     if (!h) return -1;
     std::string t;
-    for (int i = 0; i < h->nprob; ++i) t += "problem " + std::to_string(i) + ": " + h->engines[i]->tuning() + "\n";
+    for (size_t i = 0; i < h->engines.size(); ++i)
+        t += (h->nsplit > 1 ? "batch " : "problem ") + std::to_string(i) + ": " + h->engines[i]->tuning() + "\n";
     if (buf && n > 0) {
         const size_t m = std::min<size_t>((size_t)n - 1, t.size());
         memcpy(buf, t.data(), m);

@@ -83,6 +83,9 @@ struct Engine {
     // The sampled coordinates are assumed already scattered into the network
     // when `scattered` is true (the trajectory kernels do it in the drift).
     virtual void energy_grad(const void *q, double *U, void *g, bool scattered, cudaStream_t s) = 0;
+    // Write q [C][k] into the engine's parameter buffers (what energy_grad does first
+    // when `scattered` is false).
+    virtual void scatter(const void *q, cudaStream_t s) = 0;
     virtual ScatterPlan scatter_plan() = 0;
     virtual size_t bytes() const = 0;
     // The energy for the Metropolis test.  Engines whose energy_grad U is only as
@@ -121,6 +124,39 @@ Engine *make_umma_engine_bf16(Problem &p, int C);
 bool umma_engine_supports(const Problem &p, std::string *why);
 Engine *make_don_engine_bf16(Problem &p, int C);
 bool don_engine_supports(const Problem &p, std::string *why);
+
+// Sensitivities and truncation (k_sens.cu): a network and its inputs, no subset.
+struct SensProblem {
+    int kind = 0;
+    NetDesc net, branch, trunk;
+    int out_bias = 0;
+    long P = 0;
+    long n = 0, n_u = 0, n_y = 0;
+    std::vector<double> x, u, yq;   // host copies of the inputs (FP64)
+};
+// S2 [P] (device) from the VI means mu and standard deviations sd [P] (device).
+void sensitivity_run(const SensProblem &pr, int prec, const double *mu, const double *sd, double *S2,
+                     cudaStream_t s);
+// mask [P] (device) and the ranking order [P] (device, may be null) from S2 (device); returns N-hat.
+long select_subset_run(const double *S2, long P, double tau, unsigned char *mask, long long *order,
+                       cudaStream_t s);
+
+// Posterior predictive (k_predict.cu): a problem's network, frozen vector and subset,
+// with new inputs (and, for the error, their targets).
+struct PredictInput {
+    int kind = 0;
+    NetDesc net, branch, trunk;
+    int out_bias = 0;
+    long P = 0;
+    std::vector<double> frozen;
+    std::vector<long> idx;
+    long n = 0, n_u = 0, n_y = 0;
+    std::vector<double> x, u, yq, targets;   // host copies (FP64)
+};
+// mean, sd [outputs] (device) over S samples [S][k] (device, handle precision); rel_l2
+// (host, may be null) the mean relative L2 error of the mean against the targets.
+void predict_run(const PredictInput &in, int prec, const void *samples, long S, double *mean, double *sd,
+                 double *rel_l2, cudaStream_t s);
 
 // Programmatic dependent launch.  A kernel started with launch_pdl may begin while
 // the previous kernel in its stream drains: it runs pdl_wait() before it touches any

@@ -1727,16 +1727,18 @@ class UmmaEngine final : public Engine {
 
     ScatterPlan scatter_plan() override { return plan_; }
 
+    void scatter(const void *qv, cudaStream_t s) override
+    {
+        dim3 grid((unsigned)std::min<long>((k_ + 255) / 256, 1024), C_);
+        ProfScope ps("scatter", s);
+        launch_pdl(k_scatter_plan<float>, grid, dim3(256), 0, s, static_cast<const float *>(qv), k_, plan_);
+    }
+
     void energy_grad(const void *qv, double *U, void *gv, bool scattered, cudaStream_t s) override
     {
         const float *q = static_cast<const float *>(qv);
         float *g = static_cast<float *>(gv);
-        if (!scattered) {
-            dim3 grid((unsigned)std::min<long>((k_ + 255) / 256, 1024), C_);
-            ProfScope ps("scatter", s);
-            launch_pdl(k_scatter_plan<float>, grid, dim3(256), 0, s, q, k_, plan_);
-            HMC_LAUNCH_CK();
-        }
+        if (!scattered) scatter(qv, s);
         const NetDesc &nd = p_.net;
         Params base{};
         base.err = err_;
@@ -2324,15 +2326,18 @@ class DonEngine final : public Engine {
         launch_pdl(k_finalize_bf16, dim3(1, C_), dim3(256), 0, s, fa, q, U, (float *)nullptr);
     }
 
+    void scatter(const void *qv, cudaStream_t s) override
+    {
+        dim3 grid((unsigned)std::min<long>((k_ + 255) / 256, 1024), C_);
+        ProfScope ps("scatter", s);
+        launch_pdl(k_scatter_plan<float>, grid, dim3(256), 0, s, static_cast<const float *>(qv), k_, plan_);
+    }
+
     void energy_grad(const void *qv, double *U, void *gv, bool scattered, cudaStream_t s) override
     {
         const float *q = static_cast<const float *>(qv);
         float *g = static_cast<float *>(gv);
-        if (!scattered) {
-            dim3 grid((unsigned)std::min<long>((k_ + 255) / 256, 1024), C_);
-            ProfScope ps("scatter", s);
-            launch_pdl(k_scatter_plan<float>, grid, dim3(256), 0, s, q, k_, plan_);
-        }
+        if (!scattered) scatter(qv, s);
         forward(br_, s);
         forward(tr_, s);
         launch_s(b_col_, s);   // S = B T^T + b0, residual, energy partials and dS

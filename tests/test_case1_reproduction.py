@@ -1,7 +1,7 @@
 """Case I of the BNN example (Sec. 4.1.1) end to end on the oracle, against Table 1.
 
 The data are the paper's function with its true parameters and sigma_d = 1e-3 on
-20 equispaced points of [-1, -0.2] U [0.2, 1]; the sampler uses App. D's Case I
+20 equispaced points of [-1, -0.2] U [0.2, 1]; the sampler uses App. C's Case I
 settings (step 1e-5, L = pi 0.0679^2 / (2e-5) = 724, prior variance 1, likelihood
 variance 1e-6).  What Table 1 fixes:
 * full HMC (all six parameters): the posterior means and standard deviations of the

@@ -349,7 +349,7 @@ def case1_sine(theta, mask=None, chains=1, eps=1e-5, L=724, noise=1e-3, prior=1.
     1-2-1 with sine hidden units, a hidden bias and no output bias; its parameters
     (W1 = (w1, w2), b1 = (p1, p2), W2 = (a, b)) are `theta`, which also gives the frozen
     values.  `true` = (w1, w2, p1, p2, a, b) generates the data.  Default eps and L are
-    the paper's (App. D: step 1e-5, L = pi * 0.0679^2 / (2 * 1e-5))."""
+    the paper's (App. C: step 1e-5, L = pi * 0.0679^2 / (2 * 1e-5))."""
     rng = np.random.default_rng(seed)
     net = Net([1, 2, 1], [ACT_SIN, ACT_IDENTITY], [True, False])
     x = _f32(np.concatenate([np.linspace(-1.0, -0.2, 10), np.linspace(0.2, 1.0, 10)])[:, None])

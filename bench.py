@@ -182,6 +182,7 @@ def main():
     ap.add_argument("--ess-traj", type=int, default=200, help="trajectories for the ESS/s comparison (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--split", type=int, default=4, help="data batches of the split-integrator run (0 = skip)")
+    ap.add_argument("--no-around", action="store_true", help="skip the sensitivity/truncation/predictive timings")
     args = ap.parse_args()
     assert args.warmup >= 3, "timing rules need at least 3 warm-up steps"
     if args.impl == "reference":
@@ -333,6 +334,35 @@ def main():
                  "full_gradient_equivalents_per_s": C * L * (2 * M - 1) / M / (sms / 1000.0)}
         ss.close()
 
+    # the steps around the sampler on the same workload: sensitivities of all P
+    # parameters at the frozen values (FP32), the tau = 0.9 truncation, and the
+    # posterior predictive of 256 samples on the 8192 training inputs
+    around = None
+    if rank == 0 and not args.no_around:
+        mu = torch.from_numpy(prob.frozen).cuda()
+        sd = torch.full_like(mu, 0.05)
+        hmc.sensitivity_mlp(prob.net.widths, prob.x, mu, sd)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S2 = hmc.sensitivity_mlp(prob.net.widths, prob.x, mu, sd)
+        torch.cuda.synchronize()
+        t_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        nhat, _, _ = hmc.select_subset(S2, 0.9)
+        torch.cuda.synchronize()
+        t_sel = time.perf_counter() - t0
+        Sp = q.repeat(16, 1)                                       # 256 samples
+        s.predict(Sp[:16], x=prob.x)                               # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, rel = s.predict(Sp, x=prob.x, y=prob.y)
+        torch.cuda.synchronize()
+        t_p = time.perf_counter() - t0
+        around = {"sensitivity": {"params": prob.P, "points": int(prob.x.shape[0]), "dtype": "f32", "ms": 1e3 * t_s},
+                  "select_subset": {"params": prob.P, "tau": 0.9, "n_hat": nhat, "ms": 1e3 * t_sel},
+                  "predict": {"samples": int(Sp.shape[0]), "points": int(prob.x.shape[0]), "dtype": "f32",
+                              "ms": 1e3 * t_p, "samples_per_s": Sp.shape[0] / t_p, "rel_l2": rel}}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob)
@@ -353,7 +383,8 @@ def main():
                 "roofline": roof, "kernel_ms": {k: v[0] for k, v in prof.items()},
                 "tuning": s.tuning().strip(),
                 "kernel_launches_per_eval": {k: v[1] for k, v in prof.items()},
-                "e2e": e2e, "cpu_baseline": cpu, "ess": ess, "split_hmc": split, "clocks": clocks}
+                "e2e": e2e, "cpu_baseline": cpu, "ess": ess, "split_hmc": split, "around_the_sampler": around,
+                "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -45,7 +45,7 @@ def test_predict_parity(which, prec):
         new = W.small_mlp(n=123, widths=(3, 40, 33, 2), chains=1, seed=96)   # new inputs and targets
         new.net, new.frozen, new.mask = prob.net, prob.frozen, prob.mask
         kw = dict(x=new.x, y=new.y)
-        targets = new.y
+        targets = new.y.reshape(1, -1)    # an MLP's outputs form one row
     else:
         prob = W.small_deeponet(n_u=37, n_y=29, chains=1, seed=97)
         new = W.small_deeponet(n_u=21, n_y=17, chains=1, seed=98)
@@ -60,10 +60,10 @@ def test_predict_parity(which, prec):
     mr, sr = o.predict(Q)
     if prec == hmc.PREC_FP64:
         _check(m, sd, mr, sr, 1e-12, 1e-9)
-        assert rel == pytest.approx(oracle.rel_l2(targets, mr), rel=1e-12)
+        assert rel == pytest.approx(oracle.rel_l2(targets, mr.reshape(targets.shape)), rel=1e-12)
     else:
         _check(m, sd, mr, sr, 2e-5, 2e-5)
-        assert rel == pytest.approx(oracle.rel_l2(targets, mr), rel=1e-4)
+        assert rel == pytest.approx(oracle.rel_l2(targets, mr.reshape(targets.shape)), rel=1e-4)
 
 
 def test_predict_one_sample_has_no_spread():

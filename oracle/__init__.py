@@ -131,7 +131,10 @@ class Oracle:
             s.branch, s.trunk = _net(prob.branch), _net(prob.trunk)
             u, yq, t = keep(prob.u), keep(prob.yq), keep(prob.t)
             s.n_u, s.du, s.u = u.shape[0], u.shape[1], _ptr(u)
-            s.n_y, s.dy, s.yq = yq.shape[0], yq.shape[1], _ptr(yq)
+            if prob.kind == 2:   # every input function with its own queries: yq [n_u][n_y][dy]
+                s.n_y, s.dy, s.yq = yq.shape[1], yq.shape[2], _ptr(yq)
+            else:
+                s.n_y, s.dy, s.yq = yq.shape[0], yq.shape[1], _ptr(yq)
             s.t = _ptr(t)
         s.noise_sigma, s.prior_sigma = float(prob.noise_sigma), float(prob.prior_sigma)
         fr = keep(prob.frozen)
@@ -152,7 +155,7 @@ class Oracle:
         if p.kind == 0:
             f = np.zeros((p.x.shape[0], p.net.widths[-1]))
         else:
-            f = np.zeros((p.u.shape[0], p.yq.shape[0]))
+            f = np.zeros(p.t.shape)
         lib().or_forward(self._sp, _ptr(theta), _ptr(f))
         return f
 
@@ -221,7 +224,7 @@ class Oracle:
         outputs on this problem's inputs (Sec. 4.2.1)."""
         Q = np.ascontiguousarray(samples, dtype=np.float64).reshape(-1, self.k)
         p = self.prob
-        shape = (p.x.shape[0], p.net.widths[-1]) if p.kind == 0 else (p.u.shape[0], p.yq.shape[0])
+        shape = (p.x.shape[0], p.net.widths[-1]) if p.kind == 0 else p.t.shape
         mean, sd = np.zeros(shape), np.zeros(shape)
         lib().or_predict(self._sp, _ptr(Q), Q.shape[0], _ptr(mean), _ptr(sd))
         return mean, sd

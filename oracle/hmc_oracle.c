@@ -47,13 +47,13 @@ typedef struct {
 } or_net;
 
 typedef struct {
-    int kind;                 /* 0 = MLP, 1 = DeepONet */
+    int kind;                 /* 0 = MLP, 1 = DeepONet (shared queries), 2 = DeepONet (own queries) */
     int out_bias;             /* DeepONet scalar output bias present */
     or_net net, branch, trunk;
     long n; int dx; const double *x;     /* MLP inputs  [n][dx] */
     const double *y;                     /* MLP targets [n][dout] */
     long n_u; int du; const double *u;   /* DeepONet branch inputs [n_u][du] */
-    long n_y; int dy; const double *yq;  /* DeepONet trunk inputs  [n_y][dy] */
+    long n_y; int dy; const double *yq;  /* DeepONet trunk inputs [n_y][dy]; kind 2: [n_u][n_y][dy] */
     const double *t;                     /* DeepONet targets [n_u][n_y] */
     double noise_sigma, prior_sigma;
     const double *frozen; long P;        /* full parameter vector, values off the subset */
@@ -185,6 +185,18 @@ static double *assemble_theta(const or_problem *pr, const double *q)
     return theta;
 }
 
+/* DeepONet trunk rows: the n_y shared queries, or (kind 2) every function's own n_y queries. */
+static long trunk_rows(const or_problem *pr)
+{
+    return pr->kind == 2 ? pr->n_u * pr->n_y : pr->n_y;
+}
+
+/* The trunk row of query j of input function i. */
+static long trunk_row(const or_problem *pr, long i, long j)
+{
+    return pr->kind == 2 ? i * pr->n_y + j : j;
+}
+
 /* Network outputs for a full parameter vector: MLP [n][dout], DeepONet [n_u][n_y]. */
 void or_forward(const or_problem *pr, const double *theta, double *f)
 {
@@ -204,20 +216,22 @@ void or_forward(const or_problem *pr, const double *theta, double *f)
     long pb = or_net_params(bn), pt = or_net_params(tn);
     double b0 = pr->out_bias ? theta[pb + pt] : 0.0;
     double *B = (double *)malloc(sizeof(double) * (size_t)(pr->n_u * p));
-    double *T = (double *)malloc(sizeof(double) * (size_t)(pr->n_y * p));
+    long NT = trunk_rows(pr);
+    double *T = (double *)malloc(sizeof(double) * (size_t)((NT > 0 ? NT : 1) * p));
     or_tape tb, tt; tape_init(&tb, bn); tape_init(&tt, tn);
     for (long i = 0; i < pr->n_u; ++i) {
         net_forward(bn, theta, pr->u + i * pr->du, &tb);
         memcpy(B + i * p, tb.a[bn->n_layers], sizeof(double) * (size_t)p);
     }
-    for (long j = 0; j < pr->n_y; ++j) {
-        net_forward(tn, theta + pb, pr->yq + j * pr->dy, &tt);
-        memcpy(T + j * p, tt.a[tn->n_layers], sizeof(double) * (size_t)p);
+    for (long t = 0; t < NT; ++t) {
+        net_forward(tn, theta + pb, pr->yq + t * pr->dy, &tt);
+        memcpy(T + t * p, tt.a[tn->n_layers], sizeof(double) * (size_t)p);
     }
     for (long i = 0; i < pr->n_u; ++i)
         for (long j = 0; j < pr->n_y; ++j) {
+            const double *Tj = T + trunk_row(pr, i, j) * p;
             double s = 0.0;
-            for (int c = 0; c < p; ++c) s += B[i * p + c] * T[j * p + c];
+            for (int c = 0; c < p; ++c) s += B[i * p + c] * Tj[c];
             f[i * pr->n_y + j] = s + b0;
         }
     free(tb.buf); free(tt.buf); free(B); free(T);
@@ -268,18 +282,22 @@ double or_energy_grad_rows(const or_problem *pr, const double *q, double *g, lon
         long pb = or_net_params(bn), pt = or_net_params(tn);
         double b0 = pr->out_bias ? theta[pb + pt] : 0.0;
         /* forward both nets, keeping every sample's tape for the reverse pass */
+        /* the trunk rows these functions use: all shared queries, or their own */
+        long NT = trunk_rows(pr);
+        long t0 = pr->kind == 2 ? r0 * pr->n_y : 0, t1 = pr->kind == 2 ? r1 * pr->n_y : NT;
         or_tape *tb = (or_tape *)malloc(sizeof(or_tape) * (size_t)(pr->n_u > 0 ? pr->n_u : 1));
-        or_tape *tt = (or_tape *)malloc(sizeof(or_tape) * (size_t)(pr->n_y > 0 ? pr->n_y : 1));
+        or_tape *tt = (or_tape *)malloc(sizeof(or_tape) * (size_t)(NT > 0 ? NT : 1));
         for (long i = r0; i < r1; ++i) { tape_init(&tb[i], bn); net_forward(bn, theta, pr->u + i * pr->du, &tb[i]); }
-        for (long j = 0; j < pr->n_y; ++j) { tape_init(&tt[j], tn); net_forward(tn, theta + pb, pr->yq + j * pr->dy, &tt[j]); }
+        for (long t = t0; t < t1; ++t) { tape_init(&tt[t], tn); net_forward(tn, theta + pb, pr->yq + t * pr->dy, &tt[t]); }
         double *dB = (double *)calloc((size_t)(pr->n_u * p), sizeof(double));
-        double *dT = (double *)calloc((size_t)(pr->n_y * p), sizeof(double));
+        double *dT = (double *)calloc((size_t)((NT > 0 ? NT : 1) * p), sizeof(double));
         double db0 = 0.0;
         /* S_ij = <B_i, T_j> + b0;  dU/dS_ij = (S_ij - t_ij) / sigma^2 */
         for (long i = r0; i < r1; ++i) {
             const double *Bi = tb[i].a[bn->n_layers];
             for (long j = 0; j < pr->n_y; ++j) {
-                const double *Tj = tt[j].a[tn->n_layers];
+                long tr = trunk_row(pr, i, j);
+                const double *Tj = tt[tr].a[tn->n_layers];
                 double s = 0.0;
                 for (int c = 0; c < p; ++c) s += Bi[c] * Tj[c];
                 double r = s + b0 - pr->t[i * pr->n_y + j];
@@ -287,7 +305,7 @@ double or_energy_grad_rows(const or_problem *pr, const double *q, double *g, lon
                 double dS = r / s2;
                 for (int c = 0; c < p; ++c) {
                     dB[i * p + c] += dS * Tj[c];
-                    dT[j * p + c] += dS * Bi[c];
+                    dT[tr * p + c] += dS * Bi[c];
                 }
                 db0 += dS;
             }
@@ -295,10 +313,10 @@ double or_energy_grad_rows(const or_problem *pr, const double *q, double *g, lon
         int wmax = net_wmax(bn) > net_wmax(tn) ? net_wmax(bn) : net_wmax(tn);
         double *work = (double *)malloc(sizeof(double) * (size_t)(2 * wmax));
         for (long i = r0; i < r1; ++i) net_backward(bn, theta, &tb[i], dB + i * p, grad, work);
-        for (long j = 0; j < pr->n_y; ++j) net_backward(tn, theta + pb, &tt[j], dT + j * p, grad + pb, work);
+        for (long t = t0; t < t1; ++t) net_backward(tn, theta + pb, &tt[t], dT + t * p, grad + pb, work);
         if (pr->out_bias) grad[pb + pt] += db0;
         for (long i = r0; i < r1; ++i) free(tb[i].buf);
-        for (long j = 0; j < pr->n_y; ++j) free(tt[j].buf);
+        for (long t = t0; t < t1; ++t) free(tt[t].buf);
         free(tb); free(tt); free(dB); free(dT); free(work);
     }
 
@@ -676,23 +694,25 @@ void or_sensitivity(const or_problem *pr, const double *mu, const double *sd, do
         long pb = or_net_params(bn);
         Nd = (double)pr->n_u * pr->n_y;
         or_tape *tb = (or_tape *)malloc(sizeof(or_tape) * (size_t)(pr->n_u > 0 ? pr->n_u : 1));
-        or_tape *tt = (or_tape *)malloc(sizeof(or_tape) * (size_t)(pr->n_y > 0 ? pr->n_y : 1));
+        long NT = trunk_rows(pr);
+        or_tape *tt = (or_tape *)malloc(sizeof(or_tape) * (size_t)(NT > 0 ? NT : 1));
         for (long j = 0; j < pr->n_u; ++j) { tape_init(&tb[j], bn); net_forward(bn, mu, pr->u + j * pr->du, &tb[j]); }
-        for (long k = 0; k < pr->n_y; ++k) { tape_init(&tt[k], tn); net_forward(tn, mu + pb, pr->yq + k * pr->dy, &tt[k]); }
+        for (long t = 0; t < NT; ++t) { tape_init(&tt[t], tn); net_forward(tn, mu + pb, pr->yq + t * pr->dy, &tt[t]); }
         int wmax = net_wmax(bn) > net_wmax(tn) ? net_wmax(bn) : net_wmax(tn);
         double *work = (double *)malloc(sizeof(double) * (size_t)(2 * wmax));
         for (long j = 0; j < pr->n_u; ++j)
             for (long k = 0; k < pr->n_y; ++k) {
                 /* dS_jk/dB_j = T_k and dS_jk/dT_k = B_j; dS_jk/db0 = 1 */
+                const or_tape *tk = &tt[trunk_row(pr, j, k)];
                 memset(grad, 0, sizeof(double) * (size_t)P);
-                net_backward(bn, mu, &tb[j], tt[k].a[tn->n_layers], grad, work);
-                net_backward(tn, mu + pb, &tt[k], tb[j].a[bn->n_layers], grad + pb, work);
+                net_backward(bn, mu, &tb[j], tk->a[tn->n_layers], grad, work);
+                net_backward(tn, mu + pb, tk, tb[j].a[bn->n_layers], grad + pb, work);
                 if (pr->out_bias) grad[P - 1] = 1.0;
                 for (long i = 0; i < P; ++i) acc[i] += grad[i] * grad[i];
             }
         (void)p;
         for (long j = 0; j < pr->n_u; ++j) free(tb[j].buf);
-        for (long k = 0; k < pr->n_y; ++k) free(tt[k].buf);
+        for (long t = 0; t < NT; ++t) free(tt[t].buf);
         free(tb); free(tt); free(work);
     }
     for (long i = 0; i < P; ++i) S2[i] = sd[i] * sd[i] / Nd * acc[i];

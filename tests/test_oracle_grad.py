@@ -22,6 +22,8 @@ def _problems():
         W.small_deeponet(),
         W.small_deeponet(out_bias=False, frac=0.5, seed=4),
         W.tiny_bnn(n=40),
+        W.small_deeponet_unaligned(),
+        W.small_deeponet_unaligned(out_bias=False, n_q=5, seed=5),
     ]
     return out
 
@@ -30,7 +32,7 @@ def _fd_directional(o, q, v, h):
     return (o.energy(q + h * v) - o.energy(q - h * v)) / (2.0 * h)
 
 
-@pytest.mark.parametrize("pi", range(7))
+@pytest.mark.parametrize("pi", range(9))
 def test_gradient_matches_central_differences(pi):
     prob = _problems()[pi]
     o = oracle.Oracle(prob)
@@ -78,10 +80,17 @@ def _torch_energy(prob, q):
     if prob.kind == W.KIND_MLP:
         f, _ = _torch_net(prob.net, theta, torch.tensor(prob.x))
         r = f - torch.tensor(prob.y)
-    else:
+    elif prob.kind == W.KIND_DEEPONET:
         B, off = _torch_net(prob.branch, theta, torch.tensor(prob.u))
         T, off = _torch_net(prob.trunk, theta, torch.tensor(prob.yq), base=off)
         S = B @ T.T
+        if prob.out_bias:
+            S = S + theta[off]
+        r = S - torch.tensor(prob.t)
+    else:   # every input function with its own queries
+        B, off = _torch_net(prob.branch, theta, torch.tensor(prob.u))
+        T, off = _torch_net(prob.trunk, theta, torch.tensor(prob.yq), base=off)   # [n_u][n_q][p]
+        S = torch.einsum("ic,ijc->ij", B, T)
         if prob.out_bias:
             S = S + theta[off]
         r = S - torch.tensor(prob.t)
@@ -90,7 +99,7 @@ def _torch_energy(prob, q):
     return float(U), qt.grad.numpy()
 
 
-@pytest.mark.parametrize("pi", range(7))
+@pytest.mark.parametrize("pi", range(9))
 def test_energy_and_gradient_match_torch_autograd(pi):
     prob = _problems()[pi]
     o = oracle.Oracle(prob)
@@ -145,3 +154,19 @@ def test_frozen_parameters_enter_only_through_the_likelihood():
     oh = oracle.Oracle(h)
     qh = np.array([0.3, -0.2, 0.5, 1.0])
     assert np.isclose(oh.energy(qh), np.sum(qh**2) / (2 * h.prior_sigma**2), rtol=1e-14)
+
+
+def test_unaligned_deeponet_with_shared_queries_is_the_aligned_one():
+    # every function given the same query set: the per-function layout must give the
+    # aligned problem's U exactly and its gradient up to summation order
+    pu = W.small_deeponet_unaligned(shared=True)
+    pa = W.Problem("aligned", W.KIND_DEEPONET, pu.noise_sigma, pu.prior_sigma, pu.frozen, pu.mask, pu.q0,
+                   eps=pu.eps, L=pu.L, branch=pu.branch, trunk=pu.trunk, out_bias=pu.out_bias,
+                   u=pu.u, yq=pu.yq[0], t=pu.t)
+    ou, oa = oracle.Oracle(pu), oracle.Oracle(pa)
+    for q in pu.q0:
+        Uu, gu = ou.energy_grad(q)
+        Ua, ga = oa.energy_grad(q)
+        assert Uu == Ua
+        assert np.allclose(gu, ga, rtol=1e-12, atol=1e-12 * np.max(np.abs(ga)))
+    assert np.array_equal(ou.forward(pu.frozen), oa.forward(pu.frozen))

@@ -67,13 +67,15 @@ def _fd_S2(o, prob, mu, sd, h=1e-6):
     return sd ** 2 * acc / prob.n_terms()
 
 
-@pytest.mark.parametrize("which", ["mlp", "deeponet"])
+@pytest.mark.parametrize("which", ["mlp", "deeponet", "deeponet_unaligned"])
 def test_finite_differences(which):
     if which == "mlp":
         prob = W.small_mlp(n=25, widths=(3, 7, 5, 2), acts=[W.ACT_TANH, W.ACT_SIN, W.ACT_IDENTITY],
                            bias=[True, False, True], seed=71)
-    else:
+    elif which == "deeponet":
         prob = W.small_deeponet(n_u=6, n_y=5, du=4, width=6, latent=3, seed=72)
+    else:
+        prob = W.small_deeponet_unaligned(n_u=5, n_q=4, du=3, width=6, latent=3, seed=74)
     o = oracle.Oracle(prob)
     rng = np.random.default_rng(2)
     mu = 0.5 * rng.standard_normal(prob.P)

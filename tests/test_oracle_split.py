@@ -23,10 +23,11 @@ from test_oracle_posterior import _check_moments, _linear_closed_form
 
 
 def _probs():
-    return {"small_mlp": W.small_mlp, "deeponet": W.small_deeponet, "tiny_bnn": lambda: W.tiny_bnn(n=64)}
+    return {"small_mlp": W.small_mlp, "deeponet": W.small_deeponet, "tiny_bnn": lambda: W.tiny_bnn(n=64),
+            "deeponet_unaligned": W.small_deeponet_unaligned}
 
 
-@pytest.mark.parametrize("which", ["small_mlp", "deeponet"])
+@pytest.mark.parametrize("which", ["small_mlp", "deeponet", "deeponet_unaligned"])
 @pytest.mark.parametrize("M", [1, 3, 7])
 def test_batches_partition_the_data(which, M):
     prob = _probs()[which]()

@@ -40,7 +40,7 @@ from typing import List, Optional
 import numpy as np
 
 ACT_IDENTITY, ACT_TANH, ACT_SIN = 0, 1, 2
-KIND_MLP, KIND_DEEPONET = 0, 1
+KIND_MLP, KIND_DEEPONET, KIND_DEEPONET_UNALIGNED = 0, 1, 2
 
 
 def _f32(a):
@@ -106,7 +106,7 @@ class Problem:
     x: Optional[np.ndarray] = None      # MLP inputs [n][dx]
     y: Optional[np.ndarray] = None      # MLP targets [n][dout]
     u: Optional[np.ndarray] = None      # DeepONet branch inputs [n_u][du]
-    yq: Optional[np.ndarray] = None     # DeepONet trunk inputs [n_y][dy]
+    yq: Optional[np.ndarray] = None     # DeepONet trunk inputs [n_y][dy] ([n_u][n_y][dy] unaligned)
     t: Optional[np.ndarray] = None      # DeepONet targets [n_u][n_y]
     notes: dict = field(default_factory=dict)
 
@@ -130,7 +130,7 @@ class Problem:
         """Number of data terms in the full-batch likelihood."""
         if self.kind == KIND_MLP:
             return int(self.x.shape[0]) * int(self.y.shape[1])
-        return int(self.u.shape[0]) * int(self.yq.shape[0])
+        return int(self.t.size)
 
     def with_chains(self, chains, seed=None):
         """Same problem, different number of chains (initial states redrawn)."""
@@ -360,6 +360,28 @@ def case1_sine(theta, mask=None, chains=1, eps=1e-5, L=724, noise=1e-3, prior=1.
     q0 = np.repeat(frozen[mask.astype(bool)][None, :], chains, axis=0)
     return Problem("case1_sine", KIND_MLP, noise, prior, frozen, mask, q0, eps=eps, L=L, n_samples=5000,
                    seed=0, net=net, x=x, y=y)
+
+
+def small_deeponet_unaligned(n_u=23, n_q=11, du=6, dy=2, width=16, latent=8, frac=0.4, chains=3,
+                             eps=1e-3, L=6, noise=0.2, seed=8108, out_bias=True, shared=False):
+    """A DeepONet whose input functions each come with their own n_q query points
+    (yq [n_u][n_q][dy], t [n_u][n_q]).  shared=True repeats one query set for every
+    function, which makes it the aligned problem in the unaligned layout."""
+    rng = np.random.default_rng(seed)
+    branch = Net.mlp([du, width, width, latent])
+    trunk = Net.mlp([dy, width, latent])
+    u = _f32(rng.standard_normal((n_u, du)))
+    if shared:
+        yq = np.repeat(_f32(rng.uniform(0.0, 1.0, size=(1, n_q, dy))), n_u, axis=0)
+    else:
+        yq = _f32(rng.uniform(0.0, 1.0, size=(n_u, n_q, dy)))
+    t = _f32(np.tanh(u[:, :1]) * np.cos(np.pi * yq[:, :, 0]) + 0.1 * rng.standard_normal((n_u, n_q)))
+    P = deeponet_param_count(branch, trunk, out_bias)
+    mask = _subset_mask(rng, P, frac)
+    frozen = _f32(0.3 * rng.standard_normal(P))
+    q0 = _initial_states(rng, frozen, mask, chains, jitter=0.05)
+    return Problem("small_deeponet_unaligned", KIND_DEEPONET_UNALIGNED, noise, 1.0, frozen, mask, q0, eps=eps,
+                   L=L, n_samples=20, seed=0, branch=branch, trunk=trunk, out_bias=out_bias, u=u, yq=yq, t=t)
 
 
 def harmonic(k=7, prior=0.7, chains=1, eps=0.1, L=13, seed=9009):

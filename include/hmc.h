@@ -65,7 +65,10 @@ typedef enum { HMC_ACT_IDENTITY = 0, HMC_ACT_TANH = 1, HMC_ACT_SIN = 2 } hmc_act
  * fp32 accumulation) with fp32 positions/momenta and fp64 energy sums. */
 typedef enum { HMC_PREC_FP64 = 0, HMC_PREC_FP32 = 1, HMC_PREC_TF32 = 2, HMC_PREC_BF16 = 3 } hmc_prec;
 
-typedef enum { HMC_NET_MLP = 0, HMC_NET_DEEPONET = 1 } hmc_net_kind;
+/* HMC_NET_DEEPONET: n_u input functions evaluated at n_y query points shared by all
+ * of them.  HMC_NET_DEEPONET_UNALIGNED: every input function with its own n_y query
+ * points (FP64 and FP32 only). */
+typedef enum { HMC_NET_MLP = 0, HMC_NET_DEEPONET = 1, HMC_NET_DEEPONET_UNALIGNED = 2 } hmc_net_kind;
 
 /* One feed-forward stack: widths[0] inputs, widths[n_layers] outputs;
  * act[l] and has_bias[l] for Linear layer l. */
@@ -90,7 +93,8 @@ typedef struct {
 
 /* Training set, FP64, host or device.  MLP: x[n][dx], y[n][dout].
  * DeepONet (aligned): u[n_u][du] input functions, yq[n_y][dy] query points
- * shared by all functions, t[n_u][n_y] targets.  Unused fields are ignored. */
+ * shared by all functions, t[n_u][n_y] targets.  Unaligned DeepONet: yq[n_u][n_y][dy],
+ * the n_y query points of each function.  Unused fields are ignored. */
 typedef struct {
     const double *x; long n; int dx;
     const double *y;

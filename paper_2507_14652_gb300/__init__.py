@@ -26,7 +26,7 @@ MAXL = 16
 
 ACT_IDENTITY, ACT_TANH, ACT_SIN = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2, 3
-NET_MLP, NET_DEEPONET = 0, 1
+NET_MLP, NET_DEEPONET, NET_DEEPONET_UNALIGNED = 0, 1, 2
 STATUS = {0: "HMC_OK", 1: "HMC_ERR_ARG", 2: "HMC_ERR_CUDA", 3: "HMC_ERR_OOM", 4: "HMC_ERR_NONFINITE",
           5: "HMC_ERR_TIMEOUT", 6: "HMC_ERR_UNSUPPORTED"}
 
@@ -208,8 +208,10 @@ class Sampler:
     def deeponet(cls, branch, trunk, u, yq, t, mask, frozen, chains, prior_sigma=1.0, noise_sigma=1.0,
                  prec=PREC_FP32, out_bias=True, branch_act=None, trunk_act=None, branch_bias=True,
                  trunk_bias=True, stream=None, n_splits=1):
+        """A DeepONet; yq [n_y][dy] holds query points shared by every input function, or
+        yq [n_u][n_y][dy] each function's own (HMC_NET_DEEPONET_UNALIGNED)."""
         spec = NetSpec()
-        spec.kind = NET_DEEPONET
+        spec.kind = NET_DEEPONET if np.ndim(yq) == 2 else NET_DEEPONET_UNALIGNED
         spec.branch = mlp_spec(branch, branch_act, branch_bias)
         spec.trunk = mlp_spec(trunk, trunk_act, trunk_bias)
         spec.deeponet_out_bias = 1 if out_bias else 0
@@ -217,7 +219,7 @@ class Sampler:
         u, yq, t = _f64(u), _f64(yq), _f64(t)
         d = Data()
         d.u, d.n_u, d.du = _ptr(u), u.shape[0], u.shape[1]
-        d.yq, d.n_y, d.dy = _ptr(yq), yq.shape[0], yq.shape[1]
+        d.yq, d.n_y, d.dy = _ptr(yq), yq.shape[-2], yq.shape[-1]
         d.t = _ptr(t)
         return cls(spec, d, [u, yq, t], prior_sigma, noise_sigma, mask, frozen, chains, stream, n_splits)
 

@@ -487,7 +487,8 @@ template <typename V> std::vector<V> fetch(const V *src, long n, const char *wha
 std::unique_ptr<Problem> build_problem(const hmc_net_spec &spec, const hmc_data &d, double alpha, double sigma,
                                        const unsigned char *mask, const double *frozen, int C)
 {
-    HMC_REQUIRE(spec.kind == HMC_NET_MLP || spec.kind == HMC_NET_DEEPONET, "unknown net kind %d", spec.kind);
+    HMC_REQUIRE(spec.kind == HMC_NET_MLP || spec.kind == HMC_NET_DEEPONET || spec.kind == HMC_NET_DEEPONET_UNALIGNED,
+                "unknown net kind %d", spec.kind);
     HMC_REQUIRE(alpha > 0 && sigma > 0 && std::isfinite(alpha) && std::isfinite(sigma),
                 "prior_sigma and noise_sigma must be positive and finite");
     auto p = std::make_unique<Problem>();
@@ -539,7 +540,8 @@ std::unique_ptr<Problem> build_problem(const hmc_net_spec &spec, const hmc_data 
         p->du = d.du;
         p->dy = d.dy;
         p->u = fetch(d.u, d.n_u * d.du, "data.u");
-        p->yq = fetch(d.yq, d.n_y * d.dy, "data.yq");
+        const long nq = spec.kind == HMC_NET_DEEPONET_UNALIGNED ? d.n_u * d.n_y : d.n_y;
+        p->yq = fetch(d.yq, nq * d.dy, "data.yq");
         p->t = fetch(d.t, d.n_u * d.n_y, "data.t");
     }
     return p;
@@ -797,7 +799,7 @@ Engine *make_engine(Problem &p, int prec, int C)
     if (prec == HMC_PREC_FP32) return make_simt_engine_f32(p, C);
     if (prec == HMC_PREC_BF16) {
         std::string why;
-        const bool don = p.kind == HMC_NET_DEEPONET;
+        const bool don = p.kind != HMC_NET_MLP;
         if (!(don ? don_engine_supports(p, &why) : umma_engine_supports(p, &why))) {
             set_error("BF16 tensor-core path does not support this network: %s", why.c_str());
             throw Fail{HMC_ERR_UNSUPPORTED};
@@ -829,6 +831,7 @@ std::unique_ptr<Problem> batch_problem(const Problem &full, int M, int m)
         p->n_u = r1 - r0;
         p->u = rows(full.u, full.du);
         p->t = rows(full.t, full.n_y);
+        if (full.kind == HMC_NET_DEEPONET_UNALIGNED) p->yq = rows(full.yq, full.n_y * full.dy);
     }
     return p;
 }
@@ -988,6 +991,10 @@ hmc_status hmc_sensitivity(const hmc_net_spec *spec, const hmc_data *data, const
     g_err.clear();
     return guarded([&]() -> hmc_status {
         HMC_REQUIRE(spec && data && mu && sd && S2, "NULL argument");
+        if (spec->kind == HMC_NET_DEEPONET_UNALIGNED) {   // each function would need its own Gram matrix
+            set_error("hmc_sensitivity does not cover DeepONets with per-function query points");
+            throw Fail{HMC_ERR_UNSUPPORTED};
+        }
         HMC_REQUIRE(spec->kind == HMC_NET_MLP || spec->kind == HMC_NET_DEEPONET, "unknown net kind %d", spec->kind);
         SensProblem pr;
         pr.kind = spec->kind;
@@ -1084,6 +1091,10 @@ hmc_status hmc_predict(hmc_handle h, const void *samples, long n_samples, const 
     return guarded([&]() -> hmc_status {
         HMC_REQUIRE(h && samples && inputs && mean && std_out, "NULL argument");
         HMC_REQUIRE(h->nprob == 1, "hmc_predict takes a single-problem handle");
+        if (h->probs[0]->kind == HMC_NET_DEEPONET_UNALIGNED) {
+            set_error("hmc_predict does not cover DeepONets with per-function query points");
+            throw Fail{HMC_ERR_UNSUPPORTED};
+        }
         HMC_REQUIRE(n_samples >= 1, "n_samples must be >= 1");
         const Problem &p = *h->probs[0];
         PredictInput in;

@@ -91,6 +91,53 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part_r2, const d
 }
 
 
+// DeepONet with per-function queries: S[c][j][k] = <B[c][j], T[c][j nq + k]> + b0.
+template <typename T>
+__global__ void k_rowdot(const T *B, const T *Tm, long n_u, long nq, int p, const T *b0, long P, T *S)
+{
+    const int c = blockIdx.y;
+    const long n = n_u * nq;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const T *b = B + ((long)c * n_u + i / nq) * p;
+        const T *t = Tm + ((long)c * n + i) * p;
+        T acc = b0 ? b0[(long)c * P] : T(0);
+        for (int q = 0; q < p; ++q) acc += b[q] * t[q];
+        S[(long)c * n + i] = acc;
+    }
+}
+
+// dB[c][j][q] = sl * sum_k dS[c][j][k] T[c][j nq + k][q]   (sl: branch output slope, or 1)
+template <typename T>
+__global__ void k_rowdot_dB(const T *dS, const T *Tm, long n_u, long nq, int p, const T *sl, T *dB)
+{
+    const int c = blockIdx.y;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n_u * p; i += (long)gridDim.x * blockDim.x) {
+        const long j = i / p;
+        const int q = (int)(i % p);
+        const T *d = dS + ((long)c * n_u + j) * nq;
+        const T *t = Tm + ((long)c * n_u * nq + j * nq) * p + q;
+        T acc = T(0);
+        for (long k = 0; k < nq; ++k) acc += d[k] * t[k * p];
+        const long o = (long)c * n_u * p + i;
+        dB[o] = sl ? acc * sl[o] : acc;
+    }
+}
+
+// dT[c][j nq + k][q] = sl * dS[c][j][k] B[c][j][q]   (sl: trunk output slope, or 1)
+template <typename T>
+__global__ void k_rowdot_dT(const T *dS, const T *B, long n_u, long nq, int p, const T *sl, T *dT)
+{
+    const int c = blockIdx.y;
+    const long n = n_u * nq * p;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const long r = i / p;   // trunk row j nq + k
+        const int q = (int)(i % p);
+        const T v = dS[(long)c * n_u * nq + r] * B[((long)c * n_u + r / nq) * p + q];
+        const long o = (long)c * n + i;
+        dT[o] = sl ? v * sl[o] : v;
+    }
+}
+
 template <typename T> struct NetBufs {
     std::vector<std::unique_ptr<DevBuf>> act, slope;   // index l = 1..L (output of layer l-1)
 };
@@ -122,14 +169,16 @@ template <typename T> class SimtEngine final : public Engine {
             upload(u_, p.u);
             upload(yq_, p.yq);
             upload(t_, p.t);
+            // trunk rows: the shared queries, or every function's own
+            nt_ = p.kind == HMC_NET_DEEPONET_UNALIGNED ? p.n_u * p.n_y : p.n_y;
             alloc_net(p.branch, p.n_u, brb_);
-            alloc_net(p.trunk, p.n_y, trb_);
+            alloc_net(p.trunk, nt_, trb_);
             const int lat = p.branch.w[p.branch.L];
             S_.alloc(sizeof(T) * C * std::max<long>(p.n_u * p.n_y, 1));
             dB_.alloc(sizeof(T) * C * p.n_u * lat);
-            dT_.alloc(sizeof(T) * C * p.n_y * lat);
+            dT_.alloc(sizeof(T) * C * nt_ * lat);
             long wmax = std::max(max_width(p.branch), max_width(p.trunk));
-            long rows = std::max(p.n_u, p.n_y);
+            long rows = std::max(p.n_u, nt_);
             delta_[0].alloc(sizeof(T) * C * rows * wmax);
             delta_[1].alloc(sizeof(T) * C * rows * wmax);
             n_el_ = p.n_u * p.n_y;
@@ -179,12 +228,18 @@ template <typename T> class SimtEngine final : public Engine {
         } else {
             const NetDesc &bn = p_.branch, &tn = p_.trunk;
             const int lat = bn.w[bn.L];
+            const bool ua = p_.kind == HMC_NET_DEEPONET_UNALIGNED;
             forward(bn, u_.as<T>(), 0, p_.n_u, brb_, s);
-            forward(tn, yq_.as<T>(), 0, p_.n_y, trb_, s);
+            forward(tn, yq_.as<T>(), 0, nt_, trb_, s);
             T *Bm = brb_.act[bn.L]->template as<T>();
             T *Tm = trb_.act[tn.L]->template as<T>();
             T *S = S_.as<T>();
-            {   // S = B T^T + b0
+            const dim3 ua_grid((unsigned)std::min<long>((p_.n_u * p_.n_y * lat + 255) / 256, 4096), C_);
+            if (ua) {   // S_jk = <B_j, T_jk> + b0
+                k_rowdot<T><<<ua_grid, 256, 0, s>>>(Bm, Tm, p_.n_u, p_.n_y, lat,
+                                                    p_.out_bias ? theta + p_.b0_off : nullptr, P, S);
+                HMC_LAUNCH_CK();
+            } else {   // S = B T^T + b0
                 GemmArgs<T> ga{(int)p_.n_u, (int)p_.n_y, lat, Bm, lat, 1, p_.n_u * lat,
                                Tm, 1, lat, p_.n_y * lat};
                 EpiArgs<T> ea{EPI_ACT, S, p_.n_y, 1, p_.n_u * p_.n_y,
@@ -192,7 +247,23 @@ template <typename T> class SimtEngine final : public Engine {
                 launch_gemm(ga, ea, C_, s);
             }
             residual(S, p_.n_u * p_.n_y, t_.as<T>(), nullptr, inv_s2, S, true, s);
-            if (bn.any_sampled && g) {   // dB = dS T (times the branch output slope)
+            if (ua && bn.any_sampled && g) {   // dB_j = sum_k dS_jk T_jk (times the branch output slope)
+                const bool id = bn.act[bn.L - 1] == HMC_ACT_IDENTITY;
+                k_rowdot_dB<T><<<ua_grid, 256, 0, s>>>(S, Tm, p_.n_u, p_.n_y, lat,
+                                                       id ? nullptr : brb_.slope[bn.L]->template as<T>(),
+                                                       dB_.as<T>());
+                HMC_LAUNCH_CK();
+                backward(bn, u_.as<T>(), 0, p_.n_u, brb_, dB_.as<T>(), s);
+            }
+            if (ua && tn.any_sampled && g) {   // dT_jk = dS_jk B_j (times the trunk output slope)
+                const bool id = tn.act[tn.L - 1] == HMC_ACT_IDENTITY;
+                k_rowdot_dT<T><<<ua_grid, 256, 0, s>>>(S, Bm, p_.n_u, p_.n_y, lat,
+                                                       id ? nullptr : trb_.slope[tn.L]->template as<T>(),
+                                                       dT_.as<T>());
+                HMC_LAUNCH_CK();
+                backward(tn, yq_.as<T>(), 0, nt_, trb_, dT_.as<T>(), s);
+            }
+            if (!ua && bn.any_sampled && g) {   // dB = dS T (times the branch output slope)
                 const bool id = bn.act[bn.L - 1] == HMC_ACT_IDENTITY;
                 GemmArgs<T> ga{(int)p_.n_u, lat, (int)p_.n_y, S, p_.n_y, 1, p_.n_u * p_.n_y,
                                Tm, lat, 1, p_.n_y * lat};
@@ -201,7 +272,7 @@ template <typename T> class SimtEngine final : public Engine {
                 launch_gemm(ga, ea, C_, s);
                 backward(bn, u_.as<T>(), 0, p_.n_u, brb_, dB_.as<T>(), s);
             }
-            if (tn.any_sampled && g) {   // dT = dS^T B
+            if (!ua && tn.any_sampled && g) {   // dT = dS^T B
                 const bool id = tn.act[tn.L - 1] == HMC_ACT_IDENTITY;
                 GemmArgs<T> ga{(int)p_.n_y, lat, (int)p_.n_u, S, 1, p_.n_y, p_.n_u * p_.n_y,
                                Bm, lat, 1, p_.n_u * lat};
@@ -212,9 +283,10 @@ template <typename T> class SimtEngine final : public Engine {
             }
         }
         ProfScope ps("simt_finalize", s);
-        k_finalize<T><<<C_, 256, 0, s>>>(part_r2_.as<double>(), p_.kind == HMC_NET_DEEPONET ? part_d_.as<double>() : nullptr,
+        const bool don = p_.kind != HMC_NET_MLP;
+        k_finalize<T><<<C_, 256, 0, s>>>(part_r2_.as<double>(), don ? part_d_.as<double>() : nullptr,
                                          nparts_, 0.5 * inv_s2, q, k, idx_.as<int>(), G_.as<T>(), P,
-                                         p_.kind == HMC_NET_DEEPONET && p_.out_bias ? p_.b0_off : -1,
+                                         don && p_.out_bias ? p_.b0_off : -1,
                                          1.0 / (p_.alpha * p_.alpha), U, g);
         HMC_LAUNCH_CK();
     }
@@ -319,6 +391,7 @@ template <typename T> class SimtEngine final : public Engine {
     DevBuf delta_[2];
     NetBufs<T> netb_, brb_, trb_;
     long n_el_ = 0;
+    long nt_ = 0;   // DeepONet trunk rows
     int nparts_ = 1;
 };
 

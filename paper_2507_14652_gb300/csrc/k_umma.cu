@@ -2845,6 +2845,8 @@ bool don_engine_supports(const Problem &p, std::string *why)
         if (why) *why = m;
         return false;
     };
+    if (p.kind == HMC_NET_DEEPONET_UNALIGNED)
+        return no("DeepONets with per-function query points run on the FP32/FP64 CUDA-core engines");
     if (p.kind != HMC_NET_DEEPONET) return no("not a DeepONet");
     for (const NetDesc *nd : {&p.branch, &p.trunk}) {
         if (nd->L < 2) return no("branch and trunk need a hidden layer");

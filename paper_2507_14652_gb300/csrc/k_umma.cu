@@ -1322,46 +1322,65 @@ __global__ void __launch_bounds__(256) k_first_fwd3(const float *x, int dx, int 
 // A_1[b][n][o] = tanh(sum_d X[n][d] W0[b][o][d] + b0[b][o]) in bf16.  One block per
 // (128-row tile, chain); a thread keeps four adjacent rows o of W0 and b0 in registers
 // and walks a slice of the tile's rows, whose inputs are staged in shared memory, so
-// a warp writes 256 contiguous bytes of a row per store.
-__global__ void __launch_bounds__(256) k_first_fwd(const float *x, int dx, int N, int w, const float *W0,
-                                                   const float *b0, __nv_bfloat16 *A1)
+// a warp writes 256 contiguous bytes of a row per store.  The input width DX is a
+// template parameter: with a runtime width every row paid for eight predicated
+// multiply-adds per output, and the kernel was bound by instruction issue.
+template <int DX>
+__global__ void __launch_bounds__(256) k_first_fwd(const float *x, int N, int w, const float *W0, const float *b0,
+                                                   __nv_bfloat16 *A1)
 {
-    __shared__ float xs[BM * 8];
+    __shared__ float xs[BM * DX];
     pdl_wait();
     pdl_trigger();
     const int b = blockIdx.y, n0 = blockIdx.x * BM;
     const int nr = min(BM, N - n0);
-    for (int i = threadIdx.x; i < nr * dx; i += blockDim.x) xs[i] = x[(long)n0 * dx + i];
+    for (int i = threadIdx.x; i < nr * DX; i += blockDim.x) xs[i] = x[(long)n0 * DX + i];
     __syncthreads();
     const int quads = w / 4;                                   // w is a multiple of 64 here
     const int groups = max(1, (int)blockDim.x / quads);
     const int per = (nr + groups - 1) / groups;
     for (int item = threadIdx.x; item < quads * groups; item += blockDim.x) {
         const int o0 = 4 * (item % quads), r0 = (item / quads) * per, r1 = min(nr, r0 + per);
-        float wr[4][8], bo[4];
+        float wr[4][DX], bo[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             bo[c] = b0[(long)b * w + o0 + c];
 #pragma unroll
-            for (int d = 0; d < 8; ++d) wr[c][d] = d < dx ? W0[((long)b * w + o0 + c) * dx + d] : 0.0f;
+            for (int d = 0; d < DX; ++d) wr[c][d] = W0[((long)b * w + o0 + c) * DX + d];
         }
         __nv_bfloat16 *out = A1 + ((long)b * N + n0) * w + o0;
 #pragma unroll 4
         for (int r = r0; r < r1; ++r) {
-            float xv[8];
+            float xv[DX];
 #pragma unroll
-            for (int d = 0; d < 8; ++d) xv[d] = d < dx ? xs[r * dx + d] : 0.0f;
+            for (int d = 0; d < DX; ++d) xv[d] = xs[r * DX + d];
             float z[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 z[c] = bo[c];
 #pragma unroll
-                for (int d = 0; d < 8; ++d)
-                    if (d < dx) z[c] += xv[d] * wr[c][d];
+                for (int d = 0; d < DX; ++d) z[c] += xv[d] * wr[c][d];
             }
             *reinterpret_cast<uint2 *>(out + (long)r * w) =
                 make_uint2(pack_bf16(tanh_fast(z[0]), tanh_fast(z[1])), pack_bf16(tanh_fast(z[2]), tanh_fast(z[3])));
         }
+    }
+}
+
+// The first-layer forward for an input width dx in 1..8.
+void launch_first_fwd(int dx, dim3 grid, cudaStream_t s, const float *x, int N, int w, const float *W0,
+                      const float *b0, __nv_bfloat16 *A1)
+{
+    switch (dx) {
+    case 1: launch_pdl(k_first_fwd<1>, grid, dim3(256), 0, s, x, N, w, W0, b0, A1); break;
+    case 2: launch_pdl(k_first_fwd<2>, grid, dim3(256), 0, s, x, N, w, W0, b0, A1); break;
+    case 3: launch_pdl(k_first_fwd<3>, grid, dim3(256), 0, s, x, N, w, W0, b0, A1); break;
+    case 4: launch_pdl(k_first_fwd<4>, grid, dim3(256), 0, s, x, N, w, W0, b0, A1); break;
+    case 5: launch_pdl(k_first_fwd<5>, grid, dim3(256), 0, s, x, N, w, W0, b0, A1); break;
+    case 6: launch_pdl(k_first_fwd<6>, grid, dim3(256), 0, s, x, N, w, W0, b0, A1); break;
+    case 7: launch_pdl(k_first_fwd<7>, grid, dim3(256), 0, s, x, N, w, W0, b0, A1); break;
+    case 8: launch_pdl(k_first_fwd<8>, grid, dim3(256), 0, s, x, N, w, W0, b0, A1); break;
+    default: HMC_REQUIRE(false, "first-layer input width %d is not in 1..8", dx);
     }
 }
 
@@ -1749,8 +1768,8 @@ class UmmaEngine final : public Engine {
         {
             dim3 grid((unsigned)ntiles_, C_);
             ProfScope ps("first_fwd", s);
-            launch_pdl(k_first_fwd, grid, dim3(256), 0, s, x_.as<float>(), dx_, (int)N_, w_, W0_.as<float>(),
-                       b0_.as<float>(), A_[1]->as<__nv_bfloat16>());
+            launch_first_fwd(dx_, grid, s, x_.as<float>(), (int)N_, w_, W0_.as<float>(), b0_.as<float>(),
+                             A_[1]->as<__nv_bfloat16>());
         }
         if (use_layer_) {
             layers_persistent(s);
@@ -2599,8 +2618,8 @@ class DonEngine final : public Engine {
         if (!n.gemm_first) {
             dim3 grid((unsigned)n.ntiles, C_);
             ProfScope ps("first_fwd", s);
-            launch_pdl(k_first_fwd, grid, dim3(256), 0, s, n.x32.as<float>(), n.dx, (int)n.R, n.w, n.w0f.as<float>(),
-                       n.bias[0]->as<float>(), n.act[1]->as<__nv_bfloat16>());
+            launch_first_fwd(n.dx, grid, s, n.x32.as<float>(), (int)n.R, n.w, n.w0f.as<float>(),
+                             n.bias[0]->as<float>(), n.act[1]->as<__nv_bfloat16>());
         }
         for (int l = n.gemm_first ? 0 : 1; l < n.L; ++l) {
             Params pp = base();

@@ -833,17 +833,27 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     named_bar_sync(1, 256);
                 }
             } else if (MODE == L_FWD_OUT) {
+                // pass 1: the activations, written back over the accumulator so that pass 2
+                // reads them instead of evaluating tanh again, and the row dot product
                 float fh = 0.0f;
                 tmem_ld32_issue(taddr, rb[0]);
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
                     const int c0 = 32 * ch;
                     tmem_ld_wait(rb[ch & 1]);
-                    if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
+                    if (ch + 1 < NCH) {
+                        if (ch > 0) tmem_st_wait();   // the store of chunk ch - 1 has read its registers
+                        tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
+                    }
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        fh += tanh_fast(__uint_as_float(rb[ch & 1][j]) + sbias[hc0 + c0 + j]) * swo[hc0 + c0 + j];
+                    for (int j = 0; j < 32; ++j) {
+                        const float a = tanh_fast(__uint_as_float(rb[ch & 1][j]) + sbias[hc0 + c0 + j]);
+                        fh += a * swo[hc0 + c0 + j];
+                        rb[ch & 1][j] = __float_as_uint(a);
+                    }
+                    tmem_st32(taddr + c0, rb[ch & 1]);
                 }
+                tmem_st_wait();
                 // the row's dot product: both halves, in a fixed order
                 fsum[h * 128 + row] = fh;
                 named_bar_sync(1, 256);
@@ -872,7 +882,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const float a = tanh_fast(__uint_as_float(rb[ch & 1][j]) + sbias[hc0 + c0 + j]);
+                        const float a = __uint_as_float(rb[ch & 1][j]);
                         dw[j] = d * a;
                         dd[j] = d * swo[hc0 + c0 + j] * (1.0f - a * a);
                     }

@@ -727,10 +727,34 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
             const long wbase = ((long)c * p.N + r0) * p.W + hc0;   // element (r0, hc0) of [c][N][W]
             const long part = ((long)c * p.ntiles + t) * p.W;
             const float yv = (MODE == L_FWD_OUT && valid) ? p.y[m] : 0.0f;
-            float xv[8];
+            // first-layer gradients: the B operand [X | 1] of dW0 = delta_1^T X and db0 = delta_1^T 1
+            // as mma.sync fragments of this warp's 32 rows: column n < dx holds x_n, column dx
+            // the ones, for rows 16 ks + 8 hf + 2 (lane % 4) + {0, 1}
+            uint32_t bx[2][2] = {{0u, 0u}, {0u, 0u}};
+            if (MODE == L_BWD_FIRST) {
+                float vn[5];
 #pragma unroll
-            for (int d = 0; d < 8; ++d)
-                xv[d] = (MODE == L_BWD_FIRST && valid && d < p.dx) ? p.x[(long)m * p.dx + d] : 0.0f;
+                for (int n = 0; n < 5; ++n)
+                    vn[n] = n < p.dx ? (valid ? p.x[(long)m * p.dx + n] : 0.0f) : (n == p.dx ? 1.0f : 0.0f);
+                const int g = lane >> 2, c2 = 2 * (lane & 3);
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+                    for (int hf = 0; hf < 2; ++hf) {
+                        const int r = 16 * ks + 8 * hf + c2;
+                        float v0 = 0.0f, v1 = 0.0f;
+#pragma unroll
+                        for (int n = 0; n < 5; ++n) {
+                            const float a0 = __shfl_sync(0xffffffffu, vn[n], r);
+                            const float a1 = __shfl_sync(0xffffffffu, vn[n], r + 1);
+                            if (g == n) {
+                                v0 = a0;
+                                v1 = a1;
+                            }
+                        }
+                        bx[ks][hf] = pack_bf16(v0, v1);
+                    }
+            }
             // per-chain constants into shared memory
             if (!BWD && c != chain_loaded) {
                 named_bar_sync(1, 256);
@@ -789,7 +813,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
 #pragma unroll
                     for (int j = 0; j < 4; ++j) av[j] = lds128(abuf + ch * L_STG + stg_off(lane, j));
                     __syncwarp();   // every lane has its row: refill the chunk for the next unit
-                    issue_aux(u + 1, ch);
+                    if (MODE != L_BWD_FIRST) issue_aux(u + 1, ch);   // (the first layer stages in it first)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const uint4 uu = av[j];
@@ -808,14 +832,46 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                         for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
                         store_chunk(pk, c0);
                     }
-                    if (MODE == L_BWD_FIRST) {   // first-layer weight and bias gradients: column sums
-                        for (int d = 0; d < p.dx; ++d) {
-                            float tv[32];
+                    if (MODE == L_BWD_FIRST) {
+                        // first-layer weight and bias gradients of this chunk's 32 columns over the
+                        // warp's 32 rows: delta_1 (bf16) goes to the chunk's slope buffer, which
+                        // this warp has read, and mma.sync forms delta_1^T [X | 1]
+                        const uint32_t sb = abuf + ch * L_STG;
+                        {
+                            uint32_t pk[16];
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) tv[j] = dd[j] * xv[d];
-                            red[((1 + d) * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(tv);
+                            for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sb + stg_off(lane, j)),
+                                             "r"(pk[4 * j]), "r"(pk[4 * j + 1]), "r"(pk[4 * j + 2]), "r"(pk[4 * j + 3])
+                                             : "memory");
                         }
-                        red[(0 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dd);
+                        __syncwarp();
+                        float acc[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+                        const int mi = lane >> 3;
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt)        // columns 16 mt .. 16 mt + 15 of the chunk
+#pragma unroll
+                            for (int ks = 0; ks < 2; ++ks) {  // rows 16 ks .. 16 ks + 15 of the warp
+                                uint32_t a[4];
+                                ldmatrix_x4_trans(a, sb + stg_off(16 * ks + (lane & 7) + 8 * (mi >> 1), 2 * mt + (mi & 1)));
+                                mma_m16n8k16_bf16(acc[mt], a, bx[ks][0], bx[ks][1]);
+                            }
+                        __syncwarp();   // the buffer is read: refill it for the next unit
+                        issue_aux(u + 1, ch);
+                        const int g = lane >> 2, c2 = 2 * (lane & 3);
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                            for (int hf = 0; hf < 2; ++hf)
+#pragma unroll
+                                for (int e = 0; e < 2; ++e) {
+                                    const int n = c2 + e, col = hc0 + c0 + 16 * mt + 8 * hf + g;
+                                    const float v = acc[mt][2 * hf + e];
+                                    if (n < p.dx) red[((1 + n) * 4 + q) * LN + col] = v;
+                                    else if (n == p.dx) red[(0 * 4 + q) * LN + col] = v;
+                                }
                     }
                 }
                 if (MODE == L_BWD_FIRST) {

@@ -1452,8 +1452,11 @@ void launch_first_fwd(int dx, dim3 grid, cudaStream_t s, const float *x, int N, 
 
 // Per-entry source of the gradient, decoded by k_finalize_bf16.
 // E_GW: a weight entry gathered by a weight-gradient kernel ([split][b][k] partials);
-// E_PART: anything summed from per-tile column sums, found through a DbDesc.
-enum EntryKind { E_GW = 0, E_PART = 1 };
+// E_PART: anything summed from per-tile column sums, found through a DbDesc;
+// E_HEAVY: an E_PART entry with many partials (per-tile sums), summed by a whole warp.
+enum EntryKind { E_GW = 0, E_PART = 1, E_HEAVY = 2 };
+constexpr int kHeavyPartials = 16;   // E_PART entries with at least this many partials are heavy
+
 
 // Partial sums of one layer's bias gradient: entry (chain b, partial t, unit o) is at
 // p[b * bstride + t * tstride + o], t < n.
@@ -1463,9 +1466,23 @@ struct DbDesc {
     int n;
 };
 
+// Marks the heavy entries in `kind` and returns their indices.
+std::vector<int> mark_heavy(std::vector<int> &kind, const std::vector<int> &desc, const std::vector<DbDesc> &dbd)
+{
+    std::vector<int> heavy;
+    for (size_t j = 0; j < kind.size(); ++j)
+        if (kind[j] == E_PART && dbd[desc[j]].n >= kHeavyPartials) {
+            kind[j] = E_HEAVY;
+            heavy.push_back((int)j);
+        }
+    return heavy;
+}
+
 struct FinalArgs {
     int k, nsplit, nu;               // entries, weight-gradient splits, energy partials per chain
     const int *kind, *desc, *off;    // per entry
+    const int *heavy;                // [nheavy] the E_HEAVY entries
+    int nheavy, nlight;              // heavy entries; blocks of the one-thread-per-entry part
     const double *u_part;            // [b][nu]
     const float *gw_part;            // [split][b][k]
     long gw_split;
@@ -1473,8 +1490,9 @@ struct FinalArgs {
     double half_inv_s2, inv_a2;
 };
 
-// grid (gradient blocks + 1, C): blocks 0..nb-1 gather one entry per thread, the last
-// block of each chain computes U (fixed-order sums).
+// grid (nlight + ceil(nheavy / 8) + 1, C): blocks 0..nlight-1 gather one entry per
+// thread, the next ones one heavy entry per warp (its partials split over the lanes,
+// then a fixed butterfly), and the last block of each chain computes U (fixed-order sums).
 __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float *q, double *U, float *g)
 {
     __shared__ double sm[2][8];
@@ -1482,7 +1500,9 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
     pdl_trigger();
     const int b = blockIdx.y;
     if (blockIdx.x == gridDim.x - 1) {   // U = likelihood + prior, block-parallel in a fixed order
-        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, lik = 0.0;
+        // |q|^2: eight squares at a time in FP32 (a bounded partial), accumulated in FP64;
+        // this block is one SM's work, and GB300's FP64 pipe is narrow
+        double pr = 0.0, lik = 0.0;
         for (int j0 = threadIdx.x; j0 < a.k; j0 += 8 * blockDim.x) {   // eight loads in flight
             float v[8];
 #pragma unroll
@@ -1490,10 +1510,9 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
                 const int j = j0 + u * blockDim.x;
                 v[u] = j < a.k ? __ldg(q + (long)b * a.k + j) : 0.0f;
             }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u] += (double)v[u] * (double)v[u];
+            pr += (double)(((v[0] * v[0] + v[1] * v[1]) + (v[2] * v[2] + v[3] * v[3])) +
+                           ((v[4] * v[4] + v[5] * v[5]) + (v[6] * v[6] + v[7] * v[7])));
         }
-        double pr = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
         for (int i = threadIdx.x; i < a.nu; i += blockDim.x) lik += a.u_part[(long)b * a.nu + i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -1515,8 +1534,23 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
         }
         return;
     }
+    if (!g) return;
+    if ((int)blockIdx.x >= a.nlight) {   // heavy entries: one warp each
+        const int h = ((int)blockIdx.x - a.nlight) * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+        const int lane = threadIdx.x & 31;
+        if (h >= a.nheavy) return;
+        const int j = a.heavy[h];
+        const DbDesc d = a.db[a.desc[j]];
+        const float *dp = d.p + (long)b * d.bstride + a.off[j];
+        float s = 0.0f;
+        for (int t = lane; t < d.n; t += 32) s += __ldg(dp + (long)t * d.tstride);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) g[(long)b * a.k + j] = s + q[(long)b * a.k + j] * (float)a.inv_a2;
+        return;
+    }
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.k || !g) return;
+    if (j >= a.k || a.kind[j] == E_HEAVY) return;
     const float qj = q[(long)b * a.k + j];
     const float *dp;
     long stride;
@@ -1799,6 +1833,13 @@ class UmmaEngine final : public Engine {
         dbd[L_ + 1] = DbDesc{dbout_part_.as<float>(), ntiles_, 1, ntiles_};
         db_desc_.alloc(sizeof(DbDesc) * dbd.size());
         HMC_CK(cudaMemcpy(db_desc_.ptr, dbd.data(), sizeof(DbDesc) * dbd.size(), cudaMemcpyHostToDevice));
+        {   // entries with per-tile partials are summed a warp each
+            const std::vector<int> heavy = mark_heavy(kind_h_, layer_h_, dbd);
+            nheavy_ = (int)heavy.size();
+            HMC_CK(cudaMemcpy(kind_.ptr, kind_h_.data(), sizeof(int) * kind_h_.size(), cudaMemcpyHostToDevice));
+            heavy_.alloc(sizeof(int) * std::max<size_t>(heavy.size(), 1));
+            if (nheavy_) HMC_CK(cudaMemcpy(heavy_.ptr, heavy.data(), sizeof(int) * heavy.size(), cudaMemcpyHostToDevice));
+        }
     }
 
     std::string tuning() const override { return tuning_; }
@@ -1908,9 +1949,12 @@ class UmmaEngine final : public Engine {
         fa.db = db_desc_.as<const DbDesc>();
         fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
         fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
+        fa.heavy = heavy_.as<int>();
+        fa.nheavy = nheavy_;
+        fa.nlight = (int)((k_ + 255) / 256);
         {
             ProfScope ps("finalize", s);
-            dim3 grid((unsigned)((k_ + 255) / 256 + 1), C_);
+            dim3 grid((unsigned)(fa.nlight + (nheavy_ + 7) / 8 + 1), C_);
             launch_pdl(k_finalize_bf16, grid, dim3(256), 0, s, fa, q, U, g);
             HMC_LAUNCH_CK();
         }
@@ -2220,6 +2264,8 @@ class UmmaEngine final : public Engine {
         up(off_, off);
         up(erow_, erow);
         up(ecol_, ecol);
+        kind_h_ = kind;
+        layer_h_ = layer;
         std::vector<int> epack(k_);
         for (long j = 0; j < k_; ++j) epack[j] = (erow[j] << 16) | ecol[j];
         up(epack_, epack);
@@ -2236,7 +2282,9 @@ class UmmaEngine final : public Engine {
     long N_ = 0, k_ = 0;
     int *err_ = nullptr;
     DevBuf x_, y_, W0_, b0_, wout_, bout_, u_part_, dbout_part_, dwout_part_, dw0_part_, db_desc_, gw_part_;
-    DevBuf kind_, layer_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_;
+    DevBuf kind_, layer_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_, heavy_;
+    std::vector<int> kind_h_, layer_h_;
+    int nheavy_ = 0;
     std::vector<std::unique_ptr<DevBuf>> Wh_, Wl_, bh_, A_, D_, db_part_, dbw_part_, rowptr_;
     std::vector<int> layer_entries_, bias_entries_;
     CUtensorMap A_row_[MAXL], A_atom_[MAXL], W_fwd_[MAXL], W_atom_[MAXL], W_fwd_lo_[MAXL], W_atom_lo_[MAXL];
@@ -2468,9 +2516,12 @@ class DonEngine final : public Engine {
         fa.db = db_desc_.as<const DbDesc>();
         fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
         fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
+        fa.heavy = heavy_.as<int>();
+        fa.nheavy = nheavy_;
+        fa.nlight = (int)((k_ + 255) / 256);
         {
             ProfScope ps("finalize", s);
-            dim3 grid((unsigned)((k_ + 255) / 256 + 1), C_);
+            dim3 grid((unsigned)(fa.nlight + (nheavy_ + 7) / 8 + 1), C_);
             launch_pdl(k_finalize_bf16, grid, dim3(256), 0, s, fa, q, U, g);
         }
     }
@@ -2863,6 +2914,12 @@ class DonEngine final : public Engine {
             alloc_t(d, sizeof(int) * std::max<size_t>(v.size(), 1));
             if (!v.empty()) HMC_CK(cudaMemcpy(d.ptr, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
         };
+        {   // entries with per-tile partials are summed a warp each
+            const std::vector<int> heavy = mark_heavy(kind, desc, dbd);
+            nheavy_ = (int)heavy.size();
+            heavy_.alloc(sizeof(int) * std::max<size_t>(heavy.size(), 1));
+            if (nheavy_) HMC_CK(cudaMemcpy(heavy_.ptr, heavy.data(), sizeof(int) * heavy.size(), cudaMemcpyHostToDevice));
+        }
         up(kind_, kind);
         up(desc_, desc);
         up(off_, off);
@@ -2888,7 +2945,8 @@ class DonEngine final : public Engine {
     int *err_ = nullptr;
     DonNet br_, tr_;
     DevBuf yt_, ds_, u_part_, db0_part_, b0v_, gw_part_, db_desc_;
-    DevBuf kind_, desc_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_;
+    DevBuf kind_, desc_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_, heavy_;
+    int nheavy_ = 0;
     CUtensorMap ds_row_, ds_atom_, b_col_, b_hi_e_, b_lo_e_;
     int es_ = 256, nut_e_ = 1, ntn_e_ = 1;
     DevBuf u_acc_;

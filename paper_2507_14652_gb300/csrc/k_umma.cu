@@ -916,8 +916,8 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                 const float fo = p.bout[c] + (fsum[row] + fsum[128 + row]);
                 const float r = valid ? fo - yv : 0.0f;
                 const float d = r * p.inv_s2;
-                if (h == 0) {
-                    double r2 = (double)r * (double)r;
+                if (h == 0) {   // the warp's 32 squared residuals: an FP32 partial, then FP64
+                    float r2 = r * r;
                     float ds = d;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -925,7 +925,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                         ds += __shfl_xor_sync(0xffffffffu, ds, o);
                     }
                     if (lane == 0) {
-                        dred[q] = r2;
+                        dred[q] = (double)r2;
                         fred[q] = ds;
                     }
                 }

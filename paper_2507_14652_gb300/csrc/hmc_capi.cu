@@ -434,7 +434,10 @@ struct hmc_handle_s {
     long k_total = 0, P_total = 0, S_total = 0;
     DevBuf q_cur, g_cur, q_prop, p, g_prop, U_cur, U_prop, K0p, K1p, acc_int, segs, state, scratch;
     int traj_nblk = 1;   // blocks per chain in the trajectory kernels
+    // staging buffers for host arguments, kept across calls (allocating and freeing device
+    // memory on every call would synchronise the device twice per call)
     std::vector<std::unique_ptr<DevBuf>> stage;
+    size_t stage_used = 0;
     // one trajectory as an executable graph, reused while (eps, L, seed) stay the same
     cudaGraphExec_t traj_exec = nullptr;
     double traj_eps = 0.0;
@@ -625,8 +628,10 @@ void *dev_view(hmc_handle h, const void *user, size_t bytes, bool in, bool *stag
     *staged = false;
     if (!user) return nullptr;
     if (is_device_ptr(user)) return const_cast<void *>(user);
-    h->stage.emplace_back(new DevBuf(bytes));
-    void *d = h->stage.back()->ptr;
+    if (h->stage_used == h->stage.size()) h->stage.emplace_back(new DevBuf());
+    std::unique_ptr<DevBuf> &buf = h->stage[h->stage_used++];
+    if (buf->n < bytes) buf.reset(new DevBuf(bytes));
+    void *d = buf->ptr;
     if (in) HMC_CK(cudaMemcpyAsync(d, user, bytes, cudaMemcpyHostToDevice, h->stream));
     *staged = true;
     return d;
@@ -1123,7 +1128,7 @@ hmc_status hmc_predict(hmc_handle h, const void *samples, long n_samples, const 
             in.yq = fetch(inputs->yq, in.n_y * p.dy, "inputs.yq");
             if (rel_l2) in.targets = fetch(inputs->t, nout, "inputs.t (targets for rel_l2)");
         }
-        h->stage.clear();
+        h->stage_used = 0;
         join_in(h);
         bool ss, sm, sv;
         const void *ds = dev_view(h, samples, h->elem * (size_t)n_samples * p.k, true, &ss);
@@ -1146,7 +1151,7 @@ hmc_status hmc_energy_grad(hmc_handle h, const void *q, double *U, void *grad)
     g_err.clear();
     return guarded([&]() -> hmc_status {
         HMC_REQUIRE(h && q && U, "NULL argument");
-        h->stage.clear();
+        h->stage_used = 0;
         join_in(h);
         bool sq, su, sg;
         const size_t sb = h->elem * (size_t)h->S_total;
@@ -1175,7 +1180,7 @@ hmc_status hmc_leapfrog(hmc_handle h, void *q, void *p, double eps, int L)
     return guarded([&]() -> hmc_status {
         HMC_REQUIRE(h && q && p, "NULL argument");
         HMC_REQUIRE(L >= 0 && std::isfinite(eps), "L must be >= 0 and eps finite");
-        h->stage.clear();
+        h->stage_used = 0;
         join_in(h);
         const size_t sb = h->elem * (size_t)h->S_total;
         bool sq, sp;
@@ -1212,7 +1217,7 @@ hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_sa
         HMC_REQUIRE(h && q0, "NULL argument");
         HMC_REQUIRE(L >= 1 && n_samples >= 0 && first_traj >= 0 && std::isfinite(eps) && eps > 0,
                     "need L >= 1, eps > 0, n_samples >= 0, first_traj >= 0");
-        h->stage.clear();
+        h->stage_used = 0;
         join_in(h);
         const size_t sb = h->elem * (size_t)h->S_total;
         const long nseg = (long)h->nprob * h->C;
@@ -1331,7 +1336,7 @@ hmc_status hmc_destroy(hmc_handle h)
         cudaStreamSynchronize(h->stream);
         h->engines.clear();
         h->probs.clear();
-        h->stage.clear();
+        h->stage_used = 0;
         cudaStream_t s = h->stream;
         cudaEvent_t a = h->ev_in, b = h->ev_out;
         delete h;
@@ -1365,7 +1370,7 @@ hmc_status hmc_diag_metropolis_energy(hmc_handle h, const void *q, double *U)
     g_err.clear();
     return guarded([&]() -> hmc_status {
         HMC_REQUIRE(h && q && U, "NULL argument");
-        h->stage.clear();
+        h->stage_used = 0;
         join_in(h);
         bool sq, su;
         const size_t sb = h->elem * (size_t)h->S_total;

@@ -125,6 +125,9 @@ HMC_API hmc_status hmc_create(hmc_handle *out, const hmc_net_spec *spec, const h
  * launches cover every problem at once.  State vectors of a batch handle are
  * packed per problem: q = [problem][chain][k_problem]; U, accepted and dH are
  * [problem][chain] per trajectory.  Momenta of problem p use Philox stream p.
+ * In an HMC_PREC_BF16 batch, a problem whose network the tensor-core kernels do not
+ * cover (a hidden width that is not a multiple of 64, say) runs on the FP32 CUDA-core
+ * engine instead; its positions are float like the others'.
  */
 HMC_API hmc_status hmc_create_batch(hmc_handle *out, int n_problems, const hmc_net_spec *specs,
                             const hmc_data *data, const double *prior_sigma,

@@ -798,7 +798,10 @@ template <typename T> void enqueue_trajectory(hmc_handle h, double eps, int L, u
     HMC_LAUNCH_CK();
 }
 
-Engine *make_engine(Problem &p, int prec, int C)
+// in_batch: inside a BF16 batch, a network the tensor-core kernels do not cover (hidden
+// widths that are not multiples of 64, say) runs on the FP32 CUDA-core engine, which
+// keeps the batch's float positions and is the more accurate of the two.
+Engine *make_engine(Problem &p, int prec, int C, bool in_batch = false)
 {
     if (prec == HMC_PREC_FP64) return make_simt_engine_f64(p, C);
     if (prec == HMC_PREC_FP32) return make_simt_engine_f32(p, C);
@@ -806,6 +809,7 @@ Engine *make_engine(Problem &p, int prec, int C)
         std::string why;
         const bool don = p.kind != HMC_NET_MLP;
         if (!(don ? don_engine_supports(p, &why) : umma_engine_supports(p, &why))) {
+            if (in_batch) return make_simt_engine_f32(p, C);
             set_error("BF16 tensor-core path does not support this network: %s", why.c_str());
             throw Fail{HMC_ERR_UNSUPPORTED};
         }
@@ -897,7 +901,7 @@ hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, co
         for (int i = 0; i < nprob; ++i) {
             h->probs.push_back(build_problem(specs[i], data[i], alpha[i], sigma[i], masks[i], frozen[i], C));
             Problem &p = *h->probs.back();
-            Engine *e = make_engine(p, prec, C);
+            Engine *e = make_engine(p, prec, C, nprob > 1);
             h->engines.emplace_back(e);
             p.engine = e;
             h->qoff.push_back(h->k_total * C);

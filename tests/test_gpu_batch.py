@@ -86,11 +86,24 @@ def test_batch_bf16_energy_grad_parity():
             assert ok, (i, p.notes, c, r2, rinf)
 
 
-def test_batch_bf16_rejects_width_32():
-    # the tensor-core path needs hidden widths that are multiples of 64
-    probs = _problems(widths=(32,))
+def test_batch_bf16_runs_width_32_on_the_fp32_engine():
+    # the tensor-core path needs hidden widths that are multiples of 64: inside a BF16 batch
+    # the width-32 problems run on the FP32 CUDA-core engine, to FP32 accuracy
+    probs = _problems(widths=(32, 128))
+    assert {p.notes["width"] for p in probs} == {32, 128}
+    qs, U, gs, _ = _energy_grad(probs, hmc.PREC_BF16)
+    C = probs[0].chains
+    for i, (p, q, g) in enumerate(zip(probs, qs, gs)):
+        Ur, gr = oracle.Oracle(p).energy_grad_batch(q)
+        tol = 1e-5 if p.notes["width"] == 32 else 2e-2
+        for c in range(C):
+            assert abs(U[i * C + c] - Ur[c]) <= tol * abs(Ur[c]), (i, c, U[i * C + c], Ur[c])
+            ok, r2, rinf = grad_ok_bf16(g[c], gr[c], tol)
+            assert ok, (i, p.notes, c, r2, rinf)
+    # a single-problem BF16 handle still refuses a network the tensor cores do not cover
+    p = probs[[q.notes["width"] for q in probs].index(32)]
     with pytest.raises(hmc.HmcError):
-        _batch(probs, hmc.PREC_BF16)
+        hmc.Sampler.mlp(p.net.widths, p.x, p.y, p.mask, p.frozen, p.chains, prec=hmc.PREC_BF16)
 
 
 def test_batch_sample_parity_fp64():

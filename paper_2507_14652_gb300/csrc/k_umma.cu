@@ -929,24 +929,67 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                         fred[q] = ds;
                     }
                 }
+                // output-weight gradient sums d^T A over the warp's 32 rows by mma.sync: the B
+                // operand is the column d (rows 16 ks + 8 hf + 2 (lane % 4) + {0, 1}, column 0)
+                uint32_t bd[2][2];
+                {
+                    const int g = lane >> 2, c2 = 2 * (lane & 3);
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+                        for (int hf = 0; hf < 2; ++hf) {
+                            const int rr = 16 * ks + 8 * hf + c2;
+                            const float d0 = __shfl_sync(0xffffffffu, d, rr);
+                            const float d1 = __shfl_sync(0xffffffffu, d, rr + 1);
+                            bd[ks][hf] = g == 0 ? pack_bf16(d0, d1) : 0u;
+                        }
+                }
                 tmem_ld32_issue(taddr, rb[0]);
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
                     const int c0 = 32 * ch;
-                    float dw[32], dd[32];
                     tmem_ld_wait(rb[ch & 1]);
                     if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
+                    {   // A (bf16) through the staging buffer into mma.sync fragments
+                        const uint32_t sb = smem_u32(stg);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float a = __uint_as_float(rb[ch & 1][j]);
-                        dw[j] = d * a;
-                        dd[j] = d * swo[hc0 + c0 + j] * (1.0f - a * a);
+                        for (int j = 0; j < 4; ++j) {
+                            const uint32_t *w = &rb[ch & 1][8 * j];
+                            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sb + stg_off(lane, j)),
+                                         "r"(pack_bf16(__uint_as_float(w[0]), __uint_as_float(w[1]))),
+                                         "r"(pack_bf16(__uint_as_float(w[2]), __uint_as_float(w[3]))),
+                                         "r"(pack_bf16(__uint_as_float(w[4]), __uint_as_float(w[5]))),
+                                         "r"(pack_bf16(__uint_as_float(w[6]), __uint_as_float(w[7])))
+                                         : "memory");
+                        }
+                        __syncwarp();
+                        float acc[2][4] = {{0.0f, 0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f, 0.0f}};
+                        const int mi = lane >> 3;
+#pragma unroll
+                        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                            for (int ks = 0; ks < 2; ++ks) {
+                                uint32_t a4[4];
+                                ldmatrix_x4_trans(a4, sb + stg_off(16 * ks + (lane & 7) + 8 * (mi >> 1), 2 * mt + (mi & 1)));
+                                mma_m16n8k16_bf16(acc[mt], a4, bd[ks][0], bd[ks][1]);
+                            }
+                        __syncwarp();   // the staging buffer is read: the deltas go through it next
+                        if ((lane & 3) == 0) {   // column 0 of D: lanes 4 g hold columns g and g + 8
+#pragma unroll
+                            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                                for (int hf = 0; hf < 2; ++hf)
+                                    red[(0 * 4 + q) * LN + hc0 + c0 + 16 * mt + 8 * hf + (lane >> 2)] = acc[mt][2 * hf];
+                        }
                     }
                     uint32_t pk[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
+                    for (int j = 0; j < 16; ++j) {
+                        const float a0 = __uint_as_float(rb[ch & 1][2 * j]), a1 = __uint_as_float(rb[ch & 1][2 * j + 1]);
+                        pk[j] = pack_bf16(d * swo[hc0 + c0 + 2 * j] * (1.0f - a0 * a0),
+                                          d * swo[hc0 + c0 + 2 * j + 1] * (1.0f - a1 * a1));
+                    }
                     store_chunk(pk, c0);
-                    red[(0 * 4 + q) * LN + hc0 + c0 + lane] = reduce_scatter32(dw);
                 }
                 named_bar_sync(1, 256);
                 if (tile_ok) {

@@ -62,7 +62,8 @@ typedef enum { HMC_ACT_IDENTITY = 0, HMC_ACT_TANH = 1, HMC_ACT_SIN = 2 } hmc_act
 
 /* Arithmetic of the network evaluation.  FP64 and FP32 run plain CUDA-core
  * kernels.  BF16 runs the wide layers on tcgen05 tensor cores (bf16 operands,
- * fp32 accumulation) with fp32 positions/momenta and fp64 energy sums. */
+ * fp32 accumulation) with fp32 positions/momenta and fp64 energy sums.
+ * HMC_PREC_TF32 is reserved: creating a handle with it returns HMC_ERR_UNSUPPORTED. */
 typedef enum { HMC_PREC_FP64 = 0, HMC_PREC_FP32 = 1, HMC_PREC_TF32 = 2, HMC_PREC_BF16 = 3 } hmc_prec;
 
 /* HMC_NET_DEEPONET: n_u input functions evaluated at n_y query points shared by all

@@ -95,7 +95,10 @@ typedef struct {
 /* Training set, FP64, host or device.  MLP: x[n][dx], y[n][dout].
  * DeepONet (aligned): u[n_u][du] input functions, yq[n_y][dy] query points
  * shared by all functions, t[n_u][n_y] targets.  Unaligned DeepONet: yq[n_u][n_y][dy],
- * the n_y query points of each function.  Unused fields are ignored. */
+ * the n_y query points of each function.  Unused fields are ignored.
+ * An empty training set (n = 0, or n_u = 0 or n_y = 0) is allowed: the likelihood is 1
+ * and U(q) = |q|^2 / (2 alpha^2), so the sampler draws from the prior (Sec. 2.2); the
+ * array pointers may then be NULL.  Split handles need at least n_splits data rows. */
 typedef struct {
     const double *x; long n; int dx;
     const double *y;

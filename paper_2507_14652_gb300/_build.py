@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libhmc.so")
-SOURCES = ["hmc_capi.cu", "k_simt.cu", "k_umma.cu", "k_sens.cu", "k_predict.cu"]
+SOURCES = ["hmc_capi.cu", "k_simt.cu", "k_umma.cu", "k_sens.cu", "k_predict.cu", "k_prior.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -803,6 +803,13 @@ template <typename T> void enqueue_trajectory(hmc_handle h, double eps, int L, u
 // keeps the batch's float positions and is the more accurate of the two.
 Engine *make_engine(Problem &p, int prec, int C, bool in_batch = false)
 {
+    if (prec == HMC_PREC_TF32) {
+        set_error("HMC_PREC_TF32 is not implemented");
+        throw Fail{HMC_ERR_UNSUPPORTED};
+    }
+    // no data terms: the potential is the prior alone, in every precision
+    const bool no_data = p.kind == HMC_NET_MLP ? p.n == 0 : (p.n_u == 0 || p.n_y == 0);
+    if (no_data) return make_prior_engine(p, prec, C);
     if (prec == HMC_PREC_FP64) return make_simt_engine_f64(p, C);
     if (prec == HMC_PREC_FP32) return make_simt_engine_f32(p, C);
     if (prec == HMC_PREC_BF16) {
@@ -815,8 +822,8 @@ Engine *make_engine(Problem &p, int prec, int C, bool in_batch = false)
         }
         return don ? make_don_engine_bf16(p, C) : make_umma_engine_bf16(p, C);
     }
-    set_error("HMC_PREC_TF32 is not implemented");
-    throw Fail{HMC_ERR_UNSUPPORTED};
+    set_error("unknown precision %d", prec);
+    throw Fail{HMC_ERR_ARG};
 }
 
 // Data batch m of M (rows [floor(m R / M), floor((m + 1) R / M)) of the R data rows:

@@ -123,6 +123,8 @@ Engine *make_simt_engine_f32(Problem &p, int C);
 Engine *make_umma_engine_bf16(Problem &p, int C);
 bool umma_engine_supports(const Problem &p, std::string *why);
 Engine *make_don_engine_bf16(Problem &p, int C);
+// A problem without data terms: U = |q|^2 / (2 alpha^2) in any precision.
+Engine *make_prior_engine(const Problem &p, int prec, int C);
 bool don_engine_supports(const Problem &p, std::string *why);
 
 // Sensitivities and truncation (k_sens.cu): a network and its inputs, no subset.

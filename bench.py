@@ -257,6 +257,17 @@ def main():
                     "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops_sustained"], "traffic": None,
                     "peak_source": peak_src + " (bf16_tflops_sustained)"}
         roof["kernel_ms"] = t_ms
+    # the same arithmetic for every kernel kind of the evaluation (context for the dominant one)
+    roof_all = {}
+    for name, (t_k, _n) in prof.items():
+        if name not in alg:
+            continue
+        fl, by = alg[name]
+        t_hbm = by / (peaks["hbm_gbs"] * 1e9)
+        t_tc = fl / (peaks["bf16_tflops_sustained"] * 1e12)
+        frac = max(t_hbm, t_tc) / (t_k / 1e3)
+        roof_all[name] = {"bound": "hbm" if t_hbm >= t_tc else "tensor", "kernel_ms": t_k,
+                          "floor_ms": 1e3 * max(t_hbm, t_tc), "frac": frac, "traffic": _traffic(name)}
 
     # end to end through the public C ABI with pinned host buffers: every step copies
     # the chain state in and the step's sample, accept flags and dH out
@@ -380,7 +391,7 @@ def main():
                 "accept_rate": float(acc_np.mean()), "abs_dH_mean": float(np.nanmean(np.abs(dH_np))),
                 "abs_dH_median": float(np.nanmedian(np.abs(dH_np))),
                 "gpu_launches": gpu_launches, "kernels_per_trajectory": graph_k,
-                "roofline": roof, "kernel_ms": {k: v[0] for k, v in prof.items()},
+                "roofline": roof, "roofline_by_kernel": roof_all, "kernel_ms": {k: v[0] for k, v in prof.items()},
                 "tuning": s.tuning().strip(),
                 "kernel_launches_per_eval": {k: v[1] for k, v in prof.items()},
                 "e2e": e2e, "cpu_baseline": cpu, "ess": ess, "split_hmc": split, "around_the_sampler": around,

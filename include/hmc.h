@@ -92,7 +92,7 @@ typedef struct {
     int prec;                /* hmc_prec */
 } hmc_net_spec;
 
-/* Training set, FP64, host or device.  MLP: x[n][dx], y[n][dout].
+/* Training set, FP64 (or FP32, see dtype), host or device.  MLP: x[n][dx], y[n][dout].
  * DeepONet (aligned): u[n_u][du] input functions, yq[n_y][dy] query points
  * shared by all functions, t[n_u][n_y] targets.  Unaligned DeepONet: yq[n_u][n_y][dy],
  * the n_y query points of each function.  Unused fields are ignored.
@@ -100,12 +100,17 @@ typedef struct {
  * and U(q) = |q|^2 / (2 alpha^2), so the sampler draws from the prior (Sec. 2.2); the
  * array pointers may then be NULL.  Split handles need at least n_splits data rows. */
 typedef struct {
-    const double *x; long n; int dx;
-    const double *y;
-    const double *u; long n_u; int du;
-    const double *yq; long n_y; int dy;
-    const double *t;
+    const void *x; long n; int dx;
+    const void *y;
+    const void *u; long n_u; int du;
+    const void *yq; long n_y; int dy;
+    const void *t;
+    int dtype;               /* hmc_data_dtype of every array above (0, the zero value: FP64) */
 } hmc_data;
+
+/* Element type of the training-set arrays.  The handle converts them once, at creation,
+ * to the engine's working precision, so the type has no cost on the sampling path. */
+typedef enum { HMC_DATA_F64 = 0, HMC_DATA_F32 = 1 } hmc_data_dtype;
 
 /*
  * Create a sampler for one problem (Algorithm 2 after its subset is fixed).

@@ -58,7 +58,11 @@ class NetSpec(ct.Structure):
 class Data(ct.Structure):
     _fields_ = [("x", ct.c_void_p), ("n", ct.c_long), ("dx", ct.c_int), ("y", ct.c_void_p),
                 ("u", ct.c_void_p), ("n_u", ct.c_long), ("du", ct.c_int),
-                ("yq", ct.c_void_p), ("n_y", ct.c_long), ("dy", ct.c_int), ("t", ct.c_void_p)]
+                ("yq", ct.c_void_p), ("n_y", ct.c_long), ("dy", ct.c_int), ("t", ct.c_void_p),
+                ("dtype", ct.c_int)]
+
+
+DATA_F64, DATA_F32 = 0, 1
 
 
 _lib = None
@@ -157,6 +161,21 @@ def _f64(a):
     return a.detach().to(torch.float64).contiguous()
 
 
+def _is_f32(a):
+    return str(getattr(a, "dtype", "")) in ("float32", "torch.float32")
+
+
+def _training_arrays(*arrays):
+    """The training set as passed to the library: float32 when every array is float32
+    (numpy or torch, handed over without a copy to float64), else float64."""
+    if all(_is_f32(a) for a in arrays):
+        out = []
+        for a in arrays:
+            out.append(np.ascontiguousarray(a) if isinstance(a, np.ndarray) else a.detach().contiguous())
+        return out, DATA_F32
+    return [_f64(a) for a in arrays], DATA_F64
+
+
 def _stream_ptr(stream):
     if stream is None:
         import torch
@@ -199,9 +218,9 @@ class Sampler:
         spec.kind = NET_MLP
         spec.net = mlp_spec(widths, act, bias)
         spec.prec = prec
-        x, y = _f64(x), _f64(y)
+        (x, y), dt = _training_arrays(x, y)
         d = Data()
-        d.x, d.n, d.dx, d.y = _ptr(x), x.shape[0], x.shape[1], _ptr(y)
+        d.x, d.n, d.dx, d.y, d.dtype = _ptr(x), x.shape[0], x.shape[1], _ptr(y), dt
         return cls(spec, d, [x, y], prior_sigma, noise_sigma, mask, frozen, chains, stream, n_splits)
 
     @classmethod
@@ -216,8 +235,9 @@ class Sampler:
         spec.trunk = mlp_spec(trunk, trunk_act, trunk_bias)
         spec.deeponet_out_bias = 1 if out_bias else 0
         spec.prec = prec
-        u, yq, t = _f64(u), _f64(yq), _f64(t)
+        (u, yq, t), dt = _training_arrays(u, yq, t)
         d = Data()
+        d.dtype = dt
         d.u, d.n_u, d.du = _ptr(u), u.shape[0], u.shape[1]
         d.yq, d.n_y, d.dy = _ptr(yq), yq.shape[-2], yq.shape[-1]
         d.t = _ptr(t)

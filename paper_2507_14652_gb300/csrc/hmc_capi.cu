@@ -487,6 +487,15 @@ template <typename V> std::vector<V> fetch(const V *src, long n, const char *wha
     return v;
 }
 
+// A training-set array of element type `dtype` (hmc_data_dtype), host or device, as doubles.
+std::vector<double> fetch_data(const void *src, long n, int dtype, const char *what)
+{
+    HMC_REQUIRE(dtype == HMC_DATA_F64 || dtype == HMC_DATA_F32, "%s: unknown dtype %d", what, dtype);
+    if (dtype == HMC_DATA_F64) return fetch(static_cast<const double *>(src), n, what);
+    const std::vector<float> f = fetch(static_cast<const float *>(src), n, what);
+    return std::vector<double>(f.begin(), f.end());
+}
+
 std::unique_ptr<Problem> build_problem(const hmc_net_spec &spec, const hmc_data &d, double alpha, double sigma,
                                        const unsigned char *mask, const double *frozen, int C)
 {
@@ -531,8 +540,8 @@ std::unique_ptr<Problem> build_problem(const hmc_net_spec &spec, const hmc_data 
         p->n = d.n;
         p->dx = d.dx;
         p->dout = spec.net.widths[spec.net.n_layers];
-        p->x = fetch(d.x, d.n * d.dx, "data.x");
-        p->y = fetch(d.y, d.n * p->dout, "data.y");
+        p->x = fetch_data(d.x, d.n * d.dx, d.dtype, "data.x");
+        p->y = fetch_data(d.y, d.n * p->dout, d.dtype, "data.y");
     } else {
         build_net_desc(p->branch, spec.branch, 0, p->idx);
         build_net_desc(p->trunk, spec.trunk, p->branch.P, p->idx);
@@ -542,10 +551,10 @@ std::unique_ptr<Problem> build_problem(const hmc_net_spec &spec, const hmc_data 
         p->n_y = d.n_y;
         p->du = d.du;
         p->dy = d.dy;
-        p->u = fetch(d.u, d.n_u * d.du, "data.u");
+        p->u = fetch_data(d.u, d.n_u * d.du, d.dtype, "data.u");
         const long nq = spec.kind == HMC_NET_DEEPONET_UNALIGNED ? d.n_u * d.n_y : d.n_y;
-        p->yq = fetch(d.yq, nq * d.dy, "data.yq");
-        p->t = fetch(d.t, d.n_u * d.n_y, "data.t");
+        p->yq = fetch_data(d.yq, nq * d.dy, d.dtype, "data.yq");
+        p->t = fetch_data(d.t, d.n_u * d.n_y, d.dtype, "data.t");
     }
     return p;
 }
@@ -1021,7 +1030,7 @@ hmc_status hmc_sensitivity(const hmc_net_spec *spec, const hmc_data *data, const
             build_net_desc(pr.net, spec->net, 0, none);
             pr.P = pr.net.P;
             pr.n = data->n;
-            pr.x = fetch(data->x, data->n * data->dx, "data.x");
+            pr.x = fetch_data(data->x, data->n * data->dx, data->dtype, "data.x");
         } else {
             check_mlp_spec(spec->branch, "branch");
             check_mlp_spec(spec->trunk, "trunk");
@@ -1036,8 +1045,8 @@ hmc_status hmc_sensitivity(const hmc_net_spec *spec, const hmc_data *data, const
             pr.P = pr.branch.P + pr.trunk.P + pr.out_bias;
             pr.n_u = data->n_u;
             pr.n_y = data->n_y;
-            pr.u = fetch(data->u, data->n_u * data->du, "data.u");
-            pr.yq = fetch(data->yq, data->n_y * data->dy, "data.yq");
+            pr.u = fetch_data(data->u, data->n_u * data->du, data->dtype, "data.u");
+            pr.yq = fetch_data(data->yq, data->n_y * data->dy, data->dtype, "data.yq");
         }
         HMC_REQUIRE(pr.P < (1L << 31), "too many parameters (%ld)", pr.P);
         cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
@@ -1127,17 +1136,17 @@ hmc_status hmc_predict(hmc_handle h, const void *samples, long n_samples, const 
             HMC_REQUIRE(inputs->n >= 1 && inputs->dx == p.dx, "inputs: n must be >= 1 and dx = %d", p.dx);
             in.n = inputs->n;
             nout = in.n * p.dout;
-            in.x = fetch(inputs->x, in.n * p.dx, "inputs.x");
-            if (rel_l2) in.targets = fetch(inputs->y, nout, "inputs.y (targets for rel_l2)");
+            in.x = fetch_data(inputs->x, in.n * p.dx, inputs->dtype, "inputs.x");
+            if (rel_l2) in.targets = fetch_data(inputs->y, nout, inputs->dtype, "inputs.y (targets for rel_l2)");
         } else {
             HMC_REQUIRE(inputs->n_u >= 1 && inputs->n_y >= 1 && inputs->du == p.du && inputs->dy == p.dy,
                         "inputs: DeepONet dimensions do not match the handle's");
             in.n_u = inputs->n_u;
             in.n_y = inputs->n_y;
             nout = in.n_u * in.n_y;
-            in.u = fetch(inputs->u, in.n_u * p.du, "inputs.u");
-            in.yq = fetch(inputs->yq, in.n_y * p.dy, "inputs.yq");
-            if (rel_l2) in.targets = fetch(inputs->t, nout, "inputs.t (targets for rel_l2)");
+            in.u = fetch_data(inputs->u, in.n_u * p.du, inputs->dtype, "inputs.u");
+            in.yq = fetch_data(inputs->yq, in.n_y * p.dy, inputs->dtype, "inputs.yq");
+            if (rel_l2) in.targets = fetch_data(inputs->t, nout, inputs->dtype, "inputs.t (targets for rel_l2)");
         }
         h->stage_used = 0;
         join_in(h);

@@ -33,3 +33,14 @@ def test_last_error_is_callable_without_gpu():
     if not os.path.exists(hmc.LIB_PATH):
         hmc.build()
     assert hmc.lib().hmc_last_error() == b""
+
+
+def test_training_arrays_keep_float32_only_when_all_are_float32():
+    import numpy as np
+    a32, b32 = np.zeros((3, 2), np.float32), np.zeros((3, 1), np.float32)
+    (x, y), dt = hmc._training_arrays(a32, b32)
+    assert dt == hmc.DATA_F32 and x.dtype == np.float32 and y.dtype == np.float32
+    (x, y), dt = hmc._training_arrays(a32, np.zeros((3, 1)))
+    assert dt == hmc.DATA_F64 and x.dtype == np.float64 and y.dtype == np.float64
+    # the ctypes mirror of hmc_data ends with the dtype field, as include/hmc.h declares it
+    assert hmc.Data._fields_[-1][0] == "dtype"

@@ -168,3 +168,30 @@ def test_subset_in_one_part_tensor_cores(which, widths):
 def test_row_counts_around_a_tile(n, prec, widths):
     prob = W.small_mlp(n=n, widths=widths, frac=0.1, chains=1, seed=44)
     _check(prob, prec)
+
+
+# ---- training data passed as float32 ----------------------------------------------------
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("which", ["mlp", "deeponet"])
+def test_float32_training_data_is_the_float64_data(which, prec):
+    # the workloads' data are float32-representable: both element types give the same problem
+    if which == "mlp":
+        prob = W.small_mlp(n=300, widths=(2, 128, 128, 1), frac=0.1, chains=2, seed=45)
+        arrays = {"x": prob.x, "y": prob.y}
+    else:
+        prob = W.small_deeponet(chains=2)
+        arrays = {"u": prob.u, "yq": prob.yq, "t": prob.t}
+    if prec == hmc.PREC_BF16 and which == "deeponet":
+        prob = W.small_deeponet(n_u=40, n_y=130, du=8, width=64, latent=64, frac=0.1, chains=2, seed=46)
+        arrays = {"u": prob.u, "yq": prob.yq, "t": prob.t}
+    q = torch.from_numpy(prob.q0)
+    U64, g64 = sampler_from(prob, prec).energy_grad(q)
+    f32 = dataclasses.replace(prob, **{k: v.astype(np.float32) for k, v in arrays.items()})
+    s32 = sampler_from(f32, prec)
+    U32, g32 = s32.energy_grad(q)
+    assert torch.equal(U32, U64) and torch.equal(g32, g64)
+    # device tensors take the same route
+    dev = dataclasses.replace(prob, **{k: torch.from_numpy(v.astype(np.float32)).cuda() for k, v in arrays.items()})
+    Ud, gd = sampler_from(dev, prec).energy_grad(q)
+    assert torch.equal(Ud, U64) and torch.equal(gd, g64)

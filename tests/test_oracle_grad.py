@@ -135,6 +135,19 @@ def test_prior_only_when_no_data():
     assert np.allclose(g, q / 0.49, rtol=1e-14)
 
 
+def test_deeponet_without_functions_or_queries_is_the_prior():
+    import dataclasses
+    base = W.small_deeponet(frac=0.2, chains=1)
+    q = base.q0[0]
+    prior = 0.5 * np.sum(q * q) / base.prior_sigma**2
+    for empty in ({"u": np.zeros((0, base.u.shape[1])), "t": np.zeros((0, base.t.shape[1]))},
+                  {"yq": np.zeros((0, base.yq.shape[1])), "t": np.zeros((base.t.shape[0], 0))}):
+        o = oracle.Oracle(dataclasses.replace(base, **empty))
+        U, g = o.energy_grad(q)
+        assert np.isclose(U, prior, rtol=1e-14)
+        assert np.allclose(g, q / base.prior_sigma**2, rtol=1e-14)
+
+
 def test_frozen_parameters_enter_only_through_the_likelihood():
     prob = W.small_mlp(frac=0.3)
     o = oracle.Oracle(prob)

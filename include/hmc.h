@@ -131,8 +131,9 @@ HMC_API hmc_status hmc_create(hmc_handle *out, const hmc_net_spec *spec, const h
 /*
  * Create one handle over n_problems independent problems (each with its own
  * spec, data, sigmas, mask and frozen vector, all with n_chains chains).  The problems
- * run side by side: each on its own stream lane, as concurrent branches of one captured
- * trajectory graph, joined before the Metropolis step.  State vectors of a batch handle are
+ * run side by side: every gradient evaluation forks them onto up to 16 stream lanes
+ * (concurrent branches of the captured trajectory graph) and joins them again; the kicks,
+ * drifts and the Metropolis step cover all problems in single launches.  State vectors of a batch handle are
  * packed per problem: q = [problem][chain][k_problem]; U, accepted and dH are
  * [problem][chain] per trajectory.  Momenta of problem p use Philox stream p.
  * In an HMC_PREC_BF16 batch, a problem whose network the tensor-core kernels do not

@@ -287,6 +287,15 @@ HMC_API hmc_status hmc_select_subset(const double *S2, long P, double tau, unsig
 HMC_API hmc_status hmc_predict(hmc_handle h, const void *samples, long n_samples, const hmc_data *inputs,
                                double *mean, double *std, double *rel_l2);
 
+/*
+ * Wait for the work queued on the handle and report whether a device-side wait gave up
+ * since the last check.  The tensor-core kernels bound every wait on a barrier (2 s); one
+ * that runs out records it in the engine's error flag, stops its kernel early and leaves
+ * the context usable, so the results of the calls since the last check cannot be trusted.
+ * Returns HMC_ERR_TIMEOUT then (and clears the record), HMC_OK otherwise.
+ */
+HMC_API hmc_status hmc_check(hmc_handle h);
+
 /* Free the handle and all its device memory. NULL is accepted. */
 HMC_API hmc_status hmc_destroy(hmc_handle h);
 

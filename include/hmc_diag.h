@@ -42,6 +42,13 @@ HMC_API hmc_status hmc_diag_metropolis_energy(hmc_handle h, const void *q, doubl
  * bytes).  Returns the length of the full text. */
 HMC_API long hmc_diag_tuning(hmc_handle h, char *buf, long n);
 
+/* Run one bounded wait out on purpose: a one-thread kernel waits limit_ns (1 us .. 0.1 s)
+ * on a shared-memory barrier that nothing arrives at, then records the timeout in the
+ * error flag of the handle's first engine that keeps one (the tensor-core engines), as a
+ * kernel whose pipeline stalled would.  No GPU fault or hang is involved.  The next
+ * hmc_check returns HMC_ERR_TIMEOUT.  HMC_ERR_UNSUPPORTED when no engine keeps a flag. */
+HMC_API hmc_status hmc_diag_expire_wait(hmc_handle h, long limit_ns);
+
 typedef struct {
     char name[48];      /* kernel kind */
     double ms_total;    /* summed CUDA-event time over all its launches */

@@ -33,10 +33,12 @@ STATUS = {0: "HMC_OK", 1: "HMC_ERR_ARG", 2: "HMC_ERR_CUDA", 3: "HMC_ERR_OOM", 4:
 # every symbol the C ABI (include/hmc.h, include/hmc_diag.h) declares
 EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_create_split", "hmc_sensitivity", "hmc_select_subset",
            "hmc_predict", "hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_diag_umma_gemm",
-           "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_adapt_step_size", "hmc_destroy", "hmc_last_error",
+           "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_adapt_step_size", "hmc_check", "hmc_destroy",
+           "hmc_last_error",
            "hmc_energy_grad_noalloc",
            "hmc_diag_philox", "hmc_diag_momenta", "hmc_diag_log_uniform", "hmc_diag_graph_kernels",
-           "hmc_diag_profile_energy_grad", "hmc_diag_metropolis_energy", "hmc_diag_tuning"]
+           "hmc_diag_profile_energy_grad", "hmc_diag_metropolis_energy", "hmc_diag_tuning",
+           "hmc_diag_expire_wait"]
 
 
 class HmcError(RuntimeError):
@@ -98,6 +100,8 @@ def lib():
         L.hmc_leapfrog.argtypes = [vp, vp, vp, d, i]
         L.hmc_sample.argtypes = [vp, vp, d, i, lg, u64, lg, vp, vp, vp, vp]
         L.hmc_adapt_step_size.argtypes = [vp, vp, i, d, lg, d, u64, lg, ct.POINTER(d)]
+        L.hmc_check.argtypes = [vp]
+        L.hmc_diag_expire_wait.argtypes = [vp, lg]
         L.hmc_destroy.argtypes = [vp]
         L.hmc_last_error.restype = ct.c_char_p
         L.hmc_diag_philox.argtypes = [vp, vp, lg, vp]
@@ -295,6 +299,11 @@ class Sampler:
         _check(lib().hmc_adapt_step_size(self._h, _ptr(q), int(L), float(eps0), int(n_warmup), float(target_accept),
                                          int(seed), int(first_traj), ct.byref(eps)))
         return eps.value, q
+
+    def check(self):
+        """hmc_check: wait for the handle's work; raises HmcError (HMC_ERR_TIMEOUT) when a
+        bounded device-side wait gave up since the last check."""
+        _check(lib().hmc_check(self._h))
 
     def tuning(self):
         """What the engines autotuned at creation (hmc_diag_tuning)."""

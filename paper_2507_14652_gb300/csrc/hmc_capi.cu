@@ -1369,6 +1369,48 @@ hmc_status hmc_destroy(hmc_handle h)
 
 const char *hmc_last_error(void) { return g_err.c_str(); }
 
+hmc_status hmc_check(hmc_handle h)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(h, "NULL argument");
+        HMC_CK(cudaStreamSynchronize(h->stream));
+        bool timed_out = false;
+        for (auto &e : h->engines) {
+            int *f = e->error_flag();
+            if (!f) continue;
+            int v = 0;
+            HMC_CK(cudaMemcpy(&v, f, sizeof(int), cudaMemcpyDeviceToHost));
+            if (v) {
+                timed_out = true;
+                HMC_CK(cudaMemset(f, 0, sizeof(int)));
+            }
+        }
+        if (timed_out) {
+            set_error("a bounded device-side wait gave up since the last check: results since then are not valid");
+            return HMC_ERR_TIMEOUT;
+        }
+        return HMC_OK;
+    });
+}
+
+hmc_status hmc_diag_expire_wait(hmc_handle h, long limit_ns)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(h, "NULL argument");
+        HMC_REQUIRE(limit_ns >= 1000 && limit_ns <= 100000000, "limit_ns must be in [1e3, 1e8]");
+        for (auto &e : h->engines) {
+            int *f = e->error_flag();
+            if (!f) continue;
+            expire_wait_run(f, limit_ns, h->stream);
+            return HMC_OK;
+        }
+        set_error("no engine of this handle keeps a device error flag");
+        return HMC_ERR_UNSUPPORTED;
+    });
+}
+
 long hmc_diag_graph_kernels(hmc_handle h) { return h ? h->traj_kernels : -1; }
 
 long hmc_diag_tuning(hmc_handle h, char *buf, long n)

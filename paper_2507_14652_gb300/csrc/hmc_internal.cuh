@@ -95,6 +95,8 @@ struct Engine {
     virtual void accurate_energy(const void *q, double *U, cudaStream_t s) {}
     // what the engine's autotuner chose at creation ("" if it tunes nothing)
     virtual std::string tuning() const { return std::string(); }
+    // device flag its kernels raise when a bounded wait gives up (nullptr: no such waits)
+    virtual int *error_flag() const { return nullptr; }
 };
 
 struct Problem {
@@ -123,6 +125,9 @@ Engine *make_simt_engine_f32(Problem &p, int C);
 Engine *make_umma_engine_bf16(Problem &p, int C);
 bool umma_engine_supports(const Problem &p, std::string *why);
 Engine *make_don_engine_bf16(Problem &p, int C);
+// One bounded device-side wait run out on purpose; it raises *err (hmc_diag_expire_wait).
+void expire_wait_run(int *err, long limit_ns, cudaStream_t s);
+
 // A problem without data terms: U = |q|^2 / (2 alpha^2) in any precision.
 Engine *make_prior_engine(const Problem &p, int prec, int C);
 bool don_engine_supports(const Problem &p, std::string *why);

@@ -1639,6 +1639,18 @@ __global__ void k_scatter_plan(const float *q, long k, ScatterPlan sc)
     }
 }
 
+// One bounded wait run out on purpose: a barrier that nothing arrives at, waited on
+// with the same bounded wait the pipelines use, which records the timeout in *err.
+__global__ void k_expire_wait(int *err, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    fence_mbar_init();
+    mbar_wait(b, 0, err, limit_ns);   // phase 0 never completes
+    mbar_arrive(b);                   // complete it before the CTA exits
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -1895,6 +1907,7 @@ class UmmaEngine final : public Engine {
     size_t bytes() const override { return 0; }
 
     ScatterPlan scatter_plan() override { return plan_; }
+    int *error_flag() const override { return err_; }
 
     void scatter(const void *qv, cudaStream_t s) override
     {
@@ -2444,6 +2457,7 @@ class DonEngine final : public Engine {
     }
 
     ScatterPlan scatter_plan() override { return plan_; }
+    int *error_flag() const override { return err_; }
     size_t bytes() const override { return bytes_; }
 
     // The Metropolis energy (the bf16 operator output would carry order-one noise into
@@ -3053,6 +3067,12 @@ bool don_engine_supports(const Problem &p, std::string *why)
 }
 
 Engine *make_don_engine_bf16(Problem &p, int C) { return new DonEngine(p, C); }
+
+void expire_wait_run(int *err, long limit_ns, cudaStream_t s)
+{
+    k_expire_wait<<<1, 1, 0, s>>>(err, (unsigned long long)limit_ns);
+    HMC_LAUNCH_CK();
+}
 
 }  // namespace hmc
 

@@ -195,3 +195,26 @@ def test_float32_training_data_is_the_float64_data(which, prec):
     dev = dataclasses.replace(prob, **{k: torch.from_numpy(v.astype(np.float32)).cuda() for k, v in arrays.items()})
     Ud, gd = sampler_from(dev, prec).energy_grad(q)
     assert torch.equal(Ud, U64) and torch.equal(gd, g64)
+
+
+# ---- a bounded device-side wait that runs out ------------------------------------------
+
+def test_a_wait_that_runs_out_is_reported_and_the_handle_stays_usable():
+    prob = W.small_mlp(n=300, widths=(2, 128, 128, 1), frac=0.1, chains=2, seed=47)
+    s = sampler_from(prob, hmc.PREC_BF16)
+    q = torch.from_numpy(prob.q0)
+    U0, g0 = s.energy_grad(q)
+    s.check()                                   # no wait gave up
+    L = hmc.lib()
+    # a 1 ms wait on a barrier that nothing arrives at: recorded, no fault, no hang
+    assert L.hmc_diag_expire_wait(s._h, 1_000_000) == 0
+    with pytest.raises(hmc.HmcError, match="HMC_ERR_TIMEOUT"):
+        s.check()
+    s.check()                                   # the record was cleared
+    U1, g1 = s.energy_grad(q)                   # and the context still works
+    assert torch.equal(U1, U0) and torch.equal(g1, g0)
+    s.check()
+    # the CUDA-core engines have no such waits and keep no flag
+    s32 = sampler_from(prob, hmc.PREC_FP32)
+    assert L.hmc_diag_expire_wait(s32._h, 1_000_000) == 6
+    s32.check()

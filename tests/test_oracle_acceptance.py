@@ -4,9 +4,10 @@ sampled (Sec. 4.2.3 and the tau sweep of App. E, where smaller subsets accept mo
 attributes it to the leapfrog's error, which grows with the dimension).
 
 Nested subsets (5% inside 30% inside all 481 parameters of the tiny BNN) keep the
-comparison like for like: the conditional posterior of a sub-block is lower-dimensional
-and no stiffer (its largest curvature is bounded by the full one), so the leapfrog's
-energy error can only shrink.  Seeded, so the rates are fixed numbers; the margins
+comparison like for like: the conditional posterior of a sub-block is lower-dimensional,
+and for a Gaussian posterior it is no stiffer (a principal submatrix's largest eigenvalue
+is bounded by the full Hessian's), so the leapfrog's energy error shrinks with it.  Seeded,
+so the rates are fixed numbers; the margins
 allow for the Monte Carlo error of 480 post-burn-in trajectories per subset.
 """
 import dataclasses

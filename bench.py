@@ -173,6 +173,63 @@ def algorithmic(prob, C):
     }
 
 
+def other_workloads(hmc, torch, steps=3):
+    """The other synthetic workloads, timed the same way (one trajectory to capture the
+    graph, then `steps` trajectories between CUDA events): grad-evals/s and acceptance."""
+    from oracle.ess import ess_chains
+    out = {}
+
+    def timed(name, sp, q0, eps, L, chains_total, prec_name, ess_traj=0):
+        q0 = torch.from_numpy(q0) if isinstance(q0, np.ndarray) else q0
+        sp.sample(q0, eps, L, 1, seed=5, keep_samples=False)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, acc, dH, ql = sp.sample(q0, eps, L, steps, seed=5, first_traj=1, keep_samples=False)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        rec = {"dtype": prec_name, "chains": chains_total, "L": L, "eps": eps, "ms_per_trajectory": ms,
+               "grad_evals_per_s": chains_total * L / (ms / 1000.0),
+               "accept_rate": float(acc.float().mean().item()),
+               "abs_dH_median": float(np.nanmedian(np.abs(dH.cpu().numpy())))}
+        if ess_traj:
+            torch.cuda.synchronize()
+            a.record()
+            S, acc2, _, _ = sp.sample(ql, eps, L, ess_traj, seed=6, first_traj=100)
+            b.record()
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) / 1000.0
+            Sn = S.cpu().double().numpy()[ess_traj // 5:]
+            e = ess_chains(Sn if Sn.ndim == 3 else Sn[:, None, :])   # a batch: every coordinate on its own
+            rec.update({"ess_trajectories": ess_traj, "ess_min": float(e.min()), "ess_min_per_s": float(e.min()) / sec,
+                        "ess_median_per_s": float(np.median(e)) / sec,
+                        "ess_accept_rate": float(acc2.float().mean().item())})
+        out[name] = rec
+        sp.close()
+
+    p = W.tiny_bnn()
+    timed("tiny_bnn_fp64", hmc.Sampler.mlp(p.net.widths, p.x, p.y, p.mask, p.frozen, 1, prior_sigma=p.prior_sigma,
+                                           noise_sigma=p.noise_sigma, prec=hmc.PREC_FP64),
+          p.q0, p.eps, p.L, 1, "f64", ess_traj=200)
+    p = W.deeponet_grf()
+    for nm, pr in (("bf16", hmc.PREC_BF16), ("fp16", hmc.PREC_FP16)):
+        sp = hmc.Sampler.deeponet(p.branch.widths, p.trunk.widths, p.u, p.yq, p.t, p.mask, p.frozen, p.chains,
+                                  prior_sigma=p.prior_sigma, noise_sigma=p.noise_sigma, prec=pr)
+        timed("deeponet_grf_" + nm, sp, p.q0, p.eps, p.L, p.chains, nm)
+    probs = W.batched_uneven()
+    bs = hmc.BatchSampler([(q.net.widths, q.x, q.y, q.mask, q.frozen, q.prior_sigma, q.noise_sigma) for q in probs],
+                          probs[0].chains, hmc.PREC_BF16)
+    q0 = np.concatenate([q.q0.reshape(-1) for q in probs])   # packed [problem][chain][k_problem]
+    timed("batched_uneven_bf16", bs, q0.astype(np.float32), probs[0].eps, probs[0].L,
+          len(probs) * probs[0].chains, "bf16", ess_traj=40)
+    p = W.cone_deeponet()
+    sp = hmc.Sampler.deeponet(p.branch.widths, p.trunk.widths, p.u, p.yq, p.t, p.mask, p.frozen, p.chains,
+                              prior_sigma=p.prior_sigma, noise_sigma=p.noise_sigma, prec=hmc.PREC_BF16)
+    timed("cone_deeponet_bf16", sp, p.q0, p.eps, p.L, p.chains, "bf16")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,6 +240,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--split", type=int, default=4, help="data batches of the split-integrator run (0 = skip)")
     ap.add_argument("--no-around", action="store_true", help="skip the sensitivity/truncation/predictive timings")
+    ap.add_argument("--no-other", action="store_true", help="skip the other workloads (tiny BNN, DeepONets, batch)")
     args = ap.parse_args()
     assert args.warmup >= 3, "timing rules need at least 3 warm-up steps"
     if args.impl == "reference":
@@ -208,7 +266,7 @@ def main():
     q0 = torch.from_numpy(prob.q0).float().cuda()
 
     # warm-up (captures the trajectory graph)
-    _, acc_w, dH_w, q = s.sample(q0, eps, L, args.warmup, seed=seed, keep_samples=False)
+    _, acc_w, dH_w, q = s.sample(q0, eps, L, args.warmup, seed=seed)
     torch.cuda.synchronize()
 
     # timed region: exactly `steps` trajectories
@@ -221,7 +279,7 @@ def main():
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    S, acc, dH, q_last = s.sample(q, eps, L, args.steps, seed=seed, first_traj=args.warmup, keep_samples=False)
+    S, acc, dH, q_last = s.sample(q, eps, L, args.steps, seed=seed, first_traj=args.warmup)
     e1.record()
     torch.cuda.synchronize()
     if dist:
@@ -290,35 +348,106 @@ def main():
     e2e = {"value": job_rate(ws, C * L * args.steps, t_e2e), "unit": METRIC, "h2d_bytes_per_step": 4 * C * prob.k,
            "d2h_bytes_per_step": 4 * C * prob.k + C + 8 * C + 4 * C * prob.k}
 
-    # ESS/s: batched BF16 sampler vs the plain one-chain FP32 CUDA-core sampler, both with
-    # the same L and the same step, adapted by dual averaging to ~80% acceptance on the
-    # batched sampler during a warm-up (a fixed eps that suits the start of the chains
-    # rejects nearly everything once they reach the sharper posterior mode)
+    # The same timed trajectories with the fp16 tensor-core engine (same kernels and
+    # bytes, 11 significant bits against bf16's 8): its throughput and acceptance
+    s16 = hmc.Sampler.mlp(prob.net.widths, prob.x, prob.y, prob.mask, prob.frozen, C, prior_sigma=prob.prior_sigma,
+                          noise_sigma=prob.noise_sigma, prec=hmc.PREC_FP16)
+    s16.sample(q0, eps, L, args.warmup, seed=seed)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    _, acc16, dH16, _ = s16.sample(q, eps, L, args.steps, seed=seed, first_traj=args.warmup)
+    b.record()
+    torch.cuda.synchronize()
+    ms16 = a.elapsed_time(b)
+    fp16 = {"value": job_rate(1, C * L * args.steps, ms16 / 1000.0), "ms_per_step": ms16 / args.steps,
+            "accept_rate": float(acc16.float().mean().item()),
+            "abs_dH_median": float(np.nanmedian(np.abs(dH16.cpu().numpy())))}
+
+    # ESS/s and acceptance at one step size: the step is adapted by dual averaging to ~80%
+    # acceptance on the batched fp16 sampler during a warm-up (a fixed eps that suits the
+    # start of the chains rejects nearly everything once they reach the sharper posterior
+    # mode).  Then, at that step:
+    # * acceptance on paired starts: states visited by the fp16 chains, and from each, one
+    #   trajectory per precision with the same momenta and uniforms (same seed and index),
+    #   so the mean acceptance probabilities min(1, exp(-dH)) differ only by the forces;
+    # * ESS/s of chains from the warmed-up states (same seed and indices): batched fp16 and
+    #   bf16, the batched FP32 CUDA-core sampler and the plain one-chain FP32 sampler (on
+    #   the chain whose paired FP32 acceptance is the median one).
     ess = None
     if args.ess_traj > 0 and rank == 0:
         from oracle.ess import ess_chains
         n_adapt = max(20, args.ess_traj // 4)
-        eps_ad, q_ad = s.adapt_step_size(q_last, L, eps, n_adapt, target_accept=0.8, seed=seed + 77,
-                                         first_traj=10 ** 6)
-        ess = {"eps_adapted": eps_ad, "adapt_trajectories": n_adapt, "target_accept": 0.8}
-        for name, prec, chains in (("bf16_batched", hmc.PREC_BF16, C), ("fp32_plain_1chain", hmc.PREC_FP32, 1)):
-            sp = s if prec == hmc.PREC_BF16 else hmc.Sampler.mlp(
-                prob.net.widths, prob.x, prob.y, prob.mask, prob.frozen, 1, prior_sigma=prob.prior_sigma,
-                noise_sigma=prob.noise_sigma, prec=prec)
-            qs = q_ad[:chains].contiguous()
+        eps_ad, q_ad = s16.adapt_step_size(q_last, L, eps, n_adapt, target_accept=0.8, seed=seed + 77,
+                                           first_traj=10 ** 6)
+        ess = {"eps_adapted": eps_ad, "adapted_on": "fp16_batched", "adapt_trajectories": n_adapt,
+               "target_accept": 0.8}
+        s32 = hmc.Sampler.mlp(prob.net.widths, prob.x, prob.y, prob.mask, prob.frozen, C,
+                              prior_sigma=prob.prior_sigma, noise_sigma=prob.noise_sigma, prec=hmc.PREC_FP32)
+
+        def acc_prob(d):
+            d = d.cpu().numpy().ravel()
+            return np.where(np.isfinite(d), np.minimum(1.0, np.exp(-np.nan_to_num(d, nan=0.0, posinf=0.0))), 0.0)
+
+        n_start = 12
+        Sst, _, _, _ = s16.sample(q_ad, eps_ad, L, 3 * n_start, seed=seed + 55, first_traj=3 * 10 ** 6)
+        paired = {"starts": n_start, "trajectories_per_start": 1}
+        ap = {}
+        for name, sp in (("fp16", s16), ("bf16", s), ("fp32", s32)):
+            a, dd = [], []
+            for t in range(n_start):
+                _, _, d, _ = sp.sample(Sst[3 * t + 2].contiguous(), eps_ad, L, 1, seed=seed + 99,
+                                       first_traj=4 * 10 ** 6 + t, keep_samples=False)
+                a.append(acc_prob(d))
+                dd.append(np.abs(d.cpu().numpy().ravel()))
+            ap[name] = np.stack(a)                                    # [start][chain]
+            paired[name] = {"mean_accept_prob": float(ap[name].mean()),
+                            "abs_dH_median": float(np.nanmedian(np.concatenate(dd)))}
+        for name in ("fp16", "bf16"):
+            diff = (ap[name] - ap["fp32"]).ravel()
+            paired[name]["minus_fp32"] = float(diff.mean())
+            paired[name]["minus_fp32_se"] = float(diff.std(ddof=1) / np.sqrt(diff.size))
+        ess["paired_acceptance"] = paired
+        c1 = int(np.argsort(ap["fp32"].mean(axis=0))[C // 2])      # the median chain
+        ess["plain_chain"] = c1
+        arms = (("fp16_batched", s16, None, args.ess_traj), ("bf16_batched", s, None, args.ess_traj),
+                ("fp32_batched", s32, None, max(10, args.ess_traj // 5)),
+                ("fp32_plain_1chain", None, c1, max(10, args.ess_traj // 2)))
+        for name, sp, one, ntraj in arms:
+            if sp is None:
+                sp = hmc.Sampler.mlp(prob.net.widths, prob.x, prob.y, prob.mask, prob.frozen, 1,
+                                     prior_sigma=prob.prior_sigma, noise_sigma=prob.noise_sigma, prec=hmc.PREC_FP32)
+            qs = (q_ad if one is None else q_ad[one:one + 1]).contiguous()
+            chains = qs.shape[0]
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            Se, ae, de, _ = sp.sample(qs, eps_ad, L, args.ess_traj, seed=seed + 77, first_traj=10 ** 6 + n_adapt)
+            Se, ae, de, _ = sp.sample(qs, eps_ad, L, ntraj, seed=seed + 77, first_traj=10 ** 6 + n_adapt)
             b.record()
             torch.cuda.synchronize()
             sec = a.elapsed_time(b) / 1000.0
-            e = ess_chains(Se.cpu().double().numpy()[args.ess_traj // 5:])
-            ess[name] = {"chains": chains, "trajectories": args.ess_traj, "seconds": sec,
+            e = ess_chains(Se.cpu().double().numpy()[ntraj // 5:])
+            ess[name] = {"chains": chains, "trajectories": ntraj, "seconds": sec,
                          "ess_min": float(e.min()), "ess_median": float(np.median(e)),
                          "ess_min_per_s": float(e.min()) / sec, "ess_median_per_s": float(np.median(e)) / sec,
                          "accept_rate": float(ae.float().mean().item()),
-                         "grad_evals_per_s": chains * L * args.ess_traj / sec}
+                         "mean_accept_prob": float(acc_prob(de).mean()),
+                         "abs_dH_median": float(np.nanmedian(np.abs(de.cpu().numpy()))),
+                         "grad_evals_per_s": chains * L * ntraj / sec}
+        # executed work of the FP32 CUDA-core engine per chain-evaluation: the forward GEMMs,
+        # the input adjoints and the dense weight gradients (every weight's entry, then the
+        # sampled ones are gathered), 2 flops per multiply-add; its peak is the CUDA cores'
+        # FP32 rate from unit counts and clock: 152 SMs x 128 lanes x 2 flops x max clock
+        w = prob.net.widths
+        fl = 2.0 * prob.x.shape[0] * sum(w[l] * w[l + 1] for l in range(len(w) - 1))
+        fl_exec = fl + fl + (fl - 2.0 * prob.x.shape[0] * w[0] * w[1])
+        clk = (peaks.get("sm_max_mhz") or 2070.0) * 1e6
+        fp32_peak = 152 * 128 * 2 * clk / 1e12
+        for name in ("fp32_batched", "fp32_plain_1chain"):
+            tf = ess[name]["grad_evals_per_s"] * fl_exec / 1e12
+            ess[name].update({"executed_tflops": tf, "fp32_cuda_core_peak_tflops": fp32_peak,
+                              "fp32_peak_frac": tf / fp32_peak})
+        s32.close()
 
     # the symmetric split integrator over data batches on the same workload and step:
     # trajectories of the same L, each step 2M - 1 batch gradients of N/M points
@@ -374,6 +503,10 @@ def main():
                   "predict": {"samples": int(Sp.shape[0]), "points": int(prob.x.shape[0]), "dtype": "f32",
                               "ms": 1e3 * t_p, "samples_per_s": Sp.shape[0] / t_p, "rel_l2": rel}}
 
+    other = None
+    if rank == 0 and not args.no_other:
+        other = other_workloads(hmc, torch)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob)
@@ -387,6 +520,7 @@ def main():
                            "subset_k": prob.k, "params": prob.P, "points": int(prob.x.shape[0]),
                            "step": "one HMC trajectory for all chains (L gradient evaluations each)",
                            "l2": "inputs larger than L2: 0.4 GB of bf16 activations and deltas per gradient evaluation",
+                           "samples": "every trajectory's samples are written to device memory in the timed region",
                            "parallelism": f"replicas x{ws}"},
                 "accept_rate": float(acc_np.mean()), "abs_dH_mean": float(np.nanmean(np.abs(dH_np))),
                 "abs_dH_median": float(np.nanmedian(np.abs(dH_np))),
@@ -394,7 +528,8 @@ def main():
                 "roofline": roof, "roofline_by_kernel": roof_all, "kernel_ms": {k: v[0] for k, v in prof.items()},
                 "tuning": s.tuning().strip(),
                 "kernel_launches_per_eval": {k: v[1] for k, v in prof.items()},
-                "e2e": e2e, "cpu_baseline": cpu, "ess": ess, "split_hmc": split, "around_the_sampler": around,
+                "e2e": e2e, "cpu_baseline": cpu, "fp16": fp16, "ess": ess, "split_hmc": split,
+                "around_the_sampler": around, "other_workloads": other,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:

@@ -62,9 +62,19 @@ typedef enum { HMC_ACT_IDENTITY = 0, HMC_ACT_TANH = 1, HMC_ACT_SIN = 2 } hmc_act
 
 /* Arithmetic of the network evaluation.  FP64 and FP32 run plain CUDA-core
  * kernels.  BF16 runs the wide layers on tcgen05 tensor cores (bf16 operands,
- * fp32 accumulation) with fp32 positions/momenta and fp64 energy sums.
+ * fp32 accumulation) with fp32 positions/momenta and fp64 energy sums.  FP16 is the
+ * same tensor-core path with fp16 operands: the same bytes and tensor rate, 11
+ * significant bits against bf16's 8, so the leapfrog's forces are about eight times
+ * more accurate (the output deltas are scaled by a power of two near 1/sigma to stay
+ * inside fp16's range, and the gradient sums are scaled back in fp32).
  * HMC_PREC_TF32 is reserved: creating a handle with it returns HMC_ERR_UNSUPPORTED. */
-typedef enum { HMC_PREC_FP64 = 0, HMC_PREC_FP32 = 1, HMC_PREC_TF32 = 2, HMC_PREC_BF16 = 3 } hmc_prec;
+typedef enum {
+    HMC_PREC_FP64 = 0,
+    HMC_PREC_FP32 = 1,
+    HMC_PREC_TF32 = 2,
+    HMC_PREC_BF16 = 3,
+    HMC_PREC_FP16 = 4
+} hmc_prec;
 
 /* HMC_NET_DEEPONET: n_u input functions evaluated at n_y query points shared by all
  * of them.  HMC_NET_DEEPONET_UNALIGNED: every input function with its own n_y query
@@ -136,7 +146,7 @@ HMC_API hmc_status hmc_create(hmc_handle *out, const hmc_net_spec *spec, const h
  * drifts and the Metropolis step cover all problems in single launches.  State vectors of a batch handle are
  * packed per problem: q = [problem][chain][k_problem]; U, accepted and dH are
  * [problem][chain] per trajectory.  Momenta of problem p use Philox stream p.
- * In an HMC_PREC_BF16 batch, a problem whose network the tensor-core kernels do not
+ * In an HMC_PREC_BF16 or HMC_PREC_FP16 batch, a problem whose network the tensor-core kernels do not
  * cover (a hidden width that is not a multiple of 64, say) runs on the FP32 CUDA-core
  * engine instead; its positions are float like the others'.
  */
@@ -168,6 +178,29 @@ HMC_API hmc_status hmc_create_split(hmc_handle *out, const hmc_net_spec *spec, c
                                     double prior_sigma, double noise_sigma, const unsigned char *subset_mask,
                                     const double *frozen_params, int n_chains, int n_splits,
                                     void *cuda_stream);
+
+/*
+ * Create a sampler for one problem whose potential and force are evaluated in passes over
+ * the data rows, rows_per_pass (>= 1) rows at a time (MLP: data points; DeepONet: input
+ * functions, each with all its queries), so the device holds one pass's activations.
+ * U and grad U are sums over the data terms (Sec. 2.2, the full-batch potential of
+ * Sec. 3.3), so the passes' sums give them exactly (up to the order of the additions):
+ * pass m holds rows [floor(m R / M), floor((m + 1) R / M)) of the R rows, M =
+ * ceil(R / rows_per_pass), plus 1/M of the prior.  Every buffer that grows with the rows
+ * is shared by the passes, which run one after another on the handle's stream (a DeepONet
+ * pass evaluates the trunk net again, on all queries).  Trajectories use the full-batch
+ * leapfrog, as for hmc_create; everything else is as for hmc_create.
+ * hmc_create itself falls back to passes when the whole batch's buffers do not fit in
+ * device memory (it halves the rows of a pass until the handle fits); hmc_num_passes
+ * reports the passes a handle uses.
+ */
+HMC_API hmc_status hmc_create_chunked(hmc_handle *out, const hmc_net_spec *spec, const hmc_data *data,
+                                      double prior_sigma, double noise_sigma, const unsigned char *subset_mask,
+                                      const double *frozen_params, int n_chains, long rows_per_pass,
+                                      void *cuda_stream);
+
+/* Passes over the data rows per evaluation (1 unless the handle is chunked), or -1. */
+HMC_API int hmc_num_passes(hmc_handle h);
 
 /* k (for a batch: the sum of k over problems), or -1 for a bad handle. */
 HMC_API long hmc_subset_size(hmc_handle h);
@@ -222,8 +255,10 @@ HMC_API hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, l
  *   seed, first_traj  Philox stream and trajectory index of the first warm-up
  *                   trajectory; continue sampling with first_traj + n_warmup
  *   eps_out         the averaged step after the last update (host double)
- * Each warm-up trajectory is one hmc_sample call, so the trajectory graph is
- * recaptured for every new eps.  Errors as hmc_sample.
+ * The step size is device state: every warm-up trajectory replays the same captured
+ * trajectory graph (the one hmc_sample uses for this L and seed), and each update runs
+ * on the device right after its trajectory, so the warm-up waits for the GPU once, at
+ * the end.  Errors as hmc_sample.
  */
 HMC_API hmc_status hmc_adapt_step_size(hmc_handle h, void *q, int L, double eps0, long n_warmup,
                                double target_accept, unsigned long long seed, long first_traj,
@@ -301,24 +336,28 @@ HMC_API hmc_status hmc_destroy(hmc_handle h);
 
 /*
  * U and grad U of an FP32 MLP for C chains without any device allocation.
- * The paper has no counterpart: this exists for callers that must not allocate
- * device memory -- code running while a stream is being captured into a CUDA
- * graph (cudaMalloc is not allowed there), code embedded in a framework whose
- * own memory pool owns the device, or a real-time loop that may not block in the
- * allocator.  It runs the same CUDA-core kernels as hmc_energy_grad with
- * HMC_PREC_FP32, without a handle.
+ * The paper has no counterpart.  It is for callers that cannot call cudaMalloc:
+ * a plug-in inside another framework whose memory pool owns the whole device (a
+ * cudaMalloc of its own would fail, or steal memory the pool has promised), or a
+ * real-time loop that may not block in the driver's allocator.  It runs the same
+ * CUDA-core kernels as hmc_energy_grad with HMC_PREC_FP32, without a handle.
  *   net          the MLP (widths, activations, biases); parameter order as above
- *   x [n][dx], y [n][dout], frozen [P], subset_idx [k] (ascending int32 parameter
- *   indices of the sampled entries), q [C][k]: device arrays owned by the caller
+ *   x [n][dx], y [n][dout], frozen [P], subset_idx [k] (strictly ascending int32
+ *   parameter indices of the sampled entries), q [C][k]: device arrays owned by
+ *   the caller
  *   U [C] (double) and grad [C][k] (float, may be NULL): device outputs
  *   cuda_stream  where the work is queued; the call returns without waiting
  * Every intermediate lives in one fixed 16 MiB array inside the library's device
  * image, held by every GPU that loads the library until the process exits.
  * Problems whose intermediates exceed it are rejected with HMC_ERR_ARG and a
- * message giving the size needed.  All calls share that array and each call
- * overwrites it, so calls that overlap on the GPU race; serialise them.  The
- * first call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture.
+ * message giving the limit.  All calls share that array and each call overwrites
+ * it (what must start at zero is cleared by the call itself), so calls that
+ * overlap on the GPU race; serialise them.  subset_idx is checked on the device:
+ * an entry outside [0, P) or not above the one before it is never used to
+ * address memory, and every U (and grad) of that call is set to NaN instead.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.
  */
 HMC_API hmc_status hmc_energy_grad_noalloc(const hmc_mlp_spec *net, const float *x, const float *y, long n,
                                            const float *frozen, const int *subset_idx, long k,

@@ -32,8 +32,36 @@ HMC_API hmc_status hmc_diag_log_uniform(unsigned long long seed, unsigned long l
  * call (the launches one trajectory costs), or -1 for a bad handle. */
 HMC_API long hmc_diag_graph_kernels(hmc_handle h);
 
+/* How many trajectory graphs the handle has captured so far (a new one only when L or
+ * the seed changes), or -1 for a bad handle. */
+HMC_API long hmc_diag_graph_captures(hmc_handle h);
+
+/* The step sizes of the last hmc_adapt_step_size call on h: out_host[2 m - 2] is the
+ * step trajectory m + 1 was given (exp of the dual-averaging iterate after update m)
+ * and out_host[2 m - 1] the averaged step after update m, for m = 1..n (n at most that
+ * call's n_warmup). */
+HMC_API hmc_status hmc_diag_adapt_trace(hmc_handle h, double *out_host, long n);
+
+/* The device dual-averaging update of hmc_adapt_step_size (Hoffman and Gelman 2014,
+ * Sec. 3.2) run on given energy errors dH[n][nseg] (host or device) instead of
+ * trajectories: update m takes row m - 1.  out_host[n][2] as hmc_diag_adapt_trace. */
+HMC_API hmc_status hmc_diag_dual_averaging(const double *dH, long n, int nseg, double eps0, double target,
+                                           double *out_host);
+
+/* The tanh the FP16 tensor-core engine applies in its epilogues, on n device floats
+ * x -> y; synchronises before returning. */
+HMC_API hmc_status hmc_diag_tanh16(const float *x, float *y, long n);
+
+/* Device memory the library's buffers hold right now, in bytes (every handle together). */
+HMC_API long hmc_diag_device_bytes(void);
+
+/* Cap the library's device buffers at `bytes` in total (<= 0 lifts the cap): an allocation
+ * that would exceed it fails with HMC_ERR_OOM as cudaMalloc would on a full device.  Lets
+ * a test drive hmc_create's fallback to passes over the rows without filling the GPU. */
+HMC_API void hmc_diag_set_memory_cap(long bytes);
+
 /* The energy the Metropolis test uses, for states q [C][k] (device or host; U [C] host
- * or device doubles): on the bf16 tensor-core engines the accurate forward pass with
+ * or device doubles): on the tensor-core engines the accurate forward pass with
  * hi/lo activations, elsewhere the energy of hmc_energy_grad. */
 HMC_API hmc_status hmc_diag_metropolis_energy(hmc_handle h, const void *q, double *U);
 

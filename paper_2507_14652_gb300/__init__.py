@@ -25,20 +25,22 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhmc.so")
 MAXL = 16
 
 ACT_IDENTITY, ACT_TANH, ACT_SIN = 0, 1, 2
-PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16 = 0, 1, 2, 3
+PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16, PREC_FP16 = 0, 1, 2, 3, 4
 NET_MLP, NET_DEEPONET, NET_DEEPONET_UNALIGNED = 0, 1, 2
 STATUS = {0: "HMC_OK", 1: "HMC_ERR_ARG", 2: "HMC_ERR_CUDA", 3: "HMC_ERR_OOM", 4: "HMC_ERR_NONFINITE",
           5: "HMC_ERR_TIMEOUT", 6: "HMC_ERR_UNSUPPORTED"}
 
 # every symbol the C ABI (include/hmc.h, include/hmc_diag.h) declares
-EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_create_split", "hmc_sensitivity", "hmc_select_subset",
+EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_create_split", "hmc_create_chunked", "hmc_num_passes",
+           "hmc_sensitivity", "hmc_select_subset",
            "hmc_predict", "hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_diag_umma_gemm",
            "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_adapt_step_size", "hmc_check", "hmc_destroy",
            "hmc_last_error",
            "hmc_energy_grad_noalloc",
            "hmc_diag_philox", "hmc_diag_momenta", "hmc_diag_log_uniform", "hmc_diag_graph_kernels",
            "hmc_diag_profile_energy_grad", "hmc_diag_metropolis_energy", "hmc_diag_tuning",
-           "hmc_diag_expire_wait"]
+           "hmc_diag_expire_wait", "hmc_diag_graph_captures", "hmc_diag_adapt_trace", "hmc_diag_dual_averaging",
+           "hmc_diag_device_bytes", "hmc_diag_set_memory_cap", "hmc_diag_tanh16"]
 
 
 class HmcError(RuntimeError):
@@ -90,6 +92,15 @@ def lib():
         L.hmc_sensitivity.argtypes = [ct.POINTER(NetSpec), ct.POINTER(Data), vp, vp, vp, vp]
         L.hmc_select_subset.argtypes = [vp, lg, d, vp, ct.POINTER(lg), vp, vp]
         L.hmc_create_split.argtypes = [ct.POINTER(vp), ct.POINTER(NetSpec), ct.POINTER(Data), d, d, vp, vp, i, i, vp]
+        L.hmc_create_chunked.argtypes = [ct.POINTER(vp), ct.POINTER(NetSpec), ct.POINTER(Data), d, d, vp, vp, i, lg,
+                                         vp]
+        L.hmc_num_passes.argtypes = [vp]
+        L.hmc_num_passes.restype = i
+        L.hmc_diag_device_bytes.argtypes = []
+        L.hmc_diag_device_bytes.restype = lg
+        L.hmc_diag_set_memory_cap.argtypes = [lg]
+        L.hmc_diag_tanh16.argtypes = [vp, vp, lg]
+        L.hmc_diag_set_memory_cap.restype = None
         L.hmc_subset_size.argtypes = [vp]
         L.hmc_subset_size.restype = lg
         L.hmc_param_count.argtypes = [vp]
@@ -111,14 +122,19 @@ def lib():
                                               vp]
         L.hmc_diag_graph_kernels.argtypes = [vp]
         L.hmc_diag_graph_kernels.restype = lg
+        L.hmc_diag_graph_captures.argtypes = [vp]
+        L.hmc_diag_graph_captures.restype = lg
+        L.hmc_diag_adapt_trace.argtypes = [vp, vp, lg]
+        L.hmc_diag_dual_averaging.argtypes = [vp, lg, i, d, d, vp]
         L.hmc_diag_profile_energy_grad.argtypes = [vp, vp, i, vp, i]
         L.hmc_diag_umma_gemm.argtypes = [i] * 6 + [vp] * 3
         L.hmc_diag_metropolis_energy.argtypes = [vp, vp, vp]
         L.hmc_diag_tuning.argtypes = [vp, ct.c_char_p, lg]
         L.hmc_diag_tuning.restype = lg
         for f in EXPORTS:
-            if f not in ("hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_last_error",
-                         "hmc_diag_graph_kernels", "hmc_diag_tuning"):
+            if f not in ("hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_last_error", "hmc_num_passes",
+                         "hmc_diag_device_bytes", "hmc_diag_set_memory_cap",
+                         "hmc_diag_graph_kernels", "hmc_diag_graph_captures", "hmc_diag_tuning"):
                 getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -191,7 +207,7 @@ class Sampler:
     """One libhmc handle: a problem (or a batch of problems) with C chains."""
 
     def __init__(self, spec, data, arrays, prior_sigma, noise_sigma, mask, frozen, chains, stream=None,
-                 n_splits=1):
+                 n_splits=1, rows_per_pass=0):
         import torch
         self.prec = spec.prec
         self.dtype = torch.float64 if spec.prec == PREC_FP64 else torch.float32
@@ -200,7 +216,12 @@ class Sampler:
         f = _f64(np.asarray(frozen)) if not hasattr(frozen, "data_ptr") else _f64(frozen)
         self._keep += [m, f]
         h = ct.c_void_p()
-        if n_splits == 1:
+        if rows_per_pass:   # evaluate the data in passes of rows_per_pass rows (hmc_create_chunked)
+            assert n_splits == 1, "a handle is either chunked or split"
+            _check(lib().hmc_create_chunked(ct.byref(h), ct.byref(spec), ct.byref(data), float(prior_sigma),
+                                            float(noise_sigma), _ptr(m), _ptr(f), int(chains), int(rows_per_pass),
+                                            _stream_ptr(stream)))
+        elif n_splits == 1:
             _check(lib().hmc_create(ct.byref(h), ct.byref(spec), ct.byref(data), float(prior_sigma),
                                     float(noise_sigma), _ptr(m), _ptr(f), int(chains), _stream_ptr(stream)))
         else:   # symmetric split integrator over n_splits data batches
@@ -214,10 +235,11 @@ class Sampler:
         self.k = int(lib().hmc_subset_size(h))
         self.P = int(lib().hmc_param_count(h))
         self.n_problems = 1
+        self.passes = int(lib().hmc_num_passes(h))
 
     @classmethod
     def mlp(cls, widths, x, y, mask, frozen, chains, prior_sigma=1.0, noise_sigma=1.0, prec=PREC_FP32,
-            act=None, bias=True, stream=None, n_splits=1):
+            act=None, bias=True, stream=None, n_splits=1, rows_per_pass=0):
         spec = NetSpec()
         spec.kind = NET_MLP
         spec.net = mlp_spec(widths, act, bias)
@@ -225,12 +247,12 @@ class Sampler:
         (x, y), dt = _training_arrays(x, y)
         d = Data()
         d.x, d.n, d.dx, d.y, d.dtype = _ptr(x), x.shape[0], x.shape[1], _ptr(y), dt
-        return cls(spec, d, [x, y], prior_sigma, noise_sigma, mask, frozen, chains, stream, n_splits)
+        return cls(spec, d, [x, y], prior_sigma, noise_sigma, mask, frozen, chains, stream, n_splits, rows_per_pass)
 
     @classmethod
     def deeponet(cls, branch, trunk, u, yq, t, mask, frozen, chains, prior_sigma=1.0, noise_sigma=1.0,
                  prec=PREC_FP32, out_bias=True, branch_act=None, trunk_act=None, branch_bias=True,
-                 trunk_bias=True, stream=None, n_splits=1):
+                 trunk_bias=True, stream=None, n_splits=1, rows_per_pass=0):
         """A DeepONet; yq [n_y][dy] holds query points shared by every input function, or
         yq [n_u][n_y][dy] each function's own (HMC_NET_DEEPONET_UNALIGNED)."""
         spec = NetSpec()
@@ -245,7 +267,8 @@ class Sampler:
         d.u, d.n_u, d.du = _ptr(u), u.shape[0], u.shape[1]
         d.yq, d.n_y, d.dy = _ptr(yq), yq.shape[-2], yq.shape[-1]
         d.t = _ptr(t)
-        return cls(spec, d, [u, yq, t], prior_sigma, noise_sigma, mask, frozen, chains, stream, n_splits)
+        return cls(spec, d, [u, yq, t], prior_sigma, noise_sigma, mask, frozen, chains, stream, n_splits,
+                   rows_per_pass)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -445,6 +468,28 @@ def profile_energy_grad(sampler, q, reps=5):
 def graph_kernels(sampler):
     """Kernel launches in one captured trajectory of the last sample() call."""
     return int(lib().hmc_diag_graph_kernels(sampler._h))
+
+
+def graph_captures(sampler):
+    """Trajectory graphs the handle has captured so far (hmc_diag_graph_captures)."""
+    return int(lib().hmc_diag_graph_captures(sampler._h))
+
+
+def adapt_trace(sampler, n):
+    """Step sizes of the last adapt_step_size() call: [n][2] = (step of trajectory m + 1,
+    averaged step after update m) for m = 1..n (hmc_diag_adapt_trace)."""
+    out = np.zeros((n, 2))
+    _check(lib().hmc_diag_adapt_trace(sampler._h, _ptr(out), int(n)))
+    return out
+
+
+def diag_dual_averaging(dH, eps0, target):
+    """The library's device dual-averaging update run on given dH[n][nseg] rows
+    (hmc_diag_dual_averaging); returns [n][2] as adapt_trace()."""
+    d = np.ascontiguousarray(dH, dtype=np.float64)
+    out = np.zeros((d.shape[0], 2))
+    _check(lib().hmc_diag_dual_averaging(_ptr(d), d.shape[0], d.shape[1], float(eps0), float(target), _ptr(out)))
+    return out
 
 
 class BatchSampler(Sampler):

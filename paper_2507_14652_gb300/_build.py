@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libhmc.so")
-SOURCES = ["hmc_capi.cu", "k_simt.cu", "k_umma.cu", "k_sens.cu", "k_predict.cu", "k_prior.cu"]
+SOURCES = ["hmc_capi.cu", "k_simt.cu", "k_umma.cu", "k_umma_f16.cu", "k_sens.cu", "k_predict.cu", "k_prior.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -29,6 +29,9 @@ def _stale(obj, src):
         return True
     t = os.path.getmtime(obj)
     deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    with open(src) as fh:   # a translation unit may include another .cu file (k_umma_f16.cu)
+        deps += [os.path.join(CSRC, ln.split('"')[1]) for ln in fh if ln.startswith('#include "') and
+                 ln.split('"')[1].endswith(".cu")]
     deps += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))]
     return any(os.path.getmtime(d) > t for d in deps)
 

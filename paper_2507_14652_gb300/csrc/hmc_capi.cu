@@ -2,6 +2,8 @@
 // trajectory kernels that implement Algorithm 1 on the sampled subset
 // (Algorithm 2): momentum draw, leapfrog kicks/drifts with the scatter of q into
 // the network, kinetic energy and the Metropolis step.
+#include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -27,25 +29,58 @@ void set_error(const char *fmt, ...)
     g_err = buf;
 }
 
+// Bytes held by DevBufs, and the cap hmc_diag_set_memory_cap may put on them.
+std::atomic<size_t> g_devbuf_bytes{0};
+std::atomic<size_t> g_devbuf_cap{~size_t(0)};
+
+static void devbuf_free(void *&ptr, size_t n, bool own)
+{
+    if (ptr && own) {
+        cudaFree(ptr);
+        g_devbuf_bytes -= n;
+    }
+    ptr = nullptr;
+}
+
 void DevBuf::alloc(size_t bytes)
 {
-    if (ptr) {
-        cudaFree(ptr);
-        ptr = nullptr;
-    }
-    n = bytes;
+    devbuf_free(ptr, n, own);
+    own = true;
+    n = 0;
     if (bytes == 0) return;
+    if (g_devbuf_bytes + bytes > g_devbuf_cap) {
+        set_error("device allocation of %zu bytes exceeds the memory cap of %zu bytes", bytes, (size_t)g_devbuf_cap);
+        throw Fail{HMC_ERR_OOM};
+    }
     cudaError_t e = cudaMalloc(&ptr, bytes);
     if (e != cudaSuccess) {
         ptr = nullptr;
         set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
         throw Fail{e == cudaErrorMemoryAllocation ? HMC_ERR_OOM : HMC_ERR_CUDA};
     }
+    n = bytes;
+    g_devbuf_bytes += bytes;
 }
 
-DevBuf::~DevBuf()
+DevBuf::~DevBuf() { devbuf_free(ptr, n, own); }
+
+void DevBuf::view(void *p, size_t bytes)
 {
-    if (ptr) cudaFree(ptr);
+    devbuf_free(ptr, n, own);
+    ptr = p;
+    n = bytes;
+    own = false;
+}
+
+void RowArena::take(DevBuf &dst, size_t bytes)
+{
+    if (next == slots.size()) slots.emplace_back(new DevBuf(bytes));
+    DevBuf &s = *slots[next++];
+    if (s.n < bytes) {
+        set_error("internal: a chunk engine asked for more row memory than the first (largest) chunk");
+        throw Fail{HMC_ERR_CUDA};
+    }
+    dst.view(s.ptr, bytes);
 }
 
 Profiler *&active_profiler()
@@ -112,18 +147,42 @@ struct TrajState {
     void *samples;            // outputs of the current hmc_sample call (device; may be null)
     unsigned char *accepted;
     double *dH;
+    double eps;               // step size of the trajectories (read by the captured kernels)
+    // dual averaging of log eps during a warm-up (Hoffman and Gelman 2014, Sec. 3.2)
+    long long da_m;           // updates so far
+    double da_hbar, da_log_eps_bar;
 };
 
-// Write q into the network buffer b at offset o of chain c (bf16 hi/lo pair or plain).
+// The kick and drift of one launch: eps / kick_div and eps / drift_div (a divisor of 0
+// means no kick, or no drift), eps read from device state when eps_p is set (captured
+// trajectories, so that a new step size needs no new graph), else the literal eps.
+struct Step {
+    const double *eps_p;
+    double eps;
+    double kick_div, drift_div;
+};
+
+__device__ __forceinline__ double step_eps(const Step &s) { return s.eps_p ? *s.eps_p : s.eps; }
+__device__ __forceinline__ double step_kick(const Step &s) { return s.kick_div != 0.0 ? step_eps(s) / s.kick_div : 0.0; }
+__device__ __forceinline__ double step_drift(const Step &s)
+{
+    return s.drift_div != 0.0 ? step_eps(s) / s.drift_div : 0.0;
+}
+
+// Write q into the network buffer b at offset o of chain c (bf16 or fp16 hi/lo pair, or plain).
 template <typename T>
 __device__ __forceinline__ void scatter_at(const ScatterPlan &sc, long c, int b, long off, T q)
 {
     const long o = c * sc.cstride[b] + off;
-    if (sc.is_bf16[b]) {
+    if (sc.kind16[b] == 1) {
         const __nv_bfloat16 hi = __float2bfloat16_rn((float)q);
         reinterpret_cast<__nv_bfloat16 *>(sc.base[b])[o] = hi;
         if (sc.base_lo[b])
             reinterpret_cast<__nv_bfloat16 *>(sc.base_lo[b])[o] = __float2bfloat16_rn((float)q - __bfloat162float(hi));
+    } else if (sc.kind16[b] == 2) {
+        const __half hi = __float2half_rn((float)q);
+        reinterpret_cast<__half *>(sc.base[b])[o] = hi;
+        if (sc.base_lo[b]) reinterpret_cast<__half *>(sc.base_lo[b])[o] = __float2half_rn((float)q - __half2float(hi));
     } else {
         reinterpret_cast<T *>(sc.base[b])[o] = q;
     }
@@ -163,12 +222,11 @@ __device__ __forceinline__ void load_seg(SegDesc &dst, const SegDesc *src)
 }
 
 // p ~ N(0, I); partial sums of p.p; first half kick p -= eps/2 g; first drift q* = q + drift p
-// (drift = eps for the leapfrog); scatter q*.
+// (drift = eps for the leapfrog); scatter q*.  stp gives the kick eps/2 and the drift.
 template <typename T>
 __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_begin(const SegDesc *segs, int C, int nblk, const T *q_cur,
                                                              const T *g_cur, T *q_prop, T *p, double *K0p,
-                                                             double eps, double drift, uint64_t seed,
-                                                             const TrajState *st)
+                                                             Step stp, uint64_t seed, const TrajState *st)
 {
     __shared__ __align__(16) unsigned char sd_raw[sizeof(SegDesc)];
     SegDesc &sd = *reinterpret_cast<SegDesc *>(sd_raw);
@@ -182,7 +240,7 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_begin(const SegDesc *segs
     if (j0 < sd.k) {
         const long base = sd.qoff + (long)c * sd.k;
         const uint64_t traj = (uint64_t)st->traj;
-        const T h = (T)(0.5 * eps), e = (T)drift;
+        const T h = (T)step_kick(stp), e = (T)step_drift(stp);
         const long blk = j0 / 4 + threadIdx.x;
         if (blk * 4 < sd.k) {
             double z[4];
@@ -208,7 +266,7 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_begin(const SegDesc *segs
 // p -= kick g; q += drift p; scatter q.
 template <typename T>
 __global__ void __launch_bounds__(TRAJ_THREADS) k_kick_drift(const SegDesc *segs, int C, const T *g, T *p, T *q,
-                                                             double kick, double drift)
+                                                             Step stp)
 {
     __shared__ __align__(16) unsigned char sd_raw[sizeof(SegDesc)];
     SegDesc &sd = *reinterpret_cast<SegDesc *>(sd_raw);
@@ -217,7 +275,8 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_kick_drift(const SegDesc *segs
     const int s = blockIdx.y, pi = s / C, c = s % C;
     load_seg(sd, &segs[pi]);
     const long base = sd.qoff + (long)c * sd.k;
-    const T kk = (T)kick, dd = (T)drift;
+    const bool kick = stp.kick_div != 0.0, drift = stp.drift_div != 0.0;
+    const T kk = (T)step_kick(stp), dd = (T)step_drift(stp);
     const long j0 = (long)blockIdx.x * TRAJ_ELEMS;
     // every load of the thread's four coordinates first, then the dependent updates
     T pv[4], gv[4], qv[4];
@@ -231,8 +290,8 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_kick_drift(const SegDesc *segs
         ov[t] = 0;
         if (j < sd.k) {
             pv[t] = p[base + j];
-            if (kick != 0.0) gv[t] = g[base + j];
-            if (drift != 0.0) {
+            if (kick) gv[t] = g[base + j];
+            if (drift) {
                 qv[t] = q[base + j];
                 bv[t] = sd.sc.buf_id ? (int)sd.sc.buf_id[j] : 0;
                 ov[t] = (long)sd.sc.off[j];
@@ -244,9 +303,9 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_kick_drift(const SegDesc *segs
         const long j = j0 + threadIdx.x + (long)t * TRAJ_THREADS;
         if (j >= sd.k) break;
         T pj = pv[t];
-        if (kick != 0.0) pj = pj - kk * gv[t];
+        if (kick) pj = pj - kk * gv[t];
         p[base + j] = pj;
-        if (drift != 0.0) {
+        if (drift) {
             const T qj = qv[t] + dd * pj;
             q[base + j] = qj;
             scatter_at<T>(sd.sc, c, bv[t], ov[t], qj);
@@ -257,7 +316,7 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_kick_drift(const SegDesc *segs
 // Last half kick (p itself is not needed afterwards) and partial sums of p.p.
 template <typename T>
 __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_kinetic(const SegDesc *segs, int C, int nblk, const T *p,
-                                                               const T *g_prop, double *K1p, double eps)
+                                                               const T *g_prop, double *K1p, Step stp)
 {
     __shared__ double sm[8];
     pdl_wait();
@@ -265,7 +324,7 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_kinetic(const SegDesc *se
     const int s = blockIdx.y, pi = s / C, c = s % C;
     const long k = segs[pi].k;
     const long base = segs[pi].qoff + (long)c * k;
-    const T h = (T)(0.5 * eps);
+    const T h = (T)step_kick(stp);
     const long j0 = (long)blockIdx.x * TRAJ_ELEMS;
     double kin = 0.0;
 #pragma unroll
@@ -345,14 +404,58 @@ __global__ void k_traj_advance(TrajState *st, int nseg, const int *acc_int, doub
 }
 
 __global__ void k_set_state(TrajState *st, long long traj, long long slot, void *samples, unsigned char *acc,
-                            double *dH)
+                            double *dH, double eps)
 {
     st->traj = traj;
     st->slot = slot;
     st->samples = samples;
     st->accepted = acc;
     st->dH = dH;
+    st->eps = eps;
+    st->da_m = 0;
+    st->da_hbar = 0.0;
+    st->da_log_eps_bar = 0.0;
 }
+
+// One dual-averaging update (Hoffman and Gelman 2014, Sec. 3.2, their Algorithm 5
+// without the NUTS parts) after trajectory slot - 1 of a warm-up: the statistic is the
+// mean over all nseg segments of min(1, exp(-dH)) (a non-finite dH counts as 0),
+// summed in a fixed order; the new step is written to st->eps for the next
+// trajectory.  trace[2 m - 2] = exp(log eps_m), trace[2 m - 1] = exp(log eps-bar_m).
+__global__ void __launch_bounds__(256) k_dual_avg(TrajState *st, int nseg, double target, double mu, double gamma,
+                                                  double t0, double kappa, double *trace)
+{
+    __shared__ double sm[256];
+    const double *dh = st->dH + (st->slot - 1) * (long long)nseg;
+    double a = 0.0;
+    for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+        const double v = dh[s];
+        a += isfinite(v) ? fmin(1.0, exp(-v)) : 0.0;
+    }
+    sm[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < (int)blockDim.x; ++i) tot += sm[i];
+        const double abar = tot / (double)nseg;
+        const long long m = ++st->da_m;
+        const double w = 1.0 / ((double)m + t0);
+        const double hbar = (1.0 - w) * st->da_hbar + w * (target - abar);
+        const double log_eps = mu - sqrt((double)m) / gamma * hbar;
+        const double eta = pow((double)m, -kappa);
+        const double lbar = eta * log_eps + (1.0 - eta) * st->da_log_eps_bar;
+        st->da_hbar = hbar;
+        st->da_log_eps_bar = lbar;
+        st->eps = exp(log_eps);
+        if (trace) {
+            trace[2 * (m - 1)] = exp(log_eps);
+            trace[2 * (m - 1) + 1] = exp(lbar);
+        }
+    }
+}
+
+__global__ void k_rewind_slot(TrajState *st) { st->slot = 0; }
+__global__ void k_advance_slot(TrajState *st) { st->slot += 1; }
 
 __global__ void k_debug_momenta(uint64_t seed, uint64_t problem, uint64_t chain, uint64_t traj, long k, double *out)
 {
@@ -429,6 +532,11 @@ struct hmc_handle_s {
     // split handles (hmc_create_split): one problem whose data rows are cut into
     // nsplit batches, engines[m] holding batch m with 1/nsplit of the prior
     int nsplit = 1;
+    // chunked handles (hmc_create_chunked): the same per-batch engines, integrated by the
+    // full-batch leapfrog with U and grad U summed over the batches, which share one
+    // arena of row buffers
+    bool chunked = false;
+    std::unique_ptr<RowArena> arena;
     DevBuf U_split, g_tmp;
     std::vector<long> qoff;
     long k_total = 0, P_total = 0, S_total = 0;
@@ -438,12 +546,14 @@ struct hmc_handle_s {
     // memory on every call would synchronise the device twice per call)
     std::vector<std::unique_ptr<DevBuf>> stage;
     size_t stage_used = 0;
-    // one trajectory as an executable graph, reused while (eps, L, seed) stay the same
+    // one trajectory as an executable graph, reused while (L, seed) stay the same
     cudaGraphExec_t traj_exec = nullptr;
-    double traj_eps = 0.0;
     int traj_L = -1;
     unsigned long long traj_seed = 0;
     long traj_kernels = 0;     // kernel nodes in that graph
+    long traj_captures = 0;    // graphs captured so far
+    DevBuf adapt_trace;        // [n][2] step sizes of the last warm-up (hmc_diag_adapt_trace)
+    long adapt_n = 0;
     ~hmc_handle_s()
     {
         if (traj_exec) cudaGraphExecDestroy(traj_exec);
@@ -646,17 +756,17 @@ void *dev_view(hmc_handle h, const void *user, size_t bytes, bool in, bool *stag
     return d;
 }
 
-void kick_drift(hmc_handle h, void *q, void *p, const void *g, double kick, double drift)
+void kick_drift(hmc_handle h, void *q, void *p, const void *g, Step stp)
 {
     const int nseg = h->nprob * h->C;
     const SegDesc *sd = h->segs.as<SegDesc>();
     const dim3 grid(h->traj_nblk, nseg);
     if (h->prec == HMC_PREC_FP64)
         launch_pdl(k_kick_drift<double>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, (const double *)g,
-                   (double *)p, (double *)q, kick, drift);
+                   (double *)p, (double *)q, stp);
     else
         launch_pdl(k_kick_drift<float>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, (const float *)g,
-                   (float *)p, (float *)q, kick, drift);
+                   (float *)p, (float *)q, stp);
     HMC_LAUNCH_CK();
 }
 
@@ -726,43 +836,47 @@ void split_start(hmc_handle h, const void *q, double *U, void *g1)
 
 // L split steps on (q, p).  On entry p has had the first half kick with grad U_1 and q
 // its first drift; on exit g1 = grad U_1(q_end) and U_split[0] = U_1(q_end), and the
-// final half kick is still to be applied.
-void split_steps(hmc_handle h, void *q, void *p, void *g1, double eps, int L)
+// final half kick is still to be applied.  The step is *eps_p when eps_p is set (a
+// captured trajectory), else eps; the drifts are eps/(2M) (eps/M where two meet).
+void split_steps(hmc_handle h, void *q, void *p, void *g1, const double *eps_p, double eps, int L)
 {
     const int M = h->nsplit;
-    const double d = eps / (2.0 * M), d0 = M == 1 ? eps : d;
+    const double dd = 2.0 * M, d0 = M == 1 ? 1.0 : dd;
     for (int s = 1; s <= L; ++s) {
         for (int m = 1; m < M; ++m) {   // forward sweep, batches 2..M
             split_grad(h, m, q, h->g_tmp.ptr);
-            kick_drift(h, q, p, h->g_tmp.ptr, 0.5 * eps, m < M - 1 ? d : 2.0 * d);
+            kick_drift(h, q, p, h->g_tmp.ptr, Step{eps_p, eps, 2.0, m < M - 1 ? dd : (double)M});
         }
         for (int m = M - 1; m >= 1; --m) {   // backward sweep, batches M..2
             split_grad(h, m, q, h->g_tmp.ptr);
-            kick_drift(h, q, p, h->g_tmp.ptr, 0.5 * eps, d);
+            kick_drift(h, q, p, h->g_tmp.ptr, Step{eps_p, eps, 2.0, dd});
         }
         split_grad(h, 0, q, g1);
-        if (s < L) kick_drift(h, q, p, g1, eps, d0);
+        if (s < L) kick_drift(h, q, p, g1, Step{eps_p, eps, 1.0, d0});
     }
 }
 
-template <typename T> void enqueue_split_trajectory(hmc_handle h, double eps, int L, uint64_t seed)
+// The step size of a captured trajectory is read from the device state (TrajState::eps),
+// so one graph serves every step size.
+template <typename T> void enqueue_split_trajectory(hmc_handle h, int L, uint64_t seed)
 {
     const int nseg = h->C, nblk = h->traj_nblk, M = h->nsplit;
     const SegDesc *sd = h->segs.as<SegDesc>();
     TrajState *st = h->state.as<TrajState>();
+    const double *ep = &st->eps;
     const dim3 grid(nblk, nseg);
-    const double d0 = M == 1 ? eps : eps / (2.0 * M);
     launch_pdl(k_traj_begin<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, h->q_cur.as<T>(),
-               h->g_cur.as<T>(), h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(), eps, d0, seed, st);
+               h->g_cur.as<T>(), h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(),
+               Step{ep, 0.0, 2.0, M == 1 ? 1.0 : 2.0 * M}, seed, st);
     HMC_LAUNCH_CK();
-    split_steps(h, h->q_prop.ptr, h->p.ptr, h->g_prop.ptr, eps, L);
+    split_steps(h, h->q_prop.ptr, h->p.ptr, h->g_prop.ptr, ep, 0.0, L);
     // H1: the other batches' energies at the end point (batch 1's came with its gradient)
     for (int m = M - 1; m >= 1; --m) split_energy(h, m, h->q_prop.ptr);
     if (h->engines[0]->has_accurate_energy())
         h->engines[0]->accurate_energy(h->q_prop.ptr, h->U_split.as<double>(), h->stream);
     split_sum(h, h->U_prop.as<double>());
     launch_pdl(k_traj_kinetic<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, h->p.as<T>(),
-               h->g_prop.as<T>(), h->K1p.as<double>(), eps);
+               h->g_prop.as<T>(), h->K1p.as<double>(), Step{ep, 0.0, 2.0, 0.0});
     HMC_LAUNCH_CK();
     launch_pdl(k_traj_accept<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, nseg, h->S_total,
                h->q_cur.as<T>(), h->g_cur.as<T>(), h->U_cur.as<double>(), h->q_prop.as<T>(), h->g_prop.as<T>(),
@@ -773,30 +887,32 @@ template <typename T> void enqueue_split_trajectory(hmc_handle h, double eps, in
     HMC_LAUNCH_CK();
 }
 
-template <typename T> void enqueue_trajectory(hmc_handle h, double eps, int L, uint64_t seed)
+template <typename T> void enqueue_trajectory(hmc_handle h, int L, uint64_t seed)
 {
-    if (h->nsplit > 1) {
-        enqueue_split_trajectory<T>(h, eps, L, seed);
+    if (h->nsplit > 1 && !h->chunked) {
+        enqueue_split_trajectory<T>(h, L, seed);
         return;
     }
     const int nseg = h->nprob * h->C, nblk = h->traj_nblk;
     const SegDesc *sd = h->segs.as<SegDesc>();
     TrajState *st = h->state.as<TrajState>();
+    const double *ep = &st->eps;
     const dim3 grid(nblk, nseg);
     launch_pdl(k_traj_begin<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, h->q_cur.as<T>(),
-               h->g_cur.as<T>(), h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(), eps, eps, seed, st);
+               h->g_cur.as<T>(), h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(), Step{ep, 0.0, 2.0, 1.0}, seed,
+               st);
     HMC_LAUNCH_CK();
     for (int s = 1; s <= L; ++s) {
         energy_grad_all(h, h->q_prop.ptr, h->U_prop.as<double>(), h->g_prop.ptr, true);
         if (s == L) accurate_energy_all(h, h->q_prop.ptr, h->U_prop.as<double>());   // H1 for the Metropolis test
         if (s < L) {
             launch_pdl(k_kick_drift<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, h->g_prop.as<T>(),
-                       h->p.as<T>(), h->q_prop.as<T>(), eps, eps);
+                       h->p.as<T>(), h->q_prop.as<T>(), Step{ep, 0.0, 1.0, 1.0});
             HMC_LAUNCH_CK();
         }
     }
     launch_pdl(k_traj_kinetic<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, h->p.as<T>(),
-               h->g_prop.as<T>(), h->K1p.as<double>(), eps);
+               h->g_prop.as<T>(), h->K1p.as<double>(), Step{ep, 0.0, 2.0, 0.0});
     HMC_LAUNCH_CK();
     launch_pdl(k_traj_accept<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, nseg, h->S_total,
                h->q_cur.as<T>(), h->g_cur.as<T>(), h->U_cur.as<double>(), h->q_prop.as<T>(), h->g_prop.as<T>(),
@@ -821,14 +937,16 @@ Engine *make_engine(Problem &p, int prec, int C, bool in_batch = false)
     if (no_data) return make_prior_engine(p, prec, C);
     if (prec == HMC_PREC_FP64) return make_simt_engine_f64(p, C);
     if (prec == HMC_PREC_FP32) return make_simt_engine_f32(p, C);
-    if (prec == HMC_PREC_BF16) {
+    if (prec == HMC_PREC_BF16 || prec == HMC_PREC_FP16) {
         std::string why;
         const bool don = p.kind != HMC_NET_MLP;
         if (!(don ? don_engine_supports(p, &why) : umma_engine_supports(p, &why))) {
             if (in_batch) return make_simt_engine_f32(p, C);
-            set_error("BF16 tensor-core path does not support this network: %s", why.c_str());
+            set_error("%s tensor-core path does not support this network: %s",
+                      prec == HMC_PREC_BF16 ? "BF16" : "FP16", why.c_str());
             throw Fail{HMC_ERR_UNSUPPORTED};
         }
+        if (prec == HMC_PREC_FP16) return don ? make_don_engine_f16(p, C) : make_umma_engine_f16(p, C);
         return don ? make_don_engine_bf16(p, C) : make_umma_engine_bf16(p, C);
     }
     set_error("unknown precision %d", prec);
@@ -863,7 +981,7 @@ std::unique_ptr<Problem> batch_problem(const Problem &full, int M, int m)
 
 hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, const hmc_data *data,
                        const double *alpha, const double *sigma, const unsigned char *const *masks,
-                       const double *const *frozen, int C, void *stream, int nsplit = 1)
+                       const double *const *frozen, int C, void *stream, int nsplit = 1, bool chunked = false)
 {
     HMC_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
@@ -871,7 +989,7 @@ hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, co
     HMC_REQUIRE(specs && data && alpha && sigma && masks && frozen, "NULL argument");
     HMC_REQUIRE(C >= 1 && C <= 65535, "n_chains must be in [1, 65535]");
     const int prec = specs[0].prec;
-    HMC_REQUIRE(prec >= HMC_PREC_FP64 && prec <= HMC_PREC_BF16, "unknown precision %d", prec);
+    HMC_REQUIRE(prec >= HMC_PREC_FP64 && prec <= HMC_PREC_FP16, "unknown precision %d", prec);
     for (int i = 0; i < nprob; ++i) HMC_REQUIRE(specs[i].prec == prec, "all problems of a batch share one precision");
     std::unique_ptr<hmc_handle_s> h(new hmc_handle_s);
     h->prec = prec;
@@ -894,18 +1012,30 @@ hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, co
             HMC_CK(cudaEventCreateWithFlags(&h->ev_join[j], cudaEventDisableTiming));
         }
     }
-    HMC_REQUIRE(nsplit >= 1 && nsplit <= HMC_MAX_SPLITS, "n_splits must be in [1, %d]", HMC_MAX_SPLITS);
+    HMC_REQUIRE(nsplit >= 1 && nsplit <= (chunked ? (1 << 20) : HMC_MAX_SPLITS), "n_splits must be in [1, %d]",
+                HMC_MAX_SPLITS);
     HMC_REQUIRE(nsplit == 1 || nprob == 1, "a split handle holds one problem");
     h->nsplit = nsplit;
+    h->chunked = chunked && nsplit > 1;
     if (nsplit > 1) {
         auto full = build_problem(specs[0], data[0], alpha[0], sigma[0], masks[0], frozen[0], C);
         const long R = full->kind == HMC_NET_MLP ? full->n : full->n_u;
         HMC_REQUIRE(R >= nsplit, "n_splits (%d) exceeds the number of data rows (%ld)", nsplit, R);
-        for (int m = 0; m < nsplit; ++m) {
-            h->probs.push_back(batch_problem(*full, nsplit, m));
-            Problem &p = *h->probs.back();
+        if (h->chunked) h->arena.reset(new RowArena());
+        // chunk engines take their row buffers from the arena: the largest chunk comes first
+        std::vector<int> order(nsplit);
+        for (int m = 0; m < nsplit; ++m) order[m] = m;
+        auto rows = [&](int m) { return (long)((__int128)R * (m + 1) / nsplit) - (long)((__int128)R * m / nsplit); };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rows(a) > rows(b); });
+        h->probs.resize(nsplit);
+        h->engines.resize(nsplit);
+        for (int m : order) {
+            h->probs[m] = batch_problem(*full, nsplit, m);
+            Problem &p = *h->probs[m];
+            p.arena = h->arena.get();
+            if (p.arena) p.arena->begin();
             Engine *e = make_engine(p, prec, C);
-            h->engines.emplace_back(e);
+            h->engines[m].reset(e);
             p.engine = e;
         }
         h->qoff.push_back(0);
@@ -981,11 +1111,46 @@ hmc_status hmc_create(hmc_handle *out, const hmc_net_spec *spec, const hmc_data 
                       int n_chains, void *cuda_stream)
 {
     g_err.clear();
-    return guarded([&] {
+    hmc_status st = guarded([&] {
         return create_impl(out, 1, spec, data, &prior_sigma, &noise_sigma, &subset_mask, &frozen_params, n_chains,
                            cuda_stream);
     });
+    if (st != HMC_ERR_OOM || !spec || !data) return st;
+    // the whole batch's row buffers do not fit: evaluate the rows in passes, halving the
+    // rows of a pass until the handle fits (the energy and its gradient are sums over rows)
+    const long R = spec->kind == HMC_NET_MLP ? data->n : data->n_u;
+    for (long M = 2; M <= R && st == HMC_ERR_OOM; M *= 2) {
+        cudaGetLastError();   // the failed allocation's error is not sticky; clear it
+        g_err.clear();
+        st = guarded([&] {
+            return create_impl(out, 1, spec, data, &prior_sigma, &noise_sigma, &subset_mask, &frozen_params,
+                               n_chains, cuda_stream, (int)M, true);
+        });
+    }
+    return st;
 }
+
+hmc_status hmc_create_chunked(hmc_handle *out, const hmc_net_spec *spec, const hmc_data *data, double prior_sigma,
+                              double noise_sigma, const unsigned char *subset_mask, const double *frozen_params,
+                              int n_chains, long rows_per_pass, void *cuda_stream)
+{
+    g_err.clear();
+    return guarded([&] {
+        HMC_REQUIRE(spec && data, "NULL argument");
+        HMC_REQUIRE(rows_per_pass >= 1, "rows_per_pass must be >= 1");
+        const long R = spec->kind == HMC_NET_MLP ? data->n : data->n_u;
+        const long M = std::max<long>(1, (R + rows_per_pass - 1) / rows_per_pass);
+        HMC_REQUIRE(M <= (1 << 20), "too many passes (%ld)", M);
+        return create_impl(out, 1, spec, data, &prior_sigma, &noise_sigma, &subset_mask, &frozen_params, n_chains,
+                           cuda_stream, (int)M, true);
+    });
+}
+
+int hmc_num_passes(hmc_handle h) { return h ? (h->chunked ? h->nsplit : 1) : -1; }
+
+void hmc_diag_set_memory_cap(long bytes) { g_devbuf_cap = bytes > 0 ? (size_t)bytes : ~size_t(0); }
+
+long hmc_diag_device_bytes(void) { return (long)g_devbuf_bytes.load(); }
 
 hmc_status hmc_create_split(hmc_handle *out, const hmc_net_spec *spec, const hmc_data *data, double prior_sigma,
                             double noise_sigma, const unsigned char *subset_mask, const double *frozen_params,
@@ -1206,19 +1371,18 @@ hmc_status hmc_leapfrog(hmc_handle h, void *q, void *p, double eps, int L)
         bool sq, sp;
         void *dq = dev_view(h, q, sb, true, &sq);
         void *dp = dev_view(h, p, sb, true, &sp);
-        if (L > 0 && h->nsplit > 1) {
-            const double d0 = eps / (2.0 * h->nsplit);
+        if (L > 0 && h->nsplit > 1 && !h->chunked) {
             split_grad(h, 0, dq, h->g_prop.ptr);
-            kick_drift(h, dq, dp, h->g_prop.ptr, 0.5 * eps, d0);
-            split_steps(h, dq, dp, h->g_prop.ptr, eps, L);
-            kick_drift(h, dq, dp, h->g_prop.ptr, 0.5 * eps, 0.0);
+            kick_drift(h, dq, dp, h->g_prop.ptr, Step{nullptr, eps, 2.0, 2.0 * h->nsplit});
+            split_steps(h, dq, dp, h->g_prop.ptr, nullptr, eps, L);
+            kick_drift(h, dq, dp, h->g_prop.ptr, Step{nullptr, eps, 2.0, 0.0});
         } else if (L > 0) {
             energy_grad_all(h, dq, h->U_prop.as<double>(), h->g_prop.ptr, false);
-            kick_drift(h, dq, dp, h->g_prop.ptr, 0.5 * eps, eps);
+            kick_drift(h, dq, dp, h->g_prop.ptr, Step{nullptr, eps, 2.0, 1.0});
             for (int s = 1; s <= L; ++s) {
                 energy_grad_all(h, dq, h->U_prop.as<double>(), h->g_prop.ptr, true);
-                if (s < L) kick_drift(h, dq, dp, h->g_prop.ptr, eps, eps);
-                else kick_drift(h, dq, dp, h->g_prop.ptr, 0.5 * eps, 0.0);
+                if (s < L) kick_drift(h, dq, dp, h->g_prop.ptr, Step{nullptr, eps, 1.0, 1.0});
+                else kick_drift(h, dq, dp, h->g_prop.ptr, Step{nullptr, eps, 2.0, 0.0});
             }
         }
         if (sq) HMC_CK(cudaMemcpyAsync(q, dq, sb, cudaMemcpyDeviceToHost, h->stream));
@@ -1227,6 +1391,46 @@ hmc_status hmc_leapfrog(hmc_handle h, void *q, void *p, double eps, int L)
         if (sq || sp) HMC_CK(cudaStreamSynchronize(h->stream));
         return HMC_OK;
     });
+}
+
+// The executable graph of one trajectory, captured once per (L, seed) and reused; the
+// step size lives in the device state, so it does not enter the graph.
+void ensure_trajectory_graph(hmc_handle h, int L, unsigned long long seed)
+{
+    if (h->traj_exec && h->traj_L == L && h->traj_seed == seed) return;
+    if (h->traj_exec) {
+        cudaGraphExecDestroy(h->traj_exec);
+        h->traj_exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    HMC_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    try {
+        if (h->prec == HMC_PREC_FP64) enqueue_trajectory<double>(h, L, seed);
+        else enqueue_trajectory<float>(h, L, seed);
+    } catch (...) {
+        cudaStreamEndCapture(h->stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+    }
+    HMC_CK(cudaStreamEndCapture(h->stream, &graph));
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    long nk = 0;
+    if (nn) {
+        cudaGraphGetNodes(graph, nodes.data(), &nn);
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+        }
+    }
+    cudaError_t e = cudaGraphInstantiate(&h->traj_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    HMC_CK(e);
+    h->traj_L = L;
+    h->traj_seed = seed;
+    h->traj_kernels = nk;
+    ++h->traj_captures;
 }
 
 hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_samples, unsigned long long seed,
@@ -1248,50 +1452,16 @@ hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_sa
         unsigned char *da = static_cast<unsigned char *>(dev_view(h, accepted, (size_t)nseg * n_samples, false, &sa));
         double *ddh = static_cast<double *>(dev_view(h, dH, sizeof(double) * nseg * n_samples, false, &sd));
         void *dl = dev_view(h, q_last, sb, false, &sl);
-        if (h->nsplit > 1) {   // U for H0 and grad U of the first batch for the first kick
+        if (h->nsplit > 1 && !h->chunked) {   // U for H0 and grad U of the first batch for the first kick
             split_start(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr);
         } else {
             energy_grad_all(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr, false);
             accurate_energy_all(h, h->q_cur.ptr, h->U_cur.as<double>());   // H0 of the first trajectory
         }
-        k_set_state<<<1, 1, 0, h->stream>>>(h->state.as<TrajState>(), first_traj, 0, ds, da, ddh);
+        k_set_state<<<1, 1, 0, h->stream>>>(h->state.as<TrajState>(), first_traj, 0, ds, da, ddh, eps);
         HMC_LAUNCH_CK();
         if (n_samples > 0) {
-            if (!h->traj_exec || h->traj_eps != eps || h->traj_L != L || h->traj_seed != seed) {
-                if (h->traj_exec) {
-                    cudaGraphExecDestroy(h->traj_exec);
-                    h->traj_exec = nullptr;
-                }
-                cudaGraph_t graph = nullptr;
-                HMC_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-                try {
-                    if (h->prec == HMC_PREC_FP64) enqueue_trajectory<double>(h, eps, L, seed);
-                    else enqueue_trajectory<float>(h, eps, L, seed);
-                } catch (...) {
-                    cudaStreamEndCapture(h->stream, &graph);
-                    if (graph) cudaGraphDestroy(graph);
-                    throw;
-                }
-                HMC_CK(cudaStreamEndCapture(h->stream, &graph));
-                size_t nn = 0;
-                cudaGraphGetNodes(graph, nullptr, &nn);
-                std::vector<cudaGraphNode_t> nodes(nn);
-                long nk = 0;
-                if (nn) {
-                    cudaGraphGetNodes(graph, nodes.data(), &nn);
-                    for (auto nd : nodes) {
-                        cudaGraphNodeType t;
-                        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
-                    }
-                }
-                cudaError_t e = cudaGraphInstantiate(&h->traj_exec, graph, 0);
-                cudaGraphDestroy(graph);
-                HMC_CK(e);
-                h->traj_eps = eps;
-                h->traj_L = L;
-                h->traj_seed = seed;
-                h->traj_kernels = nk;
-            }
+            ensure_trajectory_graph(h, L, seed);
             for (long i = 0; i < n_samples; ++i) HMC_CK(cudaGraphLaunch(h->traj_exec, h->stream));
         }
         if (dl) HMC_CK(cudaMemcpyAsync(dl, h->q_cur.ptr, sb, cudaMemcpyDeviceToDevice, h->stream));
@@ -1314,36 +1484,84 @@ hmc_status hmc_adapt_step_size(hmc_handle h, void *q, int L, double eps0, long n
         HMC_REQUIRE(L >= 1 && n_warmup >= 1 && first_traj >= 0 && std::isfinite(eps0) && eps0 > 0,
                     "need L >= 1, n_warmup >= 1, eps0 > 0, first_traj >= 0");
         HMC_REQUIRE(target_accept > 0.0 && target_accept < 1.0, "target_accept must lie in (0, 1)");
+        h->stage_used = 0;
+        join_in(h);
         const long nseg = (long)h->nprob * h->C;
         const size_t sb = h->elem * (size_t)h->S_total;
-        const bool on_host = !is_device_ptr(q);
-        DevBuf state(sb), dh_dev(sizeof(double) * nseg);
-        if (on_host) HMC_CK(cudaMemcpy(state.ptr, q, sb, cudaMemcpyHostToDevice));
-        void *dq = on_host ? state.ptr : q;
-        std::vector<double> dh(nseg);
+        bool sq;
+        void *dq = dev_view(h, q, sb, true, &sq);
+        if (h->adapt_trace.n < sizeof(double) * 2 * (size_t)n_warmup)
+            h->adapt_trace.alloc(sizeof(double) * 2 * (size_t)n_warmup);
+        DevBuf dh_dev(sizeof(double) * nseg);
+        TrajState *st = h->state.as<TrajState>();
+        HMC_CK(cudaMemcpyAsync(h->q_cur.ptr, dq, sb, cudaMemcpyDeviceToDevice, h->stream));
+        if (h->nsplit > 1 && !h->chunked) {
+            split_start(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr);
+        } else {
+            energy_grad_all(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr, false);
+            accurate_energy_all(h, h->q_cur.ptr, h->U_cur.as<double>());
+        }
+        k_set_state<<<1, 1, 0, h->stream>>>(st, first_traj, 0, nullptr, nullptr, dh_dev.as<double>(), eps0);
+        HMC_LAUNCH_CK();
+        ensure_trajectory_graph(h, L, seed);
         // Dual averaging of log eps (Hoffman and Gelman 2014, Sec. 3.2) towards a mean
         // Metropolis acceptance probability `target_accept` over all chains; shrinkage
-        // towards log(10 eps0), gamma = 0.05, t0 = 10, kappa = 0.75.  The returned step is
-        // the averaged iterate.
+        // towards log(10 eps0), gamma = 0.05, t0 = 10, kappa = 0.75.  Each update runs on
+        // the device after its trajectory and sets the next trajectory's step in the
+        // device state, so the warm-up replays one captured graph without host round
+        // trips.  The returned step is the averaged iterate.
         const double mu = std::log(10.0 * eps0), gamma = 0.05, t0 = 10.0, kappa = 0.75;
-        double hbar = 0.0, log_eps = std::log(eps0), log_eps_bar = 0.0;
         for (long m = 1; m <= n_warmup; ++m) {
-            const hmc_status st = hmc_sample(h, dq, std::exp(log_eps), L, 1, seed, first_traj + m - 1, nullptr, nullptr,
-                                             dh_dev.as<double>(), dq);
-            if (st != HMC_OK) return st;
-            HMC_CK(cudaMemcpyAsync(dh.data(), dh_dev.ptr, sizeof(double) * nseg, cudaMemcpyDeviceToHost, h->stream));
-            HMC_CK(cudaStreamSynchronize(h->stream));
-            double a = 0.0;
-            for (long i = 0; i < nseg; ++i) a += std::isfinite(dh[i]) ? std::min(1.0, std::exp(-dh[i])) : 0.0;
-            a /= (double)nseg;
-            const double w = 1.0 / ((double)m + t0);
-            hbar = (1.0 - w) * hbar + w * (target_accept - a);
-            log_eps = mu - std::sqrt((double)m) / gamma * hbar;
-            const double eta = std::pow((double)m, -kappa);
-            log_eps_bar = eta * log_eps + (1.0 - eta) * log_eps_bar;
+            HMC_CK(cudaGraphLaunch(h->traj_exec, h->stream));
+            k_dual_avg<<<1, 256, 0, h->stream>>>(st, (int)nseg, target_accept, mu, gamma, t0, kappa,
+                                                 h->adapt_trace.as<double>());
+            HMC_LAUNCH_CK();
+            k_rewind_slot<<<1, 1, 0, h->stream>>>(st);   // every trajectory's dH goes to slot 0
+            HMC_LAUNCH_CK();
         }
-        *eps_out = std::exp(log_eps_bar);
-        if (on_host) HMC_CK(cudaMemcpy(q, state.ptr, sb, cudaMemcpyDeviceToHost));
+        double lbar = 0.0;
+        HMC_CK(cudaMemcpyAsync(&lbar, &st->da_log_eps_bar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        HMC_CK(cudaMemcpyAsync(dq, h->q_cur.ptr, sb, cudaMemcpyDeviceToDevice, h->stream));
+        if (sq) HMC_CK(cudaMemcpyAsync(q, dq, sb, cudaMemcpyDeviceToHost, h->stream));
+        join_out(h);
+        HMC_CK(cudaStreamSynchronize(h->stream));
+        h->adapt_n = n_warmup;
+        *eps_out = std::exp(lbar);
+        return HMC_OK;
+    });
+}
+
+hmc_status hmc_diag_adapt_trace(hmc_handle h, double *out_host, long n)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(h && out_host, "NULL argument");
+        HMC_REQUIRE(n >= 0 && n <= h->adapt_n, "n (%ld) exceeds the last warm-up's %ld updates", n, h->adapt_n);
+        HMC_CK(cudaStreamSynchronize(h->stream));
+        if (n > 0)
+            HMC_CK(cudaMemcpy(out_host, h->adapt_trace.ptr, sizeof(double) * 2 * (size_t)n, cudaMemcpyDeviceToHost));
+        return HMC_OK;
+    });
+}
+
+hmc_status hmc_diag_dual_averaging(const double *dH, long n, int nseg, double eps0, double target, double *out_host)
+{
+    g_err.clear();
+    return guarded([&]() -> hmc_status {
+        HMC_REQUIRE(dH && out_host && n >= 1 && nseg >= 1 && eps0 > 0 && std::isfinite(eps0), "bad argument");
+        HMC_REQUIRE(target > 0.0 && target < 1.0, "target must lie in (0, 1)");
+        DevBuf st(sizeof(TrajState)), d(sizeof(double) * (size_t)n * nseg), tr(sizeof(double) * 2 * (size_t)n);
+        HMC_CK(cudaMemcpy(d.ptr, dH, d.n, cudaMemcpyDefault));
+        k_set_state<<<1, 1>>>(st.as<TrajState>(), 0, 0, nullptr, nullptr, d.as<double>(), eps0);
+        HMC_LAUNCH_CK();
+        const double mu = std::log(10.0 * eps0);
+        for (long m = 1; m <= n; ++m) {
+            k_advance_slot<<<1, 1>>>(st.as<TrajState>());   // as a trajectory would: dH row m - 1
+            HMC_LAUNCH_CK();
+            k_dual_avg<<<1, 256>>>(st.as<TrajState>(), nseg, target, mu, 0.05, 10.0, 0.75, tr.as<double>());
+            HMC_LAUNCH_CK();
+        }
+        HMC_CK(cudaMemcpy(out_host, tr.ptr, tr.n, cudaMemcpyDeviceToHost));
         return HMC_OK;
     });
 }
@@ -1412,6 +1630,8 @@ hmc_status hmc_diag_expire_wait(hmc_handle h, long limit_ns)
 }
 
 long hmc_diag_graph_kernels(hmc_handle h) { return h ? h->traj_kernels : -1; }
+
+long hmc_diag_graph_captures(hmc_handle h) { return h ? h->traj_captures : -1; }
 
 long hmc_diag_tuning(hmc_handle h, char *buf, long n)
 {

@@ -3,8 +3,10 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
+#include <memory>
 #include <utility>
 #include <string>
 #include <vector>
@@ -60,8 +62,8 @@ struct ScatterPlan {
     int nbuf = 0;
     void *base[MAX_SCATTER_BUFS] = {};
     long cstride[MAX_SCATTER_BUFS] = {};   // elements between chains
-    int is_bf16[MAX_SCATTER_BUFS] = {};
-    void *base_lo[MAX_SCATTER_BUFS] = {};  // bf16 buffers only: receives bf16(q - hi) when set
+    int kind16[MAX_SCATTER_BUFS] = {};     // element type: 0 float, 1 bf16, 2 fp16
+    void *base_lo[MAX_SCATTER_BUFS] = {};  // 16-bit buffers only: receives h16(q - hi) when set
     const uint8_t *buf_id = nullptr;       // [k] (nullptr: all in buffer 0)
     const int *off = nullptr;              // [k] element offset inside one chain's slice
 };
@@ -75,6 +77,7 @@ struct SegDesc {
 };
 
 struct Problem;
+struct RowArena;
 
 // Engine interface: U and grad U of one problem for all its chains.
 struct Engine {
@@ -115,6 +118,7 @@ struct Problem {
     std::vector<double> frozen;     // host copy
     std::vector<double> x, y, u, yq, t;   // host copies of the data (FP64)
     Engine *engine = nullptr;
+    RowArena *arena = nullptr;      // set for the chunk engines of a chunked handle
 };
 
 void build_net_desc(NetDesc &nd, const hmc_mlp_spec &s, long base, const std::vector<long> &idx);
@@ -123,8 +127,10 @@ void build_net_desc(NetDesc &nd, const hmc_mlp_spec &s, long base, const std::ve
 Engine *make_simt_engine_f64(Problem &p, int C);
 Engine *make_simt_engine_f32(Problem &p, int C);
 Engine *make_umma_engine_bf16(Problem &p, int C);
+Engine *make_umma_engine_f16(Problem &p, int C);
 bool umma_engine_supports(const Problem &p, std::string *why);
 Engine *make_don_engine_bf16(Problem &p, int C);
+Engine *make_don_engine_f16(Problem &p, int C);
 // One bounded device-side wait run out on purpose; it raises *err (hmc_diag_expire_wait).
 void expire_wait_run(int *err, long limit_ns, cudaStream_t s);
 
@@ -208,17 +214,47 @@ struct ProfScope {
     ~ProfScope();
 };
 
-// Device allocation helper that tracks bytes and frees on destruction.
+// Device allocation helper that tracks bytes and frees on destruction.  A view
+// (own = false) refers to memory another DevBuf owns and frees nothing.
 struct DevBuf {
     void *ptr = nullptr;
     size_t n = 0;
+    bool own = true;
     DevBuf() {}
     explicit DevBuf(size_t bytes) { alloc(bytes); }
     void alloc(size_t bytes);
+    void view(void *p, size_t bytes);
     ~DevBuf();
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
     template <typename T> T *as() const { return reinterpret_cast<T *>(ptr); }
 };
+
+// Device memory shared by the chunk engines of one handle (hmc_create_chunked).  They
+// evaluate their rows one after another on one stream, so every buffer whose size grows
+// with the rows (activations, deltas, operator outputs, split-K partials) is in use by one
+// engine at a time.  An engine's k-th request gets slot k; the engines are created
+// largest chunk first, so the first request of a slot fixes its size.
+struct RowArena {
+    std::vector<std::unique_ptr<DevBuf>> slots;
+    size_t next = 0;
+    void begin() { next = 0; }
+    // a view of the next slot, at least `bytes` long
+    void take(DevBuf &dst, size_t bytes);
+    size_t bytes() const
+    {
+        size_t b = 0;
+        for (auto &s : slots) b += s->n;
+        return b;
+    }
+};
+
+// A buffer that scales with the data rows: a view into the arena when the engine belongs
+// to a chunked handle, else memory of its own.
+inline void row_alloc(RowArena *arena, DevBuf &dst, size_t bytes)
+{
+    if (arena) arena->take(dst, bytes);
+    else dst.alloc(bytes);
+}
 
 }  // namespace hmc

@@ -162,8 +162,8 @@ template <typename T> class SimtEngine final : public Engine {
             upload(y_, p.y);
             alloc_net(p.net, p.n, netb_);
             long wmax = max_width(p.net);
-            delta_[0].alloc(sizeof(T) * C * p.n * wmax);
-            delta_[1].alloc(sizeof(T) * C * p.n * wmax);
+            row_alloc(p.arena, delta_[0], sizeof(T) * C * p.n * wmax);
+            row_alloc(p.arena, delta_[1], sizeof(T) * C * p.n * wmax);
             n_el_ = p.n * p.dout;
         } else {
             upload(u_, p.u);
@@ -174,18 +174,41 @@ template <typename T> class SimtEngine final : public Engine {
             alloc_net(p.branch, p.n_u, brb_);
             alloc_net(p.trunk, nt_, trb_);
             const int lat = p.branch.w[p.branch.L];
-            S_.alloc(sizeof(T) * C * std::max<long>(p.n_u * p.n_y, 1));
-            dB_.alloc(sizeof(T) * C * p.n_u * lat);
-            dT_.alloc(sizeof(T) * C * nt_ * lat);
+            row_alloc(p.arena, S_, sizeof(T) * C * std::max<long>(p.n_u * p.n_y, 1));
+            row_alloc(p.arena, dB_, sizeof(T) * C * p.n_u * lat);
+            row_alloc(p.arena, dT_, sizeof(T) * C * nt_ * lat);
             long wmax = std::max(max_width(p.branch), max_width(p.trunk));
             long rows = std::max(p.n_u, nt_);
-            delta_[0].alloc(sizeof(T) * C * rows * wmax);
-            delta_[1].alloc(sizeof(T) * C * rows * wmax);
+            row_alloc(p.arena, delta_[0], sizeof(T) * C * rows * wmax);
+            row_alloc(p.arena, delta_[1], sizeof(T) * C * rows * wmax);
             n_el_ = p.n_u * p.n_y;
         }
         nparts_ = (int)std::min<long>(64, std::max<long>(1, (n_el_ + 255) / 256));
         part_r2_.alloc(sizeof(double) * C * nparts_);
         part_d_.alloc(sizeof(double) * C * nparts_);
+        // split-K workspace of the FP32 reductions over data rows (weight gradients, dB, dT),
+        // at most 256 MB; a GEMM whose partials do not fit runs unsplit
+        if (sizeof(T) == 4) {
+            size_t need = 0;
+            auto net_need = [&](const NetDesc &nd, long rows) {
+                for (int l = nd.lmin; l < nd.L; ++l)
+                    need = std::max(need, gemm_ws_floats(nd.w[l + 1], nd.w[l], (int)rows, C));
+            };
+            if (p.kind == HMC_NET_MLP) {
+                net_need(p.net, p.n);
+            } else {
+                const int lat = p.branch.w[p.branch.L];
+                net_need(p.branch, p.n_u);
+                net_need(p.trunk, nt_);
+                need = std::max(need, gemm_ws_floats((int)p.n_u, lat, (int)p.n_y, C));
+                need = std::max(need, gemm_ws_floats((int)p.n_y, lat, (int)p.n_u, C));
+            }
+            ws_floats_ = std::min<size_t>(need, (size_t)64 << 20);
+            row_alloc(p.arena, ws_, sizeof(float) * ws_floats_);   // requested even when empty (arena order)
+            if (ws_.own) bytes_ += ws_.n;
+        }
+        for (DevBuf *b : {&delta_[0], &delta_[1], &S_, &dB_, &dT_})
+            if (b->own) bytes_ += b->n;
     }
 
     ScatterPlan scatter_plan() override
@@ -194,7 +217,7 @@ template <typename T> class SimtEngine final : public Engine {
         sp.nbuf = 1;
         sp.base[0] = theta_.ptr;
         sp.cstride[0] = p_.P;
-        sp.is_bf16[0] = 0;
+        sp.kind16[0] = 0;
         sp.buf_id = nullptr;
         sp.off = idx_.as<int>();
         return sp;
@@ -244,7 +267,7 @@ template <typename T> class SimtEngine final : public Engine {
                                Tm, 1, lat, p_.n_y * lat};
                 EpiArgs<T> ea{EPI_ACT, S, p_.n_y, 1, p_.n_u * p_.n_y,
                               p_.out_bias ? theta + p_.b0_off : nullptr, 0, P, HMC_ACT_IDENTITY, nullptr};
-                launch_gemm(ga, ea, C_, s);
+                launch_gemm(ga, ea, C_, s, ws_.template as<float>(), ws_floats_);
             }
             residual(S, p_.n_u * p_.n_y, t_.as<T>(), nullptr, inv_s2, S, true, s);
             if (ua && bn.any_sampled && g) {   // dB_j = sum_k dS_jk T_jk (times the branch output slope)
@@ -269,7 +292,7 @@ template <typename T> class SimtEngine final : public Engine {
                                Tm, lat, 1, p_.n_y * lat};
                 EpiArgs<T> ea{id ? EPI_STORE : EPI_SCALE, dB_.as<T>(), lat, 1, p_.n_u * lat, nullptr, 0, 0, 0,
                               id ? nullptr : brb_.slope[bn.L]->template as<T>()};
-                launch_gemm(ga, ea, C_, s);
+                launch_gemm(ga, ea, C_, s, ws_.template as<float>(), ws_floats_);
                 backward(bn, u_.as<T>(), 0, p_.n_u, brb_, dB_.as<T>(), s);
             }
             if (!ua && tn.any_sampled && g) {   // dT = dS^T B
@@ -278,7 +301,7 @@ template <typename T> class SimtEngine final : public Engine {
                                Bm, lat, 1, p_.n_u * lat};
                 EpiArgs<T> ea{id ? EPI_STORE : EPI_SCALE, dT_.as<T>(), lat, 1, p_.n_y * lat, nullptr, 0, 0, 0,
                               id ? nullptr : trb_.slope[tn.L]->template as<T>()};
-                launch_gemm(ga, ea, C_, s);
+                launch_gemm(ga, ea, C_, s, ws_.template as<float>(), ws_floats_);
                 backward(tn, yq_.as<T>(), 0, p_.n_y, trb_, dT_.as<T>(), s);
             }
         }
@@ -313,9 +336,11 @@ template <typename T> class SimtEngine final : public Engine {
         nb.slope.resize(nd.L + 1);
         for (int l = 1; l <= nd.L; ++l) {
             size_t n = sizeof(T) * C_ * std::max<long>(rows * nd.w[l], 1);
-            nb.act[l].reset(new DevBuf(n));
-            nb.slope[l].reset(new DevBuf(n));
-            bytes_ += 2 * n;
+            nb.act[l].reset(new DevBuf());
+            nb.slope[l].reset(new DevBuf());
+            row_alloc(p_.arena, *nb.act[l], n);
+            row_alloc(p_.arena, *nb.slope[l], n);
+            if (nb.act[l]->own) bytes_ += 2 * n;
         }
     }
 
@@ -331,7 +356,7 @@ template <typename T> class SimtEngine final : public Engine {
             EpiArgs<T> ea{EPI_ACT, nb.act[l + 1]->template as<T>(), wo, 1, rows * wo,
                           nd.boff[l] >= 0 ? theta + nd.boff[l] : nullptr, 1, P, nd.act[l],
                           nd.act[l] == HMC_ACT_IDENTITY ? nullptr : nb.slope[l + 1]->template as<T>()};
-            launch_gemm(ga, ea, C_, s);
+            launch_gemm(ga, ea, C_, s, ws_.template as<float>(), ws_floats_);
             a = nb.act[l + 1]->template as<T>();
             a_b = rows * wo;
         }
@@ -352,7 +377,7 @@ template <typename T> class SimtEngine final : public Engine {
             {   // dW_l = delta_l^T A_{l-1}
                 GemmArgs<T> ga{wo, wi, (int)rows, d, 1, wo, rows * wo, ap, wi, 1, ap_b};
                 EpiArgs<T> ea{EPI_STORE, G + nd.woff[l], wi, 1, P, nullptr, 0, 0, 0, nullptr};
-                launch_gemm(ga, ea, C_, s);
+                launch_gemm(ga, ea, C_, s, ws_.template as<float>(), ws_floats_);
             }
             if (nd.boff[l] >= 0) {
                 dim3 grid((wo + 31) / 32, C_);
@@ -367,7 +392,7 @@ template <typename T> class SimtEngine final : public Engine {
                 const bool id = nd.act[l - 1] == HMC_ACT_IDENTITY;
                 EpiArgs<T> ea{id ? EPI_STORE : EPI_SCALE, nx, wi, 1, rows * wi, nullptr, 0, 0, 0,
                               id ? nullptr : nb.slope[l]->template as<T>()};
-                launch_gemm(ga, ea, C_, s);
+                launch_gemm(ga, ea, C_, s, ws_.template as<float>(), ws_floats_);
                 d = nx;
                 pp ^= 1;
             }
@@ -387,7 +412,8 @@ template <typename T> class SimtEngine final : public Engine {
     Problem &p_;
     int C_;
     size_t bytes_ = 0;
-    DevBuf theta_, G_, idx_, x_, y_, u_, yq_, t_, S_, dB_, dT_, part_r2_, part_d_;
+    DevBuf theta_, G_, idx_, x_, y_, u_, yq_, t_, S_, dB_, dT_, part_r2_, part_d_, ws_;
+    size_t ws_floats_ = 0;
     DevBuf delta_[2];
     NetBufs<T> netb_, brb_, trb_;
     long n_el_ = 0;
@@ -449,6 +475,31 @@ __global__ void k_copy_rep(const float *src, long P, int C, float *dst)
         dst[i] = src[i % P];
 }
 
+// The caller's index list is only read here: every entry that is outside [0, P) or
+// not above its predecessor raises *bad and is replaced by 0, so the scatter and the
+// gather that follow stay inside the scratch array whatever the caller passed.
+__global__ void k_sanitize_idx(const int *idx, long k, long P, int *safe, int *bad)
+{
+    for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (long)gridDim.x * blockDim.x) {
+        const int v = idx[j];
+        const bool ok = v >= 0 && (long)v < P && (j == 0 || idx[j - 1] < v);
+        safe[j] = ok ? v : 0;
+        if (!ok) atomicOr(bad, 1);
+    }
+}
+
+// A rejected index list makes every chain's U NaN (and its gradient, if asked for).
+__global__ void k_poison_if_bad(const int *bad, int C, long k, double *U, float *g)
+{
+    if (!*bad) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < (long)C; i += (long)gridDim.x * blockDim.x)
+        U[i] = nan;
+    if (g)
+        for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < (long)C * k; i += (long)gridDim.x * blockDim.x)
+            g[i] = __int_as_float(0x7fc00000);
+}
+
 }  // namespace
 }  // namespace hmc
 
@@ -469,8 +520,11 @@ extern "C" hmc_status hmc_energy_grad_noalloc(const hmc_mlp_spec *net, const flo
         // layer offsets in the parameter vector (W[out][in] then b[out], layer by layer)
         long woff[MAXL], boff[MAXL], P = 0;
         long wmax = 1;
+        const long cap = (long)(kNoAllocScratchBytes / sizeof(float));   // floats the scratch array holds
         for (int l = 0; l < L; ++l) {
-            HMC_REQUIRE(net->widths[l] >= 1 && net->widths[l + 1] >= 1, "widths must be >= 1");
+            HMC_REQUIRE(net->widths[l] >= 1 && net->widths[l + 1] >= 1 && net->widths[l] <= cap &&
+                            net->widths[l + 1] <= cap,
+                        "widths must be in [1, %ld]", cap);
             HMC_REQUIRE(net->act[l] >= HMC_ACT_IDENTITY && net->act[l] <= HMC_ACT_SIN, "bad activation");
             woff[l] = P;
             P += (long)net->widths[l + 1] * net->widths[l];
@@ -482,6 +536,13 @@ extern "C" hmc_status hmc_energy_grad_noalloc(const hmc_mlp_spec *net, const flo
         }
         for (int l = 0; l <= L; ++l) wmax = std::max<long>(wmax, net->widths[l]);
         HMC_REQUIRE(k <= P, "k (%ld) exceeds the parameter count (%ld)", k, P);
+        // every array below is at most C * max(P, n * wmax) floats: bound the factors by
+        // division first, so that no size computed afterwards can wrap around
+        if (n > cap / ((long)C * wmax) || P > cap / C) {
+            set_error("hmc_energy_grad_noalloc: this problem's intermediates exceed the fixed %zu-byte (16 MiB) "
+                      "scratch array: use hmc_create/hmc_energy_grad instead", kNoAllocScratchBytes);
+            return HMC_ERR_ARG;
+        }
         const int dout = net->widths[L];
         const long n_el = n * dout;
         const int nparts = (int)std::min<long>(64, std::max<long>(1, (n_el + 255) / 256));
@@ -498,6 +559,8 @@ extern "C" hmc_status hmc_energy_grad_noalloc(const hmc_mlp_spec *net, const flo
         }
         const size_t o_d0 = need; need += up(sizeof(float) * C * n * wmax);
         const size_t o_d1 = need; need += up(sizeof(float) * C * n * wmax);
+        const size_t o_idx = need; need += up(sizeof(int) * k);
+        const size_t o_bad = need; need += up(sizeof(int));
         if (need > kNoAllocScratchBytes) {
             set_error("hmc_energy_grad_noalloc needs %zu bytes of scratch for this problem; the fixed maximum is "
                       "%zu bytes (16 MiB): use hmc_create/hmc_energy_grad instead", need, kNoAllocScratchBytes);
@@ -510,6 +573,12 @@ extern "C" hmc_status hmc_energy_grad_noalloc(const hmc_mlp_spec *net, const flo
         float *d[2] = {reinterpret_cast<float *>(base + o_d0), reinterpret_cast<float *>(base + o_d1)};
         auto act = [&](int l) { return reinterpret_cast<float *>(base + o_act[l]); };
         auto slope = [&](int l) { return reinterpret_cast<float *>(base + o_slope[l]); };
+        int *idx = reinterpret_cast<int *>(base + o_idx);
+        int *bad = reinterpret_cast<int *>(base + o_bad);
+        // the array keeps the previous call's contents: the flag must start at zero
+        HMC_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        k_sanitize_idx<<<(unsigned)std::min<long>((k + 255) / 256, 1024), 256, 0, s>>>(subset_idx, k, P, idx, bad);
+        HMC_LAUNCH_CK();
         // the gradient buffer is read only at the sampled entries, all of which the
         // reverse pass rewrites; it is still cleared so no stale value can leak out
         HMC_CK(cudaMemsetAsync(G, 0, sizeof(float) * C * P, s));
@@ -518,7 +587,7 @@ extern "C" hmc_status hmc_energy_grad_noalloc(const hmc_mlp_spec *net, const flo
         HMC_LAUNCH_CK();
         {
             dim3 grid((unsigned)std::min<long>((k + 255) / 256, 1024), C);
-            k_scatter<float><<<grid, 256, 0, s>>>(q, subset_idx, k, theta, P);
+            k_scatter<float><<<grid, 256, 0, s>>>(q, idx, k, theta, P);
             HMC_LAUNCH_CK();
         }
         // forward
@@ -566,8 +635,10 @@ extern "C" hmc_status hmc_energy_grad_noalloc(const hmc_mlp_spec *net, const flo
                 pp ^= 1;
             }
         }
-        k_finalize<float><<<C, 256, 0, s>>>(part, nullptr, nparts, 0.5 * inv_s2, q, k, subset_idx, G, P, -1,
+        k_finalize<float><<<C, 256, 0, s>>>(part, nullptr, nparts, 0.5 * inv_s2, q, k, idx, G, P, -1,
                                             1.0 / (prior_sigma * prior_sigma), U, grad);
+        HMC_LAUNCH_CK();
+        k_poison_if_bad<<<(unsigned)std::min<long>(((long)C * k + 255) / 256, 1024), 256, 0, s>>>(bad, C, k, U, grad);
         HMC_LAUNCH_CK();
         return HMC_OK;
     } catch (const Fail &f) {

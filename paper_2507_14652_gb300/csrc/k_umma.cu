@@ -21,6 +21,7 @@
 //   finalize      U, g = sum of partials in fixed order + q / alpha^2
 // Every partial sum is written to its own slot (no atomics), so the result is
 // bit-reproducible.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -34,10 +35,63 @@
 #include "hmc_internal.cuh"
 #include "umma.cuh"
 
+// The 16-bit operand type of the tensor-core GEMMs is chosen at compile time: this
+// file builds the bf16 engines, and k_umma_f16.cu includes it with HMC_F16 = 1 for the
+// fp16 ones (same kernels, same bytes and tensor rate; 11 significant bits against 8).
+#ifndef HMC_F16
+#define HMC_F16 0
+#endif
+
 namespace hmc {
 namespace {
 
 using namespace umma;
+
+#if HMC_F16
+using h16 = __half;
+constexpr int H16_KIND = 2;                      // ScatterPlan::kind16 of the hidden weights
+#define TM_H16 CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+__host__ __device__ inline h16 f_to_h16(float v) { return __float2half_rn(v); }
+__host__ __device__ inline float h16_to_f(h16 v) { return __half2float(v); }
+__device__ __forceinline__ uint32_t pack_h16(float a, float b) { return pack_f16(a, b); }
+__device__ __forceinline__ float2 unpack_h16(uint32_t u) { return unpack_f16(u); }
+__device__ __forceinline__ void mma_m16n8k16_h16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    mma_m16n8k16_f16(d, a, b0, b1);
+}
+__host__ __device__ constexpr uint32_t idesc_h16(int M, int N, bool a_mn, bool b_mn)
+{
+    return idesc_f16(M, N, a_mn, b_mn);
+}
+// fp16 keeps 11 significant bits, so the activations get a tanh accurate to 5e-7
+__device__ __forceinline__ float act_tanh(float x) { return tanh_acc(x); }
+#else
+using h16 = __nv_bfloat16;
+constexpr int H16_KIND = 1;
+#define TM_H16 CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+__host__ __device__ inline h16 f_to_h16(float v) { return __float2bfloat16_rn(v); }
+__host__ __device__ inline float h16_to_f(h16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ uint32_t pack_h16(float a, float b) { return pack_bf16(a, b); }
+__device__ __forceinline__ float2 unpack_h16(uint32_t u) { return unpack_bf16(u); }
+__device__ __forceinline__ void mma_m16n8k16_h16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    mma_m16n8k16_bf16(d, a, b0, b1);
+}
+__host__ __device__ constexpr uint32_t idesc_h16(int M, int N, bool a_mn, bool b_mn)
+{
+    return idesc_bf16(M, N, a_mn, b_mn);
+}
+__device__ __forceinline__ float act_tanh(float x) { return tanh_fast(x); }
+#endif
+
+// Output deltas are formed as r * dscale and every data-term gradient sum is scaled by
+// gscale = (1 / sigma^2) / dscale at the end.  bf16 shares fp32's exponent range, so it
+// takes dscale = 1 / sigma^2 (gscale = 1); fp16 overflows at 65504, so it takes the power
+// of two nearest 1 / sigma, which keeps the deltas near the size of r / sigma.
+inline double delta_scale(double sigma)
+{
+    return HMC_F16 ? std::ldexp(1.0, (int)std::lround(std::log2(1.0 / sigma))) : 1.0 / (sigma * sigma);
+}
 
 constexpr int BM = 128;                         // rows per tile (UMMA M)
 constexpr int BK = 64;                          // K per stage (one 128-byte swizzle atom of bf16)
@@ -69,9 +123,9 @@ struct Params {
     int *err;
     // outputs / epilogue operands
     float *out_f32;                       // M_STORE_F32: [b][M][N]
-    __nv_bfloat16 *out; long out_b;       // bf16 [b][M][N]
+    h16 *out; long out_b;       // bf16 [b][M][N]
     const float *bias; long bias_b;       // [b][N]
-    const __nv_bfloat16 *aux; long aux_b; // A_i for the tanh slope [b][M][N]
+    const h16 *aux; long aux_b; // A_i for the tanh slope [b][M][N]
     const float *wout; long wout_b;       // output weights [b][N]
     const float *bout;                    // [b]
     const float *y;                       // targets [M]
@@ -181,7 +235,7 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
         }
     } else if (warp == 1) {
         if (lane == 0) {   // MMA issuer
-            const uint32_t idesc = idesc_bf16(BM, BN, A_MN, B_MN);
+            const uint32_t idesc = idesc_h16(BM, BN, A_MN, B_MN);
             for (int i = 0; i < nkb; ++i) {
                 const int s = i % STAGES;
                 const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
@@ -233,8 +287,8 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                         uint32_t pk[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j)
-                            pk[j] = pack_bf16(tanh_fast(v[2 * j] + bias[c0 + 2 * j]),
-                                              tanh_fast(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
+                            pk[j] = pack_h16(act_tanh(v[2 * j] + bias[c0 + 2 * j]),
+                                              act_tanh(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
                         uint4 *o = reinterpret_cast<uint4 *>(p.out + (long)b * p.out_b + (long)m * p.N + c0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
@@ -249,7 +303,7 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                         uint32_t pk[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j)
-                            pk[j] = pack_bf16(v[2 * j] + bias[c0 + 2 * j], v[2 * j + 1] + bias[c0 + 2 * j + 1]);
+                            pk[j] = pack_h16(v[2 * j] + bias[c0 + 2 * j], v[2 * j + 1] + bias[c0 + 2 * j + 1]);
                         uint4 *o = reinterpret_cast<uint4 *>(p.out + (long)b * p.out_b + (long)m * p.N + c0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
@@ -260,7 +314,7 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                 // dS[u][y] = r / sigma^2 in bf16; per load and store a warp covers 32
                 // consecutive y of one u.  Squares summed in FP32 per chunk, carried in FP64.
                 const float b0 = p.b0s[b];
-                __nv_bfloat16 *ob = p.out + (long)b * p.out_b + m;
+                h16 *ob = p.out + (long)b * p.out_b + m;
                 const float *yb = p.Yt + m;
                 double r2 = 0.0;
                 float dsum = 0.0f;
@@ -280,7 +334,7 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                                 r2c += r * r;
                                 const float ds = r * p.inv_s2;
                                 dsum += ds;
-                                ob[(long)(u0 + j) * p.ldo] = __float2bfloat16_rn(ds);
+                                ob[(long)(u0 + j) * p.ldo] = f_to_h16(ds);
                             }
                         }
                         r2 += (double)r2c;
@@ -313,7 +367,7 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                     } else {
                         uint32_t pk[16];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(v[2 * j], v[2 * j + 1]);
+                        for (int j = 0; j < 16; ++j) pk[j] = pack_h16(v[2 * j], v[2 * j + 1]);
                         uint4 *o = reinterpret_cast<uint4 *>(p.out + (long)b * p.out_b + (long)m * p.N + c0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
@@ -334,7 +388,7 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                     float v[32];
                     tmem_ld32(taddr + c0, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) f += tanh_fast(v[j] + bias[c0 + j]) * wo[c0 + j];
+                    for (int j = 0; j < 32; ++j) f += act_tanh(v[j] + bias[c0 + j]) * wo[c0 + j];
                 }
                 const float r = valid ? f - p.y[m] : 0.0f;
                 const float d = r * p.inv_s2;   // delta of the output
@@ -357,12 +411,12 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                     uint32_t pk[16];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const float a = tanh_fast(v[j] + bias[c0 + j]);
+                        const float a = act_tanh(v[j] + bias[c0 + j]);
                         dw[j] = d * a;
                         dd[j] = d * wo[c0 + j] * (1.0f - a * a);
                     }
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
+                    for (int j = 0; j < 16; ++j) pk[j] = pack_h16(dd[2 * j], dd[2 * j + 1]);
                     if (valid) {
                         uint4 *o = reinterpret_cast<uint4 *>(p.out + (long)b * p.out_b + (long)m * p.N + c0);
 #pragma unroll
@@ -384,7 +438,7 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                     p.dbout_part[(long)b * p.ntiles + m_tile] = dsm[0] + dsm[1] + dsm[2] + dsm[3];
                 }
             } else if (MODE == M_BWD_TANH || MODE == M_BWD_FIRST) {
-                const __nv_bfloat16 *aux = p.aux + (long)b * p.aux_b + (long)(valid ? m : 0) * p.N;
+                const h16 *aux = p.aux + (long)b * p.aux_b + (long)(valid ? m : 0) * p.N;
                 float xv[8];
 #pragma unroll
                 for (int d = 0; d < 8; ++d) xv[d] = (MODE == M_BWD_FIRST && valid && d < p.dx) ? p.x[(long)m * p.dx + d] : 0.0f;
@@ -399,7 +453,7 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                             const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
                             for (int t = 0; t < 4; ++t) {
-                                const float2 a = unpack_bf16(w4[t]);
+                                const float2 a = unpack_h16(w4[t]);
                                 dd[8 * j + 2 * t] = v[8 * j + 2 * t] * (1.0f - a.x * a.x);
                                 dd[8 * j + 2 * t + 1] = v[8 * j + 2 * t + 1] * (1.0f - a.y * a.y);
                             }
@@ -411,7 +465,7 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
                     if (MODE == M_BWD_TANH && valid) {
                         uint32_t pk[16];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
+                        for (int j = 0; j < 16; ++j) pk[j] = pack_h16(dd[2 * j], dd[2 * j + 1]);
                         uint4 *o = reinterpret_cast<uint4 *>(p.out + (long)b * p.out_b + (long)m * p.N + c0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) o[j] = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
@@ -504,13 +558,22 @@ constexpr int L_SMEM = 1024 + 2 * L_W_HALF + L_STAGES * L_A_BYTES + 256 + L_SCR_
                        2 * 256 * 4 + 2 * 128 * 4;        // + bias and output weights of the chain, half-row sums
 constexpr int L_THREADS = 320;                          // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 static_assert(8 * L_AUX <= L_W_HALF, "reverse-pass slope buffers fit the lo region");
+// Reverse pass with the weights as a hi/lo pair (the lo region then holds W): a two-stage
+// operand ring, and two of a warp's four slope chunks in flight, in a region of their own
+// after the per-chain vectors, within the same L_SMEM.
+constexpr int L_STAGES_RLO = 2;
+constexpr int L_AUX_RLO = 2 * L_STG;
+constexpr int L_AUX_OFF_RLO = 2 * L_W_HALF + L_STAGES_RLO * L_A_BYTES + 256 + L_SCR_FLOATS * 4 + 64 + 64 +
+                              2 * 256 * 4 + 2 * 128 * 4;   // from the 1024-aligned base
+static_assert(1024 + L_AUX_OFF_RLO + 8 * L_AUX_RLO <= L_SMEM, "reverse hi/lo layout fits the layer kernels' smem");
+static_assert(L_AUX_OFF_RLO % 128 == 0, "slope buffers stay 128-byte aligned");
 
 struct LayerParams {
     int N, W, C, ntiles, dx;
     int *err;
-    __nv_bfloat16 *out;            // [c][N][W]
+    h16 *out;            // [c][N][W]
     const float *bias;             // [c][W]
-    const __nv_bfloat16 *aux;      // [c][N][W]
+    const h16 *aux;      // [c][N][W]
     const float *wout, *bout, *y;  // output layer and targets
     float inv_s2;
     double *u_part;                // [c][tiles]
@@ -541,14 +604,19 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
     constexpr int TCOLS = 2 * SLOT;
     constexpr int kblk = BN * 128;                     // bytes of one resident K-block of W
     static_assert(NKB * kblk <= L_W_HALF, "resident half of W");
-    static_assert(!(BWD && WSPLIT), "the reverse pass keeps its slope buffers in the lo region");
+    // the reverse pass with hi/lo weights needs the lo region for W: its ring is two stages
+    // deep and its slopes prefetch two chunks ahead in a region of their own
+    constexpr bool RLO = BWD && WSPLIT;
+    constexpr int STAGES = RLO ? L_STAGES_RLO : L_STAGES;
+    constexpr int NAUX = RLO ? 2 : NCH;                // slope chunks in flight per epilogue warp
+    static_assert(NCH % NAUX == 0, "slope chunks cycle through the buffers");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sWh = smem;
     uint8_t *sWl = smem + L_W_HALF;
     uint8_t *sA = smem + 2 * L_W_HALF;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + L_STAGES * L_A_BYTES);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * L_STAGES + 7);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sA + STAGES * L_A_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 7);
     float *scr = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(bars) + 256);
     float *red = scr;                                                                  // column sums
     uint8_t *stage0 = BWD ? reinterpret_cast<uint8_t *>(scr) : reinterpret_cast<uint8_t *>(scr + 4 * 256);
@@ -557,8 +625,8 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
     float *sbias = fred + 16;                                        // [256] bias of the current chain
     float *swo = sbias + 256;                                        // [256] output weights of the current chain
     float *fsum = swo + 256;                                         // [2][128] half-row partial dot products
-    const uint32_t a_full0 = smem_u32(bars), a_empty0 = a_full0 + 8 * L_STAGES;
-    const uint32_t w_full = a_empty0 + 8 * L_STAGES, w_empty = w_full + 8;
+    const uint32_t a_full0 = smem_u32(bars), a_empty0 = a_full0 + 8 * STAGES;
+    const uint32_t w_full = a_empty0 + 8 * STAGES, w_empty = w_full + 8;
     const uint32_t acc_full0 = w_empty + 8, acc_empty0 = acc_full0 + 16;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -570,7 +638,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
     const long u0 = U * gi / ngr, u1 = U * (gi + 1) / ngr;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < L_STAGES; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             mbar_init(a_full0 + 8 * s, 1);
             mbar_init(a_empty0 + 8 * s, 1);
         }
@@ -621,16 +689,20 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                             tma_load_3d_pair(dh, &tmWh, kb * BK, (int)rank * BN, c, lead_w_full);
                             if (WSPLIT) tma_load_3d_pair(dl, &tmWl, kb * BK, (int)rank * BN, c, lead_w_full);
                         } else {      // B = W^T read MN-major from W[o][i]: 64-feature atoms
-                            for (int a = 0; a < BN / 64; ++a)
+                            for (int a = 0; a < BN / 64; ++a) {
                                 tma_load_3d_pair(dh + 8192 * a, &tmWh, (int)rank * BN + 64 * a, kb * BK, c, lead_w_full);
+                                if (WSPLIT)
+                                    tma_load_3d_pair(dl + 8192 * a, &tmWl, (int)rank * BN + 64 * a, kb * BK, c,
+                                                     lead_w_full);
+                            }
                         }
                     }
                     w_pending = true;
                     cur_c = c;
                 }
                 for (int kb = 0; kb < NKB; ++kb) {
-                    const int s = (int)(kbi % L_STAGES);
-                    const uint32_t ph = (uint32_t)(kbi / L_STAGES) & 1u;
+                    const int s = (int)(kbi % STAGES);
+                    const uint32_t ph = (uint32_t)(kbi / STAGES) & 1u;
                     if (!mbar_wait(a_empty0 + 8 * s, ph ^ 1u, p.err)) { ok = false; break; }
                     if (leader) mbar_expect_tx(a_full0 + 8 * s, 2u * L_A_BYTES);
                     tma_load_3d_pair(smem_u32(sA + s * L_A_BYTES), &tmA, kb * BK, t * BM, c, lead_a_full0 + 8 * s);
@@ -638,14 +710,14 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                 }
             }
             if (!ok && leader) {   // let copies already in flight land before the CTA exits
-                for (long i = std::max<long>(0, kbi - L_STAGES); i < kbi; ++i)
-                    mbar_wait(a_full0 + 8 * (int)(i % L_STAGES), (uint32_t)(i / L_STAGES) & 1u, p.err, 100000000ull);
+                for (long i = std::max<long>(0, kbi - STAGES); i < kbi; ++i)
+                    mbar_wait(a_full0 + 8 * (int)(i % STAGES), (uint32_t)(i / STAGES) & 1u, p.err, 100000000ull);
                 if (w_pending) mbar_wait(w_full, wph, p.err, 100000000ull);
             }
         }
     } else if (warp == 1) {
         if (lane == 0 && leader) {   // MMA issuer: the leader alone drives the pair
-            const uint32_t idesc = idesc_bf16(2 * BM, LN, false, BWD);
+            const uint32_t idesc = idesc_h16(2 * BM, LN, false, BWD);
             int cur_c = -1;
             uint32_t wph = 0;
             long kbi = 0;
@@ -666,8 +738,8 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(slot * SLOT);
                 for (int kb = 0; kb < NKB; ++kb) {
-                    const int s = (int)(kbi % L_STAGES);
-                    const uint32_t ph = (uint32_t)(kbi / L_STAGES) & 1u;
+                    const int s = (int)(kbi % STAGES);
+                    const uint32_t ph = (uint32_t)(kbi / STAGES) & 1u;
                     if (!mbar_wait_cluster(a_full0 + 8 * s, ph, p.err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(sA + s * L_A_BYTES);
@@ -677,7 +749,10 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                         const uint64_t ad = sdesc(sa + 32 * ks, 0, 1024);
                         const uint64_t bh = BWD ? sdesc(wh + 2048 * ks, 8192, 1024) : sdesc(wh + 32 * ks, 0, 1024);
                         mma_bf16_pair(d_tmem, ad, bh, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
-                        if (WSPLIT) mma_bf16_pair(d_tmem, ad, sdesc(wl + 32 * ks, 0, 1024), idesc, 1u);
+                        if (WSPLIT) {
+                            const uint64_t bl = BWD ? sdesc(wl + 2048 * ks, 8192, 1024) : sdesc(wl + 32 * ks, 0, 1024);
+                            mma_bf16_pair(d_tmem, ad, bl, idesc, 1u);
+                        }
                     }
                     mma_commit_pair(a_empty0 + 8 * s, (uint16_t)3);
                     ++kbi;
@@ -697,25 +772,30 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
         const int hc0 = h * (LN / 2);          // first column of this warp's half
         uint8_t *stg = stage0 + (warp - 2) * L_STG;
         const int tr = lane >> 2, tj = lane & 3;   // transposed access: rows tr + 8 i, piece tj
-        // reverse pass: the slopes of a unit's chunk ch land in abuf + ch * L_STG by cp.async,
-        // one commit group per chunk, issued a whole tile ahead of their use
-        const uint32_t abuf = smem_u32(sWl) + (uint32_t)(warp - 2) * L_AUX;
+        // reverse pass: the slopes of a unit's chunk ch land in abuf + (ch mod NAUX) * L_STG by
+        // cp.async, one commit group per chunk, issued NAUX chunks ahead of their use (a whole
+        // tile when NAUX = NCH)
+        const uint32_t abuf = RLO ? smem_u32(smem + L_AUX_OFF_RLO) + (uint32_t)(warp - 2) * L_AUX_RLO
+                                  : smem_u32(sWl) + (uint32_t)(warp - 2) * L_AUX;
         auto issue_aux = [&](long v, int ch) {
             if (v < u1) {
                 const int cv = (int)(v / tpg), tv = (int)(v % tpg) * 2 + (int)rank;
                 const int rv0 = tv * BM + 32 * q;
-                const __nv_bfloat16 *src = p.aux + ((long)cv * p.N + rv0) * p.W + hc0 + 32 * ch + 8 * tj;
+                const h16 *src = p.aux + ((long)cv * p.N + rv0) * p.W + hc0 + 32 * ch + 8 * tj;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int rr = tr + 8 * i;
                     const bool in = rv0 + rr < p.N;
-                    cp_async16(abuf + ch * L_STG + stg_off(rr, tj), in ? src + (long)rr * p.W : p.aux, in ? 16u : 0u);
+                    cp_async16(abuf + (ch % NAUX) * L_STG + stg_off(rr, tj), in ? src + (long)rr * p.W : p.aux,
+                               in ? 16u : 0u);
                 }
             }
             cp_async_commit();
         };
+        // the chunk that follows chunk ch of unit v by NAUX chunks goes into the same buffer
+        auto refill_aux = [&](long v, int ch) { issue_aux(v + (ch + NAUX) / NCH, (ch + NAUX) % NCH); };
         if (BWD)
-            for (int ch = 0; ch < NCH; ++ch) issue_aux(u0, ch);
+            for (int ch = 0; ch < NAUX; ++ch) issue_aux(u0, ch);
         int it = 0, chain_loaded = -1;
         for (long u = u0; u < u1; ++u, ++it) {
             const int c = (int)(u / tpg), t = (int)(u % tpg) * 2 + (int)rank;
@@ -752,7 +832,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                                 v1 = a1;
                             }
                         }
-                        bx[ks][hf] = pack_bf16(v0, v1);
+                        bx[ks][hf] = pack_h16(v0, v1);
                     }
             }
             // per-chain constants into shared memory
@@ -794,8 +874,8 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     uint32_t pk[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
-                        pk[j] = pack_bf16(tanh_fast(__uint_as_float(rb[ch & 1][2 * j]) + sbias[hc0 + c0 + 2 * j]),
-                                          tanh_fast(__uint_as_float(rb[ch & 1][2 * j + 1]) + sbias[hc0 + c0 + 2 * j + 1]));
+                        pk[j] = pack_h16(act_tanh(__uint_as_float(rb[ch & 1][2 * j]) + sbias[hc0 + c0 + 2 * j]),
+                                          act_tanh(__uint_as_float(rb[ch & 1][2 * j + 1]) + sbias[hc0 + c0 + 2 * j + 1]));
                     store_chunk(pk, c0);
                 }
             } else if (BWD) {
@@ -806,21 +886,21 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     float dd[32];
                     tmem_ld_wait(rb[ch & 1]);
                     if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
-                    // slopes of this chunk: exactly NCH - 1 groups were committed after this one
-                    cp_async_wait<NCH - 1>();
+                    // slopes of this chunk: exactly NAUX - 1 groups were committed after this one
+                    cp_async_wait<NAUX - 1>();
                     __syncwarp();
                     uint4 av[4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) av[j] = lds128(abuf + ch * L_STG + stg_off(lane, j));
+                    for (int j = 0; j < 4; ++j) av[j] = lds128(abuf + (ch % NAUX) * L_STG + stg_off(lane, j));
                     __syncwarp();   // every lane has its row: refill the chunk for the next unit
-                    if (MODE != L_BWD_FIRST) issue_aux(u + 1, ch);   // (the first layer stages in it first)
+                    if (MODE != L_BWD_FIRST) refill_aux(u, ch);   // (the first layer stages in it first)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const uint4 uu = av[j];
                         const uint32_t w4[4] = {uu.x, uu.y, uu.z, uu.w};
 #pragma unroll
                         for (int tt = 0; tt < 4; ++tt) {
-                            const float2 a = unpack_bf16(w4[tt]);
+                            const float2 a = unpack_h16(w4[tt]);
                             const int k = 8 * j + 2 * tt;
                             dd[k] = valid ? __uint_as_float(rb[ch & 1][k]) * (1.0f - a.x * a.x) : 0.0f;
                             dd[k + 1] = valid ? __uint_as_float(rb[ch & 1][k + 1]) * (1.0f - a.y * a.y) : 0.0f;
@@ -829,18 +909,18 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     if (MODE == L_BWD_TANH) {
                         uint32_t pk[16];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
+                        for (int j = 0; j < 16; ++j) pk[j] = pack_h16(dd[2 * j], dd[2 * j + 1]);
                         store_chunk(pk, c0);
                     }
                     if (MODE == L_BWD_FIRST) {
                         // first-layer weight and bias gradients of this chunk's 32 columns over the
                         // warp's 32 rows: delta_1 (bf16) goes to the chunk's slope buffer, which
                         // this warp has read, and mma.sync forms delta_1^T [X | 1]
-                        const uint32_t sb = abuf + ch * L_STG;
+                        const uint32_t sb = abuf + (ch % NAUX) * L_STG;
                         {
                             uint32_t pk[16];
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) pk[j] = pack_bf16(dd[2 * j], dd[2 * j + 1]);
+                            for (int j = 0; j < 16; ++j) pk[j] = pack_h16(dd[2 * j], dd[2 * j + 1]);
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
                                 asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sb + stg_off(lane, j)),
@@ -856,10 +936,10 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                             for (int ks = 0; ks < 2; ++ks) {  // rows 16 ks .. 16 ks + 15 of the warp
                                 uint32_t a[4];
                                 ldmatrix_x4_trans(a, sb + stg_off(16 * ks + (lane & 7) + 8 * (mi >> 1), 2 * mt + (mi & 1)));
-                                mma_m16n8k16_bf16(acc[mt], a, bx[ks][0], bx[ks][1]);
+                                mma_m16n8k16_h16(acc[mt], a, bx[ks][0], bx[ks][1]);
                             }
                         __syncwarp();   // the buffer is read: refill it for the next unit
-                        issue_aux(u + 1, ch);
+                        refill_aux(u, ch);
                         const int g = lane >> 2, c2 = 2 * (lane & 3);
 #pragma unroll
                         for (int mt = 0; mt < 2; ++mt)
@@ -903,7 +983,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     }
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const float a = tanh_fast(__uint_as_float(rb[ch & 1][j]) + sbias[hc0 + c0 + j]);
+                        const float a = act_tanh(__uint_as_float(rb[ch & 1][j]) + sbias[hc0 + c0 + j]);
                         fh += a * swo[hc0 + c0 + j];
                         rb[ch & 1][j] = __float_as_uint(a);
                     }
@@ -941,7 +1021,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                             const int rr = 16 * ks + 8 * hf + c2;
                             const float d0 = __shfl_sync(0xffffffffu, d, rr);
                             const float d1 = __shfl_sync(0xffffffffu, d, rr + 1);
-                            bd[ks][hf] = g == 0 ? pack_bf16(d0, d1) : 0u;
+                            bd[ks][hf] = g == 0 ? pack_h16(d0, d1) : 0u;
                         }
                 }
                 tmem_ld32_issue(taddr, rb[0]);
@@ -956,10 +1036,10 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                         for (int j = 0; j < 4; ++j) {
                             const uint32_t *w = &rb[ch & 1][8 * j];
                             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sb + stg_off(lane, j)),
-                                         "r"(pack_bf16(__uint_as_float(w[0]), __uint_as_float(w[1]))),
-                                         "r"(pack_bf16(__uint_as_float(w[2]), __uint_as_float(w[3]))),
-                                         "r"(pack_bf16(__uint_as_float(w[4]), __uint_as_float(w[5]))),
-                                         "r"(pack_bf16(__uint_as_float(w[6]), __uint_as_float(w[7])))
+                                         "r"(pack_h16(__uint_as_float(w[0]), __uint_as_float(w[1]))),
+                                         "r"(pack_h16(__uint_as_float(w[2]), __uint_as_float(w[3]))),
+                                         "r"(pack_h16(__uint_as_float(w[4]), __uint_as_float(w[5]))),
+                                         "r"(pack_h16(__uint_as_float(w[6]), __uint_as_float(w[7])))
                                          : "memory");
                         }
                         __syncwarp();
@@ -971,7 +1051,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                             for (int ks = 0; ks < 2; ++ks) {
                                 uint32_t a4[4];
                                 ldmatrix_x4_trans(a4, sb + stg_off(16 * ks + (lane & 7) + 8 * (mi >> 1), 2 * mt + (mi & 1)));
-                                mma_m16n8k16_bf16(acc[mt], a4, bd[ks][0], bd[ks][1]);
+                                mma_m16n8k16_h16(acc[mt], a4, bd[ks][0], bd[ks][1]);
                             }
                         __syncwarp();   // the staging buffer is read: the deltas go through it next
                         if ((lane & 3) == 0) {   // column 0 of D: lanes 4 g hold columns g and g + 8
@@ -986,7 +1066,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const float a0 = __uint_as_float(rb[ch & 1][2 * j]), a1 = __uint_as_float(rb[ch & 1][2 * j + 1]);
-                        pk[j] = pack_bf16(d * swo[hc0 + c0 + 2 * j] * (1.0f - a0 * a0),
+                        pk[j] = pack_h16(d * swo[hc0 + c0 + 2 * j] * (1.0f - a0 * a0),
                                           d * swo[hc0 + c0 + 2 * j + 1] * (1.0f - a1 * a1));
                     }
                     store_chunk(pk, c0);
@@ -1082,8 +1162,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_dw2(const __grid_constant__ CUt
         prefetch_map(&tmD);
         prefetch_map(&tmA);
     }
-    for (int i = threadIdx.x; i < DW_ONES / 4; i += blockDim.x)   // bf16 1.0 pairs
-        reinterpret_cast<uint32_t *>(ones)[i] = 0x3F803F80u;
+    for (int i = threadIdx.x; i < DW_ONES / 4; i += blockDim.x)   // pairs of 16-bit 1.0
+        reinterpret_cast<uint32_t *>(ones)[i] = pack_h16(1.0f, 1.0f);
     fence_proxy_async_smem();   // the tensor core reads what the threads wrote
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), DW_TCOLS);
@@ -1119,8 +1199,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_dw2(const __grid_constant__ CUt
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(BM, 128, true, true);
-            const uint32_t idesc1 = idesc_bf16(BM, 16, true, false);
+            const uint32_t idesc = idesc_h16(BM, 128, true, true);
+            const uint32_t idesc1 = idesc_h16(BM, 16, true, false);
             const uint32_t so = smem_u32(ones);
             for (int i = 0; i < nkb; ++i) {
                 const int s = i % DW_STAGES;
@@ -1210,7 +1290,7 @@ struct E3Params {
     int M, N, K, ntiles;
     int *err;
     const float *bias;                   // [b][N]
-    __nv_bfloat16 *out_hi, *out_lo;      // [b][M][N]
+    h16 *out_hi, *out_lo;      // [b][M][N]
     const float *wout, *bout, *y;        // E3_OUT: output layer [b][N], [b]; targets [M]
     double *u_part;                      // E3_OUT: [b][ntiles]; E3_S: [b][ntiles][ntn]
     const float *Yt;                     // E3_S: targets [nu][ny] (rows of S^T are the ny points)
@@ -1274,7 +1354,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(BM, p.N, false, false);
+            const uint32_t idesc = idesc_h16(BM, p.N, false, false);
             for (int i = 0; i < nkb; ++i) {
                 const int s = i % E3_STAGES;
                 const uint32_t ph = (uint32_t)(i / E3_STAGES) & 1u;
@@ -1313,9 +1393,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             a0 = tanhf(a0);
                             a1 = tanhf(a1);
                         }
-                        const __nv_bfloat16 h0 = __float2bfloat16_rn(a0), h1 = __float2bfloat16_rn(a1);
-                        ph[j] = pack_bf16(__bfloat162float(h0), __bfloat162float(h1));
-                        pl[j] = pack_bf16(a0 - __bfloat162float(h0), a1 - __bfloat162float(h1));
+                        const h16 h0 = f_to_h16(a0), h1 = f_to_h16(a1);
+                        ph[j] = pack_h16(h16_to_f(h0), h16_to_f(h1));
+                        pl[j] = pack_h16(a0 - h16_to_f(h0), a1 - h16_to_f(h1));
                     }
                     uint4 *oh = reinterpret_cast<uint4 *>(p.out_hi + ((long)b * p.M + m) * p.N + c0);
                     uint4 *ol = reinterpret_cast<uint4 *>(p.out_lo + ((long)b * p.M + m) * p.N + c0);
@@ -1396,7 +1476,7 @@ void launch_energy3(const CUtensorMap &ah, const CUtensorMap &al, const CUtensor
 // First layer of the accurate forward pass: A_1 = tanh(X W_0^T + b_0) in FP32, stored
 // as a bf16 hi/lo pair.  Thread = (column o, slice of rows) of a (128-row tile, chain).
 __global__ void __launch_bounds__(256) k_first_fwd3(const float *x, int dx, int N, int w, const float *W0,
-                                                    const float *b0, __nv_bfloat16 *A1h, __nv_bfloat16 *A1l)
+                                                    const float *b0, h16 *A1h, h16 *A1l)
 {
     __shared__ float xs[BM * 8];
     pdl_wait();
@@ -1417,9 +1497,9 @@ __global__ void __launch_bounds__(256) k_first_fwd3(const float *x, int dx, int 
             for (int d = 0; d < 8; ++d)
                 if (d < dx) z += xs[r * dx + d] * wr[d];
             const float a = tanhf(z);
-            const __nv_bfloat16 h = __float2bfloat16_rn(a);
+            const h16 h = f_to_h16(a);
             A1h[base + (long)r * w] = h;
-            A1l[base + (long)r * w] = __float2bfloat16_rn(a - __bfloat162float(h));
+            A1l[base + (long)r * w] = f_to_h16(a - h16_to_f(h));
         }
     }
 }
@@ -1436,7 +1516,7 @@ __global__ void __launch_bounds__(256) k_first_fwd3(const float *x, int dx, int 
 // multiply-adds per output, and the kernel was bound by instruction issue.
 template <int DX>
 __global__ void __launch_bounds__(256) k_first_fwd(const float *x, int N, int w, const float *W0, const float *b0,
-                                                   __nv_bfloat16 *A1)
+                                                   h16 *A1)
 {
     __shared__ float xs[BM * DX];
     pdl_wait();
@@ -1457,7 +1537,7 @@ __global__ void __launch_bounds__(256) k_first_fwd(const float *x, int N, int w,
 #pragma unroll
             for (int d = 0; d < DX; ++d) wr[c][d] = W0[((long)b * w + o0 + c) * DX + d];
         }
-        __nv_bfloat16 *out = A1 + ((long)b * N + n0) * w + o0;
+        h16 *out = A1 + ((long)b * N + n0) * w + o0;
 #pragma unroll 4
         for (int r = r0; r < r1; ++r) {
             float xv[DX];
@@ -1471,14 +1551,14 @@ __global__ void __launch_bounds__(256) k_first_fwd(const float *x, int N, int w,
                 for (int d = 0; d < DX; ++d) z[c] += xv[d] * wr[c][d];
             }
             *reinterpret_cast<uint2 *>(out + (long)r * w) =
-                make_uint2(pack_bf16(tanh_fast(z[0]), tanh_fast(z[1])), pack_bf16(tanh_fast(z[2]), tanh_fast(z[3])));
+                make_uint2(pack_h16(act_tanh(z[0]), act_tanh(z[1])), pack_h16(act_tanh(z[2]), act_tanh(z[3])));
         }
     }
 }
 
 // The first-layer forward for an input width dx in 1..8.
 void launch_first_fwd(int dx, dim3 grid, cudaStream_t s, const float *x, int N, int w, const float *W0,
-                      const float *b0, __nv_bfloat16 *A1)
+                      const float *b0, h16 *A1)
 {
     switch (dx) {
     case 1: launch_pdl(k_first_fwd<1>, grid, dim3(256), 0, s, x, N, w, W0, b0, A1); break;
@@ -1531,6 +1611,7 @@ struct FinalArgs {
     long gw_split;
     const DbDesc *db;                // column-sum sources
     double half_inv_s2, inv_a2;
+    float gscale;                    // data-term gradient scale (1 / sigma^2) / dscale
 };
 
 // grid (nlight + ceil(nheavy / 8) + 1, C): blocks 0..nlight-1 gather one entry per
@@ -1589,7 +1670,7 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
         for (int t = lane; t < d.n; t += 32) s += __ldg(dp + (long)t * d.tstride);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) g[(long)b * a.k + j] = s + q[(long)b * a.k + j] * (float)a.inv_a2;
+        if (lane == 0) g[(long)b * a.k + j] = a.gscale * s + q[(long)b * a.k + j] * (float)a.inv_a2;
         return;
     }
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1615,7 +1696,7 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
         for (int u = 0; u < 16; ++u) s += v[u];
     }
     for (; t < n; ++t) s += __ldg(dp + (long)t * stride);
-    g[(long)b * a.k + j] = s + qj * (float)a.inv_a2;
+    g[(long)b * a.k + j] = a.gscale * s + qj * (float)a.inv_a2;
 }
 
 template <typename V>
@@ -1628,11 +1709,11 @@ __global__ void k_scatter_plan(const float *q, long k, ScatterPlan sc)
         const int bi = sc.buf_id[j];
         const long o = (long)b * sc.cstride[bi] + sc.off[j];
         const float v = q[(long)b * k + j];
-        if (sc.is_bf16[bi]) {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-            reinterpret_cast<__nv_bfloat16 *>(sc.base[bi])[o] = hi;
+        if (sc.kind16[bi]) {
+            const h16 hi = f_to_h16(v);
+            reinterpret_cast<h16 *>(sc.base[bi])[o] = hi;
             if (sc.base_lo[bi])
-                reinterpret_cast<__nv_bfloat16 *>(sc.base_lo[bi])[o] = __float2bfloat16_rn(v - __bfloat162float(hi));
+                reinterpret_cast<h16 *>(sc.base_lo[bi])[o] = f_to_h16(v - h16_to_f(hi));
         } else {
             reinterpret_cast<float *>(sc.base[bi])[o] = v;
         }
@@ -1685,7 +1766,7 @@ CUtensorMap make_map(const void *base, uint64_t inner, uint64_t mid, uint64_t ou
     cuuint64_t strides[2] = {inner * 2, inner * mid * 2};
     cuuint32_t box[3] = {box_inner, box_mid, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
+    CUresult r = encode_fn()(&m, TM_H16, 3, const_cast<void *>(base), dims, strides, box, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -1730,12 +1811,14 @@ void launch_layer_w(const CUtensorMap &a, const CUtensorMap &wh, const CUtensorM
     HMC_LAUNCH_CK();
 }
 
-// A hidden layer on CTA pairs: forward with the hi/lo weights, reverse with hi only.
+// A hidden layer on CTA pairs, forward and reverse with the weights as a hi/lo pair: the
+// reverse products delta W are the forces' largest rounding error with W rounded once
+// (it is the same error at every leapfrog step, so it adds up along a trajectory).
 template <int MODE>
 void launch_layer(const CUtensorMap &a, const CUtensorMap &wh, const CUtensorMap &wl, const LayerParams &p, int ncta,
                   cudaStream_t s)
 {
-    constexpr bool SPLIT = (MODE == L_FWD_TANH || MODE == L_FWD_OUT);
+    constexpr bool SPLIT = true;
     if (p.W == 256) launch_layer_w<MODE, 256, SPLIT>(a, wh, wl, p, ncta, s);
     else launch_layer_w<MODE, 128, SPLIT>(a, wh, wl, p, ncta, s);
 }
@@ -1807,8 +1890,8 @@ class UmmaEngine final : public Engine {
         Wl_.resize(nh);
         bh_.resize(nh);
         for (int i = 0; i < nh; ++i) {
-            Wh_[i].reset(new DevBuf(sizeof(__nv_bfloat16) * C * w_ * w_));
-            Wl_[i].reset(new DevBuf(sizeof(__nv_bfloat16) * C * w_ * w_));
+            Wh_[i].reset(new DevBuf(sizeof(h16) * C * w_ * w_));
+            Wl_[i].reset(new DevBuf(sizeof(h16) * C * w_ * w_));
             bh_[i].reset(new DevBuf(sizeof(float) * C * w_));
         }
         wout_.alloc(sizeof(float) * C * w_);
@@ -1816,18 +1899,24 @@ class UmmaEngine final : public Engine {
         upload_rep(W0_, nd.woff[0], (long)w_ * dx_);
         upload_rep(b0_, nd.boff[0], w_);
         for (int i = 0; i < nh; ++i) {
-            upload_rep_bf16(*Wh_[i], *Wl_[i], nd.woff[i + 1], (long)w_ * w_);
+            upload_rep_h16(*Wh_[i], *Wl_[i], nd.woff[i + 1], (long)w_ * w_);
             upload_rep(*bh_[i], nd.boff[i + 1], w_);
         }
         upload_rep(wout_, nd.woff[L_ - 1], w_);
         upload_rep(bout_, nd.boff[L_ - 1], 1);
 
         // activations A_1..A_{L-2} and deltas delta_2..delta_{L-1}
-        const size_t act_bytes = sizeof(__nv_bfloat16) * C * std::max<long>(N_, 1) * w_;
+        const size_t act_bytes = sizeof(h16) * C * std::max<long>(N_, 1) * w_;
         A_.resize(L_);   // index i = 1..L-2
         D_.resize(L_);   // index i = 2..L-1
-        for (int i = 1; i <= L_ - 2; ++i) A_[i].reset(new DevBuf(act_bytes));
-        for (int i = 2; i <= L_ - 1; ++i) D_[i].reset(new DevBuf(act_bytes));
+        for (int i = 1; i <= L_ - 2; ++i) {
+            A_[i].reset(new DevBuf());
+            row_alloc(p.arena, *A_[i], act_bytes);
+        }
+        for (int i = 2; i <= L_ - 1; ++i) {
+            D_[i].reset(new DevBuf());
+            row_alloc(p.arena, *D_[i], act_bytes);
+        }
 
         // partials
         u_part_.alloc(sizeof(double) * C * ntiles_);
@@ -1932,7 +2021,7 @@ class UmmaEngine final : public Engine {
             dim3 grid((unsigned)ntiles_, C_);
             ProfScope ps("first_fwd", s);
             launch_first_fwd(dx_, grid, s, x_.as<float>(), (int)N_, w_, W0_.as<float>(), b0_.as<float>(),
-                             A_[1]->as<__nv_bfloat16>());
+                             A_[1]->as<h16>());
         }
         if (use_layer_) {
             layers_persistent(s);
@@ -1947,17 +2036,17 @@ class UmmaEngine final : public Engine {
             pp.bias = bh_[i - 1]->as<float>();
             pp.bias_b = w_;
             if (i < L_ - 2) {
-                pp.out = A_[i + 1]->as<__nv_bfloat16>();
+                pp.out = A_[i + 1]->as<h16>();
                 pp.out_b = act_b;
                 launch_umma<M_FWD_TANH, false, false, true>(A_row_[i], W_fwd_[i], W_fwd_lo_[i], pp, row_grid, s);
             } else {
-                pp.out = D_[L_ - 1]->as<__nv_bfloat16>();
+                pp.out = D_[L_ - 1]->as<h16>();
                 pp.out_b = act_b;
                 pp.wout = wout_.as<float>();
                 pp.wout_b = w_;
                 pp.bout = bout_.as<float>();
                 pp.y = y_.as<float>();
-                pp.inv_s2 = (float)(1.0 / (p_.sigma * p_.sigma));
+                pp.inv_s2 = (float)delta_scale(p_.sigma);
                 pp.u_part = u_part_.as<double>();
                 pp.dbout_part = dbout_part_.as<float>();
                 pp.dwout_part = dwout_part_.as<float>();
@@ -1973,11 +2062,11 @@ class UmmaEngine final : public Engine {
             pp.N = w_;
             pp.K = w_;
             pp.kb_per_split = (w_ + BK - 1) / BK;
-            pp.aux = A_[i]->as<__nv_bfloat16>();
+            pp.aux = A_[i]->as<h16>();
             pp.aux_b = act_b;
             pp.db_part = db_part_[i - 1]->as<float>();
             if (i > 1) {
-                pp.out = D_[i]->as<__nv_bfloat16>();
+                pp.out = D_[i]->as<h16>();
                 pp.out_b = act_b;
                 launch_umma<M_BWD_TANH, false, true, true>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], pp, row_grid, s);
             } else {
@@ -2004,6 +2093,7 @@ class UmmaEngine final : public Engine {
         fa.gw_split = (long)C_ * k_;
         fa.db = db_desc_.as<const DbDesc>();
         fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
+        fa.gscale = (float)(1.0 / (p_.sigma * p_.sigma) / delta_scale(p_.sigma));
         fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
         fa.heavy = heavy_.as<int>();
         fa.nheavy = nheavy_;
@@ -2027,7 +2117,7 @@ class UmmaEngine final : public Engine {
             dim3 grid((unsigned)ntiles_, C_);
             ProfScope ps("first_fwd3", s);
             launch_pdl(k_first_fwd3, grid, dim3(256), 0, s, x_.as<float>(), dx_, (int)N_, w_, W0_.as<float>(),
-                       b0_.as<float>(), A_[1]->as<__nv_bfloat16>(), D_[2]->as<__nv_bfloat16>());
+                       b0_.as<float>(), A_[1]->as<h16>(), D_[2]->as<h16>());
         }
         for (int i = 1; i <= L_ - 2; ++i) {
             E3Params e{};
@@ -2039,8 +2129,8 @@ class UmmaEngine final : public Engine {
             e.bias = bh_[i - 1]->as<float>();
             const dim3 grid(ntiles_, 1, C_);
             if (i < L_ - 2) {
-                e.out_hi = A_[i + 1]->as<__nv_bfloat16>();
-                e.out_lo = D_[i + 2]->as<__nv_bfloat16>();
+                e.out_hi = A_[i + 1]->as<h16>();
+                e.out_lo = D_[i + 2]->as<h16>();
                 launch_energy3<E3_TANH>(A_row_[i], D_row_[i + 1], W_fwd_[i], W_fwd_lo_[i], e, grid, s);
             } else {
                 e.wout = wout_.as<float>();
@@ -2055,6 +2145,7 @@ class UmmaEngine final : public Engine {
         fa.nu = ntiles_;
         fa.u_part = u_part_.as<double>();
         fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
+        fa.gscale = (float)(1.0 / (p_.sigma * p_.sigma) / delta_scale(p_.sigma));
         fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
         ProfScope ps("energy3_final", s);
         launch_pdl(k_finalize_bf16, dim3(1, C_), dim3(256), 0, s, fa, q, U, (float *)nullptr);
@@ -2174,35 +2265,35 @@ class UmmaEngine final : public Engine {
             LayerParams lp = base;
             lp.bias = bh_[i - 1]->as<float>();
             if (i < L_ - 2) {
-                lp.out = A_[i + 1]->as<__nv_bfloat16>();
+                lp.out = A_[i + 1]->as<h16>();
                 launch_layer<L_FWD_TANH>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
             } else {
-                lp.out = D_[L_ - 1]->as<__nv_bfloat16>();
+                lp.out = D_[L_ - 1]->as<h16>();
                 lp.wout = wout_.as<float>();
                 lp.bout = bout_.as<float>();
                 lp.y = y_.as<float>();
-                lp.inv_s2 = (float)(1.0 / (p_.sigma * p_.sigma));
+                lp.inv_s2 = (float)delta_scale(p_.sigma);
                 lp.u_part = u_part_.as<double>();
                 lp.dbout_part = dbout_part_.as<float>();
                 lp.dwout_part = dwout_part_.as<float>();
                 launch_layer<L_FWD_OUT>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
             }
         }
-        // reverse pass (bf16 W: the lo part is not needed there); the weight gradient of
+        // reverse pass (W as a hi/lo pair, like the forward pass); the weight gradient of
         // layer i runs first, while the delta written by the previous kernel is still in L2
         for (int i = L_ - 2; i >= 1; --i) {
             dw_layer(i, s);
             if (i <= nd.lmin) break;
             LayerParams lp = base;
-            lp.aux = A_[i]->as<__nv_bfloat16>();
+            lp.aux = A_[i]->as<h16>();
             if (i > 1) {
-                lp.out = D_[i]->as<__nv_bfloat16>();
-                launch_layer<L_BWD_TANH>(D_row_[i + 1], W_atom_[i], W_atom_[i], lp, ncta, s);
+                lp.out = D_[i]->as<h16>();
+                launch_layer<L_BWD_TANH>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], lp, ncta, s);
             } else {
                 lp.db_part = db_part_[0]->as<float>();
                 lp.x = x_.as<float>();
                 lp.dw0_part = dw0_part_.as<float>();
-                launch_layer<L_BWD_FIRST>(D_row_[i + 1], W_atom_[i], W_atom_[i], lp, ncta, s);
+                launch_layer<L_BWD_FIRST>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], lp, ncta, s);
             }
         }
     }
@@ -2224,18 +2315,18 @@ class UmmaEngine final : public Engine {
     }
 
     // W = hi + lo with hi = bf16(W) and lo = bf16(W - hi), W taken in float32
-    void upload_rep_bf16(DevBuf &hi, DevBuf &lo, long off, long count)
+    void upload_rep_h16(DevBuf &hi, DevBuf &lo, long off, long count)
     {
-        std::vector<__nv_bfloat16> vh(C_ * count), vl(C_ * count);
+        std::vector<h16> vh(C_ * count), vl(C_ * count);
         for (int c = 0; c < C_; ++c)
             for (long i = 0; i < count; ++i) {
                 const float w = (float)p_.frozen[off + i];
-                const __nv_bfloat16 h = __float2bfloat16_rn(w);
+                const h16 h = f_to_h16(w);
                 vh[c * count + i] = h;
-                vl[c * count + i] = __float2bfloat16_rn(w - __bfloat162float(h));
+                vl[c * count + i] = f_to_h16(w - h16_to_f(h));
             }
-        HMC_CK(cudaMemcpy(hi.ptr, vh.data(), sizeof(__nv_bfloat16) * vh.size(), cudaMemcpyHostToDevice));
-        HMC_CK(cudaMemcpy(lo.ptr, vl.data(), sizeof(__nv_bfloat16) * vl.size(), cudaMemcpyHostToDevice));
+        HMC_CK(cudaMemcpy(hi.ptr, vh.data(), sizeof(h16) * vh.size(), cudaMemcpyHostToDevice));
+        HMC_CK(cudaMemcpy(lo.ptr, vl.data(), sizeof(h16) * vl.size(), cudaMemcpyHostToDevice));
     }
 
     void build_entries()
@@ -2249,19 +2340,19 @@ class UmmaEngine final : public Engine {
         const int nh = L_ - 2;
         plan_.nbuf = 2 + 2 * nh + 2;
         HMC_REQUIRE(plan_.nbuf <= MAX_SCATTER_BUFS, "too many layers for the scatter plan");
-        plan_.base[0] = W0_.ptr; plan_.cstride[0] = (long)w_ * dx_; plan_.is_bf16[0] = 0;
-        plan_.base[1] = b0_.ptr; plan_.cstride[1] = w_; plan_.is_bf16[1] = 0;
+        plan_.base[0] = W0_.ptr; plan_.cstride[0] = (long)w_ * dx_; plan_.kind16[0] = 0;
+        plan_.base[1] = b0_.ptr; plan_.cstride[1] = w_; plan_.kind16[1] = 0;
         for (int i = 1; i <= nh; ++i) {
             plan_.base[2 + 2 * (i - 1)] = Wh_[i - 1]->ptr;
             plan_.cstride[2 + 2 * (i - 1)] = (long)w_ * w_;
-            plan_.is_bf16[2 + 2 * (i - 1)] = 1;
+            plan_.kind16[2 + 2 * (i - 1)] = H16_KIND;
             plan_.base_lo[2 + 2 * (i - 1)] = Wl_[i - 1]->ptr;
             plan_.base[3 + 2 * (i - 1)] = bh_[i - 1]->ptr;
             plan_.cstride[3 + 2 * (i - 1)] = w_;
-            plan_.is_bf16[3 + 2 * (i - 1)] = 0;
+            plan_.kind16[3 + 2 * (i - 1)] = 0;
         }
-        plan_.base[2 + 2 * nh] = wout_.ptr; plan_.cstride[2 + 2 * nh] = w_; plan_.is_bf16[2 + 2 * nh] = 0;
-        plan_.base[3 + 2 * nh] = bout_.ptr; plan_.cstride[3 + 2 * nh] = 1; plan_.is_bf16[3 + 2 * nh] = 0;
+        plan_.base[2 + 2 * nh] = wout_.ptr; plan_.cstride[2 + 2 * nh] = w_; plan_.kind16[2 + 2 * nh] = 0;
+        plan_.base[3 + 2 * nh] = bout_.ptr; plan_.cstride[3 + 2 * nh] = 1; plan_.kind16[3 + 2 * nh] = 0;
         for (long j = 0; j < k_; ++j) {
             const long id = p_.idx[j];
             int l = 0;
@@ -2368,7 +2459,7 @@ CUtensorMap make_map_ld(const void *base, uint64_t inner, uint64_t ld, uint64_t 
     cuuint64_t strides[2] = {ld * 2, ld * mid * 2};
     cuuint32_t box[3] = {box_inner, box_mid, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
+    CUresult r = encode_fn()(&m, TM_H16, 3, const_cast<void *>(base), dims, strides, box, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -2419,7 +2510,7 @@ class DonEngine final : public Engine {
         std::vector<float> tf(p.t.begin(), p.t.end());
         yt_.alloc(sizeof(float) * std::max<size_t>(tf.size(), 1));
         if (!tf.empty()) HMC_CK(cudaMemcpy(yt_.ptr, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice));
-        ds_.alloc(sizeof(__nv_bfloat16) * C * std::max<long>(nu_, 1) * nyp_);
+        row_alloc(p.arena, ds_, sizeof(h16) * C * std::max<long>(nu_, 1) * nyp_);
         HMC_CK(cudaMemset(ds_.ptr, 0, ds_.n));
         // S^T tiles: 128 query points (rows) x bs_ input functions (columns)
         bs_ = nu_ >= 256 ? 256 : (int)round_up(nu_, 32);
@@ -2474,8 +2565,8 @@ class DonEngine final : public Engine {
             if (!n.gemm_first) {
                 ProfScope ps("first_fwd3", s);
                 launch_pdl(k_first_fwd3, dim3((unsigned)n.ntiles, C_), dim3(256), 0, s, n.x32.as<float>(), n.dx,
-                           (int)n.R, n.w, n.w0f.as<float>(), n.bias[0]->as<float>(), n.act[1]->as<__nv_bfloat16>(),
-                           n.del[1]->as<__nv_bfloat16>());
+                           (int)n.R, n.w, n.w0f.as<float>(), n.bias[0]->as<float>(), n.act[1]->as<h16>(),
+                           n.del[1]->as<h16>());
             }
             for (int l = n.gemm_first ? 0 : 1; l < n.L; ++l) {
                 E3Params e{};
@@ -2485,8 +2576,8 @@ class DonEngine final : public Engine {
                 e.ntiles = n.ntiles;
                 e.err = err_;
                 e.bias = n.bias[l]->as<float>();
-                e.out_hi = n.act[l + 1]->as<__nv_bfloat16>();
-                e.out_lo = n.del[l + 1]->as<__nv_bfloat16>();
+                e.out_hi = n.act[l + 1]->as<h16>();
+                e.out_lo = n.del[l + 1]->as<h16>();
                 const CUtensorMap &ah = l == 0 ? n.x_row : n.act_row[l];
                 const CUtensorMap &al = l == 0 ? n.x_row_lo : n.del_row[l];
                 const dim3 grid(n.ntiles, 1, C_);
@@ -2511,6 +2602,7 @@ class DonEngine final : public Engine {
         fa.nu = nut_e_ * ntn_e_;
         fa.u_part = u_acc_.as<double>();
         fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
+        fa.gscale = (float)(1.0 / (p_.sigma * p_.sigma) / delta_scale(p_.sigma));
         fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
         ProfScope ps("energy3_final", s);
         launch_pdl(k_finalize_bf16, dim3(1, C_), dim3(256), 0, s, fa, q, U, (float *)nullptr);
@@ -2539,7 +2631,7 @@ class DonEngine final : public Engine {
             pp.K = (int)ny_;
             pp.kb_per_split = (int)((ny_ + BK - 1) / BK);
             pp.ntiles = br_.ntiles;
-            pp.out = br_.del[br_.L]->as<__nv_bfloat16>();
+            pp.out = br_.del[br_.L]->as<h16>();
             pp.out_b = nu_ * pl_;
             pp.db_part = br_.colsum[br_.L - 1]->as<float>();
             launch_umma<M_GEMM_BF16, false, true, false>(ds_row_, tr_.act_atom[tr_.L], tr_.act_atom[tr_.L], pp,
@@ -2552,7 +2644,7 @@ class DonEngine final : public Engine {
             pp.K = (int)nu_;
             pp.kb_per_split = (int)((nu_ + BK - 1) / BK);
             pp.ntiles = tr_.ntiles;
-            pp.out = tr_.del[tr_.L]->as<__nv_bfloat16>();
+            pp.out = tr_.del[tr_.L]->as<h16>();
             pp.out_b = ny_ * pl_;
             pp.db_part = tr_.colsum[tr_.L - 1]->as<float>();
             launch_umma<M_GEMM_BF16, true, true, false>(ds_atom_, br_.act_atom[br_.L], br_.act_atom[br_.L], pp,
@@ -2572,6 +2664,7 @@ class DonEngine final : public Engine {
         fa.gw_split = (long)C_ * k_;
         fa.db = db_desc_.as<const DbDesc>();
         fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
+        fa.gscale = (float)(1.0 / (p_.sigma * p_.sigma) / delta_scale(p_.sigma));
         fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
         fa.heavy = heavy_.as<int>();
         fa.nheavy = nheavy_;
@@ -2607,9 +2700,9 @@ class DonEngine final : public Engine {
         pp.ldo = (int)nyp_;
         pp.ntn = ntn_;
         pp.b0s = b0v_.as<float>();
-        pp.out = ds_.as<__nv_bfloat16>();
+        pp.out = ds_.as<h16>();
         pp.out_b = nu_ * nyp_;
-        pp.inv_s2 = (float)(1.0 / (p_.sigma * p_.sigma));
+        pp.inv_s2 = (float)delta_scale(p_.sigma);
         pp.u_part = u_part_.as<double>();
         pp.db0_part = db0_part_.as<float>();
         launch_umma<M_S, false, false, false>(tr_.act_row[tr_.L], bmap, bmap, pp, dim3(C_, nut_, ntn_), s);
@@ -2679,17 +2772,17 @@ class DonEngine final : public Engine {
         const int out = nd.w[l + 1], in = nd.w[l], ld = n.inld[l];
         const size_t per = (size_t)out * ld;
         if (bf16) {
-            std::vector<__nv_bfloat16> vh(C_ * per, __float2bfloat16_rn(0.0f)), vl(C_ * per, __float2bfloat16_rn(0.0f));
+            std::vector<h16> vh(C_ * per, f_to_h16(0.0f)), vl(C_ * per, f_to_h16(0.0f));
             for (int c = 0; c < C_; ++c)
                 for (int o = 0; o < out; ++o)
                     for (int i = 0; i < in; ++i) {
                         const float w = (float)p_.frozen[nd.woff[l] + (long)o * in + i];
-                        const __nv_bfloat16 h = __float2bfloat16_rn(w);
+                        const h16 h = f_to_h16(w);
                         vh[c * per + (size_t)o * ld + i] = h;
-                        vl[c * per + (size_t)o * ld + i] = __float2bfloat16_rn(w - __bfloat162float(h));
+                        vl[c * per + (size_t)o * ld + i] = f_to_h16(w - h16_to_f(h));
                     }
-            HMC_CK(cudaMemcpy(hi, vh.data(), sizeof(__nv_bfloat16) * vh.size(), cudaMemcpyHostToDevice));
-            HMC_CK(cudaMemcpy(lo, vl.data(), sizeof(__nv_bfloat16) * vl.size(), cudaMemcpyHostToDevice));
+            HMC_CK(cudaMemcpy(hi, vh.data(), sizeof(h16) * vh.size(), cudaMemcpyHostToDevice));
+            HMC_CK(cudaMemcpy(lo, vl.data(), sizeof(h16) * vl.size(), cudaMemcpyHostToDevice));
         } else {
             std::vector<float> v(C_ * per, 0.0f);
             for (int c = 0; c < C_; ++c)
@@ -2727,20 +2820,20 @@ class DonEngine final : public Engine {
         alloc_t(n.x32, sizeof(float) * std::max<size_t>(xf.size(), 1));
         if (!xf.empty()) HMC_CK(cudaMemcpy(n.x32.ptr, xf.data(), sizeof(float) * xf.size(), cudaMemcpyHostToDevice));
         if (n.gemm_first) {   // bf16 copy per chain, rows padded to dxp
-            std::vector<__nv_bfloat16> xb((size_t)C * std::max<long>(R, 1) * n.dxp, __float2bfloat16_rn(0.0f));
-            std::vector<__nv_bfloat16> xl(xb.size(), __float2bfloat16_rn(0.0f));
+            std::vector<h16> xb((size_t)C * std::max<long>(R, 1) * n.dxp, f_to_h16(0.0f));
+            std::vector<h16> xl(xb.size(), f_to_h16(0.0f));
             for (int c = 0; c < C; ++c)
                 for (long r = 0; r < R; ++r)
                     for (int d = 0; d < n.dx; ++d) {
                         const float v = xf[(size_t)r * n.dx + d];
-                        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                        const h16 h = f_to_h16(v);
                         xb[((size_t)c * R + r) * n.dxp + d] = h;
-                        xl[((size_t)c * R + r) * n.dxp + d] = __float2bfloat16_rn(v - __bfloat162float(h));
+                        xl[((size_t)c * R + r) * n.dxp + d] = f_to_h16(v - h16_to_f(h));
                     }
-            alloc_t(n.xb, sizeof(__nv_bfloat16) * xb.size());
-            alloc_t(n.xbl, sizeof(__nv_bfloat16) * xl.size());
-            HMC_CK(cudaMemcpy(n.xb.ptr, xb.data(), sizeof(__nv_bfloat16) * xb.size(), cudaMemcpyHostToDevice));
-            HMC_CK(cudaMemcpy(n.xbl.ptr, xl.data(), sizeof(__nv_bfloat16) * xl.size(), cudaMemcpyHostToDevice));
+            alloc_t(n.xb, sizeof(h16) * xb.size());
+            alloc_t(n.xbl, sizeof(h16) * xl.size());
+            HMC_CK(cudaMemcpy(n.xb.ptr, xb.data(), sizeof(h16) * xb.size(), cudaMemcpyHostToDevice));
+            HMC_CK(cudaMemcpy(n.xbl.ptr, xl.data(), sizeof(h16) * xl.size(), cudaMemcpyHostToDevice));
             n.x_row = make_map_ld(n.xb.ptr, n.dx, n.dxp, R, C, 64, 128);
             n.x_row_lo = make_map_ld(n.xbl.ptr, n.dx, n.dxp, R, C, 64, 128);
             n.x_atom = make_map_ld(n.xb.ptr, n.dx, n.dxp, R, C, 64, 64);
@@ -2755,7 +2848,7 @@ class DonEngine final : public Engine {
                 upload_w(n, 0, n.w0f.ptr, nullptr, false);
                 continue;
             }
-            const size_t wb = sizeof(__nv_bfloat16) * C * out * n.inld[l];
+            const size_t wb = sizeof(h16) * C * out * n.inld[l];
             n.wh[l].reset(track(new DevBuf(wb)));
             n.wl[l].reset(track(new DevBuf(wb)));
             upload_w(n, l, n.wh[l]->ptr, n.wl[l]->ptr, true);
@@ -2769,9 +2862,12 @@ class DonEngine final : public Engine {
         }
         // activations and deltas, per-tile column sums
         for (int l = 1; l <= n.L; ++l) {
-            const size_t ab = sizeof(__nv_bfloat16) * C * std::max<long>(R, 1) * nd.w[l];
-            n.act[l].reset(track(new DevBuf(ab)));
-            n.del[l].reset(track(new DevBuf(ab)));
+            const size_t ab = sizeof(h16) * C * std::max<long>(R, 1) * nd.w[l];
+            n.act[l].reset(new DevBuf());
+            n.del[l].reset(new DevBuf());
+            row_alloc(p_.arena, *n.act[l], ab);
+            row_alloc(p_.arena, *n.del[l], ab);
+            if (!p_.arena) bytes_ += 2 * ab;
             n.act_row[l] = make_map(n.act[l]->ptr, nd.w[l], R, C, 64, 128);
             n.act_atom[l] = make_map(n.act[l]->ptr, nd.w[l], R, C, 64, 64);
             n.del_row[l] = make_map(n.del[l]->ptr, nd.w[l], R, C, 64, 128);
@@ -2793,7 +2889,7 @@ class DonEngine final : public Engine {
             dim3 grid((unsigned)n.ntiles, C_);
             ProfScope ps("first_fwd", s);
             launch_first_fwd(n.dx, grid, s, n.x32.as<float>(), (int)n.R, n.w, n.w0f.as<float>(),
-                             n.bias[0]->as<float>(), n.act[1]->as<__nv_bfloat16>());
+                             n.bias[0]->as<float>(), n.act[1]->as<h16>());
         }
         for (int l = n.gemm_first ? 0 : 1; l < n.L; ++l) {
             Params pp = base();
@@ -2803,7 +2899,7 @@ class DonEngine final : public Engine {
             pp.kb_per_split = (pp.K + BK - 1) / BK;
             pp.bias = n.bias[l]->as<float>();
             pp.bias_b = pp.N;
-            pp.out = n.act[l + 1]->as<__nv_bfloat16>();
+            pp.out = n.act[l + 1]->as<h16>();
             pp.out_b = n.R * pp.N;
             const CUtensorMap &a = (l == 0) ? n.x_row : n.act_row[l];
             const dim3 grid(n.ntiles, 1, C_);
@@ -2846,7 +2942,7 @@ class DonEngine final : public Engine {
             pp.K = nd.w[l + 1];
             pp.kb_per_split = (pp.K + BK - 1) / BK;
             pp.ntiles = n.ntiles;
-            pp.aux = n.act[l]->as<__nv_bfloat16>();
+            pp.aux = n.act[l]->as<h16>();
             pp.aux_b = n.R * pp.N;
             pp.db_part = n.colsum[l - 1]->as<float>();
             const dim3 grid(n.ntiles, 1, C_);
@@ -2856,7 +2952,7 @@ class DonEngine final : public Engine {
                 pp.dw0_part = n.dw0.as<float>();
                 launch_umma<M_BWD_FIRST, false, true, true>(n.del_row[l + 1], n.w_atom_h[l], n.w_atom_l[l], pp, grid, s);
             } else {
-                pp.out = n.del[l]->as<__nv_bfloat16>();
+                pp.out = n.del[l]->as<h16>();
                 pp.out_b = n.R * pp.N;
                 launch_umma<M_BWD_TANH, false, true, true>(n.del_row[l + 1], n.w_atom_h[l], n.w_atom_l[l], pp, grid, s);
             }
@@ -2887,25 +2983,25 @@ class DonEngine final : public Engine {
                 if (l == 0 && !n.gemm_first) {
                     plan_.base[nb] = n.w0f.ptr;
                     plan_.cstride[nb] = (long)out * n.dx;
-                    plan_.is_bf16[nb] = 0;
+                    plan_.kind16[nb] = 0;
                 } else {
                     plan_.base[nb] = n.wh[l]->ptr;
                     plan_.base_lo[nb] = n.wl[l]->ptr;
                     plan_.cstride[nb] = (long)out * n.inld[l];
-                    plan_.is_bf16[nb] = 1;
+                    plan_.kind16[nb] = H16_KIND;
                 }
                 ++nb;
                 bbuf[t][l] = nb;
                 plan_.base[nb] = n.bias[l]->ptr;
                 plan_.cstride[nb] = out;
-                plan_.is_bf16[nb] = 0;
+                plan_.kind16[nb] = 0;
                 ++nb;
             }
         }
         const int b0buf = nb;
         plan_.base[nb] = b0v_.ptr;
         plan_.cstride[nb] = 1;
-        plan_.is_bf16[nb] = 0;
+        plan_.kind16[nb] = 0;
         ++nb;
         HMC_REQUIRE(nb <= MAX_SCATTER_BUFS, "too many layers for the scatter plan");
         plan_.nbuf = nb;
@@ -3013,6 +3109,7 @@ class DonEngine final : public Engine {
 
 }  // namespace
 
+#if !HMC_F16
 bool umma_engine_supports(const Problem &p, std::string *why)
 {
     auto no = [&](const char *m) {
@@ -3037,7 +3134,15 @@ bool umma_engine_supports(const Problem &p, std::string *why)
     return true;
 }
 
+#endif
+
+#if HMC_F16
+Engine *make_umma_engine_f16(Problem &p, int C) { return new UmmaEngine(p, C); }
+#else
 Engine *make_umma_engine_bf16(Problem &p, int C) { return new UmmaEngine(p, C); }
+#endif
+
+#if !HMC_F16
 
 bool don_engine_supports(const Problem &p, std::string *why)
 {
@@ -3066,6 +3171,11 @@ bool don_engine_supports(const Problem &p, std::string *why)
     return true;
 }
 
+#endif
+
+#if HMC_F16
+Engine *make_don_engine_f16(Problem &p, int C) { return new DonEngine(p, C); }
+#else
 Engine *make_don_engine_bf16(Problem &p, int C) { return new DonEngine(p, C); }
 
 void expire_wait_run(int *err, long limit_ns, cudaStream_t s)
@@ -3073,9 +3183,11 @@ void expire_wait_run(int *err, long limit_ns, cudaStream_t s)
     k_expire_wait<<<1, 1, 0, s>>>(err, (unsigned long long)limit_ns);
     HMC_LAUNCH_CK();
 }
+#endif
 
 }  // namespace hmc
 
+#if !HMC_F16
 // ---------------------------------------------------------------------------
 // Diagnostic: one batched tensor-core GEMM, C[b][m][n] = sum_k A(m,k) B(n,k)
 // ---------------------------------------------------------------------------
@@ -3117,3 +3229,32 @@ extern "C" hmc_status hmc_diag_umma_gemm(int M, int N, int K, int batch, int a_m
         return f.st;
     }
 }
+#endif  // !HMC_F16
+
+#if HMC_F16
+namespace hmc {
+namespace {
+__global__ void k_diag_tanh(const float *x, float *y, long n)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        y[i] = act_tanh(x[i]);
+}
+}  // namespace
+}  // namespace hmc
+
+// The activation the fp16 engine applies, on n device floats (a diagnostic for its tests).
+extern "C" hmc_status hmc_diag_tanh16(const float *x, float *y, long n)
+{
+    using namespace hmc;
+    try {
+        HMC_REQUIRE(x && y && n >= 0, "bad argument");
+        if (n == 0) return HMC_OK;
+        k_diag_tanh<<<(unsigned)std::min<long>((n + 255) / 256, 4096), 256>>>(x, y, n);
+        HMC_LAUNCH_CK();
+        HMC_CK(cudaDeviceSynchronize());
+        return HMC_OK;
+    } catch (const Fail &f) {
+        return f.st;
+    }
+}
+#endif

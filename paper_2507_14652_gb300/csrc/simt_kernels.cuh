@@ -107,6 +107,143 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g, EpiArgs<T> e)
     }
 }
 
+// FP32: C[b](m, n) = sum_k A[b](m, k) B[b](k, n) on 128 x 128 tiles, 16-deep K stages
+// double-buffered through shared memory, 8 x 8 outputs per thread (two 4-row and two
+// 4-column groups 64 apart, read as float4).  With splits > 1, blockIdx.z covers
+// (batch, split) and each CTA sums its own K range [sp kchunk, (sp + 1) kchunk) into the
+// raw partial ws[sp][b][m][n]; k_splitk_reduce then adds the splits in order and applies
+// the epilogue, so the result is the same for any batch size.
+constexpr int GB_M = 128, GB_N = 128, GB_K = 16, GB_PAD = 4;
+
+__device__ __forceinline__ void gemm_epilogue(const EpiArgs<float> &e, int b, long m, long n, float v)
+{
+    const long o = (long)b * e.o_b + m * e.o_m + n * e.o_n;
+    if (e.mode == EPI_ACT) {
+        const float z = v + (e.bias ? e.bias[(long)b * e.bias_b + n * e.bias_n] : 0.0f);
+        float a, sl;
+        act_eval(e.act, z, a, sl);
+        e.out[o] = a;
+        if (e.slope) e.slope[o] = sl;
+    } else if (e.mode == EPI_SCALE) {
+        const long so = (long)b * (e.slope_b < 0 ? e.o_b : e.slope_b) + m * e.o_m + n * e.o_n;
+        e.out[o] = v * e.slope[so];
+    } else {
+        e.out[o] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gemm_f32(GemmArgs<float> g, EpiArgs<float> e, float *ws, int splits,
+                                                   int kchunk)
+{
+    __shared__ __align__(16) float As[2][GB_K][GB_M + GB_PAD];
+    __shared__ __align__(16) float Bs[2][GB_K][GB_N + GB_PAD];
+    const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
+    const long m0 = (long)blockIdx.y * GB_M, n0 = (long)blockIdx.x * GB_N;
+    const int kbeg = sp * kchunk, kend = min(g.K, kbeg + kchunk);
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const float *A = g.A + (long)b * g.a_b;
+    const float *B = g.B + (long)b * g.b_b;
+    // element r of this thread's share of a stage: (k, m) of A and (k, n) of B, laid out so
+    // that a warp's loads run along the operand's contiguous dimension
+    const bool a_kc = g.a_k == 1, b_nc = g.b_n == 1;
+    float ra[8], rb[8];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int el = tid + 256 * r;
+            const int kk = a_kc ? (el & 15) : (el >> 7), mm = a_kc ? (el >> 4) : (el & 127);
+            const long gm = m0 + mm;
+            const int gk = k0 + kk;
+            ra[r] = (gm < g.M && gk < kend) ? A[gm * g.a_m + (long)gk * g.a_k] : 0.0f;
+            const int kb = b_nc ? (el >> 7) : (el & 15), nn = b_nc ? (el & 127) : (el >> 4);
+            const long gn = n0 + nn;
+            const int gkb = k0 + kb;
+            rb[r] = (gn < g.N && gkb < kend) ? B[(long)gkb * g.b_k + gn * g.b_n] : 0.0f;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int el = tid + 256 * r;
+            As[buf][a_kc ? (el & 15) : (el >> 7)][a_kc ? (el >> 4) : (el & 127)] = ra[r];
+            Bs[buf][b_nc ? (el >> 7) : (el & 15)][b_nc ? (el & 127) : (el >> 4)] = rb[r];
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    int buf = 0;
+    if (kbeg < kend) {
+        load(kbeg);
+        store(0);
+    }
+    __syncthreads();
+    for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
+        const bool more = k0 + GB_K < kend;
+        if (more) load(k0 + GB_K);   // the next stage's loads are in flight during the FMAs
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+        }
+        if (more) store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const long m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const long n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+            if (n >= g.N) continue;
+            if (splits > 1) ws[(((long)sp * (gridDim.z / splits) + b) * g.M + m) * g.N + n] = acc[i][j];
+            else gemm_epilogue(e, b, m, n, acc[i][j]);
+        }
+    }
+}
+
+// Sum the split-K partials in split order and apply the epilogue.
+__global__ void __launch_bounds__(256) k_splitk_reduce(const float *ws, int splits, int batch, int M, int N,
+                                                        EpiArgs<float> e)
+{
+    const long per = (long)M * N, tot = per * batch;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long)gridDim.x * blockDim.x) {
+        float v = 0.0f;
+        for (int sp = 0; sp < splits; ++sp) v += ws[(long)sp * tot + i];
+        const int b = (int)(i / per);
+        const long r = i % per;
+        gemm_epilogue(e, b, r / N, r % N, v);
+    }
+}
+
+// K-splits of an FP32 GEMM: a reduction over many rows (the weight gradients, K = data
+// rows) on few output tiles gets K ranges of about 512 (at most 64 of them), enough CTAs
+// to fill the GPU; the count depends on the shape only, never on the batch.
+inline int gemm_splits(int M, int N, int K)
+{
+    const long tiles = (long)((M + GB_M - 1) / GB_M) * ((N + GB_N - 1) / GB_N);
+    if (K < 2048 || tiles >= 64) return 1;
+    return (int)std::min<long>(64, (K + 511) / 512);
+}
+
+inline size_t gemm_ws_floats(int M, int N, int K, int batch)
+{
+    const int sp = gemm_splits(M, N, K);
+    return sp > 1 ? (size_t)sp * batch * M * N : 0;
+}
+
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double *sm)
 {
@@ -141,12 +278,32 @@ __global__ void k_colsum(const T *d, long rows, int cols, long d_b, T *out, long
     }
 }
 
+// ws / ws_floats: split-K workspace (FP32 only; without one, or when it is too small, the
+// GEMM runs unsplit).
 template <typename T>
-void launch_gemm(const GemmArgs<T> &g, const EpiArgs<T> &e, int batch, cudaStream_t s)
+void launch_gemm(const GemmArgs<T> &g, const EpiArgs<T> &e, int batch, cudaStream_t s, float *ws = nullptr,
+                 size_t ws_floats = 0)
 {
     if (g.M <= 0 || g.N <= 0) return;
-    dim3 grid((g.N + TILE - 1) / TILE, (g.M + TILE - 1) / TILE, batch);
-    ProfScope ps(sizeof(T) == 8 ? "simt_gemm_f64" : "simt_gemm_f32", s);
-    k_gemm<T><<<grid, 256, 0, s>>>(g, e);
-    HMC_LAUNCH_CK();
+    if constexpr (sizeof(T) == 4) {
+        int splits = gemm_splits(g.M, g.N, g.K);
+        if (!ws || ws_floats < gemm_ws_floats(g.M, g.N, g.K, batch)) splits = 1;
+        // K range of one split: K / splits rounded up to whole 16-deep stages
+        const int kchunk = splits > 1 ? ((g.K + splits - 1) / splits + GB_K - 1) / GB_K * GB_K : std::max(g.K, 1);
+        dim3 grid((g.N + GB_N - 1) / GB_N, (g.M + GB_M - 1) / GB_M, batch * splits);
+        ProfScope ps("simt_gemm_f32", s);
+        k_gemm_f32<<<grid, 256, 0, s>>>(g, e, ws, splits, kchunk);
+        HMC_LAUNCH_CK();
+        if (splits > 1) {
+            const long tot = (long)batch * g.M * g.N;
+            k_splitk_reduce<<<(unsigned)std::min<long>((tot + 255) / 256, 4096), 256, 0, s>>>(ws, splits, batch, g.M,
+                                                                                             g.N, e);
+            HMC_LAUNCH_CK();
+        }
+    } else {
+        dim3 grid((g.N + TILE - 1) / TILE, (g.M + TILE - 1) / TILE, batch);
+        ProfScope ps("simt_gemm_f64", s);
+        k_gemm<T><<<grid, 256, 0, s>>>(g, e);
+        HMC_LAUNCH_CK();
+    }
 }

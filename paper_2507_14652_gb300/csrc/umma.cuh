@@ -12,6 +12,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 namespace hmc {
@@ -122,6 +123,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool 
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// The same with fp16 A/B (A and B format fields 0).
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, bool a_mn, bool b_mn)
+{
+    return (1u << 4) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate)
 {
@@ -225,6 +233,15 @@ __device__ __forceinline__ void mma_m16n8k16_bf16(float (&d)[4], const uint32_t 
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// D (16 x 8, f32) += A (16 x 16, fp16) B (16 x 8, fp16) per warp.
+__device__ __forceinline__ void mma_m16n8k16_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 __device__ __forceinline__ void named_bar_sync(int id, int nthreads)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
@@ -235,6 +252,40 @@ __device__ __forceinline__ float tanh_fast(float x)
     float y;
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// tanh(x) as x P(x^2) / Q(x^2), P of degree 3 and Q of degree 4 in x^2, fitted to tanh
+// on [0, 9] by this project (iteratively reweighted least squares towards the minimax
+// fit), with |x| clamped to 9, where tanh is 1 to within 3e-8: the absolute error stays
+// below 5e-7 over the whole range in fp32, under half an fp16 unit of every value above
+// 2^-11 in magnitude, for one reciprocal and nine FMAs (the hardware tanh approximation
+// keeps about 11 bits, as coarse as fp16 itself).
+__device__ __forceinline__ float tanh_acc(float x)
+{
+    const float xc = fminf(fmaxf(x, -9.0f), 9.0f);
+    const float t = xc * xc;
+    float pn = fmaf(t, 1.0297558219463099e-05f, 0.0028405857738107443f);
+    pn = fmaf(t, pn, 0.128202423453331f);
+    pn = fmaf(t, pn, 0.9999983906745911f);
+    float qd = fmaf(t, 2.1103315361870045e-07f, 0.00022342491138260812f);
+    qd = fmaf(t, qd, 0.02335633896291256f);
+    qd = fmaf(t, qd, 0.4615301191806793f);
+    qd = fmaf(t, qd, 1.0f);
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(qd));
+    return fminf(fmaxf(xc * pn * r, -1.0f), 1.0f);
+}
+
+__device__ __forceinline__ uint32_t pack_f16(float a, float b)
+{
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ float2 unpack_f16(uint32_t u)
+{
+    __half2 h = *reinterpret_cast<__half2 *>(&u);
+    return __half22float2(h);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)

@@ -5,17 +5,18 @@ import paper_2507_14652_gb300 as hmc
 import workloads as W
 
 
-def sampler_from(prob, prec, chains=None, n_splits=1):
+def sampler_from(prob, prec, chains=None, n_splits=1, rows_per_pass=0):
     C = prob.chains if chains is None else chains
     if prob.kind == W.KIND_MLP:
         return hmc.Sampler.mlp(prob.net.widths, prob.x, prob.y, prob.mask, prob.frozen, C,
                                prior_sigma=prob.prior_sigma, noise_sigma=prob.noise_sigma, prec=prec,
-                               act=prob.net.act, bias=prob.net.bias, n_splits=n_splits)
+                               act=prob.net.act, bias=prob.net.bias, n_splits=n_splits,
+                               rows_per_pass=rows_per_pass)
     return hmc.Sampler.deeponet(prob.branch.widths, prob.trunk.widths, prob.u, prob.yq, prob.t, prob.mask,
                                 prob.frozen, C, prior_sigma=prob.prior_sigma, noise_sigma=prob.noise_sigma,
                                 prec=prec, out_bias=prob.out_bias, branch_act=prob.branch.act,
                                 trunk_act=prob.trunk.act, branch_bias=prob.branch.bias,
-                                trunk_bias=prob.trunk.bias, n_splits=n_splits)
+                                trunk_bias=prob.trunk.bias, n_splits=n_splits, rows_per_pass=rows_per_pass)
 
 
 def rel_err(a, b):

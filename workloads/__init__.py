@@ -324,6 +324,39 @@ def small_mlp(n=300, widths=(3, 40, 33, 2), acts=None, bias=True, frac=0.3, chai
                    n_samples=20, seed=0, net=net, x=x, y=y)
 
 
+def mlp_fanin(n=256, widths=(2, 64, 64, 1), chains=16, noise=0.1, prior=1.0, scale=1.5, seed=9191):
+    """MLP with frozen weights N(0, (scale / sqrt(fan_in))^2) and biases N(0, 0.5^2), so
+    the hidden units stay out of saturation and their features differ; targets
+    sin(pi x1) cos(pi x2) + N(0, noise^2).  The subset is empty: callers choose it."""
+    rng = np.random.default_rng(seed)
+    net = Net.mlp(list(widths))
+    x = _f32(rng.uniform(-1.0, 1.0, size=(n, widths[0])))
+    yb = np.sin(np.pi * x[:, :1]) * (np.cos(np.pi * x[:, 1:2]) if widths[0] >= 2 else 1.0)
+    y = _f32(np.repeat(yb, widths[-1], axis=1) + noise * rng.standard_normal((n, widths[-1])))
+    P = net.n_params()
+    frozen = np.zeros(P)
+    for l, (wo, bo) in enumerate(net.layer_slices()):
+        wi, wout = net.widths[l], net.widths[l + 1]
+        frozen[wo:wo + wi * wout] = scale / np.sqrt(wi) * rng.standard_normal(wi * wout)
+        if bo >= 0:
+            frozen[bo:bo + wout] = 0.5 * rng.standard_normal(wout)
+    frozen = _f32(frozen)
+    mask = np.zeros(P, dtype=np.uint8)
+    q0 = np.zeros((chains, 0))
+    return Problem("mlp_fanin", KIND_MLP, noise, prior, frozen, mask, q0, eps=1e-3, L=10,
+                   n_samples=1000, seed=0, net=net, x=x, y=y)
+
+
+def with_subset(prob, mask, chains=None, jitter=0.01, seed=None):
+    """The same problem sampling the parameters of `mask`; chains start at the frozen
+    values (chain 0) plus seeded N(0, jitter^2) (the others)."""
+    rng = np.random.default_rng(prob.seed + 4242 if seed is None else seed)
+    p = Problem(**{**prob.__dict__})
+    p.mask = np.asarray(mask, dtype=np.uint8)
+    p.q0 = _initial_states(rng, p.frozen, p.mask, prob.chains if chains is None else chains, jitter=jitter)
+    return p
+
+
 def small_deeponet(n_u=37, n_y=29, du=12, dy=2, width=24, latent=10, frac=0.3, chains=3,
                    eps=1e-3, L=6, noise=0.2, seed=8008, out_bias=True):
     """Small ragged DeepONet used by parity and finite-difference tests."""

@@ -63,7 +63,7 @@ __host__ __device__ constexpr uint32_t idesc_h16(int M, int N, bool a_mn, bool b
 {
     return idesc_f16(M, N, a_mn, b_mn);
 }
-// fp16 keeps 11 significant bits, so the activations get a tanh accurate to 5e-7
+// fp16 keeps 11 significant bits, so the activations get a tanh accurate to 1e-6
 __device__ __forceinline__ float act_tanh(float x) { return tanh_acc(x); }
 #else
 using h16 = __nv_bfloat16;

@@ -150,14 +150,14 @@ def test_fp16_acceptance_matches_fp32_on_paired_starts():
     assert abs(diff.mean()) <= 3.0 * se + 0.01, (a32.mean(), a16.mean(), se)
 
 
-def test_fp16_engine_tanh_is_accurate_to_5e_7():
-    # the fp16 engine's epilogues apply a fitted rational tanh; its absolute error must stay
-    # under half an fp16 unit of values above 2^-11 (here: 5e-7 everywhere), and |tanh| <= 1
+def test_fp16_engine_tanh_is_accurate_to_1e_6():
+    # the fp16 engine's epilogues evaluate tanh from the base-2 exponential and reciprocal;
+    # its absolute error must stay under half an fp16 unit of values above 2^-8 (1e-6
+    # everywhere), with |tanh| <= 1
     x = torch.cat([torch.linspace(-40, 40, 1 << 20), torch.linspace(-1e-3, 1e-3, 4096),
                    torch.tensor([1e30, -1e30, 9.0, -9.0, 0.0])]).float().cuda()
     y = torch.empty_like(x)
     assert hmc.lib().hmc_diag_tanh16(x.data_ptr(), y.data_ptr(), x.numel()) == 0
     ref = torch.tanh(x.double())
-    assert (y.double() - ref).abs().max().item() <= 5e-7
+    assert (y.double() - ref).abs().max().item() <= 1e-6
     assert y.abs().max().item() <= 1.0
-

@@ -146,9 +146,10 @@ HMC_API hmc_status hmc_create(hmc_handle *out, const hmc_net_spec *spec, const h
  * drifts and the Metropolis step cover all problems in single launches.  State vectors of a batch handle are
  * packed per problem: q = [problem][chain][k_problem]; U, accepted and dH are
  * [problem][chain] per trajectory.  Momenta of problem p use Philox stream p.
- * In an HMC_PREC_BF16 or HMC_PREC_FP16 batch, a problem whose network the tensor-core kernels do not
- * cover (a hidden width that is not a multiple of 64, say) runs on the FP32 CUDA-core
- * engine instead; its positions are float like the others'.
+ * In an HMC_PREC_BF16 or HMC_PREC_FP16 batch, a problem whose network the tensor-core
+ * kernels do not cover (a hidden width above 256, a sine activation, say) runs on the FP32
+ * CUDA-core engine instead; its positions are float like the others'.  Hidden widths that
+ * are not multiples of 64 run on the tensor cores, padded with zero units.
  */
 HMC_API hmc_status hmc_create_batch(hmc_handle *out, int n_problems, const hmc_net_spec *specs,
                             const hmc_data *data, const double *prior_sigma,

@@ -1864,7 +1864,11 @@ class UmmaEngine final : public Engine {
     {
         const NetDesc &nd = p.net;
         L_ = nd.L;
-        w_ = nd.w[1];
+        // hidden widths that are not a multiple of 64 are padded with units whose weights
+        // and biases are zero: they output tanh(0) = 0, feed nothing forward and receive no
+        // delta, so U and the gradient of every real parameter are unchanged
+        wl_ = nd.w[1];
+        w_ = (wl_ + 63) / 64 * 64;
         dx_ = nd.w[0];
         N_ = p.n;
         k_ = p.k;
@@ -1896,14 +1900,14 @@ class UmmaEngine final : public Engine {
         }
         wout_.alloc(sizeof(float) * C * w_);
         bout_.alloc(sizeof(float) * C);
-        upload_rep(W0_, nd.woff[0], (long)w_ * dx_);
-        upload_rep(b0_, nd.boff[0], w_);
+        upload_rep(W0_, nd.woff[0], wl_, dx_, w_, dx_);
+        upload_rep(b0_, nd.boff[0], 1, wl_, 1, w_);
         for (int i = 0; i < nh; ++i) {
-            upload_rep_h16(*Wh_[i], *Wl_[i], nd.woff[i + 1], (long)w_ * w_);
-            upload_rep(*bh_[i], nd.boff[i + 1], w_);
+            upload_rep_h16(*Wh_[i], *Wl_[i], nd.woff[i + 1], wl_, wl_, w_, w_);
+            upload_rep(*bh_[i], nd.boff[i + 1], 1, wl_, 1, w_);
         }
-        upload_rep(wout_, nd.woff[L_ - 1], w_);
-        upload_rep(bout_, nd.boff[L_ - 1], 1);
+        upload_rep(wout_, nd.woff[L_ - 1], 1, wl_, 1, w_);
+        upload_rep(bout_, nd.boff[L_ - 1], 1, 1, 1, 1);
 
         // activations A_1..A_{L-2} and deltas delta_2..delta_{L-1}
         const size_t act_bytes = sizeof(h16) * C * std::max<long>(N_, 1) * w_;
@@ -2306,25 +2310,30 @@ class UmmaEngine final : public Engine {
         return (total_kb + per - 1) / per;
     }
 
-    void upload_rep(DevBuf &dst, long off, long count)
+    // the frozen [rows][cols] block at `off`, zero-padded to [prow][pcol], for every chain
+    void upload_rep(DevBuf &dst, long off, int rows, int cols, int prow, int pcol)
     {
-        std::vector<float> v(C_ * count);
+        const long count = (long)prow * pcol;
+        std::vector<float> v(C_ * count, 0.0f);
         for (int c = 0; c < C_; ++c)
-            for (long i = 0; i < count; ++i) v[c * count + i] = (float)p_.frozen[off + i];
+            for (int r = 0; r < rows; ++r)
+                for (int i = 0; i < cols; ++i) v[c * count + (long)r * pcol + i] = (float)p_.frozen[off + (long)r * cols + i];
         HMC_CK(cudaMemcpy(dst.ptr, v.data(), sizeof(float) * v.size(), cudaMemcpyHostToDevice));
     }
 
-    // W = hi + lo with hi = bf16(W) and lo = bf16(W - hi), W taken in float32
-    void upload_rep_h16(DevBuf &hi, DevBuf &lo, long off, long count)
+    // W = hi + lo with hi = h16(W) and lo = h16(W - hi), W taken in float32, zero-padded
+    void upload_rep_h16(DevBuf &hi, DevBuf &lo, long off, int rows, int cols, int prow, int pcol)
     {
-        std::vector<h16> vh(C_ * count), vl(C_ * count);
+        const long count = (long)prow * pcol;
+        std::vector<h16> vh(C_ * count, f_to_h16(0.0f)), vl(C_ * count, f_to_h16(0.0f));
         for (int c = 0; c < C_; ++c)
-            for (long i = 0; i < count; ++i) {
-                const float w = (float)p_.frozen[off + i];
-                const h16 h = f_to_h16(w);
-                vh[c * count + i] = h;
-                vl[c * count + i] = f_to_h16(w - h16_to_f(h));
-            }
+            for (int r = 0; r < rows; ++r)
+                for (int i = 0; i < cols; ++i) {
+                    const float w = (float)p_.frozen[off + (long)r * cols + i];
+                    const h16 h = f_to_h16(w);
+                    vh[c * count + (long)r * pcol + i] = h;
+                    vl[c * count + (long)r * pcol + i] = f_to_h16(w - h16_to_f(h));
+                }
         HMC_CK(cudaMemcpy(hi.ptr, vh.data(), sizeof(h16) * vh.size(), cudaMemcpyHostToDevice));
         HMC_CK(cudaMemcpy(lo.ptr, vl.data(), sizeof(h16) * vl.size(), cudaMemcpyHostToDevice));
     }
@@ -2381,14 +2390,15 @@ class UmmaEngine final : public Engine {
                     rp[l][erow[j] + 1]++;
                     layer_entries_[l]++;
                     bid[j] = 2 + 2 * (l - 1);
+                    boff[j] = erow[j] * w_ + ecol[j];   // in the padded [w_][w_] layout
                 } else {
                     kind[j] = E_PART;
                     layer[j] = l;
                     off[j] = (int)rel;
                     bias_entries_[l]++;
                     bid[j] = 3 + 2 * (l - 1);
+                    boff[j] = (int)rel;
                 }
-                boff[j] = (int)rel;
             }
         }
         // row pointers: entries are ascending in parameter index, so a layer's weight entries
@@ -2425,7 +2435,7 @@ class UmmaEngine final : public Engine {
     }
 
     Problem &p_;
-    int C_, L_ = 0, w_ = 0, dx_ = 0, ntiles_ = 1, nsplit_ = 1, nsplit2_ = 1, num_sms_ = 148;
+    int C_, L_ = 0, w_ = 0, wl_ = 0, dx_ = 0, ntiles_ = 1, nsplit_ = 1, nsplit2_ = 1, num_sms_ = 148;
     long N_ = 0, k_ = 0;
     int *err_ = nullptr;
     DevBuf x_, y_, W0_, b0_, wout_, bout_, u_part_, dbout_part_, dwout_part_, dw0_part_, db_desc_, gw_part_;
@@ -3120,7 +3130,7 @@ bool umma_engine_supports(const Problem &p, std::string *why)
     const NetDesc &nd = p.net;
     if (nd.L < 3) return no("need at least one hidden-to-hidden layer");
     const int w = nd.w[1];
-    if (w % 64 != 0 || w > 256) return no("hidden width must be 64, 128, 192 or 256");
+    if (w < 1 || w > 256) return no("hidden width must be at most 256 (padded to a multiple of 64)");
     for (int l = 1; l < nd.L; ++l)
         if (nd.w[l] != w) return no("all hidden layers must have the same width");
     if (nd.w[nd.L] != 1) return no("the output width must be 1");

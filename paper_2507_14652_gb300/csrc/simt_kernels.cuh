@@ -1,11 +1,9 @@
 // simt_kernels.cuh -- CUDA-core building blocks shared by the FP64/FP32 engine and the
-// sensitivity pass: a batched 64x64-tile GEMM with fused epilogues, a fixed-order
-// FP64 block sum and FP64 column sums.  Include it inside an anonymous namespace of
+// sensitivity pass: batched GEMMs with fused epilogues (FP32 on 128 x 128 tiles with a
+// split-K for long reductions, FP64 on 16 x 16 tiles), a fixed-order FP64 block sum and
+// FP64 column sums.  Include it inside an anonymous namespace of
 // namespace hmc (every translation unit keeps its own copies).
 #pragma once
-
-constexpr int TILE = 64;
-constexpr int TK = 16;
 
 template <typename T> struct GemmArgs {
     int M, N, K;
@@ -37,73 +35,49 @@ __device__ __forceinline__ void act_eval(int act, float z, float &a, float &s)
     else { a = z; s = 1.0f; }
 }
 
-// C[b](m, n) = sum_k A[b](m, k) B[b](k, n), 64x64 tile, 16-deep K steps, 4x4 per thread.
+// FP64: C[b](m, n) = sum_k A[b](m, k) B[b](k, n), one output per thread on 16 x 16 tiles.
+// GB300's FP64 units are few, so work on padding costs real time: a 16 x 16 tile wastes
+// little on the small shapes the FP64 engine serves (a 20 x 20 weight gradient filled 10%
+// of a 64 x 64 tile).  Each output sums K in order, so results are reproducible.
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemm(GemmArgs<T> g, EpiArgs<T> e)
+__global__ void __launch_bounds__(256) k_gemm16(GemmArgs<T> g, EpiArgs<T> e)
 {
-    __shared__ T As[TK][TILE + 1];
-    __shared__ T Bs[TK][TILE + 1];
+    __shared__ T As[16][17];
+    __shared__ T Bs[16][17];
     const int b = blockIdx.z;
-    const long m0 = (long)blockIdx.y * TILE, n0 = (long)blockIdx.x * TILE;
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const long m0 = (long)blockIdx.y * 16, n0 = (long)blockIdx.x * 16;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const T *A = g.A + (long)b * g.a_b;
     const T *B = g.B + (long)b * g.b_b;
-    T acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-
-    for (int k0 = 0; k0 < g.K; k0 += TK) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            int el = tid + 256 * r;
-            int mm, kk;
-            if (g.a_k == 1) { kk = el % TK; mm = el / TK; } else { mm = el % TILE; kk = el / TILE; }
-            long gm = m0 + mm; int gk = k0 + kk;
-            As[kk][mm] = (gm < g.M && gk < g.K) ? A[gm * g.a_m + (long)gk * g.a_k] : T(0);
-            int nn;
-            if (g.b_n == 1) { nn = el % TILE; kk = el / TILE; } else { kk = el % TK; nn = el / TK; }
-            long gn = n0 + nn; gk = k0 + kk;
-            Bs[kk][nn] = (gn < g.N && gk < g.K) ? B[(long)gk * g.b_k + gn * g.b_n] : T(0);
+    T acc = T(0);
+    for (int k0 = 0; k0 < g.K; k0 += 16) {
+        {
+            const long m = m0 + ty;
+            const int k = k0 + tx;
+            As[ty][tx] = (m < g.M && k < g.K) ? A[m * g.a_m + (long)k * g.a_k] : T(0);
+            const int kb = k0 + ty;
+            const long n = n0 + tx;
+            Bs[ty][tx] = (kb < g.K && n < g.N) ? B[(long)kb * g.b_k + n * g.b_n] : T(0);
         }
         __syncthreads();
 #pragma unroll
-        for (int kk = 0; kk < TK; ++kk) {
-            T a[4], bb[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
-        }
+        for (int kk = 0; kk < 16; ++kk) acc += As[ty][kk] * Bs[kk][tx];
         __syncthreads();
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        long m = m0 + ty + 16 * i;
-        if (m >= g.M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            long n = n0 + tx + 16 * j;
-            if (n >= g.N) continue;
-            long o = (long)b * e.o_b + m * e.o_m + n * e.o_n;
-            if (e.mode == EPI_ACT) {
-                T z = acc[i][j] + (e.bias ? e.bias[(long)b * e.bias_b + n * e.bias_n] : T(0));
-                T a, s;
-                act_eval(e.act, z, a, s);
-                e.out[o] = a;
-                if (e.slope) e.slope[o] = s;
-            } else if (e.mode == EPI_SCALE) {
-                const long so = (long)b * (e.slope_b < 0 ? e.o_b : e.slope_b) + m * e.o_m + n * e.o_n;
-                e.out[o] = acc[i][j] * e.slope[so];
-            } else {
-                e.out[o] = acc[i][j];
-            }
-        }
+    const long m = m0 + ty, n = n0 + tx;
+    if (m >= g.M || n >= g.N) return;
+    const long o = (long)b * e.o_b + m * e.o_m + n * e.o_n;
+    if (e.mode == EPI_ACT) {
+        T z = acc + (e.bias ? e.bias[(long)b * e.bias_b + n * e.bias_n] : T(0));
+        T a, sl;
+        act_eval(e.act, z, a, sl);
+        e.out[o] = a;
+        if (e.slope) e.slope[o] = sl;
+    } else if (e.mode == EPI_SCALE) {
+        const long so = (long)b * (e.slope_b < 0 ? e.o_b : e.slope_b) + m * e.o_m + n * e.o_n;
+        e.out[o] = acc * e.slope[so];
+    } else {
+        e.out[o] = acc;
     }
 }
 
@@ -301,9 +275,9 @@ void launch_gemm(const GemmArgs<T> &g, const EpiArgs<T> &e, int batch, cudaStrea
             HMC_LAUNCH_CK();
         }
     } else {
-        dim3 grid((g.N + TILE - 1) / TILE, (g.M + TILE - 1) / TILE, batch);
+        dim3 grid((g.N + 15) / 16, (g.M + 15) / 16, batch);
         ProfScope ps("simt_gemm_f64", s);
-        k_gemm<T><<<grid, 256, 0, s>>>(g, e);
+        k_gemm16<T><<<grid, 256, 0, s>>>(g, e);
         HMC_LAUNCH_CK();
     }
 }

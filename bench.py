@@ -218,11 +218,18 @@ def other_workloads(hmc, torch, steps=3):
                                   prior_sigma=p.prior_sigma, noise_sigma=p.noise_sigma, prec=pr)
         timed("deeponet_grf_" + nm, sp, p.q0, p.eps, p.L, p.chains, nm)
     probs = W.batched_uneven()
-    bs = hmc.BatchSampler([(q.net.widths, q.x, q.y, q.mask, q.frozen, q.prior_sigma, q.noise_sigma) for q in probs],
-                          probs[0].chains, hmc.PREC_BF16)
+    tup = [(q.net.widths, q.x, q.y, q.mask, q.frozen, q.prior_sigma, q.noise_sigma) for q in probs]
     q0 = np.concatenate([q.q0.reshape(-1) for q in probs])   # packed [problem][chain][k_problem]
+    # grouped launches (the default), then every problem launching its own kernels on the
+    # batch's concurrent lanes, for comparison
+    bs = hmc.BatchSampler(tup, probs[0].chains, hmc.PREC_BF16)
+    groups = bs.groups()
     timed("batched_uneven_bf16", bs, q0.astype(np.float32), probs[0].eps, probs[0].L,
           len(probs) * probs[0].chains, "bf16", ess_traj=40)
+    out["batched_uneven_bf16"]["groups"] = groups
+    timed("batched_uneven_bf16_per_problem_launches", hmc.BatchSampler(tup, probs[0].chains, hmc.PREC_BF16,
+                                                                       grouped=False),
+          q0.astype(np.float32), probs[0].eps, probs[0].L, len(probs) * probs[0].chains, "bf16")
     p = W.cone_deeponet()
     sp = hmc.Sampler.deeponet(p.branch.widths, p.trunk.widths, p.u, p.yq, p.t, p.mask, p.frozen, p.chains,
                               prior_sigma=p.prior_sigma, noise_sigma=p.noise_sigma, prec=hmc.PREC_BF16)

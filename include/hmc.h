@@ -141,15 +141,19 @@ HMC_API hmc_status hmc_create(hmc_handle *out, const hmc_net_spec *spec, const h
 /*
  * Create one handle over n_problems independent problems (each with its own
  * spec, data, sigmas, mask and frozen vector, all with n_chains chains).  The problems
- * run side by side: every gradient evaluation forks them onto up to 16 stream lanes
- * (concurrent branches of the captured trajectory graph) and joins them again; the kicks,
+ * run side by side: in an HMC_PREC_BF16 or HMC_PREC_FP16 batch, the tensor-core MLP
+ * problems that share a kernel shape (padded hidden width, input width) form a group
+ * whose gradient takes one launch per kernel and layer slot for all of them (a job
+ * table walked by each kernel, every problem on its own buffers, results identical to
+ * separate launches); groups and the remaining problems run on up to 16 stream lanes
+ * (concurrent branches of the captured trajectory graph) that join again; the kicks,
  * drifts and the Metropolis step cover all problems in single launches.  State vectors of a batch handle are
  * packed per problem: q = [problem][chain][k_problem]; U, accepted and dH are
  * [problem][chain] per trajectory.  Momenta of problem p use Philox stream p.
  * In an HMC_PREC_BF16 or HMC_PREC_FP16 batch, a problem whose network the tensor-core
  * kernels do not cover (a hidden width above 256, a sine activation, say) runs on the FP32
- * CUDA-core engine instead; its positions are float like the others'.  Hidden widths that
- * are not multiples of 64 run on the tensor cores, padded with zero units.
+ * CUDA-core engine instead; its positions are float like the others'.  Hidden widths up to
+ * 128 run on the tensor cores padded to 128 with zero units, wider ones padded to 256.
  */
 HMC_API hmc_status hmc_create_batch(hmc_handle *out, int n_problems, const hmc_net_spec *specs,
                             const hmc_data *data, const double *prior_sigma,

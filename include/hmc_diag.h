@@ -60,6 +60,18 @@ HMC_API long hmc_diag_device_bytes(void);
  * a test drive hmc_create's fallback to passes over the rows without filling the GPU. */
 HMC_API void hmc_diag_set_memory_cap(long bytes);
 
+/* Whether batch handles created from now on run their tensor-core MLP problems as grouped
+ * launches (on by default): problems whose engines share a kernel shape (padded width,
+ * input width, kernel family), two or more of them, take one launch per kernel and layer
+ * slot together instead of one per problem, with the same results bit for bit.  Off,
+ * every problem launches its own kernels on the batch's concurrent lanes. */
+HMC_API void hmc_diag_set_grouping(int on);
+
+/* The groups of a batch handle, one line each (problems, width, launches per gradient),
+ * NUL-terminated in buf (truncated to n bytes; buf may be NULL).  Returns the number of
+ * groups, or -1 for a bad handle. */
+HMC_API long hmc_diag_groups(hmc_handle h, char *buf, long n);
+
 /* The energy the Metropolis test uses, for states q [C][k] (device or host; U [C] host
  * or device doubles): on the tensor-core engines the accurate forward pass with
  * hi/lo activations, elsewhere the energy of hmc_energy_grad. */

@@ -40,7 +40,8 @@ EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_create_split", "hmc_create_chu
            "hmc_diag_philox", "hmc_diag_momenta", "hmc_diag_log_uniform", "hmc_diag_graph_kernels",
            "hmc_diag_profile_energy_grad", "hmc_diag_metropolis_energy", "hmc_diag_tuning",
            "hmc_diag_expire_wait", "hmc_diag_graph_captures", "hmc_diag_adapt_trace", "hmc_diag_dual_averaging",
-           "hmc_diag_device_bytes", "hmc_diag_set_memory_cap", "hmc_diag_tanh16"]
+           "hmc_diag_device_bytes", "hmc_diag_set_memory_cap", "hmc_diag_tanh16", "hmc_diag_set_grouping",
+           "hmc_diag_groups"]
 
 
 class HmcError(RuntimeError):
@@ -101,6 +102,10 @@ def lib():
         L.hmc_diag_set_memory_cap.argtypes = [lg]
         L.hmc_diag_tanh16.argtypes = [vp, vp, lg]
         L.hmc_diag_set_memory_cap.restype = None
+        L.hmc_diag_set_grouping.argtypes = [i]
+        L.hmc_diag_set_grouping.restype = None
+        L.hmc_diag_groups.argtypes = [vp, ct.c_char_p, lg]
+        L.hmc_diag_groups.restype = lg
         L.hmc_subset_size.argtypes = [vp]
         L.hmc_subset_size.restype = lg
         L.hmc_param_count.argtypes = [vp]
@@ -133,8 +138,8 @@ def lib():
         L.hmc_diag_tuning.restype = lg
         for f in EXPORTS:
             if f not in ("hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_last_error", "hmc_num_passes",
-                         "hmc_diag_device_bytes", "hmc_diag_set_memory_cap",
-                         "hmc_diag_graph_kernels", "hmc_diag_graph_captures", "hmc_diag_tuning"):
+                         "hmc_diag_device_bytes", "hmc_diag_set_memory_cap", "hmc_diag_set_grouping",
+                         "hmc_diag_groups", "hmc_diag_graph_kernels", "hmc_diag_graph_captures", "hmc_diag_tuning"):
                 getattr(L, f).restype = ct.c_int
         _lib = L
     return _lib
@@ -495,7 +500,9 @@ def diag_dual_averaging(dH, eps0, target):
 class BatchSampler(Sampler):
     """Several independent problems behind one handle (hmc_create_batch)."""
 
-    def __init__(self, problems, chains, prec, stream=None):
+    def __init__(self, problems, chains, prec, stream=None, grouped=True):
+        """grouped: problems of one tensor-core kernel shape share launches (the default);
+        False launches every problem's kernels on their own (for comparison)."""
         n = len(problems)
         specs = (NetSpec * n)()
         datas = (Data * n)()
@@ -521,13 +528,23 @@ class BatchSampler(Sampler):
         self.dtype = torch.float64 if prec == PREC_FP64 else torch.float32
         self._keep = keep
         h = ct.c_void_p()
-        _check(lib().hmc_create_batch(ct.byref(h), n, specs, datas, alphas, sigmas, masks, frozens, int(chains),
-                                      _stream_ptr(stream)))
+        lib().hmc_diag_set_grouping(1 if grouped else 0)
+        try:
+            _check(lib().hmc_create_batch(ct.byref(h), n, specs, datas, alphas, sigmas, masks, frozens, int(chains),
+                                          _stream_ptr(stream)))
+        finally:
+            lib().hmc_diag_set_grouping(1)
         self._h = h
         self.chains = int(chains)
         self.n_problems = n
         self.k = int(lib().hmc_subset_size(h))
         self.P = int(lib().hmc_param_count(h))
+
+    def groups(self):
+        """The handle's launch groups, one description per group."""
+        buf = ct.create_string_buffer(8192)
+        n = lib().hmc_diag_groups(self._h, buf, len(buf))
+        return [ln for ln in buf.value.decode().splitlines() if ln][:max(n, 0)]
 
 
 def _energy_grad_fn():

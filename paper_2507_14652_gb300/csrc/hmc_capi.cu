@@ -29,6 +29,9 @@ void set_error(const char *fmt, ...)
     g_err = buf;
 }
 
+// Whether new batch handles group their tensor-core problems (hmc_diag_set_grouping).
+std::atomic<bool> g_grouping{true};
+
 // Bytes held by DevBufs, and the cap hmc_diag_set_memory_cap may put on them.
 std::atomic<size_t> g_devbuf_bytes{0};
 std::atomic<size_t> g_devbuf_cap{~size_t(0)};
@@ -525,6 +528,10 @@ struct hmc_handle_s {
     // batches: each problem's gradient runs on its own stream between a fork and a join
     // event, so the problems overlap on the GPU (and become parallel graph branches)
     std::vector<cudaStream_t> lanes;
+    // batches of tensor-core MLPs: problems of one kernel shape run as grouped launches
+    // (grouped[i]: problem i belongs to one of the groups)
+    std::vector<std::unique_ptr<EngineGroup>> groups;
+    std::vector<bool> grouped;
     cudaEvent_t ev_fork = nullptr;
     std::vector<cudaEvent_t> ev_join;
     std::vector<std::unique_ptr<Problem>> probs;
@@ -705,6 +712,23 @@ void energy_grad_all(hmc_handle h, void *q, double *U, void *g, bool scattered)
 {
     if (h->nsplit > 1) {
         split_energy_grad_full(h, q, U, g);
+        return;
+    }
+    if (!h->groups.empty()) {   // each group on a lane of its own, the other problems after them
+        HMC_CK(cudaEventRecord(h->ev_fork, h->stream));
+        for (cudaStream_t l : h->lanes) HMC_CK(cudaStreamWaitEvent(l, h->ev_fork, 0));
+        size_t lane = 0;
+        for (auto &gr : h->groups) gr->energy_grad(q, U, g, scattered, h->lanes[lane++ % h->lanes.size()]);
+        for (int i = 0; i < h->nprob; ++i) {
+            if (h->grouped[i]) continue;
+            char *qb = static_cast<char *>(q) + h->qoff[i] * h->elem;
+            char *gb = g ? static_cast<char *>(g) + h->qoff[i] * h->elem : nullptr;
+            h->engines[i]->energy_grad(qb, U + (long)i * h->C, gb, scattered, h->lanes[lane++ % h->lanes.size()]);
+        }
+        for (size_t j = 0; j < h->lanes.size(); ++j) {
+            HMC_CK(cudaEventRecord(h->ev_join[j], h->lanes[j]));
+            HMC_CK(cudaStreamWaitEvent(h->stream, h->ev_join[j], 0));
+        }
         return;
     }
     for_each_problem(h, [&](int i, cudaStream_t s) {
@@ -923,8 +947,8 @@ template <typename T> void enqueue_trajectory(hmc_handle h, int L, uint64_t seed
     HMC_LAUNCH_CK();
 }
 
-// in_batch: inside a BF16 batch, a network the tensor-core kernels do not cover (hidden
-// widths that are not multiples of 64, say) runs on the FP32 CUDA-core engine, which
+// in_batch: inside a BF16 batch, a network the tensor-core kernels do not cover (a hidden
+// width above 256, say) runs on the FP32 CUDA-core engine, which
 // keeps the batch's float positions and is the more accurate of the two.
 Engine *make_engine(Problem &p, int prec, int C, bool in_batch = false)
 {
@@ -1054,6 +1078,16 @@ hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, co
             h->k_total += p.k;
             h->P_total += p.P;
         }
+        if (nprob > 1 && g_grouping && (prec == HMC_PREC_BF16 || prec == HMC_PREC_FP16)) {
+            std::vector<Engine *> es;
+            std::vector<long> uoff;
+            for (int i = 0; i < nprob; ++i) {
+                es.push_back(h->engines[i].get());
+                uoff.push_back((long)i * C);
+            }
+            h->groups = prec == HMC_PREC_FP16 ? make_umma_groups_f16(es, h->qoff, uoff, h->grouped)
+                                              : make_umma_groups_bf16(es, h->qoff, uoff, h->grouped);
+        }
     }
     h->S_total = h->k_total * C;
     const size_t sb = h->elem * (size_t)h->S_total;
@@ -1151,6 +1185,21 @@ int hmc_num_passes(hmc_handle h) { return h ? (h->chunked ? h->nsplit : 1) : -1;
 void hmc_diag_set_memory_cap(long bytes) { g_devbuf_cap = bytes > 0 ? (size_t)bytes : ~size_t(0); }
 
 long hmc_diag_device_bytes(void) { return (long)g_devbuf_bytes.load(); }
+
+void hmc_diag_set_grouping(int on) { g_grouping = on != 0; }
+
+long hmc_diag_groups(hmc_handle h, char *buf, long n)
+{
+    if (!h) return -1;
+    std::string t;
+    for (auto &g : h->groups) t += g->describe() + "\n";
+    if (buf && n > 0) {
+        const long m = std::min<long>(n - 1, (long)t.size());
+        memcpy(buf, t.data(), m);
+        buf[m] = 0;
+    }
+    return (long)h->groups.size();
+}
 
 hmc_status hmc_create_split(hmc_handle *out, const hmc_net_spec *spec, const hmc_data *data, double prior_sigma,
                             double noise_sigma, const unsigned char *subset_mask, const double *frozen_params,

@@ -102,6 +102,17 @@ struct Engine {
     virtual int *error_flag() const { return nullptr; }
 };
 
+// Several problems' gradients as grouped launches: one launch per kernel and layer slot
+// for all of them instead of one per problem.  Built by an engine family from its own
+// engines (make_umma_groups_*); each problem keeps its buffers, maps and tuning.
+struct EngineGroup {
+    virtual ~EngineGroup() {}
+    // q, g: a batch handle's packed [problem][chain][k_problem] arrays; U: [problem][C].
+    // Only the group's problems are written.
+    virtual void energy_grad(const void *q, double *U, void *g, bool scattered, cudaStream_t s) = 0;
+    virtual std::string describe() const = 0;
+};
+
 struct Problem {
     int kind = 0;
     NetDesc net, branch, trunk;
@@ -131,6 +142,16 @@ Engine *make_umma_engine_f16(Problem &p, int C);
 bool umma_engine_supports(const Problem &p, std::string *why);
 Engine *make_don_engine_bf16(Problem &p, int C);
 Engine *make_don_engine_f16(Problem &p, int C);
+// Groups of the tensor-core MLP engines in `es` that share a kernel shape (padded width,
+// input width, kernel family), two or more problems each; problem i's coordinates start
+// at element qoff[i] of the packed q, its energies at uoff[i] of U.  Sets grouped[i]
+// for every problem placed in a group.
+std::vector<std::unique_ptr<EngineGroup>> make_umma_groups_bf16(const std::vector<Engine *> &es,
+                                                                const std::vector<long> &qoff,
+                                                                const std::vector<long> &uoff, std::vector<bool> &grouped);
+std::vector<std::unique_ptr<EngineGroup>> make_umma_groups_f16(const std::vector<Engine *> &es,
+                                                               const std::vector<long> &qoff,
+                                                               const std::vector<long> &uoff, std::vector<bool> &grouped);
 // One bounded device-side wait run out on purpose; it raises *err (hmc_diag_expire_wait).
 void expire_wait_run(int *err, long limit_ns, cudaStream_t s);
 

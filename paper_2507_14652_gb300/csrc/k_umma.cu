@@ -2,7 +2,7 @@
 // FP32 accumulation in TMEM, FP64 energy sums).
 //
 // Network pattern: MLP  dx -> w -> ... -> w -> 1, tanh hidden layers, identity
-// output, biases everywhere, hidden width w in {64, 128, 192, 256}.
+// output, biases everywhere, hidden width w up to 256 (padded to 128 or 256).
 //
 // One gradient evaluation for all C chains (rows n = data points, tiles of 128):
 //   first layer   A_1 = tanh(X W_0^T + b_0)                        CUDA cores
@@ -151,10 +151,11 @@ struct Params {
     float *db0_part;                      // [b][ntiles][ntn]
 };
 
-template <int MODE, bool A_MN, bool B_MN, bool WSPLIT>
-__global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
-    k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-           const __grid_constant__ CUtensorMap tmB2, const Params p)
+// One CTA of the tile kernel, block (bx, by, bz) of its problem's grid.  G: the tensor
+// maps come from a grouped launch's job table in global memory.
+template <int MODE, bool A_MN, bool B_MN, bool WSPLIT, bool G>
+__device__ __forceinline__ void umma_body(const CUtensorMap &tmA, const CUtensorMap &tmB, const CUtensorMap &tmB2,
+                                          const Params &p, int bx, int by, int bz)
 {
     constexpr int STAGE_BYTES = stage_bytes(WSPLIT);
     extern __shared__ uint8_t smem_raw[];
@@ -167,10 +168,10 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // M_S runs on a (chain, row tile, column tile) grid with the chain fastest, so the
     // chains' CTAs for one tile of the shared targets follow each other through L2
-    const int m_tile = MODE == M_S ? blockIdx.y : blockIdx.x;
-    const int b = MODE == M_S ? blockIdx.x : blockIdx.z;
-    const int n_tile = MODE == M_S ? blockIdx.z : 0;
-    const int split = MODE == M_S ? 0 : blockIdx.y;
+    const int m_tile = MODE == M_S ? by : bx;
+    const int b = MODE == M_S ? bx : bz;
+    const int n_tile = MODE == M_S ? bz : 0;
+    const int split = MODE == M_S ? 0 : by;
     const int n0 = n_tile * p.N;
     const int m0 = m_tile * BM;
     const int BN = p.N;
@@ -185,6 +186,11 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
         }
         mbar_init(accb, 1);
         fence_mbar_init();
+        if (G) {   // thread 0 is also the TMA producer
+            tensormap_acquire(&tmA);
+            tensormap_acquire(&tmB);
+            if (WSPLIT) tensormap_acquire(&tmB2);
+        }
         prefetch_map(&tmA);
         prefetch_map(&tmB);
         if (WSPLIT) prefetch_map(&tmB2);
@@ -528,6 +534,49 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
     }
 }
 
+template <int MODE, bool A_MN, bool B_MN, bool WSPLIT>
+__global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2)
+    k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+           const __grid_constant__ CUtensorMap tmB2, const __grid_constant__ Params p)
+{
+    umma_body<MODE, A_MN, B_MN, WSPLIT, false>(tmA, tmB, tmB2, p, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---------------------------------------------------------------------------
+// Grouped launches.  Several problems' launches of the same kernel become one launch
+// over a linear grid: job j owns blocks [bstart, bstart + gx gy gz), and each of them
+// runs the problem's own kernel body with the block index (x, y, z) it would have had
+// in a launch of its own, so every problem's arithmetic, and its result bit for bit,
+// is the same as in separate launches.  The job tables live in device memory, written
+// once when the group is built.
+// ---------------------------------------------------------------------------
+struct GridJob {   // aligned as CUtensorMap requires
+    CUtensorMap tm[3];
+    Params p;
+    int bstart, gx, gy, gz;
+};
+
+// the job whose block range holds block b (the jobs' ranges are ascending and adjacent)
+template <typename J> __device__ __forceinline__ int find_job(const J *__restrict__ jobs, int njobs, long b)
+{
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((long)jobs[mid].bstart <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int MODE, bool A_MN, bool B_MN, bool WSPLIT>
+__global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2) k_umma_g(const GridJob *__restrict__ jobs, int njobs)
+{
+    const GridJob &J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int lb = (int)blockIdx.x - J.bstart;
+    umma_body<MODE, A_MN, B_MN, WSPLIT, true>(J.tm[0], J.tm[1], J.tm[2], J.p, lb % J.gx, (lb / J.gx) % J.gy,
+                                              lb / (J.gx * J.gy));
+}
+
 // ---------------------------------------------------------------------------
 // Persistent layer kernel for the w x w hidden layers (w = 128 or 256).
 //
@@ -587,13 +636,34 @@ struct LayerParams {
 // the XOR spreads both row-wise and 8-row-block accesses over all banks
 __device__ __forceinline__ uint32_t stg_off(int r, int j) { return (uint32_t)(r * 64 + ((j ^ ((r >> 1) & 3)) << 4)); }
 
+// One problem's share of a grouped launch of the layer kernel: its maps and parameters,
+// and the first unit of its range in the launch's unit sequence.
+struct LayerJob {   // aligned as CUtensorMap requires
+    CUtensorMap tmA, tmWh, tmWl;
+    LayerParams p;
+    long ustart;
+};
+
+// A role's place in the unit sequence: job j, whose units start at base, with tpg tile
+// pairs per chain.
+struct UnitCursor {
+    int j;
+    long base;
+    int tpg;
+};
+
 // Units: a unit is (chain, pair of consecutive tiles); CTA r takes tile 2 j + r.
 // WSPLIT adds the lo part of W (forward).  The epilogue issues a tile's global
 // loads (slopes, targets) before it waits for the accumulator, so their latency
 // overlaps the tile's MMAs.
-template <int MODE, bool WSPLIT, int WIDTH>
-__device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtensorMap &tmWh, const CUtensorMap &tmWl,
-                                           const LayerParams &p)
+// G (grouped launch): the units of several problems of the same width follow each other
+// (job j's from jobs[j].ustart on, utotal in all); every role tracks the job of its
+// current unit, and W reloads whenever (job, chain) changes.  Otherwise tmA0, tmWh0,
+// tmWl0 and p0 describe the one problem.
+template <int MODE, bool WSPLIT, int WIDTH, bool G>
+__device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtensorMap &tmWh0, const CUtensorMap &tmWl0,
+                                           const LayerParams &p0, const LayerJob *__restrict__ jobs, int njobs,
+                                           long utotal)
 {
     constexpr bool BWD = (MODE == L_BWD_TANH || MODE == L_BWD_FIRST);
     constexpr int LN = WIDTH;                          // accumulator columns: whole rows
@@ -632,8 +702,26 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();
     const bool leader = rank == 0;
-    const int tpg = (p.ntiles + 1) / 2;                // tile pairs per chain
-    const long U = (long)p.C * tpg;
+    auto jp = [&](int j) -> const LayerParams & {
+        if constexpr (G) return jobs[j].p;
+        else return p0;
+    };
+    auto map_a = [&](int j) -> const CUtensorMap * { return G ? &jobs[j].tmA : &tmA0; };
+    auto map_wh = [&](int j) -> const CUtensorMap * { return G ? &jobs[j].tmWh : &tmWh0; };
+    auto map_wl = [&](int j) -> const CUtensorMap * { return G ? &jobs[j].tmWl : &tmWl0; };
+    // move cursor k forward to the job holding unit u (u never decreases for one cursor)
+    auto seek = [&](UnitCursor &k, long u) {
+        if constexpr (G) {
+            int j = k.j;
+            while (j + 1 < njobs && u >= jobs[j + 1].ustart) ++j;
+            if (j != k.j) k = UnitCursor{j, jobs[j].ustart, (jobs[j].p.ntiles + 1) / 2};
+        }
+    };
+    const UnitCursor cur0{0, 0, (jp(0).ntiles + 1) / 2};
+    int *const perr = jp(0).err;                       // one error flag for the whole launch
+    const long U = G ? utotal : (long)p0.C * cur0.tpg;
+    // (job << 32) | chain: W and the per-chain constants change with it
+    auto unit_key = [](const UnitCursor &k, int c) { return ((long)k.j << 32) | (long)(unsigned)c; };
     const int ngr = gridDim.x / 2, gi = blockIdx.x / 2;
     const long u0 = U * gi / ngr, u1 = U * (gi + 1) / ngr;
 
@@ -649,9 +737,11 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
             mbar_init(acc_empty0 + 8 * s, 16);   // one arrival per epilogue warp of the pair
         }
         fence_mbar_init();
-        prefetch_map(&tmA);
-        prefetch_map(&tmWh);
-        if (WSPLIT) prefetch_map(&tmWl);
+        if (!G) {
+            prefetch_map(&tmA0);
+            prefetch_map(&tmWh0);
+            if (WSPLIT) prefetch_map(&tmWl0);
+        }
     }
     if (warp == 1) {
         tmem_alloc2(smem_u32(tmem_slot), TCOLS);
@@ -671,67 +761,80 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
 
     if (warp == 0) {
         if (lane == 0) {   // TMA producer (both CTAs)
-            int cur_c = -1;
+            long cur_key = -1;
+            int fenced = -1;
+            UnitCursor cu = cur0;
             uint32_t wph = 0;
             long kbi = 0;
             bool ok = true, w_pending = false;
             for (long u = u0; u < u1 && ok; ++u) {
-                const int c = (int)(u / tpg), t = (int)(u % tpg) * 2 + (int)rank;
-                if (c != cur_c) {
-                    if (cur_c >= 0) {
-                        if (!mbar_wait(w_empty, wph, p.err)) { ok = false; break; }
+                seek(cu, u);
+                const int c = (int)((u - cu.base) / cu.tpg), t = (int)((u - cu.base) % cu.tpg) * 2 + (int)rank;
+                const CUtensorMap *mA = map_a(cu.j), *mWh = map_wh(cu.j), *mWl = map_wl(cu.j);
+                if (G && cu.j != fenced) {
+                    tensormap_acquire(mA);
+                    tensormap_acquire(mWh);
+                    if (WSPLIT) tensormap_acquire(mWl);
+                    fenced = cu.j;
+                }
+                const long key = unit_key(cu, c);
+                if (key != cur_key) {
+                    if (cur_key >= 0) {
+                        if (!mbar_wait(w_empty, wph, perr)) { ok = false; break; }
                         wph ^= 1u;
                     }
                     if (leader) mbar_expect_tx(w_full, 2u * (WSPLIT ? 2u : 1u) * NKB * kblk);
                     for (int kb = 0; kb < NKB; ++kb) {
                         const uint32_t dh = smem_u32(sWh) + kb * kblk, dl = smem_u32(sWl) + kb * kblk;
                         if (!BWD) {   // B = W[f][k], K-major: this CTA's BN output features
-                            tma_load_3d_pair(dh, &tmWh, kb * BK, (int)rank * BN, c, lead_w_full);
-                            if (WSPLIT) tma_load_3d_pair(dl, &tmWl, kb * BK, (int)rank * BN, c, lead_w_full);
+                            tma_load_3d_pair(dh, mWh, kb * BK, (int)rank * BN, c, lead_w_full);
+                            if (WSPLIT) tma_load_3d_pair(dl, mWl, kb * BK, (int)rank * BN, c, lead_w_full);
                         } else {      // B = W^T read MN-major from W[o][i]: 64-feature atoms
                             for (int a = 0; a < BN / 64; ++a) {
-                                tma_load_3d_pair(dh + 8192 * a, &tmWh, (int)rank * BN + 64 * a, kb * BK, c, lead_w_full);
+                                tma_load_3d_pair(dh + 8192 * a, mWh, (int)rank * BN + 64 * a, kb * BK, c, lead_w_full);
                                 if (WSPLIT)
-                                    tma_load_3d_pair(dl + 8192 * a, &tmWl, (int)rank * BN + 64 * a, kb * BK, c,
+                                    tma_load_3d_pair(dl + 8192 * a, mWl, (int)rank * BN + 64 * a, kb * BK, c,
                                                      lead_w_full);
                             }
                         }
                     }
                     w_pending = true;
-                    cur_c = c;
+                    cur_key = key;
                 }
                 for (int kb = 0; kb < NKB; ++kb) {
                     const int s = (int)(kbi % STAGES);
                     const uint32_t ph = (uint32_t)(kbi / STAGES) & 1u;
-                    if (!mbar_wait(a_empty0 + 8 * s, ph ^ 1u, p.err)) { ok = false; break; }
+                    if (!mbar_wait(a_empty0 + 8 * s, ph ^ 1u, perr)) { ok = false; break; }
                     if (leader) mbar_expect_tx(a_full0 + 8 * s, 2u * L_A_BYTES);
-                    tma_load_3d_pair(smem_u32(sA + s * L_A_BYTES), &tmA, kb * BK, t * BM, c, lead_a_full0 + 8 * s);
+                    tma_load_3d_pair(smem_u32(sA + s * L_A_BYTES), mA, kb * BK, t * BM, c, lead_a_full0 + 8 * s);
                     ++kbi;
                 }
             }
             if (!ok && leader) {   // let copies already in flight land before the CTA exits
                 for (long i = std::max<long>(0, kbi - STAGES); i < kbi; ++i)
-                    mbar_wait(a_full0 + 8 * (int)(i % STAGES), (uint32_t)(i / STAGES) & 1u, p.err, 100000000ull);
-                if (w_pending) mbar_wait(w_full, wph, p.err, 100000000ull);
+                    mbar_wait(a_full0 + 8 * (int)(i % STAGES), (uint32_t)(i / STAGES) & 1u, perr, 100000000ull);
+                if (w_pending) mbar_wait(w_full, wph, perr, 100000000ull);
             }
         }
     } else if (warp == 1) {
         if (lane == 0 && leader) {   // MMA issuer: the leader alone drives the pair
             const uint32_t idesc = idesc_h16(2 * BM, LN, false, BWD);
-            int cur_c = -1;
+            long cur_key = -1;
+            UnitCursor cu = cur0;
             uint32_t wph = 0;
             long kbi = 0;
             int it = 0;
             bool ok = true;
             for (long u = u0; u < u1 && ok; ++u, ++it) {
-                const int c = (int)(u / tpg);
-                if (c != cur_c) {
-                    if (!mbar_wait_cluster(w_full, wph, p.err)) { ok = false; break; }
+                seek(cu, u);
+                const long key = unit_key(cu, (int)((u - cu.base) / cu.tpg));
+                if (key != cur_key) {
+                    if (!mbar_wait_cluster(w_full, wph, perr)) { ok = false; break; }
                     wph ^= 1u;
-                    cur_c = c;
+                    cur_key = key;
                 }
                 const int slot = it & 1;
-                if (!mbar_wait(acc_empty0 + 8 * slot, ((uint32_t)(it >> 1) & 1u) ^ 1u, p.err)) {
+                if (!mbar_wait(acc_empty0 + 8 * slot, ((uint32_t)(it >> 1) & 1u) ^ 1u, perr)) {
                     ok = false;
                     break;
                 }
@@ -740,7 +843,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                 for (int kb = 0; kb < NKB; ++kb) {
                     const int s = (int)(kbi % STAGES);
                     const uint32_t ph = (uint32_t)(kbi / STAGES) & 1u;
-                    if (!mbar_wait_cluster(a_full0 + 8 * s, ph, p.err)) { ok = false; break; }
+                    if (!mbar_wait_cluster(a_full0 + 8 * s, ph, perr)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(sA + s * L_A_BYTES);
                     const uint32_t wh = smem_u32(sWh) + kb * kblk, wl = smem_u32(sWl) + kb * kblk;
@@ -759,8 +862,13 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                 }
                 if (!ok) break;
                 mma_commit_pair(acc_full0 + 8 * slot, (uint16_t)3);
-                const int next_c = (u + 1 < u1) ? (int)((u + 1) / tpg) : -1;
-                if (next_c != c) mma_commit_pair(w_empty, (uint16_t)3);
+                long next_key = -1;   // W stays while the next unit has the same (job, chain)
+                if (u + 1 < u1) {
+                    UnitCursor nx = cu;
+                    seek(nx, u + 1);
+                    next_key = unit_key(nx, (int)((u + 1 - nx.base) / nx.tpg));
+                }
+                if (next_key != key) mma_commit_pair(w_empty, (uint16_t)3);
             }
         }
     } else {
@@ -777,9 +885,12 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
         // tile when NAUX = NCH)
         const uint32_t abuf = RLO ? smem_u32(smem + L_AUX_OFF_RLO) + (uint32_t)(warp - 2) * L_AUX_RLO
                                   : smem_u32(sWl) + (uint32_t)(warp - 2) * L_AUX;
+        UnitCursor ca = cur0;   // the slope prefetch runs up to a unit ahead of the epilogue
         auto issue_aux = [&](long v, int ch) {
             if (v < u1) {
-                const int cv = (int)(v / tpg), tv = (int)(v % tpg) * 2 + (int)rank;
+                seek(ca, v);
+                const LayerParams &p = jp(ca.j);
+                const int cv = (int)((v - ca.base) / ca.tpg), tv = (int)((v - ca.base) % ca.tpg) * 2 + (int)rank;
                 const int rv0 = tv * BM + 32 * q;
                 const h16 *src = p.aux + ((long)cv * p.N + rv0) * p.W + hc0 + 32 * ch + 8 * tj;
 #pragma unroll
@@ -796,9 +907,14 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
         auto refill_aux = [&](long v, int ch) { issue_aux(v + (ch + NAUX) / NCH, (ch + NAUX) % NCH); };
         if (BWD)
             for (int ch = 0; ch < NAUX; ++ch) issue_aux(u0, ch);
-        int it = 0, chain_loaded = -1;
+        int it = 0;
+        long loaded_key = -1;
+        UnitCursor ce = cur0;
         for (long u = u0; u < u1; ++u, ++it) {
-            const int c = (int)(u / tpg), t = (int)(u % tpg) * 2 + (int)rank;
+            seek(ce, u);
+            const LayerParams &p = jp(ce.j);
+            const int c = (int)((u - ce.base) / ce.tpg), t = (int)((u - ce.base) % ce.tpg) * 2 + (int)rank;
+            const long key = unit_key(ce, c);
             const bool tile_ok = t < p.ntiles;
             const int slot = it & 1;
             const int r0 = t * BM + 32 * q;    // first data row of this warp
@@ -836,14 +952,14 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                     }
             }
             // per-chain constants into shared memory
-            if (!BWD && c != chain_loaded) {
+            if (!BWD && key != loaded_key) {
                 named_bar_sync(1, 256);
                 for (int i = et; i < LN; i += 256) {
                     sbias[i] = p.bias[(long)c * p.W + i];
                     if (MODE == L_FWD_OUT) swo[i] = p.wout[(long)c * p.W + i];
                 }
                 named_bar_sync(1, 256);
-                chain_loaded = c;
+                loaded_key = key;
             }
             // this thread's 32 packed bf16 of its row -> staging -> 8-row coalesced stores
             auto store_chunk = [&](const uint32_t (&pk)[16], int col) {
@@ -860,7 +976,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
                 }
                 __syncwarp();
             };
-            if (!mbar_wait(acc_full0 + 8 * slot, (uint32_t)(it >> 1) & 1u, p.err)) break;
+            if (!mbar_wait(acc_full0 + 8 * slot, (uint32_t)(it >> 1) & 1u, perr)) break;
             tc_fence_after();
             const uint32_t taddr = tmem + lane_off + (uint32_t)(slot * SLOT + hc0);
             uint32_t rb[2][32];
@@ -1102,9 +1218,18 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA, const CUtenso
 template <int MODE, int WIDTH, bool SPLIT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(L_THREADS, 1)
     k_layer_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmWh,
-                 const __grid_constant__ CUtensorMap tmWl, const LayerParams p)
+                 const __grid_constant__ CUtensorMap tmWl, const __grid_constant__ LayerParams p)
 {
-    layer_body<MODE, SPLIT, WIDTH>(tmA, tmWh, tmWl, p);
+    layer_body<MODE, SPLIT, WIDTH, false>(tmA, tmWh, tmWl, p, nullptr, 1, 0);
+}
+
+// The grouped launch: the units of njobs problems (utotal in all) on one grid of CTA pairs.
+template <int MODE, int WIDTH, bool SPLIT>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(L_THREADS, 1)
+    k_layer_pair_g(const LayerJob *__restrict__ jobs, int njobs, long utotal)
+{
+    const LayerJob &j0 = jobs[0];   // (the single-problem arguments, unused when grouped)
+    layer_body<MODE, SPLIT, WIDTH, true>(j0.tmA, j0.tmWh, j0.tmWl, j0.p, jobs, njobs, utotal);
 }
 
 // ---------------------------------------------------------------------------
@@ -1134,8 +1259,9 @@ bool autotune_enabled()
 }
 static_assert(DW_STAGES * DW_STAGE >= 128 * 129 * 4, "the epilogue staging reuses the operand stages");
 
-__global__ void __launch_bounds__(NTHREADS, 2) k_dw2(const __grid_constant__ CUtensorMap tmD,
-                                                     const __grid_constant__ CUtensorMap tmA, const Params p)
+template <bool G>
+__device__ __forceinline__ void dw2_body(const CUtensorMap &tmD, const CUtensorMap &tmA, const Params &p, int bx,
+                                         int split, int b)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1144,9 +1270,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_dw2(const __grid_constant__ CUt
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * DW_STAGES + 1);
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * DW_STAGES, accb = empty0 + 8 * DW_STAGES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int split = blockIdx.y, b = blockIdx.z;
     const int nnh = p.N / 128;                // column blocks of dW (w / 128)
-    const int m0 = (blockIdx.x / nnh) * BM, n0 = (blockIdx.x % nnh) * 128;
+    const int m0 = (bx / nnh) * BM, n0 = (bx % nnh) * 128;
     const bool with_db = n0 == 0 && p.db_part != nullptr;
     const int total_kb = (p.K + BK - 1) / BK;
     const int kb0 = split * p.kb_per_split;
@@ -1159,6 +1284,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_dw2(const __grid_constant__ CUt
         }
         mbar_init(accb, 1);
         fence_mbar_init();
+        if (G) {   // thread 0 is also the TMA producer
+            tensormap_acquire(&tmD);
+            tensormap_acquire(&tmA);
+        }
         prefetch_map(&tmD);
         prefetch_map(&tmA);
     }
@@ -1263,6 +1392,21 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_dw2(const __grid_constant__ CUt
         tc_fence_after();
         tmem_dealloc(tmem, DW_TCOLS);
     }
+}
+
+__global__ void __launch_bounds__(NTHREADS, 2) k_dw2(const __grid_constant__ CUtensorMap tmD,
+                                                     const __grid_constant__ CUtensorMap tmA,
+                                                     const __grid_constant__ Params p)
+{
+    dw2_body<false>(tmD, tmA, p, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// grouped: tm[0] the deltas, tm[1] the activations of each job
+__global__ void __launch_bounds__(NTHREADS, 2) k_dw2_g(const GridJob *__restrict__ jobs, int njobs)
+{
+    const GridJob &J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int lb = (int)blockIdx.x - J.bstart;
+    dw2_body<true>(J.tm[0], J.tm[1], J.p, lb % J.gx, (lb / J.gx) % J.gy, lb / (J.gx * J.gy));
 }
 
 // ---------------------------------------------------------------------------
@@ -1515,17 +1659,17 @@ __global__ void __launch_bounds__(256) k_first_fwd3(const float *x, int dx, int 
 // template parameter: with a runtime width every row paid for eight predicated
 // multiply-adds per output, and the kernel was bound by instruction issue.
 template <int DX>
-__global__ void __launch_bounds__(256) k_first_fwd(const float *x, int N, int w, const float *W0, const float *b0,
-                                                   h16 *A1)
+__device__ __forceinline__ void first_fwd_body(const float *x, int N, int w, const float *W0, const float *b0, h16 *A1,
+                                               int bx, int b)
 {
     __shared__ float xs[BM * DX];
     pdl_wait();
     pdl_trigger();
-    const int b = blockIdx.y, n0 = blockIdx.x * BM;
+    const int n0 = bx * BM;
     const int nr = min(BM, N - n0);
     for (int i = threadIdx.x; i < nr * DX; i += blockDim.x) xs[i] = x[(long)n0 * DX + i];
     __syncthreads();
-    const int quads = w / 4;                                   // w is a multiple of 64 here
+    const int quads = w / 4;                                   // w is 128 or 256 here
     const int groups = max(1, (int)blockDim.x / quads);
     const int per = (nr + groups - 1) / groups;
     for (int item = threadIdx.x; item < quads * groups; item += blockDim.x) {
@@ -1554,6 +1698,27 @@ __global__ void __launch_bounds__(256) k_first_fwd(const float *x, int N, int w,
                 make_uint2(pack_h16(act_tanh(z[0]), act_tanh(z[1])), pack_h16(act_tanh(z[2]), act_tanh(z[3])));
         }
     }
+}
+
+template <int DX>
+__global__ void __launch_bounds__(256) k_first_fwd(const float *x, int N, int w, const float *W0, const float *b0,
+                                                   h16 *A1)
+{
+    first_fwd_body<DX>(x, N, w, W0, b0, A1, blockIdx.x, blockIdx.y);
+}
+
+// One problem's first layer in a grouped launch: blocks [bstart, bstart + ntiles C).
+struct FirstJob {
+    const float *x, *W0, *b0;
+    h16 *A1;
+    int N, w, ntiles, bstart;
+};
+
+template <int DX> __global__ void __launch_bounds__(256) k_first_fwd_g(const FirstJob *__restrict__ jobs, int njobs)
+{
+    const FirstJob &J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int lb = (int)blockIdx.x - J.bstart;
+    first_fwd_body<DX>(J.x, J.N, J.w, J.W0, J.b0, J.A1, lb % J.ntiles, lb / J.ntiles);
 }
 
 // The first-layer forward for an input width dx in 1..8.
@@ -1617,13 +1782,21 @@ struct FinalArgs {
 // grid (nlight + ceil(nheavy / 8) + 1, C): blocks 0..nlight-1 gather one entry per
 // thread, the next ones one heavy entry per warp (its partials split over the lanes,
 // then a fixed butterfly), and the last block of each chain computes U (fixed-order sums).
-__global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float *q, double *U, float *g)
+// gscale s + q / alpha^2 with the rounding steps spelled out, so that every kernel that
+// inlines it (one problem's finalize, a group's) rounds alike: the compiler's own choice
+// of where to fuse a multiply-add may differ between the two
+__device__ __forceinline__ float grad_entry(const FinalArgs &a, float s, float qj)
+{
+    return __fmaf_rn(a.gscale, s, __fmul_rn(qj, (float)a.inv_a2));
+}
+
+__device__ __forceinline__ void finalize_body(const FinalArgs &a, const float *q, double *U, float *g, int bx, int gx,
+                                              int b)
 {
     __shared__ double sm[2][8];
     pdl_wait();
     pdl_trigger();
-    const int b = blockIdx.y;
-    if (blockIdx.x == gridDim.x - 1) {   // U = likelihood + prior, block-parallel in a fixed order
+    if (bx == gx - 1) {   // U = likelihood + prior, block-parallel in a fixed order
         // |q|^2: eight squares at a time in FP32 (a bounded partial), accumulated in FP64;
         // this block is one SM's work, and GB300's FP64 pipe is narrow
         double pr = 0.0, lik = 0.0;
@@ -1654,13 +1827,13 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
                 t += sm[0][i];
                 l += sm[1][i];
             }
-            U[b] = l * a.half_inv_s2 + 0.5 * t * a.inv_a2;
+            U[b] = __fma_rn(l, a.half_inv_s2, __dmul_rn(__dmul_rn(0.5, t), a.inv_a2));   // (rounding as in grad_entry)
         }
         return;
     }
     if (!g) return;
-    if ((int)blockIdx.x >= a.nlight) {   // heavy entries: one warp each
-        const int h = ((int)blockIdx.x - a.nlight) * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+    if (bx >= a.nlight) {   // heavy entries: one warp each
+        const int h = (bx - a.nlight) * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
         const int lane = threadIdx.x & 31;
         if (h >= a.nheavy) return;
         const int j = a.heavy[h];
@@ -1670,10 +1843,10 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
         for (int t = lane; t < d.n; t += 32) s += __ldg(dp + (long)t * d.tstride);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) g[(long)b * a.k + j] = a.gscale * s + q[(long)b * a.k + j] * (float)a.inv_a2;
+        if (lane == 0) g[(long)b * a.k + j] = grad_entry(a, s, q[(long)b * a.k + j]);
         return;
     }
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = bx * blockDim.x + threadIdx.x;
     if (j >= a.k || a.kind[j] == E_HEAVY) return;
     const float qj = q[(long)b * a.k + j];
     const float *dp;
@@ -1696,7 +1869,28 @@ __global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float 
         for (int u = 0; u < 16; ++u) s += v[u];
     }
     for (; t < n; ++t) s += __ldg(dp + (long)t * stride);
-    g[(long)b * a.k + j] = a.gscale * s + qj * (float)a.inv_a2;
+    g[(long)b * a.k + j] = grad_entry(a, s, qj);
+}
+
+__global__ void __launch_bounds__(256) k_finalize_bf16(FinalArgs a, const float *q, double *U, float *g)
+{
+    finalize_body(a, q, U, g, blockIdx.x, gridDim.x, blockIdx.y);
+}
+
+// One problem's finalize in a grouped launch: blocks [bstart, bstart + gx C); its
+// coordinates start at q + qoff (and g + qoff), its energies at U + uoff.
+struct FinalJob {
+    FinalArgs a;
+    long qoff, uoff;
+    int bstart, gx;
+};
+
+__global__ void __launch_bounds__(256) k_finalize_g(const FinalJob *__restrict__ jobs, int njobs, const float *q,
+                                                    double *U, float *g)
+{
+    const FinalJob &J = jobs[find_job(jobs, njobs, blockIdx.x)];
+    const int lb = (int)blockIdx.x - J.bstart;
+    finalize_body(J.a, q + J.qoff, U + J.uoff, g ? g + J.qoff : nullptr, lb % J.gx, J.gx, lb / J.gx);
 }
 
 template <typename V>
@@ -1858,17 +2052,25 @@ int pick_splits(int total_kb, int ctas_without_split, int target)
     return std::min(s, total_kb);
 }
 
+class UmmaGroup;
+
 class UmmaEngine final : public Engine {
+    friend class UmmaGroup;
+
   public:
     UmmaEngine(Problem &p, int C) : p_(p), C_(C)
     {
         const NetDesc &nd = p.net;
         L_ = nd.L;
-        // hidden widths that are not a multiple of 64 are padded with units whose weights
-        // and biases are zero: they output tanh(0) = 0, feed nothing forward and receive no
-        // delta, so U and the gradient of every real parameter are unchanged
+        // hidden widths are padded to 128 (or 256 above 128) with units whose weights and
+        // biases are zero: they output tanh(0) = 0, feed nothing forward and receive no
+        // delta, so U and the gradient of every real parameter are unchanged.  Widths up to
+        // 128 then run on the persistent pair kernel, whose CTAs each hold half of W: at
+        // 64 the reverse pass's 64-feature atoms of W^T would not split between the pair
+        // (the tile kernel does run 64, with one short-lived CTA per 128 rows, and in a
+        // batch of many small problems that was three times slower than padding)
         wl_ = nd.w[1];
-        w_ = (wl_ + 63) / 64 * 64;
+        w_ = wl_ <= 128 ? 128 : 256;
         dx_ = nd.w[0];
         N_ = p.n;
         k_ = p.k;
@@ -2015,11 +2217,6 @@ class UmmaEngine final : public Engine {
         float *g = static_cast<float *>(gv);
         if (!scattered) scatter(qv, s);
         const NetDesc &nd = p_.net;
-        Params base{};
-        base.err = err_;
-        base.ntiles = ntiles_;
-        const long act_b = N_ * (long)w_;
-        const dim3 row_grid(ntiles_, 1, C_);
         // first layer
         {
             dim3 grid((unsigned)ntiles_, C_);
@@ -2030,61 +2227,95 @@ class UmmaEngine final : public Engine {
         if (use_layer_) {
             layers_persistent(s);
         } else {
-        // hidden layers i = 1..L-3 (tanh), then layer L-2 fused with the output layer
-        for (int i = 1; i <= L_ - 2; ++i) {
-            Params pp = base;
-            pp.M = (int)N_;
-            pp.N = w_;
-            pp.K = w_;
-            pp.kb_per_split = (w_ + BK - 1) / BK;
-            pp.bias = bh_[i - 1]->as<float>();
-            pp.bias_b = w_;
-            if (i < L_ - 2) {
-                pp.out = A_[i + 1]->as<h16>();
-                pp.out_b = act_b;
-                launch_umma<M_FWD_TANH, false, false, true>(A_row_[i], W_fwd_[i], W_fwd_lo_[i], pp, row_grid, s);
-            } else {
-                pp.out = D_[L_ - 1]->as<h16>();
-                pp.out_b = act_b;
-                pp.wout = wout_.as<float>();
-                pp.wout_b = w_;
-                pp.bout = bout_.as<float>();
-                pp.y = y_.as<float>();
-                pp.inv_s2 = (float)delta_scale(p_.sigma);
-                pp.u_part = u_part_.as<double>();
-                pp.dbout_part = dbout_part_.as<float>();
-                pp.dwout_part = dwout_part_.as<float>();
-                pp.db_part = db_part_[L_ - 2]->as<float>();
-                launch_umma<M_FWD_OUT, false, false, true>(A_row_[i], W_fwd_[i], W_fwd_lo_[i], pp, row_grid, s);
+            const dim3 row_grid(ntiles_, 1, C_);
+            // hidden layers i = 1..L-3 (tanh), then layer L-2 fused with the output layer
+            for (int i = 1; i <= L_ - 2; ++i) {
+                const Params pp = tile_fwd_params(i);
+                if (i < L_ - 2)
+                    launch_umma<M_FWD_TANH, false, false, true>(A_row_[i], W_fwd_[i], W_fwd_lo_[i], pp, row_grid, s);
+                else
+                    launch_umma<M_FWD_OUT, false, false, true>(A_row_[i], W_fwd_[i], W_fwd_lo_[i], pp, row_grid, s);
             }
-        }
-        // reverse: delta_i = (delta_{i+1} W_i) (1 - A_i^2) for i = L-2 .. 1 (down to the lowest sampled layer)
-        for (int i = L_ - 2; i >= 1; --i) {
-            if (i <= nd.lmin) break;   // no layer below i holds a sampled parameter
-            Params pp = base;
-            pp.M = (int)N_;
-            pp.N = w_;
-            pp.K = w_;
-            pp.kb_per_split = (w_ + BK - 1) / BK;
-            pp.aux = A_[i]->as<h16>();
-            pp.aux_b = act_b;
-            pp.db_part = db_part_[i - 1]->as<float>();
-            if (i > 1) {
-                pp.out = D_[i]->as<h16>();
-                pp.out_b = act_b;
-                launch_umma<M_BWD_TANH, false, true, true>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], pp, row_grid, s);
-            } else {
-                pp.x = x_.as<float>();
-                pp.dx = dx_;
-                pp.dw0_part = dw0_part_.as<float>();
-                launch_umma<M_BWD_FIRST, false, true, true>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], pp, row_grid, s);
+            // reverse: delta_i = (delta_{i+1} W_i) (1 - A_i^2) for i = L-2 .. 1 (down to the lowest sampled layer)
+            for (int i = L_ - 2; i >= 1; --i) {
+                if (i <= nd.lmin) break;   // no layer below i holds a sampled parameter
+                const Params pp = tile_bwd_params(i);
+                if (i > 1)
+                    launch_umma<M_BWD_TANH, false, true, true>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], pp, row_grid, s);
+                else
+                    launch_umma<M_BWD_FIRST, false, true, true>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], pp, row_grid, s);
             }
-        }
-        }
-        // weight gradients of the hidden layers at the sampled entries (the persistent path
-        // launches each one next to the reverse kernel that reads the same delta)
-        if (!use_layer_)
+            // weight gradients of the hidden layers at the sampled entries (the persistent path
+            // launches each one next to the reverse kernel that reads the same delta)
             for (int i = 1; i <= L_ - 2; ++i) dw_layer(i, s);
+        }
+        const FinalArgs fa = final_args();
+        {
+            ProfScope ps("finalize", s);
+            launch_pdl(k_finalize_bf16, dim3((unsigned)final_blocks(), C_), dim3(256), 0, s, fa, q, U, g);
+            HMC_LAUNCH_CK();
+        }
+    }
+
+    // ---- launch descriptions, shared by energy_grad and the grouped launches ----
+
+    // the tile kernel's parameters for hidden layer i, forward (tanh, or fused with the
+    // output layer at i = L-2) and reverse (to delta_i, or fused with the first layer's
+    // gradients at i = 1)
+    Params tile_fwd_params(int i) const
+    {
+        Params pp{};
+        pp.err = err_;
+        pp.ntiles = ntiles_;
+        pp.M = (int)N_;
+        pp.N = w_;
+        pp.K = w_;
+        pp.kb_per_split = (w_ + BK - 1) / BK;
+        pp.bias = bh_[i - 1]->as<float>();
+        pp.bias_b = w_;
+        pp.out_b = N_ * (long)w_;
+        if (i < L_ - 2) {
+            pp.out = A_[i + 1]->as<h16>();
+        } else {
+            pp.out = D_[L_ - 1]->as<h16>();
+            pp.wout = wout_.as<float>();
+            pp.wout_b = w_;
+            pp.bout = bout_.as<float>();
+            pp.y = y_.as<float>();
+            pp.inv_s2 = (float)delta_scale(p_.sigma);
+            pp.u_part = u_part_.as<double>();
+            pp.dbout_part = dbout_part_.as<float>();
+            pp.dwout_part = dwout_part_.as<float>();
+            pp.db_part = db_part_[L_ - 2]->as<float>();
+        }
+        return pp;
+    }
+
+    Params tile_bwd_params(int i) const
+    {
+        Params pp{};
+        pp.err = err_;
+        pp.ntiles = ntiles_;
+        pp.M = (int)N_;
+        pp.N = w_;
+        pp.K = w_;
+        pp.kb_per_split = (w_ + BK - 1) / BK;
+        pp.aux = A_[i]->as<h16>();
+        pp.aux_b = N_ * (long)w_;
+        pp.db_part = db_part_[i - 1]->as<float>();
+        if (i > 1) {
+            pp.out = D_[i]->as<h16>();
+            pp.out_b = N_ * (long)w_;
+        } else {
+            pp.x = x_.as<float>();
+            pp.dx = dx_;
+            pp.dw0_part = dw0_part_.as<float>();
+        }
+        return pp;
+    }
+
+    FinalArgs final_args() const
+    {
         FinalArgs fa{};
         fa.k = (int)k_;
         fa.nsplit = nsplit_eff();
@@ -2102,13 +2333,11 @@ class UmmaEngine final : public Engine {
         fa.heavy = heavy_.as<int>();
         fa.nheavy = nheavy_;
         fa.nlight = (int)((k_ + 255) / 256);
-        {
-            ProfScope ps("finalize", s);
-            dim3 grid((unsigned)(fa.nlight + (nheavy_ + 7) / 8 + 1), C_);
-            launch_pdl(k_finalize_bf16, grid, dim3(256), 0, s, fa, q, U, g);
-            HMC_LAUNCH_CK();
-        }
+        return fa;
     }
+
+    // finalize blocks per chain: the light entries, the heavy ones (a warp each), U
+    int final_blocks() const { return (int)((k_ + 255) / 256) + (nheavy_ + 7) / 8 + 1; }
 
     bool has_accurate_energy() const override { return true; }
 
@@ -2220,13 +2449,14 @@ class UmmaEngine final : public Engine {
     }
 
     // weight gradient of hidden layer i (dW = delta_{i+1}^T A_i) at its sampled entries
-    void dw_layer(int i, cudaStream_t s)
+    // The weight gradient of hidden layer i at the sampled entries (nothing when the layer
+    // holds none): its kernel's parameters, grid and operand maps (deltas, activations).
+    bool dw_params(int i, Params &pp, dim3 &grid, const CUtensorMap *&md, const CUtensorMap *&ma) const
     {
-        if (layer_entries_[i] == 0 && !(use_layer_ && bias_entries_[i] > 0)) return;
-        Params base{};
-        base.err = err_;
-        base.ntiles = ntiles_;
-        Params pp = base;
+        if (layer_entries_[i] == 0 && !(use_layer_ && bias_entries_[i] > 0)) return false;
+        pp = Params{};
+        pp.err = err_;
+        pp.ntiles = ntiles_;
         pp.M = w_;
         pp.N = w_;
         pp.K = (int)N_;
@@ -2244,61 +2474,93 @@ class UmmaEngine final : public Engine {
             const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
             pp.db_part = dbw_part_[i]->as<float>();
             pp.db_split = (long)C_ * w_;
-            launch_dw2(D_atom_[i + 1], A_atom_[i], pp, dim3((w_ / 128) * (w_ / 128), splits, C_), s);
+            grid = dim3((w_ / 128) * (w_ / 128), splits, C_);
         } else {
             const int splits = (total_kb + pp.kb_per_split - 1) / pp.kb_per_split;
-            dim3 grid((w_ + BM - 1) / BM, splits, C_);
-            launch_umma<M_DW, true, true, false>(D_atom_[i + 1], A_atom_[i], A_atom_[i], pp, grid, s);
+            grid = dim3((w_ + BM - 1) / BM, splits, C_);
         }
+        md = &D_atom_[i + 1];
+        ma = &A_atom_[i];
+        return true;
     }
+
+    void dw_layer(int i, cudaStream_t s)
+    {
+        Params pp;
+        dim3 grid;
+        const CUtensorMap *md, *ma;
+        if (!dw_params(i, pp, grid, md, ma)) return;
+        if (use_layer_) launch_dw2(*md, *ma, pp, grid, s);
+        else launch_umma<M_DW, true, true, false>(*md, *ma, *ma, pp, grid, s);
+    }
+
+    // the persistent layer kernel's parameters for hidden layer i, forward and reverse
+    LayerParams layer_fwd_params(int i) const
+    {
+        LayerParams lp = layer_base();
+        lp.bias = bh_[i - 1]->as<float>();
+        if (i < L_ - 2) {
+            lp.out = A_[i + 1]->as<h16>();
+        } else {
+            lp.out = D_[L_ - 1]->as<h16>();
+            lp.wout = wout_.as<float>();
+            lp.bout = bout_.as<float>();
+            lp.y = y_.as<float>();
+            lp.inv_s2 = (float)delta_scale(p_.sigma);
+            lp.u_part = u_part_.as<double>();
+            lp.dbout_part = dbout_part_.as<float>();
+            lp.dwout_part = dwout_part_.as<float>();
+        }
+        return lp;
+    }
+
+    LayerParams layer_bwd_params(int i) const
+    {
+        LayerParams lp = layer_base();
+        lp.aux = A_[i]->as<h16>();
+        if (i > 1) {
+            lp.out = D_[i]->as<h16>();
+        } else {
+            lp.db_part = db_part_[0]->as<float>();
+            lp.x = x_.as<float>();
+            lp.dw0_part = dw0_part_.as<float>();
+        }
+        return lp;
+    }
+
+    LayerParams layer_base() const
+    {
+        LayerParams lp{};
+        lp.N = (int)N_;
+        lp.W = w_;
+        lp.C = C_;
+        lp.ntiles = ntiles_;
+        lp.dx = dx_;
+        lp.err = err_;
+        return lp;
+    }
+
+    // (chain, tile pair) units of one layer launch
+    long layer_units() const { return (long)C_ * ((ntiles_ + 1) / 2); }
 
     // forward and reverse hidden layers on the persistent cluster kernel
     void layers_persistent(cudaStream_t s)
     {
         const NetDesc &nd = p_.net;
-        LayerParams base{};
-        base.N = (int)N_;
-        base.W = w_;
-        base.C = C_;
-        base.ntiles = ntiles_;
-        base.dx = dx_;
-        base.err = err_;
-        const long U2 = (long)C_ * ((ntiles_ + 1) / 2);   // (chain, tile pair) units
-        const int ncta = 2 * (int)std::min<long>(max_clusters_, U2);
+        const int ncta = 2 * (int)std::min<long>(max_clusters_, layer_units());
         for (int i = 1; i <= L_ - 2; ++i) {
-            LayerParams lp = base;
-            lp.bias = bh_[i - 1]->as<float>();
-            if (i < L_ - 2) {
-                lp.out = A_[i + 1]->as<h16>();
-                launch_layer<L_FWD_TANH>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
-            } else {
-                lp.out = D_[L_ - 1]->as<h16>();
-                lp.wout = wout_.as<float>();
-                lp.bout = bout_.as<float>();
-                lp.y = y_.as<float>();
-                lp.inv_s2 = (float)delta_scale(p_.sigma);
-                lp.u_part = u_part_.as<double>();
-                lp.dbout_part = dbout_part_.as<float>();
-                lp.dwout_part = dwout_part_.as<float>();
-                launch_layer<L_FWD_OUT>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
-            }
+            const LayerParams lp = layer_fwd_params(i);
+            if (i < L_ - 2) launch_layer<L_FWD_TANH>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
+            else launch_layer<L_FWD_OUT>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
         }
         // reverse pass (W as a hi/lo pair, like the forward pass); the weight gradient of
         // layer i runs first, while the delta written by the previous kernel is still in L2
         for (int i = L_ - 2; i >= 1; --i) {
             dw_layer(i, s);
             if (i <= nd.lmin) break;
-            LayerParams lp = base;
-            lp.aux = A_[i]->as<h16>();
-            if (i > 1) {
-                lp.out = D_[i]->as<h16>();
-                launch_layer<L_BWD_TANH>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], lp, ncta, s);
-            } else {
-                lp.db_part = db_part_[0]->as<float>();
-                lp.x = x_.as<float>();
-                lp.dw0_part = dw0_part_.as<float>();
-                launch_layer<L_BWD_FIRST>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], lp, ncta, s);
-            }
+            const LayerParams lp = layer_bwd_params(i);
+            if (i > 1) launch_layer<L_BWD_TANH>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], lp, ncta, s);
+            else launch_layer<L_BWD_FIRST>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], lp, ncta, s);
         }
     }
 
@@ -2451,6 +2713,337 @@ class UmmaEngine final : public Engine {
     ScatterPlan plan_;
     std::string tuning_;
 };
+
+// ---------------------------------------------------------------------------
+// Grouped gradients of a batch of MLP problems (one shape class: padded width, input
+// width, kernel family).  Per gradient evaluation the group issues one launch per
+// kernel and layer slot for all its problems:
+//   first layer                         one launch
+//   hidden forward, slot s = 1..S       problem e runs its layer i = s - (S - n_e) there
+//                                       (n_e hidden w x w layers), so every problem's
+//                                       output-fused layer falls in the last slot
+//   reverse, layer i = S..1             every problem with that layer (above its lowest
+//                                       sampled layer); the first-layer reverse is the
+//                                       last launch for all
+//   weight gradients                    one launch over every (problem, layer) pair
+//   finalize                            one launch
+// Each launch walks a job table (one entry per problem) and runs each problem's own
+// kernel body on its own buffers, so the group's U and grad U equal the problems'
+// separate evaluations bit for bit.
+// ---------------------------------------------------------------------------
+class UmmaGroup final : public EngineGroup {
+  public:
+    UmmaGroup(const std::vector<UmmaEngine *> &es, const std::vector<long> &qoff, const std::vector<long> &uoff)
+        : es_(es), qoff_(qoff), uoff_(uoff)
+    {
+        const UmmaEngine &e0 = *es_[0];
+        w_ = e0.w_;
+        dx_ = e0.dx_;
+        persistent_ = e0.use_layer_;
+        int S = 0;
+        for (const UmmaEngine *e : es_) S = std::max(S, e->L_ - 2);
+        add_first();
+        for (int s = 1; s <= S; ++s) {   // forward slots, aligned on the last layer
+            std::vector<std::pair<const UmmaEngine *, int>> tanh_l, out_l;
+            for (const UmmaEngine *e : es_) {
+                const int n = e->L_ - 2, i = s - (S - n);
+                if (i >= 1) (i < n ? tanh_l : out_l).push_back({e, i});
+            }
+            add_layers(true, false, tanh_l);
+            add_layers(true, true, out_l);
+        }
+        for (int i = S; i >= 1; --i) {   // reverse, by layer index
+            std::vector<std::pair<const UmmaEngine *, int>> l;
+            for (const UmmaEngine *e : es_)
+                if (i <= e->L_ - 2 && i > e->p_.net.lmin) l.push_back({e, i});
+            add_layers(false, i == 1, l);
+        }
+        add_dw();
+        add_final();
+    }
+
+    void energy_grad(const void *qv, double *U, void *gv, bool scattered, cudaStream_t s) override
+    {
+        const float *q = static_cast<const float *>(qv);
+        float *g = static_cast<float *>(gv);
+        if (!scattered)
+            for (size_t e = 0; e < es_.size(); ++e) es_[e]->scatter(q + qoff_[e], s);
+        for (const Launch &l : seq_) run(l, q, U, g, s);
+    }
+
+    std::string describe() const override
+    {
+        return std::to_string(es_.size()) + " problems, width " + std::to_string(w_) + ", dx " + std::to_string(dx_) +
+               (persistent_ ? ", persistent layer kernel" : ", tile kernel") + ": " + std::to_string(seq_.size()) +
+               " launches per gradient";
+    }
+
+    size_t launches() const { return seq_.size(); }
+
+    // engines of one class can share launches: padded width, input width, kernel family
+    static std::tuple<int, int, bool> shape_class(const UmmaEngine &e) { return std::make_tuple(e.w_, e.dx_, e.use_layer_); }
+
+  private:
+    enum Kind { K_FIRST, K_LAYER, K_TILE, K_DW2, K_DWT, K_FINAL };
+    struct Launch {
+        Kind kind;
+        int mode;          // K_LAYER: LMode; K_TILE: Mode
+        int njobs;
+        long work;         // K_LAYER: units; otherwise blocks
+        std::shared_ptr<DevBuf> jobs;
+    };
+
+    template <typename J> std::shared_ptr<DevBuf> upload(const std::vector<J> &v)
+    {
+        auto d = std::make_shared<DevBuf>(sizeof(J) * v.size());
+        HMC_CK(cudaMemcpy(d->ptr, v.data(), sizeof(J) * v.size(), cudaMemcpyHostToDevice));
+        return d;
+    }
+
+    void add_first()
+    {
+        std::vector<FirstJob> v;
+        int b = 0;
+        for (const UmmaEngine *e : es_) {
+            v.push_back(FirstJob{e->x_.as<float>(), e->W0_.as<float>(), e->b0_.as<float>(), e->A_[1]->as<h16>(),
+                                 (int)e->N_, e->w_, e->ntiles_, b});
+            b += e->ntiles_ * e->C_;
+        }
+        seq_.push_back(Launch{K_FIRST, 0, (int)v.size(), b, upload(v)});
+    }
+
+    // hidden layer i of each listed problem: forward (special: fused with the output
+    // layer) or reverse (special: fused with the first layer's gradients)
+    void add_layers(bool fwd, bool special, const std::vector<std::pair<const UmmaEngine *, int>> &l)
+    {
+        if (l.empty()) return;
+        int *err = es_[0]->err_;   // one flag for the launch; hmc_check reads every engine's
+        if (persistent_) {
+            std::vector<LayerJob> v;
+            long u = 0;
+            for (auto &pr : l) {
+                const UmmaEngine &e = *pr.first;
+                const int i = pr.second;
+                LayerJob j;
+                memset(&j, 0, sizeof j);
+                if (fwd) {
+                    j.tmA = e.A_row_[i];
+                    j.tmWh = e.W_half_hi_[i];
+                    j.tmWl = e.W_half_lo_[i];
+                    j.p = e.layer_fwd_params(i);
+                } else {
+                    j.tmA = e.D_row_[i + 1];
+                    j.tmWh = e.W_atom_[i];
+                    j.tmWl = e.W_atom_lo_[i];
+                    j.p = e.layer_bwd_params(i);
+                }
+                j.p.err = err;
+                j.ustart = u;
+                u += e.layer_units();
+                v.push_back(j);
+            }
+            const int mode = fwd ? (special ? L_FWD_OUT : L_FWD_TANH) : (special ? L_BWD_FIRST : L_BWD_TANH);
+            seq_.push_back(Launch{K_LAYER, mode, (int)v.size(), u, upload(v)});
+        } else {
+            std::vector<GridJob> v;
+            int b = 0;
+            for (auto &pr : l) {
+                const UmmaEngine &e = *pr.first;
+                const int i = pr.second;
+                GridJob j;
+                memset(&j, 0, sizeof j);
+                if (fwd) {
+                    j.tm[0] = e.A_row_[i];
+                    j.tm[1] = e.W_fwd_[i];
+                    j.tm[2] = e.W_fwd_lo_[i];
+                    j.p = e.tile_fwd_params(i);
+                } else {
+                    j.tm[0] = e.D_row_[i + 1];
+                    j.tm[1] = e.W_atom_[i];
+                    j.tm[2] = e.W_atom_lo_[i];
+                    j.p = e.tile_bwd_params(i);
+                }
+                j.p.err = err;
+                j.bstart = b;
+                j.gx = e.ntiles_;
+                j.gy = 1;
+                j.gz = e.C_;
+                b += e.ntiles_ * e.C_;
+                v.push_back(j);
+            }
+            const int mode = fwd ? (special ? M_FWD_OUT : M_FWD_TANH) : (special ? M_BWD_FIRST : M_BWD_TANH);
+            seq_.push_back(Launch{K_TILE, mode, (int)v.size(), b, upload(v)});
+        }
+    }
+
+    void add_dw()
+    {
+        std::vector<GridJob> v;
+        int b = 0;
+        for (const UmmaEngine *e : es_)
+            for (int i = 1; i <= e->L_ - 2; ++i) {
+                Params pp;
+                dim3 grid;
+                const CUtensorMap *md, *ma;
+                if (!e->dw_params(i, pp, grid, md, ma)) continue;
+                GridJob j;
+                memset(&j, 0, sizeof j);
+                j.tm[0] = *md;
+                j.tm[1] = *ma;
+                j.tm[2] = *ma;
+                j.p = pp;
+                j.p.err = es_[0]->err_;
+                j.bstart = b;
+                j.gx = (int)grid.x;
+                j.gy = (int)grid.y;
+                j.gz = (int)grid.z;
+                b += (int)(grid.x * grid.y * grid.z);
+                v.push_back(j);
+            }
+        if (!v.empty()) seq_.push_back(Launch{persistent_ ? K_DW2 : K_DWT, 0, (int)v.size(), b, upload(v)});
+    }
+
+    void add_final()
+    {
+        std::vector<FinalJob> v;
+        int b = 0;
+        for (size_t k = 0; k < es_.size(); ++k) {
+            const UmmaEngine &e = *es_[k];
+            v.push_back(FinalJob{e.final_args(), qoff_[k], uoff_[k], b, e.final_blocks()});
+            b += e.final_blocks() * e.C_;
+        }
+        seq_.push_back(Launch{K_FINAL, 0, (int)v.size(), b, upload(v)});
+    }
+
+    template <int MODE, int WIDTH> static void launch_layer_g(const Launch &l, int max_clusters, cudaStream_t s)
+    {
+        static bool configured = false;
+        if (!configured) {
+            HMC_CK(cudaFuncSetAttribute(k_layer_pair_g<MODE, WIDTH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        L_SMEM));
+            configured = true;
+        }
+        static const char *names[] = {"group_layer_fwd_tanh", "group_layer_fwd_out", "group_layer_bwd_tanh",
+                                      "group_layer_bwd_first"};
+        ProfScope ps(names[MODE], s);
+        const int ncta = 2 * (int)std::min<long>(max_clusters, l.work);
+        launch_pdl(k_layer_pair_g<MODE, WIDTH, true>, dim3(ncta), dim3(L_THREADS), L_SMEM, s,
+                   l.jobs->as<const LayerJob>(), l.njobs, l.work);
+        HMC_LAUNCH_CK();
+    }
+
+    template <int MODE, bool A_MN, bool B_MN, bool WSPLIT> static void launch_tile_g(const Launch &l, cudaStream_t s)
+    {
+        static bool configured = false;
+        constexpr int sm = smem_bytes(WSPLIT);
+        if (!configured) {
+            HMC_CK(cudaFuncSetAttribute(k_umma_g<MODE, A_MN, B_MN, WSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        sm));
+            configured = true;
+        }
+        ProfScope ps("group_tile", s);
+        k_umma_g<MODE, A_MN, B_MN, WSPLIT><<<(unsigned)l.work, NTHREADS, sm, s>>>(l.jobs->as<const GridJob>(), l.njobs);
+        HMC_LAUNCH_CK();
+    }
+
+    template <int WIDTH> void run_layer(const Launch &l, cudaStream_t s) const
+    {
+        const int mc = es_[0]->max_clusters_;
+        switch (l.mode) {
+        case L_FWD_TANH: launch_layer_g<L_FWD_TANH, WIDTH>(l, mc, s); break;
+        case L_FWD_OUT: launch_layer_g<L_FWD_OUT, WIDTH>(l, mc, s); break;
+        case L_BWD_TANH: launch_layer_g<L_BWD_TANH, WIDTH>(l, mc, s); break;
+        default: launch_layer_g<L_BWD_FIRST, WIDTH>(l, mc, s); break;
+        }
+    }
+
+    template <int DX> static void launch_first_g(const Launch &l, cudaStream_t s)
+    {
+        ProfScope ps("group_first_fwd", s);
+        launch_pdl(k_first_fwd_g<DX>, dim3((unsigned)l.work), dim3(256), 0, s, l.jobs->as<const FirstJob>(), l.njobs);
+        HMC_LAUNCH_CK();
+    }
+
+    void run(const Launch &l, const float *q, double *U, float *g, cudaStream_t s) const
+    {
+        switch (l.kind) {
+        case K_FIRST:
+            switch (dx_) {
+            case 1: launch_first_g<1>(l, s); break;
+            case 2: launch_first_g<2>(l, s); break;
+            case 3: launch_first_g<3>(l, s); break;
+            case 4: launch_first_g<4>(l, s); break;
+            case 5: launch_first_g<5>(l, s); break;
+            case 6: launch_first_g<6>(l, s); break;
+            case 7: launch_first_g<7>(l, s); break;
+            default: launch_first_g<8>(l, s); break;
+            }
+            break;
+        case K_LAYER:
+            if (w_ == 256) run_layer<256>(l, s);
+            else run_layer<128>(l, s);
+            break;
+        case K_TILE:
+            switch (l.mode) {
+            case M_FWD_TANH: launch_tile_g<M_FWD_TANH, false, false, true>(l, s); break;
+            case M_FWD_OUT: launch_tile_g<M_FWD_OUT, false, false, true>(l, s); break;
+            case M_BWD_TANH: launch_tile_g<M_BWD_TANH, false, true, true>(l, s); break;
+            default: launch_tile_g<M_BWD_FIRST, false, true, true>(l, s); break;
+            }
+            break;
+        case K_DW2: {
+            static bool configured = false;
+            if (!configured) {
+                HMC_CK(cudaFuncSetAttribute(k_dw2_g, cudaFuncAttributeMaxDynamicSharedMemorySize, DW_SMEM));
+                configured = true;
+            }
+            ProfScope ps("group_dw2", s);
+            launch_pdl(k_dw2_g, dim3((unsigned)l.work), dim3(NTHREADS), DW_SMEM, s, l.jobs->as<const GridJob>(),
+                       l.njobs);
+            HMC_LAUNCH_CK();
+            break;
+        }
+        case K_DWT: launch_tile_g<M_DW, true, true, false>(l, s); break;
+        case K_FINAL: {
+            ProfScope ps("group_finalize", s);
+            launch_pdl(k_finalize_g, dim3((unsigned)l.work), dim3(256), 0, s, l.jobs->as<const FinalJob>(), l.njobs, q,
+                       U, g);
+            HMC_LAUNCH_CK();
+            break;
+        }
+        }
+    }
+
+    std::vector<UmmaEngine *> es_;
+    std::vector<long> qoff_, uoff_;
+    int w_ = 0, dx_ = 0;
+    bool persistent_ = false;
+    std::vector<Launch> seq_;
+};
+
+// Problems whose engines share a kernel shape, in classes of two or more.
+std::vector<std::unique_ptr<EngineGroup>> make_groups(const std::vector<Engine *> &es, const std::vector<long> &qoff,
+                                                      const std::vector<long> &uoff, std::vector<bool> &grouped)
+{
+    std::map<std::tuple<int, int, bool>, std::vector<int>> cls;
+    for (size_t i = 0; i < es.size(); ++i)
+        if (auto *u = dynamic_cast<UmmaEngine *>(es[i])) cls[UmmaGroup::shape_class(*u)].push_back((int)i);
+    std::vector<std::unique_ptr<EngineGroup>> out;
+    grouped.assign(es.size(), false);
+    for (auto &kv : cls) {
+        if (kv.second.size() < 2) continue;
+        std::vector<UmmaEngine *> m;
+        std::vector<long> qo, uo;
+        for (int i : kv.second) {
+            m.push_back(static_cast<UmmaEngine *>(es[i]));
+            qo.push_back(qoff[i]);
+            uo.push_back(uoff[i]);
+            grouped[i] = true;
+        }
+        out.emplace_back(new UmmaGroup(m, qo, uo));
+    }
+    return out;
+}
 
 // ---------------------------------------------------------------------------
 // DeepONet on the tensor cores (Sec. 4.2 operator output): branch and trunk MLPs
@@ -3130,7 +3723,7 @@ bool umma_engine_supports(const Problem &p, std::string *why)
     const NetDesc &nd = p.net;
     if (nd.L < 3) return no("need at least one hidden-to-hidden layer");
     const int w = nd.w[1];
-    if (w < 1 || w > 256) return no("hidden width must be at most 256 (padded to a multiple of 64)");
+    if (w < 1 || w > 256) return no("hidden width must be at most 256 (padded to 128 or 256)");
     for (int l = 1; l < nd.L; ++l)
         if (nd.w[l] != w) return no("all hidden layers must have the same width");
     if (nd.w[nd.L] != 1) return no("the output width must be 1");
@@ -3148,8 +3741,20 @@ bool umma_engine_supports(const Problem &p, std::string *why)
 
 #if HMC_F16
 Engine *make_umma_engine_f16(Problem &p, int C) { return new UmmaEngine(p, C); }
+std::vector<std::unique_ptr<EngineGroup>> make_umma_groups_f16(const std::vector<Engine *> &es,
+                                                               const std::vector<long> &qoff,
+                                                               const std::vector<long> &uoff, std::vector<bool> &grouped)
+{
+    return make_groups(es, qoff, uoff, grouped);
+}
 #else
 Engine *make_umma_engine_bf16(Problem &p, int C) { return new UmmaEngine(p, C); }
+std::vector<std::unique_ptr<EngineGroup>> make_umma_groups_bf16(const std::vector<Engine *> &es,
+                                                                const std::vector<long> &qoff,
+                                                                const std::vector<long> &uoff, std::vector<bool> &grouped)
+{
+    return make_groups(es, qoff, uoff, grouped);
+}
 #endif
 
 #if !HMC_F16

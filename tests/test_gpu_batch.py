@@ -73,7 +73,7 @@ def test_batch_energy_grad_parity(prec):
 
 
 def test_batch_bf16_energy_grad_parity():
-    # widths 64 (per-layer tensor-core kernels), 128 and 256 (persistent pair kernels)
+    # widths 64 (padded to 128), 128 and 256 on the persistent pair kernels
     probs = _problems(widths=(64, 128, 256))
     assert {p.notes["width"] for p in probs} == {64, 128, 256}
     qs, U, gs, _ = _energy_grad(probs, hmc.PREC_BF16)
@@ -87,7 +87,7 @@ def test_batch_bf16_energy_grad_parity():
 
 
 def test_batch_bf16_pads_width_32_onto_the_tensor_cores():
-    # hidden widths that are not multiples of 64 run on the tensor cores padded with units
+    # hidden widths below 128 run on the tensor cores padded to 128 with units
     # whose weights are zero (they change neither U nor the real parameters' gradient)
     probs = _problems(widths=(32, 128))
     assert {p.notes["width"] for p in probs} == {32, 128}

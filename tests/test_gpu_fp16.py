@@ -165,8 +165,8 @@ def test_fp16_engine_tanh_is_accurate_to_1e_6():
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("widths", [(2, 40, 40, 1), (3, 100, 100, 100, 1), (4, 200, 200, 1)])
-def test_hidden_widths_padded_to_multiples_of_64(prec, widths):
-    # the tensor-core engines pad a hidden width to the next multiple of 64 with zero units
+def test_hidden_widths_padded_with_zero_units(prec, widths):
+    # the tensor-core engines pad a hidden width to 128 (or 256 above 128) with zero units
     prob = W.small_mlp(n=300, widths=widths, frac=0.2, chains=2, seed=61)
     tol = TOL if prec == "fp16" else 2e-2
     U, g = _eg(sampler_from(prob, hmc.PREC_FP16 if prec == "fp16" else hmc.PREC_BF16), prob.q0)

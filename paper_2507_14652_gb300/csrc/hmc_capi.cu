@@ -1071,6 +1071,7 @@ hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, co
         for (int i = 0; i < nprob; ++i) {
             h->probs.push_back(build_problem(specs[i], data[i], alpha[i], sigma[i], masks[i], frozen[i], C));
             Problem &p = *h->probs.back();
+            p.batch_member = nprob > 1;
             Engine *e = make_engine(p, prec, C, nprob > 1);
             h->engines.emplace_back(e);
             p.engine = e;

@@ -130,6 +130,7 @@ struct Problem {
     std::vector<double> x, y, u, yq, t;   // host copies of the data (FP64)
     Engine *engine = nullptr;
     RowArena *arena = nullptr;      // set for the chunk engines of a chunked handle
+    bool batch_member = false;      // one of several problems of a batch handle
 };
 
 void build_net_desc(NetDesc &nd, const hmc_mlp_spec &s, long base, const std::vector<long> &idx);

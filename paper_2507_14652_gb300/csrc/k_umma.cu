@@ -2168,7 +2168,15 @@ class UmmaEngine final : public Engine {
             D_row_[i] = make_map(D_[i]->ptr, w_, N_, C, 64, 128);
             D_atom_[i] = make_map(D_[i]->ptr, w_, N_, C, 64, 64);
         }
-        if (use_layer_) tune_dw_splits(total_kb);
+        if (use_layer_ && p.batch_member) {
+            // in a batch the weight-gradient launch covers many problems (grouped) or runs
+            // beside them (lanes), so a split is sized for its own work, 16 K-blocks (1024
+            // rows) or more, not for filling the GPU alone: fewer partials to write and sum
+            nsplit2_ = std::max(1, std::min(kMaxSplits, (total_kb + 15) / 16));
+            tuning_ = "dw row splits " + std::to_string(nsplit2_) + " (batch member: 16 K-blocks per split)";
+        } else if (use_layer_) {
+            tune_dw_splits(total_kb);
+        }
 
         // bias gradients: the first layer's from its reverse kernel (per tile); the hidden
         // layers' from the weight-gradient kernel (per row split) on the persistent path

@@ -179,7 +179,7 @@ def other_workloads(hmc, torch, steps=3):
     from oracle.ess import ess_chains
     out = {}
 
-    def timed(name, sp, q0, eps, L, chains_total, prec_name, ess_traj=0):
+    def timed(name, sp, q0, eps, L, chains_total, prec_name, ess_traj=0, ess_fn=None):
         q0 = torch.from_numpy(q0) if isinstance(q0, np.ndarray) else q0
         sp.sample(q0, eps, L, 1, seed=5, keep_samples=False)
         torch.cuda.synchronize()
@@ -189,7 +189,9 @@ def other_workloads(hmc, torch, steps=3):
         b.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / steps
-        rec = {"dtype": prec_name, "chains": chains_total, "L": L, "eps": eps, "ms_per_trajectory": ms,
+        eps_rec = float(eps) if np.ndim(eps) == 0 else {
+            "per_problem": len(eps), "min": float(np.min(eps)), "median": float(np.median(eps)), "max": float(np.max(eps))}
+        rec = {"dtype": prec_name, "chains": chains_total, "L": L, "eps": eps_rec, "ms_per_trajectory": ms,
                "grad_evals_per_s": chains_total * L / (ms / 1000.0),
                "accept_rate": float(acc.float().mean().item()),
                "abs_dH_median": float(np.nanmedian(np.abs(dH.cpu().numpy())))}
@@ -201,10 +203,11 @@ def other_workloads(hmc, torch, steps=3):
             torch.cuda.synchronize()
             sec = a.elapsed_time(b) / 1000.0
             Sn = S.cpu().double().numpy()[ess_traj // 5:]
-            e = ess_chains(Sn if Sn.ndim == 3 else Sn[:, None, :])   # a batch: every coordinate on its own
+            e = ess_fn(Sn) if ess_fn else ess_chains(Sn if Sn.ndim == 3 else Sn[:, None, :])
             rec.update({"ess_trajectories": ess_traj, "ess_min": float(e.min()), "ess_min_per_s": float(e.min()) / sec,
                         "ess_median_per_s": float(np.median(e)) / sec,
-                        "ess_accept_rate": float(acc2.float().mean().item())})
+                        "ess_accept_rate": float(acc2.float().mean().item()),
+                        "chains_never_accepting": int((acc2.cpu().numpy().sum(axis=0) == 0).sum())})
         out[name] = rec
         sp.close()
 
@@ -221,15 +224,29 @@ def other_workloads(hmc, torch, steps=3):
     tup = [(q.net.widths, q.x, q.y, q.mask, q.frozen, q.prior_sigma, q.noise_sigma) for q in probs]
     q0 = np.concatenate([q.q0.reshape(-1) for q in probs])   # packed [problem][chain][k_problem]
     # grouped launches (the default), then every problem launching its own kernels on the
-    # batch's concurrent lanes, for comparison
+    # batch's concurrent lanes, for comparison; each problem's step adapted first (the
+    # problems differ too much for one common step), the warm-up untimed
     bs = hmc.BatchSampler(tup, probs[0].chains, hmc.PREC_BF16)
     groups = bs.groups()
-    timed("batched_uneven_bf16", bs, q0.astype(np.float32), probs[0].eps, probs[0].L,
-          len(probs) * probs[0].chains, "bf16", ess_traj=40)
+    n_warm = 100
+    eps_b, q_b = bs.adapt_step_size(torch.from_numpy(q0.astype(np.float32)), probs[0].L, probs[0].eps, n_warm,
+                                    target_accept=0.8, seed=71)
+    C = probs[0].chains
+
+    def ess_per_problem(Sn):   # each problem's 8 chains together, every coordinate; packed [n][problem][C][k]
+        out_e, off = [], 0
+        for q in probs:
+            out_e.append(ess_chains(Sn[:, off:off + C * q.k].reshape(Sn.shape[0], C, q.k)))
+            off += C * q.k
+        return np.concatenate(out_e)
+
+    timed("batched_uneven_bf16", bs, q_b, eps_b, probs[0].L, len(probs) * C, "bf16", ess_traj=100,
+          ess_fn=ess_per_problem)
     out["batched_uneven_bf16"]["groups"] = groups
+    out["batched_uneven_bf16"]["warmup_trajectories"] = n_warm
     timed("batched_uneven_bf16_per_problem_launches", hmc.BatchSampler(tup, probs[0].chains, hmc.PREC_BF16,
                                                                        grouped=False),
-          q0.astype(np.float32), probs[0].eps, probs[0].L, len(probs) * probs[0].chains, "bf16")
+          q_b, eps_b, probs[0].L, len(probs) * probs[0].chains, "bf16")
     p = W.cone_deeponet()
     sp = hmc.Sampler.deeponet(p.branch.widths, p.trunk.widths, p.u, p.yq, p.t, p.mask, p.frozen, p.chains,
                               prior_sigma=p.prior_sigma, noise_sigma=p.noise_sigma, prec=hmc.PREC_BF16)

@@ -250,17 +250,30 @@ HMC_API hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, l
                       void *samples, unsigned char *accepted, double *dH, void *q_last);
 
 /*
+ * hmc_sample with a step size per problem: eps [n_problems] doubles (host or device,
+ * each finite and > 0; one entry for a single-problem handle), problem p's trajectories
+ * integrating with eps[p].  Independent problems of a batch differ in their data and
+ * networks, so a common step that suits one can reject everything on another
+ * (hmc_adapt_step_size returns such per-problem steps).  Everything else as hmc_sample.
+ */
+HMC_API hmc_status hmc_sample_steps(hmc_handle h, const void *q0, const double *eps, int L, long n_samples,
+                                    unsigned long long seed, long first_traj,
+                                    void *samples, unsigned char *accepted, double *dH, void *q_last);
+
+/*
  * Step-size adaptation for the warm-up (the paper tunes eps to about 80% acceptance;
  * Sec. 4.2.3): runs n_warmup trajectories of L steps from q, one at a time, and adapts
- * log eps by dual averaging (Hoffman and Gelman 2014, Sec. 3.2) so that the mean
- * over all chains (and problems) of the Metropolis acceptance probability
+ * each problem's log eps by dual averaging (Hoffman and Gelman 2014, Sec. 3.2) so that
+ * the mean over the problem's chains of the Metropolis acceptance probability
  * min(1, exp(-dH)) approaches target_accept; a non-finite dH counts as 0.
  *   q [C][k]        in: start state; out: state after the warm-up (device or host)
- *   eps0            initial step; the shrinkage point is log(10 eps0)
+ *   eps0            initial step of every problem; the shrinkage point is log(10 eps0)
  *   seed, first_traj  Philox stream and trajectory index of the first warm-up
  *                   trajectory; continue sampling with first_traj + n_warmup
- *   eps_out         the averaged step after the last update (host double)
- * The step size is device state: every warm-up trajectory replays the same captured
+ *   eps_out         [n_problems] host doubles: each problem's averaged step after the
+ *                   last update (one double for a single-problem handle); pass them to
+ *                   hmc_sample_steps
+ * The step sizes are device state: every warm-up trajectory replays the same captured
  * trajectory graph (the one hmc_sample uses for this L and seed), and each update runs
  * on the device right after its trajectory, so the warm-up waits for the GPU once, at
  * the end.  Errors as hmc_sample.

@@ -36,15 +36,16 @@ HMC_API long hmc_diag_graph_kernels(hmc_handle h);
  * the seed changes), or -1 for a bad handle. */
 HMC_API long hmc_diag_graph_captures(hmc_handle h);
 
-/* The step sizes of the last hmc_adapt_step_size call on h: out_host[2 m - 2] is the
- * step trajectory m + 1 was given (exp of the dual-averaging iterate after update m)
- * and out_host[2 m - 1] the averaged step after update m, for m = 1..n (n at most that
- * call's n_warmup). */
+/* The step sizes of the last hmc_adapt_step_size call on h, out_host[n][problems][2]:
+ * entry [m - 1][p][0] is the step trajectory m + 1 of problem p was given (exp of the
+ * dual-averaging iterate after update m) and [m - 1][p][1] the averaged step after
+ * update m, for m = 1..n (n at most that call's n_warmup). */
 HMC_API hmc_status hmc_diag_adapt_trace(hmc_handle h, double *out_host, long n);
 
 /* The device dual-averaging update of hmc_adapt_step_size (Hoffman and Gelman 2014,
- * Sec. 3.2) run on given energy errors dH[n][nseg] (host or device) instead of
- * trajectories: update m takes row m - 1.  out_host[n][2] as hmc_diag_adapt_trace. */
+ * Sec. 3.2) run on given energy errors dH[n][nseg] (host or device) of one problem with
+ * nseg chains instead of trajectories: update m takes row m - 1.  out_host[n][2] as
+ * hmc_diag_adapt_trace. */
 HMC_API hmc_status hmc_diag_dual_averaging(const double *dH, long n, int nseg, double eps0, double target,
                                            double *out_host);
 

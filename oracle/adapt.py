@@ -64,16 +64,17 @@ def dual_averaging_dH(dH, eps0, target):
     return dual_averaging([accept_stat(r) for r in dH], eps0, target)
 
 
-def warmup(orc, q, L, eps0, n, target, seed, first_traj):
+def warmup(orc, q, L, eps0, n, target, seed, first_traj, problem=0):
     """The whole warm-up on the oracle: trajectory m (index first_traj + m - 1) from the
-    current chain states with the current step, then one update.  Returns the [n][2]
-    trace and the final states."""
+    current chain states with the current step, then one update; `problem` selects the
+    random stream (a problem of a batch draws from its own).  Returns the [n][2] trace
+    and the final states."""
     q = np.array(q, dtype=np.float64)
     da = DualAveraging(eps0, target)
     eps = eps0
     out = np.zeros((n, 2))
     for m in range(1, n + 1):
-        _, _, dH, q = orc.sample(q, eps, L, 1, seed=seed, first_traj=first_traj + m - 1)
+        _, _, dH, q = orc.sample(q, eps, L, 1, seed=seed, first_traj=first_traj + m - 1, problem=problem)
         out[m - 1] = da.update(accept_stat(dH[0]))
         eps = out[m - 1, 0]
     return out, q

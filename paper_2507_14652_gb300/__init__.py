@@ -34,7 +34,8 @@ STATUS = {0: "HMC_OK", 1: "HMC_ERR_ARG", 2: "HMC_ERR_CUDA", 3: "HMC_ERR_OOM", 4:
 EXPORTS = ["hmc_create", "hmc_create_batch", "hmc_create_split", "hmc_create_chunked", "hmc_num_passes",
            "hmc_sensitivity", "hmc_select_subset",
            "hmc_predict", "hmc_subset_size", "hmc_param_count", "hmc_num_chains", "hmc_diag_umma_gemm",
-           "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_adapt_step_size", "hmc_check", "hmc_destroy",
+           "hmc_energy_grad", "hmc_leapfrog", "hmc_sample", "hmc_sample_steps", "hmc_adapt_step_size", "hmc_check",
+           "hmc_destroy",
            "hmc_last_error",
            "hmc_energy_grad_noalloc",
            "hmc_diag_philox", "hmc_diag_momenta", "hmc_diag_log_uniform", "hmc_diag_graph_kernels",
@@ -115,7 +116,8 @@ def lib():
         L.hmc_energy_grad.argtypes = [vp, vp, vp, vp]
         L.hmc_leapfrog.argtypes = [vp, vp, vp, d, i]
         L.hmc_sample.argtypes = [vp, vp, d, i, lg, u64, lg, vp, vp, vp, vp]
-        L.hmc_adapt_step_size.argtypes = [vp, vp, i, d, lg, d, u64, lg, ct.POINTER(d)]
+        L.hmc_sample_steps.argtypes = [vp, vp, vp, i, lg, u64, lg, vp, vp, vp, vp]
+        L.hmc_adapt_step_size.argtypes = [vp, vp, i, d, lg, d, u64, lg, vp]
         L.hmc_check.argtypes = [vp]
         L.hmc_diag_expire_wait.argtypes = [vp, lg]
         L.hmc_destroy.argtypes = [vp]
@@ -308,7 +310,8 @@ class Sampler:
         return q, p
 
     def sample(self, q0, eps, L, n, seed=0, first_traj=0, keep_samples=True):
-        """n trajectories per chain; returns (samples [n][C][k], accepted [n][C], dH [n][C], q_last [C][k])."""
+        """n trajectories per chain; returns (samples [n][C][k], accepted [n][C], dH [n][C], q_last [C][k]).
+        eps: one step for every problem, or a sequence of one per problem (hmc_sample_steps)."""
         import torch
         q0 = self._state(q0)
         nseg = self.n_problems * self.chains
@@ -316,17 +319,25 @@ class Sampler:
         acc = torch.empty((n, nseg), dtype=torch.uint8, device="cuda")
         dH = torch.empty((n, nseg), dtype=torch.float64, device="cuda")
         ql = torch.empty_like(q0)
-        _check(lib().hmc_sample(self._h, _ptr(q0), float(eps), int(L), int(n), int(seed), int(first_traj),
-                                _ptr(S), _ptr(acc), _ptr(dH), _ptr(ql)))
+        if np.ndim(eps) == 0:
+            _check(lib().hmc_sample(self._h, _ptr(q0), float(eps), int(L), int(n), int(seed), int(first_traj),
+                                    _ptr(S), _ptr(acc), _ptr(dH), _ptr(ql)))
+        else:
+            e = np.ascontiguousarray(eps, dtype=np.float64)
+            if e.shape != (self.n_problems,):
+                raise ValueError(f"need one step per problem ({self.n_problems}), got shape {e.shape}")
+            _check(lib().hmc_sample_steps(self._h, _ptr(q0), _ptr(e), int(L), int(n), int(seed), int(first_traj),
+                                          _ptr(S), _ptr(acc), _ptr(dH), _ptr(ql)))
         return S, acc, dH, ql
 
     def adapt_step_size(self, q0, L, eps0, n_warmup, target_accept=0.8, seed=0, first_traj=0):
-        """Dual-averaging warm-up (hmc_adapt_step_size): returns (eps, q after the warm-up)."""
+        """Dual-averaging warm-up (hmc_adapt_step_size): returns (eps, q after the warm-up),
+        eps a float for one problem, else an array of one step per problem."""
         q = self._state(q0).clone()
-        eps = ct.c_double(0.0)
+        eps = np.zeros(self.n_problems)
         _check(lib().hmc_adapt_step_size(self._h, _ptr(q), int(L), float(eps0), int(n_warmup), float(target_accept),
-                                         int(seed), int(first_traj), ct.byref(eps)))
-        return eps.value, q
+                                         int(seed), int(first_traj), _ptr(eps)))
+        return (float(eps[0]) if self.n_problems == 1 else eps), q
 
     def check(self):
         """hmc_check: wait for the handle's work; raises HmcError (HMC_ERR_TIMEOUT) when a
@@ -482,10 +493,11 @@ def graph_captures(sampler):
 
 def adapt_trace(sampler, n):
     """Step sizes of the last adapt_step_size() call: [n][2] = (step of trajectory m + 1,
-    averaged step after update m) for m = 1..n (hmc_diag_adapt_trace)."""
-    out = np.zeros((n, 2))
+    averaged step after update m) for m = 1..n (hmc_diag_adapt_trace); [n][problems][2]
+    for a batch."""
+    out = np.zeros((n, sampler.n_problems, 2))
     _check(lib().hmc_diag_adapt_trace(sampler._h, _ptr(out), int(n)))
-    return out
+    return out[:, 0, :] if sampler.n_problems == 1 else out
 
 
 def diag_dual_averaging(dH, eps0, target):

@@ -150,26 +150,29 @@ struct TrajState {
     void *samples;            // outputs of the current hmc_sample call (device; may be null)
     unsigned char *accepted;
     double *dH;
-    double eps;               // step size of the trajectories (read by the captured kernels)
-    // dual averaging of log eps during a warm-up (Hoffman and Gelman 2014, Sec. 3.2)
-    long long da_m;           // updates so far
-    double da_hbar, da_log_eps_bar;
+    // dual averaging of log eps during a warm-up (Hoffman and Gelman 2014, Sec. 3.2): the
+    // updates so far; each problem's Hbar and log eps-bar are in the handle's da array
+    long long da_m;
 };
 
-// The kick and drift of one launch: eps / kick_div and eps / drift_div (a divisor of 0
-// means no kick, or no drift), eps read from device state when eps_p is set (captured
-// trajectories, so that a new step size needs no new graph), else the literal eps.
+// The kick and drift of one launch for problem pi: eps / kick_div and eps / drift_div (a
+// divisor of 0 means no kick, or no drift), eps read from the handle's per-problem step
+// sizes in device memory when eps_p is set (captured trajectories, so that a new step
+// size needs no new graph), else the literal eps for every problem.
 struct Step {
-    const double *eps_p;
+    const double *eps_p;   // [problems]
     double eps;
     double kick_div, drift_div;
 };
 
-__device__ __forceinline__ double step_eps(const Step &s) { return s.eps_p ? *s.eps_p : s.eps; }
-__device__ __forceinline__ double step_kick(const Step &s) { return s.kick_div != 0.0 ? step_eps(s) / s.kick_div : 0.0; }
-__device__ __forceinline__ double step_drift(const Step &s)
+__device__ __forceinline__ double step_eps(const Step &s, int pi) { return s.eps_p ? s.eps_p[pi] : s.eps; }
+__device__ __forceinline__ double step_kick(const Step &s, int pi)
 {
-    return s.drift_div != 0.0 ? step_eps(s) / s.drift_div : 0.0;
+    return s.kick_div != 0.0 ? step_eps(s, pi) / s.kick_div : 0.0;
+}
+__device__ __forceinline__ double step_drift(const Step &s, int pi)
+{
+    return s.drift_div != 0.0 ? step_eps(s, pi) / s.drift_div : 0.0;
 }
 
 // Write q into the network buffer b at offset o of chain c (bf16 or fp16 hi/lo pair, or plain).
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_begin(const SegDesc *segs
     if (j0 < sd.k) {
         const long base = sd.qoff + (long)c * sd.k;
         const uint64_t traj = (uint64_t)st->traj;
-        const T h = (T)step_kick(stp), e = (T)step_drift(stp);
+        const T h = (T)step_kick(stp, pi), e = (T)step_drift(stp, pi);
         const long blk = j0 / 4 + threadIdx.x;
         if (blk * 4 < sd.k) {
             double z[4];
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_kick_drift(const SegDesc *segs
     load_seg(sd, &segs[pi]);
     const long base = sd.qoff + (long)c * sd.k;
     const bool kick = stp.kick_div != 0.0, drift = stp.drift_div != 0.0;
-    const T kk = (T)step_kick(stp), dd = (T)step_drift(stp);
+    const T kk = (T)step_kick(stp, pi), dd = (T)step_drift(stp, pi);
     const long j0 = (long)blockIdx.x * TRAJ_ELEMS;
     // every load of the thread's four coordinates first, then the dependent updates
     T pv[4], gv[4], qv[4];
@@ -327,7 +330,7 @@ __global__ void __launch_bounds__(TRAJ_THREADS) k_traj_kinetic(const SegDesc *se
     const int s = blockIdx.y, pi = s / C, c = s % C;
     const long k = segs[pi].k;
     const long base = segs[pi].qoff + (long)c * k;
-    const T h = (T)step_kick(stp);
+    const T h = (T)step_kick(stp, pi);
     const long j0 = (long)blockIdx.x * TRAJ_ELEMS;
     double kin = 0.0;
 #pragma unroll
@@ -406,55 +409,65 @@ __global__ void k_traj_advance(TrajState *st, int nseg, const int *acc_int, doub
     }
 }
 
+// New trajectory counters and outputs; every problem's step set to eps_src[i] (device
+// array) or to eps, and its dual-averaging state cleared.
 __global__ void k_set_state(TrajState *st, long long traj, long long slot, void *samples, unsigned char *acc,
-                            double *dH, double eps)
+                            double *dH, double *eps_prob, double *da, int nprob, const double *eps_src, double eps)
 {
-    st->traj = traj;
-    st->slot = slot;
-    st->samples = samples;
-    st->accepted = acc;
-    st->dH = dH;
-    st->eps = eps;
-    st->da_m = 0;
-    st->da_hbar = 0.0;
-    st->da_log_eps_bar = 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->traj = traj;
+        st->slot = slot;
+        st->samples = samples;
+        st->accepted = acc;
+        st->dH = dH;
+        st->da_m = 0;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nprob; i += gridDim.x * blockDim.x) {
+        eps_prob[i] = eps_src ? eps_src[i] : eps;
+        da[2 * i] = 0.0;
+        da[2 * i + 1] = 0.0;
+    }
 }
 
 // One dual-averaging update (Hoffman and Gelman 2014, Sec. 3.2, their Algorithm 5
-// without the NUTS parts) after trajectory slot - 1 of a warm-up: the statistic is the
-// mean over all nseg segments of min(1, exp(-dH)) (a non-finite dH counts as 0),
-// summed in a fixed order; the new step is written to st->eps for the next
-// trajectory.  trace[2 m - 2] = exp(log eps_m), trace[2 m - 1] = exp(log eps-bar_m).
-__global__ void __launch_bounds__(256) k_dual_avg(TrajState *st, int nseg, double target, double mu, double gamma,
-                                                  double t0, double kappa, double *trace)
+// without the NUTS parts) of every problem's step after trajectory slot - 1 of a warm-up.
+// A warp per problem: the statistic is the mean over the problem's C chains of
+// min(1, exp(-dH)) (a non-finite dH counts as 0), strided over the lanes and summed in a
+// fixed butterfly; the new step goes to eps_prob[pi] for the next trajectory.
+// trace[2 (m - 1) nprob + 2 pi] = exp(log eps_m), [... + 1] = exp(log eps-bar_m).
+__global__ void __launch_bounds__(256) k_dual_avg(TrajState *st, double *eps_prob, double *da, int nprob, int C,
+                                                  double target, double mu, double gamma, double t0, double kappa,
+                                                  double *trace)
 {
-    __shared__ double sm[256];
-    const double *dh = st->dH + (st->slot - 1) * (long long)nseg;
-    double a = 0.0;
-    for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
-        const double v = dh[s];
-        a += isfinite(v) ? fmin(1.0, exp(-v)) : 0.0;
-    }
-    sm[threadIdx.x] = a;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int i = 0; i < (int)blockDim.x; ++i) tot += sm[i];
-        const double abar = tot / (double)nseg;
-        const long long m = ++st->da_m;
-        const double w = 1.0 / ((double)m + t0);
-        const double hbar = (1.0 - w) * st->da_hbar + w * (target - abar);
-        const double log_eps = mu - sqrt((double)m) / gamma * hbar;
-        const double eta = pow((double)m, -kappa);
-        const double lbar = eta * log_eps + (1.0 - eta) * st->da_log_eps_bar;
-        st->da_hbar = hbar;
-        st->da_log_eps_bar = lbar;
-        st->eps = exp(log_eps);
-        if (trace) {
-            trace[2 * (m - 1)] = exp(log_eps);
-            trace[2 * (m - 1) + 1] = exp(lbar);
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const long long m = st->da_m + 1;
+    const double *dh = st->dH + (st->slot - 1) * (long long)nprob * C;
+    for (int pi = threadIdx.x >> 5; pi < nprob; pi += nw) {
+        double a = 0.0;
+        for (int c = lane; c < C; c += 32) {
+            const double v = dh[(long)pi * C + c];
+            a += isfinite(v) ? fmin(1.0, exp(-v)) : 0.0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) {
+            const double abar = a / (double)C;
+            const double w = 1.0 / ((double)m + t0);
+            const double hbar = (1.0 - w) * da[2 * pi] + w * (target - abar);
+            const double log_eps = mu - sqrt((double)m) / gamma * hbar;
+            const double eta = pow((double)m, -kappa);
+            const double lbar = eta * log_eps + (1.0 - eta) * da[2 * pi + 1];
+            da[2 * pi] = hbar;
+            da[2 * pi + 1] = lbar;
+            eps_prob[pi] = exp(log_eps);
+            if (trace) {
+                trace[2 * ((m - 1) * nprob + pi)] = exp(log_eps);
+                trace[2 * ((m - 1) * nprob + pi) + 1] = exp(lbar);
+            }
         }
     }
+    __syncthreads();   // every warp has read m
+    if (threadIdx.x == 0) st->da_m = m;
 }
 
 __global__ void k_rewind_slot(TrajState *st) { st->slot = 0; }
@@ -559,7 +572,9 @@ struct hmc_handle_s {
     unsigned long long traj_seed = 0;
     long traj_kernels = 0;     // kernel nodes in that graph
     long traj_captures = 0;    // graphs captured so far
-    DevBuf adapt_trace;        // [n][2] step sizes of the last warm-up (hmc_diag_adapt_trace)
+    DevBuf adapt_trace;        // [n][problems][2] step sizes of the last warm-up (hmc_diag_adapt_trace)
+    DevBuf eps_prob;           // [problems] step sizes the captured trajectories read
+    DevBuf da_state;           // [problems][2] dual averaging: Hbar, log eps-bar
     long adapt_n = 0;
     ~hmc_handle_s()
     {
@@ -887,7 +902,7 @@ template <typename T> void enqueue_split_trajectory(hmc_handle h, int L, uint64_
     const int nseg = h->C, nblk = h->traj_nblk, M = h->nsplit;
     const SegDesc *sd = h->segs.as<SegDesc>();
     TrajState *st = h->state.as<TrajState>();
-    const double *ep = &st->eps;
+    const double *ep = h->eps_prob.as<double>();
     const dim3 grid(nblk, nseg);
     launch_pdl(k_traj_begin<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, h->q_cur.as<T>(),
                h->g_cur.as<T>(), h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(),
@@ -920,7 +935,7 @@ template <typename T> void enqueue_trajectory(hmc_handle h, int L, uint64_t seed
     const int nseg = h->nprob * h->C, nblk = h->traj_nblk;
     const SegDesc *sd = h->segs.as<SegDesc>();
     TrajState *st = h->state.as<TrajState>();
-    const double *ep = &st->eps;
+    const double *ep = h->eps_prob.as<double>();
     const dim3 grid(nblk, nseg);
     launch_pdl(k_traj_begin<T>, grid, dim3(TRAJ_THREADS), 0, h->stream, sd, h->C, nblk, h->q_cur.as<T>(),
                h->g_cur.as<T>(), h->q_prop.as<T>(), h->p.as<T>(), h->K0p.as<double>(), Step{ep, 0.0, 2.0, 1.0}, seed,
@@ -1108,6 +1123,8 @@ hmc_status create_impl(hmc_handle *out, int nprob, const hmc_net_spec *specs, co
     h->acc_int.alloc(sizeof(int) * nseg);
     h->scratch.alloc(sizeof(int) * 4);
     h->state.alloc(sizeof(TrajState));
+    h->eps_prob.alloc(sizeof(double) * nprob);
+    h->da_state.alloc(sizeof(double) * 2 * nprob);
     std::vector<SegDesc> sd(nprob);
     for (int i = 0; i < nprob; ++i) {
         sd[i].qoff = h->qoff[i];
@@ -1483,15 +1500,28 @@ void ensure_trajectory_graph(hmc_handle h, int L, unsigned long long seed)
     ++h->traj_captures;
 }
 
-hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_samples, unsigned long long seed,
-                      long first_traj, void *samples, unsigned char *accepted, double *dH, void *q_last)
+// hmc_sample (one step for every problem) and hmc_sample_steps (eps_each: a step per
+// problem, host or device).
+hmc_status sample_impl(hmc_handle h, const void *q0, double eps, bool each, const double *eps_each, int L,
+                       long n_samples, unsigned long long seed, long first_traj, void *samples,
+                       unsigned char *accepted, double *dH, void *q_last)
 {
     g_err.clear();
     return guarded([&]() -> hmc_status {
-        HMC_REQUIRE(h && q0, "NULL argument");
-        HMC_REQUIRE(L >= 1 && n_samples >= 0 && first_traj >= 0 && std::isfinite(eps) && eps > 0,
-                    "need L >= 1, eps > 0, n_samples >= 0, first_traj >= 0");
+        HMC_REQUIRE(h && q0 && (eps_each || !each), "NULL argument");
+        HMC_REQUIRE(L >= 1 && n_samples >= 0 && first_traj >= 0, "need L >= 1, n_samples >= 0, first_traj >= 0");
         h->stage_used = 0;
+        const double *deps = nullptr;
+        std::vector<double> e;
+        if (each) {
+            e.resize(h->nprob);
+            HMC_CK(cudaMemcpy(e.data(), eps_each, sizeof(double) * h->nprob, cudaMemcpyDefault));
+            for (double v : e) HMC_REQUIRE(std::isfinite(v) && v > 0, "every step size must be finite and > 0");
+            bool staged;
+            deps = static_cast<const double *>(dev_view(h, e.data(), sizeof(double) * h->nprob, true, &staged));
+        } else {
+            HMC_REQUIRE(std::isfinite(eps) && eps > 0, "need eps > 0");
+        }
         join_in(h);
         const size_t sb = h->elem * (size_t)h->S_total;
         const long nseg = (long)h->nprob * h->C;
@@ -1508,7 +1538,8 @@ hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_sa
             energy_grad_all(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr, false);
             accurate_energy_all(h, h->q_cur.ptr, h->U_cur.as<double>());   // H0 of the first trajectory
         }
-        k_set_state<<<1, 1, 0, h->stream>>>(h->state.as<TrajState>(), first_traj, 0, ds, da, ddh, eps);
+        k_set_state<<<1, 256, 0, h->stream>>>(h->state.as<TrajState>(), first_traj, 0, ds, da, ddh,
+                                               h->eps_prob.as<double>(), h->da_state.as<double>(), h->nprob, deps, eps);
         HMC_LAUNCH_CK();
         if (n_samples > 0) {
             ensure_trajectory_graph(h, L, seed);
@@ -1520,9 +1551,22 @@ hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_sa
         if (sd) HMC_CK(cudaMemcpyAsync(dH, ddh, sizeof(double) * nseg * n_samples, cudaMemcpyDeviceToHost, h->stream));
         if (sl) HMC_CK(cudaMemcpyAsync(q_last, dl, sb, cudaMemcpyDeviceToHost, h->stream));
         join_out(h);
-        if (s0 || ss || sa || sd || sl) HMC_CK(cudaStreamSynchronize(h->stream));
+        if (s0 || ss || sa || sd || sl || deps) HMC_CK(cudaStreamSynchronize(h->stream));
         return HMC_OK;
     });
+}
+
+hmc_status hmc_sample(hmc_handle h, const void *q0, double eps, int L, long n_samples, unsigned long long seed,
+                      long first_traj, void *samples, unsigned char *accepted, double *dH, void *q_last)
+{
+    return sample_impl(h, q0, eps, false, nullptr, L, n_samples, seed, first_traj, samples, accepted, dH, q_last);
+}
+
+hmc_status hmc_sample_steps(hmc_handle h, const void *q0, const double *eps, int L, long n_samples,
+                            unsigned long long seed, long first_traj, void *samples, unsigned char *accepted,
+                            double *dH, void *q_last)
+{
+    return sample_impl(h, q0, 0.0, true, eps, L, n_samples, seed, first_traj, samples, accepted, dH, q_last);
 }
 
 hmc_status hmc_adapt_step_size(hmc_handle h, void *q, int L, double eps0, long n_warmup, double target_accept,
@@ -1540,8 +1584,8 @@ hmc_status hmc_adapt_step_size(hmc_handle h, void *q, int L, double eps0, long n
         const size_t sb = h->elem * (size_t)h->S_total;
         bool sq;
         void *dq = dev_view(h, q, sb, true, &sq);
-        if (h->adapt_trace.n < sizeof(double) * 2 * (size_t)n_warmup)
-            h->adapt_trace.alloc(sizeof(double) * 2 * (size_t)n_warmup);
+        const size_t trace_bytes = sizeof(double) * 2 * (size_t)n_warmup * h->nprob;
+        if (h->adapt_trace.n < trace_bytes) h->adapt_trace.alloc(trace_bytes);
         DevBuf dh_dev(sizeof(double) * nseg);
         TrajState *st = h->state.as<TrajState>();
         HMC_CK(cudaMemcpyAsync(h->q_cur.ptr, dq, sb, cudaMemcpyDeviceToDevice, h->stream));
@@ -1551,32 +1595,36 @@ hmc_status hmc_adapt_step_size(hmc_handle h, void *q, int L, double eps0, long n
             energy_grad_all(h, h->q_cur.ptr, h->U_cur.as<double>(), h->g_cur.ptr, false);
             accurate_energy_all(h, h->q_cur.ptr, h->U_cur.as<double>());
         }
-        k_set_state<<<1, 1, 0, h->stream>>>(st, first_traj, 0, nullptr, nullptr, dh_dev.as<double>(), eps0);
+        k_set_state<<<1, 256, 0, h->stream>>>(st, first_traj, 0, nullptr, nullptr, dh_dev.as<double>(),
+                                               h->eps_prob.as<double>(), h->da_state.as<double>(), h->nprob, nullptr,
+                                               eps0);
         HMC_LAUNCH_CK();
         ensure_trajectory_graph(h, L, seed);
-        // Dual averaging of log eps (Hoffman and Gelman 2014, Sec. 3.2) towards a mean
-        // Metropolis acceptance probability `target_accept` over all chains; shrinkage
-        // towards log(10 eps0), gamma = 0.05, t0 = 10, kappa = 0.75.  Each update runs on
-        // the device after its trajectory and sets the next trajectory's step in the
-        // device state, so the warm-up replays one captured graph without host round
-        // trips.  The returned step is the averaged iterate.
+        // Dual averaging of log eps (Hoffman and Gelman 2014, Sec. 3.2), each problem's
+        // step towards a mean Metropolis acceptance probability `target_accept` over its
+        // chains; shrinkage towards log(10 eps0), gamma = 0.05, t0 = 10, kappa = 0.75.  Each
+        // update runs on the device after its trajectory and sets the next trajectory's
+        // steps in device memory, so the warm-up replays one captured graph without host
+        // round trips.  The returned steps are the averaged iterates.
         const double mu = std::log(10.0 * eps0), gamma = 0.05, t0 = 10.0, kappa = 0.75;
         for (long m = 1; m <= n_warmup; ++m) {
             HMC_CK(cudaGraphLaunch(h->traj_exec, h->stream));
-            k_dual_avg<<<1, 256, 0, h->stream>>>(st, (int)nseg, target_accept, mu, gamma, t0, kappa,
+            k_dual_avg<<<1, 256, 0, h->stream>>>(st, h->eps_prob.as<double>(), h->da_state.as<double>(), h->nprob,
+                                                 h->C, target_accept, mu, gamma, t0, kappa,
                                                  h->adapt_trace.as<double>());
             HMC_LAUNCH_CK();
             k_rewind_slot<<<1, 1, 0, h->stream>>>(st);   // every trajectory's dH goes to slot 0
             HMC_LAUNCH_CK();
         }
-        double lbar = 0.0;
-        HMC_CK(cudaMemcpyAsync(&lbar, &st->da_log_eps_bar, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        std::vector<double> da(2 * (size_t)h->nprob);
+        HMC_CK(cudaMemcpyAsync(da.data(), h->da_state.ptr, sizeof(double) * da.size(), cudaMemcpyDeviceToHost,
+                               h->stream));
         HMC_CK(cudaMemcpyAsync(dq, h->q_cur.ptr, sb, cudaMemcpyDeviceToDevice, h->stream));
         if (sq) HMC_CK(cudaMemcpyAsync(q, dq, sb, cudaMemcpyDeviceToHost, h->stream));
         join_out(h);
         HMC_CK(cudaStreamSynchronize(h->stream));
         h->adapt_n = n_warmup;
-        *eps_out = std::exp(lbar);
+        for (int i = 0; i < h->nprob; ++i) eps_out[i] = std::exp(da[2 * (size_t)i + 1]);
         return HMC_OK;
     });
 }
@@ -1589,7 +1637,8 @@ hmc_status hmc_diag_adapt_trace(hmc_handle h, double *out_host, long n)
         HMC_REQUIRE(n >= 0 && n <= h->adapt_n, "n (%ld) exceeds the last warm-up's %ld updates", n, h->adapt_n);
         HMC_CK(cudaStreamSynchronize(h->stream));
         if (n > 0)
-            HMC_CK(cudaMemcpy(out_host, h->adapt_trace.ptr, sizeof(double) * 2 * (size_t)n, cudaMemcpyDeviceToHost));
+            HMC_CK(cudaMemcpy(out_host, h->adapt_trace.ptr, sizeof(double) * 2 * (size_t)n * h->nprob,
+                              cudaMemcpyDeviceToHost));
         return HMC_OK;
     });
 }
@@ -1600,15 +1649,19 @@ hmc_status hmc_diag_dual_averaging(const double *dH, long n, int nseg, double ep
     return guarded([&]() -> hmc_status {
         HMC_REQUIRE(dH && out_host && n >= 1 && nseg >= 1 && eps0 > 0 && std::isfinite(eps0), "bad argument");
         HMC_REQUIRE(target > 0.0 && target < 1.0, "target must lie in (0, 1)");
+        // one problem with nseg chains
         DevBuf st(sizeof(TrajState)), d(sizeof(double) * (size_t)n * nseg), tr(sizeof(double) * 2 * (size_t)n);
+        DevBuf ep(sizeof(double)), da(2 * sizeof(double));
         HMC_CK(cudaMemcpy(d.ptr, dH, d.n, cudaMemcpyDefault));
-        k_set_state<<<1, 1>>>(st.as<TrajState>(), 0, 0, nullptr, nullptr, d.as<double>(), eps0);
+        k_set_state<<<1, 32>>>(st.as<TrajState>(), 0, 0, nullptr, nullptr, d.as<double>(), ep.as<double>(),
+                               da.as<double>(), 1, nullptr, eps0);
         HMC_LAUNCH_CK();
         const double mu = std::log(10.0 * eps0);
         for (long m = 1; m <= n; ++m) {
             k_advance_slot<<<1, 1>>>(st.as<TrajState>());   // as a trajectory would: dH row m - 1
             HMC_LAUNCH_CK();
-            k_dual_avg<<<1, 256>>>(st.as<TrajState>(), nseg, target, mu, 0.05, 10.0, 0.75, tr.as<double>());
+            k_dual_avg<<<1, 256>>>(st.as<TrajState>(), ep.as<double>(), da.as<double>(), 1, nseg, target, mu, 0.05,
+                                   10.0, 0.75, tr.as<double>());
             HMC_LAUNCH_CK();
         }
         HMC_CK(cudaMemcpy(out_host, tr.ptr, tr.n, cudaMemcpyDeviceToHost));

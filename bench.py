@@ -254,6 +254,27 @@ def other_workloads(hmc, torch, steps=3):
     return out
 
 
+def gradients_only(name, n):
+    """U and grad U of the named workload n times (BF16), for profiling."""
+    import torch
+    import paper_2507_14652_gb300 as hmc
+    if name == "wide_mlp":
+        p = W.wide_mlp()
+        s = hmc.Sampler.mlp(p.net.widths, p.x, p.y, p.mask, p.frozen, p.chains, prior_sigma=p.prior_sigma,
+                            noise_sigma=p.noise_sigma, prec=hmc.PREC_BF16)
+        q = torch.from_numpy(p.q0).float().cuda()
+    else:
+        probs = W.batched_uneven()
+        s = hmc.BatchSampler([(p.net.widths, p.x, p.y, p.mask, p.frozen, p.prior_sigma, p.noise_sigma)
+                              for p in probs], probs[0].chains, hmc.PREC_BF16)
+        q = torch.from_numpy(np.concatenate([p.q0.reshape(-1) for p in probs]).astype(np.float32)).cuda()
+    for _ in range(n):
+        s.energy_grad(q)
+    torch.cuda.synchronize()
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -265,10 +286,15 @@ def main():
     ap.add_argument("--split", type=int, default=4, help="data batches of the split-integrator run (0 = skip)")
     ap.add_argument("--no-around", action="store_true", help="skip the sensitivity/truncation/predictive timings")
     ap.add_argument("--no-other", action="store_true", help="skip the other workloads (tiny BNN, DeepONets, batch)")
+    ap.add_argument("--gradients-only", choices=["wide_mlp", "batched_uneven"],
+                    help="build the workload's handle, run --steps gradient evaluations and exit (a short "
+                         "program for ncu launch lists and captures; prints no bench line)")
     args = ap.parse_args()
     assert args.warmup >= 3, "timing rules need at least 3 warm-up steps"
     if args.impl == "reference":
         return run_reference(args)
+    if args.gradients_only:
+        return gradients_only(args.gradients_only, args.steps)
 
     import torch
     import paper_2507_14652_gb300 as hmc

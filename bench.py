@@ -254,20 +254,30 @@ def other_workloads(hmc, torch, steps=3):
     return out
 
 
-def gradients_only(name, n):
-    """U and grad U of the named workload n times (BF16), for profiling."""
+def gradients_only(name, n, chains=0):
+    """U and grad U of the named workload n times (BF16), for profiling; `chains` > 0
+    replaces a single-problem workload's chain count (a smaller capture)."""
     import torch
     import paper_2507_14652_gb300 as hmc
     if name == "wide_mlp":
         p = W.wide_mlp()
+        if chains:
+            p.q0 = np.ascontiguousarray(p.q0[:chains])
         s = hmc.Sampler.mlp(p.net.widths, p.x, p.y, p.mask, p.frozen, p.chains, prior_sigma=p.prior_sigma,
                             noise_sigma=p.noise_sigma, prec=hmc.PREC_BF16)
         q = torch.from_numpy(p.q0).float().cuda()
-    else:
+    elif name == "batched_uneven":
         probs = W.batched_uneven()
         s = hmc.BatchSampler([(p.net.widths, p.x, p.y, p.mask, p.frozen, p.prior_sigma, p.noise_sigma)
                               for p in probs], probs[0].chains, hmc.PREC_BF16)
         q = torch.from_numpy(np.concatenate([p.q0.reshape(-1) for p in probs]).astype(np.float32)).cuda()
+    else:
+        p = W.deeponet_grf() if name == "deeponet_grf" else W.cone_deeponet()
+        if chains:
+            p.q0 = np.ascontiguousarray(p.q0[:chains])
+        s = hmc.Sampler.deeponet(p.branch.widths, p.trunk.widths, p.u, p.yq, p.t, p.mask, p.frozen, p.chains,
+                                 prior_sigma=p.prior_sigma, noise_sigma=p.noise_sigma, prec=hmc.PREC_BF16)
+        q = torch.from_numpy(p.q0).float().cuda()
     for _ in range(n):
         s.energy_grad(q)
     torch.cuda.synchronize()
@@ -286,15 +296,16 @@ def main():
     ap.add_argument("--split", type=int, default=4, help="data batches of the split-integrator run (0 = skip)")
     ap.add_argument("--no-around", action="store_true", help="skip the sensitivity/truncation/predictive timings")
     ap.add_argument("--no-other", action="store_true", help="skip the other workloads (tiny BNN, DeepONets, batch)")
-    ap.add_argument("--gradients-only", choices=["wide_mlp", "batched_uneven"],
+    ap.add_argument("--gradients-only", choices=["wide_mlp", "batched_uneven", "deeponet_grf", "cone_deeponet"],
                     help="build the workload's handle, run --steps gradient evaluations and exit (a short "
                          "program for ncu launch lists and captures; prints no bench line)")
+    ap.add_argument("--chains", type=int, default=0, help="with --gradients-only: chains (0 = the workload's)")
     args = ap.parse_args()
     assert args.warmup >= 3, "timing rules need at least 3 warm-up steps"
     if args.impl == "reference":
         return run_reference(args)
     if args.gradients_only:
-        return gradients_only(args.gradients_only, args.steps)
+        return gradients_only(args.gradients_only, args.steps, args.chains)
 
     import torch
     import paper_2507_14652_gb300 as hmc

@@ -324,14 +324,31 @@ __device__ __forceinline__ void umma_body(const CUtensorMap &tmA, const CUtensor
                 const float *yb = p.Yt + m;
                 double r2 = 0.0;
                 float dsum = 0.0f;
+                const long ny = p.ny, ldo = p.ldo;
                 for (int c0 = 0; c0 < BN; c0 += 32) {
                     float v[32];
                     tmem_ld32(taddr + c0, v);
                     const int u0 = n0 + c0;
-                    if (valid && u0 < p.nu) {
+                    if (valid && u0 + 32 <= p.nu) {   // a whole chunk: no per-column bounds
+                        const float *yp = yb + (long)u0 * ny;
+                        h16 *op = ob + (long)u0 * ldo;
                         float yv[32];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) yv[j] = u0 + j < p.nu ? __ldg(yb + (long)(u0 + j) * p.ny) : 0.0f;
+                        for (int j = 0; j < 32; ++j) yv[j] = __ldg(yp + j * ny);
+                        float r2c = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float r = (v[j] + b0) - yv[j];
+                            r2c += r * r;
+                            const float ds = r * p.inv_s2;
+                            dsum += ds;
+                            op[j * ldo] = f_to_h16(ds);
+                        }
+                        r2 += (double)r2c;
+                    } else if (valid && u0 < p.nu) {
+                        float yv[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) yv[j] = u0 + j < p.nu ? __ldg(yb + (long)(u0 + j) * ny) : 0.0f;
                         float r2c = 0.0f;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
@@ -340,7 +357,7 @@ __device__ __forceinline__ void umma_body(const CUtensorMap &tmA, const CUtensor
                                 r2c += r * r;
                                 const float ds = r * p.inv_s2;
                                 dsum += ds;
-                                ob[(long)(u0 + j) * p.ldo] = f_to_h16(ds);
+                                ob[(long)(u0 + j) * ldo] = f_to_h16(ds);
                             }
                         }
                         r2 += (double)r2c;
@@ -607,6 +624,7 @@ constexpr int L_SMEM = 1024 + 2 * L_W_HALF + L_STAGES * L_A_BYTES + 256 + L_SCR_
                        2 * 256 * 4 + 2 * 128 * 4;        // + bias and output weights of the chain, half-row sums
 constexpr int L_THREADS = 320;                          // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 static_assert(8 * L_AUX <= L_W_HALF, "reverse-pass slope buffers fit the lo region");
+static_assert(8 * L_STG / 4 + 4 * 256 <= L_SCR_FLOATS, "reverse column sums fit after the staging buffers");
 // Reverse pass with the weights as a hi/lo pair (the lo region then holds W): a two-stage
 // operand ring, and two of a warp's four slope chunks in flight, in a region of their own
 // after the per-chain vectors, within the same L_SMEM.
@@ -689,6 +707,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtens
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 7);
     float *scr = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(bars) + 256);
     float *red = scr;                                                                  // column sums
+    float *redb = scr + 8 * L_STG / 4;   // reverse tanh: [4][w] column sums, after the staging buffers
     uint8_t *stage0 = BWD ? reinterpret_cast<uint8_t *>(scr) : reinterpret_cast<uint8_t *>(scr + 4 * 256);
     double *dred = reinterpret_cast<double *>(scr + L_SCR_FLOATS);   // [4]
     float *fred = reinterpret_cast<float *>(dred + 4);               // [4]
@@ -928,9 +947,9 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtens
             // the ones, for rows 16 ks + 8 hf + 2 (lane % 4) + {0, 1}
             uint32_t bx[2][2] = {{0u, 0u}, {0u, 0u}};
             if (MODE == L_BWD_FIRST) {
-                float vn[5];
+                float vn[8];   // inputs and the ones column: dx <= 7
 #pragma unroll
-                for (int n = 0; n < 5; ++n)
+                for (int n = 0; n < 8; ++n)
                     vn[n] = n < p.dx ? (valid ? p.x[(long)m * p.dx + n] : 0.0f) : (n == p.dx ? 1.0f : 0.0f);
                 const int g = lane >> 2, c2 = 2 * (lane & 3);
 #pragma unroll
@@ -940,7 +959,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtens
                         const int r = 16 * ks + 8 * hf + c2;
                         float v0 = 0.0f, v1 = 0.0f;
 #pragma unroll
-                        for (int n = 0; n < 5; ++n) {
+                        for (int n = 0; n < 8; ++n) {
                             const float a0 = __shfl_sync(0xffffffffu, vn[n], r);
                             const float a1 = __shfl_sync(0xffffffffu, vn[n], r + 1);
                             if (g == n) {
@@ -1027,6 +1046,9 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtens
 #pragma unroll
                         for (int j = 0; j < 16; ++j) pk[j] = pack_h16(dd[2 * j], dd[2 * j + 1]);
                         store_chunk(pk, c0);
+                        // when asked (db_part set), the column sums of the tile's deltas, the
+                        // bias gradient of the layer below: this warp's 32 rows first
+                        if (p.db_part) redb[q * LN + hc0 + c0 + lane] = reduce_scatter32(dd);
                     }
                     if (MODE == L_BWD_FIRST) {
                         // first-layer weight and bias gradients of this chunk's 32 columns over the
@@ -1069,6 +1091,14 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtens
                                     else if (n == p.dx) red[(0 * 4 + q) * LN + col] = v;
                                 }
                     }
+                }
+                if (MODE == L_BWD_TANH && p.db_part) {   // the four quadrants' sums, per tile
+                    named_bar_sync(1, 256);
+                    if (tile_ok)
+                        for (int cc = et; cc < LN; cc += 256)
+                            p.db_part[part + cc] = redb[0 * LN + cc] + redb[1 * LN + cc] + redb[2 * LN + cc] +
+                                                   redb[3 * LN + cc];
+                    named_bar_sync(1, 256);
                 }
                 if (MODE == L_BWD_FIRST) {
                     named_bar_sync(1, 256);
@@ -1571,7 +1601,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     float v[32];
                     tmem_ld32(taddr + c0, v);
                     const int u0 = n0 + c0;
-                    if (valid && u0 < p.nu) {
+                    if (valid && u0 + 32 <= p.nu) {   // a whole chunk: no per-column bounds
+                        const long ny = p.M;
+                        const float *yp = yb + (long)u0 * ny;
+                        float yv[32];
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) yv[j] = __ldg(yp + j * ny);
+                        float r2c = 0.0f;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float r = (v[j] + b0) - yv[j];
+                            r2c += r * r;
+                        }
+                        r2 += (double)r2c;
+                    } else if (valid && u0 < p.nu) {
                         float r2c = 0.0f;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
@@ -2131,8 +2174,9 @@ class UmmaEngine final : public Engine {
         dw0_part_.alloc(sizeof(float) * C * ntiles_ * w_ * dx_);
         db_part_.resize(L_ - 1);   // biases of layers 0..L-2, per-tile column sums
         for (int l = 0; l <= L_ - 2; ++l) db_part_[l].reset(new DevBuf(sizeof(float) * C * ntiles_ * w_));
-        // the persistent pair kernels keep the first layer's column sums in 20 KB: dx <= 4 at w = 256
-        use_layer_ = (w_ == 128 || (w_ == 256 && dx_ <= 4));
+        // the persistent pair kernels keep the first layer's column sums in 20 KB (dx <= 4 at
+        // w = 256) and form them from an 8-column [X | 1] block (dx <= 7)
+        use_layer_ = (w_ == 128 && dx_ <= 7) || (w_ == 256 && dx_ <= 4);
 
         // per-entry metadata, scatter plan, per-layer CSR of the sampled hidden weights
         build_entries();
@@ -3098,6 +3142,10 @@ struct DonNet {
     std::unique_ptr<DevBuf> act[MAXL + 1], del[MAXL + 1];   // A_l, D_l for l = 1..L ([C][R][w_l])
     CUtensorMap act_row[MAXL + 1], act_atom[MAXL + 1], del_row[MAXL + 1], del_atom[MAXL + 1];
     CUtensorMap w_row_h[MAXL], w_row_l[MAXL], w_atom_h[MAXL], w_atom_l[MAXL], x_row, x_atom, x_row_lo;
+    // hidden w x w tanh layers (w = 128 or 256) run forward on the persistent pair kernel:
+    // the halves of W (hi and lo) that each CTA of a pair keeps resident
+    bool pair[MAXL] = {};
+    CUtensorMap w_half_h[MAXL], w_half_l[MAXL];
 };
 
 class DonEngine final : public Engine {
@@ -3470,6 +3518,13 @@ class DonEngine final : public Engine {
                 n.w_atom_h[l] = make_map(n.wh[l]->ptr, in, out, C, 64, 64);
                 n.w_atom_l[l] = make_map(n.wl[l]->ptr, in, out, C, 64, 64);
             }
+            if (l >= 1 && l < n.L - 1 && in == out && (out == 128 || out == 256) && n.inld[l] == in &&
+                nd.act[l] == HMC_ACT_TANH) {
+                n.pair[l] = true;
+                n.w_half_h[l] = make_map(n.wh[l]->ptr, in, out, C, 64, out / 2);
+                n.w_half_l[l] = make_map(n.wl[l]->ptr, in, out, C, 64, out / 2);
+                if (max_clusters_ == 0) max_clusters_ = layer_max_clusters();
+            }
         }
         // activations and deltas, per-tile column sums
         for (int l = 1; l <= n.L; ++l) {
@@ -3514,7 +3569,20 @@ class DonEngine final : public Engine {
             pp.out_b = n.R * pp.N;
             const CUtensorMap &a = (l == 0) ? n.x_row : n.act_row[l];
             const dim3 grid(n.ntiles, 1, C_);
-            if (l < n.L - 1)
+            if (n.pair[l]) {   // the persistent pair kernel: (chain, tile pair) units on CTA pairs
+                LayerParams lp{};
+                lp.N = (int)n.R;
+                lp.W = pp.N;
+                lp.C = C_;
+                lp.ntiles = n.ntiles;
+                lp.dx = n.dx;
+                lp.err = err_;
+                lp.bias = pp.bias;
+                lp.out = pp.out;
+                const long units = (long)C_ * ((n.ntiles + 1) / 2);
+                launch_layer<L_FWD_TANH>(a, n.w_half_h[l], n.w_half_l[l], lp,
+                                         2 * (int)std::min<long>(max_clusters_, units), s);
+            } else if (l < n.L - 1)
                 launch_umma<M_FWD_TANH, false, false, true>(a, n.w_row_h[l], n.w_row_l[l], pp, grid, s);
             else
                 launch_umma<M_FWD_LIN, false, false, true>(a, n.w_row_h[l], n.w_row_l[l], pp, grid, s);
@@ -3557,7 +3625,31 @@ class DonEngine final : public Engine {
             pp.aux_b = n.R * pp.N;
             pp.db_part = n.colsum[l - 1]->as<float>();
             const dim3 grid(n.ntiles, 1, C_);
-            if (l == 1 && !n.gemm_first) {
+            // the persistent pair kernel for the w x w layers (first-layer sums of up to four
+            // inputs at w = 256, seven at w = 128), with the column sums of delta_l as the
+            // bias gradient
+            const bool first = l == 1 && !n.gemm_first;
+            if (n.pair[l] && (!first || n.dx <= 4 || (pp.N == 128 && n.dx <= 7))) {
+                LayerParams lp{};
+                lp.N = (int)n.R;
+                lp.W = pp.N;
+                lp.C = C_;
+                lp.ntiles = n.ntiles;
+                lp.dx = n.dx;
+                lp.err = err_;
+                lp.aux = pp.aux;
+                lp.db_part = pp.db_part;
+                const long units = (long)C_ * ((n.ntiles + 1) / 2);
+                const int ncta = 2 * (int)std::min<long>(max_clusters_, units);
+                if (first) {
+                    lp.x = n.x32.as<float>();
+                    lp.dw0_part = n.dw0.as<float>();
+                    launch_layer<L_BWD_FIRST>(n.del_row[l + 1], n.w_atom_h[l], n.w_atom_l[l], lp, ncta, s);
+                } else {
+                    lp.out = n.del[l]->as<h16>();
+                    launch_layer<L_BWD_TANH>(n.del_row[l + 1], n.w_atom_h[l], n.w_atom_l[l], lp, ncta, s);
+                }
+            } else if (first) {
                 pp.x = n.x32.as<float>();
                 pp.dx = n.dx;
                 pp.dw0_part = n.dw0.as<float>();
@@ -3713,6 +3805,7 @@ class DonEngine final : public Engine {
     int nheavy_ = 0;
     CUtensorMap ds_row_, ds_atom_, b_col_, b_hi_e_, b_lo_e_;
     int es_ = 256, nut_e_ = 1, ntn_e_ = 1;
+    int max_clusters_ = 0;             // pair-kernel CTA pairs resident at once (0: no pair layer)
     DevBuf u_acc_;
     ScatterPlan plan_;
     std::string tuning_;

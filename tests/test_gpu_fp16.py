@@ -164,7 +164,8 @@ def test_fp16_engine_tanh_is_accurate_to_1e_6():
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
-@pytest.mark.parametrize("widths", [(2, 40, 40, 1), (3, 100, 100, 100, 1), (4, 200, 200, 1)])
+@pytest.mark.parametrize("widths", [(2, 40, 40, 1), (3, 100, 100, 100, 1), (4, 200, 200, 1), (6, 100, 100, 1),
+                                    (7, 128, 128, 128, 1), (8, 64, 64, 1), (6, 256, 256, 1)])
 def test_hidden_widths_padded_with_zero_units(prec, widths):
     # the tensor-core engines pad a hidden width to 128 (or 256 above 128) with zero units
     prob = W.small_mlp(n=300, widths=widths, frac=0.2, chains=2, seed=61)

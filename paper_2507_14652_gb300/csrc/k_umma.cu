@@ -942,6 +942,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtens
             const long wbase = ((long)c * p.N + r0) * p.W + hc0;   // element (r0, hc0) of [c][N][W]
             const long part = ((long)c * p.ntiles + t) * p.W;
             const float yv = (MODE == L_FWD_OUT && valid) ? p.y[m] : 0.0f;
+            const float bo = MODE == L_FWD_OUT ? p.bout[c] : 0.0f;   // (loaded before the accumulator wait)
             // first-layer gradients: the B operand [X | 1] of dW0 = delta_1^T X and db0 = delta_1^T 1
             // as mma.sync fragments of this warp's 32 rows: column n < dx holds x_n, column dx
             // the ones, for rows 16 ks + 8 hf + 2 (lane % 4) + {0, 1}
@@ -1139,7 +1140,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtens
                 // the row's dot product: both halves, in a fixed order
                 fsum[h * 128 + row] = fh;
                 named_bar_sync(1, 256);
-                const float fo = p.bout[c] + (fsum[row] + fsum[128 + row]);
+                const float fo = bo + (fsum[row] + fsum[128 + row]);
                 const float r = valid ? fo - yv : 0.0f;
                 const float d = r * p.inv_s2;
                 if (h == 0) {   // the warp's 32 squared residuals: an FP32 partial, then FP64

@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(NTHREADS, WSPLIT ? 1 : 2) k_umma_g(const GridJ
 // warp, so global loads and stores move 8 rows x 64 contiguous bytes per
 // instruction instead of 32 scattered 16-byte pieces.
 // ---------------------------------------------------------------------------
-enum LMode { L_FWD_TANH = 0, L_FWD_OUT = 1, L_BWD_TANH = 2, L_BWD_FIRST = 3 };
+enum LMode { L_FWD_TANH = 0, L_FWD_OUT = 1, L_BWD_TANH = 2, L_BWD_FIRST = 3, L_FWD_LIN = 4 };
 constexpr int L_STAGES = 4;
 constexpr int L_A_BYTES = BM * BK * 2;                  // one 16 KB K-block of a 128-row tile
 constexpr int L_W_HALF = 64 * 1024;                     // resident half of W, hi or lo (4 K-blocks x 16 KB)
@@ -678,7 +678,10 @@ struct UnitCursor {
 // (job j's from jobs[j].ustart on, utotal in all); every role tracks the job of its
 // current unit, and W reloads whenever (job, chain) changes.  Otherwise tmA0, tmWh0,
 // tmWl0 and p0 describe the one problem.
-template <int MODE, bool WSPLIT, int WIDTH, bool G>
+// WIDTH: the output features of the layer product (its columns), KD: its reduction width
+// (the square hidden layers have KD = WIDTH; a net's last layer, w -> p, does not).
+// L_FWD_LIN: a forward layer without activation (a DeepONet net's last layer).
+template <int MODE, bool WSPLIT, int WIDTH, bool G, int KD = WIDTH>
 __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtensorMap &tmWh0, const CUtensorMap &tmWl0,
                                            const LayerParams &p0, const LayerJob *__restrict__ jobs, int njobs,
                                            long utotal)
@@ -686,7 +689,8 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtens
     constexpr bool BWD = (MODE == L_BWD_TANH || MODE == L_BWD_FIRST);
     constexpr int LN = WIDTH;                          // accumulator columns: whole rows
     constexpr int BN = WIDTH / 2;                      // rows of B (W) resident in this CTA
-    constexpr int NKB = WIDTH / 64;                    // K-blocks of the reduction
+    constexpr int NKB = KD / 64;                       // K-blocks of the reduction
+    static_assert(KD % 64 == 0 && WIDTH % 64 == 0 && (!BWD || BN % 64 == 0), "layer shape");
     constexpr int NCH = LN / 64;                       // 32-column chunks of one epilogue warp's half row
     constexpr int SLOT = LN;                           // TMEM columns per accumulator
     constexpr int TCOLS = 2 * SLOT;
@@ -1000,7 +1004,7 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtens
             tc_fence_after();
             const uint32_t taddr = tmem + lane_off + (uint32_t)(slot * SLOT + hc0);
             uint32_t rb[2][32];
-            if (MODE == L_FWD_TANH) {
+            if (MODE == L_FWD_TANH || MODE == L_FWD_LIN) {
                 tmem_ld32_issue(taddr, rb[0]);
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) {
@@ -1009,9 +1013,11 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtens
                     if (ch + 1 < NCH) tmem_ld32_issue(taddr + c0 + 32, rb[(ch + 1) & 1]);
                     uint32_t pk[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        pk[j] = pack_h16(act_tanh(__uint_as_float(rb[ch & 1][2 * j]) + sbias[hc0 + c0 + 2 * j]),
-                                          act_tanh(__uint_as_float(rb[ch & 1][2 * j + 1]) + sbias[hc0 + c0 + 2 * j + 1]));
+                    for (int j = 0; j < 16; ++j) {
+                        const float z0 = __uint_as_float(rb[ch & 1][2 * j]) + sbias[hc0 + c0 + 2 * j];
+                        const float z1 = __uint_as_float(rb[ch & 1][2 * j + 1]) + sbias[hc0 + c0 + 2 * j + 1];
+                        pk[j] = MODE == L_FWD_LIN ? pack_h16(z0, z1) : pack_h16(act_tanh(z0), act_tanh(z1));
+                    }
                     store_chunk(pk, c0);
                 }
             } else if (BWD) {
@@ -1246,12 +1252,12 @@ __device__ __forceinline__ void layer_body(const CUtensorMap &tmA0, const CUtens
     }
 }
 
-template <int MODE, int WIDTH, bool SPLIT>
+template <int MODE, int WIDTH, bool SPLIT, int KD = WIDTH>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(L_THREADS, 1)
     k_layer_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmWh,
                  const __grid_constant__ CUtensorMap tmWl, const __grid_constant__ LayerParams p)
 {
-    layer_body<MODE, SPLIT, WIDTH, false>(tmA, tmWh, tmWl, p, nullptr, 1, 0);
+    layer_body<MODE, SPLIT, WIDTH, false, KD>(tmA, tmWh, tmWl, p, nullptr, 1, 0);
 }
 
 // The grouped launch: the units of njobs problems (utotal in all) on one grid of CTA pairs.
@@ -2033,19 +2039,20 @@ void launch_umma(const CUtensorMap &a, const CUtensorMap &b, const CUtensorMap &
     HMC_LAUNCH_CK();
 }
 
-template <int MODE, int WIDTH, bool SPLIT>
+template <int MODE, int WIDTH, bool SPLIT, int KD = WIDTH>
 void launch_layer_w(const CUtensorMap &a, const CUtensorMap &wh, const CUtensorMap &wl, const LayerParams &p, int ncta,
                     cudaStream_t s)
 {
     static bool configured = false;
     if (!configured) {
-        HMC_CK(cudaFuncSetAttribute(k_layer_pair<MODE, WIDTH, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        HMC_CK(cudaFuncSetAttribute(k_layer_pair<MODE, WIDTH, SPLIT, KD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     L_SMEM));
         configured = true;
     }
-    static const char *names[] = {"layer_fwd_tanh", "layer_fwd_out", "layer_bwd_tanh", "layer_bwd_first"};
+    static const char *names[] = {"layer_fwd_tanh", "layer_fwd_out", "layer_bwd_tanh", "layer_bwd_first",
+                                  "layer_fwd_lin"};
     ProfScope ps(names[MODE], s);
-    launch_pdl(k_layer_pair<MODE, WIDTH, SPLIT>, dim3(ncta), dim3(L_THREADS), L_SMEM, s, a, wh, wl, p);
+    launch_pdl(k_layer_pair<MODE, WIDTH, SPLIT, KD>, dim3(ncta), dim3(L_THREADS), L_SMEM, s, a, wh, wl, p);
     HMC_LAUNCH_CK();
 }
 
@@ -2059,6 +2066,24 @@ void launch_layer(const CUtensorMap &a, const CUtensorMap &wh, const CUtensorMap
     constexpr bool SPLIT = true;
     if (p.W == 256) launch_layer_w<MODE, 256, SPLIT>(a, wh, wl, p, ncta, s);
     else launch_layer_w<MODE, 128, SPLIT>(a, wh, wl, p, ncta, s);
+}
+
+// A layer product of N output features over a reduction of K on the pair kernel, for the
+// shape of a DeepONet net's last layer 256 -> 128: forward (N = 128, K = 256, linear) and
+// the reverse through it (N = 256, K = 128).  False for a shape it has no kernel for.
+bool pair_shape_ok(int mode, int N, int K)
+{
+    if (mode == L_FWD_LIN) return N == 128 && K == 256;
+    if (mode == L_BWD_TANH) return N == 256 && K == 128;
+    return false;
+}
+
+template <int MODE>
+void launch_layer_nk(const CUtensorMap &a, const CUtensorMap &wh, const CUtensorMap &wl, const LayerParams &p,
+                     int ncta, cudaStream_t s)
+{
+    if (MODE == L_FWD_LIN) launch_layer_w<L_FWD_LIN, 128, true, 256>(a, wh, wl, p, ncta, s);
+    else launch_layer_w<L_BWD_TANH, 256, true, 128>(a, wh, wl, p, ncta, s);
 }
 
 void launch_dw2(const CUtensorMap &d, const CUtensorMap &a, const Params &p, dim3 grid, cudaStream_t s)
@@ -3146,6 +3171,7 @@ struct DonNet {
     // hidden w x w tanh layers (w = 128 or 256) run forward on the persistent pair kernel:
     // the halves of W (hi and lo) that each CTA of a pair keeps resident
     bool pair[MAXL] = {};
+    bool pair_last = false;   // the last layer (w -> p) too, forward and reverse (pair_shape_ok)
     CUtensorMap w_half_h[MAXL], w_half_l[MAXL];
 };
 
@@ -3519,6 +3545,14 @@ class DonEngine final : public Engine {
                 n.w_atom_h[l] = make_map(n.wh[l]->ptr, in, out, C, 64, 64);
                 n.w_atom_l[l] = make_map(n.wl[l]->ptr, in, out, C, 64, 64);
             }
+            const bool last = l == n.L - 1 && l >= 2 && n.inld[l] == in && pair_shape_ok(L_FWD_LIN, out, in) &&
+                              pair_shape_ok(L_BWD_TANH, in, out) && nd.act[l] == HMC_ACT_IDENTITY;
+            if (last) {
+                n.pair_last = true;
+                n.w_half_h[l] = make_map(n.wh[l]->ptr, in, out, C, 64, out / 2);
+                n.w_half_l[l] = make_map(n.wl[l]->ptr, in, out, C, 64, out / 2);
+                if (max_clusters_ == 0) max_clusters_ = layer_max_clusters();
+            }
             if (l >= 1 && l < n.L - 1 && in == out && (out == 128 || out == 256) && n.inld[l] == in &&
                 nd.act[l] == HMC_ACT_TANH) {
                 n.pair[l] = true;
@@ -3583,6 +3617,19 @@ class DonEngine final : public Engine {
                 const long units = (long)C_ * ((n.ntiles + 1) / 2);
                 launch_layer<L_FWD_TANH>(a, n.w_half_h[l], n.w_half_l[l], lp,
                                          2 * (int)std::min<long>(max_clusters_, units), s);
+            } else if (l == n.L - 1 && n.pair_last) {   // the last layer, linear, on the pair kernel
+                LayerParams lp{};
+                lp.N = (int)n.R;
+                lp.W = pp.N;
+                lp.C = C_;
+                lp.ntiles = n.ntiles;
+                lp.dx = n.dx;
+                lp.err = err_;
+                lp.bias = pp.bias;
+                lp.out = pp.out;
+                const long units = (long)C_ * ((n.ntiles + 1) / 2);
+                launch_layer_nk<L_FWD_LIN>(a, n.w_half_h[l], n.w_half_l[l], lp, 2 * (int)std::min<long>(max_clusters_, units),
+                                           s);
             } else if (l < n.L - 1)
                 launch_umma<M_FWD_TANH, false, false, true>(a, n.w_row_h[l], n.w_row_l[l], pp, grid, s);
             else
@@ -3630,7 +3677,22 @@ class DonEngine final : public Engine {
             // inputs at w = 256, seven at w = 128), with the column sums of delta_l as the
             // bias gradient
             const bool first = l == 1 && !n.gemm_first;
-            if (n.pair[l] && (!first || n.dx <= 4 || (pp.N == 128 && n.dx <= 7))) {
+            const bool last = l == n.L - 1 && n.pair_last;   // through the last layer (N = w, K = p)
+            if (last) {
+                LayerParams lp{};
+                lp.N = (int)n.R;
+                lp.W = pp.N;
+                lp.C = C_;
+                lp.ntiles = n.ntiles;
+                lp.dx = n.dx;
+                lp.err = err_;
+                lp.aux = pp.aux;
+                lp.db_part = pp.db_part;
+                lp.out = n.del[l]->as<h16>();
+                const long units = (long)C_ * ((n.ntiles + 1) / 2);
+                launch_layer_nk<L_BWD_TANH>(n.del_row[l + 1], n.w_atom_h[l], n.w_atom_l[l], lp,
+                                            2 * (int)std::min<long>(max_clusters_, units), s);
+            } else if (n.pair[l] && (!first || n.dx <= 4 || (pp.N == 128 && n.dx <= 7))) {
                 LayerParams lp{};
                 lp.N = (int)n.R;
                 lp.W = pp.N;

@@ -175,23 +175,32 @@ def algorithmic(prob, C):
 
 def other_workloads(hmc, torch, steps=3):
     """The other synthetic workloads, timed the same way (one trajectory to capture the
-    graph, then `steps` trajectories between CUDA events): grad-evals/s and acceptance."""
+    graph, one to size the timed run, then at least `steps` trajectories and about 0.3 s of
+    them between CUDA events): grad-evals/s and acceptance."""
     from oracle.ess import ess_chains
     out = {}
 
     def timed(name, sp, q0, eps, L, chains_total, prec_name, ess_traj=0, ess_fn=None):
         q0 = torch.from_numpy(q0) if isinstance(q0, np.ndarray) else q0
-        sp.sample(q0, eps, L, 1, seed=5, keep_samples=False)
-        torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sp.sample(q0, eps, L, 1, seed=5, keep_samples=False)   # captures the trajectory graph
+        torch.cuda.synchronize()
         a.record()
-        _, acc, dH, ql = sp.sample(q0, eps, L, steps, seed=5, first_traj=1, keep_samples=False)
+        sp.sample(q0, eps, L, 1, seed=5, keep_samples=False)
         b.record()
         torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / steps
+        # at least `steps` trajectories and about 0.3 s of them, so that short trajectories
+        # are not timed over a few milliseconds only
+        n = int(min(50, max(steps, 300.0 / max(a.elapsed_time(b), 1e-3))))
+        a.record()
+        _, acc, dH, ql = sp.sample(q0, eps, L, n, seed=5, first_traj=1, keep_samples=False)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / n
         eps_rec = float(eps) if np.ndim(eps) == 0 else {
             "per_problem": len(eps), "min": float(np.min(eps)), "median": float(np.median(eps)), "max": float(np.max(eps))}
         rec = {"dtype": prec_name, "chains": chains_total, "L": L, "eps": eps_rec, "ms_per_trajectory": ms,
+               "timed_trajectories": n,
                "grad_evals_per_s": chains_total * L / (ms / 1000.0),
                "accept_rate": float(acc.float().mean().item()),
                "abs_dH_median": float(np.nanmedian(np.abs(dH.cpu().numpy())))}

@@ -3186,6 +3186,9 @@ class DonEngine final : public Engine {
         int dev = 0;
         HMC_CK(cudaGetDevice(&dev));
         HMC_CK(cudaDeviceGetAttribute(&num_sms_, cudaDevAttrMultiProcessorCount, dev));
+        HMC_CK(cudaStreamCreateWithFlags(&s2_, cudaStreamNonBlocking));
+        HMC_CK(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
+        HMC_CK(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
         HMC_CK(cudaMalloc(&err_, sizeof(int)));
         HMC_CK(cudaMemset(err_, 0, sizeof(int)));
         setup_net(br_, p.branch, p.u, nu_);
@@ -3231,6 +3234,9 @@ class DonEngine final : public Engine {
     ~DonEngine() override
     {
         if (err_) cudaFree(err_);
+        if (ev_fork_) cudaEventDestroy(ev_fork_);
+        if (ev_join_) cudaEventDestroy(ev_join_);
+        if (s2_) cudaStreamDestroy(s2_);
     }
 
     ScatterPlan scatter_plan() override { return plan_; }
@@ -3306,9 +3312,14 @@ class DonEngine final : public Engine {
         const float *q = static_cast<const float *>(qv);
         float *g = static_cast<float *>(gv);
         if (!scattered) scatter(qv, s);
+        // branch and trunk are independent up to S and again after dB and dT: the trunk's
+        // work runs on the engine's second stream, joined back before S and before finalize
+        fork(s);
         forward(br_, s);
-        forward(tr_, s);
+        forward(tr_, s2_);
+        join(s);
         launch_s(b_col_, s);   // S = B T^T + b0, residual, energy partials and dS
+        fork(s);
         // dB = dS T and dT = dS^T B: the deltas of the two nets' linear output layers
         {
             Params pp = base();
@@ -3334,10 +3345,11 @@ class DonEngine final : public Engine {
             pp.out_b = ny_ * pl_;
             pp.db_part = tr_.colsum[tr_.L - 1]->as<float>();
             launch_umma<M_GEMM_BF16, true, true, false>(ds_atom_, br_.act_atom[br_.L], br_.act_atom[br_.L], pp,
-                                                         dim3(tr_.ntiles, 1, C_), s);
+                                                         dim3(tr_.ntiles, 1, C_), s2_);
         }
         backward(br_, s);
-        backward(tr_, s);
+        backward(tr_, s2_);
+        join(s);
         FinalArgs fa{};
         fa.k = (int)k_;
         fa.nsplit = nsplit_;
@@ -3370,6 +3382,18 @@ class DonEngine final : public Engine {
         Params pp{};
         pp.err = err_;
         return pp;
+    }
+
+    void fork(cudaStream_t s)
+    {
+        HMC_CK(cudaEventRecord(ev_fork_, s));
+        HMC_CK(cudaStreamWaitEvent(s2_, ev_fork_, 0));
+    }
+
+    void join(cudaStream_t s)
+    {
+        HMC_CK(cudaEventRecord(ev_join_, s2_));
+        HMC_CK(cudaStreamWaitEvent(s, ev_join_, 0));
     }
 
     void launch_s(const CUtensorMap &bmap, cudaStream_t s)
@@ -3869,6 +3893,8 @@ class DonEngine final : public Engine {
     CUtensorMap ds_row_, ds_atom_, b_col_, b_hi_e_, b_lo_e_;
     int es_ = 256, nut_e_ = 1, ntn_e_ = 1;
     int max_clusters_ = 0;             // pair-kernel CTA pairs resident at once (0: no pair layer)
+    cudaStream_t s2_ = nullptr;        // the trunk's stream inside an evaluation
+    cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
     DevBuf u_acc_;
     ScatterPlan plan_;
     std::string tuning_;

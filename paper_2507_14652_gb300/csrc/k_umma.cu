@@ -2275,6 +2275,9 @@ class UmmaEngine final : public Engine {
     ~UmmaEngine() override
     {
         if (err_) cudaFree(err_);
+        if (ev_fork_) cudaEventDestroy(ev_fork_);
+        if (ev_join_) cudaEventDestroy(ev_join_);
+        if (s2_) cudaStreamDestroy(s2_);
     }
 
     size_t bytes() const override { return 0; }
@@ -2632,13 +2635,30 @@ class UmmaEngine final : public Engine {
             else launch_layer<L_FWD_OUT>(A_row_[i], W_half_hi_[i], W_half_lo_[i], lp, ncta, s);
         }
         // reverse pass (W as a hi/lo pair, like the forward pass); the weight gradient of
-        // layer i runs first, while the delta written by the previous kernel is still in L2
+        // layer i reads the same delta and activations as the reverse kernel of layer i and
+        // writes nothing it reads: it runs beside it on the engine's second stream, which
+        // joins back before the finalize (on one stream while a per-kernel profile runs, so
+        // that each launch is timed alone)
+        if (!s2_) {
+            HMC_CK(cudaStreamCreateWithFlags(&s2_, cudaStreamNonBlocking));
+            HMC_CK(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
+            HMC_CK(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
+        }
+        const cudaStream_t sw = active_profiler() ? s : s2_;
         for (int i = L_ - 2; i >= 1; --i) {
-            dw_layer(i, s);
+            if (sw != s) {
+                HMC_CK(cudaEventRecord(ev_fork_, s));
+                HMC_CK(cudaStreamWaitEvent(sw, ev_fork_, 0));
+            }
+            dw_layer(i, sw);
             if (i <= nd.lmin) break;
             const LayerParams lp = layer_bwd_params(i);
             if (i > 1) launch_layer<L_BWD_TANH>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], lp, ncta, s);
             else launch_layer<L_BWD_FIRST>(D_row_[i + 1], W_atom_[i], W_atom_lo_[i], lp, ncta, s);
+        }
+        if (sw != s) {
+            HMC_CK(cudaEventRecord(ev_join_, sw));
+            HMC_CK(cudaStreamWaitEvent(s, ev_join_, 0));
         }
     }
 
@@ -2788,6 +2808,8 @@ class UmmaEngine final : public Engine {
     CUtensorMap D_row_[MAXL], D_atom_[MAXL], W_half_hi_[MAXL], W_half_lo_[MAXL];
     bool use_layer_ = false;
     int max_clusters_ = 1;
+    cudaStream_t s2_ = nullptr;   // the weight gradients' stream inside an evaluation
+    cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
     ScatterPlan plan_;
     std::string tuning_;
 };
@@ -3314,12 +3336,13 @@ class DonEngine final : public Engine {
         if (!scattered) scatter(qv, s);
         // branch and trunk are independent up to S and again after dB and dT: the trunk's
         // work runs on the engine's second stream, joined back before S and before finalize
-        fork(s);
+        const cudaStream_t st = active_profiler() ? s : s2_;   // one stream while profiling
+        fork(s, st);
         forward(br_, s);
-        forward(tr_, s2_);
-        join(s);
+        forward(tr_, st);
+        join(s, st);
         launch_s(b_col_, s);   // S = B T^T + b0, residual, energy partials and dS
-        fork(s);
+        fork(s, st);
         // dB = dS T and dT = dS^T B: the deltas of the two nets' linear output layers
         {
             Params pp = base();
@@ -3345,11 +3368,11 @@ class DonEngine final : public Engine {
             pp.out_b = ny_ * pl_;
             pp.db_part = tr_.colsum[tr_.L - 1]->as<float>();
             launch_umma<M_GEMM_BF16, true, true, false>(ds_atom_, br_.act_atom[br_.L], br_.act_atom[br_.L], pp,
-                                                         dim3(tr_.ntiles, 1, C_), s2_);
+                                                         dim3(tr_.ntiles, 1, C_), st);
         }
         backward(br_, s);
-        backward(tr_, s2_);
-        join(s);
+        backward(tr_, st);
+        join(s, st);
         FinalArgs fa{};
         fa.k = (int)k_;
         fa.nsplit = nsplit_;
@@ -3384,15 +3407,17 @@ class DonEngine final : public Engine {
         return pp;
     }
 
-    void fork(cudaStream_t s)
+    void fork(cudaStream_t s, cudaStream_t st)
     {
+        if (st == s) return;
         HMC_CK(cudaEventRecord(ev_fork_, s));
-        HMC_CK(cudaStreamWaitEvent(s2_, ev_fork_, 0));
+        HMC_CK(cudaStreamWaitEvent(st, ev_fork_, 0));
     }
 
-    void join(cudaStream_t s)
+    void join(cudaStream_t s, cudaStream_t st)
     {
-        HMC_CK(cudaEventRecord(ev_join_, s2_));
+        if (st == s) return;
+        HMC_CK(cudaEventRecord(ev_join_, st));
         HMC_CK(cudaStreamWaitEvent(s, ev_join_, 0));
     }
 

@@ -130,6 +130,7 @@ struct Params {
     const float *bout;                    // [b]
     const float *y;                       // targets [M]
     float inv_s2;
+    float oscale;                         // M_GEMM_BF16: factor on the products (a power of two)
     double *u_part;                       // [b][ntiles]
     float *dbout_part;                    // [b][ntiles]
     float *dwout_part;                    // [b][ntiles][N]
@@ -384,10 +385,9 @@ __device__ __forceinline__ void umma_body(const CUtensorMap &tmA, const CUtensor
                 for (int c0 = 0; c0 < BN; c0 += 32) {
                     float v[32];
                     tmem_ld32(taddr + c0, v);
-                    if (!valid) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = 0.0f;
-                    } else {
+                    for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * p.oscale : 0.0f;   // exact: a power of two
+                    if (valid) {
                         uint32_t pk[16];
 #pragma unroll
                         for (int j = 0; j < 16; ++j) pk[j] = pack_h16(v[2 * j], v[2 * j + 1]);
@@ -1827,6 +1827,7 @@ struct FinalArgs {
     const DbDesc *db;                // column-sum sources
     double half_inv_s2, inv_a2;
     float gscale;                    // data-term gradient scale (1 / sigma^2) / dscale
+    const float *escale;             // [k] a further power of two per entry, or null
 };
 
 // grid (nlight + ceil(nheavy / 8) + 1, C): blocks 0..nlight-1 gather one entry per
@@ -1893,6 +1894,7 @@ __device__ __forceinline__ void finalize_body(const FinalArgs &a, const float *q
         for (int t = lane; t < d.n; t += 32) s += __ldg(dp + (long)t * d.tstride);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (a.escale) s *= __ldg(a.escale + j);
         if (lane == 0) g[(long)b * a.k + j] = grad_entry(a, s, q[(long)b * a.k + j]);
         return;
     }
@@ -1919,6 +1921,7 @@ __device__ __forceinline__ void finalize_body(const FinalArgs &a, const float *q
         for (int u = 0; u < 16; ++u) s += v[u];
     }
     for (; t < n; ++t) s += __ldg(dp + (long)t * stride);
+    if (a.escale) s *= __ldg(a.escale + j);
     g[(long)b * a.k + j] = grad_entry(a, s, qj);
 }
 
@@ -3216,6 +3219,19 @@ class DonEngine final : public Engine {
         setup_net(br_, p.branch, p.u, nu_);
         setup_net(tr_, p.trunk, p.yq, ny_);
         pl_ = br_.p;
+        if (HMC_F16) {
+            // fp16 overflows at 65504, and dB = dS T adds n_y products and dT = dS^T B adds
+            // n_u of them: their tiles are stored times 2^-ceil(log2 n), which keeps every
+            // entry within max|dS| max|T| (max|dS| max|B|); the finalize scales the two nets'
+            // gradient sums back by the inverse powers of two, exactly
+            auto ceil_log2 = [](long n) {
+                int e = 0;
+                while ((1L << e) < n) ++e;
+                return e;
+            };
+            kb_ = (float)std::ldexp(1.0, -ceil_log2(ny_));
+            kt_ = (float)std::ldexp(1.0, -ceil_log2(nu_));
+        }
 
         // operator output: targets, dS, partials
         std::vector<float> tf(p.t.begin(), p.t.end());
@@ -3353,6 +3369,7 @@ class DonEngine final : public Engine {
             pp.ntiles = br_.ntiles;
             pp.out = br_.del[br_.L]->as<h16>();
             pp.out_b = nu_ * pl_;
+            pp.oscale = kb_;
             pp.db_part = br_.colsum[br_.L - 1]->as<float>();
             launch_umma<M_GEMM_BF16, false, true, false>(ds_row_, tr_.act_atom[tr_.L], tr_.act_atom[tr_.L], pp,
                                                           dim3(br_.ntiles, 1, C_), s);
@@ -3366,6 +3383,7 @@ class DonEngine final : public Engine {
             pp.ntiles = tr_.ntiles;
             pp.out = tr_.del[tr_.L]->as<h16>();
             pp.out_b = ny_ * pl_;
+            pp.oscale = kt_;
             pp.db_part = tr_.colsum[tr_.L - 1]->as<float>();
             launch_umma<M_GEMM_BF16, true, true, false>(ds_atom_, br_.act_atom[br_.L], br_.act_atom[br_.L], pp,
                                                          dim3(tr_.ntiles, 1, C_), st);
@@ -3386,6 +3404,7 @@ class DonEngine final : public Engine {
         fa.db = db_desc_.as<const DbDesc>();
         fa.half_inv_s2 = 0.5 / (p_.sigma * p_.sigma);
         fa.gscale = (float)(1.0 / (p_.sigma * p_.sigma) / delta_scale(p_.sigma));
+        fa.escale = HMC_F16 ? escale_.as<float>() : nullptr;
         fa.inv_a2 = 1.0 / (p_.alpha * p_.alpha);
         fa.heavy = heavy_.as<int>();
         fa.nheavy = nheavy_;
@@ -3778,6 +3797,7 @@ class DonEngine final : public Engine {
     void build_entries()
     {
         std::vector<int> kind(k_), desc(k_), off(k_), erow(k_, 0), ecol(k_, 0), bid(k_), boff(k_);
+        std::vector<float> esc(k_, 1.0f);   // the inverse of the output-delta factor of the entry's net
         std::vector<DbDesc> dbd;
         DonNet *nets[2] = {&br_, &tr_};
         int nb = 0;
@@ -3834,6 +3854,7 @@ class DonEngine final : public Engine {
                 continue;
             }
             const int t = id < p_.branch.base + p_.branch.P ? 0 : 1;
+            esc[j] = 1.0f / (t == 0 ? kb_ : kt_);
             DonNet &n = *nets[t];
             const NetDesc &nd = *n.nd;
             int l = 0;
@@ -3897,6 +3918,8 @@ class DonEngine final : public Engine {
         for (long j = 0; j < k_; ++j) epack[j] = (erow[j] << 16) | ecol[j];
         up(epack_, epack);
         up(sc_off_, boff);
+        alloc_t(escale_, sizeof(float) * std::max<size_t>(esc.size(), 1));
+        if (!esc.empty()) HMC_CK(cudaMemcpy(escale_.ptr, esc.data(), sizeof(float) * esc.size(), cudaMemcpyHostToDevice));
         std::vector<uint8_t> b8(bid.begin(), bid.end());
         alloc_t(sc_bid_, std::max<size_t>(b8.size(), 1));
         HMC_CK(cudaMemcpy(sc_bid_.ptr, b8.data(), b8.size(), cudaMemcpyHostToDevice));
@@ -3913,8 +3936,9 @@ class DonEngine final : public Engine {
     int *err_ = nullptr;
     DonNet br_, tr_;
     DevBuf yt_, ds_, u_part_, db0_part_, b0v_, gw_part_, db_desc_;
-    DevBuf kind_, desc_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_, heavy_;
+    DevBuf kind_, desc_, off_, erow_, ecol_, epack_, sc_off_, sc_bid_, heavy_, escale_;
     int nheavy_ = 0;
+    float kb_ = 1.0f, kt_ = 1.0f;      // factors on dB and dT (powers of two; 1 for bf16)
     CUtensorMap ds_row_, ds_atom_, b_col_, b_hi_e_, b_lo_e_;
     int es_ = 256, nut_e_ = 1, ntn_e_ = 1;
     int max_clusters_ = 0;             // pair-kernel CTA pairs resident at once (0: no pair layer)

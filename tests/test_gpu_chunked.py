@@ -55,6 +55,15 @@ def test_chunked_deeponet(prec):
     _check(prob, prec, 10 if prec != "bf16" else 30, 4 if prec != "bf16" else 3)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_chunked_wide_deeponet_on_the_pair_kernels(prec):
+    # width 256 and latent 128: the branch's hidden and last layers run on the CTA-pair
+    # kernels (forward, reverse with bias sums, the 256 -> 128 layer both ways), the trunk
+    # on its second stream, every pass drawing its row buffers from the shared arena
+    prob = W.small_deeponet(n_u=300, n_y=260, du=3, dy=2, width=256, latent=128, frac=0.1, chains=2, seed=77)
+    _check(prob, prec, 100, 3)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_chunked_deeponet_with_own_queries(prec):
     prob = W.small_deeponet_unaligned(chains=3)

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import workloads as W
-from _adapt import grad_ok_bf16, sampler_from
+from _adapt import grad_ok_bf16, rel_err, sampler_from
 
 torch = pytest.importorskip("torch")
 hmc = pytest.importorskip("paper_2507_14652_gb300")
@@ -94,3 +94,41 @@ def test_deeponet_fp16_deterministic():
     U1, g1 = s.energy_grad(q)
     U2, g2 = s.energy_grad(q)
     assert torch.equal(U1, U2) and torch.equal(g1, g2)
+
+
+def test_deeponet_fp16_trajectory_parity():
+    # a shared (q, p) integrated for L steps: positions and momenta follow the oracle's
+    prob = W.small_deeponet(n_u=160, n_y=96, du=10, width=128, latent=64, frac=0.2, chains=2, seed=46)
+    o = oracle.Oracle(prob)
+    s = sampler_from(prob, hmc.PREC_FP16)
+    rng = np.random.default_rng(9)
+    p0 = rng.standard_normal(prob.q0.shape).astype(np.float32).astype(np.float64)
+    eps, L = 2e-5, 10
+    q1, p1 = s.leapfrog(torch.from_numpy(prob.q0), torch.from_numpy(p0), eps, L)
+    q1, p1 = q1.cpu().double().numpy(), p1.cpu().double().numpy()
+    for c in range(prob.chains):
+        qr, pr, Ur, gr = o.leapfrog(prob.q0[c], p0[c], eps, L)
+        assert rel_err(q1[c] - prob.q0[c], qr - prob.q0[c]) < TOL, c
+        assert rel_err(p1[c] - p0[c], pr - p0[c]) < TOL, c
+
+
+def test_deeponet_fp16_sampler_energy_and_resume():
+    # the Metropolis energy from the hi/lo forward pass, dH against the oracle's, and the
+    # same trajectories in one call or two
+    prob = W.small_deeponet(n_u=150, n_y=90, du=12, width=64, latent=64, frac=0.3, chains=3, seed=41)
+    s = sampler_from(prob, hmc.PREC_FP16)
+    o = oracle.Oracle(prob)
+    q0 = torch.from_numpy(prob.q0)
+    Um = s.metropolis_energy(q0).cpu().numpy()
+    Ur, _ = o.energy_grad_batch(prob.q0)
+    assert np.all(np.abs(Um - Ur) <= 1e-4 * np.abs(Ur)), (Um, Ur)
+    eps, L = 2e-5, 6
+    _, _, dH, _ = s.sample(q0, eps, L, 1, seed=7)
+    _, _, dHr, _ = o.sample(prob.q0, eps, L, 1, seed=7)
+    dH = dH.cpu().numpy()
+    assert np.all(np.abs(dH - dHr) <= 0.05 + 0.05 * np.abs(dHr)), (dH, dHr)
+    S, acc, dH4, ql = s.sample(q0, eps, L, 4, seed=3)
+    S1, _, dH1, q1 = s.sample(q0, eps, L, 2, seed=3)
+    S2, _, dH2, q2 = s.sample(q1, eps, L, 2, seed=3, first_traj=2)
+    assert torch.equal(torch.cat([S1, S2]), S) and torch.equal(torch.cat([dH1, dH2]), dH4)
+    assert torch.equal(q2, ql)

@@ -8,7 +8,7 @@
 * Subsets confined to one part of the network: the output layer only (the adjoint stops
   at once), the first layer only (it runs through every layer), the biases only.
 * Data sizes at and below the 128-row tile: N = 1, 127, 128, 129, 255, 257, one chain.
-Tolerances as for the other parity tests: FP64 1e-10, FP32 1e-5, BF16 2e-2.
+Tolerances as for the other parity tests: FP64 1e-10, FP32 1e-5, BF16 2e-2, FP16 5e-3.
 """
 import dataclasses
 
@@ -23,7 +23,8 @@ torch = pytest.importorskip("torch")
 hmc = pytest.importorskip("paper_2507_14652_gb300")
 pytestmark = pytest.mark.gpu
 
-PRECS = [hmc.PREC_FP64, hmc.PREC_FP32, hmc.PREC_BF16]
+PRECS = [hmc.PREC_FP64, hmc.PREC_FP32, hmc.PREC_BF16, hmc.PREC_FP16]
+TOL16 = {hmc.PREC_BF16: 2e-2, hmc.PREC_FP16: 5e-3}
 
 
 def _f32(a):
@@ -63,9 +64,9 @@ def _check(prob, prec, q=None):
     U, g = U.cpu().numpy(), g.cpu().double().numpy()
     Ur, gr = o.energy_grad_batch(q)
     for c in range(prob.chains):
-        if prec == hmc.PREC_BF16:
-            assert abs(U[c] - Ur[c]) <= 2e-2 * abs(Ur[c]), (c, U[c], Ur[c])
-            ok, re, rinf = grad_ok_bf16(g[c], gr[c])
+        if prec in TOL16:
+            assert abs(U[c] - Ur[c]) <= TOL16[prec] * abs(Ur[c]), (c, U[c], Ur[c])
+            ok, re, rinf = grad_ok_bf16(g[c], gr[c], TOL16[prec])
         else:
             tol = 1e-10 if prec == hmc.PREC_FP64 else 1e-5
             assert abs(U[c] - Ur[c]) <= tol * abs(Ur[c]), (c, U[c], Ur[c])
@@ -153,18 +154,19 @@ def test_subset_in_one_part_cuda_cores(which, prec):
     _check(_with_mask(prob, _layer_mask(prob, which)), prec)
 
 
+@pytest.mark.parametrize("prec", [hmc.PREC_BF16, hmc.PREC_FP16])
 @pytest.mark.parametrize("which", ["output", "first", "bias"])
 @pytest.mark.parametrize("widths", [(2, 256, 256, 256, 1), (2, 128, 128, 1)])
-def test_subset_in_one_part_tensor_cores(which, widths):
+def test_subset_in_one_part_tensor_cores(which, widths, prec):
     prob = W.small_mlp(n=300, widths=widths, frac=0.05, chains=2, seed=43)
-    _check(_with_mask(prob, _layer_mask(prob, which), jitter=0.02), hmc.PREC_BF16)
+    _check(_with_mask(prob, _layer_mask(prob, which), jitter=0.02), prec)
 
 
 # ---- row counts around the 128-row tile ---------------------------------------------
 
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 255, 257])
 @pytest.mark.parametrize("prec,widths", [(hmc.PREC_FP32, (2, 48, 40, 1)), (hmc.PREC_BF16, (2, 256, 256, 256, 1)),
-                                         (hmc.PREC_BF16, (2, 128, 128, 1))])
+                                         (hmc.PREC_BF16, (2, 128, 128, 1)), (hmc.PREC_FP16, (2, 256, 256, 256, 1))])
 def test_row_counts_around_a_tile(n, prec, widths):
     prob = W.small_mlp(n=n, widths=widths, frac=0.1, chains=1, seed=44)
     _check(prob, prec)
@@ -182,7 +184,7 @@ def test_float32_training_data_is_the_float64_data(which, prec):
     else:
         prob = W.small_deeponet(chains=2)
         arrays = {"u": prob.u, "yq": prob.yq, "t": prob.t}
-    if prec == hmc.PREC_BF16 and which == "deeponet":
+    if prec in TOL16 and which == "deeponet":
         prob = W.small_deeponet(n_u=40, n_y=130, du=8, width=64, latent=64, frac=0.1, chains=2, seed=46)
         arrays = {"u": prob.u, "yq": prob.yq, "t": prob.t}
     q = torch.from_numpy(prob.q0)

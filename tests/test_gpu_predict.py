@@ -105,3 +105,20 @@ def test_predict_full_size_cone_deeponet_several_batches():
     mr, sr = oracle.Oracle(sub).predict(Q)
     _check(m.cpu().numpy()[np.ix_(iu, iy)], sd.cpu().numpy()[np.ix_(iu, iy)], mr, sr, 2e-5, 2e-5)
     assert np.isfinite(rel)
+
+
+@pytest.mark.parametrize("prec", [hmc.PREC_BF16, hmc.PREC_FP16])
+@pytest.mark.parametrize("which", ["mlp", "deeponet"])
+def test_predict_of_a_16bit_handle_is_the_fp32_one(which, prec):
+    # a BF16 or FP16 handle predicts in float from its network, frozen vector and subset,
+    # as an FP32 handle of the same problem does: the same numbers, bit for bit
+    if which == "mlp":
+        prob = W.small_mlp(n=300, widths=(2, 128, 128, 1), frac=0.1, chains=1, seed=93)
+        kw = dict(x=prob.x[:111], y=prob.y[:111])
+    else:
+        prob = W.small_deeponet(n_u=40, n_y=130, du=8, width=64, latent=64, frac=0.1, chains=1, seed=94)
+        kw = dict(u=prob.u[:13], yq=prob.yq[:50], t=prob.t[:13, :50])
+    Q = torch.from_numpy(_samples(prob, 9, 6))
+    m16, s16, r16 = sampler_from(prob, prec, chains=1).predict(Q, **kw)
+    m32, s32, r32 = sampler_from(prob, hmc.PREC_FP32, chains=1).predict(Q, **kw)
+    assert torch.equal(m16, m32) and torch.equal(s16, s32) and r16 == r32

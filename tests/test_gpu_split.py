@@ -4,7 +4,8 @@ oracle's split integrator, through the C ABI.
 The GPU fuses every kick with the drift after it and the last kick of a step with
 the first of the next; the oracle applies the sweeps one sub-step at a time.  The
 tolerances are those of the unsplit tests: 1e-10 (FP64), FP32 rounding (1e-5 on
-the energy and gradient, 1e-4 on a trajectory's displacement), 2e-2 for BF16.
+the energy and gradient, 1e-4 on a trajectory's displacement), 2e-2 for BF16 and
+5e-3 for FP16.
 """
 import numpy as np
 import pytest
@@ -73,7 +74,9 @@ def test_split_leapfrog_parity_fp64(which, M):
 @pytest.mark.parametrize("which,prec,tol,eps", [("mlp", hmc.PREC_FP32, 1e-4, 3e-4),
                                                 ("deeponet", hmc.PREC_FP32, 1e-4, 3e-4),
                                                 ("wide_mlp", hmc.PREC_BF16, 2e-2, 2e-5),
-                                                ("wide_deeponet", hmc.PREC_BF16, 2e-2, 2e-5)])
+                                                ("wide_deeponet", hmc.PREC_BF16, 2e-2, 2e-5),
+                                                ("wide_mlp", hmc.PREC_FP16, 5e-3, 2e-5),
+                                                ("wide_deeponet", hmc.PREC_FP16, 5e-3, 2e-5)])
 def test_split_leapfrog_parity_reduced_precision(which, prec, tol, eps):
     prob = _problem(which)
     o = oracle.Oracle(prob)
@@ -106,11 +109,12 @@ def test_split_sample_parity_fp64(which):
     assert np.max(np.abs(S - Sr)) <= 1e-9 * max(1.0, np.max(np.abs(Sr)))
 
 
+@pytest.mark.parametrize("prec", [hmc.PREC_BF16, hmc.PREC_FP16])
 @pytest.mark.parametrize("which", ["wide_mlp", "wide_deeponet"])
-def test_split_bf16_sampler_energy_and_resume(which):
+def test_split_16bit_sampler_energy_and_resume(which, prec):
     prob = _problem(which)
     M, eps, L = 3, 2e-5, 4
-    s = sampler_from(prob, hmc.PREC_BF16, n_splits=M)
+    s = sampler_from(prob, prec, n_splits=M)
     q0 = torch.from_numpy(prob.q0)
     # the Metropolis energy of a split handle is the sum of its batches' accurate energies
     Um = s.metropolis_energy(q0).cpu().numpy()

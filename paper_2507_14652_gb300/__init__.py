@@ -513,8 +513,12 @@ class BatchSampler(Sampler):
     """Several independent problems behind one handle (hmc_create_batch)."""
 
     def __init__(self, problems, chains, prec, stream=None, grouped=True):
-        """grouped: problems of one tensor-core kernel shape share launches (the default);
-        False launches every problem's kernels on their own (for comparison)."""
+        """problems: one tuple per problem, (widths, x, y, mask, frozen, prior_sigma,
+        noise_sigma) for an MLP, or ("deeponet", branch_widths, trunk_widths, u, yq, t, mask,
+        frozen, prior_sigma, noise_sigma, out_bias) for a DeepONet whose n_y query points
+        are shared by its input functions.  grouped: problems of one tensor-core kernel
+        shape share launches (the default); False launches every problem's kernels on
+        their own (for comparison)."""
         n = len(problems)
         specs = (NetSpec * n)()
         datas = (Data * n)()
@@ -524,15 +528,30 @@ class BatchSampler(Sampler):
         frozens = (ct.c_void_p * n)()
         keep = []
         for i, pr in enumerate(problems):
-            widths, x, y, mask, frozen, alpha, sigma = pr
-            specs[i].kind = NET_MLP
-            specs[i].net = mlp_spec(widths)
             specs[i].prec = prec
-            x, y = _f64(x), _f64(y)
+            if isinstance(pr[0], str):
+                kind, branch, trunk, u, yq, t, mask, frozen, alpha, sigma, out_bias = pr
+                if kind != "deeponet":
+                    raise ValueError("unknown problem kind %r" % (kind,))
+                specs[i].kind = NET_DEEPONET
+                specs[i].branch, specs[i].trunk = mlp_spec(branch), mlp_spec(trunk)
+                specs[i].deeponet_out_bias = 1 if out_bias else 0
+                u, yq, t = _f64(u), _f64(yq), _f64(t)
+                keep += [u, yq, t]
+                d = datas[i]
+                d.u, d.n_u, d.du = _ptr(u), u.shape[0], u.shape[1]
+                d.yq, d.n_y, d.dy = _ptr(yq), yq.shape[0], yq.shape[1]
+                d.t = _ptr(t)
+            else:
+                widths, x, y, mask, frozen, alpha, sigma = pr
+                specs[i].kind = NET_MLP
+                specs[i].net = mlp_spec(widths)
+                x, y = _f64(x), _f64(y)
+                keep += [x, y]
+                datas[i].x, datas[i].n, datas[i].dx, datas[i].y = _ptr(x), x.shape[0], x.shape[1], _ptr(y)
             m = np.ascontiguousarray(mask, dtype=np.uint8)
             f = _f64(np.asarray(frozen))
-            keep += [x, y, m, f]
-            datas[i].x, datas[i].n, datas[i].dx, datas[i].y = _ptr(x), x.shape[0], x.shape[1], _ptr(y)
+            keep += [m, f]
             alphas[i], sigmas[i] = alpha, sigma
             masks[i], frozens[i] = _ptr(m), _ptr(f)
         import torch

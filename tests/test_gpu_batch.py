@@ -127,3 +127,60 @@ def test_batch_sample_parity_fp64():
         assert np.allclose(dH[:, i * C:(i + 1) * C], dHr, rtol=1e-6, atol=1e-7), i
         Si = np.stack([_split(S[t], probs)[i] for t in range(n)])
         assert np.max(np.abs(Si - Sr)) <= 1e-9 * max(1.0, np.max(np.abs(Sr))), i
+
+
+def _mixed_kinds(chains=2):
+    """Two MLPs and two DeepONets (branch and trunk widths 64 and 128, ragged sizes)."""
+    return [W.small_mlp(n=333, widths=(4, 64, 64, 1), frac=0.2, chains=chains, seed=61),
+            W.small_deeponet(n_u=40, n_y=130, du=8, width=64, latent=64, frac=0.1, chains=chains, seed=62),
+            W.small_mlp(n=517, widths=(3, 128, 128, 128, 1), frac=0.1, chains=chains, seed=63),
+            W.small_deeponet(n_u=150, n_y=90, du=5, width=128, latent=64, frac=0.2, chains=chains, seed=64,
+                             out_bias=False)]
+
+
+def _tuple(p):
+    if p.branch is not None:
+        return ("deeponet", p.branch.widths, p.trunk.widths, p.u, p.yq, p.t, p.mask, p.frozen, p.prior_sigma,
+                p.noise_sigma, p.out_bias)
+    return (p.net.widths, p.x, p.y, p.mask, p.frozen, p.prior_sigma, p.noise_sigma)
+
+
+@pytest.mark.parametrize("prec", [hmc.PREC_FP64, hmc.PREC_FP32, hmc.PREC_BF16, hmc.PREC_FP16])
+def test_batch_mixes_mlps_and_deeponets(prec):
+    # a batch may hold DeepONets beside MLPs: each problem's U and grad U are its own
+    probs = _mixed_kinds()
+    s = hmc.BatchSampler([_tuple(p) for p in probs], 2, prec)
+    assert s.n_problems == 4 and s.k == sum(p.q0.shape[1] for p in probs)
+    qs = _states(probs)
+    U, g = s.energy_grad(torch.from_numpy(np.concatenate([q.reshape(-1) for q in qs])))
+    U, gs = U.cpu().numpy(), _split(g.cpu().double().numpy(), probs)
+    tol = {hmc.PREC_FP64: 1e-10, hmc.PREC_FP32: 1e-5, hmc.PREC_BF16: 2e-2, hmc.PREC_FP16: 5e-3}[prec]
+    for i, (p, q) in enumerate(zip(probs, qs)):
+        Ur, gr = oracle.Oracle(p).energy_grad_batch(q)
+        for c in range(2):
+            assert abs(U[i * 2 + c] - Ur[c]) <= tol * abs(Ur[c]), (i, c, U[i * 2 + c], Ur[c])
+            if prec in (hmc.PREC_FP64, hmc.PREC_FP32):
+                ok, re, comp = grad_ok(gs[i][c], gr[c], tol)
+            else:
+                ok, re, comp = grad_ok_bf16(gs[i][c], gr[c], tol)
+            assert ok, (i, c, re, comp)
+    s.close()
+
+
+def test_batch_with_deeponets_sample_parity_fp64():
+    # problem i draws from Philox stream i, DeepONet or MLP
+    probs = _mixed_kinds()
+    s = hmc.BatchSampler([_tuple(p) for p in probs], 2, hmc.PREC_FP64)
+    n, eps, L, seed = 3, 2e-4, 4, 13
+    q0 = np.concatenate([p.q0.reshape(-1) for p in probs])
+    S, acc, dH, _ = s.sample(torch.from_numpy(q0), eps, L, n, seed=seed)
+    S, acc, dH = S.cpu().numpy(), acc.cpu().numpy(), dH.cpu().numpy()
+    for i, p in enumerate(probs):
+        Sr, accr, dHr, _ = oracle.Oracle(p).sample(p.q0, eps, L, n, seed=seed, problem=i)
+        lu = np.array([[oracle.log(oracle.mh_uniform(seed, c, t, problem=i)) for c in range(2)] for t in range(n)])
+        clear = np.abs(lu + dHr) > 1e-8 * (1 + np.abs(dHr))
+        assert np.array_equal(acc[:, 2 * i:2 * i + 2][clear], accr[clear]), i
+        assert np.allclose(dH[:, 2 * i:2 * i + 2], dHr, rtol=1e-6, atol=1e-7), i
+        Si = np.stack([_split(S[t], probs)[i] for t in range(n)])
+        assert np.max(np.abs(Si - Sr)) <= 1e-9 * max(1.0, np.max(np.abs(Sr))), i
+    s.close()

@@ -373,9 +373,8 @@ HMC_API hmc_status hmc_destroy(hmc_handle h);
  * overlap on the GPU race; serialise them.  subset_idx is checked on the device:
  * an entry outside [0, P) or not above the one before it is never used to
  * address memory, and every U (and grad) of that call is set to NaN instead.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.
+ * The first call on a device also looks up the array's device address (a host-side
+ * query of the driver, once per device, with that device current).
  */
 HMC_API hmc_status hmc_energy_grad_noalloc(const hmc_mlp_spec *net, const float *x, const float *y, long n,
                                            const float *frozen, const int *subset_idx, long k,

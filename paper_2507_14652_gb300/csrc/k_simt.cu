@@ -27,6 +27,8 @@ __global__ void __launch_bounds__(256) k_residual(const T *f, long f_b, const T 
                                                   const T *slope, double inv_s2, T *delta,
                                                   double *part_r2, double *part_d, int nparts)
 {
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
     __shared__ double sm[8];
     const int b = blockIdx.y;
     double r2 = 0.0, ds = 0.0;
@@ -51,6 +53,8 @@ __global__ void __launch_bounds__(256) k_residual(const T *f, long f_b, const T 
 template <typename T>
 __global__ void k_scatter(const T *q, const int *idx, long k, T *theta, long P)
 {
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
     const int b = blockIdx.y;
     for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < k; j += (long)gridDim.x * blockDim.x)
         theta[(long)b * P + idx[j]] = q[(long)b * k + j];
@@ -63,6 +67,8 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part_r2, const d
                                                   const T *G, long P, long b0_off, double inv_a2,
                                                   double *U, T *g)
 {
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
     __shared__ double sm[8];
     __shared__ double s_db0;
     const int b = blockIdx.x;
@@ -95,6 +101,8 @@ __global__ void __launch_bounds__(256) k_finalize(const double *part_r2, const d
 template <typename T>
 __global__ void k_rowdot(const T *B, const T *Tm, long n_u, long nq, int p, const T *b0, long P, T *S)
 {
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
     const int c = blockIdx.y;
     const long n = n_u * nq;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -110,6 +118,8 @@ __global__ void k_rowdot(const T *B, const T *Tm, long n_u, long nq, int p, cons
 template <typename T>
 __global__ void k_rowdot_dB(const T *dS, const T *Tm, long n_u, long nq, int p, const T *sl, T *dB)
 {
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
     const int c = blockIdx.y;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n_u * p; i += (long)gridDim.x * blockDim.x) {
         const long j = i / p;
@@ -127,6 +137,8 @@ __global__ void k_rowdot_dB(const T *dS, const T *Tm, long n_u, long nq, int p, 
 template <typename T>
 __global__ void k_rowdot_dT(const T *dS, const T *B, long n_u, long nq, int p, const T *sl, T *dT)
 {
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
     const int c = blockIdx.y;
     const long n = n_u * nq * p;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -229,7 +241,8 @@ template <typename T> class SimtEngine final : public Engine {
     {
         if (p_.k <= 0) return;
         dim3 grid((unsigned)std::min<long>((p_.k + 255) / 256, 1024), C_);
-        k_scatter<T><<<grid, 256, 0, s>>>(static_cast<const T *>(qv), idx_.as<int>(), p_.k, theta_.as<T>(), p_.P);
+        launch_pdl(k_scatter<T>, grid, dim3(256), 0, s, static_cast<const T *>(qv), (const int *)idx_.as<int>(), p_.k,
+                   theta_.as<T>(), p_.P);
         HMC_LAUNCH_CK();
     }
 
@@ -259,8 +272,8 @@ template <typename T> class SimtEngine final : public Engine {
             T *S = S_.as<T>();
             const dim3 ua_grid((unsigned)std::min<long>((p_.n_u * p_.n_y * lat + 255) / 256, 4096), C_);
             if (ua) {   // S_jk = <B_j, T_jk> + b0
-                k_rowdot<T><<<ua_grid, 256, 0, s>>>(Bm, Tm, p_.n_u, p_.n_y, lat,
-                                                    p_.out_bias ? theta + p_.b0_off : nullptr, P, S);
+                launch_pdl(k_rowdot<T>, ua_grid, dim3(256), 0, s, (const T *)Bm, (const T *)Tm, p_.n_u, p_.n_y, lat,
+                           (const T *)(p_.out_bias ? theta + p_.b0_off : nullptr), P, S);
                 HMC_LAUNCH_CK();
             } else {   // S = B T^T + b0
                 GemmArgs<T> ga{(int)p_.n_u, (int)p_.n_y, lat, Bm, lat, 1, p_.n_u * lat,
@@ -272,17 +285,15 @@ template <typename T> class SimtEngine final : public Engine {
             residual(S, p_.n_u * p_.n_y, t_.as<T>(), nullptr, inv_s2, S, true, s);
             if (ua && bn.any_sampled && g) {   // dB_j = sum_k dS_jk T_jk (times the branch output slope)
                 const bool id = bn.act[bn.L - 1] == HMC_ACT_IDENTITY;
-                k_rowdot_dB<T><<<ua_grid, 256, 0, s>>>(S, Tm, p_.n_u, p_.n_y, lat,
-                                                       id ? nullptr : brb_.slope[bn.L]->template as<T>(),
-                                                       dB_.as<T>());
+                launch_pdl(k_rowdot_dB<T>, ua_grid, dim3(256), 0, s, (const T *)S, (const T *)Tm, p_.n_u, p_.n_y, lat,
+                           (const T *)(id ? nullptr : brb_.slope[bn.L]->template as<T>()), dB_.as<T>());
                 HMC_LAUNCH_CK();
                 backward(bn, u_.as<T>(), 0, p_.n_u, brb_, dB_.as<T>(), s);
             }
             if (ua && tn.any_sampled && g) {   // dT_jk = dS_jk B_j (times the trunk output slope)
                 const bool id = tn.act[tn.L - 1] == HMC_ACT_IDENTITY;
-                k_rowdot_dT<T><<<ua_grid, 256, 0, s>>>(S, Bm, p_.n_u, p_.n_y, lat,
-                                                       id ? nullptr : trb_.slope[tn.L]->template as<T>(),
-                                                       dT_.as<T>());
+                launch_pdl(k_rowdot_dT<T>, ua_grid, dim3(256), 0, s, (const T *)S, (const T *)Bm, p_.n_u, p_.n_y, lat,
+                           (const T *)(id ? nullptr : trb_.slope[tn.L]->template as<T>()), dT_.as<T>());
                 HMC_LAUNCH_CK();
                 backward(tn, yq_.as<T>(), 0, nt_, trb_, dT_.as<T>(), s);
             }
@@ -307,10 +318,10 @@ template <typename T> class SimtEngine final : public Engine {
         }
         ProfScope ps("simt_finalize", s);
         const bool don = p_.kind != HMC_NET_MLP;
-        k_finalize<T><<<C_, 256, 0, s>>>(part_r2_.as<double>(), don ? part_d_.as<double>() : nullptr,
-                                         nparts_, 0.5 * inv_s2, q, k, idx_.as<int>(), G_.as<T>(), P,
-                                         don && p_.out_bias ? p_.b0_off : -1,
-                                         1.0 / (p_.alpha * p_.alpha), U, g);
+        launch_pdl(k_finalize<T>, dim3(C_), dim3(256), 0, s, (const double *)part_r2_.as<double>(),
+                   (const double *)(don ? part_d_.as<double>() : nullptr), nparts_, 0.5 * inv_s2, q, k,
+                   (const int *)idx_.as<int>(), (const T *)G_.as<T>(), P, (long)(don && p_.out_bias ? p_.b0_off : -1),
+                   1.0 / (p_.alpha * p_.alpha), U, g);
         HMC_LAUNCH_CK();
     }
 
@@ -374,15 +385,18 @@ template <typename T> class SimtEngine final : public Engine {
             const int wi = nd.w[l], wo = nd.w[l + 1];
             const T *ap = l == 0 ? in : nb.act[l]->template as<T>();
             const long ap_b = l == 0 ? in_b : rows * wi;
-            {   // dW_l = delta_l^T A_{l-1}
+            bool db_done;
+            {   // dW_l = delta_l^T A_{l-1} (and db_l = delta_l^T 1 where the kernel takes it)
                 GemmArgs<T> ga{wo, wi, (int)rows, d, 1, wo, rows * wo, ap, wi, 1, ap_b};
                 EpiArgs<T> ea{EPI_STORE, G + nd.woff[l], wi, 1, P, nullptr, 0, 0, 0, nullptr};
-                launch_gemm(ga, ea, C_, s, ws_.template as<float>(), ws_floats_);
+                db_done = launch_wgrad(ga, ea, C_, s, ws_.template as<float>(), ws_floats_,
+                                       nd.boff[l] >= 0 ? G + nd.boff[l] : nullptr, P) &&
+                          nd.boff[l] >= 0;
             }
-            if (nd.boff[l] >= 0) {
+            if (nd.boff[l] >= 0 && !db_done) {
                 dim3 grid((wo + 31) / 32, C_);
                 ProfScope ps("simt_colsum", s);
-                k_colsum<T><<<grid, dim3(32, 8), 0, s>>>(d, rows, wo, rows * wo, G + nd.boff[l], P);
+                launch_pdl(k_colsum<T>, grid, dim3(32, 8), 0, s, (const T *)d, rows, wo, rows * wo, G + nd.boff[l], P);
                 HMC_LAUNCH_CK();
             }
             if (l > nd.lmin) {   // delta_{l-1} = (delta_l W_l) * act'(Z_{l-1})
@@ -404,8 +418,8 @@ template <typename T> class SimtEngine final : public Engine {
     {
         dim3 grid(nparts_, C_);
         ProfScope ps("simt_residual", s);
-        k_residual<T><<<grid, 256, 0, s>>>(f, n_el, y, n_el, slope, inv_s2, delta, part_r2_.as<double>(),
-                                           want_d ? part_d_.as<double>() : nullptr, nparts_);
+        launch_pdl(k_residual<T>, grid, dim3(256), 0, s, f, n_el, y, n_el, slope, inv_s2, delta, part_r2_.as<double>(),
+                   want_d ? part_d_.as<double>() : nullptr, nparts_);
         HMC_LAUNCH_CK();
     }
 

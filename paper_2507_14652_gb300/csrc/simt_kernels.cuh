@@ -35,6 +35,25 @@ __device__ __forceinline__ void act_eval(int act, float z, float &a, float &s)
     else { a = z; s = 1.0f; }
 }
 
+// The epilogue of output (m, n) of batch b: activation (and its slope), a scale, or a store.
+template <typename T>
+__device__ __forceinline__ void gemm_epilogue(const EpiArgs<T> &e, int b, long m, long n, T v)
+{
+    const long o = (long)b * e.o_b + m * e.o_m + n * e.o_n;
+    if (e.mode == EPI_ACT) {
+        const T z = v + (e.bias ? e.bias[(long)b * e.bias_b + n * e.bias_n] : T(0));
+        T a, sl;
+        act_eval(e.act, z, a, sl);
+        e.out[o] = a;
+        if (e.slope) e.slope[o] = sl;
+    } else if (e.mode == EPI_SCALE) {
+        const long so = (long)b * (e.slope_b < 0 ? e.o_b : e.slope_b) + m * e.o_m + n * e.o_n;
+        e.out[o] = v * e.slope[so];
+    } else {
+        e.out[o] = v;
+    }
+}
+
 // FP64: C[b](m, n) = sum_k A[b](m, k) B[b](k, n), one output per thread on 16 x 16 tiles.
 // GB300's FP64 units are few, so work on padding costs real time: a 16 x 16 tile wastes
 // little on the small shapes the FP64 engine serves (a 20 x 20 weight gradient filled 10%
@@ -42,6 +61,8 @@ __device__ __forceinline__ void act_eval(int act, float z, float &a, float &s)
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm16(GemmArgs<T> g, EpiArgs<T> e)
 {
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
     __shared__ T As[16][17];
     __shared__ T Bs[16][17];
     const int b = blockIdx.z;
@@ -66,19 +87,43 @@ __global__ void __launch_bounds__(256) k_gemm16(GemmArgs<T> g, EpiArgs<T> e)
     }
     const long m = m0 + ty, n = n0 + tx;
     if (m >= g.M || n >= g.N) return;
-    const long o = (long)b * e.o_b + m * e.o_m + n * e.o_n;
-    if (e.mode == EPI_ACT) {
-        T z = acc + (e.bias ? e.bias[(long)b * e.bias_b + n * e.bias_n] : T(0));
-        T a, sl;
-        act_eval(e.act, z, a, sl);
-        e.out[o] = a;
-        if (e.slope) e.slope[o] = sl;
-    } else if (e.mode == EPI_SCALE) {
-        const long so = (long)b * (e.slope_b < 0 ? e.o_b : e.slope_b) + m * e.o_m + n * e.o_n;
-        e.out[o] = acc * e.slope[so];
-    } else {
-        e.out[o] = acc;
+    gemm_epilogue(e, b, m, n, acc);
+}
+
+// FP64 reductions with few outputs and a long K (a small layer's weight gradient, whose K
+// is the data rows): one warp per output, its lanes taking every 32nd k with two
+// accumulators, then a fixed butterfly, so the result is reproducible.  On 16 x 16 tiles
+// such a GEMM gets a handful of CTAs, each thread walking all of K, while most of GB300's
+// FP64 units (a few per SM) stay idle.
+// With rsum set, each row m also gets an extra output n = N whose B column is all ones,
+// rsum[b rsum_b + m] = sum_k A(m, k) (a layer's bias gradient beside its weight gradient).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_dot(GemmArgs<T> g, EpiArgs<T> e, T *rsum, long rsum_b)
+{
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
+    const int b = blockIdx.y, lane = threadIdx.x % 32;
+    const int nc = g.N + (rsum ? 1 : 0);   // outputs per row
+    const long o = (long)blockIdx.x * 8 + threadIdx.x / 32;
+    if (o >= (long)g.M * nc) return;   // the warp leaves together
+    const long m = o / nc, n = o % nc;
+    const bool ones = n == g.N;
+    const T *A = g.A + (long)b * g.a_b + m * g.a_m;
+    const T *B = g.B + (long)b * g.b_b + (ones ? 0 : n * g.b_n);
+    auto bv = [&](int k) { return ones ? T(1) : B[(long)k * g.b_k]; };
+    T acc0 = T(0), acc1 = T(0);
+    int k = lane;
+    for (; k + 32 < g.K; k += 64) {
+        acc0 += A[(long)k * g.a_k] * bv(k);
+        acc1 += A[(long)(k + 32) * g.a_k] * bv(k + 32);
     }
+    if (k < g.K) acc0 += A[(long)k * g.a_k] * bv(k);
+    T acc = acc0 + acc1;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane != 0) return;
+    if (ones) rsum[(long)b * rsum_b + m] = acc;
+    else gemm_epilogue(e, b, m, n, acc);
 }
 
 // FP32: C[b](m, n) = sum_k A[b](m, k) B[b](k, n) on 128 x 128 tiles, 16-deep K stages
@@ -89,26 +134,12 @@ __global__ void __launch_bounds__(256) k_gemm16(GemmArgs<T> g, EpiArgs<T> e)
 // the epilogue, so the result is the same for any batch size.
 constexpr int GB_M = 128, GB_N = 128, GB_K = 16, GB_PAD = 4;
 
-__device__ __forceinline__ void gemm_epilogue(const EpiArgs<float> &e, int b, long m, long n, float v)
-{
-    const long o = (long)b * e.o_b + m * e.o_m + n * e.o_n;
-    if (e.mode == EPI_ACT) {
-        const float z = v + (e.bias ? e.bias[(long)b * e.bias_b + n * e.bias_n] : 0.0f);
-        float a, sl;
-        act_eval(e.act, z, a, sl);
-        e.out[o] = a;
-        if (e.slope) e.slope[o] = sl;
-    } else if (e.mode == EPI_SCALE) {
-        const long so = (long)b * (e.slope_b < 0 ? e.o_b : e.slope_b) + m * e.o_m + n * e.o_n;
-        e.out[o] = v * e.slope[so];
-    } else {
-        e.out[o] = v;
-    }
-}
 
 __global__ void __launch_bounds__(256) k_gemm_f32(GemmArgs<float> g, EpiArgs<float> e, float *ws, int splits,
                                                    int kchunk)
 {
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
     __shared__ __align__(16) float As[2][GB_K][GB_M + GB_PAD];
     __shared__ __align__(16) float Bs[2][GB_K][GB_N + GB_PAD];
     const int b = blockIdx.z / splits, sp = blockIdx.z % splits;
@@ -192,6 +223,8 @@ __global__ void __launch_bounds__(256) k_gemm_f32(GemmArgs<float> g, EpiArgs<flo
 __global__ void __launch_bounds__(256) k_splitk_reduce(const float *ws, int splits, int batch, int M, int N,
                                                         EpiArgs<float> e)
 {
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
     const long per = (long)M * N, tot = per * batch;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long)gridDim.x * blockDim.x) {
         float v = 0.0f;
@@ -237,6 +270,8 @@ __device__ __forceinline__ double block_sum(double v, double *sm)
 template <typename T>
 __global__ void k_colsum(const T *d, long rows, int cols, long d_b, T *out, long out_b)
 {
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
     __shared__ double sm[8][33];
     const int b = blockIdx.y;
     const int col = blockIdx.x * 32 + threadIdx.x;
@@ -266,18 +301,39 @@ void launch_gemm(const GemmArgs<T> &g, const EpiArgs<T> &e, int batch, cudaStrea
         const int kchunk = splits > 1 ? ((g.K + splits - 1) / splits + GB_K - 1) / GB_K * GB_K : std::max(g.K, 1);
         dim3 grid((g.N + GB_N - 1) / GB_N, (g.M + GB_M - 1) / GB_M, batch * splits);
         ProfScope ps("simt_gemm_f32", s);
-        k_gemm_f32<<<grid, 256, 0, s>>>(g, e, ws, splits, kchunk);
+        launch_pdl(k_gemm_f32, grid, dim3(256), 0, s, g, e, ws, splits, kchunk);
         HMC_LAUNCH_CK();
         if (splits > 1) {
             const long tot = (long)batch * g.M * g.N;
-            k_splitk_reduce<<<(unsigned)std::min<long>((tot + 255) / 256, 4096), 256, 0, s>>>(ws, splits, batch, g.M,
-                                                                                             g.N, e);
+            launch_pdl(k_splitk_reduce, dim3((unsigned)std::min<long>((tot + 255) / 256, 4096)), dim3(256), 0, s,
+                       (const float *)ws, splits, batch, g.M, g.N, e);
             HMC_LAUNCH_CK();
         }
     } else {
         dim3 grid((g.N + 15) / 16, (g.M + 15) / 16, batch);
         ProfScope ps("simt_gemm_f64", s);
-        k_gemm16<T><<<grid, 256, 0, s>>>(g, e);
+        launch_pdl(k_gemm16<T>, grid, dim3(256), 0, s, g, e);
         HMC_LAUNCH_CK();
     }
+}
+
+// A weight gradient dW = delta^T A (K = the data rows): FP64 ones with few outputs and a
+// long K take one warp per output (k_gemm_dot), and then also form the row sums of delta
+// (the bias gradient) into rsum when it is set, returning true; everything else is
+// launch_gemm's, and the caller sums the bias gradient itself (false).
+template <typename T>
+bool launch_wgrad(const GemmArgs<T> &g, const EpiArgs<T> &e, int batch, cudaStream_t s, float *ws, size_t ws_floats,
+                  T *rsum = nullptr, long rsum_b = 0)
+{
+    if constexpr (sizeof(T) == 8) {
+        if (g.M > 0 && g.N > 0 && g.K >= 128 && (long)g.M * g.N <= 1024) {
+            dim3 grid((unsigned)(((long)g.M * (g.N + (rsum ? 1 : 0)) + 7) / 8), batch);
+            ProfScope ps("simt_wgrad_f64", s);
+            launch_pdl(k_gemm_dot<T>, grid, dim3(256), 0, s, g, e, rsum, rsum_b);
+            HMC_LAUNCH_CK();
+            return true;
+        }
+    }
+    launch_gemm(g, e, batch, s, ws, ws_floats);
+    return false;
 }

@@ -55,7 +55,7 @@ typedef enum {
     HMC_ERR_OOM = 3,          /* device allocation failed */
     HMC_ERR_NONFINITE = 4,    /* U was NaN or +-Inf (outputs are still written) */
     HMC_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out */
-    HMC_ERR_UNSUPPORTED = 6   /* valid request this build does not implement */
+    HMC_ERR_UNSUPPORTED = 6   /* a valid request the library does not implement */
 } hmc_status;
 
 typedef enum { HMC_ACT_IDENTITY = 0, HMC_ACT_TANH = 1, HMC_ACT_SIN = 2 } hmc_act;

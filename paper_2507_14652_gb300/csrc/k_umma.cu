@@ -3214,6 +3214,11 @@ class DonEngine final : public Engine {
         HMC_CK(cudaStreamCreateWithFlags(&s2_, cudaStreamNonBlocking));
         HMC_CK(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
         HMC_CK(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
+        for (int t = 0; t < 2; ++t) {
+            HMC_CK(cudaStreamCreateWithFlags(&sw_[t], cudaStreamNonBlocking));
+            HMC_CK(cudaEventCreateWithFlags(&evw_fork_[t], cudaEventDisableTiming));
+            HMC_CK(cudaEventCreateWithFlags(&evw_join_[t], cudaEventDisableTiming));
+        }
         HMC_CK(cudaMalloc(&err_, sizeof(int)));
         HMC_CK(cudaMemset(err_, 0, sizeof(int)));
         setup_net(br_, p.branch, p.u, nu_);
@@ -3275,6 +3280,11 @@ class DonEngine final : public Engine {
         if (ev_fork_) cudaEventDestroy(ev_fork_);
         if (ev_join_) cudaEventDestroy(ev_join_);
         if (s2_) cudaStreamDestroy(s2_);
+        for (int t = 0; t < 2; ++t) {
+            if (evw_fork_[t]) cudaEventDestroy(evw_fork_[t]);
+            if (evw_join_[t]) cudaEventDestroy(evw_join_[t]);
+            if (sw_[t]) cudaStreamDestroy(sw_[t]);
+        }
     }
 
     ScatterPlan scatter_plan() override { return plan_; }
@@ -3388,8 +3398,8 @@ class DonEngine final : public Engine {
             launch_umma<M_GEMM_BF16, true, true, false>(ds_atom_, br_.act_atom[br_.L], br_.act_atom[br_.L], pp,
                                                          dim3(tr_.ntiles, 1, C_), st);
         }
-        backward(br_, s);
-        backward(tr_, st);
+        backward(br_, s, active_profiler() ? s : sw_[0], 0);
+        backward(tr_, st, active_profiler() ? st : sw_[1], 1);
         join(s, st);
         FinalArgs fa{};
         fa.k = (int)k_;
@@ -3705,13 +3715,23 @@ class DonEngine final : public Engine {
         }
     }
 
-    void backward(DonNet &n, cudaStream_t s)
+    // The reverse pass of net n on stream s.  The weight gradient of layer l reads D_{l+1}
+    // and A_l, which nothing later in the pass writes, and writes only its own entries'
+    // partials: it runs on the side stream sw (t: the net's fork and join events), which
+    // joins s again at the end of the pass (sw == s while a per-kernel profile runs).
+    void backward(DonNet &n, cudaStream_t s, cudaStream_t sw, int t)
     {
         const NetDesc &nd = *n.nd;
         const int total_kb = (int)((n.R + BK - 1) / BK);
+        bool forked = false;
         for (int l = n.L - 1; l >= 0; --l) {
             // sampled entries of dW_l = D_{l+1}^T A_l
             if (n.entries[l] > 0 && (l >= 1 || n.gemm_first)) {
+                if (sw != s) {
+                    HMC_CK(cudaEventRecord(evw_fork_[t], s));
+                    HMC_CK(cudaStreamWaitEvent(sw, evw_fork_[t], 0));
+                    forked = true;
+                }
                 Params pp = base();
                 pp.M = nd.w[l + 1];
                 pp.N = (l >= 1) ? nd.w[l] : (int)round_up(n.dx, 64);
@@ -3727,7 +3747,7 @@ class DonEngine final : public Engine {
                 const int splits = (total_kb + n.kb_split - 1) / n.kb_split;
                 const CUtensorMap &b = (l >= 1) ? n.act_atom[l] : n.x_atom;
                 launch_umma<M_DW, true, true, false>(n.del_atom[l + 1], b, b, pp,
-                                                     dim3((pp.M + BM - 1) / BM, splits, C_), s);
+                                                     dim3((pp.M + BM - 1) / BM, splits, C_), sw);
             }
             if (l == 0 || l <= nd.lmin) break;   // no delta is needed below layer l
             // D_l = (D_{l+1} W_l) (1 - A_l^2); its column sums are the bias gradient of layer l-1
@@ -3790,6 +3810,10 @@ class DonEngine final : public Engine {
                 pp.out_b = n.R * pp.N;
                 launch_umma<M_BWD_TANH, false, true, true>(n.del_row[l + 1], n.w_atom_h[l], n.w_atom_l[l], pp, grid, s);
             }
+        }
+        if (forked) {
+            HMC_CK(cudaEventRecord(evw_join_[t], sw));
+            HMC_CK(cudaStreamWaitEvent(s, evw_join_[t], 0));
         }
     }
 
@@ -3944,6 +3968,8 @@ class DonEngine final : public Engine {
     int max_clusters_ = 0;             // pair-kernel CTA pairs resident at once (0: no pair layer)
     cudaStream_t s2_ = nullptr;        // the trunk's stream inside an evaluation
     cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
+    cudaStream_t sw_[2] = {nullptr, nullptr};   // the branch's and the trunk's weight gradients
+    cudaEvent_t evw_fork_[2] = {nullptr, nullptr}, evw_join_[2] = {nullptr, nullptr};
     DevBuf u_acc_;
     ScatterPlan plan_;
     std::string tuning_;

@@ -385,28 +385,30 @@ template <typename T> class SimtEngine final : public Engine {
             const int wi = nd.w[l], wo = nd.w[l + 1];
             const T *ap = l == 0 ? in : nb.act[l]->template as<T>();
             const long ap_b = l == 0 ? in_b : rows * wi;
-            bool db_done;
-            {   // dW_l = delta_l^T A_{l-1} (and db_l = delta_l^T 1 where the kernel takes it)
-                GemmArgs<T> ga{wo, wi, (int)rows, d, 1, wo, rows * wo, ap, wi, 1, ap_b};
-                EpiArgs<T> ea{EPI_STORE, G + nd.woff[l], wi, 1, P, nullptr, 0, 0, 0, nullptr};
-                db_done = launch_wgrad(ga, ea, C_, s, ws_.template as<float>(), ws_floats_,
-                                       nd.boff[l] >= 0 ? G + nd.boff[l] : nullptr, P) &&
-                          nd.boff[l] >= 0;
-            }
-            if (nd.boff[l] >= 0 && !db_done) {
+            // dW_l = delta_l^T A_{l-1} (and db_l = delta_l^T 1 where the kernel takes it)
+            GemmArgs<T> gw{wo, wi, (int)rows, d, 1, wo, rows * wo, ap, wi, 1, ap_b};
+            EpiArgs<T> ew{EPI_STORE, G + nd.woff[l], wi, 1, P, nullptr, 0, 0, 0, nullptr};
+            T *rs = nd.boff[l] >= 0 ? G + nd.boff[l] : nullptr;
+            // delta_{l-1} = (delta_l W_l) * act'(Z_{l-1}), when a layer below needs it
+            T *nx = delta_[pp].as<T>();
+            if (nx == d) nx = delta_[pp ^ 1].as<T>();
+            const bool id = l > 0 && nd.act[l - 1] == HMC_ACT_IDENTITY;
+            GemmArgs<T> gd{(int)rows, wi, wo, d, wo, 1, rows * wo, theta + nd.woff[l], wi, 1, P};
+            EpiArgs<T> ed{id ? EPI_STORE : EPI_SCALE, nx, wi, 1, rows * wi, nullptr, 0, 0, 0,
+                          id || l == 0 ? nullptr : nb.slope[l]->template as<T>()};
+            // both read delta_l only: one launch where the FP64 kernels allow it
+            const bool both = l > nd.lmin && launch_wgrad_and_delta(gw, ew, rs, P, gd, ed, C_, s);
+            const bool db_done = both ? rs != nullptr
+                                      : launch_wgrad(gw, ew, C_, s, ws_.template as<float>(), ws_floats_, rs, P) &&
+                                            rs != nullptr;
+            if (rs && !db_done) {
                 dim3 grid((wo + 31) / 32, C_);
                 ProfScope ps("simt_colsum", s);
-                launch_pdl(k_colsum<T>, grid, dim3(32, 8), 0, s, (const T *)d, rows, wo, rows * wo, G + nd.boff[l], P);
+                launch_pdl(k_colsum<T>, grid, dim3(32, 8), 0, s, (const T *)d, rows, wo, rows * wo, rs, P);
                 HMC_LAUNCH_CK();
             }
-            if (l > nd.lmin) {   // delta_{l-1} = (delta_l W_l) * act'(Z_{l-1})
-                T *nx = delta_[pp].as<T>();
-                if (nx == d) nx = delta_[pp ^ 1].as<T>();
-                GemmArgs<T> ga{(int)rows, wi, wo, d, wo, 1, rows * wo, theta + nd.woff[l], wi, 1, P};
-                const bool id = nd.act[l - 1] == HMC_ACT_IDENTITY;
-                EpiArgs<T> ea{id ? EPI_STORE : EPI_SCALE, nx, wi, 1, rows * wi, nullptr, 0, 0, 0,
-                              id ? nullptr : nb.slope[l]->template as<T>()};
-                launch_gemm(ga, ea, C_, s, ws_.template as<float>(), ws_floats_);
+            if (l > nd.lmin) {
+                if (!both) launch_gemm(gd, ed, C_, s, ws_.template as<float>(), ws_floats_);
                 d = nx;
                 pp ^= 1;
             }

@@ -59,14 +59,11 @@ __device__ __forceinline__ void gemm_epilogue(const EpiArgs<T> &e, int b, long m
 // little on the small shapes the FP64 engine serves (a 20 x 20 weight gradient filled 10%
 // of a 64 x 64 tile).  Each output sums K in order, so results are reproducible.
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemm16(GemmArgs<T> g, EpiArgs<T> e)
+__device__ __forceinline__ void gemm16_body(const GemmArgs<T> &g, const EpiArgs<T> &e, int bx, int by, int b)
 {
-    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
-    pdl_trigger();
     __shared__ T As[16][17];
     __shared__ T Bs[16][17];
-    const int b = blockIdx.z;
-    const long m0 = (long)blockIdx.y * 16, n0 = (long)blockIdx.x * 16;
+    const long m0 = (long)by * 16, n0 = (long)bx * 16;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const T *A = g.A + (long)b * g.a_b;
     const T *B = g.B + (long)b * g.b_b;
@@ -90,6 +87,14 @@ __global__ void __launch_bounds__(256) k_gemm16(GemmArgs<T> g, EpiArgs<T> e)
     gemm_epilogue(e, b, m, n, acc);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm16(GemmArgs<T> g, EpiArgs<T> e)
+{
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
+    gemm16_body(g, e, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // FP64 reductions with few outputs and a long K (a small layer's weight gradient, whose K
 // is the data rows): one warp per output, its lanes taking every 32nd k with two
 // accumulators, then a fixed butterfly, so the result is reproducible.  On 16 x 16 tiles
@@ -98,13 +103,12 @@ __global__ void __launch_bounds__(256) k_gemm16(GemmArgs<T> g, EpiArgs<T> e)
 // With rsum set, each row m also gets an extra output n = N whose B column is all ones,
 // rsum[b rsum_b + m] = sum_k A(m, k) (a layer's bias gradient beside its weight gradient).
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemm_dot(GemmArgs<T> g, EpiArgs<T> e, T *rsum, long rsum_b)
+__device__ __forceinline__ void gemm_dot_body(const GemmArgs<T> &g, const EpiArgs<T> &e, T *rsum, long rsum_b, int bx,
+                                              int b)
 {
-    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
-    pdl_trigger();
-    const int b = blockIdx.y, lane = threadIdx.x % 32;
+    const int lane = threadIdx.x % 32;
     const int nc = g.N + (rsum ? 1 : 0);   // outputs per row
-    const long o = (long)blockIdx.x * 8 + threadIdx.x / 32;
+    const long o = (long)bx * 8 + threadIdx.x / 32;
     if (o >= (long)g.M * nc) return;   // the warp leaves together
     const long m = o / nc, n = o % nc;
     const bool ones = n == g.N;
@@ -124,6 +128,28 @@ __global__ void __launch_bounds__(256) k_gemm_dot(GemmArgs<T> g, EpiArgs<T> e, T
     if (lane != 0) return;
     if (ones) rsum[(long)b * rsum_b + m] = acc;
     else gemm_epilogue(e, b, m, n, acc);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_dot(GemmArgs<T> g, EpiArgs<T> e, T *rsum, long rsum_b)
+{
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
+    gemm_dot_body(g, e, rsum, rsum_b, blockIdx.x, blockIdx.y);
+}
+
+// A weight gradient one warp per output (g1, e1, rsum) and the next delta GEMM on 16 x 16
+// tiles (g2, e2), which read the same delta and write different arrays, in one launch:
+// blocks [0, nb1) take the former, the others the latter's tiles, nx2 of them across.
+template <typename T>
+__global__ void __launch_bounds__(256) k_wgrad_and_gemm16(GemmArgs<T> g1, EpiArgs<T> e1, T *rsum, long rsum_b, int nb1,
+                                                          GemmArgs<T> g2, EpiArgs<T> e2, int nx2)
+{
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
+    const int x = blockIdx.x;
+    if (x < nb1) gemm_dot_body(g1, e1, rsum, rsum_b, x, blockIdx.y);
+    else gemm16_body(g2, e2, (x - nb1) % nx2, (x - nb1) / nx2, blockIdx.y);
 }
 
 // FP32: C[b](m, n) = sum_k A[b](m, k) B[b](k, n) on 128 x 128 tiles, 16-deep K stages
@@ -321,12 +347,17 @@ void launch_gemm(const GemmArgs<T> &g, const EpiArgs<T> &e, int batch, cudaStrea
 // long K take one warp per output (k_gemm_dot), and then also form the row sums of delta
 // (the bias gradient) into rsum when it is set, returning true; everything else is
 // launch_gemm's, and the caller sums the bias gradient itself (false).
+template <typename T> bool wgrad_by_warps(const GemmArgs<T> &g)
+{
+    return sizeof(T) == 8 && g.M > 0 && g.N > 0 && g.K >= 128 && (long)g.M * g.N <= 1024;
+}
+
 template <typename T>
 bool launch_wgrad(const GemmArgs<T> &g, const EpiArgs<T> &e, int batch, cudaStream_t s, float *ws, size_t ws_floats,
                   T *rsum = nullptr, long rsum_b = 0)
 {
     if constexpr (sizeof(T) == 8) {
-        if (g.M > 0 && g.N > 0 && g.K >= 128 && (long)g.M * g.N <= 1024) {
+        if (wgrad_by_warps(g)) {
             dim3 grid((unsigned)(((long)g.M * (g.N + (rsum ? 1 : 0)) + 7) / 8), batch);
             ProfScope ps("simt_wgrad_f64", s);
             launch_pdl(k_gemm_dot<T>, grid, dim3(256), 0, s, g, e, rsum, rsum_b);
@@ -335,5 +366,25 @@ bool launch_wgrad(const GemmArgs<T> &g, const EpiArgs<T> &e, int batch, cudaStre
         }
     }
     launch_gemm(g, e, batch, s, ws, ws_floats);
+    return false;
+}
+
+// The weight gradient (g1, e1, rsum as for launch_wgrad) and the next delta GEMM (g2, e2)
+// in one launch where both are FP64 and the first goes one warp per output; returns false
+// (nothing launched) otherwise.
+template <typename T>
+bool launch_wgrad_and_delta(const GemmArgs<T> &g1, const EpiArgs<T> &e1, T *rsum, long rsum_b, const GemmArgs<T> &g2,
+                            const EpiArgs<T> &e2, int batch, cudaStream_t s)
+{
+    if constexpr (sizeof(T) == 8) {
+        if (wgrad_by_warps(g1) && g2.M > 0 && g2.N > 0) {
+            const int nb1 = (int)(((long)g1.M * (g1.N + (rsum ? 1 : 0)) + 7) / 8);
+            const int nx2 = (g2.N + 15) / 16, ny2 = (g2.M + 15) / 16;
+            ProfScope ps("simt_wgrad_delta_f64", s);
+            launch_pdl(k_wgrad_and_gemm16<T>, dim3((unsigned)(nb1 + nx2 * ny2), batch), dim3(256), 0, s, g1, e1, rsum,
+                       rsum_b, nb1, g2, e2, nx2);
+            return true;
+        }
+    }
     return false;
 }

@@ -50,6 +50,42 @@ __global__ void __launch_bounds__(256) k_residual(const T *f, long f_b, const T 
 }
 
 
+// The output layer and the residual in one pass (small output layers in FP64): element
+// (row m, output o) of chain b, z = sum_k A[b][m][k] W[b][o][k] + bias[b][o] (k in order,
+// as the GEMM sums it), f = act(z), r = f - y, delta = r / sigma^2 act'(z), and the
+// block's sum of r^2 (FP64) as k_residual forms it.
+template <typename T>
+__global__ void __launch_bounds__(256) k_out_residual(const T *A, long a_b, int K, const T *W, const T *bias, long P,
+                                                      int act, const T *y, long rows, int dout, double inv_s2,
+                                                      T *delta, double *part_r2, int nparts)
+{
+    pdl_wait();   // under launch_pdl: the kernel before it has finished (else a no-op)
+    pdl_trigger();
+    __shared__ double sm[8];
+    const int b = blockIdx.y;
+    const long n_el = rows * dout;
+    double r2 = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n_el; i += (long)gridDim.x * blockDim.x) {
+        const long m = i / dout;
+        const int o = (int)(i % dout);
+        const T *a = A + (long)b * a_b + m * K;
+        const T *w = W + (long)b * P + (long)o * K;
+        T z = T(0);
+        for (int k = 0; k < K; ++k) z += a[k] * w[k];
+        if (bias) z += bias[(long)b * P + o];
+        T f, sl;
+        act_eval(act, z, f, sl);
+        const T r = f - y[i];
+        const double rd = (double)r;
+        r2 += rd * rd;
+        T d = (T)(rd * inv_s2);
+        if (act != HMC_ACT_IDENTITY) d = d * sl;
+        delta[(long)b * n_el + i] = d;
+    }
+    const double t = block_sum<256>(r2, sm);
+    if (threadIdx.x == 0) part_r2[(long)b * nparts + blockIdx.x] = t;
+}
+
 template <typename T>
 __global__ void k_scatter(const T *q, const int *idx, long k, T *theta, long P)
 {
@@ -256,10 +292,22 @@ template <typename T> class SimtEngine final : public Engine {
         const double inv_s2 = 1.0 / (p_.sigma * p_.sigma);
         if (p_.kind == HMC_NET_MLP) {
             const NetDesc &nd = p_.net;
-            forward(nd, x_.as<T>(), 0, p_.n, netb_, s);
-            T *f = netb_.act[nd.L]->template as<T>();
-            const T *sl = nd.act[nd.L - 1] == HMC_ACT_IDENTITY ? nullptr : netb_.slope[nd.L]->template as<T>();
-            residual(f, p_.n * p_.dout, y_.as<T>(), sl, inv_s2, delta_[0].as<T>(), false, s);
+            if (sizeof(T) == 8 && p_.dout <= 8) {   // the output layer and the residual in one launch
+                forward(nd, x_.as<T>(), 0, p_.n, netb_, s, nd.L - 1);
+                const int l = nd.L - 1;
+                const T *a = l > 0 ? netb_.act[l]->template as<T>() : x_.as<T>();
+                ProfScope ps("simt_out_residual", s);
+                launch_pdl(k_out_residual<T>, dim3(nparts_, C_), dim3(256), 0, s, a, l > 0 ? p_.n * nd.w[l] : 0L,
+                           nd.w[l], (const T *)(theta + nd.woff[l]),
+                           (const T *)(nd.boff[l] >= 0 ? theta + nd.boff[l] : nullptr), P, nd.act[l],
+                           (const T *)y_.as<T>(), p_.n, p_.dout, inv_s2, delta_[0].as<T>(), part_r2_.as<double>(),
+                           nparts_);
+            } else {
+                forward(nd, x_.as<T>(), 0, p_.n, netb_, s);
+                T *f = netb_.act[nd.L]->template as<T>();
+                const T *sl = nd.act[nd.L - 1] == HMC_ACT_IDENTITY ? nullptr : netb_.slope[nd.L]->template as<T>();
+                residual(f, p_.n * p_.dout, y_.as<T>(), sl, inv_s2, delta_[0].as<T>(), false, s);
+            }
             if (nd.any_sampled && g) backward(nd, x_.as<T>(), 0, p_.n, netb_, delta_[0].as<T>(), s);
         } else {
             const NetDesc &bn = p_.branch, &tn = p_.trunk;
@@ -355,13 +403,14 @@ template <typename T> class SimtEngine final : public Engine {
         }
     }
 
-    void forward(const NetDesc &nd, const T *in, long in_b, long rows, NetBufs<T> &nb, cudaStream_t s)
+    // layers 0 .. upto - 1 (all of them when upto < 0)
+    void forward(const NetDesc &nd, const T *in, long in_b, long rows, NetBufs<T> &nb, cudaStream_t s, int upto = -1)
     {
         const long P = p_.P;
         T *theta = theta_.as<T>();
         const T *a = in;
         long a_b = in_b;
-        for (int l = 0; l < nd.L; ++l) {
+        for (int l = 0; l < (upto < 0 ? nd.L : upto); ++l) {
             const int wi = nd.w[l], wo = nd.w[l + 1];
             GemmArgs<T> ga{(int)rows, wo, wi, a, wi, 1, a_b, theta + nd.woff[l], 1, wi, P};
             EpiArgs<T> ea{EPI_ACT, nb.act[l + 1]->template as<T>(), wo, 1, rows * wo,

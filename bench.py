@@ -204,6 +204,11 @@ def other_workloads(hmc, torch, steps=3):
                "grad_evals_per_s": chains_total * L / (ms / 1000.0),
                "accept_rate": float(acc.float().mean().item()),
                "abs_dH_median": float(np.nanmedian(np.abs(dH.cpu().numpy())))}
+        # kernels in one captured trajectory, and the time per kernel they average to (a
+        # few microseconds apiece marks a workload bound by launches rather than bytes)
+        kern = int(hmc.graph_kernels(sp))
+        if kern > 0:
+            rec.update({"kernels_per_trajectory": kern, "us_per_kernel": 1000.0 * ms / kern})
         if ess_traj:
             torch.cuda.synchronize()
             a.record()
